@@ -1,0 +1,178 @@
+/*
+ * dichotomy.h -- C ABI of the GB300 (sm_103a) Dichotomy solver for tridiagonal
+ * Toeplitz systems  T x = F,  T = tridiag{t_-1, t_0, t_1}   (arXiv 1002.2469, eq. 1).
+ *
+ * Conventions shared by every entry point
+ *   - Rows are 0-based: row i reads t_-1 x[i-1] + t_0 x[i] + t_1 x[i+1] = F[i], with
+ *     x[-1] = x[N] = 0 (the Dirichlet ends of eq. 22).  t_-1 is the sub-diagonal (the
+ *     paper's c_i, eq. 2), t_1 the super-diagonal (the paper's a_i).
+ *   - Pointers named d_* are CUDA device pointers; h_* are host pointers.  FP64 vectors
+ *     are contiguous, 8-byte aligned, and not aliased with each other (x may not alias F:
+ *     DICH_ERR_ALIAS).  Host pointers passed where device pointers are required are
+ *     rejected with DICH_ERR_ARG; the library has no CPU fallback.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
+ *     Solve/adjoint calls only enqueue work: they never synchronize, never allocate
+ *     device memory and are safe to capture in a CUDA graph once the plan is bound.
+ *   - Device memory is owned by the caller.  The library owns only host-side plan
+ *     objects (freed by dichotomy_destroy / dichotomy_batch_destroy).
+ *   - Every function returns a dich_status (0 = DICH_OK).  Errors detected on the GPU
+ *     (non-finite output, plan/schedule mismatch) are latched in a device status word
+ *     inside the workspace and read back with dichotomy_status().
+ *
+ * The method (what each call computes)
+ *   N rows are split into P blocks of n rows (the last block takes the remainder; every
+ *   block has >= 2 rows, Sec. 2.1).  The Toeplitz preliminary calculation (Sec. 3.1,
+ *   Theorem 1 / eq. 20, in the exact factored form of eq. 24-25) is done once per
+ *   (t, n): recurrence roots, the two boundary spikes of the block operator T_n and the
+ *   O(1) per-block exterior ratios Z (eq. 10-12).  A solve then (a) sweeps every block
+ *   locally, giving beta^{L,R}_m of eq. 16, (b) computes the first/last value of every
+ *   block from eq. 15 as two affine scans over blocks -- the log2 P dichotomy tree of
+ *   eq. 17-19, mapped onto warp shuffles, shared memory and the grid -- and (c) applies
+ *   the basis correction that solves every block interior (eq. 7).  The result is
+ *   x = T^-1 F up to rounding.
+ */
+#ifndef DICHOTOMY_H_
+#define DICHOTOMY_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+typedef enum {
+  DICH_OK = 0,
+  DICH_ERR_ARG = 1,           /* bad size, NULL / host / misaligned pointer, bad option */
+  DICH_ERR_NOT_DOMINANT = 2,  /* |t_0| < |t_-1| + |t_1|: eq. 32-33 fails (not supported) */
+  DICH_ERR_SINGULAR = 3,      /* t_0 = 0 with dominance, or a zero block pivot (Theorem 1) */
+  DICH_ERR_TIMEOUT = 4,       /* a bounded device wait ran out (reserved) */
+  DICH_ERR_NONFINITE = 5,     /* a NaN/Inf was produced on the device */
+  DICH_ERR_CUDA = 6,          /* a CUDA runtime call failed; see dichotomy_last_cuda_error */
+  DICH_ERR_ALIAS = 7,         /* output aliases an input */
+  DICH_ERR_UNBOUND = 8,       /* solve called before the plan was bound to a workspace */
+  DICH_ERR_WORKSPACE = 9,     /* workspace too small or misaligned */
+  DICH_ERR_SCHEDULE = 10,     /* batch coefficients at solve time need a larger schedule */
+  DICH_ERR_UNSUPPORTED = 11   /* combination not supported by this build */
+} dich_status;
+
+/* ---------------------------------------------------------------- options */
+typedef enum {
+  DICH_PREC_F64 = 0,    /* every step in FP64 */
+  DICH_PREC_MIXED = 1,  /* local sweeps in FP32 with error-free transformations (compensated),
+                           interface tree, beta and scan coefficients in FP64 */
+  DICH_PREC_AUTO = 2    /* MIXED where its error bound is below 1e-13 relative, else F64 */
+} dich_precision;
+
+enum {
+  DICH_FLAG_FORCE_GENERAL = 1,  /* never truncate cross-tile coupling (3-kernel path) */
+  DICH_FLAG_CHECK_FINITE = 2    /* latch DICH_ERR_NONFINITE if any output is not finite */
+};
+
+typedef struct {
+  int32_t block_size;    /* n, rows per block; 0 = chosen by the library */
+  int32_t precision;     /* dich_precision */
+  int32_t threads;       /* window width in blocks (CTA size): 0 = default; 64, 128 or 256 */
+  int32_t flags;         /* DICH_FLAG_* */
+  double trunc_eps;      /* relative truncation of geometrically small terms; 0 = 2^-64 */
+} dich_opts;
+
+/* Read-only description of a plan (for tests, tuning and reporting). */
+typedef struct {
+  int64_t N, P;            /* rows, blocks */
+  int32_t n, n_last;       /* block size, size of the last block */
+  int32_t threads;         /* CTA width (window blocks) */
+  int32_t halo_l, halo_r;  /* halo blocks per window (0 on the general path) */
+  int32_t path;            /* 0 = single window, 1 = halo windows, 2 = general 3-kernel */
+  int32_t precision;       /* effective dich_precision (F64 or MIXED) */
+  int64_t tiles;           /* CTAs per solve */
+  int32_t Lv, Lw;          /* truncated lengths of the block spikes */
+  int32_t kl, kr;          /* blocks with end-dependent coefficients at the left/right end */
+  double rs, ib;           /* roots: |rs| <= 1 <= |1/ib| of t_1 r^2 + t_0 r + t_-1 = 0 */
+  double z;                /* rs * ib */
+  size_t workspace_bytes;
+} dich_plan_info;
+
+typedef struct dich_plan_s* dich_plan_t;
+typedef struct dich_batch_s* dich_batch_t;
+
+/* ---------------------------------------------------------------- single system */
+
+/* Build a plan for one N x N system (host only, no GPU work).  Performs the paper's
+ * Toeplitz preliminary step (Sec. 3.1-3.3): validates diagonal dominance (eq. 32-33,
+ * equality accepted), computes the recurrence roots of Theorem 1, the truncation lengths,
+ * the spikes of the block operator and the per-block exterior ratios (eq. 24-25 in
+ * overflow-free factored form).  N = 0 and N = 1 are accepted (trivial solves).
+ * Errors: DICH_ERR_ARG (N < 0, out == NULL, bad opts), DICH_ERR_NOT_DOMINANT,
+ * DICH_ERR_SINGULAR (t_0 == 0).  On error *out is set to NULL. */
+int dichotomy_plan(double t_m1, double t_0, double t_1, int64_t N, dich_plan_t* out);
+int dichotomy_plan_ex(double t_m1, double t_0, double t_1, int64_t N, const dich_opts* opts,
+                      dich_plan_t* out);
+
+/* Describe a plan.  Errors: DICH_ERR_ARG. */
+int dichotomy_plan_info(dich_plan_t plan, dich_plan_info* info);
+
+/* Bytes of device workspace the plan needs (256-byte aligned region). */
+int dichotomy_plan_workspace_bytes(dich_plan_t plan, size_t* bytes);
+
+/* Attach a caller-owned device workspace of at least dichotomy_plan_workspace_bytes
+ * bytes (256-byte aligned) and upload the plan tables into it on `stream`
+ * (one cudaMemcpyAsync from a host staging copy held by the plan; the status word is
+ * cleared).  Must precede solve/adjoint; may be called again to move the plan.
+ * Errors: DICH_ERR_ARG, DICH_ERR_WORKSPACE, DICH_ERR_CUDA. */
+int dichotomy_plan_bind(dich_plan_t plan, void* d_workspace, size_t bytes, void* stream);
+
+/* x = T^-1 F for the bound plan.  d_F, d_x: N doubles each on the device, no aliasing.
+ * Enqueues one kernel (single/halo path) or three (general path) on `stream`.
+ * Errors: DICH_ERR_ARG, DICH_ERR_ALIAS, DICH_ERR_UNBOUND, DICH_ERR_CUDA (launch). */
+int dichotomy_solve(dich_plan_t plan, const double* d_F, double* d_x, void* stream);
+
+/* Adjoint of L(x) with x = T^-1 F, given d_w = dL/dx and the forward solution d_x:
+ *   d_gF = lambda = T^-T w   (the same Dichotomy solve for T^T = tridiag{t_1, t_0, t_-1}),
+ *   d_gt[0..2] = (dL/dt_-1, dL/dt_0, dL/dt_1) = -(sum_i lambda_i x_{i-1},
+ *                sum_i lambda_i x_i, sum_i lambda_i x_{i+1}).
+ * Not in the paper.  d_gt is 3 doubles on the device.  d_gF may not alias d_w or d_x. */
+int dichotomy_adjoint(dich_plan_t plan, const double* d_w, const double* d_x, double* d_gF,
+                      double* d_gt, void* stream);
+
+/* Synchronize `stream`, read and clear the device status word of a bound plan.
+ * *device_status receives DICH_OK or the first latched device error. */
+int dichotomy_status(dich_plan_t plan, void* stream, int* device_status);
+
+void dichotomy_destroy(dich_plan_t plan);
+
+/* ---------------------------------------------------------------- batches */
+
+/* A series of independent systems (the paper's eq. 2 series, or separation-of-variables
+ * modes), stored back to back: system s occupies F[offset[s] .. offset[s] + N[s]).
+ * Prepare (host only) runs the preliminary step of every system, chooses block sizes,
+ * the precision form per system (DICH_PREC_AUTO) and an LPT-ordered list of windows.
+ * h_N, h_offset, h_tm1, h_t0, h_tp1: nsys entries each on the host.
+ * Errors: DICH_ERR_ARG, DICH_ERR_NOT_DOMINANT / DICH_ERR_SINGULAR (first bad system). */
+int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_offset,
+                            const double* h_tm1, const double* h_t0, const double* h_tp1,
+                            const dich_opts* opts, dich_batch_t* out);
+int dichotomy_batch_workspace_bytes(dich_batch_t batch, size_t* bytes);
+int dichotomy_batch_bind(dich_batch_t batch, void* d_workspace, size_t bytes, void* stream);
+/* Solve every system of the batch in one launch per precision form. */
+int dichotomy_solve_batched(dich_batch_t batch, const double* d_F, double* d_x, void* stream);
+/* Batched adjoint: d_gF like d_x; d_gt is nsys x 3 doubles (dL/dt_-1, dL/dt_0, dL/dt_1). */
+int dichotomy_adjoint_batched(dich_batch_t batch, const double* d_w, const double* d_x,
+                              double* d_gF, double* d_gt, void* stream);
+int dichotomy_batch_status(dich_batch_t batch, void* stream, int* device_status);
+/* Systems, windows and the precision form chosen per system (nsys int32, 0 = F64, 1 = MIXED). */
+int dichotomy_batch_info(dich_batch_t batch, int64_t* nsys, int64_t* windows, int32_t* h_form);
+void dichotomy_batch_destroy(dich_batch_t batch);
+
+/* ---------------------------------------------------------------- misc */
+const char* dichotomy_strerror(int status);
+/* The last CUDA error string seen by this thread (empty if none). */
+const char* dichotomy_last_cuda_error(void);
+/* Library version, e.g. "0.1.0". */
+const char* dichotomy_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DICHOTOMY_H_ */
