@@ -1,0 +1,367 @@
+"""Benchmark of the Dichotomy solve on GB300 (one JSON line on stdout, rank 0).
+
+Default workload (N = 1 GPU): the single large non-symmetric Toeplitz system
+tridiag{-1.2, 2.5, -0.8}, N = 2^26, F ~ N(0, 1) from seed 0.  A "step" is one solve of that
+system (the local sweeps, the dichotomy tree and the basis correction -- Stage 2 of the
+paper, Table 1) with the plan (Stage 1, the Toeplitz preliminary step) built before the
+timed region; Stage 1's host time is reported beside it as `plan_us`.  `value` is the
+precision form chosen by the library's AUTO policy (compensated-FP32 sweeps, FP64 tree)
+which meets the 1e-12 bar on this system; the plain FP64 solve is timed the same way and
+reported under `fp64_plain`.  Both errors against the CPU oracle are measured every run.
+
+Inputs (512 MB each for F and x) are larger than the 129 MB L2, so no flush is needed.
+Under torchrun (N > 1) every rank solves its own system of the same size: the solve does
+not shard, so the GPUs run replicas ("scaling": "weak"), timed with a barrier and the max
+over ranks.
+
+`--impl reference` times the CPU oracle (the sequential FP64 Thomas algorithm, one core)
+on the same workload as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "single Toeplitz system tridiag{-1.2, 2.5, -0.8}, N=2^26, F~N(0,1) seed 0"
+METRIC = "Gunknowns/s & HBM GB/s (% of 8 TB/s) vs plain FP64 solve, at <=1e-12 rel err"
+N_DEFAULT = 1 << 26
+T = (-1.2, 2.5, -0.8)
+BYTES_PER_UNKNOWN = 16.0   # read F, write x (algorithmic)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _src_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1002_2469_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            d = json.load(fh)
+        ent = d.get(kernel_key)
+        if ent and ent.get("src_hash") == _src_hash():
+            return ent.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_solves(plan, F, x, steps, warmup, world, events_stream):
+    """Device time of `steps` solves (CUDA events on the launching stream, barrier + sync
+    on both sides, max over ranks).  Returns (total ms, per-launch ms list)."""
+    import torch
+    for _ in range(warmup):
+        plan.solve(F, out=x)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(events_stream)
+    for k in range(steps):
+        plan.solve(F, out=x)
+        ev[k + 1].record(events_stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    total = ev[0].elapsed_time(ev[steps])
+    return max_over_ranks(total, world), per
+
+
+def run_gpu(args):
+    import torch
+    import paper_1002_2469_gb300 as D
+    import oracle
+    import workloads as W
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    N = args.n
+    # inputs: generated on the host with numpy (seed 0) so the oracle sees the same bytes
+    t, F_h = W.single_c2(N=N)
+    F = torch.from_numpy(F_h).to(dev)
+    x = torch.empty_like(F)
+    stream = torch.cuda.current_stream()
+
+    results = {}
+    for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
+        t0 = time.perf_counter()
+        plan = D.Plan(*t, N, precision=prec)
+        plan_us = (time.perf_counter() - t0) * 1e6
+        total_ms, per = time_solves(plan, F, x, args.steps, args.warmup, world, stream)
+        st = plan.status()
+        x_h = x.cpu().numpy()
+        results[name] = dict(plan=plan, plan_us=plan_us, total_ms=total_ms, per=per, status=st,
+                             x=x_h, info=plan.info)
+
+    # accuracy against the CPU oracle (the whole vector)
+    x_ref = oracle.thomas(t, F_h)
+    for r in results.values():
+        r["rel_err"] = float(np.max(np.abs(r["x"] - x_ref)) / np.max(np.abs(x_ref)))
+
+    # clocks during a separate timed pass of the headline form
+    head = results["auto"]
+    with ClockSampler(torch.cuda.current_device()) as cs:
+        total_ms2, per2 = time_solves(head["plan"], F, x, max(args.steps, 20), 2, world, stream)
+    clocks = cs.summary()
+
+    # end to end through the public API: host F (pinned) -> plan + solve -> host x, every step
+    F_pin = torch.from_numpy(F_h).pin_memory()
+    x_pin = torch.empty_like(F_pin).pin_memory()
+    Fd = torch.empty_like(F)
+    xd = torch.empty_like(F)
+    for _ in range(2):
+        p = D.Plan(*t, N, precision=D.PREC_AUTO)
+        Fd.copy_(F_pin, non_blocking=True)
+        p.solve(Fd, out=xd)
+        x_pin.copy_(xd, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0 = time.perf_counter()
+    esteps = max(3, min(args.steps, 10))
+    for _ in range(esteps):
+        p = D.Plan(*t, N, precision=D.PREC_AUTO)
+        Fd.copy_(F_pin, non_blocking=True)
+        p.solve(Fd, out=xd)
+        x_pin.copy_(xd, non_blocking=True)
+    torch.cuda.synchronize()
+    e_ms = max_over_ranks((time.perf_counter() - e0) * 1e3 / esteps, world)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(F_h, t, budget_s=args.cpu_seconds)
+
+    if rank != 0:
+        return
+    peak, peak_kind = _peaks()
+    ms = head["total_ms"] / args.steps
+    value = world * N / (ms * 1e-3) / 1e9
+    per_launch = statistics.median(head["per"])
+    achieved = BYTES_PER_UNKNOWN * N / (per_launch * 1e-3) / 1e9
+    f64 = results["fp64_plain"]
+    f64_ms = f64["total_ms"] / args.steps
+    form = "mixed" if head["info"]["precision"] == 1 else "f64"
+    kernel_key = f"k_window_{form}_NT{head['info']['threads']}_N{N}"
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "Gunknowns/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "ff32+f64" if form == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "t": list(t), "precision_form": form,
+                   "block_size": head["info"]["n"], "blocks": head["info"]["P"],
+                   "threads_per_window": head["info"]["threads"], "halo": [head["info"]["halo_l"],
+                                                                          head["info"]["halo_r"]],
+                   "path": ["single", "halo", "general"][head["info"]["path"]], "l2": "inputs > L2 (no flush)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "hbm_gbs": round(achieved, 1),
+        "hbm_pct_of_8tbs": round(100.0 * achieved / 8000.0, 1),
+        "rel_err_vs_oracle": head["rel_err"],
+        "plan_us": round(head["plan_us"], 1),
+        "device_status": head["status"],
+        "fp64_plain": {"value": round(world * N / (f64_ms * 1e-3) / 1e9, 3), "unit": "Gunknowns/s",
+                       "ms_per_step": round(f64_ms, 5), "rel_err_vs_oracle": f64["rel_err"],
+                       "bound": "alu (FP64 pipe)", "block_size": f64["info"]["n"],
+                       "threads_per_window": f64["info"]["threads"], "device_status": f64["status"]},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": _traffic(kernel_key),
+                     "peak_kind": peak_kind, "kernel": kernel_key,
+                     "algorithmic_bytes_per_launch": BYTES_PER_UNKNOWN * N},
+        "e2e": {"value": round(world * N / (e_ms * 1e-3) / 1e9, 3), "unit": "Gunknowns/s",
+                "ms_per_step": round(e_ms, 3), "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
+                "includes": "plan + H2D(F, pinned) + solve + D2H(x, pinned)"},
+        "gpu_launches": args.steps * (3 if head["info"]["path"] == 2 else 1),
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(F_h, t, budget_s=15.0):
+    """The oracle's sequential FP64 Thomas (one core) on the same system, repeated for about
+    budget_s seconds; reported in Gunknowns/s."""
+    import oracle
+    N = F_h.size
+    oracle.thomas(t, F_h[: 1 << 16])
+    done, t0 = 0, time.perf_counter()
+    while True:
+        oracle.thomas(t, F_h)
+        done += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or done >= 64:
+            break
+    return {"value": round(done * N / el / 1e9, 4), "unit": "Gunknowns/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} full solves of the N={N} system (sequential Thomas, FP64)"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed on the host cores for the same workload."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    N = args.n
+    t, F_h = W.single_c2(N=N)
+    for _ in range(args.warmup):
+        oracle.thomas(t, F_h)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.thomas(t, F_h)
+    el = time.perf_counter() - t0
+    ms = el * 1e3 / args.steps
+    value = N / (ms * 1e-3) / 1e9
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": round(value, 4), "unit": "Gunknowns/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "t": list(T), "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "Gunknowns/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full solves of the N={N} system (sequential Thomas, FP64)"},
+        "e2e": {"value": round(value, 4), "unit": "Gunknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,863 @@
+// api.cu -- host planner and the C ABI of include/dichotomy.h.
+//
+// The planner is the paper's preliminary step for Toeplitz matrices (Sec. 3.1-3.3): for a
+// system (t, N) and a block size n it computes the recurrence roots (Theorem 1), the two
+// block spikes of T_n (eq. 25 in factored form), the end-dependent exterior ratios of the
+// first and last few blocks (eq. 24) and the constant ratios of all other blocks -- an
+// O(n + log P) amount of work instead of the O(N) general preliminary step (eq. 9-12).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dichotomy.h"
+#include "launch.cuh"
+
+using namespace dich;
+
+namespace {
+
+thread_local std::string g_cuda_err;
+
+int cuda_fail(cudaError_t e) {
+  g_cuda_err = cudaGetErrorString(e);
+  return DICH_ERR_CUDA;
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// shared-memory budget per CTA so that two CTAs share an SM (load of one window overlaps the
+// compute of the other)
+constexpr size_t kSmemBudget = 110 * 1024;
+// an explicitly requested block size may use up to the per-CTA maximum (one CTA per SM)
+constexpr size_t kSmemMax = 225 * 1024;
+
+int max_rows(int NT, size_t budget) {
+  // window_smem_bytes(NT, n) <= budget
+  int n = 2;
+  while (window_smem_bytes(NT, n + 1) <= budget) ++n;
+  return n;
+}
+
+int default_threads(int form) { return form == FORM_F64 ? 64 : 128; }
+
+int validate_t(double tm1, double t0, double tp1) {
+  if (!std::isfinite(tm1) || !std::isfinite(t0) || !std::isfinite(tp1)) return DICH_ERR_ARG;
+  if (t0 == 0.0) return (tm1 == 0.0 && tp1 == 0.0) ? DICH_ERR_SINGULAR : DICH_ERR_NOT_DOMINANT;
+  const double off = std::fabs(tm1) + std::fabs(tp1);
+  // eq. 32-33: |b| >= |a| + |c| (equality accepted: the end rows are then strict)
+  if (std::fabs(t0) < off * (1.0 - 4.0 * DBL_EPSILON)) return DICH_ERR_NOT_DOMINANT;
+  return DICH_OK;
+}
+
+struct Opts {
+  int n_req = 0;
+  int prec = DICH_PREC_F64;
+  int NT = 0;
+  int flags = 0;
+  double eps = 0x1p-64;
+};
+
+int read_opts(const dich_opts* o, Opts& out) {
+  out = Opts();
+  if (!o) return DICH_OK;
+  if (o->block_size < 0 || o->block_size == 1) return DICH_ERR_ARG;
+  if (o->precision < 0 || o->precision > 2) return DICH_ERR_ARG;
+  if (o->threads != 0 && o->threads != 64 && o->threads != 128 && o->threads != 256) return DICH_ERR_ARG;
+  if (!(o->trunc_eps >= 0.0) || o->trunc_eps >= 1e-3) return DICH_ERR_ARG;
+  out.n_req = o->block_size;
+  out.prec = o->precision;
+  out.NT = o->threads;
+  out.flags = o->flags;
+  if (o->trunc_eps > 0.0) out.eps = o->trunc_eps;
+  return DICH_OK;
+}
+
+// amplification of rounding errors through the two recurrences
+double recurrence_gain(const Roots& r) {
+  const double a = std::fabs(r.rs), b = std::fabs(r.ib);
+  if (a >= 1.0 || b >= 1.0) return INFINITY;
+  return 1.0 / (1.0 - a) + 1.0 / (1.0 - b);
+}
+
+// MIXED (compensated FP32) is used under AUTO when the recurrences amplify rounding
+// errors by at most this factor.
+constexpr double kMixedGainLimit = 24.0;
+
+int pick_form(int prec, const Roots& r) {
+  if (prec == DICH_PREC_F64) return FORM_F64;
+  if (prec == DICH_PREC_MIXED) return FORM_MIXED;
+  return recurrence_gain(r) <= kMixedGainLimit ? FORM_MIXED : FORM_F64;
+}
+
+void split_ff(double d, float& h, float& l) {
+  h = (float)d;
+  l = (float)(d - (double)h);
+}
+
+// Host construction of one system's plan record and tables.
+struct SysBuild {
+  SysPlan rec{};
+  std::vector<double> tab;
+  int path = PATH_SINGLE;
+};
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Choose the block size: one window when the system fits, else the largest rows per block.
+// A last block of a single row is not allowed (Sec. 2.1 asks for sub-vectors of >= 2
+// rows), so n moves to the nearest size (below first, then above) with N mod n != 1.
+int choose_n(int64_t N, int NT, int nmax, int n_req) {
+  int n;
+  if (n_req > 0)
+    n = std::min(n_req, nmax);
+  else if (N <= (int64_t)NT * nmax)
+    n = (int)std::max<int64_t>(2, ceil_div(N, NT));
+  else
+    n = nmax;
+  if (n >= N) return (int)N;
+  auto ok = [&](int c) { return c >= 2 && (c >= N || N % c != 1); };
+  if (ok(n)) return n;
+  for (int d = 1; d < nmax; ++d) {
+    if (n - d >= 2 && ok(n - d)) return n - d;
+    if (n + d <= nmax && ok(n + d)) return (n + d >= N) ? (int)N : n + d;
+  }
+  return (int)std::min<int64_t>(N, nmax);
+}
+
+int build_system(double tm1, double t0, double tp1, int64_t N, int NT, int form, int n, const Opts& o,
+                 bool allow_general, SysBuild& sb) {
+  SysPlan& p = sb.rec;
+  std::memset(&p, 0, sizeof(p));
+  const Roots r = toeplitz_roots(tm1, t0, tp1);
+  if (!r.ok) return DICH_ERR_SINGULAR;
+  p.N = N;
+  p.n = n;
+  p.P = ceil_div(N, n);
+  p.nlast = (int)(N - (p.P - 1) * (int64_t)n);
+  if (p.nlast < 2) return DICH_ERR_ARG;  // guarded by choose_n
+  p.form = form;
+  p.tm1 = tm1;
+  p.t0 = t0;
+  p.tp1 = tp1;
+  p.rs = r.rs;
+  p.ib = r.ib;
+  p.g = r.g;
+  split_ff(r.rs, p.rs_h, p.rs_l);
+  split_ff(r.ib, p.ib_h, p.ib_l);
+  split_ff(r.g, p.g_h, p.g_l);
+
+  // truncation: geometric terms below eps (relative) are dropped; for z < 0 the Q ratios can
+  // exceed 1 by up to 2/(1-|z|), which the threshold absorbs
+  double eps = o.eps;
+  if (r.z < 0.0) eps *= 0.5 * r.omz;
+  const int64_t BIG = (int64_t)1 << 62;
+  const int64_t Ls = decay_len(std::fabs(r.rs), eps, BIG);
+  const int64_t Lb = decay_len(std::fabs(r.ib), eps, BIG);
+  const int64_t Lz = (r.omz == 0.0) ? BIG : decay_len(std::fabs(r.z), eps, BIG);
+  p.Lv = (int)std::min<int64_t>(n, Ls);
+  p.Lw = (int)std::min<int64_t>(n, Lb);
+
+  // path and halos
+  const int64_t P = p.P;
+  if (P <= NT && !(o.flags & DICH_FLAG_FORCE_GENERAL)) {
+    sb.path = PATH_SINGLE;
+    p.hl = p.hr = 0;
+    p.own = (int)P;
+  } else {
+    // the neighbour's first/last value must carry decayed coupling too: +1 row of margin
+    const int64_t hl = (std::fabs(r.rs) == 0.0) ? 1 : (Ls >= BIG ? BIG : std::max<int64_t>(1, ceil_div(Ls + 1, n)));
+    const int64_t hr = (std::fabs(r.ib) == 0.0) ? 1 : (Lb >= BIG ? BIG : std::max<int64_t>(1, ceil_div(Lb + 1, n)));
+    if (!(o.flags & DICH_FLAG_FORCE_GENERAL) && hl + hr <= NT / 2) {
+      sb.path = PATH_HALO;
+      p.hl = (int)hl;
+      p.hr = (int)hr;
+      p.own = NT - (int)hl - (int)hr;
+    } else {
+      if (!allow_general) return DICH_ERR_UNSUPPORTED;
+      sb.path = PATH_GENERAL;
+      p.hl = p.hr = 0;
+      p.own = NT;
+    }
+  }
+
+  // end tables
+  int64_t kl, kr;
+  if (Lz >= BIG) {
+    kl = P;
+    kr = 0;
+  } else {
+    kl = std::min<int64_t>(P, ceil_div(Lz + 1, n) + 1);
+    kr = std::min<int64_t>(P, ceil_div(Lz + 1, n) + 2);
+    if (kl + kr >= P) {
+      kl = P;
+      kr = 0;
+    }
+  }
+  if (kl * kBC > ((int64_t)1 << 30)) return DICH_ERR_UNSUPPORTED;
+  p.kl = (int)kl;
+  p.kr = (int)kr;
+
+  // spikes of the block operator, full blocks (eq. 25 restated: v_i = rs^{i+1} Q(n-i)/Q(n+1))
+  auto vspike = [&](int64_t nb, int64_t i) { return ipow(r.rs, i + 1) * spike_ratio(nb, i, r); };
+  auto wspike_rev = [&](int64_t nb, int64_t i) { return ipow(r.ib, i + 1) * spike_ratio(nb, i, r); };
+  p.v0 = vspike(n, 0);
+  p.vend = vspike(n, n - 1);
+  p.w0 = wspike_rev(n, n - 1);
+  p.wend = wspike_rev(n, 0);
+  const int nl = p.nlast;
+  p.v0l = vspike(nl, 0);
+  p.vendl = vspike(nl, nl - 1);
+  p.w0l = wspike_rev(nl, nl - 1);
+  p.wendl = wspike_rev(nl, 0);
+
+  // table layout
+  int64_t o_ = 0;
+  auto take = [&](int64_t cnt) {
+    const int64_t at = o_;
+    o_ += cnt;
+    return (int32_t)at;
+  };
+  p.o_v = take(p.Lv);
+  p.o_w = take(p.Lw);
+  p.o_vl = take(nl);
+  p.o_wl = take(nl);
+  p.o_vf = take(p.Lv);
+  p.o_wf = take(p.Lw);
+  p.o_vlf = take(nl);
+  p.o_wlf = take(nl);
+  p.o_bcm = take(kBC);
+  p.o_bcl = take(kl * kBC);
+  p.o_bcr = take(kr * kBC);
+  sb.tab.assign((size_t)o_, 0.0);
+  double* T = sb.tab.data();
+  auto put_ff = [&](int32_t at, double d) {
+    float h, l;
+    split_ff(d, h, l);
+    float2 f2 = make_float2(h, l);
+    std::memcpy(&T[at], &f2, sizeof(double));
+  };
+  for (int i = 0; i < p.Lv; ++i) {
+    T[p.o_v + i] = vspike(n, i);
+    put_ff(p.o_vf + i, T[p.o_v + i]);
+  }
+  for (int i = 0; i < p.Lw; ++i) {
+    T[p.o_w + i] = wspike_rev(n, i);
+    put_ff(p.o_wf + i, T[p.o_w + i]);
+  }
+  for (int i = 0; i < nl; ++i) {
+    T[p.o_vl + i] = vspike(nl, i);
+    T[p.o_wl + i] = wspike_rev(nl, i);
+    put_ff(p.o_vlf + i, T[p.o_vl + i]);
+    put_ff(p.o_wlf + i, T[p.o_wl + i]);
+  }
+  block_coeffs(N, (int64_t)1 << 40, ((int64_t)1 << 40) + n - 1, r, p.v0, p.vend, p.w0, p.wend, true, true,
+               &T[p.o_bcm]);
+  auto coeffs_of = [&](int64_t m, double* out) {
+    const int64_t s = m * (int64_t)n;
+    const int64_t e = (m == P - 1) ? N - 1 : s + n - 1;
+    const bool lb = (m == P - 1);
+    block_coeffs(N, s, e, r, lb ? p.v0l : p.v0, lb ? p.vendl : p.vend, lb ? p.w0l : p.w0, lb ? p.wendl : p.wend,
+                 false, false, out);
+  };
+  for (int64_t m = 0; m < kl; ++m) coeffs_of(m, &T[p.o_bcl + m * kBC]);
+  for (int64_t k = 0; k < kr; ++k) coeffs_of(P - kr + k, &T[p.o_bcr + k * kBC]);
+  return DICH_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = (const char*)a;
+  const char* pb = (const char*)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
+int map_status(unsigned s) {
+  if (s & ST_NONFINITE) return DICH_ERR_NONFINITE;
+  if (s & ST_SCHEDULE) return DICH_ERR_SCHEDULE;
+  return DICH_OK;
+}
+
+}  // namespace
+
+// ================================================================== single-system plan
+struct dich_plan_s {
+  int64_t N = 0;
+  double tm1 = 0, t0 = 0, tp1 = 0;
+  Opts opts;
+  int NT = 64;
+  int form = FORM_F64;
+  int path = PATH_SINGLE;
+  int n_smem = 2;
+  int64_t tiles = 0;
+  SysBuild fwd, adj;
+  // workspace layout (bytes)
+  size_t ws_bytes = 0, off_plans = 0, off_status = 0, off_tabs = 0, off_beta = 0, off_iface = 0,
+         off_scan = 0, off_part = 0;
+  std::vector<unsigned char> staging;  // [plans | status | tables]
+  char* d_ws = nullptr;
+  size_t d_ws_bytes = 0;
+};
+
+extern "C" {
+
+const char* dichotomy_version(void) { return "0.1.0"; }
+
+const char* dichotomy_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+const char* dichotomy_strerror(int s) {
+  switch (s) {
+    case DICH_OK: return "ok";
+    case DICH_ERR_ARG: return "invalid argument";
+    case DICH_ERR_NOT_DOMINANT: return "matrix is not diagonally dominant (eq. 32-33)";
+    case DICH_ERR_SINGULAR: return "matrix is singular";
+    case DICH_ERR_TIMEOUT: return "device wait timed out";
+    case DICH_ERR_NONFINITE: return "non-finite value produced on the device";
+    case DICH_ERR_CUDA: return "CUDA runtime error";
+    case DICH_ERR_ALIAS: return "output aliases an input";
+    case DICH_ERR_UNBOUND: return "plan is not bound to a device workspace";
+    case DICH_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case DICH_ERR_SCHEDULE: return "coefficients need a larger schedule than prepared";
+    case DICH_ERR_UNSUPPORTED: return "unsupported combination";
+    default: return "unknown status";
+  }
+}
+
+int dichotomy_plan_ex(double t_m1, double t_0, double t_1, int64_t N, const dich_opts* opts, dich_plan_t* out) {
+  if (!out) return DICH_ERR_ARG;
+  *out = nullptr;
+  if (N < 0) return DICH_ERR_ARG;
+  Opts o;
+  int rc = read_opts(opts, o);
+  if (rc) return rc;
+  rc = validate_t(t_m1, t_0, t_1);
+  if (rc) return rc;
+  dich_plan_s* p = new (std::nothrow) dich_plan_s();
+  if (!p) return DICH_ERR_ARG;
+  p->N = N;
+  p->tm1 = t_m1;
+  p->t0 = t_0;
+  p->tp1 = t_1;
+  p->opts = o;
+  const Roots r = toeplitz_roots(t_m1, t_0, t_1);
+  p->form = pick_form(o.prec, r);
+  p->NT = o.NT ? o.NT : default_threads(p->form);
+  if (N >= 2) {
+    const int nmax = max_rows(p->NT, o.n_req > 0 ? kSmemMax : kSmemBudget);
+    const int n = choose_n(N, p->NT, nmax, o.n_req);
+    rc = build_system(t_m1, t_0, t_1, N, p->NT, p->form, n, o, true, p->fwd);
+    if (!rc) rc = build_system(t_1, t_0, t_m1, N, p->NT, p->form, n, o, true, p->adj);
+    if (rc) {
+      delete p;
+      return rc;
+    }
+    // both solves must take the same path; the transposed system swaps the halos
+    p->path = std::max(p->fwd.path, p->adj.path);
+    if (p->path == PATH_GENERAL && (p->fwd.path != PATH_GENERAL || p->adj.path != PATH_GENERAL)) {
+      Opts og = o;
+      og.flags |= DICH_FLAG_FORCE_GENERAL;
+      build_system(t_m1, t_0, t_1, N, p->NT, p->form, n, og, true, p->fwd);
+      build_system(t_1, t_0, t_m1, N, p->NT, p->form, n, og, true, p->adj);
+    }
+    if (p->path == PATH_HALO) {  // one window geometry for both directions
+      const int hl = std::max(p->fwd.rec.hl, p->adj.rec.hl), hr = std::max(p->fwd.rec.hr, p->adj.rec.hr);
+      for (SysBuild* sb : {&p->fwd, &p->adj}) {
+        sb->rec.hl = hl;
+        sb->rec.hr = hr;
+        sb->rec.own = p->NT - hl - hr;
+      }
+      if (p->NT - hl - hr < p->NT / 2) {
+        Opts og = o;
+        og.flags |= DICH_FLAG_FORCE_GENERAL;
+        build_system(t_m1, t_0, t_1, N, p->NT, p->form, n, og, true, p->fwd);
+        build_system(t_1, t_0, t_m1, N, p->NT, p->form, n, og, true, p->adj);
+        p->path = PATH_GENERAL;
+      }
+    }
+    p->n_smem = n;
+    p->tiles = ceil_div(p->fwd.rec.P, p->fwd.rec.own);
+  } else {
+    // N = 0 or 1: trivial; keep a minimal record for the N = 1 kernel
+    std::memset(&p->fwd.rec, 0, sizeof(SysPlan));
+    p->fwd.rec.N = N;
+    p->fwd.rec.t0 = t_0;
+    p->adj.rec = p->fwd.rec;
+    p->tiles = 0;
+  }
+  // workspace layout
+  size_t o_ = 0;
+  p->off_plans = o_;
+  o_ += align_up(2 * sizeof(SysPlan));
+  p->off_status = o_;
+  o_ += kAlign;
+  p->off_tabs = o_;
+  o_ += align_up(sizeof(double) * (p->fwd.tab.size() + p->adj.tab.size()));
+  const int64_t P = (N >= 2) ? p->fwd.rec.P : 0;
+  if (p->path == PATH_GENERAL) {
+    p->off_beta = o_;
+    o_ += align_up(sizeof(double) * 2 * P);
+    p->off_iface = o_;
+    o_ += align_up(sizeof(double) * 2 * P);
+    p->off_scan = o_;
+    o_ += align_up(sizeof(double) * 6 * (size_t)ceil_div(P, kScanChunk));
+  }
+  p->off_part = o_;
+  o_ += align_up(sizeof(double) * 3 * (size_t)std::max<int64_t>(1, p->tiles));
+  p->ws_bytes = o_;
+  // staging copy: records, zero status, tables
+  p->staging.assign(p->off_tabs + sizeof(double) * (p->fwd.tab.size() + p->adj.tab.size()), 0);
+  SysPlan recs[2] = {p->fwd.rec, p->adj.rec};
+  recs[0].tab = 0;
+  recs[1].tab = (int64_t)p->fwd.tab.size();
+  std::memcpy(p->staging.data() + p->off_plans, recs, sizeof(recs));
+  if (!p->fwd.tab.empty())
+    std::memcpy(p->staging.data() + p->off_tabs, p->fwd.tab.data(), sizeof(double) * p->fwd.tab.size());
+  if (!p->adj.tab.empty())
+    std::memcpy(p->staging.data() + p->off_tabs + sizeof(double) * p->fwd.tab.size(), p->adj.tab.data(),
+                sizeof(double) * p->adj.tab.size());
+  *out = p;
+  return DICH_OK;
+}
+
+int dichotomy_plan(double t_m1, double t_0, double t_1, int64_t N, dich_plan_t* out) {
+  return dichotomy_plan_ex(t_m1, t_0, t_1, N, nullptr, out);
+}
+
+int dichotomy_plan_info(dich_plan_t p, dich_plan_info* info) {
+  if (!p || !info) return DICH_ERR_ARG;
+  std::memset(info, 0, sizeof(*info));
+  const SysPlan& r = p->fwd.rec;
+  info->N = p->N;
+  info->P = (p->N >= 2) ? r.P : 0;
+  info->n = r.n;
+  info->n_last = r.nlast;
+  info->threads = p->NT;
+  info->halo_l = r.hl;
+  info->halo_r = r.hr;
+  info->path = p->path;
+  info->precision = p->form == FORM_F64 ? DICH_PREC_F64 : DICH_PREC_MIXED;
+  info->tiles = p->tiles;
+  info->Lv = r.Lv;
+  info->Lw = r.Lw;
+  info->kl = r.kl;
+  info->kr = r.kr;
+  const Roots rt = toeplitz_roots(p->tm1, p->t0, p->tp1);
+  info->rs = rt.rs;
+  info->ib = rt.ib;
+  info->z = rt.z;
+  info->workspace_bytes = p->ws_bytes;
+  return DICH_OK;
+}
+
+int dichotomy_plan_workspace_bytes(dich_plan_t p, size_t* bytes) {
+  if (!p || !bytes) return DICH_ERR_ARG;
+  *bytes = p->ws_bytes;
+  return DICH_OK;
+}
+
+int dichotomy_plan_bind(dich_plan_t p, void* d_ws, size_t bytes, void* stream) {
+  if (!p || !d_ws) return DICH_ERR_ARG;
+  if (((uintptr_t)d_ws & (kAlign - 1)) != 0 || bytes < p->ws_bytes) return DICH_ERR_WORKSPACE;
+  if (!is_device_ptr(d_ws)) return DICH_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(d_ws, p->staging.data(), p->staging.size(), cudaMemcpyHostToDevice,
+                                  (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  p->d_ws = (char*)d_ws;
+  p->d_ws_bytes = bytes;
+  return DICH_OK;
+}
+
+static int plan_launch(dich_plan_t p, const double* F, double* x, const double* xf, double* gt, bool adjoint,
+                       cudaStream_t st) {
+  const SysPlan* d_plans = (const SysPlan*)(p->d_ws + p->off_plans);
+  const double* d_tabs = (const double*)(p->d_ws + p->off_tabs);
+  unsigned* d_status = (unsigned*)(p->d_ws + p->off_status);
+  const int sys_offset = adjoint ? 1 : 0;
+  if (p->N == 0) return DICH_OK;
+  if (p->N == 1) {
+    cudaError_t e = launch_trivial(d_plans, nullptr, 1, adjoint ? nullptr : F, x, xf, adjoint ? F : nullptr, gt,
+                                   sys_offset, st);
+    return e == cudaSuccess ? DICH_OK : cuda_fail(e);
+  }
+  WinArgs a{};
+  a.plans = d_plans;
+  a.tabs = d_tabs;
+  a.items = nullptr;
+  a.F = F;
+  a.x = x;
+  a.status = d_status;
+  a.xf = adjoint ? xf : nullptr;
+  a.part = adjoint ? (double*)(p->d_ws + p->off_part) : nullptr;
+  a.check_finite = (p->opts.flags & DICH_FLAG_CHECK_FINITE) ? 1 : 0;
+  a.n_smem = p->n_smem;
+  a.sys_offset = sys_offset;
+  const size_t smem = window_smem_bytes(p->NT, p->n_smem);
+  auto launch = [&](const WinArgs& w) {
+    return p->form == FORM_F64 ? launch_window_f64(p->NT, (int)p->tiles, smem, st, w)
+                               : launch_window_mixed(p->NT, (int)p->tiles, smem, st, w);
+  };
+  cudaError_t e;
+  if (p->path != PATH_GENERAL) {
+    a.mode = MODE_FULL;
+    e = launch(a);
+    if (e != cudaSuccess) return cuda_fail(e);
+  } else {
+    double* beta = (double*)(p->d_ws + p->off_beta);
+    double* iface = (double*)(p->d_ws + p->off_iface);
+    double* scan = (double*)(p->d_ws + p->off_scan);
+    WinArgs b = a;
+    b.mode = MODE_BETA;
+    b.beta = beta;
+    b.xf = nullptr;
+    b.part = nullptr;
+    e = launch(b);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = launch_block_scan(d_plans + sys_offset, d_tabs, p->fwd.rec.P, beta, iface, scan, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    a.mode = MODE_APPLY;
+    a.iface = iface;
+    e = launch(a);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (adjoint) {
+    e = launch_adj_finalize(a.part, nullptr, nullptr, nullptr, p->tiles, 1, gt, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return DICH_OK;
+}
+
+int dichotomy_solve(dich_plan_t p, const double* d_F, double* d_x, void* stream) {
+  if (!p) return DICH_ERR_ARG;
+  if (!p->d_ws) return DICH_ERR_UNBOUND;
+  if (p->N == 0) return DICH_OK;
+  if (!d_F || !d_x || !aligned8(d_F) || !aligned8(d_x)) return DICH_ERR_ARG;
+  const size_t nb = sizeof(double) * (size_t)p->N;
+  if (overlap(d_F, nb, d_x, nb)) return DICH_ERR_ALIAS;
+  if (!is_device_ptr(d_F) || !is_device_ptr(d_x)) return DICH_ERR_ARG;
+  return plan_launch(p, d_F, d_x, nullptr, nullptr, false, (cudaStream_t)stream);
+}
+
+int dichotomy_adjoint(dich_plan_t p, const double* d_w, const double* d_x, double* d_gF, double* d_gt,
+                      void* stream) {
+  if (!p) return DICH_ERR_ARG;
+  if (!p->d_ws) return DICH_ERR_UNBOUND;
+  if (!d_gt || !aligned8(d_gt) || !is_device_ptr(d_gt)) return DICH_ERR_ARG;
+  if (p->N == 0) {
+    cudaError_t e = cudaMemsetAsync(d_gt, 0, 3 * sizeof(double), (cudaStream_t)stream);
+    return e == cudaSuccess ? DICH_OK : cuda_fail(e);
+  }
+  if (!d_w || !d_x || !d_gF || !aligned8(d_w) || !aligned8(d_x) || !aligned8(d_gF)) return DICH_ERR_ARG;
+  const size_t nb = sizeof(double) * (size_t)p->N;
+  if (overlap(d_gF, nb, d_w, nb) || overlap(d_gF, nb, d_x, nb) || overlap(d_gt, 24, d_gF, nb)) return DICH_ERR_ALIAS;
+  if (!is_device_ptr(d_w) || !is_device_ptr(d_x) || !is_device_ptr(d_gF)) return DICH_ERR_ARG;
+  return plan_launch(p, d_w, d_gF, d_x, d_gt, true, (cudaStream_t)stream);
+}
+
+int dichotomy_status(dich_plan_t p, void* stream, int* device_status) {
+  if (!p || !device_status) return DICH_ERR_ARG;
+  if (!p->d_ws) return DICH_ERR_UNBOUND;
+  unsigned s = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpy(&s, p->d_ws + p->off_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(p->d_ws + p->off_status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_fail(e);
+  *device_status = map_status(s);
+  return DICH_OK;
+}
+
+void dichotomy_destroy(dich_plan_t p) { delete p; }
+
+}  // extern "C"
+
+// ================================================================== batches
+struct dich_batch_s {
+  int64_t nsys = 0;
+  Opts opts;
+  int NT = 128;
+  std::vector<SysBuild> fwd, adj;          // per system (N >= 2); empty records for N < 2
+  std::vector<int32_t> form;               // per system
+  std::vector<int32_t> trivial;            // systems with N == 1
+  std::vector<Item> items[2];              // per form
+  std::vector<int32_t> sys_ids[2];         // per form: its systems, in item order
+  std::vector<int64_t> first[2], count[2]; // per form, parallel to sys_ids: CTA range of each system
+  int n_smem[2] = {2, 2};
+  size_t ws_bytes = 0, off_plans = 0, off_status = 0, off_tabs = 0, off_items[2] = {0, 0},
+         off_ids[2] = {0, 0}, off_first[2] = {0, 0}, off_count[2] = {0, 0}, off_trivial = 0,
+         off_part[2] = {0, 0};
+  std::vector<unsigned char> staging;
+  char* d_ws = nullptr;
+  size_t d_ws_bytes = 0;
+};
+
+extern "C" {
+
+int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_offset, const double* h_tm1,
+                            const double* h_t0, const double* h_tp1, const dich_opts* opts, dich_batch_t* out) {
+  if (!out) return DICH_ERR_ARG;
+  *out = nullptr;
+  if (nsys < 0 || (nsys > 0 && (!h_N || !h_offset || !h_tm1 || !h_t0 || !h_tp1))) return DICH_ERR_ARG;
+  if (nsys > ((int64_t)1 << 30)) return DICH_ERR_ARG;
+  Opts o;
+  int rc = read_opts(opts, o);
+  if (rc) return rc;
+  dich_batch_s* b = new (std::nothrow) dich_batch_s();
+  if (!b) return DICH_ERR_ARG;
+  b->nsys = nsys;
+  b->opts = o;
+  b->NT = o.NT ? o.NT : 128;
+  const int nmax = max_rows(b->NT, o.n_req > 0 ? kSmemMax : kSmemBudget);
+  b->fwd.resize((size_t)nsys);
+  b->adj.resize((size_t)nsys);
+  b->form.assign((size_t)nsys, FORM_F64);
+  for (int64_t s = 0; s < nsys; ++s) {
+    if (h_N[s] < 0 || h_offset[s] < 0) {
+      delete b;
+      return DICH_ERR_ARG;
+    }
+    rc = validate_t(h_tm1[s], h_t0[s], h_tp1[s]);
+    if (rc) {
+      delete b;
+      return rc;
+    }
+    const Roots r = toeplitz_roots(h_tm1[s], h_t0[s], h_tp1[s]);
+    b->form[s] = pick_form(o.prec, r);
+    if (h_N[s] < 2) {
+      SysPlan& q = b->fwd[s].rec;
+      std::memset(&q, 0, sizeof(q));
+      q.N = h_N[s];
+      q.off = h_offset[s];
+      q.t0 = h_t0[s];
+      b->adj[s].rec = q;
+      if (h_N[s] == 1) b->trivial.push_back((int32_t)s);
+      continue;
+    }
+    const int n = choose_n(h_N[s], b->NT, nmax, o.n_req);
+    Opts oh = o;
+    oh.flags &= ~DICH_FLAG_FORCE_GENERAL;
+    rc = build_system(h_tm1[s], h_t0[s], h_tp1[s], h_N[s], b->NT, b->form[s], n, oh, false, b->fwd[s]);
+    if (!rc) rc = build_system(h_tp1[s], h_t0[s], h_tm1[s], h_N[s], b->NT, b->form[s], n, oh, false, b->adj[s]);
+    if (rc) {
+      delete b;
+      return rc;
+    }
+    for (SysBuild* sb : {&b->fwd[s], &b->adj[s]}) sb->rec.off = h_offset[s];
+    if (b->fwd[s].path == PATH_HALO || b->adj[s].path == PATH_HALO) {
+      const int hl = std::max(b->fwd[s].rec.hl, b->adj[s].rec.hl);
+      const int hr = std::max(b->fwd[s].rec.hr, b->adj[s].rec.hr);
+      if (hl + hr > b->NT / 2) {
+        delete b;
+        return DICH_ERR_UNSUPPORTED;
+      }
+      for (SysBuild* sb : {&b->fwd[s], &b->adj[s]}) {
+        sb->rec.hl = hl;
+        sb->rec.hr = hr;
+        sb->rec.own = b->NT - hl - hr;
+        sb->path = PATH_HALO;
+      }
+    }
+  }
+  // windows, longest systems first (LPT); windows of one system stay contiguous
+  std::vector<int64_t> order;
+  for (int64_t s = 0; s < nsys; ++s)
+    if (h_N[s] >= 2) order.push_back(s);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t c) { return h_N[a] > h_N[c]; });
+  for (int64_t s : order) {
+    const SysPlan& q = b->fwd[s].rec;
+    const int f = b->form[s];
+    const int64_t first = (int64_t)b->items[f].size();
+    for (int64_t m0 = 0; m0 < q.P; m0 += q.own) {
+      Item it;
+      it.m0 = m0;
+      it.sys = (int32_t)s;
+      it.n_own = (int32_t)std::min<int64_t>(q.own, q.P - m0);
+      b->items[f].push_back(it);
+    }
+    b->sys_ids[f].push_back((int32_t)s);
+    b->first[f].push_back(first);
+    b->count[f].push_back((int64_t)b->items[f].size() - first);
+    b->n_smem[f] = std::max(b->n_smem[f], q.n);
+  }
+  // tables
+  int64_t tabsz = 0;
+  for (int64_t s = 0; s < nsys; ++s) {
+    b->fwd[s].rec.tab = tabsz;
+    tabsz += (int64_t)b->fwd[s].tab.size();
+    b->adj[s].rec.tab = tabsz;
+    tabsz += (int64_t)b->adj[s].tab.size();
+  }
+  size_t o_ = 0;
+  b->off_plans = o_;
+  o_ += align_up(sizeof(SysPlan) * 2 * (size_t)std::max<int64_t>(1, nsys));
+  b->off_status = o_;
+  o_ += kAlign;
+  for (int f = 0; f < 2; ++f) {
+    b->off_items[f] = o_;
+    o_ += align_up(sizeof(Item) * std::max<size_t>(1, b->items[f].size()));
+    b->off_ids[f] = o_;
+    o_ += align_up(sizeof(int32_t) * std::max<size_t>(1, b->sys_ids[f].size()));
+    b->off_first[f] = o_;
+    o_ += align_up(sizeof(int64_t) * std::max<size_t>(1, b->first[f].size()));
+    b->off_count[f] = o_;
+    o_ += align_up(sizeof(int64_t) * std::max<size_t>(1, b->count[f].size()));
+  }
+  b->off_trivial = o_;
+  o_ += align_up(sizeof(int32_t) * std::max<size_t>(1, b->trivial.size()));
+  b->off_tabs = o_;
+  o_ += align_up(sizeof(double) * (size_t)std::max<int64_t>(1, tabsz));
+  const size_t staged = o_;
+  for (int f = 0; f < 2; ++f) {
+    b->off_part[f] = o_;
+    o_ += align_up(sizeof(double) * 3 * std::max<size_t>(1, b->items[f].size()));
+  }
+  b->ws_bytes = o_;
+  b->staging.assign(staged, 0);
+  unsigned char* S = b->staging.data();
+  for (int64_t s = 0; s < nsys; ++s) {
+    std::memcpy(S + b->off_plans + sizeof(SysPlan) * s, &b->fwd[s].rec, sizeof(SysPlan));
+    std::memcpy(S + b->off_plans + sizeof(SysPlan) * (nsys + s), &b->adj[s].rec, sizeof(SysPlan));
+    if (!b->fwd[s].tab.empty())
+      std::memcpy(S + b->off_tabs + sizeof(double) * b->fwd[s].rec.tab, b->fwd[s].tab.data(),
+                  sizeof(double) * b->fwd[s].tab.size());
+    if (!b->adj[s].tab.empty())
+      std::memcpy(S + b->off_tabs + sizeof(double) * b->adj[s].rec.tab, b->adj[s].tab.data(),
+                  sizeof(double) * b->adj[s].tab.size());
+  }
+  for (int f = 0; f < 2; ++f) {
+    if (!b->items[f].empty()) std::memcpy(S + b->off_items[f], b->items[f].data(), sizeof(Item) * b->items[f].size());
+    if (!b->sys_ids[f].empty()) {
+      std::memcpy(S + b->off_ids[f], b->sys_ids[f].data(), sizeof(int32_t) * b->sys_ids[f].size());
+      std::memcpy(S + b->off_first[f], b->first[f].data(), sizeof(int64_t) * b->first[f].size());
+      std::memcpy(S + b->off_count[f], b->count[f].data(), sizeof(int64_t) * b->count[f].size());
+    }
+  }
+  if (!b->trivial.empty())
+    std::memcpy(S + b->off_trivial, b->trivial.data(), sizeof(int32_t) * b->trivial.size());
+  *out = b;
+  return DICH_OK;
+}
+
+int dichotomy_batch_workspace_bytes(dich_batch_t b, size_t* bytes) {
+  if (!b || !bytes) return DICH_ERR_ARG;
+  *bytes = b->ws_bytes;
+  return DICH_OK;
+}
+
+int dichotomy_batch_bind(dich_batch_t b, void* d_ws, size_t bytes, void* stream) {
+  if (!b || !d_ws) return DICH_ERR_ARG;
+  if (((uintptr_t)d_ws & (kAlign - 1)) != 0 || bytes < b->ws_bytes) return DICH_ERR_WORKSPACE;
+  if (!is_device_ptr(d_ws)) return DICH_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(d_ws, b->staging.data(), b->staging.size(), cudaMemcpyHostToDevice,
+                                  (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  b->d_ws = (char*)d_ws;
+  b->d_ws_bytes = bytes;
+  return DICH_OK;
+}
+
+static int batch_launch(dich_batch_t b, const double* F, double* x, const double* xf, double* gt, bool adjoint,
+                        cudaStream_t st) {
+  const SysPlan* d_plans = (const SysPlan*)(b->d_ws + b->off_plans);
+  const double* d_tabs = (const double*)(b->d_ws + b->off_tabs);
+  unsigned* d_status = (unsigned*)(b->d_ws + b->off_status);
+  const int sys_offset = adjoint ? (int)b->nsys : 0;
+  for (int f = 0; f < 2; ++f) {
+    const int64_t nitems = (int64_t)b->items[f].size();
+    if (nitems == 0) continue;
+    WinArgs a{};
+    a.plans = d_plans;
+    a.tabs = d_tabs;
+    a.items = (const Item*)(b->d_ws + b->off_items[f]);
+    a.F = F;
+    a.x = x;
+    a.status = d_status;
+    a.xf = adjoint ? xf : nullptr;
+    a.part = adjoint ? (double*)(b->d_ws + b->off_part[f]) : nullptr;
+    a.mode = MODE_FULL;
+    a.check_finite = (b->opts.flags & DICH_FLAG_CHECK_FINITE) ? 1 : 0;
+    a.n_smem = b->n_smem[f];
+    a.sys_offset = sys_offset;
+    const size_t smem = window_smem_bytes(b->NT, a.n_smem);
+    cudaError_t e = (f == FORM_F64) ? launch_window_f64(b->NT, (int)nitems, smem, st, a)
+                                    : launch_window_mixed(b->NT, (int)nitems, smem, st, a);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (adjoint) {
+      e = launch_adj_finalize(a.part, (const int32_t*)(b->d_ws + b->off_ids[f]),
+                              (const int64_t*)(b->d_ws + b->off_first[f]),
+                              (const int64_t*)(b->d_ws + b->off_count[f]), 0, (int64_t)b->sys_ids[f].size(), gt, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+  }
+  if (!b->trivial.empty()) {
+    cudaError_t e = launch_trivial(d_plans, (const int32_t*)(b->d_ws + b->off_trivial), (int64_t)b->trivial.size(),
+                                   adjoint ? nullptr : F, x, xf, adjoint ? F : nullptr, gt, sys_offset, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return DICH_OK;
+}
+
+int dichotomy_solve_batched(dich_batch_t b, const double* d_F, double* d_x, void* stream) {
+  if (!b) return DICH_ERR_ARG;
+  if (!b->d_ws) return DICH_ERR_UNBOUND;
+  if (b->nsys == 0) return DICH_OK;
+  if (!d_F || !d_x || !aligned8(d_F) || !aligned8(d_x)) return DICH_ERR_ARG;
+  if (!is_device_ptr(d_F) || !is_device_ptr(d_x)) return DICH_ERR_ARG;
+  if (d_F == d_x) return DICH_ERR_ALIAS;
+  return batch_launch(b, d_F, d_x, nullptr, nullptr, false, (cudaStream_t)stream);
+}
+
+int dichotomy_adjoint_batched(dich_batch_t b, const double* d_w, const double* d_x, double* d_gF, double* d_gt,
+                              void* stream) {
+  if (!b) return DICH_ERR_ARG;
+  if (!b->d_ws) return DICH_ERR_UNBOUND;
+  if (b->nsys == 0) return DICH_OK;
+  if (!d_w || !d_x || !d_gF || !d_gt) return DICH_ERR_ARG;
+  if (!aligned8(d_w) || !aligned8(d_x) || !aligned8(d_gF) || !aligned8(d_gt)) return DICH_ERR_ARG;
+  if (!is_device_ptr(d_w) || !is_device_ptr(d_x) || !is_device_ptr(d_gF) || !is_device_ptr(d_gt)) return DICH_ERR_ARG;
+  if (d_gF == d_w || d_gF == d_x) return DICH_ERR_ALIAS;
+  cudaError_t e = cudaMemsetAsync(d_gt, 0, sizeof(double) * 3 * (size_t)b->nsys, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return batch_launch(b, d_w, d_gF, d_x, d_gt, true, (cudaStream_t)stream);
+}
+
+int dichotomy_batch_status(dich_batch_t b, void* stream, int* device_status) {
+  if (!b || !device_status) return DICH_ERR_ARG;
+  if (!b->d_ws) return DICH_ERR_UNBOUND;
+  unsigned s = 0;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaMemcpy(&s, b->d_ws + b->off_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(b->d_ws + b->off_status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_fail(e);
+  *device_status = map_status(s);
+  return DICH_OK;
+}
+
+int dichotomy_batch_info(dich_batch_t b, int64_t* nsys, int64_t* windows, int32_t* h_form) {
+  if (!b) return DICH_ERR_ARG;
+  if (nsys) *nsys = b->nsys;
+  if (windows) *windows = (int64_t)(b->items[0].size() + b->items[1].size());
+  if (h_form)
+    for (int64_t s = 0; s < b->nsys; ++s) h_form[s] = b->form[s];
+  return DICH_OK;
+}
+
+void dichotomy_batch_destroy(dich_batch_t b) { delete b; }
+
+}  // extern "C"

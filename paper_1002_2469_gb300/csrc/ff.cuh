@@ -1,0 +1,111 @@
+// ff.cuh -- float-float (double-FP32) helpers for the MIXED form of the Dichotomy sweeps.
+//
+// On GB300 the FP64 pipe issues about 1.6 operations per clock per SM (and FP64<->FP32
+// conversions run on it too), against about 110 FP32 FMAs.  The MIXED form therefore
+// keeps every per-element operation on the FP32/INT pipes:
+//   - FP64 input -> (hi, lo) floats with integer bit operations (no conversion unit),
+//   - the first-order recurrences in compensated FP32 arithmetic (error-free product
+//     by FMA, Knuth's TwoSum, the rounding errors carried in a second float),
+//   - (hi, lo) -> FP64 output: exact float->double by bit operations plus one FP64 add.
+// All arithmetic uses the explicit __f*_rn intrinsics so the compiler can neither fuse
+// nor reassociate the error-free transformations.
+#pragma once
+#include <cstdint>
+
+namespace dich {
+
+// p + e = a * b exactly
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// s + e = a + b exactly (Knuth; no ordering assumption)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (yh, yl) ~= (fh + fl) + (rh + rl) * (xh + xl), rounding errors of the leading terms kept
+// exactly and accumulated in yl (unnormalised float-float).
+__device__ __forceinline__ void ff_axpy(float fh, float fl, float rh, float rl, float xh, float xl,
+                                        float& yh, float& yl) {
+  float p, pe, s, se;
+  two_prod(rh, xh, p, pe);
+  two_sum(fh, p, s, se);
+  float c = __fadd_rn(fl, __fadd_rn(pe, se));
+  c = __fmaf_rn(rl, xh, c);
+  c = __fmaf_rn(rh, xl, c);
+  yh = s;
+  yl = c;
+}
+
+// (yh, yl) ~= (gh + gl) * (xh + xl)
+__device__ __forceinline__ void ff_mul(float gh, float gl, float xh, float xl, float& yh, float& yl) {
+  float p, pe;
+  two_prod(gh, xh, p, pe);
+  float c = __fmaf_rn(gl, xh, pe);
+  c = __fmaf_rn(gh, xl, c);
+  yh = p;
+  yl = c;
+}
+
+// (xh, xl) += (ch + cl) * (vh + vl)
+__device__ __forceinline__ void ff_fma_acc(float ch, float cl, float vh, float vl, float& xh, float& xl) {
+  float p, pe, s, se;
+  two_prod(ch, vh, p, pe);
+  float pc = __fmaf_rn(cl, vh, __fmaf_rn(ch, vl, pe));
+  two_sum(xh, p, s, se);
+  xl = __fadd_rn(xl, __fadd_rn(pc, se));
+  xh = s;
+}
+
+// FP64 -> (hi, lo) by integer operations.  hi keeps the leading 24 significant bits
+// (truncated), lo the next 23 (truncated), so |d - hi - lo| < 2^-46 |d|.  Valid for
+// 2^-80 <= |d| < 2^127; below 2^-80 lo is dropped, below 2^-126 the value flushes to 0,
+// above 2^127 (and Inf/NaN) hi becomes Inf/NaN so the output is flagged non-finite.
+__device__ __forceinline__ float2 f64_to_ff(double d) {
+  const unsigned hw = (unsigned)__double2hiint(d);
+  const unsigned lw = (unsigned)__double2loint(d);
+  const unsigned sgn = hw & 0x80000000u;
+  const int E = (int)((hw >> 20) & 0x7FFu);
+  const unsigned m23 = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+  const int ef = E - 896;
+  unsigned hib = sgn | ((unsigned)ef << 23) | m23;
+  if (ef < 1) hib = sgn;
+  if (ef > 254) hib = sgn | 0x7F800000u | ((E == 2047 && ((hw & 0xFFFFFu) | lw)) ? 0x400000u : 0u);
+  const unsigned r = lw & 0x1FFFFFFFu;
+  const float rf = __fsub_rn(__uint_as_float(0x4B000000u | (r >> 6)), 8388608.0f);
+  const int es = E - 942;
+  float lo = (es >= 1 && ef <= 254) ? __fmul_rn(rf, __uint_as_float((unsigned)es << 23)) : 0.0f;
+  lo = __uint_as_float(__float_as_uint(lo) | sgn);
+  return make_float2(__uint_as_float(hib), lo);
+}
+
+// exact float -> double by integer operations (denormal floats flush to signed zero)
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned s = b & 0x80000000u;
+  const unsigned e = (b >> 23) & 0xFFu;
+  const unsigned m = b & 0x7FFFFFu;
+  const unsigned ed = (e == 0u) ? 0u : ((e == 255u) ? 0x7FFu : e + 896u);
+  const unsigned md = (e == 0u) ? 0u : m;
+  const unsigned hi = s | (ed << 20) | (md >> 3);
+  const unsigned lo = md << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// (h, l) -> FP64: both parts converted exactly, one FP64 addition.
+__device__ __forceinline__ double ff_to_f64(float h, float l) {
+  return __dadd_rn(f32_to_f64_bits(h), f32_to_f64_bits(l));
+}
+
+// FP64 -> float-float with correct rounding of hi (FP64 pipe; used once per block only)
+__device__ __forceinline__ float2 f64_to_ff_rn(double d) {
+  const float h = __double2float_rn(d);
+  const float l = __double2float_rn(__dsub_rn(d, (double)h));
+  return make_float2(h, l);
+}
+
+}  // namespace dich

@@ -1,0 +1,278 @@
+// k_aux.cu -- general-path block scan, adjoint gradient finalisation, one-row systems.
+#include "launch.cuh"
+
+namespace dich {
+
+__device__ __forceinline__ const double* bc_of(const SysPlan* pp, const double* tab, int64_t m) {
+  if (m < pp->kl) return tab + pp->o_bcl + m * kBC;
+  if (m >= pp->P - pp->kr) return tab + pp->o_bcr + (m - (pp->P - pp->kr)) * kBC;
+  return tab + pp->o_bcm;
+}
+
+// CTA scans of affine maps t -> a t + b.  Prefix: maps of threads 0..tid composed left to
+// right (lower index applied first).  Suffix: maps of threads tid..NTH-1 composed right to
+// left (higher index applied first).  (ia, ib): inclusive composite; (ea, eb): exclusive.
+// `sh` holds 4 * NTH/32 doubles; the CTA must call these uniformly.
+template <int NTH>
+__device__ __forceinline__ void cta_prefix(double& ia, double& ib, double& ea, double& eb, double* sh) {
+  constexpr int NW = NTH / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const double ya = __shfl_up_sync(0xffffffffu, ia, d), yb = __shfl_up_sync(0xffffffffu, ib, d);
+    if (lane >= d) {
+      ib = fma(ia, yb, ib);
+      ia = ia * ya;
+    }
+  }
+  if (lane == 31) {
+    sh[wid] = ia;
+    sh[NW + wid] = ib;
+  }
+  double pa = __shfl_up_sync(0xffffffffu, ia, 1), pb = __shfl_up_sync(0xffffffffu, ib, 1);
+  if (lane == 0) {
+    pa = 1.0;
+    pb = 0.0;
+  }
+  __syncthreads();
+  double ma = 1.0, mb = 0.0;  // composite of the previous warps
+  for (int w = 0; w < wid; ++w) {
+    mb = fma(sh[w], mb, sh[NW + w]);
+    ma = sh[w] * ma;
+  }
+  __syncthreads();
+  ea = pa * ma;
+  eb = fma(pa, mb, pb);
+  ib = fma(ia, mb, ib);
+  ia = ia * ma;
+}
+
+template <int NTH>
+__device__ __forceinline__ void cta_suffix(double& ia, double& ib, double& ea, double& eb, double* sh) {
+  constexpr int NW = NTH / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const double ya = __shfl_down_sync(0xffffffffu, ia, d), yb = __shfl_down_sync(0xffffffffu, ib, d);
+    if (lane + d < 32) {
+      ib = fma(ia, yb, ib);
+      ia = ia * ya;
+    }
+  }
+  if (lane == 0) {
+    sh[2 * NW + wid] = ia;
+    sh[3 * NW + wid] = ib;
+  }
+  double pa = __shfl_down_sync(0xffffffffu, ia, 1), pb = __shfl_down_sync(0xffffffffu, ib, 1);
+  if (lane == 31) {
+    pa = 1.0;
+    pb = 0.0;
+  }
+  __syncthreads();
+  double ma = 1.0, mb = 0.0;  // composite of the following warps
+  for (int w = NW - 1; w > wid; --w) {
+    mb = fma(sh[2 * NW + w], mb, sh[3 * NW + w]);
+    ma = sh[2 * NW + w] * ma;
+  }
+  __syncthreads();
+  ea = pa * ma;
+  eb = fma(pa, mb, pb);
+  ib = fma(ia, mb, ib);
+  ia = ia * ma;
+}
+
+// per-thread composite of its kScanPer blocks
+__device__ __forceinline__ void thread_maps(const SysPlan* pp, const double* tab, int64_t P, const double* beta,
+                                            int64_t m_first, double& pa, double& pb, double& sa, double& sb) {
+  pa = 1.0; pb = 0.0; sa = 1.0; sb = 0.0;
+  for (int k = 0; k < kScanPer; ++k) {
+    const int64_t m = m_first + k;
+    if (m >= P) break;
+    const double* bc = bc_of(pp, tab, m);
+    const double bR = beta[2 * m + 1];
+    pb = fma(bc[BC_A], pb, bc[BC_B] * bR);
+    pa = bc[BC_A] * pa;
+  }
+  for (int k = kScanPer - 1; k >= 0; --k) {
+    const int64_t m = m_first + k;
+    if (m >= P) continue;
+    const double* bc = bc_of(pp, tab, m);
+    const double bL = beta[2 * m];
+    sb = fma(bc[BC_C], sb, bc[BC_D] * bL);
+    sa = bc[BC_C] * sa;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_bscan_reduce(const SysPlan* pp, const double* tabs, int64_t P,
+                                                               const double* beta, double* agg) {
+  __shared__ double sh[4 * kScanThreads / 32];
+  const double* tab = tabs + pp->tab;
+  const int64_t m_first = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPer;
+  double pa, pb, sa, sb, ea, eb;
+  thread_maps(pp, tab, P, beta, m_first, pa, pb, sa, sb);
+  cta_prefix<kScanThreads>(pa, pb, ea, eb, sh);
+  cta_suffix<kScanThreads>(sa, sb, ea, eb, sh);
+  if (threadIdx.x == kScanThreads - 1) {
+    agg[4 * (size_t)blockIdx.x + 0] = pa;
+    agg[4 * (size_t)blockIdx.x + 1] = pb;
+  }
+  if (threadIdx.x == 0) {
+    agg[4 * (size_t)blockIdx.x + 2] = sa;
+    agg[4 * (size_t)blockIdx.x + 3] = sb;
+  }
+}
+
+// carry[2 c] = A entering chunk c, carry[2 c + 1] = B at the end of chunk c
+__global__ void __launch_bounds__(1024) k_bscan_top(const double* agg, int64_t nchunks, double* carry) {
+  __shared__ double sh[4 * 1024 / 32];
+  __shared__ double run;
+  if (threadIdx.x == 0) run = 0.0;
+  __syncthreads();
+  for (int64_t g0 = 0; g0 < nchunks; g0 += 1024) {
+    const int64_t c = g0 + threadIdx.x;
+    double ia = 1.0, ib = 0.0, ea, eb;
+    if (c < nchunks) {
+      ia = agg[4 * c];
+      ib = agg[4 * c + 1];
+    }
+    cta_prefix<1024>(ia, ib, ea, eb, sh);
+    const double r = run;
+    if (c < nchunks) carry[2 * c] = fma(ea, r, eb);
+    __syncthreads();
+    if (threadIdx.x == 1023) run = fma(ia, r, ib);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) run = 0.0;
+  __syncthreads();
+  const int64_t ngroups = (nchunks + 1023) / 1024;
+  for (int64_t g = ngroups - 1; g >= 0; --g) {
+    const int64_t c = g * 1024 + threadIdx.x;
+    double ia = 1.0, ib = 0.0, ea, eb;
+    if (c < nchunks) {
+      ia = agg[4 * c + 2];
+      ib = agg[4 * c + 3];
+    }
+    cta_suffix<1024>(ia, ib, ea, eb, sh);
+    const double r = run;
+    if (c < nchunks) carry[2 * c + 1] = fma(ea, r, eb);
+    __syncthreads();
+    if (threadIdx.x == 0) run = fma(ia, r, ib);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_bscan_apply(const SysPlan* pp, const double* tabs, int64_t P,
+                                                              const double* beta, const double* carry,
+                                                              double* iface) {
+  __shared__ double sh[4 * kScanThreads / 32];
+  const double* tab = tabs + pp->tab;
+  const int64_t m_first = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPer;
+  double pa, pb, sa, sb, ea, eb, fa, fb;
+  thread_maps(pp, tab, P, beta, m_first, pa, pb, sa, sb);
+  cta_prefix<kScanThreads>(pa, pb, ea, eb, sh);
+  cta_suffix<kScanThreads>(sa, sb, fa, fb, sh);
+  double Acur = fma(ea, carry[2 * (size_t)blockIdx.x], eb);
+  const double Bend = fma(fa, carry[2 * (size_t)blockIdx.x + 1], fb);
+  double Am[kScanPer], Bm[kScanPer];
+  for (int k = 0; k < kScanPer; ++k) {
+    const int64_t m = m_first + k;
+    Am[k] = Acur;
+    if (m < P) {
+      const double* bc = bc_of(pp, tab, m);
+      Acur = fma(bc[BC_A], Acur, bc[BC_B] * beta[2 * m + 1]);
+    }
+  }
+  double Bcur = Bend;
+  for (int k = kScanPer - 1; k >= 0; --k) {
+    const int64_t m = m_first + k;
+    Bm[k] = Bcur;
+    if (m < P) {
+      const double* bc = bc_of(pp, tab, m);
+      Bcur = fma(bc[BC_C], Bcur, bc[BC_D] * beta[2 * m]);
+    }
+  }
+  for (int k = 0; k < kScanPer; ++k) {
+    const int64_t m = m_first + k;
+    if (m >= P) break;
+    const double* bc = bc_of(pp, tab, m);
+    const double bL = beta[2 * m], bR = beta[2 * m + 1];
+    iface[2 * m] = Am[k] + bL + bc[BC_TL] * Bm[k];
+    iface[2 * m + 1] = fma(bc[BC_TR], Am[k], bR + Bm[k]);
+  }
+}
+
+cudaError_t launch_block_scan(const SysPlan* plan, const double* tabs, int64_t P, const double* beta,
+                              double* iface, double* scratch, cudaStream_t st) {
+  const int64_t nchunks = (P + kScanChunk - 1) / kScanChunk;
+  double* agg = scratch;
+  double* carry = scratch + 4 * nchunks;
+  k_bscan_reduce<<<(unsigned)nchunks, kScanThreads, 0, st>>>(plan, tabs, P, beta, agg);
+  k_bscan_top<<<1, 1024, 0, st>>>(agg, nchunks, carry);
+  k_bscan_apply<<<(unsigned)nchunks, kScanThreads, 0, st>>>(plan, tabs, P, beta, carry, iface);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_adj_finalize(const double* part, const int32_t* sys_ids,
+                                                      const int64_t* first, const int64_t* count, int64_t count0,
+                                                      double* gt) {
+  __shared__ double sh[3 * 256];
+  const int64_t k = blockIdx.x;
+  const int64_t s = sys_ids ? sys_ids[k] : k;
+  const int64_t f = first ? first[k] : 0;
+  const int64_t c = count ? count[k] : count0;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (int64_t i = threadIdx.x; i < c; i += 256) {
+    a0 += part[3 * (f + i)];
+    a1 += part[3 * (f + i) + 1];
+    a2 += part[3 * (f + i) + 2];
+  }
+  sh[threadIdx.x] = a0;
+  sh[256 + threadIdx.x] = a1;
+  sh[512 + threadIdx.x] = a2;
+  __syncthreads();
+  for (int d = 128; d > 0; d >>= 1) {
+    if ((int)threadIdx.x < d) {
+      sh[threadIdx.x] += sh[threadIdx.x + d];
+      sh[256 + threadIdx.x] += sh[256 + threadIdx.x + d];
+      sh[512 + threadIdx.x] += sh[512 + threadIdx.x + d];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) gt[3 * s + threadIdx.x] = -sh[256 * threadIdx.x];
+}
+
+cudaError_t launch_adj_finalize(const double* part, const int32_t* sys_ids, const int64_t* first,
+                                const int64_t* count, int64_t count0, int64_t nsys, double* gt, cudaStream_t st) {
+  if (nsys <= 0) return cudaSuccess;
+  k_adj_finalize<<<(unsigned)nsys, 256, 0, st>>>(part, sys_ids, first, count, count0, gt);
+  return cudaGetLastError();
+}
+
+// x = F / t_0 for one-row systems; adjoint form when w != nullptr:
+//   gF = w / t_0, dL/dt_0 = -gF * xf, dL/dt_-1 = dL/dt_1 = 0.
+__global__ void k_trivial(const SysPlan* plans, const int32_t* idx, int64_t nidx, const double* F, double* x,
+                          const double* xf, const double* w, double* gt, int sys_offset) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nidx) return;
+  const int s = idx ? idx[k] : 0;
+  const SysPlan* pp = plans + s + sys_offset;
+  const int64_t o = pp->off;
+  if (w == nullptr) {
+    x[o] = F[o] / pp->t0;
+  } else {
+    const double lam = w[o] / pp->t0;
+    x[o] = lam;
+    gt[3 * s + 0] = 0.0;
+    gt[3 * s + 1] = -lam * xf[o];
+    gt[3 * s + 2] = 0.0;
+  }
+}
+
+cudaError_t launch_trivial(const SysPlan* plans, const int32_t* idx, int64_t nidx, const double* F, double* x,
+                           const double* xf, const double* w, double* gt, int sys_offset, cudaStream_t st) {
+  if (nidx <= 0) return cudaSuccess;
+  k_trivial<<<(unsigned)((nidx + 127) / 128), 128, 0, st>>>(plans, idx, nidx, F, x, xf, w, gt, sys_offset);
+  return cudaGetLastError();
+}
+
+}  // namespace dich

@@ -1,0 +1,26 @@
+// k_f64.cu -- FP64 instantiations of the window kernel.
+#include "launch.cuh"
+
+namespace dich {
+
+template <int NT>
+static cudaError_t launch_one(int grid, size_t smem, cudaStream_t st, const WinArgs& a) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_window<NT, FORM_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_window<NT, FORM_F64><<<grid, NT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_window_f64(int NT, int grid, size_t smem, cudaStream_t st, const WinArgs& a) {
+  switch (NT) {
+    case 64: return launch_one<64>(grid, smem, st, a);
+    case 128: return launch_one<128>(grid, smem, st, a);
+    case 256: return launch_one<256>(grid, smem, st, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace dich

@@ -1,0 +1,26 @@
+// k_mixed.cu -- MIXED-form (compensated FP32 sweeps, FP64 tree) instantiations of the window kernel.
+#include "launch.cuh"
+
+namespace dich {
+
+template <int NT>
+static cudaError_t launch_one(int grid, size_t smem, cudaStream_t st, const WinArgs& a) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_window<NT, FORM_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_window<NT, FORM_MIXED><<<grid, NT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_window_mixed(int NT, int grid, size_t smem, cudaStream_t st, const WinArgs& a) {
+  switch (NT) {
+    case 64: return launch_one<64>(grid, smem, st, a);
+    case 128: return launch_one<128>(grid, smem, st, a);
+    case 256: return launch_one<256>(grid, smem, st, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace dich

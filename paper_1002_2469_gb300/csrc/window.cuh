@@ -1,0 +1,427 @@
+// window.cuh -- the Dichotomy window kernel (sm_103a).
+//
+// One CTA of NT threads handles a window of up to NT consecutive blocks of one system;
+// thread b owns window block b.  Per window:
+//   1. load F of the window into shared memory, transposed (row i of every block side by
+//      side, stride NT+1 doubles), with coalesced 256-byte warp loads;
+//   2. local sweeps (a1): every thread runs the two first-order recurrences of its block
+//      (u_i = f_i + rs u_{i-1}, X_i = u_i + ib X_{i+1}, xp_i = g X_i) in place, giving the
+//      block ends alpha, omega of T_n^-1 F_m and then beta^{L,R}_m of eq. 16 through the
+//      2x2 map M;
+//   3. the dichotomy tree (a2): eq. 15 as two affine scans (prefix A, suffix B) -- five
+//      warp-shuffle levels, then one shared-memory level across warps -- and the
+//      first/last values x_s, x_e of every block (eq. 18);
+//   4. the basis correction (a3): x = xp + (x_{s-1} - xp(-1)) v + x_{e+1} w, applied only
+//      where the spikes v, w exceed the truncation threshold, and the coalesced store.
+// Windows of a long system overlap by halo blocks on each side whose coupling into the
+// own blocks has decayed below 2^-64 (the truncation is exact to that level); on the
+// general path the window instead takes the first/last values from a global scan.
+#pragma once
+#include "dich_internal.cuh"
+#include "ff.cuh"
+
+namespace dich {
+
+struct WinArgs {
+  const SysPlan* plans;   // plan records (device)
+  const double* tabs;     // table buffer (device)
+  const Item* items;      // batched: one item per CTA; nullptr: single system, window = blockIdx
+  const double* F;        // right-hand sides
+  double* x;              // solutions
+  unsigned* status;       // device status word
+  const double* iface;    // MODE_APPLY: (x_s, x_e) per block
+  double* beta;           // MODE_BETA: (beta^L, beta^R) per block
+  const double* xf;       // adjoint: forward solution (gradient sums), else nullptr
+  double* part;           // adjoint: per-CTA partial sums [3 per CTA]
+  int32_t mode;
+  int32_t check_finite;
+  int32_t n_smem;         // shared-memory rows (>= largest block size in the launch)
+  int32_t sys_offset;     // added to the item's system index (adjoint twin records)
+};
+
+// shared memory bytes for a window kernel of width NT and n_smem rows
+__host__ __device__ inline size_t window_smem_bytes(int NT, int n_smem) {
+  const size_t nw = (size_t)(NT / 32);
+  return sizeof(double) * ((size_t)n_smem * (size_t)(NT + 1) + 4 * (size_t)n_smem + 4 * (size_t)NT + 4 * nw + 8);
+}
+
+template <int NT, int FORM>
+__global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
+  constexpr int NW = NT / 32;
+  constexpr int LD = NT + 1;
+  extern __shared__ __align__(16) double sm[];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int ns = A.n_smem;
+  double* S = sm;
+  double* tv = S + (size_t)ns * LD;
+  double* tw = tv + ns;
+  double* tvl = tw + ns;
+  double* twl = tvl + ns;
+  double* sxs = twl + ns;
+  double* sxe = sxs + NT;
+  double* scl = sxe + NT;
+  double* scr = scl + NT;
+  double* swa = scr + NT;  // 4 * NW scan scratch
+  float2* S2 = reinterpret_cast<float2*>(S);
+
+  // ---------------------------------------------------------------- the window
+  int sys;
+  int64_t m0;
+  int nown;
+  if (A.items) {
+    const Item it = A.items[blockIdx.x];
+    sys = it.sys;
+    m0 = it.m0;
+    nown = it.n_own;
+  } else {
+    sys = 0;
+    m0 = 0;
+    nown = 0;
+  }
+  sys += A.sys_offset;
+  const SysPlan* pp = A.plans + sys;
+  const int64_t P = pp->P;
+  if (!A.items) {
+    nown = pp->own;
+    m0 = (int64_t)blockIdx.x * nown;
+    if (m0 + nown > P) nown = (int)(P - m0);
+  }
+  int hl = 0, hr = 0;
+  if (A.mode == MODE_FULL) {
+    hl = (int)min((int64_t)pp->hl, m0);
+    hr = (int)min((int64_t)pp->hr, P - m0 - nown);
+  }
+  const int64_t wlo = m0 - hl;
+  const int nwin = hl + nown + hr;
+  const int n = pp->n, nlast = pp->nlast;
+  const int Lv = pp->Lv, Lw = pp->Lw;
+  const int64_t off = pp->off;
+  const double* tab = A.tabs + pp->tab;
+  const bool has_last = (wlo + nwin == P);
+
+  // ---------------------------------------------------------------- tables -> smem
+  if (FORM == FORM_F64) {
+    for (int i = tid; i < Lv; i += NT) tv[i] = tab[pp->o_v + i];
+    for (int i = tid; i < Lw; i += NT) tw[i] = tab[pp->o_w + i];
+    if (has_last)
+      for (int i = tid; i < nlast; i += NT) {
+        tvl[i] = tab[pp->o_vl + i];
+        twl[i] = tab[pp->o_wl + i];
+      }
+  } else {
+    for (int i = tid; i < Lv; i += NT) tv[i] = tab[pp->o_vf + i];
+    for (int i = tid; i < Lw; i += NT) tw[i] = tab[pp->o_wf + i];
+    if (has_last)
+      for (int i = tid; i < nlast; i += NT) {
+        tvl[i] = tab[pp->o_vlf + i];
+        twl[i] = tab[pp->o_wlf + i];
+      }
+  }
+
+  // ---------------------------------------------------------------- F -> smem (transposed)
+  for (int b = wid; b < nwin; b += NW) {
+    const int64_t m = wlo + b;
+    const int nb = (m == P - 1) ? nlast : n;
+    const double* src = A.F + off + m * (int64_t)n;
+    int i = lane;
+    for (; i + 96 < nb; i += 128) {
+      const double f0 = __ldcs(src + i), f1 = __ldcs(src + i + 32), f2 = __ldcs(src + i + 64),
+                   f3 = __ldcs(src + i + 96);
+      if (FORM == FORM_F64) {
+        S[(i)*LD + b] = f0;
+        S[(i + 32) * LD + b] = f1;
+        S[(i + 64) * LD + b] = f2;
+        S[(i + 96) * LD + b] = f3;
+      } else {
+        S2[(i)*LD + b] = f64_to_ff(f0);
+        S2[(i + 32) * LD + b] = f64_to_ff(f1);
+        S2[(i + 64) * LD + b] = f64_to_ff(f2);
+        S2[(i + 96) * LD + b] = f64_to_ff(f3);
+      }
+    }
+    for (; i < nb; i += 32) {
+      const double f0 = __ldcs(src + i);
+      if (FORM == FORM_F64)
+        S[i * LD + b] = f0;
+      else
+        S2[i * LD + b] = f64_to_ff(f0);
+    }
+  }
+  __syncthreads();
+
+  // ---------------------------------------------------------------- local sweeps (a1)
+  const bool act = tid < nwin;
+  const int64_t mb = wlo + tid;
+  const bool lastb = act && (mb == P - 1);
+  const int nbk = lastb ? nlast : n;
+  double xm1 = 0.0, alpha = 0.0, omega = 0.0;
+  if (act) {
+    const double v0 = lastb ? pp->v0l : pp->v0;
+    const double vend = lastb ? pp->vendl : pp->vend;
+    if (FORM == FORM_F64) {
+      const double rs = pp->rs, ib = pp->ib, g = pp->g;
+      double* col = S + tid;
+      double u = 0.0;
+      int i = 0;
+      for (; i + 4 <= nbk; i += 4) {
+        const double f0 = col[(i)*LD], f1 = col[(i + 1) * LD], f2 = col[(i + 2) * LD], f3 = col[(i + 3) * LD];
+        const double u0 = fma(rs, u, f0);
+        const double u1 = fma(rs, u0, f1);
+        const double u2 = fma(rs, u1, f2);
+        const double u3 = fma(rs, u2, f3);
+        col[(i)*LD] = u0;
+        col[(i + 1) * LD] = u1;
+        col[(i + 2) * LD] = u2;
+        col[(i + 3) * LD] = u3;
+        u = u3;
+      }
+      for (; i < nbk; ++i) {
+        u = fma(rs, u, col[i * LD]);
+        col[i * LD] = u;
+      }
+      double X = 0.0;
+      i = nbk - 1;
+      for (; i - 3 >= 0; i -= 4) {
+        const double a0 = col[(i)*LD], a1 = col[(i - 1) * LD], a2 = col[(i - 2) * LD], a3 = col[(i - 3) * LD];
+        const double X0 = fma(ib, X, a0);
+        const double X1 = fma(ib, X0, a1);
+        const double X2 = fma(ib, X1, a2);
+        const double X3 = fma(ib, X2, a3);
+        col[(i)*LD] = g * X0;
+        col[(i - 1) * LD] = g * X1;
+        col[(i - 2) * LD] = g * X2;
+        col[(i - 3) * LD] = g * X3;
+        X = X3;
+      }
+      for (; i >= 0; --i) {
+        X = fma(ib, X, col[i * LD]);
+        col[i * LD] = g * X;
+      }
+      xm1 = g * ib * X;
+      alpha = col[0] - xm1 * v0;
+      omega = col[(nbk - 1) * LD] - xm1 * vend;
+    } else {
+      const float rh = pp->rs_h, rl = pp->rs_l, bh = pp->ib_h, bl = pp->ib_l, gh = pp->g_h, gl = pp->g_l;
+      float2* col = S2 + tid;
+      float uh = 0.f, ul = 0.f;
+      int i = 0;
+      for (; i + 4 <= nbk; i += 4) {
+        const float2 f0 = col[(i)*LD], f1 = col[(i + 1) * LD], f2 = col[(i + 2) * LD], f3 = col[(i + 3) * LD];
+        float2 o0, o1, o2, o3;
+        ff_axpy(f0.x, f0.y, rh, rl, uh, ul, o0.x, o0.y);
+        ff_axpy(f1.x, f1.y, rh, rl, o0.x, o0.y, o1.x, o1.y);
+        ff_axpy(f2.x, f2.y, rh, rl, o1.x, o1.y, o2.x, o2.y);
+        ff_axpy(f3.x, f3.y, rh, rl, o2.x, o2.y, o3.x, o3.y);
+        col[(i)*LD] = o0;
+        col[(i + 1) * LD] = o1;
+        col[(i + 2) * LD] = o2;
+        col[(i + 3) * LD] = o3;
+        uh = o3.x;
+        ul = o3.y;
+      }
+      for (; i < nbk; ++i) {
+        const float2 f0 = col[i * LD];
+        ff_axpy(f0.x, f0.y, rh, rl, uh, ul, uh, ul);
+        col[i * LD] = make_float2(uh, ul);
+      }
+      float Xh = 0.f, Xl = 0.f;
+      i = nbk - 1;
+      for (; i - 3 >= 0; i -= 4) {
+        const float2 a0 = col[(i)*LD], a1 = col[(i - 1) * LD], a2 = col[(i - 2) * LD], a3 = col[(i - 3) * LD];
+        float2 X0, X1, X2, X3, y0, y1, y2, y3;
+        ff_axpy(a0.x, a0.y, bh, bl, Xh, Xl, X0.x, X0.y);
+        ff_axpy(a1.x, a1.y, bh, bl, X0.x, X0.y, X1.x, X1.y);
+        ff_axpy(a2.x, a2.y, bh, bl, X1.x, X1.y, X2.x, X2.y);
+        ff_axpy(a3.x, a3.y, bh, bl, X2.x, X2.y, X3.x, X3.y);
+        ff_mul(gh, gl, X0.x, X0.y, y0.x, y0.y);
+        ff_mul(gh, gl, X1.x, X1.y, y1.x, y1.y);
+        ff_mul(gh, gl, X2.x, X2.y, y2.x, y2.y);
+        ff_mul(gh, gl, X3.x, X3.y, y3.x, y3.y);
+        col[(i)*LD] = y0;
+        col[(i - 1) * LD] = y1;
+        col[(i - 2) * LD] = y2;
+        col[(i - 3) * LD] = y3;
+        Xh = X3.x;
+        Xl = X3.y;
+      }
+      for (; i >= 0; --i) {
+        const float2 a0 = col[i * LD];
+        ff_axpy(a0.x, a0.y, bh, bl, Xh, Xl, Xh, Xl);
+        float2 y0;
+        ff_mul(gh, gl, Xh, Xl, y0.x, y0.y);
+        col[i * LD] = y0;
+      }
+      const double X0d = (double)Xh + (double)Xl;
+      xm1 = pp->g * pp->ib * X0d;
+      const float2 p0 = col[0], pe = col[(nbk - 1) * LD];
+      alpha = ((double)p0.x + (double)p0.y) - xm1 * v0;
+      omega = ((double)pe.x + (double)pe.y) - xm1 * vend;
+    }
+  }
+
+  // ---------------------------------------------------------------- beta (eq. 16)
+  const double* bc = tab + pp->o_bcm;
+  if (act) {
+    if (mb < pp->kl)
+      bc = tab + pp->o_bcl + mb * kBC;
+    else if (mb >= P - pp->kr)
+      bc = tab + pp->o_bcr + (mb - (P - pp->kr)) * kBC;
+  }
+  const double bL = act ? fma(bc[BC_M00], alpha, bc[BC_M01] * omega) : 0.0;
+  const double bR = act ? fma(bc[BC_M10], alpha, bc[BC_M11] * omega) : 0.0;
+
+  if (A.mode == MODE_BETA) {
+    if (act) {
+      A.beta[2 * mb] = bL;
+      A.beta[2 * mb + 1] = bR;
+    }
+    return;
+  }
+
+  double XL = 0.0, XR = 0.0;
+  if (A.mode == MODE_FULL) {
+    // ------------------------------------------------------------ dichotomy tree (a2)
+    // prefix maps A -> a A + b beta^R (left to right), suffix maps B -> c B + d beta^L
+    double pa = act ? bc[BC_A] : 1.0, pb = act ? bc[BC_B] * bR : 0.0;
+    double qa = act ? bc[BC_C] : 1.0, qb = act ? bc[BC_D] * bL : 0.0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const double ya = __shfl_up_sync(0xffffffffu, pa, d), yb = __shfl_up_sync(0xffffffffu, pb, d);
+      const double za = __shfl_down_sync(0xffffffffu, qa, d), zb = __shfl_down_sync(0xffffffffu, qb, d);
+      if (lane >= d) {
+        pb = fma(pa, yb, pb);
+        pa = pa * ya;
+      }
+      if (lane + d < 32) {
+        qb = fma(qa, zb, qb);
+        qa = qa * za;
+      }
+    }
+    if (lane == 31) {
+      swa[wid] = pa;
+      swa[NW + wid] = pb;
+    }
+    if (lane == 0) {
+      swa[2 * NW + wid] = qa;
+      swa[3 * NW + wid] = qb;
+    }
+    // previous lane's inclusive prefix, next lane's inclusive suffix
+    double ea = __shfl_up_sync(0xffffffffu, pa, 1), eb = __shfl_up_sync(0xffffffffu, pb, 1);
+    double fa = __shfl_down_sync(0xffffffffu, qa, 1), fb = __shfl_down_sync(0xffffffffu, qb, 1);
+    if (lane == 0) {
+      ea = 1.0;
+      eb = 0.0;
+    }
+    if (lane == 31) {
+      fa = 1.0;
+      fb = 0.0;
+    }
+    __syncthreads();
+    double Aw = 0.0, Bw = 0.0;  // zero coupling enters at both window ends
+    for (int w = 0; w < wid; ++w) Aw = fma(swa[w], Aw, swa[NW + w]);
+    for (int w = NW - 1; w > wid; --w) Bw = fma(swa[2 * NW + w], Bw, swa[3 * NW + w]);
+    const double Am = fma(ea, Aw, eb);
+    const double Bm = fma(fa, Bw, fb);
+    const double xs = Am + bL + bc[BC_TL] * Bm;
+    const double xe = fma(bc[BC_TR], Am, bR + Bm);
+    sxs[tid] = xs;
+    sxe[tid] = xe;
+    __syncthreads();
+    if (act) {
+      XL = (mb == 0 || tid == 0) ? 0.0 : sxe[tid - 1];
+      XR = (mb == P - 1 || tid + 1 >= nwin) ? 0.0 : sxs[tid + 1];
+    }
+  } else {  // MODE_APPLY: first/last values of the neighbours from the global scan
+    if (act) {
+      XL = (mb == 0) ? 0.0 : A.iface[2 * (mb - 1) + 1];
+      XR = (mb == P - 1) ? 0.0 : A.iface[2 * (mb + 1)];
+    }
+  }
+  scl[tid] = XL - xm1;
+  scr[tid] = XR;
+  __syncthreads();
+
+  // ---------------------------------------------------------------- correction + store (a3)
+  const bool adj = (A.xf != nullptr);
+  double g0 = 0.0, gm = 0.0, gp = 0.0;
+  unsigned bad = 0u;
+  const int64_t N = pp->N;
+  for (int b = hl + wid; b < hl + nown; b += NW) {
+    const int64_t m = wlo + b;
+    const bool lb = (m == P - 1);
+    const int nb = lb ? nlast : n;
+    const int lv = lb ? nlast : Lv, lw = lb ? nlast : Lw;
+    const double cL = scl[b], cR = scr[b];
+    const int64_t row0 = m * (int64_t)n;
+    double* dst = A.x + off + row0;
+    if (FORM == FORM_F64) {
+      const double* v = lb ? tvl : tv;
+      const double* wr = lb ? twl : tw;
+      for (int i = lane; i < nb; i += 32) {
+        double val = S[i * LD + b];
+        if (i < lv) val = fma(cL, v[i], val);
+        const int j = nb - 1 - i;
+        if (j < lw) val = fma(cR, wr[j], val);
+        __stcs(dst + i, val);
+        if (A.check_finite && !isfinite(val)) bad = 1u;
+        if (adj) {
+          const int64_t r = row0 + i;
+          const double* xr = A.xf + off + r;
+          g0 = fma(val, xr[0], g0);
+          if (r > 0) gm = fma(val, xr[-1], gm);
+          if (r + 1 < N) gp = fma(val, xr[1], gp);
+        }
+      }
+    } else {
+      const float2* v = reinterpret_cast<const float2*>(lb ? tvl : tv);
+      const float2* wr = reinterpret_cast<const float2*>(lb ? twl : tw);
+      const float2 cl2 = f64_to_ff_rn(cL), cr2 = f64_to_ff_rn(cR);
+      for (int i = lane; i < nb; i += 32) {
+        float2 val = S2[i * LD + b];
+        if (i < lv) {
+          const float2 vv = v[i];
+          ff_fma_acc(cl2.x, cl2.y, vv.x, vv.y, val.x, val.y);
+        }
+        const int j = nb - 1 - i;
+        if (j < lw) {
+          const float2 ww = wr[j];
+          ff_fma_acc(cr2.x, cr2.y, ww.x, ww.y, val.x, val.y);
+        }
+        const double dv = ff_to_f64(val.x, val.y);
+        __stcs(dst + i, dv);
+        if (A.check_finite && !isfinite(dv)) bad = 1u;
+        if (adj) {
+          const int64_t r = row0 + i;
+          const double* xr = A.xf + off + r;
+          g0 = fma(dv, xr[0], g0);
+          if (r > 0) gm = fma(dv, xr[-1], gm);
+          if (r + 1 < N) gp = fma(dv, xr[1], gp);
+        }
+      }
+    }
+  }
+  if (bad) atomicOr(A.status, (unsigned)ST_NONFINITE);
+  if (adj) {
+    // CTA sum of the three gradient partials in a fixed order
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      g0 += __shfl_down_sync(0xffffffffu, g0, d);
+      gm += __shfl_down_sync(0xffffffffu, gm, d);
+      gp += __shfl_down_sync(0xffffffffu, gp, d);
+    }
+    __syncthreads();
+    if (lane == 0) {
+      swa[wid] = gm;
+      swa[NW + wid] = g0;
+      swa[2 * NW + wid] = gp;
+    }
+    __syncthreads();
+    if (tid < 3) {
+      double s = 0.0;
+      for (int w = 0; w < NW; ++w) s += swa[tid * NW + w];
+      A.part[3 * (size_t)blockIdx.x + tid] = s;
+    }
+  }
+}
+
+}  // namespace dich

@@ -1,0 +1,296 @@
+"""Python face of the Dichotomy solver: the C entry points with torch tensors.
+
+Functions named after the C ABI (``dichotomy_plan``, ``dichotomy_solve``, ...) marshal
+torch CUDA tensors to device pointers and torch's current stream to a cudaStream_t.  The
+classes ``Plan`` and ``Batch`` own the device workspace (a uint8 torch tensor) that the
+library needs; ``DichotomySolve`` / ``DichotomySolveBatched`` are autograd Functions whose
+backward is the library's adjoint kernel (Not in the paper: dL/dF = T^-T w,
+dL/dt = -(sum lambda_i x_{i-1}, sum lambda_i x_i, sum lambda_i x_{i+1})).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import (FLAG_CHECK_FINITE, FLAG_FORCE_GENERAL, PREC_AUTO, PREC_F64, PREC_MIXED, DichotomyError,
+                   check, make_opts)
+
+__all__ = [
+    "dichotomy_plan", "dichotomy_plan_info", "dichotomy_plan_workspace_bytes", "dichotomy_plan_bind",
+    "dichotomy_solve", "dichotomy_adjoint", "dichotomy_status", "dichotomy_destroy",
+    "dichotomy_batch_prepare", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
+    "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
+    "dichotomy_batch_destroy", "Plan", "Batch", "solve", "DichotomySolve", "DichotomySolveBatched",
+    "PREC_F64", "PREC_MIXED", "PREC_AUTO", "FLAG_FORCE_GENERAL", "FLAG_CHECK_FINITE", "DichotomyError",
+]
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev(t: torch.Tensor, name: str) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor (the solver has no CPU path)")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ C entry points
+def dichotomy_plan(t_m1: float, t_0: float, t_1: float, N: int, opts=None) -> ctypes.c_void_p:
+    L = _lib.load()
+    h = ctypes.c_void_p()
+    if opts is None:
+        check(L.dichotomy_plan(float(t_m1), float(t_0), float(t_1), int(N), ctypes.byref(h)), "dichotomy_plan")
+    else:
+        check(L.dichotomy_plan_ex(float(t_m1), float(t_0), float(t_1), int(N), ctypes.byref(opts), ctypes.byref(h)),
+              "dichotomy_plan_ex")
+    return h
+
+
+def dichotomy_plan_info(plan) -> dict:
+    info = _lib.dich_plan_info()
+    check(_lib.load().dichotomy_plan_info(plan, ctypes.byref(info)), "dichotomy_plan_info")
+    return {name: getattr(info, name) for name, _ in info._fields_}
+
+
+def dichotomy_plan_workspace_bytes(plan) -> int:
+    n = ctypes.c_size_t()
+    check(_lib.load().dichotomy_plan_workspace_bytes(plan, ctypes.byref(n)), "dichotomy_plan_workspace_bytes")
+    return int(n.value)
+
+
+def dichotomy_plan_bind(plan, workspace: torch.Tensor, stream=None) -> None:
+    if not workspace.is_cuda:
+        raise TypeError("workspace must be a CUDA tensor")
+    check(_lib.load().dichotomy_plan_bind(plan, ctypes.c_void_p(workspace.data_ptr()),
+                                          workspace.numel() * workspace.element_size(), _stream(stream)),
+          "dichotomy_plan_bind")
+
+
+def dichotomy_solve(plan, F: torch.Tensor, x: torch.Tensor, stream=None) -> None:
+    check(_lib.load().dichotomy_solve(plan, _dev(F, "F"), _dev(x, "x"), _stream(stream)), "dichotomy_solve")
+
+
+def dichotomy_adjoint(plan, w: torch.Tensor, x: torch.Tensor, gF: torch.Tensor, gt: torch.Tensor,
+                      stream=None) -> None:
+    check(_lib.load().dichotomy_adjoint(plan, _dev(w, "w"), _dev(x, "x"), _dev(gF, "gF"), _dev(gt, "gt"),
+                                        _stream(stream)), "dichotomy_adjoint")
+
+
+def dichotomy_status(plan, stream=None) -> int:
+    s = ctypes.c_int(0)
+    check(_lib.load().dichotomy_status(plan, _stream(stream), ctypes.byref(s)), "dichotomy_status")
+    return int(s.value)
+
+
+def dichotomy_destroy(plan) -> None:
+    _lib.load().dichotomy_destroy(plan)
+
+
+def _host_i64(a):
+    import numpy as np
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+
+
+def _host_f64(a):
+    import numpy as np
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def dichotomy_batch_prepare(N, offset, t_m1, t_0, t_1, opts=None) -> ctypes.c_void_p:
+    N, offset = _host_i64(N), _host_i64(offset)
+    tm1, t0, tp1 = _host_f64(t_m1), _host_f64(t_0), _host_f64(t_1)
+    nsys = N.size
+    if not (offset.size == tm1.size == t0.size == tp1.size == nsys):
+        raise ValueError("batch arrays must have one entry per system")
+    h = ctypes.c_void_p()
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    check(_lib.load().dichotomy_batch_prepare(nsys, p(N), p(offset), p(tm1), p(t0), p(tp1),
+                                              ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)),
+          "dichotomy_batch_prepare")
+    return h
+
+
+def dichotomy_batch_workspace_bytes(batch) -> int:
+    n = ctypes.c_size_t()
+    check(_lib.load().dichotomy_batch_workspace_bytes(batch, ctypes.byref(n)), "dichotomy_batch_workspace_bytes")
+    return int(n.value)
+
+
+def dichotomy_batch_bind(batch, workspace: torch.Tensor, stream=None) -> None:
+    check(_lib.load().dichotomy_batch_bind(batch, ctypes.c_void_p(workspace.data_ptr()),
+                                           workspace.numel() * workspace.element_size(), _stream(stream)),
+          "dichotomy_batch_bind")
+
+
+def dichotomy_solve_batched(batch, F: torch.Tensor, x: torch.Tensor, stream=None) -> None:
+    check(_lib.load().dichotomy_solve_batched(batch, _dev(F, "F"), _dev(x, "x"), _stream(stream)),
+          "dichotomy_solve_batched")
+
+
+def dichotomy_adjoint_batched(batch, w, x, gF, gt, stream=None) -> None:
+    check(_lib.load().dichotomy_adjoint_batched(batch, _dev(w, "w"), _dev(x, "x"), _dev(gF, "gF"), _dev(gt, "gt"),
+                                                _stream(stream)), "dichotomy_adjoint_batched")
+
+
+def dichotomy_batch_status(batch, stream=None) -> int:
+    s = ctypes.c_int(0)
+    check(_lib.load().dichotomy_batch_status(batch, _stream(stream), ctypes.byref(s)), "dichotomy_batch_status")
+    return int(s.value)
+
+
+def dichotomy_batch_info(batch) -> dict:
+    import numpy as np
+    ns, nw = ctypes.c_int64(), ctypes.c_int64()
+    check(_lib.load().dichotomy_batch_info(batch, ctypes.byref(ns), ctypes.byref(nw), None), "dichotomy_batch_info")
+    forms = np.zeros(ns.value, dtype=np.int32)
+    check(_lib.load().dichotomy_batch_info(batch, None, None, forms.ctypes.data_as(ctypes.c_void_p)),
+          "dichotomy_batch_info")
+    return {"nsys": ns.value, "windows": nw.value, "form": forms}
+
+
+def dichotomy_batch_destroy(batch) -> None:
+    _lib.load().dichotomy_batch_destroy(batch)
+
+
+# ------------------------------------------------------------------ owning wrappers
+class Plan:
+    """A bound single-system plan: T = tridiag{t_m1, t_0, t_1} of order N on a CUDA device."""
+
+    def __init__(self, t_m1, t_0, t_1, N, block_size=0, precision=PREC_F64, threads=0, flags=0, trunc_eps=0.0,
+                 device=None, stream=None):
+        self.t = (float(t_m1), float(t_0), float(t_1))
+        self.N = int(N)
+        self._h = None
+        opts = make_opts(block_size, precision, threads, flags, trunc_eps)
+        self._h = dichotomy_plan(t_m1, t_0, t_1, N, opts)
+        self.info = dichotomy_plan_info(self._h)
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.empty(max(1, self.info["workspace_bytes"]), dtype=torch.uint8, device=dev)
+        dichotomy_plan_bind(self._h, self.workspace, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def solve(self, F: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        x = torch.empty_like(F) if out is None else out
+        dichotomy_solve(self._h, F, x, stream)
+        return x
+
+    def adjoint(self, w: torch.Tensor, x: torch.Tensor, stream=None):
+        gF = torch.empty_like(w)
+        gt = torch.empty(3, dtype=torch.float64, device=w.device)
+        dichotomy_adjoint(self._h, w, x, gF, gt, stream)
+        return gF, gt
+
+    def status(self, stream=None) -> int:
+        return dichotomy_status(self._h, stream)
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and _lib._lib_obj is not None:
+            _lib._lib_obj.dichotomy_destroy(self._h)
+            self._h = None
+
+
+class Batch:
+    """A bound batch of independent Toeplitz systems stored back to back in one vector."""
+
+    def __init__(self, N, t_m1, t_0, t_1, offset=None, block_size=0, precision=PREC_F64, threads=0, flags=0,
+                 trunc_eps=0.0, device=None, stream=None):
+        import numpy as np
+        N = _host_i64(N)
+        if offset is None:
+            offset = np.concatenate([[0], np.cumsum(N)[:-1]]).astype(np.int64) if N.size else np.zeros(0, np.int64)
+        self.N = N
+        self.offset = _host_i64(offset)
+        self.total = int((self.offset + N).max()) if N.size else 0
+        self._h = None
+        opts = make_opts(block_size, precision, threads, flags, trunc_eps)
+        self._h = dichotomy_batch_prepare(N, self.offset, t_m1, t_0, t_1, opts)
+        self.info = dichotomy_batch_info(self._h)
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.empty(max(1, dichotomy_batch_workspace_bytes(self._h)), dtype=torch.uint8, device=dev)
+        dichotomy_batch_bind(self._h, self.workspace, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def nsys(self) -> int:
+        return int(self.N.size)
+
+    def solve(self, F: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        x = torch.empty_like(F) if out is None else out
+        dichotomy_solve_batched(self._h, F, x, stream)
+        return x
+
+    def adjoint(self, w: torch.Tensor, x: torch.Tensor, stream=None):
+        gF = torch.empty_like(w)
+        gt = torch.empty((self.nsys, 3), dtype=torch.float64, device=w.device)
+        dichotomy_adjoint_batched(self._h, w, x, gF, gt, stream)
+        return gF, gt
+
+    def status(self, stream=None) -> int:
+        return dichotomy_batch_status(self._h, stream)
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and _lib._lib_obj is not None:
+            _lib._lib_obj.dichotomy_batch_destroy(self._h)
+            self._h = None
+
+
+def solve(t, F: torch.Tensor, **kw) -> torch.Tensor:
+    """One-shot x = T^-1 F (plans and binds on every call; keep a Plan for repeated solves)."""
+    return Plan(t[0], t[1], t[2], F.numel(), **kw).solve(F)
+
+
+# ------------------------------------------------------------------ autograd
+class DichotomySolve(torch.autograd.Function):
+    """x = T(t)^-1 F for one system; t = tensor([t_-1, t_0, t_1]) (float64).
+
+    The backward pass is one adjoint launch: dL/dF = T^-T dL/dx and dL/dt from the fused
+    -lambda.x products.  (The coefficients are read on the host to build the plan.)"""
+
+    @staticmethod
+    def forward(ctx, F, t, precision=PREC_F64):
+        tv = [float(v) for v in t.detach().cpu().tolist()]
+        plan = Plan(tv[0], tv[1], tv[2], F.numel(), precision=precision, device=F.device)
+        x = plan.solve(F.detach().contiguous())
+        ctx.plan = plan
+        ctx.save_for_backward(x)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        gF, gt = ctx.plan.adjoint(gx.contiguous(), x)
+        return gF, gt.to(dtype=torch.float64), None
+
+
+class DichotomySolveBatched(torch.autograd.Function):
+    """Batched x_s = T(t_s)^-1 F_s; F: [sum N] (systems back to back), t: [nsys, 3]."""
+
+    @staticmethod
+    def forward(ctx, F, t, N, precision=PREC_F64):
+        tv = t.detach().cpu().double().numpy()
+        batch = Batch(N, tv[:, 0], tv[:, 1], tv[:, 2], precision=precision, device=F.device)
+        x = batch.solve(F.detach().contiguous())
+        ctx.batch = batch
+        ctx.save_for_backward(x)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        gF, gt = ctx.batch.adjoint(gx.contiguous(), x)
+        return gF, gt, None, None

@@ -1,0 +1,179 @@
+"""CPU tests of the C ABI boundary: the library loads, exports every symbol that
+include/dichotomy.h declares, and its host-only planning logic (the Toeplitz preliminary
+step, block partition, path choice, argument validation) behaves.  No GPU calls."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    from paper_1002_2469_gb300 import _lib as L
+    return L, L.load()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "dichotomy.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dichotomy_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_north_star_calls():
+    syms = declared_symbols()
+    for s in ("dichotomy_plan", "dichotomy_solve", "dichotomy_solve_batched", "dichotomy_adjoint"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol():
+    L, lib = _lib()
+    for s in declared_symbols():
+        assert hasattr(lib, s), f"{s} not exported"
+    assert sorted(L.EXPORTS) == declared_symbols()
+    assert lib.dichotomy_version().decode().count(".") == 2
+
+
+def test_exports_are_c_symbols_in_the_binary():
+    L, _ = _lib()
+    out = os.popen(f"nm -D --defined-only {L.lib_path()}").read()
+    names = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    for s in declared_symbols():
+        assert s in names
+
+
+def test_library_targets_sm_103a_only():
+    L, _ = _lib()
+    out = os.popen(f"cuobjdump --list-elf {L.lib_path()} 2>/dev/null").read()
+    if not out:
+        pytest.skip("cuobjdump unavailable")
+    archs = set(re.findall(r"sm_\d+a?", out))
+    assert archs == {"sm_103a"}
+
+
+def plan_info(t, N, **kw):
+    from paper_1002_2469_gb300 import dichotomy as D
+    h = D.dichotomy_plan(t[0], t[1], t[2], N, D.make_opts(**kw) if kw else None)
+    try:
+        return D.dichotomy_plan_info(h)
+    finally:
+        D.dichotomy_destroy(h)
+
+
+def status_of(t, N, **kw):
+    from paper_1002_2469_gb300 import _lib as L
+    lib = L.load()
+    h = ctypes.c_void_p()
+    opts = L.make_opts(**kw)
+    rc = lib.dichotomy_plan_ex(t[0], t[1], t[2], N, ctypes.byref(opts), ctypes.byref(h))
+    if rc == 0:
+        lib.dichotomy_destroy(h)
+    return rc
+
+
+def test_roots_match_characteristic_polynomial():
+    for t in [(-1.2, 2.5, -0.8), (-1.0, 4.0, -1.0), (0.7, 2.5, -1.1), (-1.0, 2.001, -1.0), (0.0, 2.0, -1.0)]:
+        info = plan_info(t, 1000)
+        tm1, t0, tp1 = t
+        roots = np.roots([tp1, t0, tm1]) if tp1 != 0 else np.array([-tm1 / t0])
+        small = roots[np.argmin(np.abs(roots))]
+        assert abs(info["rs"] - small) < 1e-13 * max(1.0, abs(small))
+        if tp1 != 0 and tm1 != 0:
+            big = roots[np.argmax(np.abs(roots))]
+            assert abs(info["ib"] - 1.0 / big) < 1e-13
+        assert abs(info["z"] - info["rs"] * info["ib"]) < 1e-15
+        assert abs(info["rs"]) <= 1.0 and abs(info["ib"]) <= 1.0
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 7, 64, 65, 129, 1000, 4097, 65537, 1 << 20, (1 << 26) + 1])
+@pytest.mark.parametrize("threads", [64, 128, 256])
+def test_partition_every_block_has_two_rows(N, threads):
+    info = plan_info((-1.2, 2.5, -0.8), N, threads=threads)
+    n, P, nl = info["n"], info["P"], info["n_last"]
+    assert n >= 2 and nl >= 2 and nl <= n
+    assert (P - 1) * n + nl == N
+    assert info["tiles"] >= 1
+    if P <= threads:
+        assert info["path"] == 0 and info["tiles"] == 1
+
+
+def test_halo_path_and_general_path():
+    strong = plan_info((-1.2, 2.5, -0.8), 1 << 24)
+    assert strong["path"] == 1 and strong["halo_l"] >= 1 and strong["halo_r"] >= 1
+    # the halo covers the decay of the coupling: |rs|^(n * halo_l) is below 2^-64
+    assert abs(strong["rs"]) ** (strong["n"] * strong["halo_l"]) < 2.0 ** -64
+    assert abs(strong["ib"]) ** (strong["n"] * strong["halo_r"]) < 2.0 ** -64
+    forced = plan_info((-1.2, 2.5, -0.8), 1 << 24, flags=1)
+    assert forced["path"] == 2 and forced["halo_l"] == 0
+    # the 1-D Laplacian has a double root on the unit circle: no decay, general path
+    lap = plan_info((-1.0, 2.0, -1.0), 1 << 20)
+    assert lap["path"] == 2
+    assert lap["kl"] == lap["P"]          # every block keeps end-dependent ratios
+
+
+def test_spike_truncation_lengths():
+    info = plan_info((-1.0, 4.0, -1.0), 1 << 22)
+    rs = abs(info["rs"])
+    # v_i ~ rs^{i+1}: the first dropped term is below 2^-64
+    assert rs ** (info["Lv"]) < 2.0 ** -64 * 4
+    assert info["Lv"] < info["n"]
+
+
+@pytest.mark.parametrize("t,code", [
+    ((-1.0, 1.5, -1.0), 2),        # not diagonally dominant (eq. 32-33)
+    ((0.0, 0.0, 0.0), 3),          # singular
+    ((float("nan"), 2.0, -1.0), 1),
+    ((-1.0, float("inf"), -1.0), 1),
+])
+def test_plan_rejects_bad_coefficients(t, code):
+    assert status_of(t, 100) == code
+
+
+def test_plan_argument_validation():
+    assert status_of((-1.0, 4.0, -1.0), -1) == 1
+    assert status_of((-1.0, 4.0, -1.0), 100, block_size=1) == 1
+    assert status_of((-1.0, 4.0, -1.0), 100, threads=96) == 1
+    assert status_of((-1.0, 4.0, -1.0), 100, precision=7) == 1
+    assert status_of((-1.0, 4.0, -1.0), 0) == 0
+    assert status_of((-1.0, 4.0, -1.0), 1) == 0
+    # dominance with equality is accepted (end rows strict)
+    assert status_of((-1.2, 2.0, -0.8), 100) == 0
+
+
+def test_precision_policy_auto():
+    strong = plan_info((-1.2, 2.5, -0.8), 1 << 20, precision=2)
+    weak = plan_info((-1.0, 2.0 + 1e-6, -1.0), 1 << 20, precision=2)
+    assert strong["precision"] == 1 and weak["precision"] == 0
+
+
+def test_batch_prepare_host_only():
+    from paper_1002_2469_gb300 import dichotomy as D
+    N = np.array([0, 1, 2, 100, 5000, 300000])
+    tm1 = np.full(N.size, -0.8)
+    t0 = np.full(N.size, 2.5)
+    tp1 = np.full(N.size, -1.2)
+    h = D.dichotomy_batch_prepare(N, np.concatenate([[0], np.cumsum(N)[:-1]]), tm1, t0, tp1)
+    try:
+        info = D.dichotomy_batch_info(h)
+        assert info["nsys"] == N.size
+        assert info["windows"] >= 4
+        assert D.dichotomy_batch_workspace_bytes(h) > 0
+    finally:
+        D.dichotomy_batch_destroy(h)
+
+
+def test_unbound_and_null_arguments_are_rejected_without_a_gpu():
+    from paper_1002_2469_gb300 import _lib as L
+    lib = L.load()
+    h = ctypes.c_void_p()
+    assert lib.dichotomy_plan(-1.0, 4.0, -1.0, 10, ctypes.byref(h)) == 0
+    try:
+        assert lib.dichotomy_solve(h, None, None, None) == 8          # DICH_ERR_UNBOUND
+        assert lib.dichotomy_plan_bind(h, None, 0, None) == 1         # NULL workspace
+        assert lib.dichotomy_plan(-1.0, 4.0, -1.0, 10, None) == 1     # NULL out
+    finally:
+        lib.dichotomy_destroy(h)
+    assert lib.dichotomy_strerror(2).decode().startswith("matrix is not")

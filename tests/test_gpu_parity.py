@@ -1,0 +1,312 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Bar (the benchmark spec's tolerance): norm-wise relative error max|x - x_oracle| / max|x_oracle|
+<= 1e-12 for diagonally dominant FP64 systems, in both the FP64 and the MIXED form.  For the
+ill-conditioned extras (weak dominance, the 1-D Laplacian) the binary128 oracle arbitrates:
+the GPU error against it must stay within the FP64 oracle's own error (times a small factor).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import workloads as W  # noqa: E402
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def D():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1002_2469_gb300 as pkg
+    return pkg
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def gpu_solve(D, t, F, **kw):
+    plan = D.Plan(t[0], t[1], t[2], F.size, **kw)
+    Fd = torch.from_numpy(F).cuda()
+    x = plan.solve(Fd)
+    st = plan.status()
+    assert st == 0, f"device status {st}"
+    return x.cpu().numpy(), plan.info
+
+
+T_WELL = [(-1.0, 4.0, -1.0), (-1.2, 2.5, -0.8), (-0.8, 2.5, -1.2), (0.7, 2.5, -1.1), (0.0, 2.0, -1.0),
+          (-1.0, 2.0, 0.0), (-0.5, 3.0, 0.25), (2.0, -5.0, 1.5)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("t", T_WELL)
+@pytest.mark.parametrize("N", [2, 3, 5, 31, 64, 257, 1000, 4097, 65537, 300001])
+def test_single_well_conditioned(D, t, N, prec):
+    rng = np.random.default_rng(N)
+    F = rng.uniform(-1, 1, N)
+    x, info = gpu_solve(D, t, F, precision=prec)
+    assert rel(x, oracle.thomas(t, F)) < TOL, info
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("threads", [64, 128, 256])
+@pytest.mark.parametrize("bs", [2, 3, 7, 32, 45, 100])
+def test_block_sizes_and_widths(D, threads, bs, prec):
+    t = (-1.2, 2.5, -0.8)
+    N = 77777
+    F = np.random.default_rng(bs).standard_normal(N)
+    x, info = gpu_solve(D, t, F, block_size=bs, threads=threads, precision=prec)
+    assert info["n"] <= bs + 2
+    assert rel(x, oracle.thomas(t, F)) < TOL, info
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("t", [(-1.2, 2.5, -0.8), (-1.0, 4.0, -1.0), (-1.0, 2.001, -1.0)])
+def test_general_path_matches_halo_path(D, t, prec):
+    N = 1 << 19
+    F = np.random.default_rng(7).standard_normal(N)
+    xg, ig = gpu_solve(D, t, F, flags=1, precision=prec)
+    xh, ih = gpu_solve(D, t, F, precision=prec)
+    assert ig["path"] == 2
+    ref = oracle.thomas(t, F)
+    assert rel(xg, ref) < TOL and rel(xh, ref) < TOL
+
+
+@pytest.mark.parametrize("t,N", [((-1.0, 2.001, -1.0), 200000), ((-1.0, 2.0, -1.0), 4096),
+                                 ((-1.2, 2.0, -0.8), 50000), ((-1.0, 2.0 + 5.88e-7, -1.0), 4096)])
+def test_ill_conditioned_against_binary128(D, t, N):
+    F = np.random.default_rng(3).uniform(-1, 1, N)
+    xq = oracle.thomas_q(t, F)
+    e_oracle = rel(oracle.thomas(t, F), xq)
+    x, info = gpu_solve(D, t, F)
+    assert rel(x, xq) <= max(TOL, 20 * e_oracle), info
+
+
+def test_c1_full_and_manufactured(D):
+    t, F = W.single_c1()
+    x, info = gpu_solve(D, t, F, block_size=256)
+    assert info["P"] == 256
+    assert rel(x, oracle.thomas(t, F)) < TOL
+    xs = W.manufactured_x(65536)
+    Fm = oracle.matvec(t, xs)
+    x2, _ = gpu_solve(D, t, Fm, block_size=256)
+    assert rel(x2, oracle.thomas(t, Fm)) < TOL
+    assert rel(x2, xs) < 1e-14
+
+
+@pytest.mark.parametrize("weak", [False, True])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_c2_full_size(D, weak, prec):
+    t, F = W.single_c2(weak=weak)
+    x, info = gpu_solve(D, t, F, precision=prec)
+    ref = oracle.thomas(t, F)
+    assert rel(x, ref) < TOL, info
+    # and the oracle, sampled: residual rows of the GPU solution
+    idx = np.random.default_rng(0).integers(1, F.size - 1, 1000)
+    r = t[0] * x[idx - 1] + t[1] * x[idx] + t[2] * x[idx + 1] - F[idx]
+    assert np.max(np.abs(r)) < 1e-12 * (abs(t[0]) + abs(t[1]) + abs(t[2])) * np.max(np.abs(x))
+
+
+def test_determinism_and_p_invariance(D):
+    t = (-1.2, 2.5, -0.8)
+    N = 123457
+    F = np.random.default_rng(11).standard_normal(N)
+    plan = D.Plan(*t, N)
+    Fd = torch.from_numpy(F).cuda()
+    a = plan.solve(Fd).cpu().numpy()
+    b = plan.solve(Fd).cpu().numpy()
+    assert np.array_equal(a, b)
+    xs = [gpu_solve(D, t, F, block_size=bs)[0] for bs in (3, 17, 64, 150)]
+    for x in xs:
+        assert rel(x, a) < 2e-15
+
+
+def test_trivial_sizes(D):
+    for N in (0, 1, 2):
+        F = np.arange(1, N + 1, dtype=np.float64)
+        plan = D.Plan(-1.0, 4.0, -1.0, N)
+        x = plan.solve(torch.from_numpy(F).cuda()).cpu().numpy()
+        if N:
+            assert rel(x, oracle.thomas((-1.0, 4.0, -1.0), F)) < TOL
+
+
+def test_nonfinite_is_flagged(D):
+    N = 10000
+    F = np.ones(N)
+    F[5000] = np.inf
+    plan = D.Plan(-1.0, 4.0, -1.0, N, flags=2)
+    plan.solve(torch.from_numpy(F).cuda())
+    assert plan.status() == 5
+    assert plan.status() == 0   # the word is cleared by reading it
+
+
+def test_bad_arguments_are_rejected(D):
+    N = 1000
+    plan = D.Plan(-1.0, 4.0, -1.0, N)
+    Fh = torch.ones(N, dtype=torch.float64)
+    Fd = Fh.cuda()
+    with pytest.raises(TypeError):
+        plan.solve(Fh)                                           # host tensor: no CPU path
+    with pytest.raises(D.DichotomyError) as e:
+        D.dichotomy_solve(plan.handle, Fd, Fd)                   # x aliases F
+    assert e.value.code == 7
+    import ctypes
+    from paper_1002_2469_gb300 import _lib as L
+    lib = L.load()
+    # a host pointer passed through the C ABI is refused (no CPU fallback)
+    rc = lib.dichotomy_solve(plan.handle, ctypes.c_void_p(Fh.data_ptr()), ctypes.c_void_p(Fd.data_ptr()), None)
+    assert rc == 1
+    # misaligned device pointer
+    rc = lib.dichotomy_solve(plan.handle, ctypes.c_void_p(Fd.data_ptr() + 4), ctypes.c_void_p(Fd.data_ptr()), None)
+    assert rc == 1
+
+
+# ------------------------------------------------------------------ batches
+def batch_solve(D, N, tm1, t0, tp1, F, **kw):
+    b = D.Batch(N, tm1, t0, tp1, **kw)
+    x = b.solve(torch.from_numpy(F).cuda())
+    assert b.status() == 0
+    return x.cpu().numpy(), b
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_batched_uneven_small(D, prec):
+    N, off, tm1, t0, tp1, F = W.uneven_c4(nsys=300, hi=1 << 16)
+    x, b = batch_solve(D, N, tm1, t0, tp1, F, precision=prec)
+    ref = oracle.thomas_batched(tm1, t0, tp1, N, off, F)
+    worst = max(rel(x[o:o + n], ref[o:o + n]) for o, n in zip(off, N))
+    assert worst < TOL
+
+
+def test_batched_edge_systems(D):
+    N = np.array([1, 2, 3, 0, 5, 64, 65, 4099, 70001, 1])
+    off = W.offsets(N)
+    rng = np.random.default_rng(5)
+    tm1 = rng.uniform(-1, -0.5, N.size)
+    tp1 = rng.uniform(-1, -0.5, N.size)
+    t0 = rng.uniform(2.05, 4, N.size)
+    F = rng.uniform(-1, 1, int(N.sum()))
+    x, _ = batch_solve(D, N, tm1, t0, tp1, F)
+    ref = oracle.thomas_batched(tm1, t0, tp1, N, off, F)
+    for o, n in zip(off, N):
+        if n:
+            assert rel(x[o:o + n], ref[o:o + n]) < TOL
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_c3_poisson_full(D, prec):
+    tm1, t0, tp1, N, rhs = W.poisson_c3()
+    F = rhs.reshape(-1)
+    x, b = batch_solve(D, N, tm1, t0, tp1, F, precision=prec)
+    off = W.offsets(N)
+    ref = oracle.thomas_batched(tm1, t0, tp1, N, off, F)
+    errs = np.array([rel(x[o:o + n], ref[o:o + n]) for o, n in zip(off, N)])
+    assert errs.max() < TOL, (int(errs.argmax()), errs.max())
+
+
+def test_c4_full_size_sampled(D):
+    N, off, tm1, t0, tp1, _ = W.uneven_c4(with_rhs=False)
+    total = int(N.sum())
+    Fd = W.device_uniform(total, W.SEED_RHS, "cuda")
+    b = D.Batch(N, tm1, t0, tp1, precision=2)
+    xd = b.solve(Fd)
+    assert b.status() == 0
+    pick = np.random.default_rng(0).choice(N.size, 40, replace=False)
+    pick = np.concatenate([pick, [int(np.argmax(N)), int(np.argmin(N))]])
+    for s in pick:
+        o, n = int(off[s]), int(N[s])
+        F = Fd[o:o + n].cpu().numpy()
+        ref = oracle.thomas((tm1[s], t0[s], tp1[s]), F)
+        assert rel(xd[o:o + n].cpu().numpy(), ref) < TOL, s
+
+
+# ------------------------------------------------------------------ adjoint
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("t", [(-1.2, 2.5, -0.8), (0.7, 2.5, -1.1), (-1.0, 4.0, -1.0)])
+@pytest.mark.parametrize("N", [1, 2, 50, 4097, 300001])
+def test_adjoint_single(D, t, N, prec):
+    rng = np.random.default_rng(N)
+    F = rng.uniform(-1, 1, N)
+    w = rng.uniform(-1, 1, N)
+    plan = D.Plan(*t, N, precision=prec)
+    x = plan.solve(torch.from_numpy(F).cuda())
+    gF, gt = plan.adjoint(torch.from_numpy(w).cuda(), x)
+    lam_ref, gt_ref = oracle.adjoint(t, w, oracle.thomas(t, F))
+    assert rel(gF.cpu().numpy(), lam_ref) < TOL
+    g = gt.cpu().numpy()
+    assert np.all(np.abs(g - gt_ref) <= TOL * np.max(np.abs(gt_ref)) + 1e-300)
+
+
+def test_adjoint_general_path(D):
+    t = (-1.2, 2.5, -0.8)
+    N = 1 << 18
+    rng = np.random.default_rng(1)
+    F, w = rng.uniform(-1, 1, N), rng.uniform(-1, 1, N)
+    plan = D.Plan(*t, N, flags=1)
+    x = plan.solve(torch.from_numpy(F).cuda())
+    gF, gt = plan.adjoint(torch.from_numpy(w).cuda(), x)
+    lam_ref, gt_ref = oracle.adjoint(t, w, oracle.thomas(t, F))
+    assert rel(gF.cpu().numpy(), lam_ref) < TOL
+    assert np.max(np.abs(gt.cpu().numpy() - gt_ref)) <= TOL * np.max(np.abs(gt_ref))
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_adjoint_batched_c5_reduced(D, prec):
+    Ns, off, tm1, t0, tp1, F, w = W.adjoint_c5(nsys=64)
+    b = D.Batch(Ns, tm1, t0, tp1, precision=prec)
+    x = b.solve(torch.from_numpy(F).cuda())
+    gF, gt = b.adjoint(torch.from_numpy(w).cuda(), x)
+    gF, gt = gF.cpu().numpy(), gt.cpu().numpy()
+    for s in range(Ns.size):
+        sl = slice(off[s], off[s] + Ns[s])
+        tt = (tm1[s], t0[s], tp1[s])
+        lam, g = oracle.adjoint(tt, w[sl], oracle.thomas(tt, F[sl]))
+        assert rel(gF[sl], lam) < TOL
+        assert np.max(np.abs(gt[s] - g)) <= TOL * np.max(np.abs(g))
+
+
+def test_adjoint_finite_differences(D):
+    """Central differences (h = 1e-6) of L = <w, x(t)> against the adjoint gradient."""
+    t = np.array([-1.2, 2.5, -0.8])
+    N = 100000
+    rng = np.random.default_rng(2)
+    F, w = rng.uniform(-1, 1, N), rng.uniform(-1, 1, N)
+    Fd, wd = torch.from_numpy(F).cuda(), torch.from_numpy(w).cuda()
+    plan = D.Plan(*t, N)
+    x = plan.solve(Fd)
+    gF, gt = plan.adjoint(wd, x)
+    h = 1e-6
+    for k in range(3):
+        tp, tm = t.copy(), t.copy()
+        tp[k] += h
+        tm[k] -= h
+        lp = float(torch.dot(wd, D.Plan(*tp, N).solve(Fd)))
+        lm = float(torch.dot(wd, D.Plan(*tm, N).solve(Fd)))
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - float(gt[k])) <= 1e-6 * max(1.0, abs(fd))
+    # and in F on a sample of indices
+    for i in np.random.default_rng(0).integers(0, N, 8):
+        Fp = Fd.clone(); Fp[i] += h
+        Fm = Fd.clone(); Fm[i] -= h
+        fd = (float(torch.dot(wd, plan.solve(Fp))) - float(torch.dot(wd, plan.solve(Fm)))) / (2 * h)
+        assert abs(fd - float(gF[i])) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_autograd_function(D):
+    t = torch.tensor([-1.2, 2.5, -0.8], dtype=torch.float64, device="cuda", requires_grad=True)
+    N = 5000
+    F = torch.from_numpy(np.random.default_rng(4).uniform(-1, 1, N)).cuda().requires_grad_(True)
+    w = torch.from_numpy(np.random.default_rng(5).uniform(-1, 1, N)).cuda()
+    x = D.DichotomySolve.apply(F, t)
+    (x * w).sum().backward()
+    tt = tuple(t.detach().cpu().tolist())
+    lam, g = oracle.adjoint(tt, w.cpu().numpy(), oracle.thomas(tt, F.detach().cpu().numpy()))
+    assert rel(F.grad.cpu().numpy(), lam) < TOL
+    assert np.max(np.abs(t.grad.cpu().numpy() - g)) <= TOL * np.max(np.abs(g))
