@@ -112,18 +112,24 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Choose the block size: one window when the system fits, else the largest rows per block.
 // A last block of a single row is not allowed (Sec. 2.1 asks for sub-vectors of >= 2
-// rows), so n moves to the nearest size (below first, then above) with N mod n != 1.
+// rows), so n moves to the nearest size with N mod n != 1: upwards when the system fits in
+// one window (every larger n still does), else downwards first.
 int choose_n(int64_t N, int NT, int nmax, int n_req) {
+  auto ok = [&](int64_t c) { return c >= 2 && (c >= N || N % c != 1); };
+  const bool one_window = (n_req <= 0) && (N <= (int64_t)NT * nmax);
   int n;
   if (n_req > 0)
     n = std::min(n_req, nmax);
-  else if (N <= (int64_t)NT * nmax)
+  else if (one_window)
     n = (int)std::max<int64_t>(2, ceil_div(N, NT));
   else
     n = nmax;
   if (n >= N) return (int)N;
-  auto ok = [&](int c) { return c >= 2 && (c >= N || N % c != 1); };
   if (ok(n)) return n;
+  if (one_window) {
+    for (int c = n + 1; c <= nmax; ++c)
+      if (ok(c)) return (c >= N) ? (int)N : c;
+  }
   for (int d = 1; d < nmax; ++d) {
     if (n - d >= 2 && ok(n - d)) return n - d;
     if (n + d <= nmax && ok(n + d)) return (n + d >= N) ? (int)N : n + d;

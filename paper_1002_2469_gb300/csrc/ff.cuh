@@ -83,6 +83,29 @@ __device__ __forceinline__ float2 f64_to_ff(double d) {
   return make_float2(__uint_as_float(hib), lo);
 }
 
+// Scaled split: the same as f64_to_ff for d * 2^s (s chosen per window so that the largest
+// |F| of the window sits near 2^16); exact in the scaling, no FP64 operation.
+__device__ __forceinline__ float2 f64_to_ff_sc(double d, int s) {
+  const unsigned hw = (unsigned)__double2hiint(d);
+  const unsigned lw = (unsigned)__double2loint(d);
+  const unsigned sgn = hw & 0x80000000u;
+  const int E0 = (int)((hw >> 20) & 0x7FFu);
+  const int E = E0 + s;
+  const unsigned m23 = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+  const int ef = E - 896;
+  const bool special = (E0 == 2047);
+  unsigned hib = sgn | ((unsigned)ef << 23) | m23;
+  if (ef < 1 || E0 == 0) hib = sgn;
+  if (ef > 254 || special) hib = sgn | 0x7F800000u | ((special && ((hw & 0xFFFFFu) | lw)) ? 0x400000u : 0u);
+  const unsigned r = lw & 0x1FFFFFFFu;
+  const float rf = __fsub_rn(__uint_as_float(0x4B000000u | (r >> 6)), 8388608.0f);
+  const int es = E - 942;
+  float lo = (es >= 1 && ef <= 254 && E0 != 0 && !special) ? __fmul_rn(rf, __uint_as_float((unsigned)es << 23))
+                                                          : 0.0f;
+  lo = __uint_as_float(__float_as_uint(lo) | sgn);
+  return make_float2(__uint_as_float(hib), lo);
+}
+
 // exact float -> double by integer operations (denormal floats flush to signed zero)
 __device__ __forceinline__ double f32_to_f64_bits(float f) {
   const unsigned b = __float_as_uint(f);
@@ -96,9 +119,71 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// float * 2^-s -> double by integer operations (the window scale removed exactly; results
+// below the FP64 normal range flush to signed zero)
+__device__ __forceinline__ double f32_to_f64_bits_sc(float f, int s) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sg = b & 0x80000000u;
+  const int e = (int)((b >> 23) & 0xFFu);
+  const unsigned m = b & 0x7FFFFFu;
+  int ed = e + 896 - s;
+  unsigned md = m;
+  if (e == 255 || ed >= 2047) {
+    ed = 2047;
+    md = (e == 255) ? m : 0u;
+  }
+  if (e == 0 || ed <= 0) {
+    ed = 0;
+    md = 0u;
+  }
+  const unsigned hi = sg | ((unsigned)ed << 20) | (md >> 3);
+  const unsigned lo = md << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ double ff_to_f64_sc(float h, float l, int s) {
+  return __dadd_rn(f32_to_f64_bits_sc(h, s), f32_to_f64_bits_sc(l, s));
+}
+
 // (h, l) -> FP64: both parts converted exactly, one FP64 addition.
 __device__ __forceinline__ double ff_to_f64(float h, float l) {
   return __dadd_rn(f32_to_f64_bits(h), f32_to_f64_bits(l));
+}
+
+// (h, l) * 2^-s -> FP64 with integer operations only (no FP64 pipe).  (h, l) is first
+// renormalised with TwoSum so |e| <= ulp(s1)/2; s1 gives the leading 24 bits of the double,
+// e is aligned to the double's last bit and added to the 53-bit significand as an integer
+// (bits of e below the double's ulp are truncated: error < 2 ulp of the result).
+__device__ __forceinline__ double ff_to_f64_int(float h, float l, int s) {
+  float s1, e1;
+  two_sum(h, l, s1, e1);
+  const unsigned b1 = __float_as_uint(s1);
+  const unsigned sg = b1 & 0x80000000u;
+  const int E1 = (int)((b1 >> 23) & 0xFFu);
+  if (E1 == 0) return __hiloint2double((int)sg, 0);                 // zero (or float denormal)
+  if (E1 == 255) return __hiloint2double((int)(sg | 0x7FF00000u | ((b1 & 0x7FFFFFu) ? 0x80000u : 0u)), 0);
+  unsigned long long M = (1ull << 52) | ((unsigned long long)(b1 & 0x7FFFFFu) << 29);
+  const unsigned be = __float_as_uint(e1);
+  const int Ee = (int)((be >> 23) & 0xFFu);
+  if (Ee != 0) {
+    const unsigned long long Me = (unsigned long long)((be & 0x7FFFFFu) | 0x800000u);
+    const int sh = Ee - E1 + 29;      // <= 5 because |e1| <= ulp(s1)/2
+    unsigned long long K = 0ull;
+    if (sh >= 0)
+      K = Me << sh;
+    else if (sh > -24)
+      K = Me >> (-sh);
+    M = ((be ^ b1) & 0x80000000u) ? M - K : M + K;
+  }
+  int Ed = E1 + 896 - s;
+  if (M < (1ull << 52)) {             // borrow from an exact power of two: renormalise
+    M <<= 1;
+    Ed -= 1;
+  }
+  if (Ed <= 0) return __hiloint2double((int)sg, 0);
+  if (Ed >= 2047) return __hiloint2double((int)(sg | 0x7FF00000u), 0);
+  const unsigned hi = sg | ((unsigned)Ed << 20) | ((unsigned)(M >> 32) & 0xFFFFFu);
+  return __hiloint2double((int)hi, (int)(unsigned)M);
 }
 
 // FP64 -> float-float with correct rounding of hi (FP64 pipe; used once per block only)

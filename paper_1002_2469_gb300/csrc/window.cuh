@@ -2,8 +2,10 @@
 //
 // One CTA of NT threads handles a window of up to NT consecutive blocks of one system;
 // thread b owns window block b.  Per window:
-//   1. load F of the window into shared memory, transposed (row i of every block side by
-//      side, stride NT+1 doubles), with coalesced 256-byte warp loads;
+//   1. the window's rows of F (contiguous in HBM) are copied into shared memory with
+//      8-byte cp.async copies, every thread issuing all of its copies before waiting, into
+//      a transposed layout (row i of all blocks side by side, stride NT+1 doubles, so the
+//      per-thread sweeps below read conflict-free);
 //   2. local sweeps (a1): every thread runs the two first-order recurrences of its block
 //      (u_i = f_i + rs u_{i-1}, X_i = u_i + ib X_{i+1}, xp_i = g X_i) in place, giving the
 //      block ends alpha, omega of T_n^-1 F_m and then beta^{L,R}_m of eq. 16 through the
@@ -12,10 +14,15 @@
 //      warp-shuffle levels, then one shared-memory level across warps -- and the
 //      first/last values x_s, x_e of every block (eq. 18);
 //   4. the basis correction (a3): x = xp + (x_{s-1} - xp(-1)) v + x_{e+1} w, applied only
-//      where the spikes v, w exceed the truncation threshold, and the coalesced store.
+//      where the spikes v, w exceed the truncation threshold, and a contiguous,
+//      coalesced store of the own rows.
 // Windows of a long system overlap by halo blocks on each side whose coupling into the
 // own blocks has decayed below 2^-64 (the truncation is exact to that level); on the
 // general path the window instead takes the first/last values from a global scan.
+//
+// MIXED form: the sweeps run in compensated FP32 (ff.cuh) on values scaled per block by an
+// exact power of two (largest |F| of the block near 2^16); everything that leaves a block
+// (alpha, omega, xp(-1), beta, the tree) is unscaled FP64.
 #pragma once
 #include "dich_internal.cuh"
 #include "ff.cuh"
@@ -42,8 +49,17 @@ struct WinArgs {
 // shared memory bytes for a window kernel of width NT and n_smem rows
 __host__ __device__ inline size_t window_smem_bytes(int NT, int n_smem) {
   const size_t nw = (size_t)(NT / 32);
-  return sizeof(double) * ((size_t)n_smem * (size_t)(NT + 1) + 4 * (size_t)n_smem + 4 * (size_t)NT + 4 * nw + 8);
+  return sizeof(double) * ((size_t)n_smem * (size_t)(NT + 1) + 4 * (size_t)n_smem + 5 * (size_t)NT + 4 * nw + 8);
 }
+
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// 2^k as a double for |k| <= 1000 (bit construction)
+__device__ __forceinline__ double pow2i(int k) { return __hiloint2double((1023 + k) << 20, 0); }
 
 template <int NT, int FORM>
 __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
@@ -61,7 +77,8 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   double* sxe = sxs + NT;
   double* scl = sxe + NT;
   double* scr = scl + NT;
-  double* swa = scr + NT;  // 4 * NW scan scratch
+  int* ssc = reinterpret_cast<int*>(scr + NT);    // per-block scale exponents (MIXED)
+  double* swa = scr + 2 * NT;                     // 4 * NW scan scratch
   float2* S2 = reinterpret_cast<float2*>(S);
 
   // ---------------------------------------------------------------- the window
@@ -98,8 +115,25 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   const int64_t off = pp->off;
   const double* tab = A.tabs + pp->tab;
   const bool has_last = (wlo + nwin == P);
+  const int64_t row_lo = wlo * (int64_t)n;                   // first row of the window
+  const int len = nwin * n - (has_last ? (n - nlast) : 0);  // rows in the window
 
-  // ---------------------------------------------------------------- tables -> smem
+  // ---------------------------------------------------------------- F -> smem (transposed, async)
+  {
+    const double* src = A.F + off + row_lo;
+    int b = tid / n, i = tid - (tid / n) * n;
+    const int db = NT / n, di = NT - (NT / n) * n;
+    for (int j = tid; j < len; j += NT) {
+      cp_async8(&S[i * LD + b], src + j);
+      i += di;
+      b += db;
+      if (i >= n) {
+        i -= n;
+        ++b;
+      }
+    }
+  }
+  // tables -> smem (overlaps the copies in flight)
   if (FORM == FORM_F64) {
     for (int i = tid; i < Lv; i += NT) tv[i] = tab[pp->o_v + i];
     for (int i = tid; i < Lw; i += NT) tw[i] = tab[pp->o_w + i];
@@ -117,36 +151,7 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
         twl[i] = tab[pp->o_wlf + i];
       }
   }
-
-  // ---------------------------------------------------------------- F -> smem (transposed)
-  for (int b = wid; b < nwin; b += NW) {
-    const int64_t m = wlo + b;
-    const int nb = (m == P - 1) ? nlast : n;
-    const double* src = A.F + off + m * (int64_t)n;
-    int i = lane;
-    for (; i + 96 < nb; i += 128) {
-      const double f0 = __ldcs(src + i), f1 = __ldcs(src + i + 32), f2 = __ldcs(src + i + 64),
-                   f3 = __ldcs(src + i + 96);
-      if (FORM == FORM_F64) {
-        S[(i)*LD + b] = f0;
-        S[(i + 32) * LD + b] = f1;
-        S[(i + 64) * LD + b] = f2;
-        S[(i + 96) * LD + b] = f3;
-      } else {
-        S2[(i)*LD + b] = f64_to_ff(f0);
-        S2[(i + 32) * LD + b] = f64_to_ff(f1);
-        S2[(i + 64) * LD + b] = f64_to_ff(f2);
-        S2[(i + 96) * LD + b] = f64_to_ff(f3);
-      }
-    }
-    for (; i < nb; i += 32) {
-      const double f0 = __ldcs(src + i);
-      if (FORM == FORM_F64)
-        S[i * LD + b] = f0;
-      else
-        S2[i * LD + b] = f64_to_ff(f0);
-    }
-  }
+  cp_async_wait_all();
   __syncthreads();
 
   // ---------------------------------------------------------------- local sweeps (a1)
@@ -155,6 +160,7 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   const bool lastb = act && (mb == P - 1);
   const int nbk = lastb ? nlast : n;
   double xm1 = 0.0, alpha = 0.0, omega = 0.0;
+  int bscale = 0;
   if (act) {
     const double v0 = lastb ? pp->v0l : pp->v0;
     const double vend = lastb ? pp->vendl : pp->vend;
@@ -202,11 +208,18 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
       omega = col[(nbk - 1) * LD] - xm1 * vend;
     } else {
       const float rh = pp->rs_h, rl = pp->rs_l, bh = pp->ib_h, bl = pp->ib_l, gh = pp->g_h, gl = pp->g_l;
+      const double* cold = S + tid;
       float2* col = S2 + tid;
+      // block scale: largest exponent of the block's F near 2^16 (exact power of two)
+      unsigned e = 0u;
+      const unsigned* colw = reinterpret_cast<const unsigned*>(cold);
+      for (int i = 0; i < nbk; ++i) e = max(e, (colw[2 * i * LD + 1] >> 20) & 0x7FFu);
+      bscale = (e == 0u || e == 2047u) ? 0 : max(-1000, min(1000, (1023 + 16) - (int)e));
       float uh = 0.f, ul = 0.f;
       int i = 0;
       for (; i + 4 <= nbk; i += 4) {
-        const float2 f0 = col[(i)*LD], f1 = col[(i + 1) * LD], f2 = col[(i + 2) * LD], f3 = col[(i + 3) * LD];
+        const float2 f0 = f64_to_ff_sc(cold[(i)*LD], bscale), f1 = f64_to_ff_sc(cold[(i + 1) * LD], bscale),
+                     f2 = f64_to_ff_sc(cold[(i + 2) * LD], bscale), f3 = f64_to_ff_sc(cold[(i + 3) * LD], bscale);
         float2 o0, o1, o2, o3;
         ff_axpy(f0.x, f0.y, rh, rl, uh, ul, o0.x, o0.y);
         ff_axpy(f1.x, f1.y, rh, rl, o0.x, o0.y, o1.x, o1.y);
@@ -220,7 +233,7 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
         ul = o3.y;
       }
       for (; i < nbk; ++i) {
-        const float2 f0 = col[i * LD];
+        const float2 f0 = f64_to_ff_sc(cold[i * LD], bscale);
         ff_axpy(f0.x, f0.y, rh, rl, uh, ul, uh, ul);
         col[i * LD] = make_float2(uh, ul);
       }
@@ -251,11 +264,13 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
         ff_mul(gh, gl, Xh, Xl, y0.x, y0.y);
         col[i * LD] = y0;
       }
-      const double X0d = (double)Xh + (double)Xl;
+      // block-end quantities in unscaled FP64
+      const double down = pow2i(-bscale);
+      const double X0d = ((double)Xh + (double)Xl) * down;
       xm1 = pp->g * pp->ib * X0d;
       const float2 p0 = col[0], pe = col[(nbk - 1) * LD];
-      alpha = ((double)p0.x + (double)p0.y) - xm1 * v0;
-      omega = ((double)pe.x + (double)pe.y) - xm1 * vend;
+      alpha = ((double)p0.x + (double)p0.y) * down - xm1 * v0;
+      omega = ((double)pe.x + (double)pe.y) * down - xm1 * vend;
     }
   }
 
@@ -337,8 +352,16 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
       XR = (mb == P - 1) ? 0.0 : A.iface[2 * (mb + 1)];
     }
   }
-  scl[tid] = XL - xm1;
-  scr[tid] = XR;
+  if (FORM == FORM_F64) {
+    scl[tid] = XL - xm1;
+    scr[tid] = XR;
+  } else {  // correction coefficients in the block's scaled units, as float-float
+    const double up = pow2i(bscale);
+    const float2 c1 = f64_to_ff_rn((XL - xm1) * up), c2 = f64_to_ff_rn(XR * up);
+    reinterpret_cast<float2*>(scl)[tid] = c1;
+    reinterpret_cast<float2*>(scr)[tid] = c2;
+    ssc[tid] = bscale;
+  }
   __syncthreads();
 
   // ---------------------------------------------------------------- correction + store (a3)
@@ -346,57 +369,51 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   double g0 = 0.0, gm = 0.0, gp = 0.0;
   unsigned bad = 0u;
   const int64_t N = pp->N;
-  for (int b = hl + wid; b < hl + nown; b += NW) {
-    const int64_t m = wlo + b;
-    const bool lb = (m == P - 1);
-    const int nb = lb ? nlast : n;
-    const int lv = lb ? nlast : Lv, lw = lb ? nlast : Lw;
-    const double cL = scl[b], cR = scr[b];
-    const int64_t row0 = m * (int64_t)n;
-    double* dst = A.x + off + row0;
-    if (FORM == FORM_F64) {
-      const double* v = lb ? tvl : tv;
-      const double* wr = lb ? twl : tw;
-      for (int i = lane; i < nb; i += 32) {
+  {
+    const int jlo = hl * n;
+    const int jhi = min(len, (hl + nown) * n);
+    double* dst = A.x + off + row_lo;
+    int b = (jlo + tid) / n, i = (jlo + tid) - ((jlo + tid) / n) * n;
+    const int db = NT / n, di = NT - (NT / n) * n;
+    for (int j = jlo + tid; j < jhi; j += NT) {
+      const bool lb = has_last && (b == nwin - 1);
+      const int nb = lb ? nlast : n;
+      const int lv = lb ? nlast : Lv, lw = lb ? nlast : Lw;
+      const int jr = nb - 1 - i;
+      double dv;
+      if (FORM == FORM_F64) {
         double val = S[i * LD + b];
-        if (i < lv) val = fma(cL, v[i], val);
-        const int j = nb - 1 - i;
-        if (j < lw) val = fma(cR, wr[j], val);
-        __stcs(dst + i, val);
-        if (A.check_finite && !isfinite(val)) bad = 1u;
-        if (adj) {
-          const int64_t r = row0 + i;
-          const double* xr = A.xf + off + r;
-          g0 = fma(val, xr[0], g0);
-          if (r > 0) gm = fma(val, xr[-1], gm);
-          if (r + 1 < N) gp = fma(val, xr[1], gp);
-        }
-      }
-    } else {
-      const float2* v = reinterpret_cast<const float2*>(lb ? tvl : tv);
-      const float2* wr = reinterpret_cast<const float2*>(lb ? twl : tw);
-      const float2 cl2 = f64_to_ff_rn(cL), cr2 = f64_to_ff_rn(cR);
-      for (int i = lane; i < nb; i += 32) {
+        if (i < lv) val = fma(scl[b], (lb ? tvl : tv)[i], val);
+        if (jr < lw) val = fma(scr[b], (lb ? twl : tw)[jr], val);
+        dv = val;
+      } else {
         float2 val = S2[i * LD + b];
         if (i < lv) {
-          const float2 vv = v[i];
-          ff_fma_acc(cl2.x, cl2.y, vv.x, vv.y, val.x, val.y);
+          const float2 c = reinterpret_cast<const float2*>(scl)[b];
+          const float2 vv = reinterpret_cast<const float2*>(lb ? tvl : tv)[i];
+          ff_fma_acc(c.x, c.y, vv.x, vv.y, val.x, val.y);
         }
-        const int j = nb - 1 - i;
-        if (j < lw) {
-          const float2 ww = wr[j];
-          ff_fma_acc(cr2.x, cr2.y, ww.x, ww.y, val.x, val.y);
+        if (jr < lw) {
+          const float2 c = reinterpret_cast<const float2*>(scr)[b];
+          const float2 ww = reinterpret_cast<const float2*>(lb ? twl : tw)[jr];
+          ff_fma_acc(c.x, c.y, ww.x, ww.y, val.x, val.y);
         }
-        const double dv = ff_to_f64(val.x, val.y);
-        __stcs(dst + i, dv);
-        if (A.check_finite && !isfinite(dv)) bad = 1u;
-        if (adj) {
-          const int64_t r = row0 + i;
-          const double* xr = A.xf + off + r;
-          g0 = fma(dv, xr[0], g0);
-          if (r > 0) gm = fma(dv, xr[-1], gm);
-          if (r + 1 < N) gp = fma(dv, xr[1], gp);
-        }
+        dv = ff_to_f64_int(val.x, val.y, ssc[b]);
+      }
+      __stcs(dst + j, dv);
+      if (A.check_finite && !isfinite(dv)) bad = 1u;
+      if (adj) {
+        const int64_t r = row_lo + j;
+        const double* xr = A.xf + off + r;
+        g0 = fma(dv, xr[0], g0);
+        if (r > 0) gm = fma(dv, xr[-1], gm);
+        if (r + 1 < N) gp = fma(dv, xr[1], gp);
+      }
+      i += di;
+      b += db;
+      if (i >= n) {
+        i -= n;
+        ++b;
       }
     }
   }
