@@ -47,6 +47,10 @@ int max_rows(int NT, size_t budget) {
 
 int default_threads(int form) { return form == FORM_F64 ? 64 : 128; }
 
+// rows per block for multi-window systems (measured on GB300 at N = 2^26: small windows let
+// several CTAs share an SM so loads, sweeps, tree and stores of different windows overlap)
+int default_rows(int form) { return form == FORM_F64 ? 64 : 32; }
+
 int validate_t(double tm1, double t0, double tp1) {
   if (!std::isfinite(tm1) || !std::isfinite(t0) || !std::isfinite(tp1)) return DICH_ERR_ARG;
   if (t0 == 0.0) return (tm1 == 0.0 && tp1 == 0.0) ? DICH_ERR_SINGULAR : DICH_ERR_NOT_DOMINANT;
@@ -114,7 +118,7 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // A last block of a single row is not allowed (Sec. 2.1 asks for sub-vectors of >= 2
 // rows), so n moves to the nearest size with N mod n != 1: upwards when the system fits in
 // one window (every larger n still does), else downwards first.
-int choose_n(int64_t N, int NT, int nmax, int n_req) {
+int choose_n(int64_t N, int NT, int nmax, int n_req, int n_def) {
   auto ok = [&](int64_t c) { return c >= 2 && (c >= N || N % c != 1); };
   const bool one_window = (n_req <= 0) && (N <= (int64_t)NT * nmax);
   int n;
@@ -123,7 +127,7 @@ int choose_n(int64_t N, int NT, int nmax, int n_req) {
   else if (one_window)
     n = (int)std::max<int64_t>(2, ceil_div(N, NT));
   else
-    n = nmax;
+    n = std::min(nmax, n_def);
   if (n >= N) return (int)N;
   if (ok(n)) return n;
   if (one_window) {
@@ -367,7 +371,7 @@ int dichotomy_plan_ex(double t_m1, double t_0, double t_1, int64_t N, const dich
   p->NT = o.NT ? o.NT : default_threads(p->form);
   if (N >= 2) {
     const int nmax = max_rows(p->NT, o.n_req > 0 ? kSmemMax : kSmemBudget);
-    const int n = choose_n(N, p->NT, nmax, o.n_req);
+    const int n = choose_n(N, p->NT, nmax, o.n_req, default_rows(p->form));
     rc = build_system(t_m1, t_0, t_1, N, p->NT, p->form, n, o, true, p->fwd);
     if (!rc) rc = build_system(t_1, t_0, t_m1, N, p->NT, p->form, n, o, true, p->adj);
     if (rc) {
@@ -655,7 +659,7 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
       if (h_N[s] == 1) b->trivial.push_back((int32_t)s);
       continue;
     }
-    const int n = choose_n(h_N[s], b->NT, nmax, o.n_req);
+    const int n = choose_n(h_N[s], b->NT, nmax, o.n_req, default_rows(b->form[s]));
     Opts oh = o;
     oh.flags &= ~DICH_FLAG_FORCE_GENERAL;
     rc = build_system(h_tm1[s], h_t0[s], h_tp1[s], h_N[s], b->NT, b->form[s], n, oh, false, b->fwd[s]);

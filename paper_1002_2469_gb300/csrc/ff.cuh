@@ -86,6 +86,10 @@ __device__ __forceinline__ float2 f64_to_ff(double d) {
 // Scaled split: the same as f64_to_ff for d * 2^s (s chosen per window so that the largest
 // |F| of the window sits near 2^16); exact in the scaling, no FP64 operation.
 __device__ __forceinline__ float2 f64_to_ff_sc(double d, int s) {
+  if ((((unsigned)__double2hiint(d) >> 20) & 0x7FFu) == 0u && d != 0.0) {  // FP64 subnormal
+    d = d * 18446744073709551616.0;   // * 2^64, exact
+    s -= 64;
+  }
   const unsigned hw = (unsigned)__double2hiint(d);
   const unsigned lw = (unsigned)__double2loint(d);
   const unsigned sgn = hw & 0x80000000u;
@@ -180,7 +184,11 @@ __device__ __forceinline__ double ff_to_f64_int(float h, float l, int s) {
     M <<= 1;
     Ed -= 1;
   }
-  if (Ed <= 0) return __hiloint2double((int)sg, 0);
+  if (Ed <= 0) {                      // below the normal range: FP64 subnormal (truncated)
+    const int sh = 1 - Ed;
+    M = (sh < 64) ? (M >> sh) : 0ull;
+    return __hiloint2double((int)(sg | ((unsigned)(M >> 32) & 0xFFFFFu)), (int)(unsigned)M);
+  }
   if (Ed >= 2047) return __hiloint2double((int)(sg | 0x7FF00000u), 0);
   const unsigned hi = sg | ((unsigned)Ed << 20) | ((unsigned)(M >> 32) & 0xFFFFFu);
   return __hiloint2double((int)hi, (int)(unsigned)M);

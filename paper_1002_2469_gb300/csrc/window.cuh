@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
       unsigned e = 0u;
       const unsigned* colw = reinterpret_cast<const unsigned*>(cold);
       for (int i = 0; i < nbk; ++i) e = max(e, (colw[2 * i * LD + 1] >> 20) & 0x7FFu);
-      bscale = (e == 0u || e == 2047u) ? 0 : max(-1000, min(1000, (1023 + 16) - (int)e));
+      // (e == 0: zeros or subnormals only -> the largest scale; e == 2047: Inf/NaN -> none)
+      bscale = (e == 2047u) ? 0 : ((e == 0u) ? 1000 : max(-1000, min(1000, (1023 + 16) - (int)e)));
       float uh = 0.f, ul = 0.f;
       int i = 0;
       for (; i + 4 <= nbk; i += 4) {
