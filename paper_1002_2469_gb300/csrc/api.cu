@@ -245,6 +245,14 @@ int build_system(double tm1, double t0, double tp1, int64_t N, int NT, int form,
   p.o_bcm = take(kBC);
   p.o_bcl = take(kl * kBC);
   p.o_bcr = take(kr * kBC);
+  p.o_bcmf = take(kBC);
+  p.o_bclf = take(kl * kBC);
+  p.o_bcrf = take(kr * kBC);
+  split_ff(r.g * r.ib, p.gib_h, p.gib_l);
+  split_ff(p.v0, p.v0_h, p.v0_l);
+  split_ff(p.vend, p.vend_h, p.vend_l);
+  split_ff(p.v0l, p.v0l_h, p.v0l_l);
+  split_ff(p.vendl, p.vendl_h, p.vendl_l);
   sb.tab.assign((size_t)o_, 0.0);
   double* T = sb.tab.data();
   auto put_ff = [&](int32_t at, double d) {
@@ -278,6 +286,9 @@ int build_system(double tm1, double t0, double tp1, int64_t N, int NT, int form,
   };
   for (int64_t m = 0; m < kl; ++m) coeffs_of(m, &T[p.o_bcl + m * kBC]);
   for (int64_t k = 0; k < kr; ++k) coeffs_of(P - kr + k, &T[p.o_bcr + k * kBC]);
+  for (int j = 0; j < kBC; ++j) put_ff(p.o_bcmf + j, T[p.o_bcm + j]);
+  for (int64_t j = 0; j < kl * kBC; ++j) put_ff(p.o_bclf + (int32_t)j, T[p.o_bcl + j]);
+  for (int64_t j = 0; j < kr * kBC; ++j) put_ff(p.o_bcrf + (int32_t)j, T[p.o_bcr + j]);
   return DICH_OK;
 }
 

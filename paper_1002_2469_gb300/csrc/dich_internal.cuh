@@ -84,6 +84,10 @@ struct SysPlan {
   int32_t o_v, o_w, o_vl, o_wl;             // v[Lv], w_rev[Lw], v_last[nlast], w_last_rev[nlast]
   int32_t o_vf, o_wf, o_vlf, o_wlf;         // float-float copies (float2 per entry)
   int32_t o_bcm, o_bcl, o_bcr, pad2_;       // middle record, left table [kl], right table [kr]
+  int32_t o_bcmf, o_bclf, o_bcrf, pad3_;    // the same records as float-float (float2 per entry)
+  // float-float copies of g * ib and of the corner spikes (MIXED form)
+  float gib_h, gib_l;
+  float v0_h, v0_l, vend_h, vend_l, v0l_h, v0l_l, vendl_h, vendl_l;
 };
 static_assert(sizeof(SysPlan) % 8 == 0, "SysPlan must be 8-byte granular");
 

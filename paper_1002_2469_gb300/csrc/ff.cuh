@@ -86,7 +86,8 @@ __device__ __forceinline__ float2 f64_to_ff(double d) {
 // Scaled split: the same as f64_to_ff for d * 2^s (s chosen per window so that the largest
 // |F| of the window sits near 2^16); exact in the scaling, no FP64 operation.
 __device__ __forceinline__ float2 f64_to_ff_sc(double d, int s) {
-  if ((((unsigned)__double2hiint(d) >> 20) & 0x7FFu) == 0u && d != 0.0) {  // FP64 subnormal
+  const unsigned hw0 = (unsigned)__double2hiint(d);
+  if (((hw0 >> 20) & 0x7FFu) == 0u && ((hw0 & 0x7FFFFFFFu) | (unsigned)__double2loint(d)) != 0u) {  // subnormal
     d = d * 18446744073709551616.0;   // * 2^64, exact
     s -= 64;
   }
@@ -200,5 +201,53 @@ __device__ __forceinline__ float2 f64_to_ff_rn(double d) {
   const float l = __double2float_rn(__dsub_rn(d, (double)h));
   return make_float2(h, l);
 }
+
+// ---------------------------------------------------------------- float-float values for the
+// per-block quantities and the dichotomy tree of the MIXED form (normalised: |l| <= ulp(h)/2)
+struct ffv {
+  float h, l;
+};
+
+__device__ __forceinline__ ffv ff_make(float h, float l) {  // FastTwoSum renormalisation
+  const float s = __fadd_rn(h, l);
+  return ffv{s, __fsub_rn(l, __fsub_rn(s, h))};
+}
+__device__ __forceinline__ ffv ff_of(float2 v) { return ff_make(v.x, v.y); }
+__device__ __forceinline__ ffv ff_zero() { return ffv{0.f, 0.f}; }
+__device__ __forceinline__ ffv ff_one() { return ffv{1.f, 0.f}; }
+__device__ __forceinline__ ffv ff_neg(ffv a) { return ffv{-a.h, -a.l}; }
+
+__device__ __forceinline__ ffv ff_add(ffv a, ffv b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return ff_make(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ ffv ff_sub(ffv a, ffv b) { return ff_add(a, ff_neg(b)); }
+
+__device__ __forceinline__ ffv ff_mul(ffv a, ffv b) {
+  float p, e;
+  two_prod(a.h, b.h, p, e);
+  e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+  return ff_make(p, e);
+}
+
+// a * b + c
+__device__ __forceinline__ ffv ff_fma(ffv a, ffv b, ffv c) {
+  float p, e, s, f;
+  two_prod(a.h, b.h, p, e);
+  two_sum(p, c.h, s, f);
+  float lo = __fadd_rn(__fadd_rn(e, f), c.l);
+  lo = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, lo));
+  return ff_make(s, lo);
+}
+
+__device__ __forceinline__ ffv ff_shfl_up(ffv a, int d) {
+  return ffv{__shfl_up_sync(0xffffffffu, a.h, d), __shfl_up_sync(0xffffffffu, a.l, d)};
+}
+__device__ __forceinline__ ffv ff_shfl_down(ffv a, int d) {
+  return ffv{__shfl_down_sync(0xffffffffu, a.h, d), __shfl_down_sync(0xffffffffu, a.l, d)};
+}
+__device__ __forceinline__ double ff_to_double(ffv a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ float2 ff_f2(ffv a) { return make_float2(a.h, a.l); }
 
 }  // namespace dich

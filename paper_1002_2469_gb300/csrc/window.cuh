@@ -20,10 +20,13 @@
 // own blocks has decayed below 2^-64 (the truncation is exact to that level); on the
 // general path the window instead takes the first/last values from a global scan.
 //
-// MIXED form: the sweeps run in compensated FP32 (ff.cuh) on values scaled per block by an
-// exact power of two (largest |F| of the block near 2^16); everything that leaves a block
-// (alpha, omega, xp(-1), beta, the tree) is unscaled FP64.
+// MIXED form: the sweeps run in compensated FP32 (ff.cuh) and the per-block quantities and the
+// tree in float-float, all on values scaled per window by an exact power of two (largest |F|
+// of the window near 2^16); only the general path's beta and first/last values cross the
+// window boundary, as unscaled FP64.
 #pragma once
+#include <type_traits>
+
 #include "dich_internal.cuh"
 #include "ff.cuh"
 
@@ -61,6 +64,36 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // 2^k as a double for |k| <= 1000 (bit construction)
 __device__ __forceinline__ double pow2i(int k) { return __hiloint2double((1023 + k) << 20, 0); }
 
+// Arithmetic of the per-block quantities and of the dichotomy tree: FP64 in the FP64 form,
+// float-float on the FP32 pipe in the MIXED form (GB300's FP64 pipe is ~70x slower).
+struct OpsF64 {
+  using V = double;
+  static __device__ __forceinline__ V zero() { return 0.0; }
+  static __device__ __forceinline__ V one() { return 1.0; }
+  static __device__ __forceinline__ V add(V a, V b) { return a + b; }
+  static __device__ __forceinline__ V sub(V a, V b) { return a - b; }
+  static __device__ __forceinline__ V mul(V a, V b) { return a * b; }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return ::fma(a, b, c); }
+  static __device__ __forceinline__ V up(V a, int d) { return __shfl_up_sync(0xffffffffu, a, d); }
+  static __device__ __forceinline__ V down(V a, int d) { return __shfl_down_sync(0xffffffffu, a, d); }
+  // block coefficient record j (BC_*) of the record at table offset `rec` (plan offsets in doubles)
+  static __device__ __forceinline__ V bc(const double* tab, int64_t rec, int j) { return tab[rec + j]; }
+};
+struct OpsFF {
+  using V = ffv;
+  static __device__ __forceinline__ V zero() { return ff_zero(); }
+  static __device__ __forceinline__ V one() { return ff_one(); }
+  static __device__ __forceinline__ V add(V a, V b) { return ff_add(a, b); }
+  static __device__ __forceinline__ V sub(V a, V b) { return ff_sub(a, b); }
+  static __device__ __forceinline__ V mul(V a, V b) { return ff_mul(a, b); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return ff_fma(a, b, c); }
+  static __device__ __forceinline__ V up(V a, int d) { return ff_shfl_up(a, d); }
+  static __device__ __forceinline__ V down(V a, int d) { return ff_shfl_down(a, d); }
+  static __device__ __forceinline__ V bc(const double* tab, int64_t rec, int j) {
+    return ff_of(reinterpret_cast<const float2*>(tab)[rec + j]);
+  }
+};
+
 template <int NT, int FORM>
 __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   constexpr int NW = NT / 32;
@@ -77,7 +110,6 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   double* sxe = sxs + NT;
   double* scl = sxe + NT;
   double* scr = scl + NT;
-  int* ssc = reinterpret_cast<int*>(scr + NT);    // per-block scale exponents (MIXED)
   double* swa = scr + 2 * NT;                     // 4 * NW scan scratch
   float2* S2 = reinterpret_cast<float2*>(S);
 
@@ -134,7 +166,7 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
     }
   }
   // tables -> smem (overlaps the copies in flight)
-  if (FORM == FORM_F64) {
+  if constexpr (FORM == FORM_F64) {
     for (int i = tid; i < Lv; i += NT) tv[i] = tab[pp->o_v + i];
     for (int i = tid; i < Lw; i += NT) tw[i] = tab[pp->o_w + i];
     if (has_last)
@@ -159,12 +191,32 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   const int64_t mb = wlo + tid;
   const bool lastb = act && (mb == P - 1);
   const int nbk = lastb ? nlast : n;
-  double xm1 = 0.0, alpha = 0.0, omega = 0.0;
-  int bscale = 0;
+  using O = typename std::conditional<FORM == FORM_F64, OpsF64, OpsFF>::type;
+  using V = typename O::V;
+  V xm1 = O::zero(), alpha = O::zero(), omega = O::zero();
+
+  // MIXED: one exact power-of-two scale per window puts its largest |F| near 2^16, so the
+  // float-float sweeps and tree keep full relative precision at any magnitude of F
+  int wscale = 0;
+  if constexpr (FORM == FORM_MIXED) {
+    unsigned e = 0u;
+    if (act) {
+      const unsigned* colw = reinterpret_cast<const unsigned*>(S + tid);
+      for (int i = 0; i < nbk; ++i) e = max(e, (colw[2 * i * LD + 1] >> 20) & 0x7FFu);
+    }
+    e = __reduce_max_sync(0xffffffffu, e);
+    unsigned* sexp = reinterpret_cast<unsigned*>(swa);
+    if (lane == 0) sexp[wid] = e;
+    __syncthreads();
+    e = 0u;
+    for (int w = 0; w < NW; ++w) e = max(e, sexp[w]);
+    __syncthreads();
+    // e == 0: zeros or subnormals only -> the largest scale; e == 2047: Inf/NaN -> none
+    wscale = (e == 2047u) ? 0 : ((e == 0u) ? 1000 : max(-1000, min(1000, (1023 + 16) - (int)e)));
+  }
+
   if (act) {
-    const double v0 = lastb ? pp->v0l : pp->v0;
-    const double vend = lastb ? pp->vendl : pp->vend;
-    if (FORM == FORM_F64) {
+    if constexpr (FORM == FORM_F64) {
       const double rs = pp->rs, ib = pp->ib, g = pp->g;
       double* col = S + tid;
       double u = 0.0;
@@ -203,24 +255,21 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
         X = fma(ib, X, col[i * LD]);
         col[i * LD] = g * X;
       }
-      xm1 = g * ib * X;
-      alpha = col[0] - xm1 * v0;
-      omega = col[(nbk - 1) * LD] - xm1 * vend;
+      const double v0 = lastb ? pp->v0l : pp->v0;
+      const double vend = lastb ? pp->vendl : pp->vend;
+      const double xm = g * ib * X;
+      xm1 = xm;
+      alpha = col[0] - xm * v0;
+      omega = col[(nbk - 1) * LD] - xm * vend;
     } else {
       const float rh = pp->rs_h, rl = pp->rs_l, bh = pp->ib_h, bl = pp->ib_l, gh = pp->g_h, gl = pp->g_l;
       const double* cold = S + tid;
       float2* col = S2 + tid;
-      // block scale: largest exponent of the block's F near 2^16 (exact power of two)
-      unsigned e = 0u;
-      const unsigned* colw = reinterpret_cast<const unsigned*>(cold);
-      for (int i = 0; i < nbk; ++i) e = max(e, (colw[2 * i * LD + 1] >> 20) & 0x7FFu);
-      // (e == 0: zeros or subnormals only -> the largest scale; e == 2047: Inf/NaN -> none)
-      bscale = (e == 2047u) ? 0 : ((e == 0u) ? 1000 : max(-1000, min(1000, (1023 + 16) - (int)e)));
       float uh = 0.f, ul = 0.f;
       int i = 0;
       for (; i + 4 <= nbk; i += 4) {
-        const float2 f0 = f64_to_ff_sc(cold[(i)*LD], bscale), f1 = f64_to_ff_sc(cold[(i + 1) * LD], bscale),
-                     f2 = f64_to_ff_sc(cold[(i + 2) * LD], bscale), f3 = f64_to_ff_sc(cold[(i + 3) * LD], bscale);
+        const float2 f0 = f64_to_ff_sc(cold[(i)*LD], wscale), f1 = f64_to_ff_sc(cold[(i + 1) * LD], wscale),
+                     f2 = f64_to_ff_sc(cold[(i + 2) * LD], wscale), f3 = f64_to_ff_sc(cold[(i + 3) * LD], wscale);
         float2 o0, o1, o2, o3;
         ff_axpy(f0.x, f0.y, rh, rl, uh, ul, o0.x, o0.y);
         ff_axpy(f1.x, f1.y, rh, rl, o0.x, o0.y, o1.x, o1.y);
@@ -234,7 +283,7 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
         ul = o3.y;
       }
       for (; i < nbk; ++i) {
-        const float2 f0 = f64_to_ff_sc(cold[i * LD], bscale);
+        const float2 f0 = f64_to_ff_sc(cold[i * LD], wscale);
         ff_axpy(f0.x, f0.y, rh, rl, uh, ul, uh, ul);
         col[i * LD] = make_float2(uh, ul);
       }
@@ -265,104 +314,116 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
         ff_mul(gh, gl, Xh, Xl, y0.x, y0.y);
         col[i * LD] = y0;
       }
-      // block-end quantities in unscaled FP64
-      const double down = pow2i(-bscale);
-      const double X0d = ((double)Xh + (double)Xl) * down;
-      xm1 = pp->g * pp->ib * X0d;
-      const float2 p0 = col[0], pe = col[(nbk - 1) * LD];
-      alpha = ((double)p0.x + (double)p0.y) * down - xm1 * v0;
-      omega = ((double)pe.x + (double)pe.y) * down - xm1 * vend;
+      // block-end quantities (float-float, window-scaled units)
+      const ffv gib = ffv{pp->gib_h, pp->gib_l};
+      const ffv v0 = lastb ? ffv{pp->v0l_h, pp->v0l_l} : ffv{pp->v0_h, pp->v0_l};
+      const ffv vend = lastb ? ffv{pp->vendl_h, pp->vendl_l} : ffv{pp->vend_h, pp->vend_l};
+      const ffv xm = ff_mul(gib, ff_make(Xh, Xl));
+      xm1 = xm;
+      alpha = ff_sub(ff_of(col[0]), ff_mul(xm, v0));
+      omega = ff_sub(ff_of(col[(nbk - 1) * LD]), ff_mul(xm, vend));
     }
   }
 
   // ---------------------------------------------------------------- beta (eq. 16)
-  const double* bc = tab + pp->o_bcm;
+  int64_t rec = (FORM == FORM_F64) ? pp->o_bcm : pp->o_bcmf;
   if (act) {
     if (mb < pp->kl)
-      bc = tab + pp->o_bcl + mb * kBC;
+      rec = ((FORM == FORM_F64) ? pp->o_bcl : pp->o_bclf) + mb * kBC;
     else if (mb >= P - pp->kr)
-      bc = tab + pp->o_bcr + (mb - (P - pp->kr)) * kBC;
+      rec = ((FORM == FORM_F64) ? pp->o_bcr : pp->o_bcrf) + (mb - (P - pp->kr)) * kBC;
   }
-  const double bL = act ? fma(bc[BC_M00], alpha, bc[BC_M01] * omega) : 0.0;
-  const double bR = act ? fma(bc[BC_M10], alpha, bc[BC_M11] * omega) : 0.0;
+  const V bL = act ? O::fma(O::bc(tab, rec, BC_M00), alpha, O::mul(O::bc(tab, rec, BC_M01), omega)) : O::zero();
+  const V bR = act ? O::fma(O::bc(tab, rec, BC_M10), alpha, O::mul(O::bc(tab, rec, BC_M11), omega)) : O::zero();
 
-  if (A.mode == MODE_BETA) {
+  if (A.mode == MODE_BETA) {  // general path: beta leaves the window as unscaled FP64
     if (act) {
-      A.beta[2 * mb] = bL;
-      A.beta[2 * mb + 1] = bR;
+      if constexpr (FORM == FORM_F64) {
+        A.beta[2 * mb] = *reinterpret_cast<const double*>(&bL);
+        A.beta[2 * mb + 1] = *reinterpret_cast<const double*>(&bR);
+      } else {
+        const double dn = pow2i(-wscale);
+        A.beta[2 * mb] = ff_to_double(*reinterpret_cast<const ffv*>(&bL)) * dn;
+        A.beta[2 * mb + 1] = ff_to_double(*reinterpret_cast<const ffv*>(&bR)) * dn;
+      }
     }
     return;
   }
 
-  double XL = 0.0, XR = 0.0;
+  V XL = O::zero(), XR = O::zero();
+  V* swv = reinterpret_cast<V*>(swa);
+  V* sxsv = reinterpret_cast<V*>(sxs);
+  V* sxev = reinterpret_cast<V*>(sxe);
   if (A.mode == MODE_FULL) {
     // ------------------------------------------------------------ dichotomy tree (a2)
     // prefix maps A -> a A + b beta^R (left to right), suffix maps B -> c B + d beta^L
-    double pa = act ? bc[BC_A] : 1.0, pb = act ? bc[BC_B] * bR : 0.0;
-    double qa = act ? bc[BC_C] : 1.0, qb = act ? bc[BC_D] * bL : 0.0;
+    V pa = act ? O::bc(tab, rec, BC_A) : O::one();
+    V pb = act ? O::mul(O::bc(tab, rec, BC_B), bR) : O::zero();
+    V qa = act ? O::bc(tab, rec, BC_C) : O::one();
+    V qb = act ? O::mul(O::bc(tab, rec, BC_D), bL) : O::zero();
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      const double ya = __shfl_up_sync(0xffffffffu, pa, d), yb = __shfl_up_sync(0xffffffffu, pb, d);
-      const double za = __shfl_down_sync(0xffffffffu, qa, d), zb = __shfl_down_sync(0xffffffffu, qb, d);
+      const V ya = O::up(pa, d), yb = O::up(pb, d);
+      const V za = O::down(qa, d), zb = O::down(qb, d);
       if (lane >= d) {
-        pb = fma(pa, yb, pb);
-        pa = pa * ya;
+        pb = O::fma(pa, yb, pb);
+        pa = O::mul(pa, ya);
       }
       if (lane + d < 32) {
-        qb = fma(qa, zb, qb);
-        qa = qa * za;
+        qb = O::fma(qa, zb, qb);
+        qa = O::mul(qa, za);
       }
     }
     if (lane == 31) {
-      swa[wid] = pa;
-      swa[NW + wid] = pb;
+      swv[wid] = pa;
+      swv[NW + wid] = pb;
     }
     if (lane == 0) {
-      swa[2 * NW + wid] = qa;
-      swa[3 * NW + wid] = qb;
+      swv[2 * NW + wid] = qa;
+      swv[3 * NW + wid] = qb;
     }
     // previous lane's inclusive prefix, next lane's inclusive suffix
-    double ea = __shfl_up_sync(0xffffffffu, pa, 1), eb = __shfl_up_sync(0xffffffffu, pb, 1);
-    double fa = __shfl_down_sync(0xffffffffu, qa, 1), fb = __shfl_down_sync(0xffffffffu, qb, 1);
+    V ea = O::up(pa, 1), eb = O::up(pb, 1);
+    V fa = O::down(qa, 1), fb = O::down(qb, 1);
     if (lane == 0) {
-      ea = 1.0;
-      eb = 0.0;
+      ea = O::one();
+      eb = O::zero();
     }
     if (lane == 31) {
-      fa = 1.0;
-      fb = 0.0;
+      fa = O::one();
+      fb = O::zero();
     }
     __syncthreads();
-    double Aw = 0.0, Bw = 0.0;  // zero coupling enters at both window ends
-    for (int w = 0; w < wid; ++w) Aw = fma(swa[w], Aw, swa[NW + w]);
-    for (int w = NW - 1; w > wid; --w) Bw = fma(swa[2 * NW + w], Bw, swa[3 * NW + w]);
-    const double Am = fma(ea, Aw, eb);
-    const double Bm = fma(fa, Bw, fb);
-    const double xs = Am + bL + bc[BC_TL] * Bm;
-    const double xe = fma(bc[BC_TR], Am, bR + Bm);
-    sxs[tid] = xs;
-    sxe[tid] = xe;
+    V Aw = O::zero(), Bw = O::zero();  // zero coupling enters at both window ends
+    for (int w = 0; w < wid; ++w) Aw = O::fma(swv[w], Aw, swv[NW + w]);
+    for (int w = NW - 1; w > wid; --w) Bw = O::fma(swv[2 * NW + w], Bw, swv[3 * NW + w]);
+    const V Am = O::fma(ea, Aw, eb);
+    const V Bm = O::fma(fa, Bw, fb);
+    sxsv[tid] = O::add(O::fma(O::bc(tab, rec, BC_TL), Bm, bL), Am);            // x_s (eq. 18)
+    sxev[tid] = O::fma(O::bc(tab, rec, BC_TR), Am, O::add(bR, Bm));           // x_e
     __syncthreads();
     if (act) {
-      XL = (mb == 0 || tid == 0) ? 0.0 : sxe[tid - 1];
-      XR = (mb == P - 1 || tid + 1 >= nwin) ? 0.0 : sxs[tid + 1];
+      if (!(mb == 0 || tid == 0)) XL = sxev[tid - 1];
+      if (!(mb == P - 1 || tid + 1 >= nwin)) XR = sxsv[tid + 1];
     }
   } else {  // MODE_APPLY: first/last values of the neighbours from the global scan
     if (act) {
-      XL = (mb == 0) ? 0.0 : A.iface[2 * (mb - 1) + 1];
-      XR = (mb == P - 1) ? 0.0 : A.iface[2 * (mb + 1)];
+      const double dl = (mb == 0) ? 0.0 : A.iface[2 * (mb - 1) + 1];
+      const double dr = (mb == P - 1) ? 0.0 : A.iface[2 * (mb + 1)];
+      if constexpr (FORM == FORM_F64) {
+        *reinterpret_cast<double*>(&XL) = dl;
+        *reinterpret_cast<double*>(&XR) = dr;
+      } else {
+        const double upw = pow2i(wscale);
+        const float2 a2 = f64_to_ff_rn(dl * upw), b2 = f64_to_ff_rn(dr * upw);
+        *reinterpret_cast<ffv*>(&XL) = ffv{a2.x, a2.y};
+        *reinterpret_cast<ffv*>(&XR) = ffv{b2.x, b2.y};
+      }
     }
   }
-  if (FORM == FORM_F64) {
-    scl[tid] = XL - xm1;
-    scr[tid] = XR;
-  } else {  // correction coefficients in the block's scaled units, as float-float
-    const double up = pow2i(bscale);
-    const float2 c1 = f64_to_ff_rn((XL - xm1) * up), c2 = f64_to_ff_rn(XR * up);
-    reinterpret_cast<float2*>(scl)[tid] = c1;
-    reinterpret_cast<float2*>(scr)[tid] = c2;
-    ssc[tid] = bscale;
-  }
+  // correction coefficients of the block spikes (a3): x = xp + cL v + cR w
+  reinterpret_cast<V*>(scl)[tid] = O::sub(XL, xm1);
+  reinterpret_cast<V*>(scr)[tid] = XR;
   __syncthreads();
 
   // ---------------------------------------------------------------- correction + store (a3)
@@ -382,7 +443,7 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
       const int lv = lb ? nlast : Lv, lw = lb ? nlast : Lw;
       const int jr = nb - 1 - i;
       double dv;
-      if (FORM == FORM_F64) {
+      if constexpr (FORM == FORM_F64) {
         double val = S[i * LD + b];
         if (i < lv) val = fma(scl[b], (lb ? tvl : tv)[i], val);
         if (jr < lw) val = fma(scr[b], (lb ? twl : tw)[jr], val);
@@ -399,7 +460,7 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
           const float2 ww = reinterpret_cast<const float2*>(lb ? twl : tw)[jr];
           ff_fma_acc(c.x, c.y, ww.x, ww.y, val.x, val.y);
         }
-        dv = ff_to_f64_int(val.x, val.y, ssc[b]);
+        dv = ff_to_f64_int(val.x, val.y, wscale);
       }
       __stcs(dst + j, dv);
       if (A.check_finite && !isfinite(dv)) bad = 1u;
