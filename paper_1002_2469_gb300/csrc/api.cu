@@ -38,14 +38,21 @@ constexpr size_t kSmemBudget = 110 * 1024;
 // an explicitly requested block size may use up to the per-CTA maximum (one CTA per SM)
 constexpr size_t kSmemMax = 225 * 1024;
 
-int max_rows(int NT, size_t budget) {
-  // window_smem_bytes(NT, n) <= budget
+// window width in blocks: the MIXED kernel gives every thread two blocks
+int window_blocks(int NT, int form) { return form == FORM_MIXED ? 2 * NT : NT; }
+
+size_t smem_bytes(int NT, int n, int form) {
+  return form == FORM_MIXED ? window2_smem_bytes(NT, n) : window_smem_bytes(NT, n);
+}
+
+int max_rows(int NT, int form, size_t budget) {
+  // smem_bytes(NT, n, form) <= budget
   int n = 2;
-  while (window_smem_bytes(NT, n + 1) <= budget) ++n;
+  while (smem_bytes(NT, n + 1, form) <= budget) ++n;
   return n;
 }
 
-int default_threads(int form) { return form == FORM_F64 ? 64 : 128; }
+int default_threads(int form) { return form == FORM_F64 ? 64 : 64; }
 
 // rows per block for multi-window systems (measured on GB300 at N = 2^26: small windows let
 // several CTAs share an SM so loads, sweeps, tree and stores of different windows overlap)
@@ -176,7 +183,8 @@ int build_system(double tm1, double t0, double tp1, int64_t N, int NT, int form,
 
   // path and halos
   const int64_t P = p.P;
-  if (P <= NT && !(o.flags & DICH_FLAG_FORCE_GENERAL)) {
+  const int WB = window_blocks(NT, form);
+  if (P <= WB && !(o.flags & DICH_FLAG_FORCE_GENERAL)) {
     sb.path = PATH_SINGLE;
     p.hl = p.hr = 0;
     p.own = (int)P;
@@ -184,16 +192,16 @@ int build_system(double tm1, double t0, double tp1, int64_t N, int NT, int form,
     // the neighbour's first/last value must carry decayed coupling too: +1 row of margin
     const int64_t hl = (std::fabs(r.rs) == 0.0) ? 1 : (Ls >= BIG ? BIG : std::max<int64_t>(1, ceil_div(Ls + 1, n)));
     const int64_t hr = (std::fabs(r.ib) == 0.0) ? 1 : (Lb >= BIG ? BIG : std::max<int64_t>(1, ceil_div(Lb + 1, n)));
-    if (!(o.flags & DICH_FLAG_FORCE_GENERAL) && hl + hr <= NT / 2) {
+    if (!(o.flags & DICH_FLAG_FORCE_GENERAL) && hl + hr <= WB / 2) {
       sb.path = PATH_HALO;
       p.hl = (int)hl;
       p.hr = (int)hr;
-      p.own = NT - (int)hl - (int)hr;
+      p.own = WB - (int)hl - (int)hr;
     } else {
       if (!allow_general) return DICH_ERR_UNSUPPORTED;
       sb.path = PATH_GENERAL;
       p.hl = p.hr = 0;
-      p.own = NT;
+      p.own = WB;
     }
   }
 
@@ -381,8 +389,9 @@ int dichotomy_plan_ex(double t_m1, double t_0, double t_1, int64_t N, const dich
   p->form = pick_form(o.prec, r);
   p->NT = o.NT ? o.NT : default_threads(p->form);
   if (N >= 2) {
-    const int nmax = max_rows(p->NT, o.n_req > 0 ? kSmemMax : kSmemBudget);
-    const int n = choose_n(N, p->NT, nmax, o.n_req, default_rows(p->form));
+    const int nmax = max_rows(p->NT, p->form, o.n_req > 0 ? kSmemMax : kSmemBudget);
+    const int WB = window_blocks(p->NT, p->form);
+    const int n = choose_n(N, WB, nmax, o.n_req, default_rows(p->form));
     rc = build_system(t_m1, t_0, t_1, N, p->NT, p->form, n, o, true, p->fwd);
     if (!rc) rc = build_system(t_1, t_0, t_m1, N, p->NT, p->form, n, o, true, p->adj);
     if (rc) {
@@ -402,9 +411,9 @@ int dichotomy_plan_ex(double t_m1, double t_0, double t_1, int64_t N, const dich
       for (SysBuild* sb : {&p->fwd, &p->adj}) {
         sb->rec.hl = hl;
         sb->rec.hr = hr;
-        sb->rec.own = p->NT - hl - hr;
+        sb->rec.own = WB - hl - hr;
       }
-      if (p->NT - hl - hr < p->NT / 2) {
+      if (WB - hl - hr < WB / 2) {
         Opts og = o;
         og.flags |= DICH_FLAG_FORCE_GENERAL;
         build_system(t_m1, t_0, t_1, N, p->NT, p->form, n, og, true, p->fwd);
@@ -529,7 +538,7 @@ static int plan_launch(dich_plan_t p, const double* F, double* x, const double* 
   a.check_finite = (p->opts.flags & DICH_FLAG_CHECK_FINITE) ? 1 : 0;
   a.n_smem = p->n_smem;
   a.sys_offset = sys_offset;
-  const size_t smem = window_smem_bytes(p->NT, p->n_smem);
+  const size_t smem = smem_bytes(p->NT, p->n_smem, p->form);
   auto launch = [&](const WinArgs& w) {
     return p->form == FORM_F64 ? launch_window_f64(p->NT, (int)p->tiles, smem, st, w)
                                : launch_window_mixed(p->NT, (int)p->tiles, smem, st, w);
@@ -643,8 +652,7 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
   if (!b) return DICH_ERR_ARG;
   b->nsys = nsys;
   b->opts = o;
-  b->NT = o.NT ? o.NT : 128;
-  const int nmax = max_rows(b->NT, o.n_req > 0 ? kSmemMax : kSmemBudget);
+  b->NT = o.NT ? o.NT : 64;
   b->fwd.resize((size_t)nsys);
   b->adj.resize((size_t)nsys);
   b->form.assign((size_t)nsys, FORM_F64);
@@ -670,7 +678,8 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
       if (h_N[s] == 1) b->trivial.push_back((int32_t)s);
       continue;
     }
-    const int n = choose_n(h_N[s], b->NT, nmax, o.n_req, default_rows(b->form[s]));
+    const int nmax = max_rows(b->NT, b->form[s], o.n_req > 0 ? kSmemMax : kSmemBudget);
+    const int n = choose_n(h_N[s], window_blocks(b->NT, b->form[s]), nmax, o.n_req, default_rows(b->form[s]));
     Opts oh = o;
     oh.flags &= ~DICH_FLAG_FORCE_GENERAL;
     rc = build_system(h_tm1[s], h_t0[s], h_tp1[s], h_N[s], b->NT, b->form[s], n, oh, false, b->fwd[s]);
@@ -683,14 +692,15 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
     if (b->fwd[s].path == PATH_HALO || b->adj[s].path == PATH_HALO) {
       const int hl = std::max(b->fwd[s].rec.hl, b->adj[s].rec.hl);
       const int hr = std::max(b->fwd[s].rec.hr, b->adj[s].rec.hr);
-      if (hl + hr > b->NT / 2) {
+      const int WBs = window_blocks(b->NT, b->form[s]);
+      if (hl + hr > WBs / 2) {
         delete b;
         return DICH_ERR_UNSUPPORTED;
       }
       for (SysBuild* sb : {&b->fwd[s], &b->adj[s]}) {
         sb->rec.hl = hl;
         sb->rec.hr = hr;
-        sb->rec.own = b->NT - hl - hr;
+        sb->rec.own = WBs - hl - hr;
         sb->path = PATH_HALO;
       }
     }
@@ -815,7 +825,7 @@ static int batch_launch(dich_batch_t b, const double* F, double* x, const double
     a.check_finite = (b->opts.flags & DICH_FLAG_CHECK_FINITE) ? 1 : 0;
     a.n_smem = b->n_smem[f];
     a.sys_offset = sys_offset;
-    const size_t smem = window_smem_bytes(b->NT, a.n_smem);
+    const size_t smem = smem_bytes(b->NT, a.n_smem, f);
     cudaError_t e = (f == FORM_F64) ? launch_window_f64(b->NT, (int)nitems, smem, st, a)
                                     : launch_window_mixed(b->NT, (int)nitems, smem, st, a);
     if (e != cudaSuccess) return cuda_fail(e);

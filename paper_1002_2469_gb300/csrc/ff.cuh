@@ -250,4 +250,112 @@ __device__ __forceinline__ ffv ff_shfl_down(ffv a, int d) {
 __device__ __forceinline__ double ff_to_double(ffv a) { return (double)a.h + (double)a.l; }
 __device__ __forceinline__ float2 ff_f2(ffv a) { return make_float2(a.h, a.l); }
 
+// ---------------------------------------------------------------- packed (two-chain) helpers
+// The MIXED window kernel advances two blocks per thread; both chains go through one
+// f32x2 instruction (sm_100+ FFMA2/FADD2/FMUL2: half the issue slots of scalar FP32).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// two chains of ff_axpy: y = f + r * x with f, x, y as (hi pair, lo pair), r a float-float scalar
+__device__ __forceinline__ void ff_axpy2(float2 fh, float2 fl, float2 rh, float2 rl, float2 xh, float2 xl,
+                                         float2& yh, float2& yl) {
+  const float2 p = mul2(rh, xh);
+  const float2 pe = fma2(rh, xh, make_float2(-p.x, -p.y));
+  const float2 s = add2(fh, p);
+  const float2 bb = sub2(s, fh);
+  const float2 se = add2(sub2(fh, sub2(s, bb)), sub2(p, bb));
+  float2 c = add2(fl, add2(pe, se));
+  c = fma2(rl, xh, c);
+  c = fma2(rh, xl, c);
+  yh = s;
+  yl = c;
+}
+
+// two chains of ff_mul: y = g * x
+__device__ __forceinline__ void ff_mul2(float2 gh, float2 gl, float2 xh, float2 xl, float2& yh, float2& yl) {
+  const float2 p = mul2(gh, xh);
+  float2 c = fma2(gh, xh, make_float2(-p.x, -p.y));
+  c = fma2(gl, xh, c);
+  c = fma2(gh, xl, c);
+  yh = p;
+  yl = c;
+}
+
+// two chains of x += c * v, c and v float-float (per chain)
+__device__ __forceinline__ void ff_fma_acc2(float2 ch, float2 cl, float2 vh, float2 vl, float2& xh, float2& xl) {
+  const float2 p = mul2(ch, vh);
+  const float2 pe = fma2(ch, vh, make_float2(-p.x, -p.y));
+  const float2 pc = fma2(cl, vh, fma2(ch, vl, pe));
+  const float2 s = add2(xh, p);
+  const float2 bb = sub2(s, xh);
+  const float2 se = add2(sub2(xh, sub2(s, bb)), sub2(p, bb));
+  xl = add2(xl, add2(pc, se));
+  xh = s;
+}
+
+// FP64 -> (hi, lo) floats of d * 2^s with integer operations; `sb` = s - 896 is precomputed.
+// hi = leading 24 bits (truncated), lo = next 23 bits (truncated); values whose scaled
+// exponent falls outside the float range flush to zero (hi) / drop lo, exponents of
+// Inf/NaN give Inf/NaN.  Subnormal FP64 inputs are rescaled exactly first (rare path).
+__device__ __forceinline__ void split_sc(double d, int s, float& hi, float& lo) {
+  unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
+  int sb = s - 896;
+  if ((hw & 0x7FF00000u) == 0u && ((hw & 0x000FFFFFu) | lw) != 0u) {   // FP64 subnormal
+    const double d2 = d * 18446744073709551616.0;                      // * 2^64, exact
+    hw = (unsigned)__double2hiint(d2);
+    lw = (unsigned)__double2loint(d2);
+    sb -= 64;
+  }
+  const unsigned sgn = hw & 0x80000000u;
+  const int E0 = (int)((hw >> 20) & 0x7FFu);
+  const int ef = E0 + sb;                                             // float exponent of hi
+  const unsigned m23 = __funnelshift_l(lw, hw, 3) & 0x7FFFFFu;        // 23 fraction bits
+  unsigned hib = sgn | ((unsigned)ef << 23) | m23;
+  const bool in_range = ((unsigned)(ef - 1) < 254u) && (E0 != 0);
+  if (!in_range) hib = (E0 == 2047) ? (sgn | 0x7F800000u | (m23 ? 0x400000u : 0u)) :
+                                      ((ef > 254 && E0 != 0) ? (sgn | 0x7F800000u) : sgn);
+  const float rf = __fsub_rn(__uint_as_float(0x4B000000u | ((lw >> 6) & 0x7FFFFFu)), 8388608.0f);
+  const int es = ef - 46;                                             // exponent of the lo scale
+  const float sc = __uint_as_float((unsigned)es << 23);
+  float l = __fmul_rn(rf, sc);
+  l = ((unsigned)(es - 1) < 254u && in_range) ? l : 0.0f;
+  hi = __uint_as_float(hib);
+  lo = __uint_as_float(__float_as_uint(l) | sgn);
+}
+
+// (h, l) * 2^-s -> FP64 with 32-bit integer operations only.  FastTwoSum renormalises
+// (|e| <= ulp(s1)/2 when |l| <= |h|); e is turned into an integer count K of the double's
+// last place (bits below it truncated) and added to the 64-bit pattern of s1 with one
+// carry-propagating add.  Results below the FP64 normal range become subnormal or zero.
+__device__ __forceinline__ double join_sc(float h, float l, int s) {
+  const float s1 = __fadd_rn(h, l);
+  const float e1 = __fsub_rn(l, __fsub_rn(s1, h));
+  const unsigned b1 = __float_as_uint(s1), be = __float_as_uint(e1);
+  const unsigned sg = b1 & 0x80000000u;
+  const int E1 = (int)((b1 >> 23) & 0xFFu);
+  const unsigned f1 = b1 & 0x7FFFFFu;
+  const int Ed = E1 + 896 - s;
+  const int Ee = (int)((be >> 23) & 0xFFu);
+  const unsigned Me = (be & 0x7FFFFFu) | 0x800000u;
+  const int sh = Ee - E1 + 29;                 // <= 5
+  unsigned K = (sh >= 0) ? (Me << sh) : ((sh > -32) ? (Me >> (-sh)) : 0u);
+  if (Ee == 0) K = 0u;
+  if (f1 == 0u && ((be ^ b1) & 0x80000000u)) K <<= 1;   // below an exact power of two
+  const int Ks = ((be ^ b1) & 0x80000000u) ? -(int)K : (int)K;
+  unsigned lo = f1 << 29;
+  unsigned hi = sg | ((unsigned)Ed << 20) | (f1 >> 3);
+  // 64-bit add of the signed count to (hi:lo), magnitude direction (sign bit untouched)
+  asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, %3;" : "+r"(lo), "+r"(hi) : "r"((unsigned)Ks),
+      "r"((unsigned)(Ks >> 31)));
+  if ((unsigned)(Ed - 1) >= 2046u || E1 == 0 || E1 == 255) {   // rare: zero, Inf/NaN, out of range
+    if (E1 == 0) return __hiloint2double((int)sg, 0);
+    if (E1 == 255 || Ed >= 2047) return __hiloint2double((int)(sg | 0x7FF00000u | (E1 == 255 && f1 ? 0x80000u : 0u)), 0);
+    return (double)s1 * __hiloint2double((1023 - s) << 20, 0) + (double)e1 * __hiloint2double((1023 - s) << 20, 0);
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 }  // namespace dich

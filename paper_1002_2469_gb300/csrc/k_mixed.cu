@@ -1,4 +1,4 @@
-// k_mixed.cu -- MIXED-form (compensated FP32 sweeps, FP64 tree) instantiations of the window kernel.
+// k_mixed.cu -- instantiations of the MIXED-form window kernel (two blocks per thread, packed FP32x2).
 #include "launch.cuh"
 
 namespace dich {
@@ -6,11 +6,11 @@ namespace dich {
 template <int NT>
 static cudaError_t launch_one(int grid, size_t smem, cudaStream_t st, const WinArgs& a) {
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_window<NT, FORM_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_window2<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_window<NT, FORM_MIXED><<<grid, NT, smem, st>>>(a);
+  k_window2<NT><<<grid, NT, smem, st>>>(a);
   return cudaGetLastError();
 }
 

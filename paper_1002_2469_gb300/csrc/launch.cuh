@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include "window.cuh"
+#include "window_mixed.cuh"
 
 namespace dich {
 

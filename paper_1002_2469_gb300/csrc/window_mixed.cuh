@@ -1,0 +1,449 @@
+// window_mixed.cuh -- the MIXED-form window kernel: two blocks per thread, packed FP32x2.
+//
+// Same steps as k_window (window.cuh): load the window transposed, local sweeps (a1), beta,
+// the dichotomy tree (a2), the spike correction and store (a3).  Differences:
+//   - thread t owns the adjacent window blocks 2t and 2t+1; shared-memory rows hold a
+//     thread's pair in one 16-byte slot, and both recurrences advance through one f32x2
+//     instruction (sm_100+ FFMA2/FADD2/FMUL2), halving the issue slots of the sweeps and
+//     doubling the independent work per thread;
+//   - the per-row layout of a pair is [hi(2t), hi(2t+1), lo(2t), lo(2t+1)] during the
+//     sweeps and [x(2t), x(2t+1)] as FP64 after the correction;
+//   - the thread composes its two blocks' affine maps before the warp/CTA scans;
+//   - the correction and the FP64 join run per thread along its own columns (no per-element
+//     index bookkeeping), then the CTA stores its own rows with contiguous coalesced writes.
+// Arithmetic: compensated FP32 sweeps, float-float block quantities and tree, one exact
+// power-of-two scale per window (see ff.cuh).
+#pragma once
+#include "window.cuh"
+
+namespace dich {
+
+// shared memory of the MIXED window kernel: NT threads, 2 NT window blocks, n_smem rows
+__host__ __device__ inline size_t window2_smem_bytes(int NT, int n_smem) {
+  const size_t nw = (size_t)(NT / 32);
+  const size_t LD = 2 * (size_t)NT + 2;
+  return sizeof(double) * ((size_t)n_smem * LD + 4 * (size_t)n_smem + 8 * (size_t)NT + 4 * nw + 8);
+}
+
+// forward and backward sweeps of a thread's pair of blocks, in place.  GUARD: the two blocks
+// may differ in size (the system's last block) or be inactive (nb = 0): rows at or beyond a
+// block's size enter as zero, which keeps its backward recurrence exact.
+template <int LD, bool GUARD>
+__device__ __forceinline__ void sweep_pair(double* S, int tid, int nrow, int nb0, int nb1, int wscale,
+                                           const SysPlan* pp, float2& Xh, float2& Xl) {
+  const float2 rh = f2(pp->rs_h), rl = f2(pp->rs_l), bh = f2(pp->ib_h), bl = f2(pp->ib_l);
+  const float2 gh = f2(pp->g_h), gl = f2(pp->g_l);
+  float2 uh = f2(0.f), ul = f2(0.f);
+  for (int i = 0; i < nrow; ++i) {
+    double* row = S + (size_t)i * LD + 2 * tid;
+    const double2 fd = *reinterpret_cast<const double2*>(row);
+    float2 fh, fl;
+    split_sc(fd.x, wscale, fh.x, fl.x);
+    split_sc(fd.y, wscale, fh.y, fl.y);
+    if (GUARD) {
+      if (i >= nb0) fh.x = fl.x = 0.f;
+      if (i >= nb1) fh.y = fl.y = 0.f;
+    }
+    ff_axpy2(fh, fl, rh, rl, uh, ul, uh, ul);
+    *reinterpret_cast<float4*>(row) = make_float4(uh.x, uh.y, ul.x, ul.y);
+  }
+  float2 xh = f2(0.f), xl = f2(0.f);
+  for (int i = nrow - 1; i >= 0; --i) {
+    double* row = S + (size_t)i * LD + 2 * tid;
+    float4 q = *reinterpret_cast<const float4*>(row);
+    if (GUARD) {
+      if (i >= nb0) q.x = q.z = 0.f;
+      if (i >= nb1) q.y = q.w = 0.f;
+    }
+    ff_axpy2(make_float2(q.x, q.y), make_float2(q.z, q.w), bh, bl, xh, xl, xh, xl);
+    float2 yh, yl;
+    ff_mul2(gh, gl, xh, xl, yh, yl);
+    *reinterpret_cast<float4*>(row) = make_float4(yh.x, yh.y, yl.x, yl.y);
+  }
+  Xh = xh;
+  Xl = xl;
+}
+
+// correction x = xp + cL v + cR w along the thread's pair of columns and the FP64 join, in place.
+template <int LD, bool GUARD>
+__device__ __forceinline__ void correct_pair(double* S, int tid, int nrow, int nb0, int nb1, bool last0,
+                                             bool last1, int n, int nlast, int Lv, int Lw, const float2* tv,
+                                             const float2* tw, const float2* tvl, const float2* twl, ffv cL0,
+                                             ffv cL1, ffv cR0, ffv cR1, int wscale) {
+  const float2 clh = make_float2(cL0.h, cL1.h), cll = make_float2(cL0.l, cL1.l);
+  const float2 crh = make_float2(cR0.h, cR1.h), crl = make_float2(cR0.l, cR1.l);
+  if (!GUARD) {
+    // both blocks full size: one spike table, one row index for both
+    for (int i = 0; i < nrow; ++i) {
+      double* row = S + (size_t)i * LD + 2 * tid;
+      const float4 q = *reinterpret_cast<const float4*>(row);
+      float2 xh = make_float2(q.x, q.y), xl = make_float2(q.z, q.w);
+      if (i < Lv) {
+        const float2 v = tv[i];
+        ff_fma_acc2(clh, cll, f2(v.x), f2(v.y), xh, xl);
+      }
+      const int j = n - 1 - i;
+      if (j < Lw) {
+        const float2 w = tw[j];
+        ff_fma_acc2(crh, crl, f2(w.x), f2(w.y), xh, xl);
+      }
+      *reinterpret_cast<double2*>(row) = make_double2(join_sc(xh.x, xl.x, wscale), join_sc(xh.y, xl.y, wscale));
+    }
+  } else {
+    const int lv0 = last0 ? nlast : Lv, lw0 = last0 ? nlast : Lw;
+    const int lv1 = last1 ? nlast : Lv, lw1 = last1 ? nlast : Lw;
+    const float2* v0t = last0 ? tvl : tv;
+    const float2* w0t = last0 ? twl : tw;
+    const float2* v1t = last1 ? tvl : tv;
+    const float2* w1t = last1 ? twl : tw;
+    for (int i = 0; i < nrow; ++i) {
+      double* row = S + (size_t)i * LD + 2 * tid;
+      const float4 q = *reinterpret_cast<const float4*>(row);
+      float2 xh = make_float2(q.x, q.y), xl = make_float2(q.z, q.w);
+      float2 vh = f2(0.f), vl = f2(0.f), wh = f2(0.f), wl = f2(0.f);
+      if (i < nb0 && i < lv0) {
+        vh.x = v0t[i].x;
+        vl.x = v0t[i].y;
+      }
+      if (i < nb1 && i < lv1) {
+        vh.y = v1t[i].x;
+        vl.y = v1t[i].y;
+      }
+      const int j0 = nb0 - 1 - i, j1 = nb1 - 1 - i;
+      if (i < nb0 && j0 < lw0) {
+        wh.x = w0t[j0].x;
+        wl.x = w0t[j0].y;
+      }
+      if (i < nb1 && j1 < lw1) {
+        wh.y = w1t[j1].x;
+        wl.y = w1t[j1].y;
+      }
+      ff_fma_acc2(clh, cll, vh, vl, xh, xl);
+      ff_fma_acc2(crh, crl, wh, wl, xh, xl);
+      double d0 = (i < nb0) ? join_sc(xh.x, xl.x, wscale) : 0.0;
+      double d1 = (i < nb1) ? join_sc(xh.y, xl.y, wscale) : 0.0;
+      *reinterpret_cast<double2*>(row) = make_double2(d0, d1);
+    }
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_window2(const WinArgs A) {
+  constexpr int NW = NT / 32;
+  constexpr int WB = 2 * NT;       // window blocks
+  constexpr int LD = 2 * NT + 2;   // shared row stride in doubles (even: 16-byte pairs)
+  using O = OpsFF;
+  extern __shared__ __align__(16) double sm[];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int ns = A.n_smem;
+  double* S = sm;
+  float2* tv = reinterpret_cast<float2*>(S + (size_t)ns * LD);
+  float2* tw = tv + ns;
+  float2* tvl = tw + ns;
+  float2* twl = tvl + ns;
+  ffv* sxs = reinterpret_cast<ffv*>(twl + ns);
+  ffv* sxe = sxs + WB;
+  ffv* swv = sxe + WB;  // 4 * NW scan scratch (also the exponent maxima)
+  // (4 NT doubles of the budget reserved after swv are unused here; keeps the size formula simple)
+
+  // ---------------------------------------------------------------- the window
+  int sys;
+  int64_t m0;
+  int nown;
+  if (A.items) {
+    const Item it = A.items[blockIdx.x];
+    sys = it.sys;
+    m0 = it.m0;
+    nown = it.n_own;
+  } else {
+    sys = 0;
+    m0 = 0;
+    nown = 0;
+  }
+  sys += A.sys_offset;
+  const SysPlan* pp = A.plans + sys;
+  const int64_t P = pp->P;
+  if (!A.items) {
+    nown = pp->own;
+    m0 = (int64_t)blockIdx.x * nown;
+    if (m0 + nown > P) nown = (int)(P - m0);
+  }
+  int hl = 0, hr = 0;
+  if (A.mode == MODE_FULL) {
+    hl = (int)min((int64_t)pp->hl, m0);
+    hr = (int)min((int64_t)pp->hr, P - m0 - nown);
+  }
+  const int64_t wlo = m0 - hl;
+  const int nwin = hl + nown + hr;
+  const int n = pp->n, nlast = pp->nlast;
+  const int Lv = pp->Lv, Lw = pp->Lw;
+  const int64_t off = pp->off;
+  const double* tab = A.tabs + pp->tab;
+  const bool has_last = (wlo + nwin == P);
+  const int64_t row_lo = wlo * (int64_t)n;
+  const int len = nwin * n - (has_last ? (n - nlast) : 0);
+
+  // ---------------------------------------------------------------- F -> smem (transposed, async)
+  {
+    const double* src = A.F + off + row_lo;
+    int b = tid / n, i = tid - (tid / n) * n;
+    const int db = NT / n, di = NT - (NT / n) * n;
+    for (int j = tid; j < len; j += NT) {
+      cp_async8(&S[(size_t)i * LD + b], src + j);
+      i += di;
+      b += db;
+      if (i >= n) {
+        i -= n;
+        ++b;
+      }
+    }
+  }
+  {
+    const float2* tf = reinterpret_cast<const float2*>(tab);
+    for (int i = tid; i < Lv; i += NT) tv[i] = tf[pp->o_vf + i];
+    for (int i = tid; i < Lw; i += NT) tw[i] = tf[pp->o_wf + i];
+    if (has_last)
+      for (int i = tid; i < nlast; i += NT) {
+        tvl[i] = tf[pp->o_vlf + i];
+        twl[i] = tf[pp->o_wlf + i];
+      }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  // ---------------------------------------------------------------- the thread's two blocks
+  const int b0 = 2 * tid, b1 = 2 * tid + 1;
+  const bool act0 = b0 < nwin, act1 = b1 < nwin;
+  const int64_t mb0 = wlo + b0, mb1 = wlo + b1;
+  const bool last0 = act0 && (mb0 == P - 1), last1 = act1 && (mb1 == P - 1);
+  const int nb0 = act0 ? (last0 ? nlast : n) : 0;
+  const int nb1 = act1 ? (last1 ? nlast : n) : 0;
+  const int nrow = max(nb0, nb1);
+  const bool full = (nb0 == n) && (nb1 == n);
+
+  // window scale: largest |F| of the window near 2^16 (exact power of two)
+  int wscale;
+  {
+    unsigned e = 0u;
+    for (int i = 0; i < nrow; ++i) {
+      const uint4 q = *reinterpret_cast<const uint4*>(S + (size_t)i * LD + 2 * tid);
+      if (i < nb0) e = max(e, (q.y >> 20) & 0x7FFu);
+      if (i < nb1) e = max(e, (q.w >> 20) & 0x7FFu);
+    }
+    e = __reduce_max_sync(0xffffffffu, e);
+    unsigned* sexp = reinterpret_cast<unsigned*>(swv);
+    if (lane == 0) sexp[wid] = e;
+    __syncthreads();
+    e = 0u;
+    for (int w = 0; w < NW; ++w) e = max(e, sexp[w]);
+    __syncthreads();
+    wscale = (e == 2047u) ? 0 : ((e == 0u) ? 1000 : max(-1000, min(1000, (1023 + 16) - (int)e)));
+  }
+
+  // ---------------------------------------------------------------- local sweeps (a1)
+  float2 Xh, Xl;
+  if (full)
+    sweep_pair<LD, false>(S, tid, nrow, nb0, nb1, wscale, pp, Xh, Xl);
+  else
+    sweep_pair<LD, true>(S, tid, nrow, nb0, nb1, wscale, pp, Xh, Xl);
+
+  // block-end quantities: xp(-1) = g ib X_0, alpha = xp_0 - xp(-1) v_0, omega = xp_{n-1} - xp(-1) v_{n-1}
+  const ffv gib = ffv{pp->gib_h, pp->gib_l};
+  ffv xm0 = ff_zero(), xm1 = ff_zero(), al0 = ff_zero(), al1 = ff_zero(), om0 = ff_zero(), om1 = ff_zero();
+  if (act0) {
+    const ffv v0 = last0 ? ffv{pp->v0l_h, pp->v0l_l} : ffv{pp->v0_h, pp->v0_l};
+    const ffv ve = last0 ? ffv{pp->vendl_h, pp->vendl_l} : ffv{pp->vend_h, pp->vend_l};
+    xm0 = ff_mul(gib, ff_make(Xh.x, Xl.x));
+    const float4 q0 = *reinterpret_cast<const float4*>(S + 2 * tid);
+    const float4 qe = *reinterpret_cast<const float4*>(S + (size_t)(nb0 - 1) * LD + 2 * tid);
+    al0 = ff_sub(ff_make(q0.x, q0.z), ff_mul(xm0, v0));
+    om0 = ff_sub(ff_make(qe.x, qe.z), ff_mul(xm0, ve));
+  }
+  if (act1) {
+    const ffv v0 = last1 ? ffv{pp->v0l_h, pp->v0l_l} : ffv{pp->v0_h, pp->v0_l};
+    const ffv ve = last1 ? ffv{pp->vendl_h, pp->vendl_l} : ffv{pp->vend_h, pp->vend_l};
+    xm1 = ff_mul(gib, ff_make(Xh.y, Xl.y));
+    const float4 q0 = *reinterpret_cast<const float4*>(S + 2 * tid);
+    const float4 qe = *reinterpret_cast<const float4*>(S + (size_t)(nb1 - 1) * LD + 2 * tid);
+    al1 = ff_sub(ff_make(q0.y, q0.w), ff_mul(xm1, v0));
+    om1 = ff_sub(ff_make(qe.y, qe.w), ff_mul(xm1, ve));
+  }
+
+  // ---------------------------------------------------------------- beta (eq. 16)
+  auto rec_of = [&](int64_t m) -> int64_t {
+    if (m < pp->kl) return pp->o_bclf + m * kBC;
+    if (m >= P - pp->kr) return pp->o_bcrf + (m - (P - pp->kr)) * kBC;
+    return pp->o_bcmf;
+  };
+  const int64_t r0 = act0 ? rec_of(mb0) : pp->o_bcmf;
+  const int64_t r1 = act1 ? rec_of(mb1) : pp->o_bcmf;
+  ffv bL0 = ff_zero(), bR0 = ff_zero(), bL1 = ff_zero(), bR1 = ff_zero();
+  if (act0) {
+    bL0 = O::fma(O::bc(tab, r0, BC_M00), al0, O::mul(O::bc(tab, r0, BC_M01), om0));
+    bR0 = O::fma(O::bc(tab, r0, BC_M10), al0, O::mul(O::bc(tab, r0, BC_M11), om0));
+  }
+  if (act1) {
+    bL1 = O::fma(O::bc(tab, r1, BC_M00), al1, O::mul(O::bc(tab, r1, BC_M01), om1));
+    bR1 = O::fma(O::bc(tab, r1, BC_M10), al1, O::mul(O::bc(tab, r1, BC_M11), om1));
+  }
+
+  if (A.mode == MODE_BETA) {  // general path: beta leaves the window as unscaled FP64
+    const double dn = pow2i(-wscale);
+    if (act0) {
+      A.beta[2 * mb0] = ff_to_double(bL0) * dn;
+      A.beta[2 * mb0 + 1] = ff_to_double(bR0) * dn;
+    }
+    if (act1) {
+      A.beta[2 * mb1] = ff_to_double(bL1) * dn;
+      A.beta[2 * mb1 + 1] = ff_to_double(bR1) * dn;
+    }
+    return;
+  }
+
+  ffv XL0 = ff_zero(), XR0 = ff_zero(), XL1 = ff_zero(), XR1 = ff_zero();
+  if (A.mode == MODE_FULL) {
+    // ------------------------------------------------------------ dichotomy tree (a2)
+    const ffv a0 = act0 ? O::bc(tab, r0, BC_A) : ff_one(), pb0 = act0 ? O::mul(O::bc(tab, r0, BC_B), bR0) : ff_zero();
+    const ffv a1 = act1 ? O::bc(tab, r1, BC_A) : ff_one(), pb1 = act1 ? O::mul(O::bc(tab, r1, BC_B), bR1) : ff_zero();
+    const ffv c0 = act0 ? O::bc(tab, r0, BC_C) : ff_one(), qb0 = act0 ? O::mul(O::bc(tab, r0, BC_D), bL0) : ff_zero();
+    const ffv c1 = act1 ? O::bc(tab, r1, BC_C) : ff_one(), qb1 = act1 ? O::mul(O::bc(tab, r1, BC_D), bL1) : ff_zero();
+    // the thread's composite maps: prefix = block 1 after block 0; suffix = block 0 after block 1
+    ffv pa = O::mul(a1, a0), pb = O::fma(a1, pb0, pb1);
+    ffv qa = O::mul(c0, c1), qb = O::fma(c0, qb1, qb0);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const ffv ya = O::up(pa, d), yb = O::up(pb, d);
+      const ffv za = O::down(qa, d), zb = O::down(qb, d);
+      if (lane >= d) {
+        pb = O::fma(pa, yb, pb);
+        pa = O::mul(pa, ya);
+      }
+      if (lane + d < 32) {
+        qb = O::fma(qa, zb, qb);
+        qa = O::mul(qa, za);
+      }
+    }
+    if (lane == 31) {
+      swv[wid] = pa;
+      swv[NW + wid] = pb;
+    }
+    if (lane == 0) {
+      swv[2 * NW + wid] = qa;
+      swv[3 * NW + wid] = qb;
+    }
+    ffv ea = O::up(pa, 1), eb = O::up(pb, 1);
+    ffv fa = O::down(qa, 1), fb = O::down(qb, 1);
+    if (lane == 0) {
+      ea = ff_one();
+      eb = ff_zero();
+    }
+    if (lane == 31) {
+      fa = ff_one();
+      fb = ff_zero();
+    }
+    __syncthreads();
+    ffv Aw = ff_zero(), Bw = ff_zero();  // zero coupling enters at both window ends
+    for (int w = 0; w < wid; ++w) Aw = O::fma(swv[w], Aw, swv[NW + w]);
+    for (int w = NW - 1; w > wid; --w) Bw = O::fma(swv[2 * NW + w], Bw, swv[3 * NW + w]);
+    const ffv A0 = O::fma(ea, Aw, eb);                       // entering block 0
+    const ffv A1 = O::fma(a0, A0, pb0);                      // entering block 1
+    const ffv B1 = O::fma(fa, Bw, fb);                       // beyond block 1
+    const ffv B0 = O::fma(c1, B1, qb1);                      // beyond block 0
+    if (act0) {
+      sxs[b0] = O::add(O::fma(O::bc(tab, r0, BC_TL), B0, bL0), A0);
+      sxe[b0] = O::fma(O::bc(tab, r0, BC_TR), A0, O::add(bR0, B0));
+    }
+    if (act1) {
+      sxs[b1] = O::add(O::fma(O::bc(tab, r1, BC_TL), B1, bL1), A1);
+      sxe[b1] = O::fma(O::bc(tab, r1, BC_TR), A1, O::add(bR1, B1));
+    }
+    __syncthreads();
+    if (act0) {
+      if (!(mb0 == 0 || b0 == 0)) XL0 = sxe[b0 - 1];
+      if (!(mb0 == P - 1 || b0 + 1 >= nwin)) XR0 = sxs[b0 + 1];
+    }
+    if (act1) {
+      XL1 = sxe[b0];
+      if (!(mb1 == P - 1 || b1 + 1 >= nwin)) XR1 = sxs[b1 + 1];
+    }
+  } else {  // MODE_APPLY: neighbours' first/last values from the global scan (unscaled FP64)
+    const double upw = pow2i(wscale);
+    auto to_ff = [&](double d) {
+      const float2 t = f64_to_ff_rn(d * upw);
+      return ffv{t.x, t.y};
+    };
+    if (act0) {
+      if (mb0 > 0) XL0 = to_ff(A.iface[2 * (mb0 - 1) + 1]);
+      if (mb0 < P - 1) XR0 = to_ff(A.iface[2 * (mb0 + 1)]);
+    }
+    if (act1) {
+      if (mb1 > 0) XL1 = to_ff(A.iface[2 * (mb1 - 1) + 1]);
+      if (mb1 < P - 1) XR1 = to_ff(A.iface[2 * (mb1 + 1)]);
+    }
+  }
+
+  // ---------------------------------------------------------------- correction (a3), per column
+  const ffv cL0 = ff_sub(XL0, xm0), cL1 = ff_sub(XL1, xm1);
+  if (full)
+    correct_pair<LD, false>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL0, cL1, XR0,
+                            XR1, wscale);
+  else if (nrow > 0)
+    correct_pair<LD, true>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL0, cL1, XR0,
+                           XR1, wscale);
+  __syncthreads();
+
+  // ---------------------------------------------------------------- coalesced store of the own rows
+  const bool adj = (A.xf != nullptr);
+  double g0 = 0.0, gm = 0.0, gp = 0.0;
+  unsigned bad = 0u;
+  const int64_t N = pp->N;
+  {
+    const int jlo = hl * n;
+    const int jhi = min(len, (hl + nown) * n);
+    double* dst = A.x + off + row_lo;
+    int b = (jlo + tid) / n, i = (jlo + tid) - ((jlo + tid) / n) * n;
+    const int db = NT / n, di = NT - (NT / n) * n;
+    for (int j = jlo + tid; j < jhi; j += NT) {
+      const double dv = S[(size_t)i * LD + b];
+      __stcs(dst + j, dv);
+      if (A.check_finite && !isfinite(dv)) bad = 1u;
+      if (adj) {
+        const int64_t r = row_lo + j;
+        const double* xr = A.xf + off + r;
+        g0 = fma(dv, xr[0], g0);
+        if (r > 0) gm = fma(dv, xr[-1], gm);
+        if (r + 1 < N) gp = fma(dv, xr[1], gp);
+      }
+      i += di;
+      b += db;
+      if (i >= n) {
+        i -= n;
+        ++b;
+      }
+    }
+  }
+  if (bad) atomicOr(A.status, (unsigned)ST_NONFINITE);
+  if (adj) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      g0 += __shfl_down_sync(0xffffffffu, g0, d);
+      gm += __shfl_down_sync(0xffffffffu, gm, d);
+      gp += __shfl_down_sync(0xffffffffu, gp, d);
+    }
+    double* sred = reinterpret_cast<double*>(swv);
+    __syncthreads();
+    if (lane == 0) {
+      sred[wid] = gm;
+      sred[NW + wid] = g0;
+      sred[2 * NW + wid] = gp;
+    }
+    __syncthreads();
+    if (tid < 3) {
+      double s = 0.0;
+      for (int w = 0; w < NW; ++w) s += sred[tid * NW + w];
+      A.part[3 * (size_t)blockIdx.x + tid] = s;
+    }
+  }
+}
+
+}  // namespace dich
