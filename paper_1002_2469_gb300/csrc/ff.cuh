@@ -296,6 +296,21 @@ __device__ __forceinline__ void ff_fma_acc2(float2 ch, float2 cl, float2 vh, flo
   xh = s;
 }
 
+// rare paths kept out of line so that their FP64 operations are not if-converted into the
+// per-element code (GB300's FP64 pipe is ~70x slower than FP32)
+__device__ __noinline__ double rescale_subnormal(double d) { return d * 18446744073709551616.0; }  // * 2^64
+__device__ __noinline__ double join_rare(float s1, float e1, int s) {
+  const unsigned b1 = __float_as_uint(s1);
+  const unsigned sg = b1 & 0x80000000u;
+  const int E1 = (int)((b1 >> 23) & 0xFFu);
+  const unsigned f1 = b1 & 0x7FFFFFu;
+  if (E1 == 0) return __hiloint2double((int)sg, 0);
+  if (E1 == 255 || E1 + 896 - s >= 2047)
+    return __hiloint2double((int)(sg | 0x7FF00000u | (E1 == 255 && f1 ? 0x80000u : 0u)), 0);
+  const double sc = __hiloint2double((1023 - s) << 20, 0);
+  return (double)s1 * sc + (double)e1 * sc;   // the FP64 unit rounds into the subnormal range
+}
+
 // FP64 -> (hi, lo) floats of d * 2^s with integer operations; `sb` = s - 896 is precomputed.
 // hi = leading 24 bits (truncated), lo = next 23 bits (truncated); values whose scaled
 // exponent falls outside the float range flush to zero (hi) / drop lo, exponents of
@@ -304,7 +319,7 @@ __device__ __forceinline__ void split_sc(double d, int s, float& hi, float& lo) 
   unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
   int sb = s - 896;
   if ((hw & 0x7FF00000u) == 0u && ((hw & 0x000FFFFFu) | lw) != 0u) {   // FP64 subnormal
-    const double d2 = d * 18446744073709551616.0;                      // * 2^64, exact
+    const double d2 = rescale_subnormal(d);                            // * 2^64, exact
     hw = (unsigned)__double2hiint(d2);
     lw = (unsigned)__double2loint(d2);
     sb -= 64;
@@ -350,11 +365,7 @@ __device__ __forceinline__ double join_sc(float h, float l, int s) {
   // 64-bit add of the signed count to (hi:lo), magnitude direction (sign bit untouched)
   asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, %3;" : "+r"(lo), "+r"(hi) : "r"((unsigned)Ks),
       "r"((unsigned)(Ks >> 31)));
-  if ((unsigned)(Ed - 1) >= 2046u || E1 == 0 || E1 == 255) {   // rare: zero, Inf/NaN, out of range
-    if (E1 == 0) return __hiloint2double((int)sg, 0);
-    if (E1 == 255 || Ed >= 2047) return __hiloint2double((int)(sg | 0x7FF00000u | (E1 == 255 && f1 ? 0x80000u : 0u)), 0);
-    return (double)s1 * __hiloint2double((1023 - s) << 20, 0) + (double)e1 * __hiloint2double((1023 - s) << 20, 0);
-  }
+  if ((unsigned)(Ed - 1) >= 2046u || (unsigned)(E1 - 1) >= 254u) return join_rare(s1, e1, s);
   return __hiloint2double((int)hi, (int)lo);
 }
 

@@ -22,7 +22,7 @@ namespace dich {
 __host__ __device__ inline size_t window2_smem_bytes(int NT, int n_smem) {
   const size_t nw = (size_t)(NT / 32);
   const size_t LD = 2 * (size_t)NT + 2;
-  return sizeof(double) * ((size_t)n_smem * LD + 4 * (size_t)n_smem + 8 * (size_t)NT + 4 * nw + 8);
+  return sizeof(double) * ((size_t)n_smem * LD + 4 * (size_t)n_smem + 4 * (size_t)NT + 4 * nw + 8);
 }
 
 // forward and backward sweeps of a thread's pair of blocks, in place.  GUARD: the two blocks
@@ -34,6 +34,7 @@ __device__ __forceinline__ void sweep_pair(double* S, int tid, int nrow, int nb0
   const float2 rh = f2(pp->rs_h), rl = f2(pp->rs_l), bh = f2(pp->ib_h), bl = f2(pp->ib_l);
   const float2 gh = f2(pp->g_h), gl = f2(pp->g_l);
   float2 uh = f2(0.f), ul = f2(0.f);
+#pragma unroll 4
   for (int i = 0; i < nrow; ++i) {
     double* row = S + (size_t)i * LD + 2 * tid;
     const double2 fd = *reinterpret_cast<const double2*>(row);
@@ -48,6 +49,7 @@ __device__ __forceinline__ void sweep_pair(double* S, int tid, int nrow, int nb0
     *reinterpret_cast<float4*>(row) = make_float4(uh.x, uh.y, ul.x, ul.y);
   }
   float2 xh = f2(0.f), xl = f2(0.f);
+#pragma unroll 4
   for (int i = nrow - 1; i >= 0; --i) {
     double* row = S + (size_t)i * LD + 2 * tid;
     float4 q = *reinterpret_cast<const float4*>(row);
@@ -74,6 +76,7 @@ __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow, int n
   const float2 crh = make_float2(cR0.h, cR1.h), crl = make_float2(cR0.l, cR1.l);
   if (!GUARD) {
     // both blocks full size: one spike table, one row index for both
+#pragma unroll 4
     for (int i = 0; i < nrow; ++i) {
       double* row = S + (size_t)i * LD + 2 * tid;
       const float4 q = *reinterpret_cast<const float4*>(row);
@@ -144,7 +147,6 @@ __global__ void __launch_bounds__(NT) k_window2(const WinArgs A) {
   ffv* sxs = reinterpret_cast<ffv*>(twl + ns);
   ffv* sxe = sxs + WB;
   ffv* swv = sxe + WB;  // 4 * NW scan scratch (also the exponent maxima)
-  // (4 NT doubles of the budget reserved after swv are unused here; keeps the size formula simple)
 
   // ---------------------------------------------------------------- the window
   int sys;
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(NT) k_window2(const WinArgs A) {
     for (int j = jlo + tid; j < jhi; j += NT) {
       const double dv = S[(size_t)i * LD + b];
       __stcs(dst + j, dv);
-      if (A.check_finite && !isfinite(dv)) bad = 1u;
+      if (A.check_finite && ((__double2hiint(dv) >> 20) & 0x7FF) == 0x7FF) bad = 1u;
       if (adj) {
         const int64_t r = row_lo + j;
         const double* xr = A.xf + off + r;
