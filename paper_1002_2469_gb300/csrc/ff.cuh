@@ -298,8 +298,8 @@ __device__ __forceinline__ void ff_fma_acc2(float2 ch, float2 cl, float2 vh, flo
 
 // rare paths kept out of line so that their FP64 operations are not if-converted into the
 // per-element code (GB300's FP64 pipe is ~70x slower than FP32)
-__device__ __noinline__ double rescale_subnormal(double d) { return d * 18446744073709551616.0; }  // * 2^64
-__device__ __noinline__ double join_rare(float s1, float e1, int s) {
+static __device__ __noinline__ double rescale_subnormal(double d) { return d * 18446744073709551616.0; }  // * 2^64
+static __device__ __noinline__ double join_rare(float s1, float e1, int s) {
   const unsigned b1 = __float_as_uint(s1);
   const unsigned sg = b1 & 0x80000000u;
   const int E1 = (int)((b1 >> 23) & 0xFFu);
