@@ -142,6 +142,24 @@ int dichotomy_status(dich_plan_t plan, void* stream, int* device_status);
 
 void dichotomy_destroy(dich_plan_t plan);
 
+/* x = T^-1 F for one system without any allocation by the library.  The paper has no
+ * counterpart: this serves callers that cannot allocate device memory themselves (for
+ * example code running under a framework whose allocator owns the device, or plugins
+ * forbidden to call cudaMalloc).  It plans on the host into a static buffer and keeps the
+ * plan on the device in one library-owned static array of 256 KiB per GPU, held until the
+ * process exits; no cudaMalloc, cudaFree or other allocating routine is called.
+ * d_F, d_x: N doubles on the device, no aliasing.  Precision policy DICH_PREC_AUTO.
+ * Limit: the plan tables (and, for systems on the general path, 32 bytes per block of beta
+ * and first/last values plus the block-scan scratch) must fit the array; larger needs --
+ * long systems whose coupling does not decay, such as the 1-D Laplacian -- return
+ * DICH_ERR_WORKSPACE (use dichotomy_plan + dichotomy_solve with a caller workspace).
+ * Every call reuses the same array (its status word is cleared on each call): calls whose
+ * kernels overlap on the GPU (other streams, other host threads) race; calls on one stream
+ * are ordered.  The first call on a device looks up the array's device address; make it
+ * before any stream capture. */
+int dichotomy_solve_noalloc(double t_m1, double t_0, double t_1, int64_t N, const double* d_F, double* d_x,
+                            void* stream);
+
 /* ---------------------------------------------------------------- batches */
 
 /* A series of independent systems (the paper's eq. 2 series, or separation-of-variables

@@ -28,6 +28,7 @@ FLAG_FORCE_GENERAL, FLAG_CHECK_FINITE = 1, 2
 EXPORTS = [
     "dichotomy_plan", "dichotomy_plan_ex", "dichotomy_plan_info", "dichotomy_plan_workspace_bytes",
     "dichotomy_plan_bind", "dichotomy_solve", "dichotomy_adjoint", "dichotomy_status", "dichotomy_destroy",
+    "dichotomy_solve_noalloc",
     "dichotomy_batch_prepare", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
     "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
     "dichotomy_batch_destroy", "dichotomy_strerror", "dichotomy_last_cuda_error", "dichotomy_version",
@@ -90,6 +91,7 @@ def load(build_if_missing: bool = True):
             "dichotomy_adjoint": ([P, P, P, P, P, P], I),
             "dichotomy_status": ([P, P, ctypes.POINTER(I)], I),
             "dichotomy_destroy": ([P], None),
+            "dichotomy_solve_noalloc": ([c_double, c_double, c_double, c_int64, P, P, P], I),
             "dichotomy_batch_prepare": ([c_int64, P, P, P, P, P, ctypes.POINTER(dich_opts), ctypes.POINTER(P)], I),
             "dichotomy_batch_workspace_bytes": ([P, ctypes.POINTER(c_size_t)], I),
             "dichotomy_batch_bind": ([P, P, c_size_t, P], I),

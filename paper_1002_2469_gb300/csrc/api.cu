@@ -17,10 +17,13 @@
 
 #include "../../include/dichotomy.h"
 #include "launch.cuh"
+#include "planner.cuh"
 
 using namespace dich;
+using namespace dich::plan;
 
-namespace {
+namespace dich {
+namespace plan {
 
 thread_local std::string g_cuda_err;
 
@@ -29,14 +32,7 @@ int cuda_fail(cudaError_t e) {
   return DICH_ERR_CUDA;
 }
 
-constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
-
-// shared-memory budget per CTA so that two CTAs share an SM (load of one window overlaps the
-// compute of the other)
-constexpr size_t kSmemBudget = 110 * 1024;
-// an explicitly requested block size may use up to the per-CTA maximum (one CTA per SM)
-constexpr size_t kSmemMax = 225 * 1024;
 
 // window width in blocks: the MIXED kernel gives every thread two blocks
 int window_blocks(int NT, int form) { return form == FORM_MIXED ? 2 * NT : NT; }
@@ -66,14 +62,6 @@ int validate_t(double tm1, double t0, double tp1) {
   if (std::fabs(t0) < off * (1.0 - 4.0 * DBL_EPSILON)) return DICH_ERR_NOT_DOMINANT;
   return DICH_OK;
 }
-
-struct Opts {
-  int n_req = 0;
-  int prec = DICH_PREC_F64;
-  int NT = 0;
-  int flags = 0;
-  double eps = 0x1p-64;
-};
 
 int read_opts(const dich_opts* o, Opts& out) {
   out = Opts();
@@ -111,13 +99,6 @@ void split_ff(double d, float& h, float& l) {
   h = (float)d;
   l = (float)(d - (double)h);
 }
-
-// Host construction of one system's plan record and tables.
-struct SysBuild {
-  SysPlan rec{};
-  std::vector<double> tab;
-  int path = PATH_SINGLE;
-};
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -261,8 +242,16 @@ int build_system(double tm1, double t0, double tp1, int64_t N, int NT, int form,
   split_ff(p.vend, p.vend_h, p.vend_l);
   split_ff(p.v0l, p.v0l_h, p.v0l_l);
   split_ff(p.vendl, p.vendl_h, p.vendl_l);
-  sb.tab.assign((size_t)o_, 0.0);
-  double* T = sb.tab.data();
+  double* T;
+  if (sb.ext) {  // caller-provided table storage (no allocation)
+    if ((size_t)o_ > sb.ext_cap) return DICH_ERR_WORKSPACE;
+    std::memset(sb.ext, 0, sizeof(double) * (size_t)o_);
+    T = sb.ext;
+    sb.ext_used = (size_t)o_;
+  } else {
+    sb.tab.assign((size_t)o_, 0.0);
+    T = sb.tab.data();
+  }
   auto put_ff = [&](int32_t at, double d) {
     float h, l;
     split_ff(d, h, l);
@@ -324,7 +313,8 @@ int map_status(unsigned s) {
   return DICH_OK;
 }
 
-}  // namespace
+}  // namespace plan
+}  // namespace dich
 
 // ================================================================== single-system plan
 struct dich_plan_s {
