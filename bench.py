@@ -213,6 +213,7 @@ def run_gpu(args):
     # clocks during a separate timed pass of the headline form, long enough (~1.5 s) for the
     # 200 ms nvidia-smi samples; its per-step time is reported beside the main one
     head = results["auto"]
+    f64 = results["fp64_plain"]
     clock_steps = max(args.steps, int(1500.0 / max(head["total_ms"] / args.steps, 1e-3)))
     with ClockSampler(torch.cuda.current_device()) as cs:
         total_ms2, per2 = time_solves(head["plan"], F, x, clock_steps, 2, world, stream)
@@ -246,6 +247,15 @@ def run_gpu(args):
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(F_h, t, budget_s=args.cpu_seconds)
 
+    # the batched configurations, timed the same way (device events, inputs resident)
+    others = {}
+    if not args.no_other_configs:
+        del F, x, Fd, xd, results
+        head.pop("x", None)
+        f64.pop("x", None)
+        torch.cuda.empty_cache()
+        others = other_configs(D, W, oracle, stream, world, steps=max(5, min(args.steps, 20)))
+
     if rank != 0:
         return
     peak, peak_kind = _peaks()
@@ -253,7 +263,6 @@ def run_gpu(args):
     value = world * N / (ms * 1e-3) / 1e9
     per_launch = statistics.median(head["per"])
     achieved = BYTES_PER_UNKNOWN * N / (per_launch * 1e-3) / 1e9
-    f64 = results["fp64_plain"]
     f64_ms = f64["total_ms"] / args.steps
     form = "mixed" if head["info"]["precision"] == 1 else "f64"
     kernel_key = f"k_window_{form}_NT{head['info']['threads']}_N{N}"
@@ -297,7 +306,97 @@ def run_gpu(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if others:
+        line["other_configs"] = others
     print(json.dumps(line), flush=True)
+
+
+def _time_batch(solve, steps, world, stream):
+    import torch
+    for _ in range(3):
+        solve()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        solve()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return max_over_ranks(e0.elapsed_time(e1), world) / steps
+
+
+def other_configs(D, W, oracle, stream, world, steps=10):
+    """C3 (2-D Poisson modes), C4 (uneven series), C5 (adjoint): ms and Gunknowns/s per form,
+    with the max relative error against the oracle on a sample of systems."""
+    import torch
+    out = {}
+    rng = np.random.default_rng(0)
+
+    def sample_err(xd, Fd, N, off, tm1, t0, tp1, k=24):
+        errs = []
+        for s_ in rng.choice(N.size, min(k, N.size), replace=False):
+            o, n = int(off[s_]), int(N[s_])
+            ref = oracle.thomas((tm1[s_], t0[s_], tp1[s_]), Fd[o:o + n].cpu().numpy())
+            errs.append(float(np.max(np.abs(xd[o:o + n].cpu().numpy() - ref)) / max(np.max(np.abs(ref)), 1e-300)))
+        return max(errs)
+
+    # C3: 4096 Poisson modes of N = 4096 (DST of a seeded smooth source)
+    tm1, t0, tp1, N, rhs = W.poisson_c3()
+    off = W.offsets(N)
+    Fd = torch.from_numpy(rhs.reshape(-1)).cuda()
+    xd = torch.empty_like(Fd)
+    c3 = {"unknowns": int(N.sum())}
+    for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
+        b = D.Batch(N, tm1, t0, tp1, precision=prec)
+        ms = _time_batch(lambda: b.solve(Fd, out=xd), steps, world, stream)
+        forms = b.info["form"]
+        c3[name] = {"ms": round(ms, 4), "Gunknowns_s": round(N.sum() / ms / 1e6, 2),
+                    "hbm_GBs": round(16 * N.sum() / ms / 1e6, 1), "mixed_systems": int(forms.sum()),
+                    "max_rel_err_sampled": sample_err(xd, Fd, N, off, tm1, t0, tp1)}
+    out["c3_poisson_4096x4096"] = c3
+    del Fd, xd
+
+    # C4: 10000 systems, N log-uniform in [256, 2^20]
+    N, off, tm1, t0, tp1, _ = W.uneven_c4(with_rhs=False)
+    Fd = W.device_uniform(int(N.sum()), W.SEED_RHS, "cuda")
+    xd = torch.empty_like(Fd)
+    c4 = {"unknowns": int(N.sum())}
+    for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
+        b = D.Batch(N, tm1, t0, tp1, precision=prec)
+        ms = _time_batch(lambda: b.solve(Fd, out=xd), max(3, steps // 2), world, stream)
+        c4[name] = {"ms": round(ms, 3), "Gunknowns_s": round(N.sum() / ms / 1e6, 2),
+                    "hbm_GBs": round(16 * N.sum() / ms / 1e6, 1), "windows": int(b.info["windows"]),
+                    "max_rel_err_sampled": sample_err(xd, Fd, N, off, tm1, t0, tp1)}
+    out["c4_uneven_10000"] = c4
+    del Fd, xd
+    torch.cuda.empty_cache()
+
+    # C5: forward + adjoint over 1024 systems of N = 65536
+    Ns, off, tm1, t0, tp1, _, _ = W.adjoint_c5(with_data=False)
+    Fd = W.device_uniform(int(Ns.sum()), W.SEED_RHS, "cuda")
+    wd = W.device_uniform(int(Ns.sum()), W.SEED_W, "cuda")
+    xd = torch.empty_like(Fd)
+    c5 = {"unknowns": int(Ns.sum())}
+    for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
+        b = D.Batch(Ns, tm1, t0, tp1, precision=prec)
+        gF = torch.empty_like(Fd)
+        gt = torch.empty((Ns.size, 3), dtype=torch.float64, device="cuda")
+
+        def step():
+            b.solve(Fd, out=xd)
+            D.dichotomy_adjoint_batched(b.handle, wd, xd, gF, gt)
+        ms = _time_batch(step, steps, world, stream)
+        s_ = 7
+        o, n = int(off[s_]), int(Ns[s_])
+        tt = (tm1[s_], t0[s_], tp1[s_])
+        lam, g = oracle.adjoint(tt, wd[o:o + n].cpu().numpy(), oracle.thomas(tt, Fd[o:o + n].cpu().numpy()))
+        c5[name] = {"ms_forward_plus_adjoint": round(ms, 4), "Gunknowns_s": round(Ns.sum() / ms / 1e6, 2),
+                    "rel_err_gF_sys7": float(np.max(np.abs(gF[o:o + n].cpu().numpy() - lam)) / np.max(np.abs(lam))),
+                    "rel_err_gt_sys7": float(np.max(np.abs(gt[s_].cpu().numpy() - g)) / np.max(np.abs(g)))}
+    out["c5_adjoint_1024x65536"] = c5
+    return out
 
 
 def cpu_baseline(F_h, t, budget_s=15.0):
@@ -358,6 +457,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
