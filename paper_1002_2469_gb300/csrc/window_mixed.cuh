@@ -76,7 +76,7 @@ __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow, int n
   const float2 crh = make_float2(cR0.h, cR1.h), crl = make_float2(cR0.l, cR1.l);
   if (!GUARD) {
     // both blocks full size: one spike table, one row index for both
-#pragma unroll 4
+#pragma unroll 2
     for (int i = 0; i < nrow; ++i) {
       double* row = S + (size_t)i * LD + 2 * tid;
       const float4 q = *reinterpret_cast<const float4*>(row);
@@ -90,7 +90,7 @@ __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow, int n
         const float2 w = tw[j];
         ff_fma_acc2(crh, crl, f2(w.x), f2(w.y), xh, xl);
       }
-      *reinterpret_cast<double2*>(row) = make_double2(join_sc(xh.x, xl.x, wscale), join_sc(xh.y, xl.y, wscale));
+      *reinterpret_cast<double2*>(row) = make_double2(join_dadd(xh.x, xl.x, wscale), join_dadd(xh.y, xl.y, wscale));
     }
   } else {
     const int lv0 = last0 ? nlast : Lv, lw0 = last0 ? nlast : Lw;
@@ -123,8 +123,8 @@ __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow, int n
       }
       ff_fma_acc2(clh, cll, vh, vl, xh, xl);
       ff_fma_acc2(crh, crl, wh, wl, xh, xl);
-      double d0 = (i < nb0) ? join_sc(xh.x, xl.x, wscale) : 0.0;
-      double d1 = (i < nb1) ? join_sc(xh.y, xl.y, wscale) : 0.0;
+      double d0 = (i < nb0) ? join_dadd(xh.x, xl.x, wscale) : 0.0;
+      double d1 = (i < nb1) ? join_dadd(xh.y, xl.y, wscale) : 0.0;
       *reinterpret_cast<double2*>(row) = make_double2(d0, d1);
     }
   }
