@@ -48,11 +48,11 @@ int max_rows(int NT, int form, size_t budget) {
   return n;
 }
 
-int default_threads(int form) { return form == FORM_F64 ? 64 : 64; }
+int default_threads(int form) { return form == FORM_F64 ? 64 : 128; }
 
 // rows per block for multi-window systems (measured on GB300 at N = 2^26: small windows let
 // several CTAs share an SM so loads, sweeps, tree and stores of different windows overlap)
-int default_rows(int form) { return form == FORM_F64 ? 64 : 32; }
+int default_rows(int form) { return form == FORM_F64 ? 64 : 16; }
 
 int validate_t(double tm1, double t0, double tp1) {
   if (!std::isfinite(tm1) || !std::isfinite(t0) || !std::isfinite(tp1)) return DICH_ERR_ARG;

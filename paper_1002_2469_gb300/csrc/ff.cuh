@@ -369,34 +369,28 @@ __device__ __forceinline__ double join_sc(float h, float l, int s) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
-// float * 2^-s -> double bits for the join: exact; zero/out-of-range give +-0 (used for the
-// low part, whose range is never critical)
-__device__ __forceinline__ double f32_to_f64_flush(float f, int s) {
-  const unsigned b = __float_as_uint(f);
-  const int e = (int)((b >> 23) & 0xFFu);
-  const int ed = e + 896 - s;
-  const unsigned m = b & 0x7FFFFFu;
-  const bool ok = ((unsigned)(ed - 1) < 2046u) && ((unsigned)(e - 1) < 254u);
-  const unsigned hi = (b & 0x80000000u) | (ok ? (((unsigned)ed << 20) | (m >> 3)) : 0u);
-  const unsigned lo = ok ? (m << 29) : 0u;
-  return __hiloint2double((int)hi, (int)lo);
-}
-
 // (h, l) * 2^-s -> FP64 with both parts converted exactly by integer operations and one FP64
 // addition (the FP64 pipe does one operation per element; the integer-only join_sc needs about
-// twice the issue slots).  Out-of-range leading parts take the out-of-line path.
+// twice the issue slots).  Anything outside the plain case -- a zero or subnormal leading part,
+// a part whose unscaled exponent leaves the FP64 normal range, Inf/NaN -- takes the
+// out-of-line FP64 path, which rounds into the subnormal range correctly.
+static __device__ __noinline__ double join_slow(float h, float l, int s) {
+  const double sc = __hiloint2double((1023 - s) << 20, 0);
+  return (double)h * sc + (double)l * sc;
+}
 __device__ __forceinline__ double join_dadd(float h, float l, int s) {
-  const unsigned b = __float_as_uint(h);
-  const int e = (int)((b >> 23) & 0xFFu);
-  const int ed = e + 896 - s;
-  if ((unsigned)(ed - 1) >= 2046u || (unsigned)(e - 1) >= 254u) {
-    if (e == 0) return f32_to_f64_flush(l, s);       // h == 0 (or float subnormal): the value is l
-    const float s1 = __fadd_rn(h, l);
-    return join_rare(s1, __fsub_rn(l, __fsub_rn(s1, h)), s);
-  }
-  const unsigned m = b & 0x7FFFFFu;
-  const double hd = __hiloint2double((int)((b & 0x80000000u) | ((unsigned)ed << 20) | (m >> 3)), (int)(m << 29));
-  return __dadd_rn(hd, f32_to_f64_flush(l, s));
+  const unsigned bh = __float_as_uint(h), bl = __float_as_uint(l);
+  const int eh = (int)((bh >> 23) & 0xFFu), el = (int)((bl >> 23) & 0xFFu);
+  const int edh = eh + 896 - s, edl = el + 896 - s;
+  const bool okh = ((unsigned)(edh - 1) < 2046u) && ((unsigned)(eh - 1) < 254u);
+  const bool okl = (el == 0) || (((unsigned)(edl - 1) < 2046u) && (el != 255));
+  if (!(okh && okl)) return join_slow(h, l, s);
+  const unsigned mh = bh & 0x7FFFFFu, ml = bl & 0x7FFFFFu;
+  const double hd = __hiloint2double((int)((bh & 0x80000000u) | ((unsigned)edh << 20) | (mh >> 3)), (int)(mh << 29));
+  const double ld = (el == 0) ? 0.0
+                              : __hiloint2double((int)((bl & 0x80000000u) | ((unsigned)edl << 20) | (ml >> 3)),
+                                                 (int)(ml << 29));
+  return __dadd_rn(hd, ld);
 }
 
 }  // namespace dich
