@@ -334,11 +334,15 @@ def other_configs(D, W, oracle, stream, world, steps=10):
     out = {}
     rng = np.random.default_rng(0)
 
-    def sample_err(xd, Fd, N, off, tm1, t0, tp1, k=24):
+    def sample_err(xd, Fd, N, off, tm1, t0, tp1, k=24, exact=False):
+        """Largest norm-wise relative error over k sampled systems, against the oracle's FP64
+        Thomas, or (exact=True) against its binary128 Thomas, for systems so ill-conditioned
+        that the FP64 oracle's own error approaches the tolerance."""
         errs = []
+        solve = oracle.thomas_q if exact else oracle.thomas
         for s_ in rng.choice(N.size, min(k, N.size), replace=False):
             o, n = int(off[s_]), int(N[s_])
-            ref = oracle.thomas((tm1[s_], t0[s_], tp1[s_]), Fd[o:o + n].cpu().numpy())
+            ref = solve((tm1[s_], t0[s_], tp1[s_]), Fd[o:o + n].cpu().numpy())
             errs.append(float(np.max(np.abs(xd[o:o + n].cpu().numpy() - ref)) / max(np.max(np.abs(ref)), 1e-300)))
         return max(errs)
 
@@ -354,7 +358,7 @@ def other_configs(D, W, oracle, stream, world, steps=10):
         forms = b.info["form"]
         c3[name] = {"ms": round(ms, 4), "Gunknowns_s": round(N.sum() / ms / 1e6, 2),
                     "hbm_GBs": round(16 * N.sum() / ms / 1e6, 1), "mixed_systems": int(forms.sum()),
-                    "max_rel_err_sampled": sample_err(xd, Fd, N, off, tm1, t0, tp1)}
+                    "max_rel_err_sampled_vs_binary128": sample_err(xd, Fd, N, off, tm1, t0, tp1, exact=True)}
     out["c3_poisson_4096x4096"] = c3
     del Fd, xd
 

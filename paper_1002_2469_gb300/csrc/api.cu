@@ -611,7 +611,7 @@ void dichotomy_destroy(dich_plan_t p) { delete p; }
 struct dich_batch_s {
   int64_t nsys = 0;
   Opts opts;
-  int NT = 128;
+  int NT[2] = {64, 128};                  // window width per form
   std::vector<SysBuild> fwd, adj;          // per system (N >= 2); empty records for N < 2
   std::vector<int32_t> form;               // per system
   std::vector<int32_t> trivial;            // systems with N == 1
@@ -642,7 +642,7 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
   if (!b) return DICH_ERR_ARG;
   b->nsys = nsys;
   b->opts = o;
-  b->NT = o.NT ? o.NT : 64;
+  for (int f = 0; f < 2; ++f) b->NT[f] = o.NT ? o.NT : default_threads(f);
   b->fwd.resize((size_t)nsys);
   b->adj.resize((size_t)nsys);
   b->form.assign((size_t)nsys, FORM_F64);
@@ -668,12 +668,13 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
       if (h_N[s] == 1) b->trivial.push_back((int32_t)s);
       continue;
     }
-    const int nmax = max_rows(b->NT, b->form[s], o.n_req > 0 ? kSmemMax : kSmemBudget);
-    const int n = choose_n(h_N[s], window_blocks(b->NT, b->form[s]), nmax, o.n_req, default_rows(b->form[s]));
+    const int NTs = b->NT[b->form[s]];
+    const int nmax = max_rows(NTs, b->form[s], o.n_req > 0 ? kSmemMax : kSmemBudget);
+    const int n = choose_n(h_N[s], window_blocks(NTs, b->form[s]), nmax, o.n_req, default_rows(b->form[s]));
     Opts oh = o;
     oh.flags &= ~DICH_FLAG_FORCE_GENERAL;
-    rc = build_system(h_tm1[s], h_t0[s], h_tp1[s], h_N[s], b->NT, b->form[s], n, oh, false, b->fwd[s]);
-    if (!rc) rc = build_system(h_tp1[s], h_t0[s], h_tm1[s], h_N[s], b->NT, b->form[s], n, oh, false, b->adj[s]);
+    rc = build_system(h_tm1[s], h_t0[s], h_tp1[s], h_N[s], NTs, b->form[s], n, oh, false, b->fwd[s]);
+    if (!rc) rc = build_system(h_tp1[s], h_t0[s], h_tm1[s], h_N[s], NTs, b->form[s], n, oh, false, b->adj[s]);
     if (rc) {
       delete b;
       return rc;
@@ -682,7 +683,7 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
     if (b->fwd[s].path == PATH_HALO || b->adj[s].path == PATH_HALO) {
       const int hl = std::max(b->fwd[s].rec.hl, b->adj[s].rec.hl);
       const int hr = std::max(b->fwd[s].rec.hr, b->adj[s].rec.hr);
-      const int WBs = window_blocks(b->NT, b->form[s]);
+      const int WBs = window_blocks(NTs, b->form[s]);
       if (hl + hr > WBs / 2) {
         delete b;
         return DICH_ERR_UNSUPPORTED;
@@ -815,9 +816,9 @@ static int batch_launch(dich_batch_t b, const double* F, double* x, const double
     a.check_finite = (b->opts.flags & DICH_FLAG_CHECK_FINITE) ? 1 : 0;
     a.n_smem = b->n_smem[f];
     a.sys_offset = sys_offset;
-    const size_t smem = smem_bytes(b->NT, a.n_smem, f);
-    cudaError_t e = (f == FORM_F64) ? launch_window_f64(b->NT, (int)nitems, smem, st, a)
-                                    : launch_window_mixed(b->NT, (int)nitems, smem, st, a);
+    const size_t smem = smem_bytes(b->NT[f], a.n_smem, f);
+    cudaError_t e = (f == FORM_F64) ? launch_window_f64(b->NT[f], (int)nitems, smem, st, a)
+                                    : launch_window_mixed(b->NT[f], (int)nitems, smem, st, a);
     if (e != cudaSuccess) return cuda_fail(e);
     if (adjoint) {
       e = launch_adj_finalize(a.part, (const int32_t*)(b->d_ws + b->off_ids[f]),
