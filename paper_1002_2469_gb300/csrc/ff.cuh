@@ -27,174 +27,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// (yh, yl) ~= (fh + fl) + (rh + rl) * (xh + xl), rounding errors of the leading terms kept
-// exactly and accumulated in yl (unnormalised float-float).
-__device__ __forceinline__ void ff_axpy(float fh, float fl, float rh, float rl, float xh, float xl,
-                                        float& yh, float& yl) {
-  float p, pe, s, se;
-  two_prod(rh, xh, p, pe);
-  two_sum(fh, p, s, se);
-  float c = __fadd_rn(fl, __fadd_rn(pe, se));
-  c = __fmaf_rn(rl, xh, c);
-  c = __fmaf_rn(rh, xl, c);
-  yh = s;
-  yl = c;
-}
-
-// (yh, yl) ~= (gh + gl) * (xh + xl)
-__device__ __forceinline__ void ff_mul(float gh, float gl, float xh, float xl, float& yh, float& yl) {
-  float p, pe;
-  two_prod(gh, xh, p, pe);
-  float c = __fmaf_rn(gl, xh, pe);
-  c = __fmaf_rn(gh, xl, c);
-  yh = p;
-  yl = c;
-}
-
-// (xh, xl) += (ch + cl) * (vh + vl)
-__device__ __forceinline__ void ff_fma_acc(float ch, float cl, float vh, float vl, float& xh, float& xl) {
-  float p, pe, s, se;
-  two_prod(ch, vh, p, pe);
-  float pc = __fmaf_rn(cl, vh, __fmaf_rn(ch, vl, pe));
-  two_sum(xh, p, s, se);
-  xl = __fadd_rn(xl, __fadd_rn(pc, se));
-  xh = s;
-}
-
-// FP64 -> (hi, lo) by integer operations.  hi keeps the leading 24 significant bits
-// (truncated), lo the next 23 (truncated), so |d - hi - lo| < 2^-46 |d|.  Valid for
-// 2^-80 <= |d| < 2^127; below 2^-80 lo is dropped, below 2^-126 the value flushes to 0,
-// above 2^127 (and Inf/NaN) hi becomes Inf/NaN so the output is flagged non-finite.
-__device__ __forceinline__ float2 f64_to_ff(double d) {
-  const unsigned hw = (unsigned)__double2hiint(d);
-  const unsigned lw = (unsigned)__double2loint(d);
-  const unsigned sgn = hw & 0x80000000u;
-  const int E = (int)((hw >> 20) & 0x7FFu);
-  const unsigned m23 = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
-  const int ef = E - 896;
-  unsigned hib = sgn | ((unsigned)ef << 23) | m23;
-  if (ef < 1) hib = sgn;
-  if (ef > 254) hib = sgn | 0x7F800000u | ((E == 2047 && ((hw & 0xFFFFFu) | lw)) ? 0x400000u : 0u);
-  const unsigned r = lw & 0x1FFFFFFFu;
-  const float rf = __fsub_rn(__uint_as_float(0x4B000000u | (r >> 6)), 8388608.0f);
-  const int es = E - 942;
-  float lo = (es >= 1 && ef <= 254) ? __fmul_rn(rf, __uint_as_float((unsigned)es << 23)) : 0.0f;
-  lo = __uint_as_float(__float_as_uint(lo) | sgn);
-  return make_float2(__uint_as_float(hib), lo);
-}
-
-// Scaled split: the same as f64_to_ff for d * 2^s (s chosen per window so that the largest
-// |F| of the window sits near 2^16); exact in the scaling, no FP64 operation.
-__device__ __forceinline__ float2 f64_to_ff_sc(double d, int s) {
-  const unsigned hw0 = (unsigned)__double2hiint(d);
-  if (((hw0 >> 20) & 0x7FFu) == 0u && ((hw0 & 0x7FFFFFFFu) | (unsigned)__double2loint(d)) != 0u) {  // subnormal
-    d = d * 18446744073709551616.0;   // * 2^64, exact
-    s -= 64;
-  }
-  const unsigned hw = (unsigned)__double2hiint(d);
-  const unsigned lw = (unsigned)__double2loint(d);
-  const unsigned sgn = hw & 0x80000000u;
-  const int E0 = (int)((hw >> 20) & 0x7FFu);
-  const int E = E0 + s;
-  const unsigned m23 = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
-  const int ef = E - 896;
-  const bool special = (E0 == 2047);
-  unsigned hib = sgn | ((unsigned)ef << 23) | m23;
-  if (ef < 1 || E0 == 0) hib = sgn;
-  if (ef > 254 || special) hib = sgn | 0x7F800000u | ((special && ((hw & 0xFFFFFu) | lw)) ? 0x400000u : 0u);
-  const unsigned r = lw & 0x1FFFFFFFu;
-  const float rf = __fsub_rn(__uint_as_float(0x4B000000u | (r >> 6)), 8388608.0f);
-  const int es = E - 942;
-  float lo = (es >= 1 && ef <= 254 && E0 != 0 && !special) ? __fmul_rn(rf, __uint_as_float((unsigned)es << 23))
-                                                          : 0.0f;
-  lo = __uint_as_float(__float_as_uint(lo) | sgn);
-  return make_float2(__uint_as_float(hib), lo);
-}
-
-// exact float -> double by integer operations (denormal floats flush to signed zero)
-__device__ __forceinline__ double f32_to_f64_bits(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned s = b & 0x80000000u;
-  const unsigned e = (b >> 23) & 0xFFu;
-  const unsigned m = b & 0x7FFFFFu;
-  const unsigned ed = (e == 0u) ? 0u : ((e == 255u) ? 0x7FFu : e + 896u);
-  const unsigned md = (e == 0u) ? 0u : m;
-  const unsigned hi = s | (ed << 20) | (md >> 3);
-  const unsigned lo = md << 29;
-  return __hiloint2double((int)hi, (int)lo);
-}
-
-// float * 2^-s -> double by integer operations (the window scale removed exactly; results
-// below the FP64 normal range flush to signed zero)
-__device__ __forceinline__ double f32_to_f64_bits_sc(float f, int s) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned sg = b & 0x80000000u;
-  const int e = (int)((b >> 23) & 0xFFu);
-  const unsigned m = b & 0x7FFFFFu;
-  int ed = e + 896 - s;
-  unsigned md = m;
-  if (e == 255 || ed >= 2047) {
-    ed = 2047;
-    md = (e == 255) ? m : 0u;
-  }
-  if (e == 0 || ed <= 0) {
-    ed = 0;
-    md = 0u;
-  }
-  const unsigned hi = sg | ((unsigned)ed << 20) | (md >> 3);
-  const unsigned lo = md << 29;
-  return __hiloint2double((int)hi, (int)lo);
-}
-
-__device__ __forceinline__ double ff_to_f64_sc(float h, float l, int s) {
-  return __dadd_rn(f32_to_f64_bits_sc(h, s), f32_to_f64_bits_sc(l, s));
-}
-
-// (h, l) -> FP64: both parts converted exactly, one FP64 addition.
-__device__ __forceinline__ double ff_to_f64(float h, float l) {
-  return __dadd_rn(f32_to_f64_bits(h), f32_to_f64_bits(l));
-}
-
-// (h, l) * 2^-s -> FP64 with integer operations only (no FP64 pipe).  (h, l) is first
-// renormalised with TwoSum so |e| <= ulp(s1)/2; s1 gives the leading 24 bits of the double,
-// e is aligned to the double's last bit and added to the 53-bit significand as an integer
-// (bits of e below the double's ulp are truncated: error < 2 ulp of the result).
-__device__ __forceinline__ double ff_to_f64_int(float h, float l, int s) {
-  float s1, e1;
-  two_sum(h, l, s1, e1);
-  const unsigned b1 = __float_as_uint(s1);
-  const unsigned sg = b1 & 0x80000000u;
-  const int E1 = (int)((b1 >> 23) & 0xFFu);
-  if (E1 == 0) return __hiloint2double((int)sg, 0);                 // zero (or float denormal)
-  if (E1 == 255) return __hiloint2double((int)(sg | 0x7FF00000u | ((b1 & 0x7FFFFFu) ? 0x80000u : 0u)), 0);
-  unsigned long long M = (1ull << 52) | ((unsigned long long)(b1 & 0x7FFFFFu) << 29);
-  const unsigned be = __float_as_uint(e1);
-  const int Ee = (int)((be >> 23) & 0xFFu);
-  if (Ee != 0) {
-    const unsigned long long Me = (unsigned long long)((be & 0x7FFFFFu) | 0x800000u);
-    const int sh = Ee - E1 + 29;      // <= 5 because |e1| <= ulp(s1)/2
-    unsigned long long K = 0ull;
-    if (sh >= 0)
-      K = Me << sh;
-    else if (sh > -24)
-      K = Me >> (-sh);
-    M = ((be ^ b1) & 0x80000000u) ? M - K : M + K;
-  }
-  int Ed = E1 + 896 - s;
-  if (M < (1ull << 52)) {             // borrow from an exact power of two: renormalise
-    M <<= 1;
-    Ed -= 1;
-  }
-  if (Ed <= 0) {                      // below the normal range: FP64 subnormal (truncated)
-    const int sh = 1 - Ed;
-    M = (sh < 64) ? (M >> sh) : 0ull;
-    return __hiloint2double((int)(sg | ((unsigned)(M >> 32) & 0xFFFFFu)), (int)(unsigned)M);
-  }
-  if (Ed >= 2047) return __hiloint2double((int)(sg | 0x7FF00000u), 0);
-  const unsigned hi = sg | ((unsigned)Ed << 20) | ((unsigned)(M >> 32) & 0xFFFFFu);
-  return __hiloint2double((int)hi, (int)(unsigned)M);
-}
-
 // FP64 -> float-float with correct rounding of hi (FP64 pipe; used once per block only)
 __device__ __forceinline__ float2 f64_to_ff_rn(double d) {
   const float h = __double2float_rn(d);
@@ -248,7 +80,6 @@ __device__ __forceinline__ ffv ff_shfl_down(ffv a, int d) {
   return ffv{__shfl_down_sync(0xffffffffu, a.h, d), __shfl_down_sync(0xffffffffu, a.l, d)};
 }
 __device__ __forceinline__ double ff_to_double(ffv a) { return (double)a.h + (double)a.l; }
-__device__ __forceinline__ float2 ff_f2(ffv a) { return make_float2(a.h, a.l); }
 
 // ---------------------------------------------------------------- packed (two-chain) helpers
 // The MIXED window kernel advances two blocks per thread; both chains go through one
@@ -259,7 +90,9 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// two chains of ff_axpy: y = f + r * x with f, x, y as (hi pair, lo pair), r a float-float scalar
+// two chains of y ~= f + r * x, with f, x, y as (hi pair, lo pair) and r a float-float scalar:
+// the rounding errors of the leading product (FMA) and sum (TwoSum) are kept exactly and
+// accumulated, with the cross terms, in the unnormalised low part
 __device__ __forceinline__ void ff_axpy2(float2 fh, float2 fl, float2 rh, float2 rl, float2 xh, float2 xl,
                                          float2& yh, float2& yl) {
   const float2 p = mul2(rh, xh);
@@ -274,7 +107,7 @@ __device__ __forceinline__ void ff_axpy2(float2 fh, float2 fl, float2 rh, float2
   yl = c;
 }
 
-// two chains of ff_mul: y = g * x
+// two chains of y ~= g * x (error-free leading product plus cross terms)
 __device__ __forceinline__ void ff_mul2(float2 gh, float2 gl, float2 xh, float2 xl, float2& yh, float2& yl) {
   const float2 p = mul2(gh, xh);
   float2 c = fma2(gh, xh, make_float2(-p.x, -p.y));
@@ -299,19 +132,8 @@ __device__ __forceinline__ void ff_fma_acc2(float2 ch, float2 cl, float2 vh, flo
 // rare paths kept out of line so that their FP64 operations are not if-converted into the
 // per-element code (GB300's FP64 pipe is ~70x slower than FP32)
 static __device__ __noinline__ double rescale_subnormal(double d) { return d * 18446744073709551616.0; }  // * 2^64
-static __device__ __noinline__ double join_rare(float s1, float e1, int s) {
-  const unsigned b1 = __float_as_uint(s1);
-  const unsigned sg = b1 & 0x80000000u;
-  const int E1 = (int)((b1 >> 23) & 0xFFu);
-  const unsigned f1 = b1 & 0x7FFFFFu;
-  if (E1 == 0) return __hiloint2double((int)sg, 0);
-  if (E1 == 255 || E1 + 896 - s >= 2047)
-    return __hiloint2double((int)(sg | 0x7FF00000u | (E1 == 255 && f1 ? 0x80000u : 0u)), 0);
-  const double sc = __hiloint2double((1023 - s) << 20, 0);
-  return (double)s1 * sc + (double)e1 * sc;   // the FP64 unit rounds into the subnormal range
-}
 
-// FP64 -> (hi, lo) floats of d * 2^s with integer operations; `sb` = s - 896 is precomputed.
+// FP64 -> (hi, lo) floats of d * 2^s with integer operations.
 // hi = leading 24 bits (truncated), lo = next 23 bits (truncated); values whose scaled
 // exponent falls outside the float range flush to zero (hi) / drop lo, exponents of
 // Inf/NaN give Inf/NaN.  Subnormal FP64 inputs are rescaled exactly first (rare path).
@@ -341,43 +163,60 @@ __device__ __forceinline__ void split_sc(double d, int s, float& hi, float& lo) 
   lo = __uint_as_float(__float_as_uint(l) | sgn);
 }
 
-// (h, l) * 2^-s -> FP64 with 32-bit integer operations only.  FastTwoSum renormalises
-// (|e| <= ulp(s1)/2 when |l| <= |h|); e is turned into an integer count K of the double's
-// last place (bits below it truncated) and added to the 64-bit pattern of s1 with one
-// carry-propagating add.  Results below the FP64 normal range become subnormal or zero.
-__device__ __forceinline__ double join_sc(float h, float l, int s) {
-  const float s1 = __fadd_rn(h, l);
-  const float e1 = __fsub_rn(l, __fsub_rn(s1, h));
-  const unsigned b1 = __float_as_uint(s1), be = __float_as_uint(e1);
-  const unsigned sg = b1 & 0x80000000u;
-  const int E1 = (int)((b1 >> 23) & 0xFFu);
-  const unsigned f1 = b1 & 0x7FFFFFu;
-  const int Ed = E1 + 896 - s;
-  const int Ee = (int)((be >> 23) & 0xFFu);
-  const unsigned Me = (be & 0x7FFFFFu) | 0x800000u;
-  const int sh = Ee - E1 + 29;                 // <= 5
-  unsigned K = (sh >= 0) ? (Me << sh) : ((sh > -32) ? (Me >> (-sh)) : 0u);
-  if (Ee == 0) K = 0u;
-  if (f1 == 0u && ((be ^ b1) & 0x80000000u)) K <<= 1;   // below an exact power of two
-  const int Ks = ((be ^ b1) & 0x80000000u) ? -(int)K : (int)K;
-  unsigned lo = f1 << 29;
-  unsigned hi = sg | ((unsigned)Ed << 20) | (f1 >> 3);
-  // 64-bit add of the signed count to (hi:lo), magnitude direction (sign bit untouched)
-  asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, %3;" : "+r"(lo), "+r"(hi) : "r"((unsigned)Ks),
-      "r"((unsigned)(Ks >> 31)));
-  if ((unsigned)(Ed - 1) >= 2046u || (unsigned)(E1 - 1) >= 254u) return join_rare(s1, e1, s);
-  return __hiloint2double((int)hi, (int)lo);
-}
-
-// (h, l) * 2^-s -> FP64 with both parts converted exactly by integer operations and one FP64
-// addition (the FP64 pipe does one operation per element; the integer-only join_sc needs about
-// twice the issue slots).  Anything outside the plain case -- a zero or subnormal leading part,
-// a part whose unscaled exponent leaves the FP64 normal range, Inf/NaN -- takes the
-// out-of-line FP64 path, which rounds into the subnormal range correctly.
+// exact (h, l) * 2^-s on the FP64 pipe, out of line (rare cases of the joins below); the FP64
+// unit rounds into the subnormal range correctly
 static __device__ __noinline__ double join_slow(float h, float l, int s) {
   const double sc = __hiloint2double((1023 - s) << 20, 0);
   return (double)h * sc + (double)l * sc;
 }
+
+// ---------------------------------------------------------------- fast windows
+// A window is "fast" when every |F| of it is a normal FP64 number whose exponent lies within
+// 119 of the window's largest (emax) and emax is in [239, 1935] (the window scale is then
+// s = 1039 - emax, inside [-896, 800]).  In such a window the split and the join below need
+// no range handling: every scaled float exponent and every rebuilt FP64 exponent is in range.
+
+// constants of a fast window with scale s
+struct FastK {
+  unsigned split;   // added to the funnel-shifted FP64 bits: float exponent of hi, minus 23
+  unsigned join;    // added to a float's shifted bits: FP64 exponent rebias (896 - s) << 20
+};
+__device__ __forceinline__ FastK fast_k(int s) {
+  return FastK{(unsigned)(s - 896 - 23) << 23, (unsigned)(896 - s) << 20};
+}
+
+// d * 2^s -> (hi, lo) in a fast window: hi = leading 24 significant bits, lo = next 23 (both
+// truncated).  The float exponent of hi, ef = 143 - (emax - E), is in [24, 143]:
+//   T  = sign | (ef - 23) << 23 | m23    (nine low exponent bits of d shifted in, rebiased mod 2^8)
+//   hi = T + 23 << 23
+//   lo = (T's sign/exponent | next 23 fraction bits) - (T's sign/exponent), exact (Sterbenz).
+__device__ __forceinline__ void split_fast(double d, const FastK& k, float& hi, float& lo) {
+  const unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
+  const unsigned x = __funnelshift_l(lw, hw, 3);
+  const unsigned t = ((x + k.split) & 0x7FFFFFFFu) | (hw & 0x80000000u);
+  const unsigned b = t & 0xFF800000u;
+  hi = __uint_as_float(t + (23u << 23));
+  lo = __fsub_rn(__uint_as_float(b | ((lw >> 6) & 0x7FFFFFu)), __uint_as_float(b));
+}
+
+// (h, l) * 2^-s -> FP64 in a fast window: both floats rebuilt as exact FP64 bit patterns and
+// added once on the FP64 pipe.  A float's bits shifted right by 3 (sign kept) give the FP64
+// fraction and exponent fields; adding (896 - s) << 20 rebiases and unscales the exponent,
+// which stays inside [1, 2046] for every normal float because s is in [-896, 800].  A zero
+// or subnormal l contributes nothing (exactly zero, or a subnormal FP64 far below half an
+// ulp of the result when s <= 800); a zero or subnormal h takes the exact out-of-line path.
+__device__ __forceinline__ double join_fast(float h, float l, int s, const FastK& k) {
+  const unsigned bh = __float_as_uint(h), bl = __float_as_uint(l);
+  if ((bh & 0x7F800000u) == 0u) return join_slow(h, l, s);
+  const unsigned hh = ((unsigned)((int)bh >> 3) & 0x8FFFFFFFu) + k.join;
+  const unsigned lh = ((unsigned)((int)bl >> 3) & 0x8FFFFFFFu) + ((bl & 0x7F800000u) ? k.join : 0u);
+  return __dadd_rn(__hiloint2double((int)hh, (int)(bh << 29)), __hiloint2double((int)lh, (int)(bl << 29)));
+}
+
+// (h, l) * 2^-s -> FP64 in any window: both parts converted exactly by integer operations and
+// one FP64 addition.  Anything outside the plain case -- a zero or subnormal leading part,
+// a part whose unscaled exponent leaves the FP64 normal range, Inf/NaN -- takes the
+// out-of-line FP64 path, which rounds into the subnormal range correctly.
 __device__ __forceinline__ double join_dadd(float h, float l, int s) {
   const unsigned bh = __float_as_uint(h), bl = __float_as_uint(l);
   const int eh = (int)((bh >> 23) & 0xFFu), el = (int)((bl >> 23) & 0xFFu);

@@ -6,11 +6,11 @@ namespace dich {
 template <int NT>
 static cudaError_t launch_one(int grid, size_t smem, cudaStream_t st, const WinArgs& a) {
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_window<NT, FORM_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_window<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_window<NT, FORM_F64><<<grid, NT, smem, st>>>(a);
+  k_window<NT><<<grid, NT, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -20,15 +20,11 @@
 // own blocks has decayed below 2^-64 (the truncation is exact to that level); on the
 // general path the window instead takes the first/last values from a global scan.
 //
-// MIXED form: the sweeps run in compensated FP32 (ff.cuh) and the per-block quantities and the
-// tree in float-float, all on values scaled per window by an exact power of two (largest |F|
-// of the window near 2^16); only the general path's beta and first/last values cross the
-// window boundary, as unscaled FP64.
+// This file holds the FP64 form (one block per thread) and what both window kernels share;
+// the MIXED form's kernel is in window_mixed.cuh.
 #pragma once
-#include <type_traits>
 
 #include "dich_internal.cuh"
-#include "ff.cuh"
 
 namespace dich {
 
@@ -64,37 +60,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // 2^k as a double for |k| <= 1000 (bit construction)
 __device__ __forceinline__ double pow2i(int k) { return __hiloint2double((1023 + k) << 20, 0); }
 
-// Arithmetic of the per-block quantities and of the dichotomy tree: FP64 in the FP64 form,
-// float-float on the FP32 pipe in the MIXED form (GB300's FP64 pipe is ~70x slower).
-struct OpsF64 {
-  using V = double;
-  static __device__ __forceinline__ V zero() { return 0.0; }
-  static __device__ __forceinline__ V one() { return 1.0; }
-  static __device__ __forceinline__ V add(V a, V b) { return a + b; }
-  static __device__ __forceinline__ V sub(V a, V b) { return a - b; }
-  static __device__ __forceinline__ V mul(V a, V b) { return a * b; }
-  static __device__ __forceinline__ V fma(V a, V b, V c) { return ::fma(a, b, c); }
-  static __device__ __forceinline__ V up(V a, int d) { return __shfl_up_sync(0xffffffffu, a, d); }
-  static __device__ __forceinline__ V down(V a, int d) { return __shfl_down_sync(0xffffffffu, a, d); }
-  // block coefficient record j (BC_*) of the record at table offset `rec` (plan offsets in doubles)
-  static __device__ __forceinline__ V bc(const double* tab, int64_t rec, int j) { return tab[rec + j]; }
-};
-struct OpsFF {
-  using V = ffv;
-  static __device__ __forceinline__ V zero() { return ff_zero(); }
-  static __device__ __forceinline__ V one() { return ff_one(); }
-  static __device__ __forceinline__ V add(V a, V b) { return ff_add(a, b); }
-  static __device__ __forceinline__ V sub(V a, V b) { return ff_sub(a, b); }
-  static __device__ __forceinline__ V mul(V a, V b) { return ff_mul(a, b); }
-  static __device__ __forceinline__ V fma(V a, V b, V c) { return ff_fma(a, b, c); }
-  static __device__ __forceinline__ V up(V a, int d) { return ff_shfl_up(a, d); }
-  static __device__ __forceinline__ V down(V a, int d) { return ff_shfl_down(a, d); }
-  static __device__ __forceinline__ V bc(const double* tab, int64_t rec, int j) {
-    return ff_of(reinterpret_cast<const float2*>(tab)[rec + j]);
-  }
-};
-
-template <int NT, int FORM>
+template <int NT>
 __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   constexpr int NW = NT / 32;
   constexpr int LD = NT + 1;
@@ -111,7 +77,6 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   double* scl = sxe + NT;
   double* scr = scl + NT;
   double* swa = scr + 2 * NT;                     // 4 * NW scan scratch
-  float2* S2 = reinterpret_cast<float2*>(S);
 
   // ---------------------------------------------------------------- the window
   int sys;
@@ -166,23 +131,13 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
     }
   }
   // tables -> smem (overlaps the copies in flight)
-  if constexpr (FORM == FORM_F64) {
-    for (int i = tid; i < Lv; i += NT) tv[i] = tab[pp->o_v + i];
-    for (int i = tid; i < Lw; i += NT) tw[i] = tab[pp->o_w + i];
-    if (has_last)
-      for (int i = tid; i < nlast; i += NT) {
-        tvl[i] = tab[pp->o_vl + i];
-        twl[i] = tab[pp->o_wl + i];
-      }
-  } else {
-    for (int i = tid; i < Lv; i += NT) tv[i] = tab[pp->o_vf + i];
-    for (int i = tid; i < Lw; i += NT) tw[i] = tab[pp->o_wf + i];
-    if (has_last)
-      for (int i = tid; i < nlast; i += NT) {
-        tvl[i] = tab[pp->o_vlf + i];
-        twl[i] = tab[pp->o_wlf + i];
-      }
-  }
+  for (int i = tid; i < Lv; i += NT) tv[i] = tab[pp->o_v + i];
+  for (int i = tid; i < Lw; i += NT) tw[i] = tab[pp->o_w + i];
+  if (has_last)
+    for (int i = tid; i < nlast; i += NT) {
+      tvl[i] = tab[pp->o_vl + i];
+      twl[i] = tab[pp->o_wl + i];
+    }
   cp_async_wait_all();
   __syncthreads();
 
@@ -191,239 +146,136 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   const int64_t mb = wlo + tid;
   const bool lastb = act && (mb == P - 1);
   const int nbk = lastb ? nlast : n;
-  using O = typename std::conditional<FORM == FORM_F64, OpsF64, OpsFF>::type;
-  using V = typename O::V;
-  V xm1 = O::zero(), alpha = O::zero(), omega = O::zero();
-
-  // MIXED: one exact power-of-two scale per window puts its largest |F| near 2^16, so the
-  // float-float sweeps and tree keep full relative precision at any magnitude of F
-  int wscale = 0;
-  if constexpr (FORM == FORM_MIXED) {
-    unsigned e = 0u;
-    if (act) {
-      const unsigned* colw = reinterpret_cast<const unsigned*>(S + tid);
-      for (int i = 0; i < nbk; ++i) e = max(e, (colw[2 * i * LD + 1] >> 20) & 0x7FFu);
-    }
-    e = __reduce_max_sync(0xffffffffu, e);
-    unsigned* sexp = reinterpret_cast<unsigned*>(swa);
-    if (lane == 0) sexp[wid] = e;
-    __syncthreads();
-    e = 0u;
-    for (int w = 0; w < NW; ++w) e = max(e, sexp[w]);
-    __syncthreads();
-    // e == 0: zeros or subnormals only -> the largest scale; e == 2047: Inf/NaN -> none
-    wscale = (e == 2047u) ? 0 : ((e == 0u) ? 1000 : max(-1000, min(1000, (1023 + 16) - (int)e)));
-  }
-
+  double xm1 = 0.0, alpha = 0.0, omega = 0.0;
   if (act) {
-    if constexpr (FORM == FORM_F64) {
-      const double rs = pp->rs, ib = pp->ib, g = pp->g;
-      double* col = S + tid;
-      double u = 0.0;
-      int i = 0;
-      for (; i + 4 <= nbk; i += 4) {
-        const double f0 = col[(i)*LD], f1 = col[(i + 1) * LD], f2 = col[(i + 2) * LD], f3 = col[(i + 3) * LD];
-        const double u0 = fma(rs, u, f0);
-        const double u1 = fma(rs, u0, f1);
-        const double u2 = fma(rs, u1, f2);
-        const double u3 = fma(rs, u2, f3);
-        col[(i)*LD] = u0;
-        col[(i + 1) * LD] = u1;
-        col[(i + 2) * LD] = u2;
-        col[(i + 3) * LD] = u3;
-        u = u3;
-      }
-      for (; i < nbk; ++i) {
-        u = fma(rs, u, col[i * LD]);
-        col[i * LD] = u;
-      }
-      double X = 0.0;
-      i = nbk - 1;
-      for (; i - 3 >= 0; i -= 4) {
-        const double a0 = col[(i)*LD], a1 = col[(i - 1) * LD], a2 = col[(i - 2) * LD], a3 = col[(i - 3) * LD];
-        const double X0 = fma(ib, X, a0);
-        const double X1 = fma(ib, X0, a1);
-        const double X2 = fma(ib, X1, a2);
-        const double X3 = fma(ib, X2, a3);
-        col[(i)*LD] = g * X0;
-        col[(i - 1) * LD] = g * X1;
-        col[(i - 2) * LD] = g * X2;
-        col[(i - 3) * LD] = g * X3;
-        X = X3;
-      }
-      for (; i >= 0; --i) {
-        X = fma(ib, X, col[i * LD]);
-        col[i * LD] = g * X;
-      }
-      const double v0 = lastb ? pp->v0l : pp->v0;
-      const double vend = lastb ? pp->vendl : pp->vend;
-      const double xm = g * ib * X;
-      xm1 = xm;
-      alpha = col[0] - xm * v0;
-      omega = col[(nbk - 1) * LD] - xm * vend;
-    } else {
-      const float rh = pp->rs_h, rl = pp->rs_l, bh = pp->ib_h, bl = pp->ib_l, gh = pp->g_h, gl = pp->g_l;
-      const double* cold = S + tid;
-      float2* col = S2 + tid;
-      float uh = 0.f, ul = 0.f;
-      int i = 0;
-      for (; i + 4 <= nbk; i += 4) {
-        const float2 f0 = f64_to_ff_sc(cold[(i)*LD], wscale), f1 = f64_to_ff_sc(cold[(i + 1) * LD], wscale),
-                     f2 = f64_to_ff_sc(cold[(i + 2) * LD], wscale), f3 = f64_to_ff_sc(cold[(i + 3) * LD], wscale);
-        float2 o0, o1, o2, o3;
-        ff_axpy(f0.x, f0.y, rh, rl, uh, ul, o0.x, o0.y);
-        ff_axpy(f1.x, f1.y, rh, rl, o0.x, o0.y, o1.x, o1.y);
-        ff_axpy(f2.x, f2.y, rh, rl, o1.x, o1.y, o2.x, o2.y);
-        ff_axpy(f3.x, f3.y, rh, rl, o2.x, o2.y, o3.x, o3.y);
-        col[(i)*LD] = o0;
-        col[(i + 1) * LD] = o1;
-        col[(i + 2) * LD] = o2;
-        col[(i + 3) * LD] = o3;
-        uh = o3.x;
-        ul = o3.y;
-      }
-      for (; i < nbk; ++i) {
-        const float2 f0 = f64_to_ff_sc(cold[i * LD], wscale);
-        ff_axpy(f0.x, f0.y, rh, rl, uh, ul, uh, ul);
-        col[i * LD] = make_float2(uh, ul);
-      }
-      float Xh = 0.f, Xl = 0.f;
-      i = nbk - 1;
-      for (; i - 3 >= 0; i -= 4) {
-        const float2 a0 = col[(i)*LD], a1 = col[(i - 1) * LD], a2 = col[(i - 2) * LD], a3 = col[(i - 3) * LD];
-        float2 X0, X1, X2, X3, y0, y1, y2, y3;
-        ff_axpy(a0.x, a0.y, bh, bl, Xh, Xl, X0.x, X0.y);
-        ff_axpy(a1.x, a1.y, bh, bl, X0.x, X0.y, X1.x, X1.y);
-        ff_axpy(a2.x, a2.y, bh, bl, X1.x, X1.y, X2.x, X2.y);
-        ff_axpy(a3.x, a3.y, bh, bl, X2.x, X2.y, X3.x, X3.y);
-        ff_mul(gh, gl, X0.x, X0.y, y0.x, y0.y);
-        ff_mul(gh, gl, X1.x, X1.y, y1.x, y1.y);
-        ff_mul(gh, gl, X2.x, X2.y, y2.x, y2.y);
-        ff_mul(gh, gl, X3.x, X3.y, y3.x, y3.y);
-        col[(i)*LD] = y0;
-        col[(i - 1) * LD] = y1;
-        col[(i - 2) * LD] = y2;
-        col[(i - 3) * LD] = y3;
-        Xh = X3.x;
-        Xl = X3.y;
-      }
-      for (; i >= 0; --i) {
-        const float2 a0 = col[i * LD];
-        ff_axpy(a0.x, a0.y, bh, bl, Xh, Xl, Xh, Xl);
-        float2 y0;
-        ff_mul(gh, gl, Xh, Xl, y0.x, y0.y);
-        col[i * LD] = y0;
-      }
-      // block-end quantities (float-float, window-scaled units)
-      const ffv gib = ffv{pp->gib_h, pp->gib_l};
-      const ffv v0 = lastb ? ffv{pp->v0l_h, pp->v0l_l} : ffv{pp->v0_h, pp->v0_l};
-      const ffv vend = lastb ? ffv{pp->vendl_h, pp->vendl_l} : ffv{pp->vend_h, pp->vend_l};
-      const ffv xm = ff_mul(gib, ff_make(Xh, Xl));
-      xm1 = xm;
-      alpha = ff_sub(ff_of(col[0]), ff_mul(xm, v0));
-      omega = ff_sub(ff_of(col[(nbk - 1) * LD]), ff_mul(xm, vend));
+    const double rs = pp->rs, ib = pp->ib, g = pp->g;
+    double* col = S + tid;
+    double u = 0.0;
+    int i = 0;
+    for (; i + 4 <= nbk; i += 4) {
+      const double f0 = col[(i)*LD], f1 = col[(i + 1) * LD], f2 = col[(i + 2) * LD], f3 = col[(i + 3) * LD];
+      const double u0 = fma(rs, u, f0);
+      const double u1 = fma(rs, u0, f1);
+      const double u2 = fma(rs, u1, f2);
+      const double u3 = fma(rs, u2, f3);
+      col[(i)*LD] = u0;
+      col[(i + 1) * LD] = u1;
+      col[(i + 2) * LD] = u2;
+      col[(i + 3) * LD] = u3;
+      u = u3;
     }
+    for (; i < nbk; ++i) {
+      u = fma(rs, u, col[i * LD]);
+      col[i * LD] = u;
+    }
+    double X = 0.0;
+    i = nbk - 1;
+    for (; i - 3 >= 0; i -= 4) {
+      const double a0 = col[(i)*LD], a1 = col[(i - 1) * LD], a2 = col[(i - 2) * LD], a3 = col[(i - 3) * LD];
+      const double X0 = fma(ib, X, a0);
+      const double X1 = fma(ib, X0, a1);
+      const double X2 = fma(ib, X1, a2);
+      const double X3 = fma(ib, X2, a3);
+      col[(i)*LD] = g * X0;
+      col[(i - 1) * LD] = g * X1;
+      col[(i - 2) * LD] = g * X2;
+      col[(i - 3) * LD] = g * X3;
+      X = X3;
+    }
+    for (; i >= 0; --i) {
+      X = fma(ib, X, col[i * LD]);
+      col[i * LD] = g * X;
+    }
+    const double v0 = lastb ? pp->v0l : pp->v0;
+    const double vend = lastb ? pp->vendl : pp->vend;
+    const double xm = g * ib * X;
+    xm1 = xm;
+    alpha = col[0] - xm * v0;
+    omega = col[(nbk - 1) * LD] - xm * vend;
   }
 
   // ---------------------------------------------------------------- beta (eq. 16)
-  int64_t rec = (FORM == FORM_F64) ? pp->o_bcm : pp->o_bcmf;
+  int64_t rec = pp->o_bcm;
   if (act) {
     if (mb < pp->kl)
-      rec = ((FORM == FORM_F64) ? pp->o_bcl : pp->o_bclf) + mb * kBC;
+      rec = pp->o_bcl + mb * kBC;
     else if (mb >= P - pp->kr)
-      rec = ((FORM == FORM_F64) ? pp->o_bcr : pp->o_bcrf) + (mb - (P - pp->kr)) * kBC;
+      rec = pp->o_bcr + (mb - (P - pp->kr)) * kBC;
   }
-  const V bL = act ? O::fma(O::bc(tab, rec, BC_M00), alpha, O::mul(O::bc(tab, rec, BC_M01), omega)) : O::zero();
-  const V bR = act ? O::fma(O::bc(tab, rec, BC_M10), alpha, O::mul(O::bc(tab, rec, BC_M11), omega)) : O::zero();
+  const double* bc = tab + rec;
+  const double bL = act ? fma(bc[BC_M00], alpha, bc[BC_M01] * omega) : 0.0;
+  const double bR = act ? fma(bc[BC_M10], alpha, bc[BC_M11] * omega) : 0.0;
 
-  if (A.mode == MODE_BETA) {  // general path: beta leaves the window as unscaled FP64
+  if (A.mode == MODE_BETA) {  // general path: beta leaves the window
     if (act) {
-      if constexpr (FORM == FORM_F64) {
-        A.beta[2 * mb] = *reinterpret_cast<const double*>(&bL);
-        A.beta[2 * mb + 1] = *reinterpret_cast<const double*>(&bR);
-      } else {
-        const double dn = pow2i(-wscale);
-        A.beta[2 * mb] = ff_to_double(*reinterpret_cast<const ffv*>(&bL)) * dn;
-        A.beta[2 * mb + 1] = ff_to_double(*reinterpret_cast<const ffv*>(&bR)) * dn;
-      }
+      A.beta[2 * mb] = bL;
+      A.beta[2 * mb + 1] = bR;
     }
     return;
   }
 
-  V XL = O::zero(), XR = O::zero();
-  V* swv = reinterpret_cast<V*>(swa);
-  V* sxsv = reinterpret_cast<V*>(sxs);
-  V* sxev = reinterpret_cast<V*>(sxe);
+  double XL = 0.0, XR = 0.0;
   if (A.mode == MODE_FULL) {
     // ------------------------------------------------------------ dichotomy tree (a2)
     // prefix maps A -> a A + b beta^R (left to right), suffix maps B -> c B + d beta^L
-    V pa = act ? O::bc(tab, rec, BC_A) : O::one();
-    V pb = act ? O::mul(O::bc(tab, rec, BC_B), bR) : O::zero();
-    V qa = act ? O::bc(tab, rec, BC_C) : O::one();
-    V qb = act ? O::mul(O::bc(tab, rec, BC_D), bL) : O::zero();
+    double pa = act ? bc[BC_A] : 1.0;
+    double pb = act ? bc[BC_B] * bR : 0.0;
+    double qa = act ? bc[BC_C] : 1.0;
+    double qb = act ? bc[BC_D] * bL : 0.0;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      const V ya = O::up(pa, d), yb = O::up(pb, d);
-      const V za = O::down(qa, d), zb = O::down(qb, d);
+      const double ya = __shfl_up_sync(0xffffffffu, pa, d), yb = __shfl_up_sync(0xffffffffu, pb, d);
+      const double za = __shfl_down_sync(0xffffffffu, qa, d), zb = __shfl_down_sync(0xffffffffu, qb, d);
       if (lane >= d) {
-        pb = O::fma(pa, yb, pb);
-        pa = O::mul(pa, ya);
+        pb = fma(pa, yb, pb);
+        pa = pa * ya;
       }
       if (lane + d < 32) {
-        qb = O::fma(qa, zb, qb);
-        qa = O::mul(qa, za);
+        qb = fma(qa, zb, qb);
+        qa = qa * za;
       }
     }
     if (lane == 31) {
-      swv[wid] = pa;
-      swv[NW + wid] = pb;
+      swa[wid] = pa;
+      swa[NW + wid] = pb;
     }
     if (lane == 0) {
-      swv[2 * NW + wid] = qa;
-      swv[3 * NW + wid] = qb;
+      swa[2 * NW + wid] = qa;
+      swa[3 * NW + wid] = qb;
     }
     // previous lane's inclusive prefix, next lane's inclusive suffix
-    V ea = O::up(pa, 1), eb = O::up(pb, 1);
-    V fa = O::down(qa, 1), fb = O::down(qb, 1);
+    double ea = __shfl_up_sync(0xffffffffu, pa, 1), eb = __shfl_up_sync(0xffffffffu, pb, 1);
+    double fa = __shfl_down_sync(0xffffffffu, qa, 1), fb = __shfl_down_sync(0xffffffffu, qb, 1);
     if (lane == 0) {
-      ea = O::one();
-      eb = O::zero();
+      ea = 1.0;
+      eb = 0.0;
     }
     if (lane == 31) {
-      fa = O::one();
-      fb = O::zero();
+      fa = 1.0;
+      fb = 0.0;
     }
     __syncthreads();
-    V Aw = O::zero(), Bw = O::zero();  // zero coupling enters at both window ends
-    for (int w = 0; w < wid; ++w) Aw = O::fma(swv[w], Aw, swv[NW + w]);
-    for (int w = NW - 1; w > wid; --w) Bw = O::fma(swv[2 * NW + w], Bw, swv[3 * NW + w]);
-    const V Am = O::fma(ea, Aw, eb);
-    const V Bm = O::fma(fa, Bw, fb);
-    sxsv[tid] = O::add(O::fma(O::bc(tab, rec, BC_TL), Bm, bL), Am);            // x_s (eq. 18)
-    sxev[tid] = O::fma(O::bc(tab, rec, BC_TR), Am, O::add(bR, Bm));           // x_e
+    double Aw = 0.0, Bw = 0.0;  // zero coupling enters at both window ends
+    for (int w = 0; w < wid; ++w) Aw = fma(swa[w], Aw, swa[NW + w]);
+    for (int w = NW - 1; w > wid; --w) Bw = fma(swa[2 * NW + w], Bw, swa[3 * NW + w]);
+    const double Am = fma(ea, Aw, eb);
+    const double Bm = fma(fa, Bw, fb);
+    sxs[tid] = fma(bc[BC_TL], Bm, bL) + Am;            // x_s (eq. 18)
+    sxe[tid] = fma(bc[BC_TR], Am, bR + Bm);            // x_e
     __syncthreads();
     if (act) {
-      if (!(mb == 0 || tid == 0)) XL = sxev[tid - 1];
-      if (!(mb == P - 1 || tid + 1 >= nwin)) XR = sxsv[tid + 1];
+      if (!(mb == 0 || tid == 0)) XL = sxe[tid - 1];
+      if (!(mb == P - 1 || tid + 1 >= nwin)) XR = sxs[tid + 1];
     }
   } else {  // MODE_APPLY: first/last values of the neighbours from the global scan
     if (act) {
-      const double dl = (mb == 0) ? 0.0 : A.iface[2 * (mb - 1) + 1];
-      const double dr = (mb == P - 1) ? 0.0 : A.iface[2 * (mb + 1)];
-      if constexpr (FORM == FORM_F64) {
-        *reinterpret_cast<double*>(&XL) = dl;
-        *reinterpret_cast<double*>(&XR) = dr;
-      } else {
-        const double upw = pow2i(wscale);
-        const float2 a2 = f64_to_ff_rn(dl * upw), b2 = f64_to_ff_rn(dr * upw);
-        *reinterpret_cast<ffv*>(&XL) = ffv{a2.x, a2.y};
-        *reinterpret_cast<ffv*>(&XR) = ffv{b2.x, b2.y};
-      }
+      XL = (mb == 0) ? 0.0 : A.iface[2 * (mb - 1) + 1];
+      XR = (mb == P - 1) ? 0.0 : A.iface[2 * (mb + 1)];
     }
   }
   // correction coefficients of the block spikes (a3): x = xp + cL v + cR w
-  reinterpret_cast<V*>(scl)[tid] = O::sub(XL, xm1);
-  reinterpret_cast<V*>(scr)[tid] = XR;
+  scl[tid] = XL - xm1;
+  scr[tid] = XR;
   __syncthreads();
 
   // ---------------------------------------------------------------- correction + store (a3)
@@ -442,26 +294,9 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
       const int nb = lb ? nlast : n;
       const int lv = lb ? nlast : Lv, lw = lb ? nlast : Lw;
       const int jr = nb - 1 - i;
-      double dv;
-      if constexpr (FORM == FORM_F64) {
-        double val = S[i * LD + b];
-        if (i < lv) val = fma(scl[b], (lb ? tvl : tv)[i], val);
-        if (jr < lw) val = fma(scr[b], (lb ? twl : tw)[jr], val);
-        dv = val;
-      } else {
-        float2 val = S2[i * LD + b];
-        if (i < lv) {
-          const float2 c = reinterpret_cast<const float2*>(scl)[b];
-          const float2 vv = reinterpret_cast<const float2*>(lb ? tvl : tv)[i];
-          ff_fma_acc(c.x, c.y, vv.x, vv.y, val.x, val.y);
-        }
-        if (jr < lw) {
-          const float2 c = reinterpret_cast<const float2*>(scr)[b];
-          const float2 ww = reinterpret_cast<const float2*>(lb ? twl : tw)[jr];
-          ff_fma_acc(c.x, c.y, ww.x, ww.y, val.x, val.y);
-        }
-        dv = ff_to_f64_int(val.x, val.y, wscale);
-      }
+      double dv = S[i * LD + b];
+      if (i < lv) dv = fma(scl[b], (lb ? tvl : tv)[i], dv);
+      if (jr < lw) dv = fma(scr[b], (lb ? twl : tw)[jr], dv);
       __stcs(dst + j, dv);
       if (A.check_finite && !isfinite(dv)) bad = 1u;
       if (adj) {

@@ -1,6 +1,6 @@
 // window_mixed.cuh -- the MIXED-form window kernel: two blocks per thread, packed FP32x2.
 //
-// Same steps as k_window (window.cuh): load the window transposed, local sweeps (a1), beta,
+// Same steps as the FP64 form's k_window (window.cuh): load the window transposed, local sweeps (a1), beta,
 // the dichotomy tree (a2), the spike correction and store (a3).  Differences:
 //   - thread t owns the adjacent window blocks 2t and 2t+1; shared-memory rows hold a
 //     thread's pair in one 16-byte slot, and both recurrences advance through one f32x2
@@ -14,9 +14,24 @@
 // Arithmetic: compensated FP32 sweeps, float-float block quantities and tree, one exact
 // power-of-two scale per window (see ff.cuh).
 #pragma once
+#include "ff.cuh"
 #include "window.cuh"
 
 namespace dich {
+
+// float-float arithmetic of the per-block quantities and of the dichotomy tree
+struct OpsFF {
+  using V = ffv;
+  static __device__ __forceinline__ V add(V a, V b) { return ff_add(a, b); }
+  static __device__ __forceinline__ V mul(V a, V b) { return ff_mul(a, b); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return ff_fma(a, b, c); }
+  static __device__ __forceinline__ V up(V a, int d) { return ff_shfl_up(a, d); }
+  static __device__ __forceinline__ V down(V a, int d) { return ff_shfl_down(a, d); }
+  // block coefficient record j (BC_*) of the record at float-pair offset `rec`
+  static __device__ __forceinline__ V bc(const double* tab, int64_t rec, int j) {
+    return ff_of(reinterpret_cast<const float2*>(tab)[rec + j]);
+  }
+};
 
 // shared memory of the MIXED window kernel: NT threads, 2 NT window blocks, n_smem rows
 __host__ __device__ inline size_t window2_smem_bytes(int NT, int n_smem) {
@@ -28,9 +43,10 @@ __host__ __device__ inline size_t window2_smem_bytes(int NT, int n_smem) {
 // forward and backward sweeps of a thread's pair of blocks, in place.  GUARD: the two blocks
 // may differ in size (the system's last block) or be inactive (nb = 0): rows at or beyond a
 // block's size enter as zero, which keeps its backward recurrence exact.
-template <int LD, bool GUARD>
+template <int LD, bool GUARD, bool FAST>
 __device__ __forceinline__ void sweep_pair(double* S, int tid, int nrow, int nb0, int nb1, int wscale,
                                            const SysPlan* pp, float2& Xh, float2& Xl) {
+  const FastK fk = fast_k(wscale);
   const float2 rh = f2(pp->rs_h), rl = f2(pp->rs_l), bh = f2(pp->ib_h), bl = f2(pp->ib_l);
   const float2 gh = f2(pp->g_h), gl = f2(pp->g_l);
   float2 uh = f2(0.f), ul = f2(0.f);
@@ -39,8 +55,13 @@ __device__ __forceinline__ void sweep_pair(double* S, int tid, int nrow, int nb0
     double* row = S + (size_t)i * LD + 2 * tid;
     const double2 fd = *reinterpret_cast<const double2*>(row);
     float2 fh, fl;
-    split_sc(fd.x, wscale, fh.x, fl.x);
-    split_sc(fd.y, wscale, fh.y, fl.y);
+    if (FAST) {
+      split_fast(fd.x, fk, fh.x, fl.x);
+      split_fast(fd.y, fk, fh.y, fl.y);
+    } else {
+      split_sc(fd.x, wscale, fh.x, fl.x);
+      split_sc(fd.y, wscale, fh.y, fl.y);
+    }
     if (GUARD) {
       if (i >= nb0) fh.x = fl.x = 0.f;
       if (i >= nb1) fh.y = fl.y = 0.f;
@@ -67,13 +88,14 @@ __device__ __forceinline__ void sweep_pair(double* S, int tid, int nrow, int nb0
 }
 
 // correction x = xp + cL v + cR w along the thread's pair of columns and the FP64 join, in place.
-template <int LD, bool GUARD>
+template <int LD, bool GUARD, bool FAST>
 __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow, int nb0, int nb1, bool last0,
                                              bool last1, int n, int nlast, int Lv, int Lw, const float2* tv,
                                              const float2* tw, const float2* tvl, const float2* twl, ffv cL0,
                                              ffv cL1, ffv cR0, ffv cR1, int wscale) {
   const float2 clh = make_float2(cL0.h, cL1.h), cll = make_float2(cL0.l, cL1.l);
   const float2 crh = make_float2(cR0.h, cR1.h), crl = make_float2(cR0.l, cR1.l);
+  const FastK fk = fast_k(wscale);
   if (!GUARD) {
     // both blocks full size: one spike table, one row index for both
 #pragma unroll 2
@@ -90,7 +112,12 @@ __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow, int n
         const float2 w = tw[j];
         ff_fma_acc2(crh, crl, f2(w.x), f2(w.y), xh, xl);
       }
-      *reinterpret_cast<double2*>(row) = make_double2(join_dadd(xh.x, xl.x, wscale), join_dadd(xh.y, xl.y, wscale));
+      if (FAST)
+        *reinterpret_cast<double2*>(row) =
+            make_double2(join_fast(xh.x, xl.x, wscale, fk), join_fast(xh.y, xl.y, wscale, fk));
+      else
+        *reinterpret_cast<double2*>(row) =
+            make_double2(join_dadd(xh.x, xl.x, wscale), join_dadd(xh.y, xl.y, wscale));
     }
   } else {
     const int lv0 = last0 ? nlast : Lv, lw0 = last0 ? nlast : Lw;
@@ -223,31 +250,63 @@ __global__ void __launch_bounds__(NT) k_window2(const WinArgs A) {
   const int nrow = max(nb0, nb1);
   const bool full = (nb0 == n) && (nb1 == n);
 
-  // window scale: largest |F| of the window near 2^16 (exact power of two)
+  // window scale: largest |F| of the window near 2^16 (exact power of two).  The largest and
+  // smallest FP64 high words (sign cleared) give the exponent range of the window: a window of
+  // normal values within 2^119 of each other, not too close to the ends of the FP64 range,
+  // takes the fast split and join (ff.cuh).
   int wscale;
+  bool fast;
   {
-    unsigned e = 0u;
-    for (int i = 0; i < nrow; ++i) {
-      const uint4 q = *reinterpret_cast<const uint4*>(S + (size_t)i * LD + 2 * tid);
-      if (i < nb0) e = max(e, (q.y >> 20) & 0x7FFu);
-      if (i < nb1) e = max(e, (q.w >> 20) & 0x7FFu);
+    unsigned hmax = 0u, hmin = 0xFFFFFFFFu;
+    if (full) {
+#pragma unroll 4
+      for (int i = 0; i < nrow; ++i) {
+        const uint4 q = *reinterpret_cast<const uint4*>(S + (size_t)i * LD + 2 * tid);
+        const unsigned a = q.y & 0x7FFFFFFFu, c = q.w & 0x7FFFFFFFu;
+        hmax = max(hmax, max(a, c));
+        hmin = min(hmin, min(a, c));
+      }
+    } else {
+      for (int i = 0; i < nrow; ++i) {
+        const uint4 q = *reinterpret_cast<const uint4*>(S + (size_t)i * LD + 2 * tid);
+        if (i < nb0) {
+          hmax = max(hmax, q.y & 0x7FFFFFFFu);
+          hmin = min(hmin, q.y & 0x7FFFFFFFu);
+        }
+        if (i < nb1) {
+          hmax = max(hmax, q.w & 0x7FFFFFFFu);
+          hmin = min(hmin, q.w & 0x7FFFFFFFu);
+        }
+      }
     }
-    e = __reduce_max_sync(0xffffffffu, e);
+    hmax = __reduce_max_sync(0xffffffffu, hmax);
+    hmin = __reduce_min_sync(0xffffffffu, hmin);
     unsigned* sexp = reinterpret_cast<unsigned*>(swv);
-    if (lane == 0) sexp[wid] = e;
+    if (lane == 0) {
+      sexp[wid] = hmax;
+      sexp[NW + wid] = hmin;
+    }
     __syncthreads();
-    e = 0u;
-    for (int w = 0; w < NW; ++w) e = max(e, sexp[w]);
+    hmax = 0u;
+    hmin = 0xFFFFFFFFu;
+    for (int w = 0; w < NW; ++w) {
+      hmax = max(hmax, sexp[w]);
+      hmin = min(hmin, sexp[NW + w]);
+    }
     __syncthreads();
-    wscale = (e == 2047u) ? 0 : ((e == 0u) ? 1000 : max(-1000, min(1000, (1023 + 16) - (int)e)));
+    const int emax = (int)(hmax >> 20), emin = (int)(hmin >> 20);
+    wscale = (emax == 2047) ? 0 : ((emax == 0) ? 1000 : max(-1000, min(1000, (1023 + 16) - emax)));
+    fast = (emin >= 1) && (emax >= 239) && (emax <= 1935) && (emax - emin <= 119);
   }
 
   // ---------------------------------------------------------------- local sweeps (a1)
   float2 Xh, Xl;
-  if (full)
-    sweep_pair<LD, false>(S, tid, nrow, nb0, nb1, wscale, pp, Xh, Xl);
+  if (full && fast)
+    sweep_pair<LD, false, true>(S, tid, nrow, nb0, nb1, wscale, pp, Xh, Xl);
+  else if (full)
+    sweep_pair<LD, false, false>(S, tid, nrow, nb0, nb1, wscale, pp, Xh, Xl);
   else
-    sweep_pair<LD, true>(S, tid, nrow, nb0, nb1, wscale, pp, Xh, Xl);
+    sweep_pair<LD, true, false>(S, tid, nrow, nb0, nb1, wscale, pp, Xh, Xl);
 
   // block-end quantities: xp(-1) = g ib X_0, alpha = xp_0 - xp(-1) v_0, omega = xp_{n-1} - xp(-1) v_{n-1}
   const ffv gib = ffv{pp->gib_h, pp->gib_l};
@@ -386,12 +445,15 @@ __global__ void __launch_bounds__(NT) k_window2(const WinArgs A) {
 
   // ---------------------------------------------------------------- correction (a3), per column
   const ffv cL0 = ff_sub(XL0, xm0), cL1 = ff_sub(XL1, xm1);
-  if (full)
-    correct_pair<LD, false>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL0, cL1, XR0,
-                            XR1, wscale);
+  if (full && fast)
+    correct_pair<LD, false, true>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL0, cL1,
+                                  XR0, XR1, wscale);
+  else if (full)
+    correct_pair<LD, false, false>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL0,
+                                   cL1, XR0, XR1, wscale);
   else if (nrow > 0)
-    correct_pair<LD, true>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL0, cL1, XR0,
-                           XR1, wscale);
+    correct_pair<LD, true, false>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL0, cL1,
+                                  XR0, XR1, wscale);
   __syncthreads();
 
   // ---------------------------------------------------------------- coalesced store of the own rows

@@ -141,6 +141,37 @@ def test_mixed_dynamic_range(D, scale):
     assert rel(x, oracle.thomas(t, F)) < TOL
 
 
+def test_mixed_window_classes(D):
+    """Windows whose F are all normal and within 2^119 of each other take the MIXED kernel's
+    fast conversions; zeros, subnormals, a wider spread or an all-zero stretch take the general
+    ones.  One system crossing all of these matches the oracle, overall and per stretch."""
+    t = (-1.2, 2.5, -0.8)
+    rng = np.random.default_rng(11)
+    seg = 12000
+    parts = [rng.standard_normal(seg)]                         # fast
+    p = rng.standard_normal(seg)
+    p[::5] = 0.0
+    parts.append(p)                                            # exact zeros
+    p = rng.standard_normal(seg)
+    p[::7] *= 1e-40
+    parts.append(p)                                            # spread beyond 2^119
+    parts.append(rng.standard_normal(seg) * 1e-3)              # fast, other scale
+    parts.append(np.zeros(seg))                                # all zero
+    p = rng.standard_normal(seg)
+    p[3::11] = 1e-310
+    parts.append(p)                                            # FP64 subnormals
+    parts.append(-np.abs(rng.standard_normal(seg - 3)))        # fast, ragged tail
+    F = np.concatenate(parts)
+    ref = oracle.thomas(t, F)
+    for threads, bs in ((0, 0), (64, 12), (256, 16)):
+        x, info = gpu_solve(D, t, F, precision=1, threads=threads, block_size=bs)
+        assert info["precision"] == 1
+        assert rel(x, ref) < TOL
+        for k in (0, 1, 2, 3, 5, 6):
+            sl = slice(k * seg, min((k + 1) * seg, F.size))
+            assert rel(x[sl], ref[sl]) < 1e-11, (threads, bs, k)
+
+
 def test_trivial_sizes(D):
     for N in (0, 1, 2):
         F = np.arange(1, N + 1, dtype=np.float64)
