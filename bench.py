@@ -5,8 +5,8 @@ tridiag{-1.2, 2.5, -0.8}, N = 2^26, F ~ N(0, 1) from seed 0.  A "step" is one so
 system (the local sweeps, the dichotomy tree and the basis correction -- Stage 2 of the
 paper, Table 1) with the plan (Stage 1, the Toeplitz preliminary step) built before the
 timed region; Stage 1's host time is reported beside it as `plan_us`.  `value` is the
-precision form chosen by the library's AUTO policy (compensated-FP32 sweeps, FP64 tree)
-which meets the 1e-12 bar on this system; the plain FP64 solve is timed the same way and
+precision form chosen by the library's AUTO policy (compensated-FP32 sweeps, float-float
+block quantities and tree) which meets the 1e-12 bar on this system; the plain FP64 solve is timed the same way and
 reported under `fp64_plain`.  Both errors against the CPU oracle are measured every run.
 
 Inputs (512 MB each for F and x) are larger than the 129 MB L2, so no flush is needed.
@@ -209,6 +209,7 @@ def run_gpu(args):
     x_ref = oracle.thomas(t, F_h)
     for r in results.values():
         r["rel_err"] = float(np.max(np.abs(r["x"] - x_ref)) / np.max(np.abs(x_ref)))
+        r["backward_err"] = backward_error(t, F_h, r["x"])
 
     # clocks during a separate timed pass of the headline form, long enough (~1.5 s) for the
     # 200 ms nvidia-smi samples; its per-step time is reported beside the main one
@@ -288,10 +289,12 @@ def run_gpu(args):
         "hbm_gbs": round(achieved, 1),
         "hbm_pct_of_8tbs": round(100.0 * achieved / 8000.0, 1),
         "rel_err_vs_oracle": head["rel_err"],
+        "backward_err": head["backward_err"],
         "plan_us": round(head["plan_us"], 1),
         "device_status": head["status"],
         "fp64_plain": {"value": round(world * N / (f64_ms * 1e-3) / 1e9, 3), "unit": "Gunknowns/s",
                        "ms_per_step": round(f64_ms, 5), "rel_err_vs_oracle": f64["rel_err"],
+                       "backward_err": f64["backward_err"],
                        "bound": "alu (FP64 pipe)", "block_size": f64["info"]["n"],
                        "threads_per_window": f64["info"]["threads"], "device_status": f64["status"]},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -327,9 +330,20 @@ def _time_batch(solve, steps, world, stream):
     return max_over_ranks(e0.elapsed_time(e1), world) / steps
 
 
+def backward_error(t, F, x):
+    """Norm-wise backward error ||F - T x||_inf / (||T||_inf ||x||_inf + ||F||_inf)."""
+    tm1, t0, tp1 = t
+    r = F - t0 * x
+    r[1:] -= tm1 * x[:-1]
+    r[:-1] -= tp1 * x[1:]
+    normT = abs(tm1) + abs(t0) + abs(tp1)
+    return float(np.max(np.abs(r)) / (normT * np.max(np.abs(x)) + np.max(np.abs(F))))
+
+
 def other_configs(D, W, oracle, stream, world, steps=10):
-    """C3 (2-D Poisson modes), C4 (uneven series), C5 (adjoint): ms and Gunknowns/s per form,
-    with the max relative error against the oracle on a sample of systems."""
+    """C1 (latency), the weakly dominant C2 variant, C3 (2-D Poisson modes), C4 (uneven series),
+    C5 (adjoint): time and Gunknowns/s per form, with the error against the oracle (on a
+    sample of systems for the batches)."""
     import torch
     out = {}
     rng = np.random.default_rng(0)
@@ -345,6 +359,42 @@ def other_configs(D, W, oracle, stream, world, steps=10):
             ref = solve((tm1[s_], t0[s_], tp1[s_]), Fd[o:o + n].cpu().numpy())
             errs.append(float(np.max(np.abs(xd[o:o + n].cpu().numpy() - ref)) / max(np.max(np.abs(ref)), 1e-300)))
         return max(errs)
+
+    # C1: tridiag{-1, 4, -1}, N = 65536 (1 MB in, 1 MB out): latency of one solve, three
+    # buffer sets in rotation, many back-to-back solves between two events
+    t1, F1 = W.single_c1()
+    sets = [(torch.from_numpy(F1 * (1.0 + 0.1 * k)).cuda(), torch.empty(F1.size, dtype=torch.float64, device="cuda"))
+            for k in range(3)]
+    c1 = {"unknowns": int(F1.size)}
+    for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
+        plan = D.Plan(*t1, F1.size, precision=prec)
+        reps = 300
+        us = 1e3 * _time_batch(lambda: [plan.solve(Fk, out=xk) for Fk, xk in sets], reps, world, stream) / 3
+        err = max(float(np.max(np.abs(xk.cpu().numpy() - oracle.thomas(t1, Fk.cpu().numpy())))
+                        / np.max(np.abs(oracle.thomas(t1, Fk.cpu().numpy())))) for Fk, xk in sets)
+        c1[name] = {"us_per_solve": round(us, 2), "Gunknowns_s": round(F1.size / us / 1e3, 2), "windows": plan.info["tiles"],
+                    "rel_err": err}
+    out["c1_latency_65536"] = c1
+    del sets
+
+    # C2 variant: the weakly dominant tridiag{-1, 2.001, -1} at N = 2^26 (decay length ~1400
+    # rows; the AUTO policy takes the FP64 form here, gain 64 > 24)
+    t2w, F2w = W.single_c2(weak=True)
+    Fd = torch.from_numpy(F2w).cuda()
+    xd = torch.empty_like(Fd)
+    ref2w = oracle.thomas(t2w, F2w)
+    c2w = {"unknowns": int(F2w.size)}
+    for name, prec in (("auto", D.PREC_AUTO), ("mixed", D.PREC_MIXED), ("fp64_plain", D.PREC_F64)):
+        plan = D.Plan(*t2w, F2w.size, precision=prec)
+        ms = _time_batch(lambda: plan.solve(Fd, out=xd), steps, world, stream)
+        xh = xd.cpu().numpy()
+        c2w[name] = {"ms": round(ms, 4), "Gunknowns_s": round(F2w.size / ms / 1e6, 2),
+                     "form": ["f64", "mixed"][plan.info["precision"]], "path": ["single", "halo", "general"][plan.info["path"]],
+                     "block_size": plan.info["n"], "halo": [plan.info["halo_l"], plan.info["halo_r"]],
+                     "rel_err": float(np.max(np.abs(xh - ref2w)) / np.max(np.abs(ref2w))),
+                     "backward_err": backward_error(t2w, F2w, xh)}
+    out["c2_weak_2e26"] = c2w
+    del Fd, xd, ref2w
 
     # C3: 4096 Poisson modes of N = 4096 (DST of a seeded smooth source)
     tm1, t0, tp1, N, rhs = W.poisson_c3()

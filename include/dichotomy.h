@@ -110,6 +110,19 @@ int dichotomy_plan(double t_m1, double t_0, double t_1, int64_t N, dich_plan_t* 
 int dichotomy_plan_ex(double t_m1, double t_0, double t_1, int64_t N, const dich_opts* opts,
                       dich_plan_t* out);
 
+/* A plan for the quasi-Toeplitz matrix of Sec. 3.1, eq. 21: tridiag{t_-1, t_0, t_1} of order N
+ * with the first diagonal entry t_0 + psi and the last t_0 + chi (Neumann or Robin ends; a
+ * single row reads t_0 + psi + chi).  The solve is the Toeplitz Dichotomy solve y = T^-1 F
+ * followed by the rank-2 corner correction x = y - c_0 g - c_1 h (Sherman-Morrison-Woodbury:
+ * g, h are the first and last columns of T^-1 in closed form, kept where they exceed the
+ * truncation threshold, and (c_0, c_1) solves a 2x2 system in psi y_0, chi y_{N-1}); two extra
+ * small kernels per solve.  psi = chi = 0 gives the plain Toeplitz plan.  dichotomy_solve and
+ * dichotomy_solve_series serve the plan; dichotomy_adjoint returns DICH_ERR_UNSUPPORTED.
+ * Errors: as dichotomy_plan_ex; DICH_ERR_NOT_DOMINANT when an end row loses dominance
+ * (|t_0 + psi| < |t_1| or |t_0 + chi| < |t_-1|), DICH_ERR_SINGULAR when the corner system is. */
+int dichotomy_plan_quasi(double t_m1, double t_0, double t_1, double psi, double chi, int64_t N,
+                         const dich_opts* opts, dich_plan_t* out);
+
 /* Describe a plan.  Errors: DICH_ERR_ARG. */
 int dichotomy_plan_info(dich_plan_t plan, dich_plan_info* info);
 
@@ -127,6 +140,16 @@ int dichotomy_plan_bind(dich_plan_t plan, void* d_workspace, size_t bytes, void*
  * Enqueues one kernel (single/halo path) or three (general path) on `stream`.
  * Errors: DICH_ERR_ARG, DICH_ERR_ALIAS, DICH_ERR_UNBOUND, DICH_ERR_CUDA (launch). */
 int dichotomy_solve(dich_plan_t plan, const double* d_F, double* d_x, void* stream);
+
+/* A series with a constant matrix (Sec. 1, eq. 2; Sec. 3.1): x_k = T^-1 F_k for the M
+ * right-hand sides F_k = d_F + k ldf, x_k = d_x + k ldx (k = 0 .. M-1; row-major [M][N] when
+ * ldf = ldx = N).  The plan (the preliminary step) serves every right-hand side.  The single
+ * and halo paths enqueue one kernel per 65535 right-hand sides; the general path three
+ * kernels per right-hand side, in order on `stream`.  M = 1 is dichotomy_solve.
+ * Errors: DICH_ERR_ARG (M < 0, ld < N for M > 1, null/misaligned/host pointers),
+ * DICH_ERR_ALIAS (the F and x ranges overlap), DICH_ERR_UNBOUND, DICH_ERR_CUDA (launch). */
+int dichotomy_solve_series(dich_plan_t plan, int64_t M, const double* d_F, int64_t ldf, double* d_x,
+                           int64_t ldx, void* stream);
 
 /* Adjoint of L(x) with x = T^-1 F, given d_w = dL/dx and the forward solution d_x:
  *   d_gF = lambda = T^-T w   (the same Dichotomy solve for T^T = tridiag{t_1, t_0, t_-1}),

@@ -56,12 +56,13 @@ def _load():
             D = ctypes.c_double
             lib.oracle_thomas_f64.argtypes = [I64, D, D, D, P, P]
             lib.oracle_thomas_q.argtypes = [I64, D, D, D, P, P]
+            lib.oracle_thomas_tridiag.argtypes = [I64, P, P, P, P, P]
             lib.oracle_thomas_batched.argtypes = [I64, P, P, P, P, P, P, P, ctypes.c_int]
             lib.oracle_adjoint_f64.argtypes = [I64, D, D, D, P, P, P, P]
             lib.oracle_dich_eq15.argtypes = [I64, D, D, D, P, I64, P, P, P, P, P, P]
             lib.oracle_dich_levels.argtypes = [I64, D, D, D, P, I64, P, P, P]
             lib.oracle_dich_prelim.argtypes = [I64, D, D, D, I64, P, P, P, P, P]
-            for f in (lib.oracle_thomas_f64, lib.oracle_thomas_q, lib.oracle_thomas_batched,
+            for f in (lib.oracle_thomas_f64, lib.oracle_thomas_q, lib.oracle_thomas_tridiag, lib.oracle_thomas_batched,
                       lib.oracle_adjoint_f64, lib.oracle_dich_eq15, lib.oracle_dich_levels,
                       lib.oracle_dich_prelim):
                 f.restype = ctypes.c_int
@@ -93,6 +94,29 @@ def thomas(t, F) -> np.ndarray:
     _check(_load().oracle_thomas_f64(F.size, float(t[0]), float(t[1]), float(t[2]), _ptr(F), _ptr(x)),
            "thomas")
     return x
+
+
+def thomas_tridiag(sub, dia, sup, F) -> np.ndarray:
+    """x = A^-1 F for a general tridiagonal A (row i: sub[i], dia[i], sup[i]) by Thomas, FP64."""
+    sub, dia, sup, F = _f64(sub), _f64(dia), _f64(sup), _f64(F)
+    if not (sub.size == dia.size == sup.size == F.size):
+        raise ValueError("sub, dia, sup and F must have one entry per row")
+    x = np.empty_like(F)
+    _check(_load().oracle_thomas_tridiag(F.size, _ptr(sub), _ptr(dia), _ptr(sup), _ptr(F), _ptr(x)),
+           "thomas_tridiag")
+    return x
+
+
+def thomas_quasi(t, psi, chi, F) -> np.ndarray:
+    """x = A^-1 F for the quasi-Toeplitz matrix of eq. 21: tridiag{t_-1, t_0, t_1} with the first
+    diagonal entry t_0 + psi and the last t_0 + chi (a single row: t_0 + psi + chi)."""
+    F = _f64(F)
+    n = F.size
+    dia = np.full(n, float(t[1]))
+    if n:
+        dia[0] += psi
+        dia[-1] += chi
+    return thomas_tridiag(np.full(n, float(t[0])), dia, np.full(n, float(t[2])), F)
 
 
 def thomas_q(t, F) -> np.ndarray:

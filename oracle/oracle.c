@@ -17,6 +17,8 @@
  *                           -- the "sequential version of the Thomas
  *                           algorithm" the paper uses for eq. 7 (Sec. 2.2).
  *   oracle_thomas_q         the same in binary128 (arbiter).
+ *   oracle_thomas_tridiag   Thomas for a general tridiagonal matrix (three arrays),
+ *                           e.g. the quasi-Toeplitz matrices of eq. 21.
  *   oracle_thomas_batched   one Thomas per system over a pthread pool.
  *   oracle_adjoint_f64      lambda = T^-T w and dL/dt for L = <w, x>.
  *   oracle_dich_eq15        the paper's Dichotomy formulas written out for a
@@ -70,6 +72,15 @@ static int thomas_general(int64_t n, const double* sub, const double* dia,
   free(cp);
   free(dp);
   return 0;
+}
+
+/* General tridiagonal solve, FP64: row i reads sub[i] x[i-1] + dia[i] x[i] + sup[i] x[i+1]
+ * = f[i] (sub[0] and sup[n-1] unused).  Serves the quasi-Toeplitz matrices of eq. 21 (t_0
+ * replaced by t_0 + psi in the first row and t_0 + chi in the last). */
+int oracle_thomas_tridiag(int64_t n, const double* sub, const double* dia, const double* sup,
+                          const double* f, double* x) {
+  if (n < 0) return 3;
+  return thomas_general(n, sub, dia, sup, f, x);
 }
 
 /* Toeplitz solve, FP64. */

@@ -26,8 +26,8 @@ PREC_F64, PREC_MIXED, PREC_AUTO = 0, 1, 2
 FLAG_FORCE_GENERAL, FLAG_CHECK_FINITE = 1, 2
 
 EXPORTS = [
-    "dichotomy_plan", "dichotomy_plan_ex", "dichotomy_plan_info", "dichotomy_plan_workspace_bytes",
-    "dichotomy_plan_bind", "dichotomy_solve", "dichotomy_adjoint", "dichotomy_status", "dichotomy_destroy",
+    "dichotomy_plan", "dichotomy_plan_ex", "dichotomy_plan_quasi", "dichotomy_plan_info", "dichotomy_plan_workspace_bytes",
+    "dichotomy_plan_bind", "dichotomy_solve", "dichotomy_solve_series", "dichotomy_adjoint", "dichotomy_status", "dichotomy_destroy",
     "dichotomy_solve_noalloc",
     "dichotomy_batch_prepare", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
     "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
@@ -84,10 +84,13 @@ def load(build_if_missing: bool = True):
             "dichotomy_plan": ([c_double, c_double, c_double, c_int64, ctypes.POINTER(P)], I),
             "dichotomy_plan_ex": ([c_double, c_double, c_double, c_int64, ctypes.POINTER(dich_opts),
                                    ctypes.POINTER(P)], I),
+            "dichotomy_plan_quasi": ([c_double, c_double, c_double, c_double, c_double, c_int64,
+                                      ctypes.POINTER(dich_opts), ctypes.POINTER(P)], I),
             "dichotomy_plan_info": ([P, ctypes.POINTER(dich_plan_info)], I),
             "dichotomy_plan_workspace_bytes": ([P, ctypes.POINTER(c_size_t)], I),
             "dichotomy_plan_bind": ([P, P, c_size_t, P], I),
             "dichotomy_solve": ([P, P, P, P], I),
+            "dichotomy_solve_series": ([P, c_int64, P, c_int64, P, c_int64, P], I),
             "dichotomy_adjoint": ([P, P, P, P, P, P], I),
             "dichotomy_status": ([P, P, ctypes.POINTER(I)], I),
             "dichotomy_destroy": ([P], None),

@@ -327,6 +327,12 @@ struct dich_plan_s {
   int n_smem = 2;
   int64_t tiles = 0;
   SysBuild fwd, adj;
+  // quasi-Toeplitz corners (eq. 21): t_0 + psi in row 0, t_0 + chi in row N-1
+  bool quasi = false;
+  double psi = 0.0, chi = 0.0;
+  int64_t Lg = 0, Lh = 0;              // kept rows of g = T^-1 e_0 and h = T^-1 e_{N-1}
+  double W[4] = {1.0, 0.0, 0.0, 1.0};  // (I + K)^-1 of the Sherman-Morrison-Woodbury step
+  std::vector<double> corner;          // g[Lg], then h[Lh] (h[k] is row N-1-k)
   // workspace layout (bytes)
   size_t ws_bytes = 0, off_plans = 0, off_status = 0, off_tabs = 0, off_beta = 0, off_iface = 0,
          off_scan = 0, off_part = 0;
@@ -359,6 +365,95 @@ const char* dichotomy_strerror(int s) {
   }
 }
 
+// Workspace layout and the staging copy of a plan: records, status word, tables (forward,
+// transposed, quasi-Toeplitz corners), general-path scratch, adjoint partials.
+static void plan_layout(dich_plan_s* p) {
+  // workspace layout
+  size_t o_ = 0;
+  p->off_plans = o_;
+  o_ += align_up(2 * sizeof(SysPlan));
+  p->off_status = o_;
+  o_ += kAlign;
+  p->off_tabs = o_;
+  o_ += align_up(sizeof(double) * (p->fwd.tab.size() + p->adj.tab.size() + p->corner.size()));
+  const int64_t P = (p->N >= 2) ? p->fwd.rec.P : 0;
+  if (p->path == PATH_GENERAL) {
+    p->off_beta = o_;
+    o_ += align_up(sizeof(double) * 2 * P);
+    p->off_iface = o_;
+    o_ += align_up(sizeof(double) * 2 * P);
+    p->off_scan = o_;
+    o_ += align_up(sizeof(double) * 6 * (size_t)ceil_div(P, kScanChunk));
+  }
+  p->off_part = o_;
+  o_ += align_up(sizeof(double) * 3 * (size_t)std::max<int64_t>(1, p->tiles));
+  p->ws_bytes = o_;
+  // staging copy: records, zero status, tables
+  p->staging.assign(p->off_tabs + sizeof(double) * (p->fwd.tab.size() + p->adj.tab.size() + p->corner.size()), 0);
+  SysPlan recs[2] = {p->fwd.rec, p->adj.rec};
+  recs[0].tab = 0;
+  recs[1].tab = (int64_t)p->fwd.tab.size();
+  std::memcpy(p->staging.data() + p->off_plans, recs, sizeof(recs));
+  if (!p->fwd.tab.empty())
+    std::memcpy(p->staging.data() + p->off_tabs, p->fwd.tab.data(), sizeof(double) * p->fwd.tab.size());
+  if (!p->adj.tab.empty())
+    std::memcpy(p->staging.data() + p->off_tabs + sizeof(double) * p->fwd.tab.size(), p->adj.tab.data(),
+                sizeof(double) * p->adj.tab.size());
+  if (!p->corner.empty())
+    std::memcpy(p->staging.data() + p->off_tabs + sizeof(double) * (p->fwd.tab.size() + p->adj.tab.size()),
+                p->corner.data(), sizeof(double) * p->corner.size());
+}
+
+// Blocks, halo/general path and windows of a single-system plan for window width NT and block
+// size n (fills p->NT, fwd, adj, path, n_smem, tiles).
+static int plan_geometry(dich_plan_s* p, const Opts& o, int NT, int n) {
+  const int WB = window_blocks(NT, p->form);
+  p->NT = NT;
+  int rc = build_system(p->tm1, p->t0, p->tp1, p->N, NT, p->form, n, o, true, p->fwd);
+  if (!rc) rc = build_system(p->tp1, p->t0, p->tm1, p->N, NT, p->form, n, o, true, p->adj);
+  if (rc) return rc;
+  // both solves must take the same path; the transposed system swaps the halos
+  p->path = std::max(p->fwd.path, p->adj.path);
+  if (p->path == PATH_GENERAL && (p->fwd.path != PATH_GENERAL || p->adj.path != PATH_GENERAL)) {
+    Opts og = o;
+    og.flags |= DICH_FLAG_FORCE_GENERAL;
+    build_system(p->tm1, p->t0, p->tp1, p->N, NT, p->form, n, og, true, p->fwd);
+    build_system(p->tp1, p->t0, p->tm1, p->N, NT, p->form, n, og, true, p->adj);
+  }
+  if (p->path == PATH_HALO) {  // one window geometry for both directions
+    const int hl = std::max(p->fwd.rec.hl, p->adj.rec.hl), hr = std::max(p->fwd.rec.hr, p->adj.rec.hr);
+    for (SysBuild* sb : {&p->fwd, &p->adj}) {
+      sb->rec.hl = hl;
+      sb->rec.hr = hr;
+      sb->rec.own = WB - hl - hr;
+    }
+    if (WB - hl - hr < WB / 2) {
+      Opts og = o;
+      og.flags |= DICH_FLAG_FORCE_GENERAL;
+      build_system(p->tm1, p->t0, p->tp1, p->N, NT, p->form, n, og, true, p->fwd);
+      build_system(p->tp1, p->t0, p->tm1, p->N, NT, p->form, n, og, true, p->adj);
+      p->path = PATH_GENERAL;
+    }
+  }
+  p->n_smem = n;
+  p->tiles = ceil_div(p->fwd.rec.P, p->fwd.rec.own);
+  return DICH_OK;
+}
+
+// SMs of the current device (0 when no device is visible: plans are then built for the defaults)
+static int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms;
+}
+
 int dichotomy_plan_ex(double t_m1, double t_0, double t_1, int64_t N, const dich_opts* opts, dich_plan_t* out) {
   if (!out) return DICH_ERR_ARG;
   *out = nullptr;
@@ -379,40 +474,46 @@ int dichotomy_plan_ex(double t_m1, double t_0, double t_1, int64_t N, const dich
   p->form = pick_form(o.prec, r);
   p->NT = o.NT ? o.NT : default_threads(p->form);
   if (N >= 2) {
-    const int nmax = max_rows(p->NT, p->form, o.n_req > 0 ? kSmemMax : kSmemBudget);
-    const int WB = window_blocks(p->NT, p->form);
-    const int n = choose_n(N, WB, nmax, o.n_req, default_rows(p->form));
-    rc = build_system(t_m1, t_0, t_1, N, p->NT, p->form, n, o, true, p->fwd);
-    if (!rc) rc = build_system(t_1, t_0, t_m1, N, p->NT, p->form, n, o, true, p->adj);
+    const int n0 = choose_n(N, window_blocks(p->NT, p->form),
+                            max_rows(p->NT, p->form, o.n_req > 0 ? kSmemMax : kSmemBudget), o.n_req,
+                            default_rows(p->form));
+    rc = plan_geometry(p, o, p->NT, n0);
     if (rc) {
       delete p;
       return rc;
     }
-    // both solves must take the same path; the transposed system swaps the halos
-    p->path = std::max(p->fwd.path, p->adj.path);
-    if (p->path == PATH_GENERAL && (p->fwd.path != PATH_GENERAL || p->adj.path != PATH_GENERAL)) {
-      Opts og = o;
-      og.flags |= DICH_FLAG_FORCE_GENERAL;
-      build_system(t_m1, t_0, t_1, N, p->NT, p->form, n, og, true, p->fwd);
-      build_system(t_1, t_0, t_m1, N, p->NT, p->form, n, og, true, p->adj);
-    }
-    if (p->path == PATH_HALO) {  // one window geometry for both directions
-      const int hl = std::max(p->fwd.rec.hl, p->adj.rec.hl), hr = std::max(p->fwd.rec.hr, p->adj.rec.hr);
-      for (SysBuild* sb : {&p->fwd, &p->adj}) {
-        sb->rec.hl = hl;
-        sb->rec.hr = hr;
-        sb->rec.own = WB - hl - hr;
+    // A multi-window system with fewer windows than twice the GPU's SMs is latency-bound: unless
+    // the caller fixed the geometry, take narrower windows, then shorter blocks, while the system
+    // stays on the halo path (halo at most half the window).  Measured on GB300: N = 65536 solves
+    // 2x faster with 64-thread windows of 2-row blocks than with the large-N default.
+    const int sms = device_sms();
+    if (o.NT == 0 && o.n_req == 0 && p->path == PATH_HALO && p->tiles < 2 * (int64_t)sms) {
+      const int nmin = (p->form == FORM_MIXED) ? 2 : 4;
+      int NT = p->NT, n = n0;
+      while (p->tiles < 2 * (int64_t)sms) {
+        if (NT > 64)
+          NT = 64;
+        else if (n / 2 >= nmin)
+          n /= 2;
+        else
+          break;
+        dich_plan_s q;
+        q.N = N;
+        q.tm1 = t_m1;
+        q.t0 = t_0;
+        q.tp1 = t_1;
+        q.opts = o;
+        q.form = p->form;
+        const int nc = choose_n(N, window_blocks(NT, p->form), max_rows(NT, p->form, kSmemBudget), n, n);
+        if (plan_geometry(&q, o, NT, nc) != DICH_OK || q.path != PATH_HALO) break;
+        p->NT = NT;
+        p->fwd = std::move(q.fwd);
+        p->adj = std::move(q.adj);
+        p->path = q.path;
+        p->n_smem = q.n_smem;
+        p->tiles = q.tiles;
       }
-      if (WB - hl - hr < WB / 2) {
-        Opts og = o;
-        og.flags |= DICH_FLAG_FORCE_GENERAL;
-        build_system(t_m1, t_0, t_1, N, p->NT, p->form, n, og, true, p->fwd);
-        build_system(t_1, t_0, t_m1, N, p->NT, p->form, n, og, true, p->adj);
-        p->path = PATH_GENERAL;
-      }
     }
-    p->n_smem = n;
-    p->tiles = ceil_div(p->fwd.rec.P, p->fwd.rec.own);
   } else {
     // N = 0 or 1: trivial; keep a minimal record for the N = 1 kernel
     std::memset(&p->fwd.rec, 0, sizeof(SysPlan));
@@ -421,43 +522,67 @@ int dichotomy_plan_ex(double t_m1, double t_0, double t_1, int64_t N, const dich
     p->adj.rec = p->fwd.rec;
     p->tiles = 0;
   }
-  // workspace layout
-  size_t o_ = 0;
-  p->off_plans = o_;
-  o_ += align_up(2 * sizeof(SysPlan));
-  p->off_status = o_;
-  o_ += kAlign;
-  p->off_tabs = o_;
-  o_ += align_up(sizeof(double) * (p->fwd.tab.size() + p->adj.tab.size()));
-  const int64_t P = (N >= 2) ? p->fwd.rec.P : 0;
-  if (p->path == PATH_GENERAL) {
-    p->off_beta = o_;
-    o_ += align_up(sizeof(double) * 2 * P);
-    p->off_iface = o_;
-    o_ += align_up(sizeof(double) * 2 * P);
-    p->off_scan = o_;
-    o_ += align_up(sizeof(double) * 6 * (size_t)ceil_div(P, kScanChunk));
-  }
-  p->off_part = o_;
-  o_ += align_up(sizeof(double) * 3 * (size_t)std::max<int64_t>(1, p->tiles));
-  p->ws_bytes = o_;
-  // staging copy: records, zero status, tables
-  p->staging.assign(p->off_tabs + sizeof(double) * (p->fwd.tab.size() + p->adj.tab.size()), 0);
-  SysPlan recs[2] = {p->fwd.rec, p->adj.rec};
-  recs[0].tab = 0;
-  recs[1].tab = (int64_t)p->fwd.tab.size();
-  std::memcpy(p->staging.data() + p->off_plans, recs, sizeof(recs));
-  if (!p->fwd.tab.empty())
-    std::memcpy(p->staging.data() + p->off_tabs, p->fwd.tab.data(), sizeof(double) * p->fwd.tab.size());
-  if (!p->adj.tab.empty())
-    std::memcpy(p->staging.data() + p->off_tabs + sizeof(double) * p->fwd.tab.size(), p->adj.tab.data(),
-                sizeof(double) * p->adj.tab.size());
+  plan_layout(p);
   *out = p;
   return DICH_OK;
 }
 
 int dichotomy_plan(double t_m1, double t_0, double t_1, int64_t N, dich_plan_t* out) {
   return dichotomy_plan_ex(t_m1, t_0, t_1, N, nullptr, out);
+}
+
+int dichotomy_plan_quasi(double t_m1, double t_0, double t_1, double psi, double chi, int64_t N,
+                         const dich_opts* opts, dich_plan_t* out) {
+  if (!out) return DICH_ERR_ARG;
+  *out = nullptr;
+  if (!std::isfinite(psi) || !std::isfinite(chi)) return DICH_ERR_ARG;
+  if (N >= 2) {
+    // the end rows of eq. 21 must keep dominance (eq. 32-33; the interior rows are T's)
+    const double tol = 1.0 - 4.0 * DBL_EPSILON;
+    if (std::fabs(t_0 + psi) < std::fabs(t_1) * tol || std::fabs(t_0 + chi) < std::fabs(t_m1) * tol)
+      return DICH_ERR_NOT_DOMINANT;
+    if (t_0 + psi == 0.0 || t_0 + chi == 0.0) return DICH_ERR_SINGULAR;
+  } else if (N == 1 && t_0 + psi + chi == 0.0) {
+    return DICH_ERR_SINGULAR;
+  }
+  dich_plan_t p = nullptr;
+  int rc = dichotomy_plan_ex(t_m1, t_0, t_1, N, opts, &p);
+  if (rc) return rc;
+  p->quasi = (psi != 0.0 || chi != 0.0);
+  p->psi = psi;
+  p->chi = chi;
+  if (p->quasi && N == 1) {
+    // one row: t_0 + psi + chi
+    p->fwd.rec.t0 = p->adj.rec.t0 = t_0 + psi + chi;
+    p->quasi = false;
+    plan_layout(p);
+  } else if (p->quasi && N >= 2) {
+    // g = T^-1 e_0 and h = T^-1 e_{N-1} in closed form (the block spikes of a block of N rows):
+    //   g_i = -(1/q) rs^i Q(N-i)/Q(N+1),   h at row N-1-k = -(1/q) ib^k Q(N-k)/Q(N+1)
+    const Roots r = toeplitz_roots(t_m1, t_0, t_1);
+    const double eps = p->opts.eps;
+    p->Lg = decay_len(std::fabs(r.rs), eps, N);
+    p->Lh = decay_len(std::fabs(r.ib), eps, N);
+    p->corner.resize((size_t)(p->Lg + p->Lh));
+    for (int64_t i = 0; i < p->Lg; ++i) p->corner[(size_t)i] = r.g * ipow(r.rs, i) * spike_ratio(N, i, r);
+    for (int64_t k = 0; k < p->Lh; ++k) p->corner[(size_t)(p->Lg + k)] = r.g * ipow(r.ib, k) * spike_ratio(N, k, r);
+    const double qN1 = qnum(N + 1, r), qN = qnum(N, r);
+    const double g0 = r.g * qN / qN1, gN = r.g * ipow(r.rs, N - 1) / qN1;   // (T^-1)_{0,0}, (T^-1)_{N-1,0}
+    const double h0 = r.g * ipow(r.ib, N - 1) / qN1, hN = r.g * qN / qN1;   // (T^-1)_{0,N-1}, (T^-1)_{N-1,N-1}
+    const double k00 = 1.0 + psi * g0, k01 = psi * h0, k10 = chi * gN, k11 = 1.0 + chi * hN;
+    const double det = k00 * k11 - k01 * k10;
+    if (!std::isfinite(det) || std::fabs(det) <= 64.0 * DBL_EPSILON * (std::fabs(k00 * k11) + std::fabs(k01 * k10))) {
+      dichotomy_destroy(p);
+      return DICH_ERR_SINGULAR;
+    }
+    p->W[0] = k11 / det;
+    p->W[1] = -k01 / det;
+    p->W[2] = -k10 / det;
+    p->W[3] = k00 / det;
+    plan_layout(p);
+  }
+  *out = p;
+  return DICH_OK;
 }
 
 int dichotomy_plan_info(dich_plan_t p, dich_plan_info* info) {
@@ -505,16 +630,19 @@ int dichotomy_plan_bind(dich_plan_t p, void* d_ws, size_t bytes, void* stream) {
 }
 
 static int plan_launch(dich_plan_t p, const double* F, double* x, const double* xf, double* gt, bool adjoint,
-                       cudaStream_t st) {
+                       cudaStream_t st, int64_t M = 1, int64_t ldf = 0, int64_t ldx = 0) {
   const SysPlan* d_plans = (const SysPlan*)(p->d_ws + p->off_plans);
   const double* d_tabs = (const double*)(p->d_ws + p->off_tabs);
   unsigned* d_status = (unsigned*)(p->d_ws + p->off_status);
   const int sys_offset = adjoint ? 1 : 0;
   if (p->N == 0) return DICH_OK;
   if (p->N == 1) {
-    cudaError_t e = launch_trivial(d_plans, nullptr, 1, adjoint ? nullptr : F, x, xf, adjoint ? F : nullptr, gt,
-                                   sys_offset, st);
-    return e == cudaSuccess ? DICH_OK : cuda_fail(e);
+    for (int64_t k = 0; k < M; ++k) {
+      cudaError_t e = launch_trivial(d_plans, nullptr, 1, adjoint ? nullptr : F + k * ldf, x + k * ldx, xf,
+                                     adjoint ? F : nullptr, gt, sys_offset, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return DICH_OK;
   }
   WinArgs a{};
   a.plans = d_plans;
@@ -528,16 +656,30 @@ static int plan_launch(dich_plan_t p, const double* F, double* x, const double* 
   a.check_finite = (p->opts.flags & DICH_FLAG_CHECK_FINITE) ? 1 : 0;
   a.n_smem = p->n_smem;
   a.sys_offset = sys_offset;
+  a.ldf = ldf;
+  a.ldx = ldx;
   const size_t smem = smem_bytes(p->NT, p->n_smem, p->form);
-  auto launch = [&](const WinArgs& w) {
-    return p->form == FORM_F64 ? launch_window_f64(p->NT, (int)p->tiles, smem, st, w)
-                               : launch_window_mixed(p->NT, (int)p->tiles, smem, st, w);
+  auto launch = [&](const WinArgs& w, int gy) {
+    return p->form == FORM_F64 ? launch_window_f64(p->NT, (int)p->tiles, smem, st, w, gy)
+                               : launch_window_mixed(p->NT, (int)p->tiles, smem, st, w, gy);
   };
   cudaError_t e;
   if (p->path != PATH_GENERAL) {
+    // every right-hand side of a series in one launch (grid.y), at most 65535 per launch
     a.mode = MODE_FULL;
-    e = launch(a);
-    if (e != cudaSuccess) return cuda_fail(e);
+    for (int64_t k0 = 0; k0 < M; k0 += 65535) {
+      WinArgs w = a;
+      w.F = F + k0 * ldf;
+      w.x = x + k0 * ldx;
+      e = launch(w, (int)std::min<int64_t>(65535, M - k0));
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+  } else if (M > 1) {
+    // general path: the per-block scratch serves one right-hand side at a time (stream order)
+    for (int64_t k = 0; k < M; ++k) {
+      const int rc = plan_launch(p, F + k * ldf, x + k * ldx, nullptr, nullptr, false, st);
+      if (rc != DICH_OK) return rc;
+    }
   } else {
     double* beta = (double*)(p->d_ws + p->off_beta);
     double* iface = (double*)(p->d_ws + p->off_iface);
@@ -547,17 +689,23 @@ static int plan_launch(dich_plan_t p, const double* F, double* x, const double* 
     b.beta = beta;
     b.xf = nullptr;
     b.part = nullptr;
-    e = launch(b);
+    e = launch(b, 1);
     if (e != cudaSuccess) return cuda_fail(e);
     e = launch_block_scan(d_plans + sys_offset, d_tabs, p->fwd.rec.P, beta, iface, scan, st);
     if (e != cudaSuccess) return cuda_fail(e);
     a.mode = MODE_APPLY;
     a.iface = iface;
-    e = launch(a);
+    e = launch(a, 1);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   if (adjoint) {
     e = launch_adj_finalize(a.part, nullptr, nullptr, nullptr, p->tiles, 1, gt, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (p->quasi && !adjoint && !(p->path == PATH_GENERAL && M > 1)) {
+    const double* ctab = d_tabs + p->fwd.tab.size() + p->adj.tab.size();
+    CornerArgs c{p->N, p->Lg, p->Lh, ctab, ctab + p->Lg, p->psi, p->chi, p->W[0], p->W[1], p->W[2], p->W[3]};
+    e = launch_corner(x, M, M > 1 ? ldx : 0, c, st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   return DICH_OK;
@@ -574,9 +722,26 @@ int dichotomy_solve(dich_plan_t p, const double* d_F, double* d_x, void* stream)
   return plan_launch(p, d_F, d_x, nullptr, nullptr, false, (cudaStream_t)stream);
 }
 
+int dichotomy_solve_series(dich_plan_t p, int64_t M, const double* d_F, int64_t ldf, double* d_x, int64_t ldx,
+                           void* stream) {
+  if (!p || M < 0) return DICH_ERR_ARG;
+  if (!p->d_ws) return DICH_ERR_UNBOUND;
+  if (p->N == 0 || M == 0) return DICH_OK;
+  if (!d_F || !d_x || !aligned8(d_F) || !aligned8(d_x)) return DICH_ERR_ARG;
+  if (M > 1 && (ldf < p->N || ldx < p->N)) return DICH_ERR_ARG;
+  if (M > 1 && (ldf > INT64_MAX / M || ldx > INT64_MAX / M)) return DICH_ERR_ARG;
+  const int64_t sf = (M > 1) ? ldf : 0, sx = (M > 1) ? ldx : 0;
+  const size_t nf = sizeof(double) * (size_t)((M - 1) * sf + p->N);
+  const size_t nx = sizeof(double) * (size_t)((M - 1) * sx + p->N);
+  if (overlap(d_F, nf, d_x, nx)) return DICH_ERR_ALIAS;
+  if (!is_device_ptr(d_F) || !is_device_ptr(d_x)) return DICH_ERR_ARG;
+  return plan_launch(p, d_F, d_x, nullptr, nullptr, false, (cudaStream_t)stream, M, sf, sx);
+}
+
 int dichotomy_adjoint(dich_plan_t p, const double* d_w, const double* d_x, double* d_gF, double* d_gt,
                       void* stream) {
   if (!p) return DICH_ERR_ARG;
+  if (p->quasi) return DICH_ERR_UNSUPPORTED;
   if (!p->d_ws) return DICH_ERR_UNBOUND;
   if (!d_gt || !aligned8(d_gt) || !is_device_ptr(d_gt)) return DICH_ERR_ARG;
   if (p->N == 0) {

@@ -95,11 +95,11 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // accumulated, with the cross terms, in the unnormalised low part
 __device__ __forceinline__ void ff_axpy2(float2 fh, float2 fl, float2 rh, float2 rl, float2 xh, float2 xl,
                                          float2& yh, float2& yl) {
-  const float2 p = mul2(rh, xh);
-  const float2 pe = fma2(rh, xh, make_float2(-p.x, -p.y));
-  const float2 s = add2(fh, p);
+  const float2 pn = mul2(make_float2(-rh.x, -rh.y), xh);
+  const float2 pe = fma2(rh, xh, pn);
+  const float2 s = sub2(fh, pn);
   const float2 bb = sub2(s, fh);
-  const float2 se = add2(sub2(fh, sub2(s, bb)), sub2(p, bb));
+  const float2 se = sub2(sub2(fh, sub2(s, bb)), add2(pn, bb));
   float2 c = add2(fl, add2(pe, se));
   c = fma2(rl, xh, c);
   c = fma2(rh, xl, c);
@@ -110,7 +110,7 @@ __device__ __forceinline__ void ff_axpy2(float2 fh, float2 fl, float2 rh, float2
 // two chains of y ~= g * x (error-free leading product plus cross terms)
 __device__ __forceinline__ void ff_mul2(float2 gh, float2 gl, float2 xh, float2 xl, float2& yh, float2& yl) {
   const float2 p = mul2(gh, xh);
-  float2 c = fma2(gh, xh, make_float2(-p.x, -p.y));
+  float2 c = fma2(gh, xh, mul2(make_float2(-gh.x, -gh.y), xh));
   c = fma2(gl, xh, c);
   c = fma2(gh, xl, c);
   yh = p;
@@ -119,12 +119,12 @@ __device__ __forceinline__ void ff_mul2(float2 gh, float2 gl, float2 xh, float2 
 
 // two chains of x += c * v, c and v float-float (per chain)
 __device__ __forceinline__ void ff_fma_acc2(float2 ch, float2 cl, float2 vh, float2 vl, float2& xh, float2& xl) {
-  const float2 p = mul2(ch, vh);
-  const float2 pe = fma2(ch, vh, make_float2(-p.x, -p.y));
+  const float2 pn = mul2(make_float2(-ch.x, -ch.y), vh);
+  const float2 pe = fma2(ch, vh, pn);
   const float2 pc = fma2(cl, vh, fma2(ch, vl, pe));
-  const float2 s = add2(xh, p);
+  const float2 s = sub2(xh, pn);
   const float2 bb = sub2(s, xh);
-  const float2 se = add2(sub2(xh, sub2(s, bb)), sub2(p, bb));
+  const float2 se = sub2(sub2(xh, sub2(s, bb)), add2(pn, bb));
   xl = add2(xl, add2(pc, se));
   xh = s;
 }

@@ -1,4 +1,5 @@
-// k_aux.cu -- general-path block scan, adjoint gradient finalisation, one-row systems.
+// k_aux.cu -- general-path block scan, adjoint gradient finalisation, one-row systems,
+// quasi-Toeplitz corner correction.
 #include "launch.cuh"
 
 namespace dich {
@@ -272,6 +273,62 @@ cudaError_t launch_trivial(const SysPlan* plans, const int32_t* idx, int64_t nid
                            const double* xf, const double* w, double* gt, int sys_offset, cudaStream_t st) {
   if (nidx <= 0) return cudaSuccess;
   k_trivial<<<(unsigned)((nidx + 127) / 128), 128, 0, st>>>(plans, idx, nidx, F, x, xf, w, gt, sys_offset);
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------- quasi-Toeplitz corners (eq. 21)
+// A = T + psi e_0 e_0^T + chi e_{N-1} e_{N-1}^T.  With y = T^-1 F (the Toeplitz solve, already in
+// x), g = T^-1 e_0, h = T^-1 e_{N-1}, the Sherman-Morrison-Woodbury identity gives
+//   A^-1 F = y - c_0 g - c_1 h,   (c_0, c_1) = W (psi y_0, chi y_{N-1}),
+//   W = (I + [[psi g_0, psi h_0], [chi g_{N-1}, chi h_{N-1}]])^-1.
+// g is kept for its first Lg rows and h (indexed from the end) for its last Lh rows, where they
+// exceed the truncation threshold.  Pass 1 (ends = false) corrects rows 1..N-2 and leaves
+// rows 0 and N-1 -- which every CTA reads for c -- untouched; pass 2 (ends = true, one thread
+// per right-hand side) then corrects those two.  grid.y runs over the right-hand sides of a
+// series (x + y ldx).
+__global__ void k_corner(double* x, int64_t ldx, CornerArgs c, bool ends) {
+  double* xr = x + (int64_t)blockIdx.y * ldx;
+  const int64_t N = c.N;
+  const double y0 = xr[0], yn = xr[N - 1];
+  const double a = c.psi * y0, b = c.chi * yn;
+  const double c0 = fma(c.w00, a, c.w01 * b), c1 = fma(c.w10, a, c.w11 * b);
+  auto corr = [&](int64_t i) {
+    double v = xr[i];
+    if (i < c.Lg) v = fma(-c0, c.g[i], v);
+    const int64_t k = N - 1 - i;
+    if (k < c.Lh) v = fma(-c1, c.h[k], v);
+    return v;
+  };
+  if (ends) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const double v0 = corr(0), vn = (N > 1) ? corr(N - 1) : v0;
+      xr[0] = v0;
+      if (N > 1) xr[N - 1] = vn;
+    }
+    return;
+  }
+  // rows 1..N-2 inside [0, Lg) or [N - Lh, N): one range when the two meet
+  const int64_t lo1 = 1, hi1 = min(c.Lg, N - 1);
+  const int64_t lo2 = max(N - c.Lh, (int64_t)1), hi2 = N - 1;
+  const bool merged = lo2 <= hi1;
+  const int64_t n1 = merged ? (hi2 - lo1) : max(hi1 - lo1, (int64_t)0);
+  const int64_t n2 = merged ? 0 : max(hi2 - lo2, (int64_t)0);
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n1 + n2; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = (j < n1) ? lo1 + j : lo2 + (j - n1);
+    xr[i] = corr(i);
+  }
+}
+
+cudaError_t launch_corner(double* x, int64_t M, int64_t ldx, const CornerArgs& c, cudaStream_t st) {
+  if (c.N <= 0 || M <= 0) return cudaSuccess;
+  const int64_t rows = min(c.N, c.Lg + c.Lh);
+  const unsigned gx = (unsigned)max((int64_t)1, min((rows + 255) / 256, (int64_t)1184));
+  for (int64_t k0 = 0; k0 < M; k0 += 65535) {
+    const unsigned gy = (unsigned)min((int64_t)65535, M - k0);
+    k_corner<<<dim3(gx, gy), 256, 0, st>>>(x + k0 * ldx, ldx, c, false);
+    k_corner<<<dim3(1, gy), 32, 0, st>>>(x + k0 * ldx, ldx, c, true);
+  }
   return cudaGetLastError();
 }
 

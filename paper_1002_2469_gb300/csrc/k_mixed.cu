@@ -4,21 +4,21 @@
 namespace dich {
 
 template <int NT>
-static cudaError_t launch_one(int grid, size_t smem, cudaStream_t st, const WinArgs& a) {
+static cudaError_t launch_one(int grid, int grid_y, size_t smem, cudaStream_t st, const WinArgs& a) {
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_window2<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_window2<NT><<<grid, NT, smem, st>>>(a);
+  k_window2<NT><<<dim3(grid, grid_y), NT, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_window_mixed(int NT, int grid, size_t smem, cudaStream_t st, const WinArgs& a) {
+cudaError_t launch_window_mixed(int NT, int grid, size_t smem, cudaStream_t st, const WinArgs& a, int grid_y) {
   switch (NT) {
-    case 64: return launch_one<64>(grid, smem, st, a);
-    case 128: return launch_one<128>(grid, smem, st, a);
-    case 256: return launch_one<256>(grid, smem, st, a);
+    case 64: return launch_one<64>(grid, grid_y, smem, st, a);
+    case 128: return launch_one<128>(grid, grid_y, smem, st, a);
+    case 256: return launch_one<256>(grid, grid_y, smem, st, a);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -7,9 +7,10 @@
 
 namespace dich {
 
-// window kernel of width NT (64, 128 or 256) in the given form; returns the launch error
-cudaError_t launch_window_f64(int NT, int grid, size_t smem, cudaStream_t st, const WinArgs& a);
-cudaError_t launch_window_mixed(int NT, int grid, size_t smem, cudaStream_t st, const WinArgs& a);
+// window kernel of width NT (64, 128 or 256) in the given form, grid (grid, grid_y): grid_y
+// right-hand sides of a series (WinArgs::ldf, ldx); returns the launch error
+cudaError_t launch_window_f64(int NT, int grid, size_t smem, cudaStream_t st, const WinArgs& a, int grid_y = 1);
+cudaError_t launch_window_mixed(int NT, int grid, size_t smem, cudaStream_t st, const WinArgs& a, int grid_y = 1);
 
 // general path: first/last values of every block from per-block beta (global block scan)
 //   beta [2P] -> iface [2P]; scratch needs 6 * ceil(P / kScanChunk) doubles.
@@ -30,5 +31,18 @@ cudaError_t launch_adj_finalize(const double* part, const int32_t* sys_ids, cons
 cudaError_t launch_trivial(const SysPlan* plans, const int32_t* idx, int64_t nidx, const double* F,
                            double* x, const double* xf, const double* w, double* gt, int sys_offset,
                            cudaStream_t st);
+
+// quasi-Toeplitz corner data of a plan (eq. 21): g[Lg] = T^-1 e_0 (leading rows), h[Lh] = T^-1 e_{N-1}
+// (trailing rows, h[k] is row N-1-k), W = (I + K)^-1 of the Sherman-Morrison-Woodbury step
+struct CornerArgs {
+  int64_t N, Lg, Lh;
+  const double* g;
+  const double* h;
+  double psi, chi;
+  double w00, w01, w10, w11;
+};
+
+// x_k <- A^-1 F_k from y_k = T^-1 F_k (already in x_k = x + k ldx), k = 0..M-1: two kernels
+cudaError_t launch_corner(double* x, int64_t M, int64_t ldx, const CornerArgs& c, cudaStream_t st);
 
 }  // namespace dich

@@ -43,6 +43,7 @@ struct WinArgs {
   int32_t check_finite;
   int32_t n_smem;         // shared-memory rows (>= largest block size in the launch)
   int32_t sys_offset;     // added to the item's system index (adjoint twin records)
+  int64_t ldf, ldx;       // series: right-hand side blockIdx.y starts at F + y ldf, its solution at x + y ldx
 };
 
 // shared memory bytes for a window kernel of width NT and n_smem rows
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
 
   // ---------------------------------------------------------------- F -> smem (transposed, async)
   {
-    const double* src = A.F + off + row_lo;
+    const double* src = A.F + (int64_t)blockIdx.y * A.ldf + off + row_lo;
     int b = tid / n, i = tid - (tid / n) * n;
     const int db = NT / n, di = NT - (NT / n) * n;
     for (int j = tid; j < len; j += NT) {
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   {
     const int jlo = hl * n;
     const int jhi = min(len, (hl + nown) * n);
-    double* dst = A.x + off + row_lo;
+    double* dst = A.x + (int64_t)blockIdx.y * A.ldx + off + row_lo;
     int b = (jlo + tid) / n, i = (jlo + tid) - ((jlo + tid) / n) * n;
     const int db = NT / n, di = NT - (NT / n) * n;
     for (int j = jlo + tid; j < jhi; j += NT) {

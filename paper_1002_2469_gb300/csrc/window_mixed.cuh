@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(NT) k_window2(const WinArgs A) {
 
   // ---------------------------------------------------------------- F -> smem (transposed, async)
   {
-    const double* src = A.F + off + row_lo;
+    const double* src = A.F + (int64_t)blockIdx.y * A.ldf + off + row_lo;
     int b = tid / n, i = tid - (tid / n) * n;
     const int db = NT / n, di = NT - (NT / n) * n;
     for (int j = tid; j < len; j += NT) {
@@ -464,12 +464,9 @@ __global__ void __launch_bounds__(NT) k_window2(const WinArgs A) {
   {
     const int jlo = hl * n;
     const int jhi = min(len, (hl + nown) * n);
-    double* dst = A.x + off + row_lo;
-    int b = (jlo + tid) / n, i = (jlo + tid) - ((jlo + tid) / n) * n;
-    const int db = NT / n, di = NT - (NT / n) * n;
-    for (int j = jlo + tid; j < jhi; j += NT) {
-      const double dv = S[(size_t)i * LD + b];
-      __stcs(dst + j, dv);
+    double* dst = A.x + (int64_t)blockIdx.y * A.ldx + off + row_lo;
+    // per stored value: the non-finite flag and the adjoint's gradient partials
+    auto take = [&](double dv, int j) {
       if (A.check_finite && ((__double2hiint(dv) >> 20) & 0x7FF) == 0x7FF) bad = 1u;
       if (adj) {
         const int64_t r = row_lo + j;
@@ -478,11 +475,42 @@ __global__ void __launch_bounds__(NT) k_window2(const WinArgs A) {
         if (r > 0) gm = fma(dv, xr[-1], gm);
         if (r + 1 < N) gp = fma(dv, xr[1], gp);
       }
-      i += di;
-      b += db;
-      if (i >= n) {
-        i -= n;
-        ++b;
+    };
+    if ((n & 1) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0u) {
+      // even n: rows j, j + 1 (j even) are consecutive rows of one block -> one 16-byte store
+      int b = (jlo + 2 * tid) / n, i = (jlo + 2 * tid) - ((jlo + 2 * tid) / n) * n;
+      const int db = (2 * NT) / n, di = (2 * NT) - ((2 * NT) / n) * n;
+      for (int j = jlo + 2 * tid; j < jhi; j += 2 * NT) {
+        const double d0 = S[(size_t)i * LD + b];
+        if (j + 1 < jhi) {
+          const double d1 = S[(size_t)(i + 1) * LD + b];
+          __stcs(reinterpret_cast<double2*>(dst + j), make_double2(d0, d1));
+          take(d0, j);
+          take(d1, j + 1);
+        } else {
+          __stcs(dst + j, d0);
+          take(d0, j);
+        }
+        i += di;
+        b += db;
+        if (i >= n) {
+          i -= n;
+          ++b;
+        }
+      }
+    } else {
+      int b = (jlo + tid) / n, i = (jlo + tid) - ((jlo + tid) / n) * n;
+      const int db = NT / n, di = NT - (NT / n) * n;
+      for (int j = jlo + tid; j < jhi; j += NT) {
+        const double dv = S[(size_t)i * LD + b];
+        __stcs(dst + j, dv);
+        take(dv, j);
+        i += di;
+        b += db;
+        if (i >= n) {
+          i -= n;
+          ++b;
+        }
       }
     }
   }

@@ -18,8 +18,8 @@ from ._lib import (FLAG_CHECK_FINITE, FLAG_FORCE_GENERAL, PREC_AUTO, PREC_F64, P
                    check, make_opts)
 
 __all__ = [
-    "dichotomy_plan", "dichotomy_plan_info", "dichotomy_plan_workspace_bytes", "dichotomy_plan_bind",
-    "dichotomy_solve", "dichotomy_adjoint", "dichotomy_status", "dichotomy_destroy",
+    "dichotomy_plan", "dichotomy_plan_quasi", "dichotomy_plan_info", "dichotomy_plan_workspace_bytes", "dichotomy_plan_bind",
+    "dichotomy_solve", "dichotomy_solve_series", "dichotomy_adjoint", "dichotomy_status", "dichotomy_destroy",
     "dichotomy_batch_prepare", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
     "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
     "dichotomy_batch_destroy", "Plan", "Batch", "solve", "DichotomySolve", "DichotomySolveBatched",
@@ -55,6 +55,16 @@ def dichotomy_plan(t_m1: float, t_0: float, t_1: float, N: int, opts=None) -> ct
     return h
 
 
+def dichotomy_plan_quasi(t_m1: float, t_0: float, t_1: float, psi: float, chi: float, N: int,
+                         opts=None) -> ctypes.c_void_p:
+    """Plan for the quasi-Toeplitz matrix of eq. 21 (t_0 + psi in the first row, t_0 + chi in the last)."""
+    h = ctypes.c_void_p()
+    o = make_opts() if opts is None else opts
+    check(_lib.load().dichotomy_plan_quasi(float(t_m1), float(t_0), float(t_1), float(psi), float(chi), int(N),
+                                          ctypes.byref(o), ctypes.byref(h)), "dichotomy_plan_quasi")
+    return h
+
+
 def dichotomy_plan_info(plan) -> dict:
     info = _lib.dich_plan_info()
     check(_lib.load().dichotomy_plan_info(plan, ctypes.byref(info)), "dichotomy_plan_info")
@@ -77,6 +87,25 @@ def dichotomy_plan_bind(plan, workspace: torch.Tensor, stream=None) -> None:
 
 def dichotomy_solve(plan, F: torch.Tensor, x: torch.Tensor, stream=None) -> None:
     check(_lib.load().dichotomy_solve(plan, _dev(F, "F"), _dev(x, "x"), _stream(stream)), "dichotomy_solve")
+
+
+def _dev_rows(t: torch.Tensor, name: str):
+    """Pointer and row stride (in elements) of a 2-D float64 CUDA tensor with unit column stride."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor (the solver has no CPU path)")
+    if t.dtype != torch.float64 or t.dim() != 2 or (t.shape[1] > 1 and t.stride(1) != 1):
+        raise TypeError(f"{name} must be a 2-D float64 tensor with contiguous rows")
+    return ctypes.c_void_p(t.data_ptr()), int(t.stride(0))
+
+
+def dichotomy_solve_series(plan, F: torch.Tensor, x: torch.Tensor, stream=None) -> None:
+    """x[k] = T^-1 F[k] for every row k of the [M, N] tensors F and x (rows may be strided)."""
+    pF, ldf = _dev_rows(F, "F")
+    px, ldx = _dev_rows(x, "x")
+    if F.shape != x.shape:
+        raise ValueError("F and x must have the same shape")
+    check(_lib.load().dichotomy_solve_series(plan, int(F.shape[0]), pF, ldf, px, ldx, _stream(stream)),
+          "dichotomy_solve_series")
 
 
 def dichotomy_adjoint(plan, w: torch.Tensor, x: torch.Tensor, gF: torch.Tensor, gt: torch.Tensor,
@@ -163,15 +192,20 @@ def dichotomy_batch_destroy(batch) -> None:
 
 # ------------------------------------------------------------------ owning wrappers
 class Plan:
-    """A bound single-system plan: T = tridiag{t_m1, t_0, t_1} of order N on a CUDA device."""
+    """A bound single-system plan: T = tridiag{t_m1, t_0, t_1} of order N on a CUDA device (with
+    psi, chi: the quasi-Toeplitz matrix of eq. 21, t_0 + psi in the first row, t_0 + chi in the last)."""
 
     def __init__(self, t_m1, t_0, t_1, N, block_size=0, precision=PREC_F64, threads=0, flags=0, trunc_eps=0.0,
-                 device=None, stream=None):
+                 device=None, stream=None, psi=0.0, chi=0.0):
         self.t = (float(t_m1), float(t_0), float(t_1))
         self.N = int(N)
+        self.corners = (float(psi), float(chi))
         self._h = None
         opts = make_opts(block_size, precision, threads, flags, trunc_eps)
-        self._h = dichotomy_plan(t_m1, t_0, t_1, N, opts)
+        if psi or chi:
+            self._h = dichotomy_plan_quasi(t_m1, t_0, t_1, psi, chi, N, opts)
+        else:
+            self._h = dichotomy_plan(t_m1, t_0, t_1, N, opts)
         self.info = dichotomy_plan_info(self._h)
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.workspace = torch.empty(max(1, self.info["workspace_bytes"]), dtype=torch.uint8, device=dev)
@@ -184,6 +218,12 @@ class Plan:
     def solve(self, F: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         x = torch.empty_like(F) if out is None else out
         dichotomy_solve(self._h, F, x, stream)
+        return x
+
+    def solve_series(self, F: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Every row of F ([M, N]) solved with this plan (a series with a constant matrix)."""
+        x = torch.empty_like(F) if out is None else out
+        dichotomy_solve_series(self._h, F, x, stream)
         return x
 
     def adjoint(self, w: torch.Tensor, x: torch.Tensor, stream=None):

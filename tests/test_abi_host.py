@@ -177,3 +177,32 @@ def test_unbound_and_null_arguments_are_rejected_without_a_gpu():
     finally:
         lib.dichotomy_destroy(h)
     assert lib.dichotomy_strerror(2).decode().startswith("matrix is not")
+
+
+def test_quasi_plan_validation_and_series_arguments_without_a_gpu():
+    from paper_1002_2469_gb300 import _lib as L
+    lib = L.load()
+    o = L.make_opts()
+
+    def quasi(t, psi, chi, N):
+        h = ctypes.c_void_p()
+        rc = lib.dichotomy_plan_quasi(t[0], t[1], t[2], psi, chi, N, ctypes.byref(o), ctypes.byref(h))
+        if rc == 0:
+            lib.dichotomy_destroy(h)
+        return rc
+
+    t = (-1.0, 2.5, -1.0)
+    assert quasi(t, -1.0, -1.0, 1000) == 0          # Neumann-type end rows (1.5, -1): dominant
+    assert quasi(t, -2.0, 0.0, 1000) == 2           # |t_0 + psi| < |t_1|: first row not dominant
+    assert quasi(t, 0.0, -2.0, 1000) == 2           # last row not dominant
+    assert quasi(t, -1.0, -1.5, 1) == 3             # one row: t_0 + psi + chi = 0
+    assert quasi(t, float("nan"), 0.0, 10) == 1
+    assert quasi(t, 0.0, 0.0, 1000) == 0            # plain Toeplitz
+    h = ctypes.c_void_p()
+    assert lib.dichotomy_plan_quasi(*t, 0.3, 0.2, 100, ctypes.byref(o), ctypes.byref(h)) == 0
+    try:
+        assert lib.dichotomy_adjoint(h, None, None, None, None, None) == 11   # DICH_ERR_UNSUPPORTED
+        assert lib.dichotomy_solve_series(h, 2, None, 100, None, 100, None) == 8   # unbound
+        assert lib.dichotomy_solve_series(h, -1, None, 100, None, 100, None) == 1  # M < 0
+    finally:
+        lib.dichotomy_destroy(h)

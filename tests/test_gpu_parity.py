@@ -172,6 +172,93 @@ def test_mixed_window_classes(D):
             assert rel(x[sl], ref[sl]) < 1e-11, (threads, bs, k)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("t,N", [((-1.2, 2.5, -0.8), 100000), ((-1.0, 4.0, -1.0), 3000), ((-1.0, 2.001, -1.0), 60000),
+                                 ((-0.5, 3.0, 0.25), 2), ((-1.0, 4.0, -1.0), 1)])
+def test_series_constant_matrix(D, t, N, prec):
+    """A series with one matrix (eq. 2): every row of F solved with one plan, rows strided;
+    each equals the single-system solve bit for bit and the oracle to the tolerance."""
+    M = 5
+    rng = np.random.default_rng(N + prec)
+    F = rng.standard_normal((M, N))
+    plan = D.Plan(*t, N, precision=prec)
+    big = torch.zeros((M, N + 3), dtype=torch.float64, device="cuda")
+    big[:, :N] = torch.from_numpy(F).cuda()
+    X = torch.full((M, N + 7), float("nan"), dtype=torch.float64, device="cuda")
+    D.dichotomy_solve_series(plan.handle, big[:, :N], X[:, :N])
+    assert plan.status() == 0
+    Xh = X.cpu().numpy()
+    assert np.all(np.isnan(Xh[:, N:]))                 # nothing written between the rows
+    for k in range(M):
+        single = plan.solve(torch.from_numpy(F[k]).cuda()).cpu().numpy()
+        assert np.array_equal(Xh[k, :N], single)
+        assert rel(Xh[k, :N], oracle.thomas(t, F[k])) < TOL
+
+
+def test_series_many_right_hand_sides(D):
+    """More right-hand sides than one launch's grid.y (65535): the series is split in launches."""
+    t, N, M = (-1.2, 2.5, -0.8), 40, 70001
+    F = torch.from_numpy(np.random.default_rng(5).standard_normal((M, N))).cuda()
+    plan = D.Plan(*t, N, precision=D.PREC_AUTO)
+    X = plan.solve_series(F)
+    assert plan.status() == 0
+    for k in (0, 1, 65534, 65535, 65536, M - 1):
+        Fk = F[k].cpu().numpy()
+        assert rel(X[k].cpu().numpy(), oracle.thomas(t, Fk)) < TOL
+
+
+def test_series_arguments(D):
+    plan = D.Plan(-1.0, 4.0, -1.0, 100)
+    F = torch.zeros((3, 100), dtype=torch.float64, device="cuda")
+    x = torch.zeros((3, 100), dtype=torch.float64, device="cuda")
+    lib = D._lib.load()
+    P = D._lib.ctypes.c_void_p
+    st = P(torch.cuda.current_stream().cuda_stream)
+    assert lib.dichotomy_solve_series(plan.handle, -1, P(F.data_ptr()), 100, P(x.data_ptr()), 100, st) == 1
+    assert lib.dichotomy_solve_series(plan.handle, 3, P(F.data_ptr()), 99, P(x.data_ptr()), 100, st) == 1
+    assert lib.dichotomy_solve_series(plan.handle, 3, P(F.data_ptr()), 100, P(F.data_ptr() + 800), 100, st) == 7
+    assert lib.dichotomy_solve_series(plan.handle, 0, P(F.data_ptr()), 100, P(x.data_ptr()), 100, st) == 0
+
+
+QUASI = [((-1.0, 2.5, -1.0), -1.0, -1.0),      # Neumann-type ends
+         ((-1.2, 2.5, -0.8), 0.7, -0.3),       # Robin-type, non-symmetric
+         ((0.7, 2.5, -1.1), -0.5, 1.5),
+         ((-1.0, 2.001, -1.0), -0.9, 0.0),     # weakly dominant: long corner columns
+         ((-1.0, 4.0, -1.0), 2.0, -2.5)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("t,psi,chi", QUASI)
+@pytest.mark.parametrize("N", [2, 3, 50, 4097, 300001])
+def test_quasi_toeplitz_eq21(D, t, psi, chi, N, prec):
+    """eq. 21 (t_0 + psi in the first row, t_0 + chi in the last) against the oracle's Thomas
+    on the same matrix."""
+    F = np.random.default_rng(N).standard_normal(N)
+    plan = D.Plan(*t, N, precision=prec, psi=psi, chi=chi)
+    x = plan.solve(torch.from_numpy(F).cuda()).cpu().numpy()
+    assert plan.status() == 0
+    assert rel(x, oracle.thomas_quasi(t, psi, chi, F)) < TOL, plan.info
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_quasi_toeplitz_series_and_paths(D, prec):
+    """Quasi-Toeplitz plans through the series entry point, on the halo and the general path."""
+    t, psi, chi, N, M = (-1.2, 2.5, -0.8), -0.8, 0.4, 70001, 3
+    F = np.random.default_rng(9).standard_normal((M, N))
+    for flags in (0, 1):
+        plan = D.Plan(*t, N, precision=prec, psi=psi, chi=chi, flags=flags)
+        X = plan.solve_series(torch.from_numpy(F).cuda()).cpu().numpy()
+        assert plan.status() == 0
+        for k in range(M):
+            assert rel(X[k], oracle.thomas_quasi(t, psi, chi, F[k])) < TOL, (flags, k)
+
+
+def test_quasi_one_row(D):
+    plan = D.Plan(-1.0, 4.0, -1.0, 1, psi=0.5, chi=0.25)
+    x = plan.solve(torch.tensor([3.0], dtype=torch.float64, device="cuda")).cpu().numpy()
+    assert x[0] == 3.0 / 4.75
+
+
 def test_trivial_sizes(D):
     for N in (0, 1, 2):
         F = np.arange(1, N + 1, dtype=np.float64)

@@ -302,3 +302,44 @@ def test_planted_mistakes_are_caught(tmp_path):
     assert not pins_fail(oracle.build_variant(0, str(tmp_path)))
     for k in range(1, 7):
         assert pins_fail(oracle.build_variant(k, str(tmp_path))), f"mutant {k} slipped through"
+
+
+# ------------------------------------------------------------------ general and quasi-Toeplitz (eq. 21)
+@pytest.mark.parametrize("N", [1, 2, 3, 17, 300])
+def test_tridiag_vs_dense_lu(N):
+    """The general Thomas solve against numpy's dense LU of the same matrix, built row by row."""
+    rng = np.random.default_rng(N)
+    sub, sup = rng.uniform(-1, 1, N), rng.uniform(-1, 1, N)
+    dia = (np.abs(sub) + np.abs(sup) + rng.uniform(0.1, 2.0, N)) * rng.choice([-1.0, 1.0], N)
+    A = np.zeros((N, N))
+    for i in range(N):
+        A[i, i] = dia[i]
+        if i > 0:
+            A[i, i - 1] = sub[i]
+        if i < N - 1:
+            A[i, i + 1] = sup[i]
+    F = rng.standard_normal(N)
+    assert rel(oracle.thomas_tridiag(sub, dia, sup, F), np.linalg.solve(A, F)) < 1e-14
+
+
+def test_tridiag_constant_arrays_equal_toeplitz():
+    t = (-1.2, 2.5, -0.8)
+    F = np.random.default_rng(1).standard_normal(5000)
+    n = F.size
+    x = oracle.thomas_tridiag(np.full(n, t[0]), np.full(n, t[1]), np.full(n, t[2]), F)
+    assert np.array_equal(x, oracle.thomas(t, F))
+    assert np.array_equal(oracle.thomas_quasi(t, 0.0, 0.0, F), oracle.thomas(t, F))
+
+
+@pytest.mark.parametrize("t,psi,chi", [((-1.0, 2.5, -1.0), -1.0, -1.0),     # Neumann-type rows [1.5, -1]
+                                       ((-1.2, 2.5, -0.8), 0.7, -0.3),
+                                       ((-1.0, 4.0, -1.0), 2.0, 0.0),
+                                       ((0.7, 2.5, -1.1), -0.5, 1.5)])
+def test_quasi_toeplitz_eq21_vs_dense(t, psi, chi):
+    """eq. 21: the Toeplitz matrix with t_0 + psi in the first and t_0 + chi in the last row."""
+    N = 64
+    A = np.diag(np.full(N, t[1])) + np.diag(np.full(N - 1, t[0]), -1) + np.diag(np.full(N - 1, t[2]), 1)
+    A[0, 0] = t[1] + psi
+    A[N - 1, N - 1] = t[1] + chi
+    F = np.random.default_rng(2).standard_normal(N)
+    assert rel(oracle.thomas_quasi(t, psi, chi, F), np.linalg.solve(A, F)) < 1e-14
