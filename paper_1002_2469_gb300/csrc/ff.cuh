@@ -129,6 +129,55 @@ __device__ __forceinline__ void ff_fma_acc2(float2 ch, float2 cl, float2 vh, flo
   xh = s;
 }
 
+// ---------------------------------------------------------------- packed float-float pairs
+// ff2 holds two float-float values, one per block of a thread's pair (lane x: block 2t, lane y:
+// block 2t+1), so the per-block quantities and the tree advance both blocks -- or the prefix
+// and the suffix scan -- with one f32x2 instruction per step.  Same arithmetic as ffv.
+struct ff2 {
+  float2 h, l;
+};
+__device__ __forceinline__ ff2 ff2_make(float2 h, float2 l) {  // FastTwoSum renormalisation
+  const float2 s = add2(h, l);
+  return ff2{s, sub2(l, sub2(s, h))};
+}
+__device__ __forceinline__ ff2 ff2_pair(ffv a, ffv b) { return ff2{make_float2(a.h, b.h), make_float2(a.l, b.l)}; }
+__device__ __forceinline__ ffv ff2_x(const ff2& a) { return ffv{a.h.x, a.l.x}; }
+__device__ __forceinline__ ffv ff2_y(const ff2& a) { return ffv{a.h.y, a.l.y}; }
+__device__ __forceinline__ ff2 ff2_bcast(ffv a) { return ff2{f2(a.h), f2(a.l)}; }
+__device__ __forceinline__ ff2 ff2_add(const ff2& a, const ff2& b) {
+  const float2 s = add2(a.h, b.h);
+  const float2 bb = sub2(s, a.h);
+  const float2 e = add2(sub2(a.h, sub2(s, bb)), sub2(b.h, bb));
+  return ff2_make(s, add2(e, add2(a.l, b.l)));
+}
+__device__ __forceinline__ ff2 ff2_sub(const ff2& a, const ff2& b) {
+  const float2 s = sub2(a.h, b.h);
+  const float2 bb = sub2(s, a.h);
+  const float2 e = sub2(sub2(a.h, sub2(s, bb)), add2(b.h, bb));
+  return ff2_make(s, add2(e, sub2(a.l, b.l)));
+}
+__device__ __forceinline__ ff2 ff2_mul(const ff2& a, const ff2& b) {
+  const float2 p = mul2(a.h, b.h);
+  float2 e = fma2(a.h, b.h, make_float2(-p.x, -p.y));
+  e = fma2(a.h, b.l, fma2(a.l, b.h, e));
+  return ff2_make(p, e);
+}
+// a * b + c
+__device__ __forceinline__ ff2 ff2_fma(const ff2& a, const ff2& b, const ff2& c) {
+  const float2 p = mul2(a.h, b.h);
+  const float2 e = fma2(a.h, b.h, make_float2(-p.x, -p.y));
+  const float2 s = add2(p, c.h);
+  const float2 bb = sub2(s, p);
+  const float2 f = add2(sub2(p, sub2(s, bb)), sub2(c.h, bb));
+  float2 lo = add2(add2(e, f), c.l);
+  lo = fma2(a.h, b.l, fma2(a.l, b.h, lo));
+  return ff2_make(s, lo);
+}
+// per-lane choice: lane x from a if px else from b, lane y likewise
+__device__ __forceinline__ ff2 ff2_sel(bool px, bool py, const ff2& a, const ff2& b) {
+  return ff2{make_float2(px ? a.h.x : b.h.x, py ? a.h.y : b.h.y), make_float2(px ? a.l.x : b.l.x, py ? a.l.y : b.l.y)};
+}
+
 // rare paths kept out of line so that their FP64 operations are not if-converted into the
 // per-element code (GB300's FP64 pipe is ~70x slower than FP32)
 static __device__ __noinline__ double rescale_subnormal(double d) { return d * 18446744073709551616.0; }  // * 2^64

@@ -91,10 +91,9 @@ __device__ __forceinline__ void sweep_pair(double* S, int tid, int nrow, int nb0
 template <int LD, bool GUARD, bool FAST>
 __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow, int nb0, int nb1, bool last0,
                                              bool last1, int n, int nlast, int Lv, int Lw, const float2* tv,
-                                             const float2* tw, const float2* tvl, const float2* twl, ffv cL0,
-                                             ffv cL1, ffv cR0, ffv cR1, int wscale) {
-  const float2 clh = make_float2(cL0.h, cL1.h), cll = make_float2(cL0.l, cL1.l);
-  const float2 crh = make_float2(cR0.h, cR1.h), crl = make_float2(cR0.l, cR1.l);
+                                             const float2* tw, const float2* tvl, const float2* twl, const ff2& cL,
+                                             const ff2& cR, int wscale) {
+  const float2 clh = cL.h, cll = cL.l, crh = cR.h, crl = cR.l;
   const FastK fk = fast_k(wscale);
   if (!GUARD) {
     // both blocks full size: one spike table, one row index for both
@@ -158,7 +157,7 @@ __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow, int n
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) k_window2(const WinArgs A) {
+__global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   constexpr int NW = NT / 32;
   constexpr int WB = 2 * NT;       // window blocks
   constexpr int LD = 2 * NT + 2;   // shared row stride in doubles (even: 16-byte pairs)
@@ -308,26 +307,24 @@ __global__ void __launch_bounds__(NT) k_window2(const WinArgs A) {
   else
     sweep_pair<LD, true, false>(S, tid, nrow, nb0, nb1, wscale, pp, Xh, Xl);
 
+  // Per-block quantities and the tree advance the thread's two blocks (or the prefix and the
+  // suffix scan) together in packed float-float pairs (ff2: lane x = block 2t, lane y = block
+  // 2t+1); inactive blocks enter as zero values and identity maps.
+  const ff2 zero2{f2(0.f), f2(0.f)}, one2{f2(1.f), f2(0.f)};
+
   // block-end quantities: xp(-1) = g ib X_0, alpha = xp_0 - xp(-1) v_0, omega = xp_{n-1} - xp(-1) v_{n-1}
-  const ffv gib = ffv{pp->gib_h, pp->gib_l};
-  ffv xm0 = ff_zero(), xm1 = ff_zero(), al0 = ff_zero(), al1 = ff_zero(), om0 = ff_zero(), om1 = ff_zero();
-  if (act0) {
-    const ffv v0 = last0 ? ffv{pp->v0l_h, pp->v0l_l} : ffv{pp->v0_h, pp->v0_l};
-    const ffv ve = last0 ? ffv{pp->vendl_h, pp->vendl_l} : ffv{pp->vend_h, pp->vend_l};
-    xm0 = ff_mul(gib, ff_make(Xh.x, Xl.x));
+  ff2 xm, al, om;
+  {
+    const ffv v0f{pp->v0_h, pp->v0_l}, v0l{pp->v0l_h, pp->v0l_l}, vef{pp->vend_h, pp->vend_l},
+        vel{pp->vendl_h, pp->vendl_l};
+    const ff2 v0 = ff2_pair(last0 ? v0l : v0f, last1 ? v0l : v0f);
+    const ff2 ve = ff2_pair(last0 ? vel : vef, last1 ? vel : vef);
+    xm = ff2_mul(ff2_bcast(ffv{pp->gib_h, pp->gib_l}), ff2_make(Xh, Xl));
     const float4 q0 = *reinterpret_cast<const float4*>(S + 2 * tid);
-    const float4 qe = *reinterpret_cast<const float4*>(S + (size_t)(nb0 - 1) * LD + 2 * tid);
-    al0 = ff_sub(ff_make(q0.x, q0.z), ff_mul(xm0, v0));
-    om0 = ff_sub(ff_make(qe.x, qe.z), ff_mul(xm0, ve));
-  }
-  if (act1) {
-    const ffv v0 = last1 ? ffv{pp->v0l_h, pp->v0l_l} : ffv{pp->v0_h, pp->v0_l};
-    const ffv ve = last1 ? ffv{pp->vendl_h, pp->vendl_l} : ffv{pp->vend_h, pp->vend_l};
-    xm1 = ff_mul(gib, ff_make(Xh.y, Xl.y));
-    const float4 q0 = *reinterpret_cast<const float4*>(S + 2 * tid);
-    const float4 qe = *reinterpret_cast<const float4*>(S + (size_t)(nb1 - 1) * LD + 2 * tid);
-    al1 = ff_sub(ff_make(q0.y, q0.w), ff_mul(xm1, v0));
-    om1 = ff_sub(ff_make(qe.y, qe.w), ff_mul(xm1, ve));
+    const float4 qe0 = *reinterpret_cast<const float4*>(S + (size_t)max(nb0 - 1, 0) * LD + 2 * tid);
+    const float4 qe1 = *reinterpret_cast<const float4*>(S + (size_t)max(nb1 - 1, 0) * LD + 2 * tid);
+    al = ff2_sub(ff2_make(make_float2(q0.x, q0.y), make_float2(q0.z, q0.w)), ff2_mul(xm, v0));
+    om = ff2_sub(ff2_make(make_float2(qe0.x, qe1.y), make_float2(qe0.z, qe1.w)), ff2_mul(xm, ve));
   }
 
   // ---------------------------------------------------------------- beta (eq. 16)
@@ -338,25 +335,23 @@ __global__ void __launch_bounds__(NT) k_window2(const WinArgs A) {
   };
   const int64_t r0 = act0 ? rec_of(mb0) : pp->o_bcmf;
   const int64_t r1 = act1 ? rec_of(mb1) : pp->o_bcmf;
-  ffv bL0 = ff_zero(), bR0 = ff_zero(), bL1 = ff_zero(), bR1 = ff_zero();
-  if (act0) {
-    bL0 = O::fma(O::bc(tab, r0, BC_M00), al0, O::mul(O::bc(tab, r0, BC_M01), om0));
-    bR0 = O::fma(O::bc(tab, r0, BC_M10), al0, O::mul(O::bc(tab, r0, BC_M11), om0));
-  }
-  if (act1) {
-    bL1 = O::fma(O::bc(tab, r1, BC_M00), al1, O::mul(O::bc(tab, r1, BC_M01), om1));
-    bR1 = O::fma(O::bc(tab, r1, BC_M10), al1, O::mul(O::bc(tab, r1, BC_M11), om1));
-  }
+  const float2* tf = reinterpret_cast<const float2*>(tab);
+  auto bc2 = [&](int j) {  // coefficient j of both blocks' records
+    const float2 c0 = tf[r0 + j], c1 = tf[r1 + j];
+    return ff2_make(make_float2(c0.x, c1.x), make_float2(c0.y, c1.y));
+  };
+  const ff2 bL = ff2_sel(act0, act1, ff2_fma(bc2(BC_M00), al, ff2_mul(bc2(BC_M01), om)), zero2);
+  const ff2 bR = ff2_sel(act0, act1, ff2_fma(bc2(BC_M10), al, ff2_mul(bc2(BC_M11), om)), zero2);
 
   if (A.mode == MODE_BETA) {  // general path: beta leaves the window as unscaled FP64
     const double dn = pow2i(-wscale);
     if (act0) {
-      A.beta[2 * mb0] = ff_to_double(bL0) * dn;
-      A.beta[2 * mb0 + 1] = ff_to_double(bR0) * dn;
+      A.beta[2 * mb0] = ff_to_double(ff2_x(bL)) * dn;
+      A.beta[2 * mb0 + 1] = ff_to_double(ff2_x(bR)) * dn;
     }
     if (act1) {
-      A.beta[2 * mb1] = ff_to_double(bL1) * dn;
-      A.beta[2 * mb1 + 1] = ff_to_double(bR1) * dn;
+      A.beta[2 * mb1] = ff_to_double(ff2_y(bL)) * dn;
+      A.beta[2 * mb1 + 1] = ff_to_double(ff2_y(bR)) * dn;
     }
     return;
   }
@@ -364,26 +359,29 @@ __global__ void __launch_bounds__(NT) k_window2(const WinArgs A) {
   ffv XL0 = ff_zero(), XR0 = ff_zero(), XL1 = ff_zero(), XR1 = ff_zero();
   if (A.mode == MODE_FULL) {
     // ------------------------------------------------------------ dichotomy tree (a2)
-    const ffv a0 = act0 ? O::bc(tab, r0, BC_A) : ff_one(), pb0 = act0 ? O::mul(O::bc(tab, r0, BC_B), bR0) : ff_zero();
-    const ffv a1 = act1 ? O::bc(tab, r1, BC_A) : ff_one(), pb1 = act1 ? O::mul(O::bc(tab, r1, BC_B), bR1) : ff_zero();
-    const ffv c0 = act0 ? O::bc(tab, r0, BC_C) : ff_one(), qb0 = act0 ? O::mul(O::bc(tab, r0, BC_D), bL0) : ff_zero();
-    const ffv c1 = act1 ? O::bc(tab, r1, BC_C) : ff_one(), qb1 = act1 ? O::mul(O::bc(tab, r1, BC_D), bL1) : ff_zero();
-    // the thread's composite maps: prefix = block 1 after block 0; suffix = block 0 after block 1
-    ffv pa = O::mul(a1, a0), pb = O::fma(a1, pb0, pb1);
-    ffv qa = O::mul(c0, c1), qb = O::fma(c0, qb1, qb0);
+    // block maps: prefix A -> a A + b beta^R, suffix B -> c B + d beta^L
+    const ff2 av = ff2_sel(act0, act1, bc2(BC_A), one2), cv = ff2_sel(act0, act1, bc2(BC_C), one2);
+    const ff2 pbv = ff2_mul(bc2(BC_B), bR), qbv = ff2_mul(bc2(BC_D), bL);
+    // the thread's composite maps, lane x the prefix (block 1 after block 0), lane y the suffix
+    // (block 0 after block 1): (a1 a0, c0 c1) and (a1 pb0 + pb1, c0 qb1 + qb0)
+    const ff2 m1{make_float2(av.h.y, cv.h.x), make_float2(av.l.y, cv.l.x)};
+    ff2 Sv = ff2_mul(m1, ff2{make_float2(av.h.x, cv.h.y), make_float2(av.l.x, cv.l.y)});
+    ff2 Tv = ff2_fma(m1, ff2{make_float2(pbv.h.x, qbv.h.y), make_float2(pbv.l.x, qbv.l.y)},
+                     ff2{make_float2(pbv.h.y, qbv.h.x), make_float2(pbv.l.y, qbv.l.x)});
+    // warp scans: the prefix from lane - d, the suffix from lane + d; identity maps past the ends
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      const ffv ya = O::up(pa, d), yb = O::up(pb, d);
-      const ffv za = O::down(qa, d), zb = O::down(qb, d);
-      if (lane >= d) {
-        pb = O::fma(pa, yb, pb);
-        pa = O::mul(pa, ya);
-      }
-      if (lane + d < 32) {
-        qb = O::fma(qa, zb, qb);
-        qa = O::mul(qa, za);
-      }
+      const float yah = __shfl_up_sync(0xffffffffu, Sv.h.x, d), yal = __shfl_up_sync(0xffffffffu, Sv.l.x, d);
+      const float ybh = __shfl_up_sync(0xffffffffu, Tv.h.x, d), ybl = __shfl_up_sync(0xffffffffu, Tv.l.x, d);
+      const float zah = __shfl_down_sync(0xffffffffu, Sv.h.y, d), zal = __shfl_down_sync(0xffffffffu, Sv.l.y, d);
+      const float zbh = __shfl_down_sync(0xffffffffu, Tv.h.y, d), zbl = __shfl_down_sync(0xffffffffu, Tv.l.y, d);
+      const bool up = lane >= d, dn = lane + d < 32;
+      const ff2 Ya{make_float2(up ? yah : 1.f, dn ? zah : 1.f), make_float2(up ? yal : 0.f, dn ? zal : 0.f)};
+      const ff2 Yb{make_float2(up ? ybh : 0.f, dn ? zbh : 0.f), make_float2(up ? ybl : 0.f, dn ? zbl : 0.f)};
+      Tv = ff2_fma(Sv, Yb, Tv);
+      Sv = ff2_mul(Sv, Ya);
     }
+    const ffv pa = ff2_x(Sv), pb = ff2_x(Tv), qa = ff2_y(Sv), qb = ff2_y(Tv);
     if (lane == 31) {
       swv[wid] = pa;
       swv[NW + wid] = pb;
@@ -406,17 +404,21 @@ __global__ void __launch_bounds__(NT) k_window2(const WinArgs A) {
     ffv Aw = ff_zero(), Bw = ff_zero();  // zero coupling enters at both window ends
     for (int w = 0; w < wid; ++w) Aw = O::fma(swv[w], Aw, swv[NW + w]);
     for (int w = NW - 1; w > wid; --w) Bw = O::fma(swv[2 * NW + w], Bw, swv[3 * NW + w]);
-    const ffv A0 = O::fma(ea, Aw, eb);                       // entering block 0
-    const ffv A1 = O::fma(a0, A0, pb0);                      // entering block 1
-    const ffv B1 = O::fma(fa, Bw, fb);                       // beyond block 1
-    const ffv B0 = O::fma(c1, B1, qb1);                      // beyond block 0
+    // (A entering block 0, B beyond block 1), then (A entering block 1, B beyond block 0)
+    const ff2 E = ff2_fma(ff2_pair(ea, fa), ff2_pair(Aw, Bw), ff2_pair(eb, fb));
+    const ff2 G = ff2_fma(ff2_pair(ff2_x(av), ff2_y(cv)), E, ff2_pair(ff2_x(pbv), ff2_y(qbv)));
+    const ff2 Av{make_float2(E.h.x, G.h.x), make_float2(E.l.x, G.l.x)};   // (A_0, A_1)
+    const ff2 Bv{make_float2(G.h.y, E.h.y), make_float2(G.l.y, E.l.y)};   // (B_0, B_1)
+    // first/last values of both blocks (eq. 18)
+    const ff2 xs = ff2_add(ff2_fma(bc2(BC_TL), Bv, bL), Av);
+    const ff2 xe = ff2_fma(bc2(BC_TR), Av, ff2_add(bR, Bv));
     if (act0) {
-      sxs[b0] = O::add(O::fma(O::bc(tab, r0, BC_TL), B0, bL0), A0);
-      sxe[b0] = O::fma(O::bc(tab, r0, BC_TR), A0, O::add(bR0, B0));
+      sxs[b0] = ff2_x(xs);
+      sxe[b0] = ff2_x(xe);
     }
     if (act1) {
-      sxs[b1] = O::add(O::fma(O::bc(tab, r1, BC_TL), B1, bL1), A1);
-      sxe[b1] = O::fma(O::bc(tab, r1, BC_TR), A1, O::add(bR1, B1));
+      sxs[b1] = ff2_y(xs);
+      sxe[b1] = ff2_y(xe);
     }
     __syncthreads();
     if (act0) {
@@ -444,16 +446,16 @@ __global__ void __launch_bounds__(NT) k_window2(const WinArgs A) {
   }
 
   // ---------------------------------------------------------------- correction (a3), per column
-  const ffv cL0 = ff_sub(XL0, xm0), cL1 = ff_sub(XL1, xm1);
+  const ff2 cL = ff2_sub(ff2_pair(XL0, XL1), xm), cR = ff2_pair(XR0, XR1);
   if (full && fast)
-    correct_pair<LD, false, true>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL0, cL1,
-                                  XR0, XR1, wscale);
+    correct_pair<LD, false, true>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL, cR,
+                                  wscale);
   else if (full)
-    correct_pair<LD, false, false>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL0,
-                                   cL1, XR0, XR1, wscale);
+    correct_pair<LD, false, false>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL, cR,
+                                   wscale);
   else if (nrow > 0)
-    correct_pair<LD, true, false>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL0, cL1,
-                                  XR0, XR1, wscale);
+    correct_pair<LD, true, false>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL, cR,
+                                  wscale);
   __syncthreads();
 
   // ---------------------------------------------------------------- coalesced store of the own rows
