@@ -16,6 +16,10 @@ over ranks.
 
 `--impl reference` times the CPU oracle (the sequential FP64 Thomas algorithm, one core)
 on the same workload as the reference arm.
+
+The CPU leg: the oracle (test infrastructure under oracle/) is called only for the reference
+solutions of the error columns and for the cpu_baseline / reference timings, always after the
+GPU work it checks; no timed GPU region and no library call goes through it.
 """
 from __future__ import annotations
 
@@ -149,13 +153,21 @@ def barrier(world):
 
 
 def max_over_ranks(v: float, world: int) -> float:
+    """The largest v over the ranks (NCCL on device tensors, gloo on host tensors)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_value(units_per_rank: int, ms_per_rank: float, world: int) -> float:
+    """Gunknowns/s of the whole job: every rank's units over the slowest rank's time."""
+    ms = max_over_ranks(ms_per_rank, world)
+    return world * units_per_rank / (ms * 1e-3) / 1e9
 
 
 def time_solves(plan, F, x, steps, warmup, world, events_stream):
@@ -450,6 +462,27 @@ def other_configs(D, W, oracle, stream, world, steps=10):
                     "rel_err_gF_sys7": float(np.max(np.abs(gF[o:o + n].cpu().numpy() - lam)) / np.max(np.abs(lam))),
                     "rel_err_gt_sys7": float(np.max(np.abs(gt[s_].cpu().numpy() - g)) / np.max(np.abs(g)))}
     out["c5_adjoint_1024x65536"] = c5
+    del Fd, wd, xd
+    torch.cuda.empty_cache()
+
+    # f3: 2-D Dirichlet Poisson by separation of variables on a 4096 x 4096-interval grid
+    # (M = 4095 interior points per direction): DST-I along x, the 4095 mode systems through the
+    # batched Dichotomy solve, inverse DST-I; manufactured solution u* ~ U[-1, 1]
+    from paper_1002_2469_gb300 import poisson as PS
+    from oracle import poisson as OP
+    M = 4095
+    us = np.random.default_rng(0).uniform(-1.0, 1.0, (M, M))
+    fd = torch.from_numpy(OP.laplacian5(us)).cuda()
+    solver = PS.Poisson2D(M)
+    ms_total = _time_batch(lambda: solver.solve(fd), steps, world, stream)
+    rhs = torch.empty(M * M, dtype=torch.float64, device="cuda")
+    v = torch.empty_like(rhs)
+    ms_solve = _time_batch(lambda: solver.batch.solve(rhs, out=v), steps, world, stream)
+    u = solver.solve(fd).cpu().numpy()
+    out["f3_poisson2d_4095"] = {"unknowns": M * M, "ms_total": round(ms_total, 4), "ms_dichotomy": round(ms_solve, 4),
+                                "Gunknowns_s": round(M * M / ms_total / 1e6, 2),
+                                "form": "AUTO per mode", "transform": "DST-I via torch.fft (cuFFT)",
+                                "rel_err_vs_manufactured": float(np.max(np.abs(u - us)) / np.max(np.abs(us)))}
     return out
 
 

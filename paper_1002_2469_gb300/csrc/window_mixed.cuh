@@ -43,9 +43,10 @@ __host__ __device__ inline size_t window2_smem_bytes(int NT, int n_smem) {
 // forward and backward sweeps of a thread's pair of blocks, in place.  GUARD: the two blocks
 // may differ in size (the system's last block) or be inactive (nb = 0): rows at or beyond a
 // block's size enter as zero, which keeps its backward recurrence exact.
-template <int LD, bool GUARD, bool FAST>
-__device__ __forceinline__ void sweep_pair(double* S, int tid, int nrow, int nb0, int nb1, int wscale,
+template <int LD, bool GUARD, bool FAST, int NR = 0>
+__device__ __forceinline__ void sweep_pair(double* S, int tid, int nrow_, int nb0, int nb1, int wscale,
                                            const SysPlan* pp, float2& Xh, float2& Xl) {
+  const int nrow = NR ? NR : nrow_;
   const FastK fk = fast_k(wscale);
   const float2 rh = f2(pp->rs_h), rl = f2(pp->rs_l), bh = f2(pp->ib_h), bl = f2(pp->ib_l);
   const float2 gh = f2(pp->g_h), gl = f2(pp->g_l);
@@ -88,11 +89,12 @@ __device__ __forceinline__ void sweep_pair(double* S, int tid, int nrow, int nb0
 }
 
 // correction x = xp + cL v + cR w along the thread's pair of columns and the FP64 join, in place.
-template <int LD, bool GUARD, bool FAST>
-__device__ __forceinline__ void correct_pair(double* S, int tid, int nrow, int nb0, int nb1, bool last0,
+template <int LD, bool GUARD, bool FAST, int NR = 0>
+__device__ __forceinline__ void correct_pair(double* S, int tid, int nrow_, int nb0, int nb1, bool last0,
                                              bool last1, int n, int nlast, int Lv, int Lw, const float2* tv,
                                              const float2* tw, const float2* tvl, const float2* twl, const ff2& cL,
                                              const ff2& cR, int wscale) {
+  const int nrow = NR ? NR : nrow_;
   const float2 clh = cL.h, cll = cL.l, crh = cR.h, crl = cR.l;
   const FastK fk = fast_k(wscale);
   if (!GUARD) {
@@ -300,7 +302,9 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
 
   // ---------------------------------------------------------------- local sweeps (a1)
   float2 Xh, Xl;
-  if (full && fast)
+  if (full && fast && n == 16)
+    sweep_pair<LD, false, true, 16>(S, tid, nrow, nb0, nb1, wscale, pp, Xh, Xl);
+  else if (full && fast)
     sweep_pair<LD, false, true>(S, tid, nrow, nb0, nb1, wscale, pp, Xh, Xl);
   else if (full)
     sweep_pair<LD, false, false>(S, tid, nrow, nb0, nb1, wscale, pp, Xh, Xl);
@@ -447,7 +451,10 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
 
   // ---------------------------------------------------------------- correction (a3), per column
   const ff2 cL = ff2_sub(ff2_pair(XL0, XL1), xm), cR = ff2_pair(XR0, XR1);
-  if (full && fast)
+  if (full && fast && n == 16)
+    correct_pair<LD, false, true, 16>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL,
+                                      cR, wscale);
+  else if (full && fast)
     correct_pair<LD, false, true>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL, cR,
                                   wscale);
   else if (full)

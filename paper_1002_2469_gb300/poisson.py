@@ -1,0 +1,64 @@
+"""The 2-D Dirichlet Poisson problem by separation of variables (Sec. 3.2 and Sec. 4).
+
+-Laplace(u) = f on the unit square, u = 0 on the boundary, five-point stencil on a grid of
+(M + 1) x (M + 1) intervals (h = 1 / (M + 1)), unknowns u[i, j] = u(x_i, y_j), i, j = 1..M, stored
+as an [M, M] tensor (row i = x_i).  The orthonormal DST-I along x diagonalises the x part of the
+operator; mode k = 1..M leaves one tridiagonal Toeplitz system along y,
+
+    -v[k, j-1] + (2 + 4 sin^2(k pi / (2 (M + 1)))) v[k, j] - v[k, j+1] = h^2 fhat[k, j],
+
+the series of Sec. 3.2 with one t_0 per mode.  All M systems are solved as one batch by the
+Dichotomy kernels (the library's batched entry point); the inverse DST-I (the same transform)
+returns u.  The transforms use torch's FFT (cuFFT): DST-I of length M through a real FFT of
+length 2 (M + 1).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import dichotomy as _d
+
+__all__ = ["dst1", "mode_t0", "Poisson2D"]
+
+
+def dst1(a: torch.Tensor, dim: int = 0) -> torch.Tensor:
+    """Orthonormal DST-I along `dim`: X_k = sqrt(2 / (M + 1)) sum_j a_j sin(pi j k / (M + 1)),
+    j, k = 1..M.  It is its own inverse.  With a zero-padded to 2 (M + 1) points (a_j at
+    position j, j = 1..M), the real FFT gives Y_k = sum_j a_j exp(-i pi j k / (M + 1)), so the
+    sine sum is -Im(Y_k)."""
+    M = a.shape[dim]
+    pad = torch.nn.functional.pad(a.movedim(dim, -1), (1, 0)).movedim(-1, dim)    # a_j at position j
+    Y = torch.fft.rfft(pad, n=2 * (M + 1), dim=dim)
+    return (Y.imag.narrow(dim, 1, M) * (-math.sqrt(2.0 / (M + 1)))).contiguous()
+
+
+def mode_t0(M: int) -> np.ndarray:
+    """t_0 of the tridiagonal system of mode k = 1..M: 2 + 4 sin^2(k pi / (2 (M + 1)))."""
+    k = np.arange(1, M + 1, dtype=np.float64)
+    return 2.0 + 4.0 * np.sin(k * math.pi / (2.0 * (M + 1))) ** 2
+
+
+class Poisson2D:
+    """Solver for an [M, M] interior grid; the batch of M mode systems is planned once."""
+
+    def __init__(self, M: int, precision: int = _d.PREC_AUTO, device=None):
+        self.M = int(M)
+        self.h = 1.0 / (self.M + 1)
+        t0 = mode_t0(self.M)
+        ones = np.ones(self.M)
+        self.batch = _d.Batch(np.full(self.M, self.M, dtype=np.int64), -ones, t0, -ones, precision=precision)
+        self.device = device
+
+    def solve(self, f: torch.Tensor) -> torch.Tensor:
+        """u for the right-hand side f ([M, M], float64, CUDA)."""
+        if f.shape != (self.M, self.M):
+            raise ValueError(f"f must be [{self.M}, {self.M}]")
+        rhs = (self.h * self.h) * dst1(f, dim=0)                  # [k, j]: mode k along y
+        v = self.batch.solve(rhs.reshape(-1)).reshape(self.M, self.M)
+        return dst1(v, dim=0)
+
+    def status(self) -> int:
+        return self.batch.status()

@@ -343,3 +343,31 @@ def test_quasi_toeplitz_eq21_vs_dense(t, psi, chi):
     A[N - 1, N - 1] = t[1] + chi
     F = np.random.default_rng(2).standard_normal(N)
     assert rel(oracle.thomas_quasi(t, psi, chi, F), np.linalg.solve(A, F)) < 1e-14
+
+
+# ------------------------------------------------------------------ 2-D Poisson by separation of variables
+def test_poisson2d_oracle_vs_dense_kronecker():
+    """The separation-of-variables oracle against a dense solve of the five-point Laplacian,
+    assembled independently as a Kronecker sum."""
+    from oracle import poisson as OP
+    M = 15
+    h = 1.0 / (M + 1)
+    T = (np.diag(np.full(M, 2.0)) - np.diag(np.ones(M - 1), 1) - np.diag(np.ones(M - 1), -1)) / (h * h)
+    L = np.kron(T, np.eye(M)) + np.kron(np.eye(M), T)          # row-major [i, j] -> i * M + j
+    f = np.random.default_rng(4).standard_normal((M, M))
+    u = np.linalg.solve(L, f.reshape(-1)).reshape(M, M)
+    assert rel(OP.poisson2d(f), u) < 1e-13
+    assert rel(OP.laplacian5(u), f) < 1e-12
+
+
+@pytest.mark.parametrize("p,q", [(1, 1), (3, 5), (20, 2)])
+def test_poisson2d_single_mode(p, q):
+    """f = sin(p pi x) sin(q pi y) excites one mode: u = f / lambda_pq, lambda_pq =
+    (4 sin^2(p pi h / 2) + 4 sin^2(q pi h / 2)) / h^2 (the discrete eigenvalue)."""
+    from oracle import poisson as OP
+    M = 63
+    h = 1.0 / (M + 1)
+    x = np.arange(1, M + 1) * h
+    f = np.outer(np.sin(p * math.pi * x), np.sin(q * math.pi * x))
+    lam = (4 * math.sin(p * math.pi * h / 2) ** 2 + 4 * math.sin(q * math.pi * h / 2) ** 2) / h ** 2
+    assert rel(OP.poisson2d(f), f / lam) < 1e-13
