@@ -96,6 +96,7 @@ typedef struct {
 
 typedef struct dich_plan_s* dich_plan_t;
 typedef struct dich_batch_s* dich_batch_t;
+typedef struct dich_gen_s* dich_gen_t;
 
 /* ---------------------------------------------------------------- single system */
 
@@ -212,6 +213,39 @@ const char* dichotomy_strerror(int status);
 const char* dichotomy_last_cuda_error(void);
 /* Library version, e.g. "0.1.0". */
 const char* dichotomy_version(void);
+
+/* ---------------------------------------------------------------- general tridiagonal matrices
+ * The Dichotomy Algorithm for a general (non-Toeplitz) tridiagonal matrix (Sec. 2): row i reads
+ * a_i x_{i-1} + b_i x_i + c_i x_{i+1} = F_i (a_0 and c_{N-1} are ignored).  The preliminary step
+ * (Sec. 2.3) is the general O(N) one, run on the host by dichotomy_gen_plan: the whole-system
+ * elimination factors (the homogeneous solutions that give the exterior vectors of eq. 10-12 as
+ * ratios), each block's own Thomas factors and spikes, and the block maps of the dichotomy tree.
+ * Every solve of a series (eq. 2) reuses it.  FP64 only.  The plan keeps 5 doubles per row in
+ * the device workspace (40 bytes per row, plus 80 bytes per block). */
+
+/* Plan for the N x N matrix given by the host arrays h_a (sub-diagonal), h_b (diagonal), h_c
+ * (super-diagonal), N entries each (copied; the caller keeps ownership).  opts as for
+ * dichotomy_plan_ex (precision DICH_PREC_MIXED: DICH_ERR_UNSUPPORTED).  Every row must satisfy
+ * |b_i| >= |a_i| + |c_i| (eq. 32-33).  Errors: DICH_ERR_ARG (null, negative N, non-finite entry,
+ * bad opts), DICH_ERR_NOT_DOMINANT, DICH_ERR_SINGULAR (a zero pivot), DICH_ERR_UNSUPPORTED. */
+int dichotomy_gen_plan(int64_t N, const double* h_a, const double* h_b, const double* h_c, const dich_opts* opts,
+                       dich_gen_t* out);
+/* Geometry of a general plan (the Toeplitz-only fields are zero).  Errors: DICH_ERR_ARG. */
+int dichotomy_gen_info(dich_gen_t plan, dich_plan_info* info);
+/* Bytes of device workspace (256-byte aligned region). */
+int dichotomy_gen_workspace_bytes(dich_gen_t plan, size_t* bytes);
+/* Attach the caller's workspace and upload the plan on `stream`; returns after the upload has
+ * completed.  Errors: DICH_ERR_ARG, DICH_ERR_WORKSPACE, DICH_ERR_CUDA. */
+int dichotomy_gen_bind(dich_gen_t plan, void* d_workspace, size_t bytes, void* stream);
+/* x = A^-1 F: one kernel (one window or halo windows) or three (general path) on `stream`.
+ * Errors: DICH_ERR_ARG, DICH_ERR_ALIAS, DICH_ERR_UNBOUND, DICH_ERR_CUDA. */
+int dichotomy_gen_solve(dich_gen_t plan, const double* d_F, double* d_x, void* stream);
+/* The series form (as dichotomy_solve_series). */
+int dichotomy_gen_solve_series(dich_gen_t plan, int64_t M, const double* d_F, int64_t ldf, double* d_x,
+                               int64_t ldx, void* stream);
+/* Synchronize, read and clear the device status word (as dichotomy_status). */
+int dichotomy_gen_status(dich_gen_t plan, void* stream, int* device_status);
+void dichotomy_gen_destroy(dich_gen_t plan);
 
 #ifdef __cplusplus
 }

@@ -32,6 +32,8 @@ EXPORTS = [
     "dichotomy_batch_prepare", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
     "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
     "dichotomy_batch_destroy", "dichotomy_strerror", "dichotomy_last_cuda_error", "dichotomy_version",
+    "dichotomy_gen_plan", "dichotomy_gen_info", "dichotomy_gen_workspace_bytes", "dichotomy_gen_bind",
+    "dichotomy_gen_solve", "dichotomy_gen_solve_series", "dichotomy_gen_status", "dichotomy_gen_destroy",
 ]
 
 
@@ -106,6 +108,14 @@ def load(build_if_missing: bool = True):
             "dichotomy_strerror": ([I], ctypes.c_char_p),
             "dichotomy_last_cuda_error": ([], ctypes.c_char_p),
             "dichotomy_version": ([], ctypes.c_char_p),
+            "dichotomy_gen_plan": ([c_int64, P, P, P, ctypes.POINTER(dich_opts), ctypes.POINTER(P)], I),
+            "dichotomy_gen_info": ([P, ctypes.POINTER(dich_plan_info)], I),
+            "dichotomy_gen_workspace_bytes": ([P, ctypes.POINTER(c_size_t)], I),
+            "dichotomy_gen_bind": ([P, P, c_size_t, P], I),
+            "dichotomy_gen_solve": ([P, P, P, P], I),
+            "dichotomy_gen_solve_series": ([P, c_int64, P, c_int64, P, c_int64, P], I),
+            "dichotomy_gen_status": ([P, P, ctypes.POINTER(I)], I),
+            "dichotomy_gen_destroy": ([P], None),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)

@@ -1,0 +1,407 @@
+// general.cu -- general (non-Toeplitz) tridiagonal systems: the O(N) preliminary step of the
+// Dichotomy Algorithm on the host (Sec. 2.3) and the solve by the window kernel of
+// window_gen.cuh, behind the dichotomy_gen_* entry points of include/dichotomy.h.
+//
+// Preliminary step, in the terms of the Toeplitz restatement (exterior ratios and block maps
+// from the homogeneous solutions phi, vanishing left of row 0, and psi, vanishing right of row
+// N-1): the whole-system forward elimination factors cp_i = c_i / (b_i - a_i cp_{i-1}) give
+// phi_i / phi_{i+1} = -cp_i, the backward ones cq_i = a_i / (b_i - c_i cq_{i+1}) give
+// psi_i / psi_{i-1} = -cq_i.  Per block m = [s, e]:
+//   kL = -cp_{s-1}, kR = -cq_{e+1} (zero at the system ends),
+//   a = prod_{i=s+1..e+1} (-cq_i), b = kR, c = prod_{i=s-1..e-1} (-cp_i), d = kL,
+//   tL = prod_{i=s..e-1} (-cp_i) = phi_s / phi_e, tR = prod_{i=s+1..e} (-cq_i) = psi_e / psi_s,
+//   the block's own Thomas factors and spikes v = T_m^-1 (-a_s e_0), w = T_m^-1 (-c_e e_{n-1}),
+//   M = (I - [[kL v_0, kR w_0], [kL v_end, kR w_end]])^-1 (eq. 16 restated).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/dichotomy.h"
+#include "launch.cuh"
+#include "planner.cuh"
+#include "window_gen.cuh"
+
+using namespace dich;
+using namespace dich::plan;
+
+namespace dich {
+
+template <int NT>
+static cudaError_t launch_gen_one(int grid, int grid_y, size_t smem, cudaStream_t st, const GenArgs& a) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_window_gen<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_window_gen<NT><<<dim3(grid, grid_y), NT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_window_gen(int NT, int grid, size_t smem, cudaStream_t st, const GenArgs& a, int grid_y) {
+  switch (NT) {
+    case 64: return launch_gen_one<64>(grid, grid_y, smem, st, a);
+    case 128: return launch_gen_one<128>(grid, grid_y, smem, st, a);
+    case 256: return launch_gen_one<256>(grid, grid_y, smem, st, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace dich
+
+struct dich_gen_s {
+  int64_t N = 0;
+  Opts opts;
+  int NT = 64;
+  int path = PATH_SINGLE;
+  int64_t tiles = 0;
+  int64_t stride = 0;                 // doubles per per-row field
+  SysPlan rec{};                      // geometry record read by the kernels
+  std::vector<double> recs;           // block records, kBC doubles per block
+  std::vector<double> rows;           // per-row fields (window_gen.cuh layout)
+  size_t ws_bytes = 0, off_plan = 0, off_status = 0, off_recs = 0, off_rows = 0, off_beta = 0, off_iface = 0,
+         off_scan = 0;
+  char* d_ws = nullptr;
+};
+
+namespace {
+
+constexpr int kGenDefaultRows = 32;
+
+// the O(N) preliminary step; returns a status code
+int gen_build(dich_gen_s* g, const double* a, const double* b, const double* c) {
+  const int64_t N = g->N;
+  SysPlan& r = g->rec;
+  std::memset(&r, 0, sizeof(r));
+  r.N = N;
+  if (N == 1) {
+    r.t0 = b[0];
+    return DICH_OK;
+  }
+  const int NT = g->NT;
+  const size_t budget = g->opts.n_req > 0 ? kSmemMax : kSmemBudget;
+  int nmax = 2;
+  while (window_gen_smem_bytes(NT, nmax + 1) <= budget) ++nmax;
+  const int n = choose_n(N, NT, nmax, g->opts.n_req, kGenDefaultRows);
+  const int64_t P = ceil_div(N, n);
+  r.n = n;
+  r.P = P;
+  r.nlast = (int)(N - (P - 1) * (int64_t)n);
+  if (r.nlast < 2) return DICH_ERR_ARG;
+  r.kl = (int32_t)std::min<int64_t>(P, INT32_MAX);
+  r.kr = 0;
+  r.form = FORM_F64;
+  r.t0 = b[0];
+
+  // whole-system elimination factors
+  std::vector<double> cp((size_t)N), cq((size_t)N);
+  double prev = 0.0;
+  for (int64_t i = 0; i < N; ++i) {
+    const double den = b[i] - (i > 0 ? a[i] * prev : 0.0);
+    if (den == 0.0 || !std::isfinite(den)) return DICH_ERR_SINGULAR;
+    prev = (i < N - 1 ? c[i] : 0.0) / den;
+    cp[(size_t)i] = prev;
+  }
+  prev = 0.0;
+  for (int64_t i = N - 1; i >= 0; --i) {
+    const double den = b[i] - (i < N - 1 ? c[i] * prev : 0.0);
+    if (den == 0.0 || !std::isfinite(den)) return DICH_ERR_SINGULAR;
+    prev = (i > 0 ? a[i] : 0.0) / den;
+    cq[(size_t)i] = prev;
+  }
+
+  const int64_t Ppad = (P + 31) / 32 * 32;
+  g->stride = Ppad * n;
+  g->rows.assign((size_t)(kGenFields * g->stride), 0.0);
+  g->recs.assign((size_t)(P * kBC), 0.0);
+  double* fa = g->rows.data() + GF_A * g->stride;
+  double* frd = g->rows.data() + GF_RD * g->stride;
+  double* fcp = g->rows.data() + GF_CP * g->stride;
+  double* fv = g->rows.data() + GF_V * g->stride;
+  double* fw = g->rows.data() + GF_W * g->stride;
+  std::vector<double> lcp((size_t)n), lrd((size_t)n), z((size_t)n);
+  double amax = 0.0, cmax = 0.0;
+  for (int64_t m = 0; m < P; ++m) {
+    const int64_t s = m * n;
+    const int nb = (m == P - 1) ? r.nlast : n;
+    const int64_t e = s + nb - 1;
+    // the block's own Thomas factors (zero values outside the block)
+    for (int i = 0; i < nb; ++i) {
+      const int64_t row = s + i;
+      const double den = b[row] - (i > 0 ? a[row] * lcp[(size_t)i - 1] : 0.0);
+      if (den == 0.0 || !std::isfinite(den)) return DICH_ERR_SINGULAR;
+      lrd[(size_t)i] = 1.0 / den;
+      lcp[(size_t)i] = (i < nb - 1 ? c[row] : 0.0) / den;
+      const int64_t k = gen_index(m, i, n);
+      fa[k] = (i > 0) ? a[row] : 0.0;
+      frd[k] = lrd[(size_t)i];
+      fcp[k] = lcp[(size_t)i];
+    }
+    // spikes v = T_m^-1 (-a_s e_0), w = T_m^-1 (-c_e e_{nb-1})
+    const double as = (s > 0) ? a[s] : 0.0, ce = (e < N - 1) ? c[e] : 0.0;
+    z[0] = -as * lrd[0];
+    for (int i = 1; i < nb; ++i) z[(size_t)i] = -a[s + i] * z[(size_t)i - 1] * lrd[(size_t)i];
+    double vn = z[(size_t)nb - 1];
+    fv[gen_index(m, nb - 1, n)] = vn;
+    for (int i = nb - 2; i >= 0; --i) {
+      vn = z[(size_t)i] - lcp[(size_t)i] * vn;
+      fv[gen_index(m, i, n)] = vn;
+    }
+    double wn = -ce * lrd[(size_t)nb - 1];
+    fw[gen_index(m, nb - 1, n)] = wn;
+    for (int i = nb - 2; i >= 0; --i) {
+      wn = -lcp[(size_t)i] * wn;
+      fw[gen_index(m, i, n)] = wn;
+    }
+    const double v0 = fv[gen_index(m, 0, n)], vend = fv[gen_index(m, nb - 1, n)];
+    const double w0 = fw[gen_index(m, 0, n)], wend = fw[gen_index(m, nb - 1, n)];
+    // exterior ratios and block maps
+    const double kL = (m > 0) ? -cp[(size_t)s - 1] : 0.0;
+    const double kR = (m < P - 1) ? -cq[(size_t)e + 1] : 0.0;
+    double pa = 0.0, pc = 0.0, tL = 1.0, tR = 1.0;
+    if (m < P - 1) {
+      pa = 1.0;
+      for (int64_t i = s + 1; i <= e + 1; ++i) pa *= -cq[(size_t)i];
+    }
+    if (m > 0) {
+      pc = 1.0;
+      for (int64_t i = s - 1; i <= e - 1; ++i) pc *= -cp[(size_t)i];
+    }
+    for (int64_t i = s; i <= e - 1; ++i) tL *= -cp[(size_t)i];
+    for (int64_t i = s + 1; i <= e; ++i) tR *= -cq[(size_t)i];
+    const double p00 = 1.0 - kL * v0, p01 = -kR * w0, p10 = -kL * vend, p11 = 1.0 - kR * wend;
+    const double det = p00 * p11 - p01 * p10;
+    if (det == 0.0 || !std::isfinite(det)) return DICH_ERR_SINGULAR;
+    double* rc = g->recs.data() + m * kBC;
+    rc[BC_A] = pa;
+    rc[BC_B] = kR;
+    rc[BC_C] = pc;
+    rc[BC_D] = kL;
+    rc[BC_TL] = tL;
+    rc[BC_TR] = tR;
+    rc[BC_M00] = p11 / det;
+    rc[BC_M01] = -p01 / det;
+    rc[BC_M10] = -p10 / det;
+    rc[BC_M11] = p00 / det;
+    if (m < P - 1) amax = std::max(amax, std::fabs(pa));
+    if (m > 0) cmax = std::max(cmax, std::fabs(pc));
+  }
+
+  // windows: one window, halo windows (coupling beyond the halo below eps), or the general path
+  const double eps = g->opts.eps;
+  auto halo_of = [&](double mx) -> int64_t {
+    if (mx == 0.0) return 1;
+    if (mx >= 1.0) return P;
+    return (int64_t)std::ceil(std::log(eps) / std::log(mx)) + 1;
+  };
+  const int64_t hl = halo_of(amax), hr = halo_of(cmax);
+  if (P <= NT) {
+    g->path = PATH_SINGLE;
+    r.own = (int32_t)P;
+  } else if (!(g->opts.flags & DICH_FLAG_FORCE_GENERAL) && hl + hr <= NT / 2) {
+    g->path = PATH_HALO;
+    r.hl = (int32_t)hl;
+    r.hr = (int32_t)hr;
+    r.own = (int32_t)(NT - hl - hr);
+  } else {
+    g->path = PATH_GENERAL;
+    r.own = NT;
+  }
+  g->tiles = ceil_div(P, r.own);
+  return DICH_OK;
+}
+
+void gen_layout(dich_gen_s* g) {
+  size_t o = 0;
+  g->off_plan = o;
+  o += align_up(sizeof(SysPlan));
+  g->off_status = o;
+  o += kAlign;
+  g->off_recs = o;
+  o += align_up(sizeof(double) * g->recs.size());
+  g->off_rows = o;
+  o += align_up(sizeof(double) * g->rows.size());
+  if (g->path == PATH_GENERAL) {
+    const int64_t P = g->rec.P;
+    g->off_beta = o;
+    o += align_up(sizeof(double) * 2 * P);
+    g->off_iface = o;
+    o += align_up(sizeof(double) * 2 * P);
+    g->off_scan = o;
+    o += align_up(sizeof(double) * 6 * (size_t)ceil_div(P, kScanChunk));
+  }
+  g->ws_bytes = o;
+}
+
+int gen_launch(dich_gen_s* g, const double* F, double* x, cudaStream_t st, int64_t M, int64_t ldf, int64_t ldx) {
+  const SysPlan* d_plan = (const SysPlan*)(g->d_ws + g->off_plan);
+  const double* d_recs = (const double*)(g->d_ws + g->off_recs);
+  unsigned* d_status = (unsigned*)(g->d_ws + g->off_status);
+  if (g->N == 1) {
+    for (int64_t k = 0; k < M; ++k) {
+      cudaError_t e = launch_trivial(d_plan, nullptr, 1, F + k * ldf, x + k * ldx, nullptr, nullptr, nullptr, 0, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return DICH_OK;
+  }
+  GenArgs ga{};
+  ga.w.plans = d_plan;
+  ga.w.tabs = d_recs;
+  ga.w.status = d_status;
+  ga.w.check_finite = (g->opts.flags & DICH_FLAG_CHECK_FINITE) ? 1 : 0;
+  ga.w.n_smem = g->rec.n;
+  ga.rows = (const double*)(g->d_ws + g->off_rows);
+  ga.stride = g->stride;
+  const size_t smem = window_gen_smem_bytes(g->NT, g->rec.n);
+  cudaError_t e;
+  if (g->path != PATH_GENERAL) {
+    ga.w.mode = MODE_FULL;
+    ga.w.ldf = ldf;
+    ga.w.ldx = ldx;
+    for (int64_t k0 = 0; k0 < M; k0 += 65535) {
+      GenArgs w = ga;
+      w.w.F = F + k0 * ldf;
+      w.w.x = x + k0 * ldx;
+      e = launch_window_gen(g->NT, (int)g->tiles, smem, st, w, (int)std::min<int64_t>(65535, M - k0));
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return DICH_OK;
+  }
+  double* beta = (double*)(g->d_ws + g->off_beta);
+  double* iface = (double*)(g->d_ws + g->off_iface);
+  double* scan = (double*)(g->d_ws + g->off_scan);
+  for (int64_t k = 0; k < M; ++k) {
+    GenArgs w = ga;
+    w.w.F = F + k * ldf;
+    w.w.x = x + k * ldx;
+    w.w.mode = MODE_BETA;
+    w.w.beta = beta;
+    e = launch_window_gen(g->NT, (int)g->tiles, smem, st, w, 1);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = launch_block_scan(d_plan, d_recs, g->rec.P, beta, iface, scan, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    w.w.mode = MODE_APPLY;
+    w.w.iface = iface;
+    e = launch_window_gen(g->NT, (int)g->tiles, smem, st, w, 1);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return DICH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dichotomy_gen_plan(int64_t N, const double* h_a, const double* h_b, const double* h_c, const dich_opts* opts,
+                       dich_gen_t* out) {
+  if (!out) return DICH_ERR_ARG;
+  *out = nullptr;
+  if (N < 0 || (N > 0 && (!h_a || !h_b || !h_c))) return DICH_ERR_ARG;
+  Opts o;
+  int rc = read_opts(opts, o);
+  if (rc) return rc;
+  if (o.prec == DICH_PREC_MIXED) return DICH_ERR_UNSUPPORTED;
+  // eq. 32-33 row by row (a_0 and c_{N-1} lie outside the matrix)
+  for (int64_t i = 0; i < N; ++i) {
+    const double ai = (i > 0) ? h_a[i] : 0.0, ci = (i < N - 1) ? h_c[i] : 0.0;
+    if (!std::isfinite(ai) || !std::isfinite(h_b[i]) || !std::isfinite(ci)) return DICH_ERR_ARG;
+    if (h_b[i] == 0.0) return (ai == 0.0 && ci == 0.0) ? DICH_ERR_SINGULAR : DICH_ERR_NOT_DOMINANT;
+    if (std::fabs(h_b[i]) < (std::fabs(ai) + std::fabs(ci)) * (1.0 - 4.0 * DBL_EPSILON)) return DICH_ERR_NOT_DOMINANT;
+  }
+  dich_gen_s* g = new (std::nothrow) dich_gen_s();
+  if (!g) return DICH_ERR_ARG;
+  g->N = N;
+  g->opts = o;
+  g->NT = o.NT ? o.NT : 64;
+  if (N >= 1) {
+    rc = gen_build(g, h_a, h_b, h_c);
+    if (rc) {
+      delete g;
+      return rc;
+    }
+  }
+  gen_layout(g);
+  *out = g;
+  return DICH_OK;
+}
+
+int dichotomy_gen_info(dich_gen_t g, dich_plan_info* info) {
+  if (!g || !info) return DICH_ERR_ARG;
+  std::memset(info, 0, sizeof(*info));
+  info->N = g->N;
+  info->P = g->rec.P;
+  info->n = g->rec.n;
+  info->n_last = g->rec.nlast;
+  info->threads = g->NT;
+  info->halo_l = g->rec.hl;
+  info->halo_r = g->rec.hr;
+  info->path = g->path;
+  info->precision = DICH_PREC_F64;
+  info->tiles = g->tiles;
+  info->workspace_bytes = g->ws_bytes;
+  return DICH_OK;
+}
+
+int dichotomy_gen_workspace_bytes(dich_gen_t g, size_t* bytes) {
+  if (!g || !bytes) return DICH_ERR_ARG;
+  *bytes = g->ws_bytes;
+  return DICH_OK;
+}
+
+int dichotomy_gen_bind(dich_gen_t g, void* d_ws, size_t bytes, void* stream) {
+  if (!g || !d_ws) return DICH_ERR_ARG;
+  if (((uintptr_t)d_ws & (kAlign - 1)) != 0 || bytes < g->ws_bytes) return DICH_ERR_WORKSPACE;
+  if (!is_device_ptr(d_ws)) return DICH_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* base = (char*)d_ws;
+  cudaError_t e = cudaMemcpyAsync(base + g->off_plan, &g->rec, sizeof(SysPlan), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + g->off_status, 0, kAlign, st);
+  if (e == cudaSuccess && !g->recs.empty())
+    e = cudaMemcpyAsync(base + g->off_recs, g->recs.data(), sizeof(double) * g->recs.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !g->rows.empty())
+    e = cudaMemcpyAsync(base + g->off_rows, g->rows.data(), sizeof(double) * g->rows.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the host tables may be freed or reused after bind
+  if (e != cudaSuccess) return cuda_fail(e);
+  g->d_ws = base;
+  return DICH_OK;
+}
+
+int dichotomy_gen_solve_series(dich_gen_t g, int64_t M, const double* d_F, int64_t ldf, double* d_x, int64_t ldx,
+                               void* stream) {
+  if (!g || M < 0) return DICH_ERR_ARG;
+  if (!g->d_ws) return DICH_ERR_UNBOUND;
+  if (g->N == 0 || M == 0) return DICH_OK;
+  if (!d_F || !d_x || !aligned8(d_F) || !aligned8(d_x)) return DICH_ERR_ARG;
+  if (M > 1 && (ldf < g->N || ldx < g->N)) return DICH_ERR_ARG;
+  if (M > 1 && (ldf > INT64_MAX / M || ldx > INT64_MAX / M)) return DICH_ERR_ARG;
+  const int64_t sf = (M > 1) ? ldf : 0, sx = (M > 1) ? ldx : 0;
+  const size_t nf = sizeof(double) * (size_t)((M - 1) * sf + g->N);
+  const size_t nx = sizeof(double) * (size_t)((M - 1) * sx + g->N);
+  if (overlap(d_F, nf, d_x, nx)) return DICH_ERR_ALIAS;
+  if (!is_device_ptr(d_F) || !is_device_ptr(d_x)) return DICH_ERR_ARG;
+  return gen_launch(g, d_F, d_x, (cudaStream_t)stream, M, sf, sx);
+}
+
+int dichotomy_gen_solve(dich_gen_t g, const double* d_F, double* d_x, void* stream) {
+  return dichotomy_gen_solve_series(g, 1, d_F, 0, d_x, 0, stream);
+}
+
+int dichotomy_gen_status(dich_gen_t g, void* stream, int* device_status) {
+  if (!g || !device_status) return DICH_ERR_ARG;
+  if (!g->d_ws) return DICH_ERR_UNBOUND;
+  unsigned s = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpy(&s, g->d_ws + g->off_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(g->d_ws + g->off_status, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_fail(e);
+  *device_status = map_status(s);
+  return DICH_OK;
+}
+
+void dichotomy_gen_destroy(dich_gen_t g) { delete g; }
+
+}  // extern "C"

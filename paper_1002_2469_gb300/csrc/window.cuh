@@ -61,6 +61,68 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // 2^k as a double for |k| <= 1000 (bit construction)
 __device__ __forceinline__ double pow2i(int k) { return __hiloint2double((1023 + k) << 20, 0); }
 
+// The dichotomy tree of one FP64 window (a2): eq. 15 as two affine scans over the window's blocks
+// (prefix maps A -> a A + b beta^R left to right, suffix maps B -> c B + d beta^L right to left),
+// five warp-shuffle levels and one shared-memory level, then the first/last values of every
+// block (eq. 18) in sxs/sxe and the neighbours' values each block needs: XL = x_{s-1}, XR = x_{e+1}.
+// bc: the block's coefficient record; zero coupling enters at both window ends.
+template <int NT>
+__device__ __forceinline__ void tree_f64(const double* bc, bool act, double bL, double bR, int64_t mb, int64_t P,
+                                         int nwin, int tid, double* swa, double* sxs, double* sxe, double& XL,
+                                         double& XR) {
+  constexpr int NW = NT / 32;
+  const int lane = tid & 31, wid = tid >> 5;
+  double pa = act ? bc[BC_A] : 1.0;
+  double pb = act ? bc[BC_B] * bR : 0.0;
+  double qa = act ? bc[BC_C] : 1.0;
+  double qb = act ? bc[BC_D] * bL : 0.0;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const double ya = __shfl_up_sync(0xffffffffu, pa, d), yb = __shfl_up_sync(0xffffffffu, pb, d);
+    const double za = __shfl_down_sync(0xffffffffu, qa, d), zb = __shfl_down_sync(0xffffffffu, qb, d);
+    if (lane >= d) {
+      pb = fma(pa, yb, pb);
+      pa = pa * ya;
+    }
+    if (lane + d < 32) {
+      qb = fma(qa, zb, qb);
+      qa = qa * za;
+    }
+  }
+  if (lane == 31) {
+    swa[wid] = pa;
+    swa[NW + wid] = pb;
+  }
+  if (lane == 0) {
+    swa[2 * NW + wid] = qa;
+    swa[3 * NW + wid] = qb;
+  }
+  // previous lane's inclusive prefix, next lane's inclusive suffix
+  double ea = __shfl_up_sync(0xffffffffu, pa, 1), eb = __shfl_up_sync(0xffffffffu, pb, 1);
+  double fa = __shfl_down_sync(0xffffffffu, qa, 1), fb = __shfl_down_sync(0xffffffffu, qb, 1);
+  if (lane == 0) {
+    ea = 1.0;
+    eb = 0.0;
+  }
+  if (lane == 31) {
+    fa = 1.0;
+    fb = 0.0;
+  }
+  __syncthreads();
+  double Aw = 0.0, Bw = 0.0;  // zero coupling enters at both window ends
+  for (int w = 0; w < wid; ++w) Aw = fma(swa[w], Aw, swa[NW + w]);
+  for (int w = NW - 1; w > wid; --w) Bw = fma(swa[2 * NW + w], Bw, swa[3 * NW + w]);
+  const double Am = fma(ea, Aw, eb);
+  const double Bm = fma(fa, Bw, fb);
+  sxs[tid] = fma(bc[BC_TL], Bm, bL) + Am;            // x_s (eq. 18)
+  sxe[tid] = fma(bc[BC_TR], Am, bR + Bm);            // x_e
+  __syncthreads();
+  if (act) {
+    if (!(mb == 0 || tid == 0)) XL = sxe[tid - 1];
+    if (!(mb == P - 1 || tid + 1 >= nwin)) XR = sxs[tid + 1];
+  }
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   constexpr int NW = NT / 32;
@@ -217,57 +279,7 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
 
   double XL = 0.0, XR = 0.0;
   if (A.mode == MODE_FULL) {
-    // ------------------------------------------------------------ dichotomy tree (a2)
-    // prefix maps A -> a A + b beta^R (left to right), suffix maps B -> c B + d beta^L
-    double pa = act ? bc[BC_A] : 1.0;
-    double pb = act ? bc[BC_B] * bR : 0.0;
-    double qa = act ? bc[BC_C] : 1.0;
-    double qb = act ? bc[BC_D] * bL : 0.0;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const double ya = __shfl_up_sync(0xffffffffu, pa, d), yb = __shfl_up_sync(0xffffffffu, pb, d);
-      const double za = __shfl_down_sync(0xffffffffu, qa, d), zb = __shfl_down_sync(0xffffffffu, qb, d);
-      if (lane >= d) {
-        pb = fma(pa, yb, pb);
-        pa = pa * ya;
-      }
-      if (lane + d < 32) {
-        qb = fma(qa, zb, qb);
-        qa = qa * za;
-      }
-    }
-    if (lane == 31) {
-      swa[wid] = pa;
-      swa[NW + wid] = pb;
-    }
-    if (lane == 0) {
-      swa[2 * NW + wid] = qa;
-      swa[3 * NW + wid] = qb;
-    }
-    // previous lane's inclusive prefix, next lane's inclusive suffix
-    double ea = __shfl_up_sync(0xffffffffu, pa, 1), eb = __shfl_up_sync(0xffffffffu, pb, 1);
-    double fa = __shfl_down_sync(0xffffffffu, qa, 1), fb = __shfl_down_sync(0xffffffffu, qb, 1);
-    if (lane == 0) {
-      ea = 1.0;
-      eb = 0.0;
-    }
-    if (lane == 31) {
-      fa = 1.0;
-      fb = 0.0;
-    }
-    __syncthreads();
-    double Aw = 0.0, Bw = 0.0;  // zero coupling enters at both window ends
-    for (int w = 0; w < wid; ++w) Aw = fma(swa[w], Aw, swa[NW + w]);
-    for (int w = NW - 1; w > wid; --w) Bw = fma(swa[2 * NW + w], Bw, swa[3 * NW + w]);
-    const double Am = fma(ea, Aw, eb);
-    const double Bm = fma(fa, Bw, fb);
-    sxs[tid] = fma(bc[BC_TL], Bm, bL) + Am;            // x_s (eq. 18)
-    sxe[tid] = fma(bc[BC_TR], Am, bR + Bm);            // x_e
-    __syncthreads();
-    if (act) {
-      if (!(mb == 0 || tid == 0)) XL = sxe[tid - 1];
-      if (!(mb == P - 1 || tid + 1 >= nwin)) XR = sxs[tid + 1];
-    }
+    tree_f64<NT>(bc, act, bL, bR, mb, P, nwin, tid, swa, sxs, sxe, XL, XR);
   } else {  // MODE_APPLY: first/last values of the neighbours from the global scan
     if (act) {
       XL = (mb == 0) ? 0.0 : A.iface[2 * (mb - 1) + 1];

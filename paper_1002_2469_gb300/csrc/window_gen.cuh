@@ -1,0 +1,174 @@
+// window_gen.cuh -- the window kernel for a general (non-Toeplitz) tridiagonal matrix, FP64.
+//
+// Row i reads a_i x_{i-1} + b_i x_i + c_i x_{i+1} = F_i.  The Dichotomy steps are those of the
+// Toeplitz kernel (window.cuh) with the preliminary quantities taken from the plan instead of
+// closed forms (Sec. 2.3, the general preliminary step):
+//   - local solve of each block m (rows s..e) with zero outside values, y = T_m^-1 F_m, by the
+//     block's own Thomas factors (forward z_i = (F_i - a_i z_{i-1}) rd_i, backward
+//     y_i = z_i - cp_i y_{i+1}; rd_i, cp_i precomputed per row);
+//   - alpha = y_s, omega = y_e, beta = M (alpha, omega) with the block's record (eq. 16);
+//   - the dichotomy tree over the window's blocks (tree_f64, eq. 15, 18);
+//   - interiors (eq. 7): x = y + x_{s-1} v + x_{e+1} w with the block spikes
+//     v = T_m^-1 (-a_s e_0), w = T_m^-1 (-c_e e_{n-1}) stored per row.
+// Per-row tables are interleaved by groups of 32 blocks (gen_index), so that the threads of a
+// warp -- consecutive blocks, one per thread -- read row i of their blocks contiguously.
+#pragma once
+#include "window.cuh"
+
+namespace dich {
+
+// per-row table fields of a general plan
+enum GenField : int { GF_A = 0, GF_RD = 1, GF_CP = 2, GF_V = 3, GF_W = 4, kGenFields = 5 };
+
+// element (block m, row i) of one field; n = rows per block
+__host__ __device__ inline int64_t gen_index(int64_t m, int i, int n) {
+  return ((m >> 5) * (int64_t)n + i) * 32 + (m & 31);
+}
+
+struct GenArgs {
+  WinArgs w;            // one plan record (plans[0]), block records in tabs, F, x, status, mode
+  const double* rows;   // per-row tables: field f at rows + f * stride
+  int64_t stride;       // doubles per field
+};
+
+// shared memory of the general window kernel: NT threads, n_smem rows
+__host__ __device__ inline size_t window_gen_smem_bytes(int NT, int n_smem) {
+  const size_t nw = (size_t)(NT / 32);
+  return sizeof(double) * ((size_t)n_smem * (size_t)(NT + 1) + 4 * (size_t)NT + 4 * nw + 8);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_window_gen(const GenArgs G) {
+  constexpr int LD = NT + 1;
+  const WinArgs& A = G.w;
+  extern __shared__ __align__(16) double sm[];
+  const int tid = threadIdx.x;
+  const int ns = A.n_smem;
+  double* S = sm;
+  double* sxs = S + (size_t)ns * LD;
+  double* sxe = sxs + NT;
+  double* scl = sxe + NT;
+  double* scr = scl + NT;
+  double* swa = scr + NT;                          // 4 * NW scan scratch
+
+  // ---------------------------------------------------------------- the window
+  const SysPlan* pp = A.plans;
+  const int64_t P = pp->P;
+  const int nown0 = pp->own;
+  const int64_t m0 = (int64_t)blockIdx.x * nown0;
+  const int nown = (int)min((int64_t)nown0, P - m0);
+  int hl = 0, hr = 0;
+  if (A.mode == MODE_FULL) {
+    hl = (int)min((int64_t)pp->hl, m0);
+    hr = (int)min((int64_t)pp->hr, P - m0 - nown);
+  }
+  const int64_t wlo = m0 - hl;
+  const int nwin = hl + nown + hr;
+  const int n = pp->n, nlast = pp->nlast;
+  const bool has_last = (wlo + nwin == P);
+  const int64_t row_lo = wlo * (int64_t)n;
+  const int len = nwin * n - (has_last ? (n - nlast) : 0);
+  const double* Fw = A.F + (int64_t)blockIdx.y * A.ldf;
+  double* xw = A.x + (int64_t)blockIdx.y * A.ldx;
+
+  // ---------------------------------------------------------------- F -> smem (transposed, async)
+  {
+    const double* src = Fw + row_lo;
+    int b = tid / n, i = tid - (tid / n) * n;
+    const int db = NT / n, di = NT - (NT / n) * n;
+    for (int j = tid; j < len; j += NT) {
+      cp_async8(&S[i * LD + b], src + j);
+      i += di;
+      b += db;
+      if (i >= n) {
+        i -= n;
+        ++b;
+      }
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  // ---------------------------------------------------------------- local solves (a1)
+  const bool act = tid < nwin;
+  const int64_t mb = wlo + tid;
+  const int nbk = (act && mb == P - 1) ? nlast : n;
+  const double* ra = G.rows + GF_A * G.stride;
+  const double* rd = G.rows + GF_RD * G.stride;
+  const double* rc = G.rows + GF_CP * G.stride;
+  const double* rv = G.rows + GF_V * G.stride;
+  const double* rw = G.rows + GF_W * G.stride;
+  double alpha = 0.0, omega = 0.0;
+  double* col = S + tid;
+  if (act) {
+    double z = 0.0;
+#pragma unroll 4
+    for (int i = 0; i < nbk; ++i) {
+      const int64_t k = gen_index(mb, i, n);
+      z = fma(-ra[k], z, col[i * LD]) * rd[k];
+      col[i * LD] = z;
+    }
+    double y = 0.0;
+#pragma unroll 4
+    for (int i = nbk - 1; i >= 0; --i) {
+      y = fma(-rc[gen_index(mb, i, n)], y, col[i * LD]);
+      col[i * LD] = y;
+    }
+    alpha = col[0];
+    omega = col[(nbk - 1) * LD];
+  }
+
+  // ---------------------------------------------------------------- beta (eq. 16)
+  const double* bc = A.tabs + pp->o_bcl + (act ? mb : 0) * kBC;
+  const double bL = act ? fma(bc[BC_M00], alpha, bc[BC_M01] * omega) : 0.0;
+  const double bR = act ? fma(bc[BC_M10], alpha, bc[BC_M11] * omega) : 0.0;
+  if (A.mode == MODE_BETA) {
+    if (act) {
+      A.beta[2 * mb] = bL;
+      A.beta[2 * mb + 1] = bR;
+    }
+    return;
+  }
+
+  double XL = 0.0, XR = 0.0;
+  if (A.mode == MODE_FULL) {
+    tree_f64<NT>(bc, act, bL, bR, mb, P, nwin, tid, swa, sxs, sxe, XL, XR);
+  } else if (act) {  // MODE_APPLY: neighbours' first/last values from the global scan
+    XL = (mb == 0) ? 0.0 : A.iface[2 * (mb - 1) + 1];
+    XR = (mb == P - 1) ? 0.0 : A.iface[2 * (mb + 1)];
+  }
+
+  // ---------------------------------------------------------------- interiors (eq. 7), per column
+  if (act) {
+#pragma unroll 4
+    for (int i = 0; i < nbk; ++i) {
+      const int64_t k = gen_index(mb, i, n);
+      col[i * LD] = fma(XR, rw[k], fma(XL, rv[k], col[i * LD]));
+    }
+  }
+  __syncthreads();
+
+  // ---------------------------------------------------------------- coalesced store of the own rows
+  unsigned bad = 0u;
+  {
+    const int jlo = hl * n;
+    const int jhi = min(len, (hl + nown) * n);
+    double* dst = xw + row_lo;
+    int b = (jlo + tid) / n, i = (jlo + tid) - ((jlo + tid) / n) * n;
+    const int db = NT / n, di = NT - (NT / n) * n;
+    for (int j = jlo + tid; j < jhi; j += NT) {
+      const double dv = S[i * LD + b];
+      __stcs(dst + j, dv);
+      if (A.check_finite && !isfinite(dv)) bad = 1u;
+      i += di;
+      b += db;
+      if (i >= n) {
+        i -= n;
+        ++b;
+      }
+    }
+  }
+  if (bad) atomicOr(A.status, (unsigned)ST_NONFINITE);
+}
+
+}  // namespace dich

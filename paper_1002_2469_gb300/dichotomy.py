@@ -22,7 +22,7 @@ __all__ = [
     "dichotomy_solve", "dichotomy_solve_series", "dichotomy_adjoint", "dichotomy_status", "dichotomy_destroy",
     "dichotomy_batch_prepare", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
     "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
-    "dichotomy_batch_destroy", "Plan", "Batch", "solve", "DichotomySolve", "DichotomySolveBatched",
+    "dichotomy_batch_destroy", "Plan", "Batch", "GenPlan", "solve", "DichotomySolve", "DichotomySolveBatched",
     "PREC_F64", "PREC_MIXED", "PREC_AUTO", "FLAG_FORCE_GENERAL", "FLAG_CHECK_FINITE", "DichotomyError",
 ]
 
@@ -287,6 +287,57 @@ class Batch:
         if getattr(self, "_h", None) is not None and _lib._lib_obj is not None:
             _lib._lib_obj.dichotomy_batch_destroy(self._h)
             self._h = None
+
+
+class GenPlan:
+    """A bound plan for a general tridiagonal matrix (sub-diagonal a, diagonal b, super-diagonal c,
+    host arrays of N entries; a[0] and c[N-1] are ignored): the general O(N) preliminary step of
+    the Dichotomy Algorithm, then any number of FP64 solves."""
+
+    def __init__(self, a, b, c, block_size=0, threads=0, flags=0, trunc_eps=0.0, device=None, stream=None):
+        a, b, c = _host_f64(a), _host_f64(b), _host_f64(c)
+        if not (a.size == b.size == c.size):
+            raise ValueError("a, b and c must have one entry per row")
+        self.N = int(b.size)
+        self._h = None
+        L = _lib.load()
+        h = ctypes.c_void_p()
+        opts = make_opts(block_size, PREC_F64, threads, flags, trunc_eps)
+        check(L.dichotomy_gen_plan(self.N, a.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p),
+                                   c.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts), ctypes.byref(h)),
+              "dichotomy_gen_plan")
+        self._h = h
+        info = _lib.dich_plan_info()
+        check(L.dichotomy_gen_info(h, ctypes.byref(info)), "dichotomy_gen_info")
+        self.info = {k: getattr(info, k) for k, _ in info._fields_}
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.empty(max(1, self.info["workspace_bytes"]) + 256, dtype=torch.uint8, device=dev)
+        base = (self.workspace.data_ptr() + 255) // 256 * 256
+        check(L.dichotomy_gen_bind(h, ctypes.c_void_p(base), self.info["workspace_bytes"], _stream(stream)),
+              "dichotomy_gen_bind")
+
+    def solve(self, F: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        x = torch.empty_like(F) if out is None else out
+        check(_lib.load().dichotomy_gen_solve(self._h, _dev(F, "F"), _dev(x, "x"), _stream(stream)),
+              "dichotomy_gen_solve")
+        return x
+
+    def solve_series(self, F: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        x = torch.empty_like(F) if out is None else out
+        pF, ldf = _dev_rows(F, "F")
+        px, ldx = _dev_rows(x, "x")
+        check(_lib.load().dichotomy_gen_solve_series(self._h, int(F.shape[0]), pF, ldf, px, ldx, _stream(stream)),
+              "dichotomy_gen_solve_series")
+        return x
+
+    def status(self, stream=None) -> int:
+        s = ctypes.c_int(0)
+        check(_lib.load().dichotomy_gen_status(self._h, _stream(stream), ctypes.byref(s)), "dichotomy_gen_status")
+        return int(s.value)
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and _lib._lib_obj is not None:
+            _lib._lib_obj.dichotomy_gen_destroy(self._h)
 
 
 def solve(t, F: torch.Tensor, **kw) -> torch.Tensor:

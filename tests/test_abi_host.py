@@ -206,3 +206,43 @@ def test_quasi_plan_validation_and_series_arguments_without_a_gpu():
         assert lib.dichotomy_solve_series(h, -1, None, 100, None, 100, None) == 1  # M < 0
     finally:
         lib.dichotomy_destroy(h)
+
+
+def test_general_plan_validation_and_geometry_without_a_gpu():
+    from paper_1002_2469_gb300 import _lib as L
+    lib = L.load()
+
+    def gen(a, b, c, **kw):
+        a, b, c = (np.ascontiguousarray(v, dtype=np.float64) for v in (a, b, c))
+        h = ctypes.c_void_p()
+        o = L.make_opts(**kw)
+        rc = lib.dichotomy_gen_plan(b.size, a.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p),
+                                    c.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o), ctypes.byref(h))
+        info = None
+        if rc == 0:
+            info = L.dich_plan_info()
+            assert lib.dichotomy_gen_info(h, ctypes.byref(info)) == 0
+            lib.dichotomy_gen_destroy(h)
+        return rc, info
+
+    rng = np.random.default_rng(0)
+    N = 1 << 18
+    a, c = rng.uniform(-1, 1, N), rng.uniform(-1, 1, N)
+    b = np.abs(a) + np.abs(c) + rng.uniform(0.5, 1.0, N)
+    rc, info = gen(a, b, c)
+    assert rc == 0 and info.path == 1 and info.halo_l >= 1          # strong dominance: halo windows
+    rc, info = gen(a, b, c, flags=1)
+    assert rc == 0 and info.path == 2
+    rc, info = gen(a[:1000], b[:1000], c[:1000])
+    assert rc == 0 and (info.P - 1) * info.n + info.n_last == 1000
+    bad = b.copy()
+    bad[17] = 0.5 * (abs(a[17]) + abs(c[17]))
+    assert gen(a, bad, c)[0] == 2                                   # a row without dominance
+    z = b.copy()
+    z[0] = 0.0
+    assert gen(np.zeros(N), z, np.zeros(N))[0] == 3                 # zero row: singular
+    nan = b.copy()
+    nan[5] = np.nan
+    assert gen(a, nan, c)[0] == 1
+    assert gen(a, b, c, precision=1)[0] == 11                       # FP64 only
+    assert gen([0.0], [2.0], [0.0])[0] == 0
