@@ -89,11 +89,15 @@ __device__ __forceinline__ void sweep_pair(double* S, int tid, int nrow_, int nb
 }
 
 // correction x = xp + cL v + cR w along the thread's pair of columns and the FP64 join, in place.
+// tv4[i] = (v_h, v_h, v_l, v_l) and tw4[j] = (w_h, w_h, w_l, w_l) hold the full-size blocks' spikes
+// (w reversed) with both lanes filled and zeros past their truncation lengths, so the full-block
+// loop needs neither bounds nor lane moves.  The system's last block (size nlast) reads its own
+// spikes from global memory (tvl, twl: float-float pairs).
 template <int LD, bool GUARD, bool FAST, int NR = 0>
 __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow_, int nb0, int nb1, bool last0,
-                                             bool last1, int n, int nlast, int Lv, int Lw, const float2* tv,
-                                             const float2* tw, const float2* tvl, const float2* twl, const ff2& cL,
-                                             const ff2& cR, int wscale) {
+                                             bool last1, int n, const float4* tv4, const float4* tw4,
+                                             const float2* tvl, const float2* twl, const ff2& cL, const ff2& cR,
+                                             int wscale) {
   const int nrow = NR ? NR : nrow_;
   const float2 clh = cL.h, cll = cL.l, crh = cR.h, crl = cR.l;
   const FastK fk = fast_k(wscale);
@@ -104,15 +108,9 @@ __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow_, int 
       double* row = S + (size_t)i * LD + 2 * tid;
       const float4 q = *reinterpret_cast<const float4*>(row);
       float2 xh = make_float2(q.x, q.y), xl = make_float2(q.z, q.w);
-      if (i < Lv) {
-        const float2 v = tv[i];
-        ff_fma_acc2(clh, cll, f2(v.x), f2(v.y), xh, xl);
-      }
-      const int j = n - 1 - i;
-      if (j < Lw) {
-        const float2 w = tw[j];
-        ff_fma_acc2(crh, crl, f2(w.x), f2(w.y), xh, xl);
-      }
+      const float4 v = tv4[i], w = tw4[n - 1 - i];
+      ff_fma_acc2(clh, cll, make_float2(v.x, v.y), make_float2(v.z, v.w), xh, xl);
+      ff_fma_acc2(crh, crl, make_float2(w.x, w.y), make_float2(w.z, w.w), xh, xl);
       if (FAST)
         *reinterpret_cast<double2*>(row) =
             make_double2(join_fast(xh.x, xl.x, wscale, fk), join_fast(xh.y, xl.y, wscale, fk));
@@ -121,33 +119,27 @@ __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow_, int 
             make_double2(join_dadd(xh.x, xl.x, wscale), join_dadd(xh.y, xl.y, wscale));
     }
   } else {
-    const int lv0 = last0 ? nlast : Lv, lw0 = last0 ? nlast : Lw;
-    const int lv1 = last1 ? nlast : Lv, lw1 = last1 ? nlast : Lw;
-    const float2* v0t = last0 ? tvl : tv;
-    const float2* w0t = last0 ? twl : tw;
-    const float2* v1t = last1 ? tvl : tv;
-    const float2* w1t = last1 ? twl : tw;
     for (int i = 0; i < nrow; ++i) {
       double* row = S + (size_t)i * LD + 2 * tid;
       const float4 q = *reinterpret_cast<const float4*>(row);
       float2 xh = make_float2(q.x, q.y), xl = make_float2(q.z, q.w);
       float2 vh = f2(0.f), vl = f2(0.f), wh = f2(0.f), wl = f2(0.f);
-      if (i < nb0 && i < lv0) {
-        vh.x = v0t[i].x;
-        vl.x = v0t[i].y;
-      }
-      if (i < nb1 && i < lv1) {
-        vh.y = v1t[i].x;
-        vl.y = v1t[i].y;
-      }
       const int j0 = nb0 - 1 - i, j1 = nb1 - 1 - i;
-      if (i < nb0 && j0 < lw0) {
-        wh.x = w0t[j0].x;
-        wl.x = w0t[j0].y;
+      if (i < nb0) {
+        const float2 v = last0 ? tvl[i] : make_float2(tv4[i].x, tv4[i].z);
+        const float2 w = last0 ? twl[j0] : make_float2(tw4[j0].x, tw4[j0].z);
+        vh.x = v.x;
+        vl.x = v.y;
+        wh.x = w.x;
+        wl.x = w.y;
       }
-      if (i < nb1 && j1 < lw1) {
-        wh.y = w1t[j1].x;
-        wl.y = w1t[j1].y;
+      if (i < nb1) {
+        const float2 v = last1 ? tvl[i] : make_float2(tv4[i].x, tv4[i].z);
+        const float2 w = last1 ? twl[j1] : make_float2(tw4[j1].x, tw4[j1].z);
+        vh.y = v.x;
+        vl.y = v.y;
+        wh.y = w.x;
+        wl.y = w.y;
       }
       ff_fma_acc2(clh, cll, vh, vl, xh, xl);
       ff_fma_acc2(crh, crl, wh, wl, xh, xl);
@@ -168,11 +160,9 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int ns = A.n_smem;
   double* S = sm;
-  float2* tv = reinterpret_cast<float2*>(S + (size_t)ns * LD);
-  float2* tw = tv + ns;
-  float2* tvl = tw + ns;
-  float2* twl = tvl + ns;
-  ffv* sxs = reinterpret_cast<ffv*>(twl + ns);
+  float4* tv4 = reinterpret_cast<float4*>(S + (size_t)ns * LD);   // spikes, both lanes, zero-padded
+  float4* tw4 = tv4 + ns;
+  ffv* sxs = reinterpret_cast<ffv*>(tw4 + ns);
   ffv* sxe = sxs + WB;
   ffv* swv = sxe + WB;  // 4 * NW scan scratch (also the exponent maxima)
 
@@ -230,13 +220,12 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   }
   {
     const float2* tf = reinterpret_cast<const float2*>(tab);
-    for (int i = tid; i < Lv; i += NT) tv[i] = tf[pp->o_vf + i];
-    for (int i = tid; i < Lw; i += NT) tw[i] = tf[pp->o_wf + i];
-    if (has_last)
-      for (int i = tid; i < nlast; i += NT) {
-        tvl[i] = tf[pp->o_vlf + i];
-        twl[i] = tf[pp->o_wlf + i];
-      }
+    for (int i = tid; i < ns; i += NT) {
+      const float2 v = (i < Lv) ? tf[pp->o_vf + i] : make_float2(0.f, 0.f);
+      const float2 w = (i < Lw) ? tf[pp->o_wf + i] : make_float2(0.f, 0.f);
+      tv4[i] = make_float4(v.x, v.x, v.y, v.y);
+      tw4[i] = make_float4(w.x, w.x, w.y, w.y);
+    }
   }
   cp_async_wait_all();
   __syncthreads();
@@ -451,17 +440,19 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
 
   // ---------------------------------------------------------------- correction (a3), per column
   const ff2 cL = ff2_sub(ff2_pair(XL0, XL1), xm), cR = ff2_pair(XR0, XR1);
+  const float2* tvl_g = reinterpret_cast<const float2*>(tab) + pp->o_vlf;    // last block's spikes
+  const float2* twl_g = reinterpret_cast<const float2*>(tab) + pp->o_wlf;
   if (full && fast && n == 16)
-    correct_pair<LD, false, true, 16>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL,
-                                      cR, wscale);
+    correct_pair<LD, false, true, 16>(S, tid, nrow, nb0, nb1, last0, last1, n, tv4, tw4, tvl_g, twl_g, cL, cR,
+                                  wscale);
   else if (full && fast)
-    correct_pair<LD, false, true>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL, cR,
+    correct_pair<LD, false, true>(S, tid, nrow, nb0, nb1, last0, last1, n, tv4, tw4, tvl_g, twl_g, cL, cR,
                                   wscale);
   else if (full)
-    correct_pair<LD, false, false>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL, cR,
-                                   wscale);
+    correct_pair<LD, false, false>(S, tid, nrow, nb0, nb1, last0, last1, n, tv4, tw4, tvl_g, twl_g, cL, cR,
+                                  wscale);
   else if (nrow > 0)
-    correct_pair<LD, true, false>(S, tid, nrow, nb0, nb1, last0, last1, n, nlast, Lv, Lw, tv, tw, tvl, twl, cL, cR,
+    correct_pair<LD, true, false>(S, tid, nrow, nb0, nb1, last0, last1, n, tv4, tw4, tvl_g, twl_g, cL, cR,
                                   wscale);
   __syncthreads();
 
