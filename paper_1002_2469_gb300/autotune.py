@@ -35,11 +35,12 @@ def _roots(t):
     return abs(tm1 / q), abs(tp1 / q)
 
 
-def key_of(t, N: int, form: int) -> str:
+def key_of(t, N: int, form: int, device_name: str | None = None) -> str:
+    """Cache key: GPU name, precision form, log2 N bucket and log2 decay-length bucket."""
     rs, ib = _roots(t)
     r = max(rs, ib)
     L = 1e9 if r >= 1.0 else (1 if r == 0.0 else math.log(2.0 ** -64) / math.log(r))
-    dev = torch.cuda.get_device_name()
+    dev = device_name if device_name is not None else torch.cuda.get_device_name()
     return f"{dev}|form{form}|logN{int(math.log2(max(N, 2)))}|logL{int(math.log2(max(L, 1.0)))}"
 
 
@@ -60,6 +61,7 @@ def _save(d):
 
 
 def _time(plan, F, x, reps=5, inner=5):
+    """Median over `reps` of the mean device time (ms) of `inner` solves of a Plan or Batch."""
     for _ in range(3):
         plan.solve(F, out=x)
     torch.cuda.synchronize()
@@ -126,3 +128,31 @@ def plan(t, N: int, precision: int = D.PREC_AUTO, tune_if_missing: bool = False)
     if not kw:
         kw = {"precision": precision}
     return D.Plan(*t, N, **kw)
+
+
+BATCH_CANDIDATES = [(0, 0), (64, 16), (128, 16), (64, 32), (128, 24), (256, 16)]
+
+
+def tune_batch(N, t_m1, t_0, t_1, precision: int = D.PREC_AUTO, candidates=None, verbose: bool = False) -> dict:
+    """Time (threads, block size) candidates for one batch of systems (sizes N, coefficient
+    arrays) with the library's batched solve and return the fastest as {"threads",
+    "block_size", "ms"}; (0, 0) is the library's default choice.  Not cached: a batch's
+    composition is its own key."""
+    import numpy as np
+    N = np.asarray(N, dtype=np.int64)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    F = torch.randn(int(N.sum()), dtype=torch.float64, device="cuda", generator=g)
+    x = torch.empty_like(F)
+    best = None
+    for nt, bs in (candidates or BATCH_CANDIDATES):
+        try:
+            b = D.Batch(N, t_m1, t_0, t_1, precision=precision, threads=nt, block_size=bs)
+        except D.DichotomyError:
+            continue
+        ms = _time(b, F, x)
+        if verbose:
+            print(f"threads={nt} n={bs} -> {ms:.4f} ms")
+        if best is None or ms < best["ms"]:
+            best = {"threads": nt, "block_size": bs, "ms": ms}
+    return best

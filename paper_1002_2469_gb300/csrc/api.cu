@@ -780,6 +780,17 @@ struct dich_batch_s {
   std::vector<SysBuild> fwd, adj;          // per system (N >= 2); empty records for N < 2
   std::vector<int32_t> form;               // per system
   std::vector<int32_t> trivial;            // systems with N == 1
+  std::vector<int32_t> general;            // systems on the general path
+  // general-path systems per form: windows, scan chunk map, their systems and first chunks,
+  // gradient ranges; beta and first/last values of all of them in two shared buffers
+  std::vector<Item> gitems[2];
+  std::vector<int32_t> gcmap[2], gsys[2];
+  std::vector<int64_t> gc0[2], gfirst[2], gcount[2];
+  int64_t gblocks = 0;
+  int n_smem_g[2] = {2, 2};
+  size_t off_gitems[2] = {0, 0}, off_gcmap[2] = {0, 0}, off_gsys[2] = {0, 0}, off_gc0[2] = {0, 0},
+         off_gfirst[2] = {0, 0}, off_gcount[2] = {0, 0}, off_gscan[2] = {0, 0}, off_gpart[2] = {0, 0},
+         off_gbeta = 0, off_giface = 0;
   std::vector<Item> items[2];              // per form
   std::vector<int32_t> sys_ids[2];         // per form: its systems, in item order
   std::vector<int64_t> first[2], count[2]; // per form, parallel to sys_ids: CTA range of each system
@@ -838,33 +849,45 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
     const int n = choose_n(h_N[s], window_blocks(NTs, b->form[s]), nmax, o.n_req, default_rows(b->form[s]));
     Opts oh = o;
     oh.flags &= ~DICH_FLAG_FORCE_GENERAL;
-    rc = build_system(h_tm1[s], h_t0[s], h_tp1[s], h_N[s], NTs, b->form[s], n, oh, false, b->fwd[s]);
-    if (!rc) rc = build_system(h_tp1[s], h_t0[s], h_tm1[s], h_N[s], NTs, b->form[s], n, oh, false, b->adj[s]);
+    rc = build_system(h_tm1[s], h_t0[s], h_tp1[s], h_N[s], NTs, b->form[s], n, oh, true, b->fwd[s]);
+    if (!rc) rc = build_system(h_tp1[s], h_t0[s], h_tm1[s], h_N[s], NTs, b->form[s], n, oh, true, b->adj[s]);
     if (rc) {
       delete b;
       return rc;
     }
-    for (SysBuild* sb : {&b->fwd[s], &b->adj[s]}) sb->rec.off = h_offset[s];
-    if (b->fwd[s].path == PATH_HALO || b->adj[s].path == PATH_HALO) {
+    const int WBs = window_blocks(NTs, b->form[s]);
+    bool general = (b->fwd[s].path == PATH_GENERAL || b->adj[s].path == PATH_GENERAL);
+    if (!general && (b->fwd[s].path == PATH_HALO || b->adj[s].path == PATH_HALO)) {
       const int hl = std::max(b->fwd[s].rec.hl, b->adj[s].rec.hl);
       const int hr = std::max(b->fwd[s].rec.hr, b->adj[s].rec.hr);
-      const int WBs = window_blocks(NTs, b->form[s]);
       if (hl + hr > WBs / 2) {
-        delete b;
-        return DICH_ERR_UNSUPPORTED;
-      }
-      for (SysBuild* sb : {&b->fwd[s], &b->adj[s]}) {
-        sb->rec.hl = hl;
-        sb->rec.hr = hr;
-        sb->rec.own = WBs - hl - hr;
-        sb->path = PATH_HALO;
+        general = true;
+      } else {
+        for (SysBuild* sb : {&b->fwd[s], &b->adj[s]}) {
+          sb->rec.hl = hl;
+          sb->rec.hr = hr;
+          sb->rec.own = WBs - hl - hr;
+          sb->path = PATH_HALO;
+        }
       }
     }
+    if (general) {
+      // coupling longer than half a window: this system takes the general path (its own beta
+      // pass, block scan and apply pass) after the windowed launches
+      Opts og = oh;
+      og.flags |= DICH_FLAG_FORCE_GENERAL;
+      build_system(h_tm1[s], h_t0[s], h_tp1[s], h_N[s], NTs, b->form[s], n, og, true, b->fwd[s]);
+      build_system(h_tp1[s], h_t0[s], h_tm1[s], h_N[s], NTs, b->form[s], n, og, true, b->adj[s]);
+      b->general.push_back((int32_t)s);
+    }
+    for (SysBuild* sb : {&b->fwd[s], &b->adj[s]}) sb->rec.off = h_offset[s];
   }
   // windows, longest systems first (LPT); windows of one system stay contiguous
   std::vector<int64_t> order;
+  std::vector<char> is_general((size_t)nsys, 0);
+  for (int32_t s : b->general) is_general[(size_t)s] = 1;
   for (int64_t s = 0; s < nsys; ++s)
-    if (h_N[s] >= 2) order.push_back(s);
+    if (h_N[s] >= 2 && !is_general[(size_t)s]) order.push_back(s);
   std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t c) { return h_N[a] > h_N[c]; });
   for (int64_t s : order) {
     const SysPlan& q = b->fwd[s].rec;
@@ -881,6 +904,29 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
     b->first[f].push_back(first);
     b->count[f].push_back((int64_t)b->items[f].size() - first);
     b->n_smem[f] = std::max(b->n_smem[f], q.n);
+  }
+  // general-path systems: block offsets in the shared buffers, windows without halo, scan chunks
+  for (int32_t s : b->general) {
+    SysPlan& rf = b->fwd[(size_t)s].rec;
+    rf.gboff = b->gblocks;
+    b->adj[(size_t)s].rec.gboff = b->gblocks;
+    b->gblocks += rf.P;
+    const int f = b->form[(size_t)s];
+    const int64_t first = (int64_t)b->gitems[f].size();
+    for (int64_t m0 = 0; m0 < rf.P; m0 += rf.own) {
+      Item it;
+      it.m0 = m0;
+      it.sys = s;
+      it.n_own = (int32_t)std::min<int64_t>(rf.own, rf.P - m0);
+      b->gitems[f].push_back(it);
+    }
+    b->gfirst[f].push_back(first);
+    b->gcount[f].push_back((int64_t)b->gitems[f].size() - first);
+    const int64_t nch = ceil_div(rf.P, kScanChunk);
+    b->gc0[f].push_back((int64_t)b->gcmap[f].size());
+    for (int64_t c = 0; c < nch; ++c) b->gcmap[f].push_back((int32_t)b->gsys[f].size());
+    b->gsys[f].push_back(s);
+    b->n_smem_g[f] = std::max(b->n_smem_g[f], rf.n);
   }
   // tables
   int64_t tabsz = 0;
@@ -907,12 +953,36 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
   }
   b->off_trivial = o_;
   o_ += align_up(sizeof(int32_t) * std::max<size_t>(1, b->trivial.size()));
+  for (int f = 0; f < 2; ++f) {
+    b->off_gitems[f] = o_;
+    o_ += align_up(sizeof(Item) * std::max<size_t>(1, b->gitems[f].size()));
+    b->off_gcmap[f] = o_;
+    o_ += align_up(sizeof(int32_t) * std::max<size_t>(1, b->gcmap[f].size()));
+    b->off_gsys[f] = o_;
+    o_ += align_up(sizeof(int32_t) * std::max<size_t>(1, b->gsys[f].size()));
+    b->off_gc0[f] = o_;
+    o_ += align_up(sizeof(int64_t) * std::max<size_t>(1, b->gc0[f].size()));
+    b->off_gfirst[f] = o_;
+    o_ += align_up(sizeof(int64_t) * std::max<size_t>(1, b->gfirst[f].size()));
+    b->off_gcount[f] = o_;
+    o_ += align_up(sizeof(int64_t) * std::max<size_t>(1, b->gcount[f].size()));
+  }
   b->off_tabs = o_;
   o_ += align_up(sizeof(double) * (size_t)std::max<int64_t>(1, tabsz));
   const size_t staged = o_;
   for (int f = 0; f < 2; ++f) {
     b->off_part[f] = o_;
     o_ += align_up(sizeof(double) * 3 * std::max<size_t>(1, b->items[f].size()));
+  }
+  b->off_gbeta = o_;
+  o_ += align_up(sizeof(double) * 2 * (size_t)std::max<int64_t>(1, b->gblocks));
+  b->off_giface = o_;
+  o_ += align_up(sizeof(double) * 2 * (size_t)std::max<int64_t>(1, b->gblocks));
+  for (int f = 0; f < 2; ++f) {
+    b->off_gscan[f] = o_;
+    o_ += align_up(sizeof(double) * 6 * std::max<size_t>(1, b->gcmap[f].size()));
+    b->off_gpart[f] = o_;
+    o_ += align_up(sizeof(double) * 3 * std::max<size_t>(1, b->gitems[f].size()));
   }
   b->ws_bytes = o_;
   b->staging.assign(staged, 0);
@@ -937,6 +1007,15 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
   }
   if (!b->trivial.empty())
     std::memcpy(S + b->off_trivial, b->trivial.data(), sizeof(int32_t) * b->trivial.size());
+  for (int f = 0; f < 2; ++f) {
+    if (b->gitems[f].empty()) continue;
+    std::memcpy(S + b->off_gitems[f], b->gitems[f].data(), sizeof(Item) * b->gitems[f].size());
+    std::memcpy(S + b->off_gcmap[f], b->gcmap[f].data(), sizeof(int32_t) * b->gcmap[f].size());
+    std::memcpy(S + b->off_gsys[f], b->gsys[f].data(), sizeof(int32_t) * b->gsys[f].size());
+    std::memcpy(S + b->off_gc0[f], b->gc0[f].data(), sizeof(int64_t) * b->gc0[f].size());
+    std::memcpy(S + b->off_gfirst[f], b->gfirst[f].data(), sizeof(int64_t) * b->gfirst[f].size());
+    std::memcpy(S + b->off_gcount[f], b->gcount[f].data(), sizeof(int64_t) * b->gcount[f].size());
+  }
   *out = b;
   return DICH_OK;
 }
@@ -995,6 +1074,52 @@ static int batch_launch(dich_batch_t b, const double* F, double* x, const double
   if (!b->trivial.empty()) {
     cudaError_t e = launch_trivial(d_plans, (const int32_t*)(b->d_ws + b->off_trivial), (int64_t)b->trivial.size(),
                                    adjoint ? nullptr : F, x, xf, adjoint ? F : nullptr, gt, sys_offset, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  // systems on the general path, per form: one beta pass over all their windows, one block scan
+  // over all their blocks, one apply pass (with the gradient sums for the adjoint)
+  for (int f = 0; f < 2; ++f) {
+    const int64_t ng = (int64_t)b->gitems[f].size();
+    if (ng == 0) continue;
+    WinArgs a{};
+    a.plans = d_plans;
+    a.tabs = d_tabs;
+    a.items = (const Item*)(b->d_ws + b->off_gitems[f]);
+    a.F = F;
+    a.x = x;
+    a.status = d_status;
+    a.check_finite = (b->opts.flags & DICH_FLAG_CHECK_FINITE) ? 1 : 0;
+    a.n_smem = b->n_smem_g[f];
+    a.sys_offset = sys_offset;
+    double* beta = (double*)(b->d_ws + b->off_gbeta);
+    double* iface = (double*)(b->d_ws + b->off_giface);
+    const size_t smem = smem_bytes(b->NT[f], a.n_smem, f);
+    auto launch = [&](const WinArgs& w) {
+      return f == FORM_F64 ? launch_window_f64(b->NT[f], (int)ng, smem, st, w)
+                           : launch_window_mixed(b->NT[f], (int)ng, smem, st, w);
+    };
+    WinArgs wb = a;
+    wb.mode = MODE_BETA;
+    wb.beta = beta;
+    cudaError_t e = launch(wb);
+    if (e == cudaSuccess) {
+      ScanMap map{(const int32_t*)(b->d_ws + b->off_gcmap[f]), (const int32_t*)(b->d_ws + b->off_gsys[f]),
+                  (const int64_t*)(b->d_ws + b->off_gc0[f])};
+      e = launch_block_scan_batched(d_plans + sys_offset, d_tabs, map, (int64_t)b->gcmap[f].size(),
+                                    (int64_t)b->gsys[f].size(), beta, iface, (double*)(b->d_ws + b->off_gscan[f]),
+                                    st);
+    }
+    if (e == cudaSuccess) {
+      a.mode = MODE_APPLY;
+      a.iface = iface;
+      a.xf = adjoint ? xf : nullptr;
+      a.part = adjoint ? (double*)(b->d_ws + b->off_gpart[f]) : nullptr;
+      e = launch(a);
+    }
+    if (e == cudaSuccess && adjoint)
+      e = launch_adj_finalize(a.part, (const int32_t*)(b->d_ws + b->off_gsys[f]),
+                              (const int64_t*)(b->d_ws + b->off_gfirst[f]),
+                              (const int64_t*)(b->d_ws + b->off_gcount[f]), 0, (int64_t)b->gsys[f].size(), gt, st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   return DICH_OK;

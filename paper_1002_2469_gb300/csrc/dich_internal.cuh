@@ -79,7 +79,8 @@ struct SysPlan {
   float rs_h, rs_l, ib_h, ib_l, g_h, g_l;   // float-float splits of rs, ib, g
   double v0, vend, w0, wend;                // corner spikes, full-size blocks
   double v0l, vendl, w0l, wendl;            // corner spikes, last block
-  double pad_[2];
+  int64_t gboff;    // general path in a batch: first block of this system in the beta / first-last buffers
+  double pad_;
   // table sub-offsets (in doubles, relative to `tab`)
   int32_t o_v, o_w, o_vl, o_wl;             // v[Lv], w_rev[Lw], v_last[nlast], w_last_rev[nlast]
   int32_t o_vf, o_wf, o_vlf, o_wlf;         // float-float copies (float2 per entry)

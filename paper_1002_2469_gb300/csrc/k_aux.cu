@@ -104,13 +104,29 @@ __device__ __forceinline__ void thread_maps(const SysPlan* pp, const double* tab
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_bscan_reduce(const SysPlan* pp, const double* tabs, int64_t P,
-                                                               const double* beta, double* agg) {
+// Chunk c of a scan: its system (the single system of `plans` when map.cmap is null, else the
+// general-path system map.sys[map.cmap[c]] of a batch) and its chunk index within that system.
+__device__ __forceinline__ const SysPlan* chunk_system(const SysPlan* plans, const ScanMap& map, int64_t c,
+                                                      int64_t& lc) {
+  if (!map.cmap) {
+    lc = c;
+    return plans;
+  }
+  const int j = map.cmap[c];
+  lc = c - map.c0[j];
+  return plans + map.sys[j];
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_bscan_reduce(const SysPlan* plans, const double* tabs, ScanMap map,
+                                                               const double* beta_base, double* agg) {
   __shared__ double sh[4 * kScanThreads / 32];
+  int64_t lc;
+  const SysPlan* pp = chunk_system(plans, map, blockIdx.x, lc);
   const double* tab = tabs + pp->tab;
-  const int64_t m_first = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPer;
+  const double* beta = beta_base + 2 * pp->gboff;
+  const int64_t m_first = lc * kScanChunk + (int64_t)threadIdx.x * kScanPer;
   double pa, pb, sa, sb, ea, eb;
-  thread_maps(pp, tab, P, beta, m_first, pa, pb, sa, sb);
+  thread_maps(pp, tab, pp->P, beta, m_first, pa, pb, sa, sb);
   cta_prefix<kScanThreads>(pa, pb, ea, eb, sh);
   cta_suffix<kScanThreads>(sa, sb, ea, eb, sh);
   if (threadIdx.x == kScanThreads - 1) {
@@ -123,22 +139,29 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan_reduce(const SysPlan* pp
   }
 }
 
-// carry[2 c] = A entering chunk c, carry[2 c + 1] = B at the end of chunk c
-__global__ void __launch_bounds__(1024) k_bscan_top(const double* agg, int64_t nchunks, double* carry) {
+// One CTA per system: over the system's chunks c0 .. c0 + nchunks - 1,
+// carry[2 c] = A entering chunk c, carry[2 c + 1] = B at the end of chunk c.
+__global__ void __launch_bounds__(1024) k_bscan_top(const SysPlan* plans, ScanMap map, const double* agg,
+                                                    double* carry) {
   __shared__ double sh[4 * 1024 / 32];
   __shared__ double run;
+  const SysPlan* pp = map.cmap ? plans + map.sys[blockIdx.x] : plans;
+  const int64_t cbase = map.cmap ? map.c0[blockIdx.x] : 0;
+  const int64_t nchunks = (pp->P + kScanChunk - 1) / kScanChunk;
+  const double* ag = agg + 4 * cbase;
+  double* ca = carry + 2 * cbase;
   if (threadIdx.x == 0) run = 0.0;
   __syncthreads();
   for (int64_t g0 = 0; g0 < nchunks; g0 += 1024) {
     const int64_t c = g0 + threadIdx.x;
     double ia = 1.0, ib = 0.0, ea, eb;
     if (c < nchunks) {
-      ia = agg[4 * c];
-      ib = agg[4 * c + 1];
+      ia = ag[4 * c];
+      ib = ag[4 * c + 1];
     }
     cta_prefix<1024>(ia, ib, ea, eb, sh);
     const double r = run;
-    if (c < nchunks) carry[2 * c] = fma(ea, r, eb);
+    if (c < nchunks) ca[2 * c] = fma(ea, r, eb);
     __syncthreads();
     if (threadIdx.x == 1023) run = fma(ia, r, ib);
     __syncthreads();
@@ -150,24 +173,29 @@ __global__ void __launch_bounds__(1024) k_bscan_top(const double* agg, int64_t n
     const int64_t c = g * 1024 + threadIdx.x;
     double ia = 1.0, ib = 0.0, ea, eb;
     if (c < nchunks) {
-      ia = agg[4 * c + 2];
-      ib = agg[4 * c + 3];
+      ia = ag[4 * c + 2];
+      ib = ag[4 * c + 3];
     }
     cta_suffix<1024>(ia, ib, ea, eb, sh);
     const double r = run;
-    if (c < nchunks) carry[2 * c + 1] = fma(ea, r, eb);
+    if (c < nchunks) ca[2 * c + 1] = fma(ea, r, eb);
     __syncthreads();
     if (threadIdx.x == 0) run = fma(ia, r, ib);
     __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_bscan_apply(const SysPlan* pp, const double* tabs, int64_t P,
-                                                              const double* beta, const double* carry,
-                                                              double* iface) {
+__global__ void __launch_bounds__(kScanThreads) k_bscan_apply(const SysPlan* plans, const double* tabs, ScanMap map,
+                                                              const double* beta_base, const double* carry,
+                                                              double* iface_base) {
   __shared__ double sh[4 * kScanThreads / 32];
+  int64_t lc;
+  const SysPlan* pp = chunk_system(plans, map, blockIdx.x, lc);
+  const int64_t P = pp->P;
   const double* tab = tabs + pp->tab;
-  const int64_t m_first = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPer;
+  const double* beta = beta_base + 2 * pp->gboff;
+  double* iface = iface_base + 2 * pp->gboff;
+  const int64_t m_first = lc * kScanChunk + (int64_t)threadIdx.x * kScanPer;
   double pa, pb, sa, sb, ea, eb, fa, fb;
   thread_maps(pp, tab, P, beta, m_first, pa, pb, sa, sb);
   cta_prefix<kScanThreads>(pa, pb, ea, eb, sh);
@@ -205,11 +233,18 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan_apply(const SysPlan* pp,
 cudaError_t launch_block_scan(const SysPlan* plan, const double* tabs, int64_t P, const double* beta,
                               double* iface, double* scratch, cudaStream_t st) {
   const int64_t nchunks = (P + kScanChunk - 1) / kScanChunk;
+  return launch_block_scan_batched(plan, tabs, ScanMap{}, nchunks, 1, beta, iface, scratch, st);
+}
+
+cudaError_t launch_block_scan_batched(const SysPlan* plans, const double* tabs, const ScanMap& map, int64_t nchunks,
+                                      int64_t nsys, const double* beta, double* iface, double* scratch,
+                                      cudaStream_t st) {
+  if (nchunks <= 0) return cudaSuccess;
   double* agg = scratch;
   double* carry = scratch + 4 * nchunks;
-  k_bscan_reduce<<<(unsigned)nchunks, kScanThreads, 0, st>>>(plan, tabs, P, beta, agg);
-  k_bscan_top<<<1, 1024, 0, st>>>(agg, nchunks, carry);
-  k_bscan_apply<<<(unsigned)nchunks, kScanThreads, 0, st>>>(plan, tabs, P, beta, carry, iface);
+  k_bscan_reduce<<<(unsigned)nchunks, kScanThreads, 0, st>>>(plans, tabs, map, beta, agg);
+  k_bscan_top<<<(unsigned)nsys, 1024, 0, st>>>(plans, map, agg, carry);
+  k_bscan_apply<<<(unsigned)nchunks, kScanThreads, 0, st>>>(plans, tabs, map, beta, carry, iface);
   return cudaGetLastError();
 }
 

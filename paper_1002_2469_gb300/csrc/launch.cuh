@@ -20,6 +20,19 @@ constexpr int kScanChunk = kScanThreads * kScanPer;
 cudaError_t launch_block_scan(const SysPlan* plan, const double* tabs, int64_t P, const double* beta,
                               double* iface, double* scratch, cudaStream_t st);
 
+// the general-path systems of a batch in one scan: chunk c (kScanChunk blocks) belongs to system
+// plans[sys[cmap[c]]], whose chunks start at c0[cmap[c]]; a system's beta and first/last values
+// start at block SysPlan::gboff of the shared buffers.  A null cmap is the single-system scan.
+struct ScanMap {
+  const int32_t* cmap;
+  const int32_t* sys;
+  const int64_t* c0;
+};
+//   scratch: 6 doubles per chunk; nsys systems, nchunks chunks in all
+cudaError_t launch_block_scan_batched(const SysPlan* plans, const double* tabs, const ScanMap& map, int64_t nchunks,
+                                      int64_t nsys, const double* beta, double* iface, double* scratch,
+                                      cudaStream_t st);
+
 // adjoint: gt[3 s + j] = -(sum of part[3 i + j] over the CTAs i of system s), fixed order.
 //   For k = 0..nsys-1: s = sys_ids[k], CTAs first[k] .. first[k] + count[k] - 1 (device
 //   arrays), or (nullptr) one system s = k = 0 covering CTAs 0 .. count0 - 1.

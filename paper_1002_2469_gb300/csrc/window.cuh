@@ -271,8 +271,8 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
 
   if (A.mode == MODE_BETA) {  // general path: beta leaves the window
     if (act) {
-      A.beta[2 * mb] = bL;
-      A.beta[2 * mb + 1] = bR;
+      A.beta[2 * (pp->gboff + mb)] = bL;
+      A.beta[2 * (pp->gboff + mb) + 1] = bR;
     }
     return;
   }
@@ -282,8 +282,8 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
     tree_f64<NT>(bc, act, bL, bR, mb, P, nwin, tid, swa, sxs, sxe, XL, XR);
   } else {  // MODE_APPLY: first/last values of the neighbours from the global scan
     if (act) {
-      XL = (mb == 0) ? 0.0 : A.iface[2 * (mb - 1) + 1];
-      XR = (mb == P - 1) ? 0.0 : A.iface[2 * (mb + 1)];
+      XL = (mb == 0) ? 0.0 : A.iface[2 * (pp->gboff + mb - 1) + 1];
+      XR = (mb == P - 1) ? 0.0 : A.iface[2 * (pp->gboff + mb + 1)];
     }
   }
   // correction coefficients of the block spikes (a3): x = xp + cL v + cR w

@@ -124,8 +124,8 @@ __global__ void __launch_bounds__(NT) k_window_gen(const GenArgs G) {
   const double bR = act ? fma(bc[BC_M10], alpha, bc[BC_M11] * omega) : 0.0;
   if (A.mode == MODE_BETA) {
     if (act) {
-      A.beta[2 * mb] = bL;
-      A.beta[2 * mb + 1] = bR;
+      A.beta[2 * (pp->gboff + mb)] = bL;
+      A.beta[2 * (pp->gboff + mb) + 1] = bR;
     }
     return;
   }
@@ -134,8 +134,8 @@ __global__ void __launch_bounds__(NT) k_window_gen(const GenArgs G) {
   if (A.mode == MODE_FULL) {
     tree_f64<NT>(bc, act, bL, bR, mb, P, nwin, tid, swa, sxs, sxe, XL, XR);
   } else if (act) {  // MODE_APPLY: neighbours' first/last values from the global scan
-    XL = (mb == 0) ? 0.0 : A.iface[2 * (mb - 1) + 1];
-    XR = (mb == P - 1) ? 0.0 : A.iface[2 * (mb + 1)];
+    XL = (mb == 0) ? 0.0 : A.iface[2 * (pp->gboff + mb - 1) + 1];
+    XR = (mb == P - 1) ? 0.0 : A.iface[2 * (pp->gboff + mb + 1)];
   }
 
   // ---------------------------------------------------------------- interiors (eq. 7), per column

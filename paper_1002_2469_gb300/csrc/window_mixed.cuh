@@ -339,12 +339,12 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   if (A.mode == MODE_BETA) {  // general path: beta leaves the window as unscaled FP64
     const double dn = pow2i(-wscale);
     if (act0) {
-      A.beta[2 * mb0] = ff_to_double(ff2_x(bL)) * dn;
-      A.beta[2 * mb0 + 1] = ff_to_double(ff2_x(bR)) * dn;
+      A.beta[2 * (pp->gboff + mb0)] = ff_to_double(ff2_x(bL)) * dn;
+      A.beta[2 * (pp->gboff + mb0) + 1] = ff_to_double(ff2_x(bR)) * dn;
     }
     if (act1) {
-      A.beta[2 * mb1] = ff_to_double(ff2_y(bL)) * dn;
-      A.beta[2 * mb1 + 1] = ff_to_double(ff2_y(bR)) * dn;
+      A.beta[2 * (pp->gboff + mb1)] = ff_to_double(ff2_y(bL)) * dn;
+      A.beta[2 * (pp->gboff + mb1) + 1] = ff_to_double(ff2_y(bR)) * dn;
     }
     return;
   }
@@ -429,12 +429,12 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
       return ffv{t.x, t.y};
     };
     if (act0) {
-      if (mb0 > 0) XL0 = to_ff(A.iface[2 * (mb0 - 1) + 1]);
-      if (mb0 < P - 1) XR0 = to_ff(A.iface[2 * (mb0 + 1)]);
+      if (mb0 > 0) XL0 = to_ff(A.iface[2 * (pp->gboff + mb0 - 1) + 1]);
+      if (mb0 < P - 1) XR0 = to_ff(A.iface[2 * (pp->gboff + mb0 + 1)]);
     }
     if (act1) {
-      if (mb1 > 0) XL1 = to_ff(A.iface[2 * (mb1 - 1) + 1]);
-      if (mb1 < P - 1) XR1 = to_ff(A.iface[2 * (mb1 + 1)]);
+      if (mb1 > 0) XL1 = to_ff(A.iface[2 * (pp->gboff + mb1 - 1) + 1]);
+      if (mb1 < P - 1) XR1 = to_ff(A.iface[2 * (pp->gboff + mb1 + 1)]);
     }
   }
 
@@ -442,7 +442,10 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   const ff2 cL = ff2_sub(ff2_pair(XL0, XL1), xm), cR = ff2_pair(XR0, XR1);
   const float2* tvl_g = reinterpret_cast<const float2*>(tab) + pp->o_vlf;    // last block's spikes
   const float2* twl_g = reinterpret_cast<const float2*>(tab) + pp->o_wlf;
-  if (full && fast && n == 16)
+  // blocks of the halo are not stored: a thread whose two blocks both lie in it skips the correction
+  const bool owns = (b1 >= hl) && (b0 < hl + nown);
+  if (!owns) {
+  } else if (full && fast && n == 16)
     correct_pair<LD, false, true, 16>(S, tid, nrow, nb0, nb1, last0, last1, n, tv4, tw4, tvl_g, twl_g, cL, cR,
                                   wscale);
   else if (full && fast)

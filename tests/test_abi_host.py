@@ -246,3 +246,16 @@ def test_general_plan_validation_and_geometry_without_a_gpu():
     assert gen(a, nan, c)[0] == 1
     assert gen(a, b, c, precision=1)[0] == 11                       # FP64 only
     assert gen([0.0], [2.0], [0.0])[0] == 0
+
+
+def test_batch_with_long_coupling_prepares_without_a_gpu():
+    """A system whose coupling outlasts half a window (here the 1-D Laplacian) is planned on the
+    general path inside the batch instead of being refused."""
+    from paper_1002_2469_gb300 import dichotomy as D
+    N = np.array([1 << 20, 5000])
+    h = D.dichotomy_batch_prepare(N, np.array([0, 1 << 20]), np.array([-1.0, -1.0]), np.array([2.0, 4.0]),
+                                  np.array([-1.0, -1.0]), D.make_opts(precision=2))
+    try:
+        assert D.dichotomy_batch_workspace_bytes(h) > 32 * (1 << 20) // 16   # beta and first/last values
+    finally:
+        D.dichotomy_batch_destroy(h)

@@ -331,6 +331,43 @@ def test_batched_edge_systems(D):
             assert rel(x[o:o + n], ref[o:o + n]) < TOL
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_batched_general_path_systems(D, prec):
+    """Systems whose coupling outlasts half a window (the 1-D Laplacian, weakly dominant and
+    low Poisson modes) take the general path inside a batch, beside windowed ones; forward and
+    adjoint against the oracle (binary128 arbitrating the ill-conditioned ones)."""
+    N = np.array([100000, 3000, 131072, 70001, 1, 50000])
+    tm1 = np.array([-1.0, -1.0, -1.0, -1.2, -1.0, -0.7])
+    t0 = np.array([2.0, 4.0, 2.0 + 5.88e-7, 2.5, 3.0, 1.7 + 1e-4])
+    tp1 = np.array([-1.0, -1.0, -1.0, -0.8, -1.0, -1.0])
+    off = W.offsets(N)
+    rng = np.random.default_rng(13)
+    F = rng.uniform(-1, 1, int(N.sum()))
+    w = rng.uniform(-1, 1, int(N.sum()))
+    b = D.Batch(N, tm1, t0, tp1, precision=prec)
+    Fd = torch.from_numpy(F).cuda()
+    x = b.solve(Fd)
+    gF, gt = b.adjoint(torch.from_numpy(w).cuda(), x)
+    assert b.status() == 0
+    x, gF, gt = x.cpu().numpy(), gF.cpu().numpy(), gt.cpu().numpy()
+    import math
+    for s in range(N.size):
+        sl = slice(int(off[s]), int(off[s] + N[s]))
+        t = (tm1[s], t0[s], tp1[s])
+        xq = oracle.thomas_q(t, F[sl])
+        e_or = rel(oracle.thomas(t, F[sl]), xq)
+        assert rel(x[sl], xq) <= max(TOL, 20 * e_or), s
+        lam, g = oracle.adjoint(t, w[sl], oracle.thomas(t, F[sl]))
+        lamq = oracle.thomas_q((tp1[s], t0[s], tm1[s]), w[sl])
+        e_lam = rel(lam, lamq)
+        assert rel(gF[sl], lamq) <= max(TOL, 20 * e_lam), s
+        # dL/dt from the binary128 solutions, summed exactly: the GPU's gradient may be as far
+        # from it as its forward and adjoint solutions allow
+        gq = -np.array([math.fsum(lamq[1:] * xq[:-1]), math.fsum(lamq * xq), math.fsum(lamq[:-1] * xq[1:])])
+        e_g = np.max(np.abs(g - gq)) / np.max(np.abs(gq))
+        assert np.max(np.abs(gt[s] - gq)) / np.max(np.abs(gq)) <= max(1e-10, 20 * max(e_or, e_lam, e_g)), s
+
+
 @pytest.fixture(scope="module")
 def c3_reference():
     """C3 inputs, the FP64 oracle and the binary128 oracle for every mode."""
@@ -460,3 +497,45 @@ def test_autograd_function(D):
     lam, g = oracle.adjoint(tt, w.cpu().numpy(), oracle.thomas(tt, F.detach().cpu().numpy()))
     assert rel(F.grad.cpu().numpy(), lam) < TOL
     assert np.max(np.abs(t.grad.cpu().numpy() - g)) <= TOL * np.max(np.abs(g))
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_cuda_graph_capture_and_replay(D, flags):
+    """A bound plan's solve only enqueues kernels on the caller's stream (no allocation, no host
+    synchronisation), so it can be captured once in a CUDA graph and replayed on new data."""
+    t, N = (-1.2, 2.5, -0.8), 100000
+    rng = np.random.default_rng(21)
+    F = torch.from_numpy(rng.standard_normal(N)).cuda()
+    x = torch.empty_like(F)
+    plan = D.Plan(*t, N, precision=D.PREC_AUTO, flags=flags)
+    plan.solve(F, out=x)                       # warm-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.solve(F, out=x)
+    for _ in range(2):
+        Fh = rng.standard_normal(N)
+        F.copy_(torch.from_numpy(Fh))
+        g.replay()
+        torch.cuda.synchronize()
+        assert rel(x.cpu().numpy(), oracle.thomas(t, Fh)) < TOL
+    assert plan.status() == 0
+
+
+def test_cuda_graph_capture_of_a_batch(D):
+    N, off, tm1, t0, tp1, F = W.uneven_c4(nsys=40, hi=1 << 14)
+    b = D.Batch(N, tm1, t0, tp1, precision=D.PREC_AUTO)
+    Fd = torch.from_numpy(F).cuda()
+    x = torch.empty_like(Fd)
+    b.solve(Fd, out=x)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.solve(Fd, out=x)
+    x.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    ref = oracle.thomas_batched(tm1, t0, tp1, N, off, F)
+    for s in range(N.size):
+        sl = slice(int(off[s]), int(off[s] + N[s]))
+        assert rel(x[sl].cpu().numpy(), ref[sl]) < TOL
