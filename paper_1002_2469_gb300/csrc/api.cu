@@ -102,13 +102,16 @@ void split_ff(double d, float& h, float& l) {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Choose the block size: one window when the system fits, else the largest rows per block.
-// A last block of a single row is not allowed (Sec. 2.1 asks for sub-vectors of >= 2
-// rows), so n moves to the nearest size with N mod n != 1: upwards when the system fits in
-// one window (every larger n still does), else downwards first.
+// Choose the block size: one window when the system fits in one window of default-size
+// blocks (n = ceil(N / window blocks) <= n_def), else n_def rows per block.  Longer blocks
+// would fit one window up to nmax rows, but they serialise the sweeps and enlarge the shared
+// memory of every CTA of a batched launch (measured: a batch with some one-window systems of
+// 50-row blocks ran at half speed).  A last block of a single row is not allowed (Sec. 2.1
+// asks for sub-vectors of >= 2 rows), so n moves to the nearest size with N mod n != 1:
+// upwards when the system fits in one window (every larger n still does), else downwards first.
 int choose_n(int64_t N, int NT, int nmax, int n_req, int n_def) {
   auto ok = [&](int64_t c) { return c >= 2 && (c >= N || N % c != 1); };
-  const bool one_window = (n_req <= 0) && (N <= (int64_t)NT * nmax);
+  const bool one_window = (n_req <= 0) && (N <= (int64_t)NT * std::min(nmax, n_def));
   int n;
   if (n_req > 0)
     n = std::min(n_req, nmax);
@@ -774,8 +777,17 @@ void dichotomy_destroy(dich_plan_t p) { delete p; }
 
 // ================================================================== batches
 struct dich_batch_s {
+  ~dich_batch_s() {
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (aux) cudaStreamDestroy(aux);
+  }
   int64_t nsys = 0;
   Opts opts;
+  // a second stream for the FP64-form windows when a batch has both forms: the two launches
+  // overlap (fork/join through events on the caller's stream; CUDA-graph capture follows them)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int NT[2] = {64, 128};                  // window width per form
   std::vector<SysBuild> fwd, adj;          // per system (N >= 2); empty records for N < 2
   std::vector<int32_t> form;               // per system
@@ -1035,6 +1047,17 @@ int dichotomy_batch_bind(dich_batch_t b, void* d_ws, size_t bytes, void* stream)
   if (e != cudaSuccess) return cuda_fail(e);
   b->d_ws = (char*)d_ws;
   b->d_ws_bytes = bytes;
+  if (!b->items[0].empty() && !b->items[1].empty() && !b->aux) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) == cudaSuccess) {
+      // both forms overlap from now on
+    } else {
+      cudaGetLastError();   // no second stream: the two forms run one after the other
+    }
+  }
   return DICH_OK;
 }
 
@@ -1044,9 +1067,17 @@ static int batch_launch(dich_batch_t b, const double* F, double* x, const double
   const double* d_tabs = (const double*)(b->d_ws + b->off_tabs);
   unsigned* d_status = (unsigned*)(b->d_ws + b->off_status);
   const int sys_offset = adjoint ? (int)b->nsys : 0;
+  // both forms present: the FP64-form windows go to the second stream after a fork event
+  const bool fork = b->aux && b->ev_fork && b->ev_join && !b->items[0].empty() && !b->items[1].empty();
+  if (fork) {
+    cudaError_t e = cudaEventRecord(b->ev_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   for (int f = 0; f < 2; ++f) {
     const int64_t nitems = (int64_t)b->items[f].size();
     if (nitems == 0) continue;
+    const cudaStream_t sf = (fork && f == FORM_F64) ? b->aux : st;
     WinArgs a{};
     a.plans = d_plans;
     a.tabs = d_tabs;
@@ -1061,15 +1092,20 @@ static int batch_launch(dich_batch_t b, const double* F, double* x, const double
     a.n_smem = b->n_smem[f];
     a.sys_offset = sys_offset;
     const size_t smem = smem_bytes(b->NT[f], a.n_smem, f);
-    cudaError_t e = (f == FORM_F64) ? launch_window_f64(b->NT[f], (int)nitems, smem, st, a)
-                                    : launch_window_mixed(b->NT[f], (int)nitems, smem, st, a);
+    cudaError_t e = (f == FORM_F64) ? launch_window_f64(b->NT[f], (int)nitems, smem, sf, a)
+                                    : launch_window_mixed(b->NT[f], (int)nitems, smem, sf, a);
     if (e != cudaSuccess) return cuda_fail(e);
     if (adjoint) {
       e = launch_adj_finalize(a.part, (const int32_t*)(b->d_ws + b->off_ids[f]),
                               (const int64_t*)(b->d_ws + b->off_first[f]),
-                              (const int64_t*)(b->d_ws + b->off_count[f]), 0, (int64_t)b->sys_ids[f].size(), gt, st);
+                              (const int64_t*)(b->d_ws + b->off_count[f]), 0, (int64_t)b->sys_ids[f].size(), gt, sf);
       if (e != cudaSuccess) return cuda_fail(e);
     }
+  }
+  if (fork) {
+    cudaError_t e = cudaEventRecord(b->ev_join, b->aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->ev_join, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
   }
   if (!b->trivial.empty()) {
     cudaError_t e = launch_trivial(d_plans, (const int32_t*)(b->d_ws + b->off_trivial), (int64_t)b->trivial.size(),

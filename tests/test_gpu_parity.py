@@ -523,7 +523,11 @@ def test_cuda_graph_capture_and_replay(D, flags):
 
 
 def test_cuda_graph_capture_of_a_batch(D):
+    """A batch with both precision forms (the FP64-form windows run on the library's second
+    stream, forked from and joined to the caller's) captured and replayed."""
     N, off, tm1, t0, tp1, F = W.uneven_c4(nsys=40, hi=1 << 14)
+    t0 = t0.copy()
+    t0[:5] = np.abs(tm1[:5]) + np.abs(tp1[:5]) + 1e-4          # weak dominance: the FP64 form under AUTO
     b = D.Batch(N, tm1, t0, tp1, precision=D.PREC_AUTO)
     Fd = torch.from_numpy(F).cuda()
     x = torch.empty_like(Fd)
@@ -535,7 +539,9 @@ def test_cuda_graph_capture_of_a_batch(D):
     x.zero_()
     g.replay()
     torch.cuda.synchronize()
-    ref = oracle.thomas_batched(tm1, t0, tp1, N, off, F)
+    assert set(b.info["form"].tolist()) == {0, 1}
     for s in range(N.size):
         sl = slice(int(off[s]), int(off[s] + N[s]))
-        assert rel(x[sl].cpu().numpy(), ref[sl]) < TOL
+        t = (tm1[s], t0[s], tp1[s])
+        xq = oracle.thomas_q(t, F[sl])
+        assert rel(x[sl].cpu().numpy(), xq) <= max(TOL, 20 * rel(oracle.thomas(t, F[sl]), xq)), s
