@@ -462,6 +462,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   // ---------------------------------------------------------------- coalesced store of the own rows
   const bool adj = (A.xf != nullptr);
   double g0 = 0.0, gm = 0.0, gp = 0.0;
+  double g0b = 0.0, gmb = 0.0, gpb = 0.0;   // second accumulator set: independent FP64 chains
   unsigned bad = 0u;
   const int64_t N = pp->N;
   {
@@ -488,8 +489,20 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
         if (j + 1 < jhi) {
           const double d1 = S[(size_t)(i + 1) * LD + b];
           __stcs(reinterpret_cast<double2*>(dst + j), make_double2(d0, d1));
-          take(d0, j);
-          take(d1, j + 1);
+          if (A.check_finite && (((__double2hiint(d0) >> 20) & 0x7FF) == 0x7FF ||
+                                 ((__double2hiint(d1) >> 20) & 0x7FF) == 0x7FF))
+            bad = 1u;
+          if (adj) {  // rows r, r + 1: four loads of the forward solution, two accumulator sets
+            const int64_t r = row_lo + j;
+            const double* xr = A.xf + off + r;
+            const double xm1 = (r > 0) ? xr[-1] : 0.0, x0 = xr[0], x1 = xr[1], x2 = (r + 2 < N) ? xr[2] : 0.0;
+            g0 = fma(d0, x0, g0);
+            gm = fma(d0, xm1, gm);
+            gp = fma(d0, x1, gp);
+            g0b = fma(d1, x1, g0b);
+            gmb = fma(d1, x0, gmb);
+            gpb = fma(d1, x2, gpb);
+          }
         } else {
           __stcs(dst + j, d0);
           take(d0, j);
@@ -519,6 +532,9 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   }
   if (bad) atomicOr(A.status, (unsigned)ST_NONFINITE);
   if (adj) {
+    g0 += g0b;
+    gm += gmb;
+    gp += gpb;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
       g0 += __shfl_down_sync(0xffffffffu, g0, d);
