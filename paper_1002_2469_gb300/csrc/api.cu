@@ -831,6 +831,19 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
   b->nsys = nsys;
   b->opts = o;
   for (int f = 0; f < 2; ++f) b->NT[f] = o.NT ? o.NT : default_threads(f);
+  if (!o.NT && o.n_req == 0) {
+    // few FP64-form windows (a handful of ill-conditioned systems beside many MIXED ones, such as
+    // the lowest Poisson modes) are latency-bound: 256-thread windows of shorter blocks
+    int64_t w64 = 0;
+    for (int64_t s = 0; s < nsys; ++s) {
+      if (h_N[s] < 2 || !std::isfinite(h_tm1[s]) || !std::isfinite(h_t0[s]) || !std::isfinite(h_tp1[s])) continue;
+      const Roots r = toeplitz_roots(h_tm1[s], h_t0[s], h_tp1[s]);
+      if (r.ok && pick_form(o.prec, r) == FORM_F64)
+        w64 += ceil_div(h_N[s], (int64_t)default_threads(FORM_F64) * default_rows(FORM_F64));
+    }
+    const int sms = device_sms();
+    if (w64 > 0 && w64 < 2 * (int64_t)sms) b->NT[FORM_F64] = 256;
+  }
   b->fwd.resize((size_t)nsys);
   b->adj.resize((size_t)nsys);
   b->form.assign((size_t)nsys, FORM_F64);
@@ -1074,7 +1087,9 @@ static int batch_launch(dich_batch_t b, const double* F, double* x, const double
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
     if (e != cudaSuccess) return cuda_fail(e);
   }
-  for (int f = 0; f < 2; ++f) {
+  // FP64-form windows first: with a fork their long CTAs then start beside the MIXED waves
+  // instead of after them
+  for (int f : {FORM_F64, FORM_MIXED}) {
     const int64_t nitems = (int64_t)b->items[f].size();
     if (nitems == 0) continue;
     const cudaStream_t sf = (fork && f == FORM_F64) ? b->aux : st;
