@@ -67,7 +67,9 @@ typedef enum {
 
 enum {
   DICH_FLAG_FORCE_GENERAL = 1,  /* never truncate cross-tile coupling (3-kernel path) */
-  DICH_FLAG_CHECK_FINITE = 2    /* latch DICH_ERR_NONFINITE if any output is not finite */
+  DICH_FLAG_CHECK_FINITE = 2,   /* latch DICH_ERR_NONFINITE if any output is not finite */
+  DICH_FLAG_HOST_PRELIM = 4,    /* general matrices: preliminary step on the host at plan time */
+  DICH_FLAG_DEVICE_PRELIM = 8   /* general matrices: preliminary step on the device at bind time */
 };
 
 typedef struct {
@@ -217,25 +219,32 @@ const char* dichotomy_version(void);
 /* ---------------------------------------------------------------- general tridiagonal matrices
  * The Dichotomy Algorithm for a general (non-Toeplitz) tridiagonal matrix (Sec. 2): row i reads
  * a_i x_{i-1} + b_i x_i + c_i x_{i+1} = F_i (a_0 and c_{N-1} are ignored).  The preliminary step
- * (Sec. 2.3) is the general O(N) one, run on the host by dichotomy_gen_plan: the whole-system
- * elimination factors (the homogeneous solutions that give the exterior vectors of eq. 10-12 as
- * ratios), each block's own Thomas factors and spikes, and the block maps of the dichotomy tree.
- * Every solve of a series (eq. 2) reuses it.  FP64 only.  The plan keeps 5 doubles per row in
- * the device workspace (40 bytes per row, plus 80 bytes per block). */
+ * (Sec. 2.3) is the general O(N) one: the whole-system elimination factors (the homogeneous
+ * solutions that give the exterior vectors of eq. 10-12 as ratios), each block's own Thomas
+ * factors and spikes, and the block maps of the dichotomy tree.  It runs on the device at bind
+ * time (from 2^15 rows, or with DICH_FLAG_DEVICE_PRELIM: the elimination factors as prefix and
+ * suffix products of 2x2 matrices over the blocks) or on the host at plan time (below 2^15 rows,
+ * or with DICH_FLAG_HOST_PRELIM).  Every solve of a series (eq. 2) reuses it.  FP64 only.  The
+ * plan keeps 5 doubles per row in the device workspace (40 bytes per row, plus 80 bytes per
+ * block); the device preliminary adds 24 bytes per row (the matrix) and 64 per block. */
 
 /* Plan for the N x N matrix given by the host arrays h_a (sub-diagonal), h_b (diagonal), h_c
  * (super-diagonal), N entries each (copied; the caller keeps ownership).  opts as for
  * dichotomy_plan_ex (precision DICH_PREC_MIXED: DICH_ERR_UNSUPPORTED).  Every row must satisfy
  * |b_i| >= |a_i| + |c_i| (eq. 32-33).  Errors: DICH_ERR_ARG (null, negative N, non-finite entry,
- * bad opts), DICH_ERR_NOT_DOMINANT, DICH_ERR_SINGULAR (a zero pivot), DICH_ERR_UNSUPPORTED. */
+ * bad opts), DICH_ERR_NOT_DOMINANT, DICH_ERR_SINGULAR (a zero pivot; with the device preliminary
+ * reported by dichotomy_gen_bind), DICH_ERR_UNSUPPORTED. */
 int dichotomy_gen_plan(int64_t N, const double* h_a, const double* h_b, const double* h_c, const dich_opts* opts,
                        dich_gen_t* out);
-/* Geometry of a general plan (the Toeplitz-only fields are zero).  Errors: DICH_ERR_ARG. */
+/* Geometry of a general plan (the Toeplitz-only fields are zero).  With the device preliminary,
+ * path, halo_l, halo_r and tiles are provisional (general path) until dichotomy_gen_bind has
+ * returned.  Errors: DICH_ERR_ARG. */
 int dichotomy_gen_info(dich_gen_t plan, dich_plan_info* info);
 /* Bytes of device workspace (256-byte aligned region). */
 int dichotomy_gen_workspace_bytes(dich_gen_t plan, size_t* bytes);
-/* Attach the caller's workspace and upload the plan on `stream`; returns after the upload has
- * completed.  Errors: DICH_ERR_ARG, DICH_ERR_WORKSPACE, DICH_ERR_CUDA. */
+/* Attach the caller's workspace and upload the plan on `stream` (with the device preliminary:
+ * upload the matrix and run the preliminary step there); returns after all of it has completed.
+ * Errors: DICH_ERR_ARG, DICH_ERR_WORKSPACE, DICH_ERR_SINGULAR, DICH_ERR_CUDA. */
 int dichotomy_gen_bind(dich_gen_t plan, void* d_workspace, size_t bytes, void* stream);
 /* x = A^-1 F: one kernel (one window or halo windows) or three (general path) on `stream`.
  * Errors: DICH_ERR_ARG, DICH_ERR_ALIAS, DICH_ERR_UNBOUND, DICH_ERR_CUDA. */

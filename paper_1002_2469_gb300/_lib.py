@@ -23,7 +23,7 @@ STATUS_NAMES = {
     9: "DICH_ERR_WORKSPACE", 10: "DICH_ERR_SCHEDULE", 11: "DICH_ERR_UNSUPPORTED",
 }
 PREC_F64, PREC_MIXED, PREC_AUTO = 0, 1, 2
-FLAG_FORCE_GENERAL, FLAG_CHECK_FINITE = 1, 2
+FLAG_FORCE_GENERAL, FLAG_CHECK_FINITE, FLAG_HOST_PRELIM, FLAG_DEVICE_PRELIM = 1, 2, 4, 8
 
 EXPORTS = [
     "dichotomy_plan", "dichotomy_plan_ex", "dichotomy_plan_quasi", "dichotomy_plan_info", "dichotomy_plan_workspace_bytes",

@@ -24,6 +24,7 @@
 #include "../../include/dichotomy.h"
 #include "launch.cuh"
 #include "planner.cuh"
+#include "gen_prelim.cuh"
 #include "window_gen.cuh"
 
 using namespace dich;
@@ -60,27 +61,28 @@ struct dich_gen_s {
   int64_t tiles = 0;
   int64_t stride = 0;                 // doubles per per-row field
   SysPlan rec{};                      // geometry record read by the kernels
-  std::vector<double> recs;           // block records, kBC doubles per block
-  std::vector<double> rows;           // per-row fields (window_gen.cuh layout)
+  std::vector<double> recs;           // block records, kBC doubles per block (host preliminary)
+  std::vector<double> rows;           // per-row fields (window_gen.cuh layout; host preliminary)
+  bool device_prelim = false;         // preliminary step on the device at bind time
+  std::vector<double> ha, hb, hc;     // the matrix, kept for the device preliminary
   size_t ws_bytes = 0, off_plan = 0, off_status = 0, off_recs = 0, off_rows = 0, off_beta = 0, off_iface = 0,
-         off_scan = 0;
+         off_scan = 0, off_raw = 0, off_comp = 0, off_chunk = 0, off_max = 0;
   char* d_ws = nullptr;
 };
 
 namespace {
 
 constexpr int kGenDefaultRows = 32;
+constexpr int64_t kGenDevicePrelimMin = 1 << 15;   // default: device preliminary from this many rows
 
-// the O(N) preliminary step; returns a status code
-int gen_build(dich_gen_s* g, const double* a, const double* b, const double* c) {
+// block geometry (block size n, P blocks, the last one nlast rows); returns a status code
+int gen_geometry(dich_gen_s* g, double b0) {
   const int64_t N = g->N;
   SysPlan& r = g->rec;
   std::memset(&r, 0, sizeof(r));
   r.N = N;
-  if (N == 1) {
-    r.t0 = b[0];
-    return DICH_OK;
-  }
+  r.t0 = b0;
+  if (N == 1) return DICH_OK;
   const int NT = g->NT;
   const size_t budget = g->opts.n_req > 0 ? kSmemMax : kSmemBudget;
   int nmax = 2;
@@ -94,7 +96,49 @@ int gen_build(dich_gen_s* g, const double* a, const double* b, const double* c) 
   r.kl = (int32_t)std::min<int64_t>(P, INT32_MAX);
   r.kr = 0;
   r.form = FORM_F64;
-  r.t0 = b[0];
+  r.own = NT;
+  g->path = (P <= NT) ? PATH_SINGLE : PATH_GENERAL;   // final once the largest map factors are known
+  g->tiles = ceil_div(P, (int64_t)NT);
+  const int64_t Ppad = (P + 31) / 32 * 32;
+  g->stride = Ppad * n;
+  return DICH_OK;
+}
+
+// windows: one window, halo windows (coupling beyond the halo below eps), or the general path,
+// from the largest |a| over blocks 0..P-2 and |c| over blocks 1..P-1 of the block maps
+void gen_decide(dich_gen_s* g, double amax, double cmax) {
+  SysPlan& r = g->rec;
+  const int64_t P = r.P;
+  const int NT = g->NT;
+  const double eps = g->opts.eps;
+  auto halo_of = [&](double mx) -> int64_t {
+    if (mx == 0.0) return 1;
+    if (mx >= 1.0) return P;
+    return (int64_t)std::ceil(std::log(eps) / std::log(mx)) + 1;
+  };
+  const int64_t hl = halo_of(amax), hr = halo_of(cmax);
+  r.hl = r.hr = 0;
+  if (P <= NT) {
+    g->path = PATH_SINGLE;
+    r.own = (int32_t)P;
+  } else if (!(g->opts.flags & DICH_FLAG_FORCE_GENERAL) && hl + hr <= NT / 2) {
+    g->path = PATH_HALO;
+    r.hl = (int32_t)hl;
+    r.hr = (int32_t)hr;
+    r.own = (int32_t)(NT - hl - hr);
+  } else {
+    g->path = PATH_GENERAL;
+    r.own = NT;
+  }
+  g->tiles = ceil_div(P, (int64_t)r.own);
+}
+
+// the O(N) preliminary step on the host; returns a status code
+int gen_host_tables(dich_gen_s* g, const double* a, const double* b, const double* c) {
+  const int64_t N = g->N;
+  const SysPlan& r = g->rec;
+  const int n = r.n;
+  const int64_t P = r.P;
 
   // whole-system elimination factors
   std::vector<double> cp((size_t)N), cq((size_t)N);
@@ -113,8 +157,6 @@ int gen_build(dich_gen_s* g, const double* a, const double* b, const double* c) 
     cq[(size_t)i] = prev;
   }
 
-  const int64_t Ppad = (P + 31) / 32 * 32;
-  g->stride = Ppad * n;
   g->rows.assign((size_t)(kGenFields * g->stride), 0.0);
   g->recs.assign((size_t)(P * kBC), 0.0);
   double* fa = g->rows.data() + GF_A * g->stride;
@@ -190,27 +232,7 @@ int gen_build(dich_gen_s* g, const double* a, const double* b, const double* c) 
     if (m > 0) cmax = std::max(cmax, std::fabs(pc));
   }
 
-  // windows: one window, halo windows (coupling beyond the halo below eps), or the general path
-  const double eps = g->opts.eps;
-  auto halo_of = [&](double mx) -> int64_t {
-    if (mx == 0.0) return 1;
-    if (mx >= 1.0) return P;
-    return (int64_t)std::ceil(std::log(eps) / std::log(mx)) + 1;
-  };
-  const int64_t hl = halo_of(amax), hr = halo_of(cmax);
-  if (P <= NT) {
-    g->path = PATH_SINGLE;
-    r.own = (int32_t)P;
-  } else if (!(g->opts.flags & DICH_FLAG_FORCE_GENERAL) && hl + hr <= NT / 2) {
-    g->path = PATH_HALO;
-    r.hl = (int32_t)hl;
-    r.hr = (int32_t)hr;
-    r.own = (int32_t)(NT - hl - hr);
-  } else {
-    g->path = PATH_GENERAL;
-    r.own = NT;
-  }
-  g->tiles = ceil_div(P, r.own);
+  gen_decide(g, amax, cmax);
   return DICH_OK;
 }
 
@@ -221,10 +243,21 @@ void gen_layout(dich_gen_s* g) {
   g->off_status = o;
   o += kAlign;
   g->off_recs = o;
-  o += align_up(sizeof(double) * g->recs.size());
+  o += align_up(sizeof(double) * kBC * (size_t)g->rec.P);
   g->off_rows = o;
-  o += align_up(sizeof(double) * g->rows.size());
-  if (g->path == PATH_GENERAL) {
+  if (g->N > 1) o += align_up(sizeof(double) * (size_t)(kGenFields * g->stride));
+  if (g->device_prelim) {   // the matrix, block composites, chunk products, largest map factors
+    const int64_t nch = ceil_div(g->rec.P, (int64_t)kPreChunk);
+    g->off_raw = o;
+    o += align_up(sizeof(double) * 3 * (size_t)g->N);
+    g->off_comp = o;
+    o += align_up(sizeof(Mat2) * 2 * (size_t)g->rec.P);
+    g->off_chunk = o;
+    o += align_up(sizeof(Mat2) * 2 * (size_t)nch);
+    g->off_max = o;
+    o += kAlign;
+  }
+  if (g->path == PATH_GENERAL) {   // always reserved with the device preliminary (path known at bind)
     const int64_t P = g->rec.P;
     g->off_beta = o;
     o += align_up(sizeof(double) * 2 * P);
@@ -234,6 +267,52 @@ void gen_layout(dich_gen_s* g) {
     o += align_up(sizeof(double) * 6 * (size_t)ceil_div(P, kScanChunk));
   }
   g->ws_bytes = o;
+}
+
+// the O(N) preliminary step on the device (gen_prelim.cuh), into the workspace at `base`; reads
+// back the largest map factors and decides the path; returns a status code
+int gen_device_tables(dich_gen_s* g, char* base, cudaStream_t st) {
+  const SysPlan& r = g->rec;
+  const int64_t N = g->N, P = r.P;
+  const int64_t nch = ceil_div(P, (int64_t)kPreChunk);
+  PreArgs A{};
+  A.N = N;
+  A.P = P;
+  A.n = r.n;
+  A.nlast = r.nlast;
+  double* raw = (double*)(base + g->off_raw);
+  A.a = raw;
+  A.b = raw + N;
+  A.c = raw + 2 * N;
+  A.rows = (double*)(base + g->off_rows);
+  A.stride = g->stride;
+  A.recs = (double*)(base + g->off_recs);
+  A.fwd = (Mat2*)(base + g->off_comp);
+  A.bwd = A.fwd + P;
+  A.chunk = (Mat2*)(base + g->off_chunk);
+  A.maxes = (unsigned long long*)(base + g->off_max);
+  const size_t nb = sizeof(double) * (size_t)N;
+  cudaError_t e = cudaMemcpyAsync(raw, g->ha.data(), nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(raw + N, g->hb.data(), nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(raw + 2 * N, g->hc.data(), nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A.rows, 0, sizeof(double) * (size_t)(kGenFields * g->stride), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A.maxes, 0, 3 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  k_pre_blocks<<<(unsigned)nch, kPreThreads, 0, st>>>(A);
+  k_pre_chunk<<<(unsigned)nch, kPreThreads, 0, st>>>(A);
+  k_pre_top<<<1, 32, 0, st>>>(A, nch);
+  k_pre_records<<<(unsigned)nch, kPreThreads, 0, st>>>(A);
+  e = cudaGetLastError();
+  unsigned long long mx[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(mx, A.maxes, sizeof(mx), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (mx[2]) return DICH_ERR_SINGULAR;
+  double amax, cmax;
+  std::memcpy(&amax, &mx[0], sizeof(double));
+  std::memcpy(&cmax, &mx[1], sizeof(double));
+  gen_decide(g, amax, cmax);
+  return DICH_OK;
 }
 
 int gen_launch(dich_gen_s* g, const double* F, double* x, cudaStream_t st, int64_t M, int64_t ldf, int64_t ldx) {
@@ -317,7 +396,24 @@ int dichotomy_gen_plan(int64_t N, const double* h_a, const double* h_b, const do
   g->opts = o;
   g->NT = o.NT ? o.NT : 64;
   if (N >= 1) {
-    rc = gen_build(g, h_a, h_b, h_c);
+    rc = gen_geometry(g, h_b[0]);
+    if (rc == DICH_OK && N > 1) {
+      g->device_prelim = (o.flags & DICH_FLAG_DEVICE_PRELIM) ||
+                         (!(o.flags & DICH_FLAG_HOST_PRELIM) && N >= kGenDevicePrelimMin);
+      if (g->device_prelim) {
+        try {
+          g->ha.assign(h_a, h_a + N);
+          g->hb.assign(h_b, h_b + N);
+          g->hc.assign(h_c, h_c + N);
+          g->ha[0] = 0.0;
+          g->hc[(size_t)N - 1] = 0.0;
+        } catch (...) {
+          rc = DICH_ERR_ARG;
+        }
+      } else {
+        rc = gen_host_tables(g, h_a, h_b, h_c);
+      }
+    }
     if (rc) {
       delete g;
       return rc;
@@ -357,6 +453,10 @@ int dichotomy_gen_bind(dich_gen_t g, void* d_ws, size_t bytes, void* stream) {
   if (!is_device_ptr(d_ws)) return DICH_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   char* base = (char*)d_ws;
+  if (g->device_prelim) {
+    const int rc = gen_device_tables(g, base, st);
+    if (rc) return rc;
+  }
   cudaError_t e = cudaMemcpyAsync(base + g->off_plan, &g->rec, sizeof(SysPlan), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + g->off_status, 0, kAlign, st);
   if (e == cudaSuccess && !g->recs.empty())

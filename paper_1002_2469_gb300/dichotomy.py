@@ -14,7 +14,7 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import (FLAG_CHECK_FINITE, FLAG_FORCE_GENERAL, PREC_AUTO, PREC_F64, PREC_MIXED, DichotomyError,
+from ._lib import (FLAG_CHECK_FINITE, FLAG_DEVICE_PRELIM, FLAG_FORCE_GENERAL, FLAG_HOST_PRELIM, PREC_AUTO, PREC_F64, PREC_MIXED, DichotomyError,
                    check, make_opts)
 
 __all__ = [
@@ -23,7 +23,7 @@ __all__ = [
     "dichotomy_batch_prepare", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
     "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
     "dichotomy_batch_destroy", "Plan", "Batch", "GenPlan", "solve", "DichotomySolve", "DichotomySolveBatched",
-    "PREC_F64", "PREC_MIXED", "PREC_AUTO", "FLAG_FORCE_GENERAL", "FLAG_CHECK_FINITE", "DichotomyError",
+    "PREC_F64", "PREC_MIXED", "PREC_AUTO", "FLAG_FORCE_GENERAL", "FLAG_CHECK_FINITE", "FLAG_HOST_PRELIM", "FLAG_DEVICE_PRELIM", "DichotomyError",
 ]
 
 
@@ -315,6 +315,8 @@ class GenPlan:
         base = (self.workspace.data_ptr() + 255) // 256 * 256
         check(L.dichotomy_gen_bind(h, ctypes.c_void_p(base), self.info["workspace_bytes"], _stream(stream)),
               "dichotomy_gen_bind")
+        check(L.dichotomy_gen_info(h, ctypes.byref(info)), "dichotomy_gen_info")   # path final after bind
+        self.info = {k: getattr(info, k) for k, _ in info._fields_}
 
     def solve(self, F: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         x = torch.empty_like(F) if out is None else out

@@ -229,10 +229,13 @@ def test_general_plan_validation_and_geometry_without_a_gpu():
     N = 1 << 18
     a, c = rng.uniform(-1, 1, N), rng.uniform(-1, 1, N)
     b = np.abs(a) + np.abs(c) + rng.uniform(0.5, 1.0, N)
-    rc, info = gen(a, b, c)
+    rc, info = gen(a, b, c, flags=4)
     assert rc == 0 and info.path == 1 and info.halo_l >= 1          # strong dominance: halo windows
-    rc, info = gen(a, b, c, flags=1)
+    rc, info = gen(a, b, c, flags=1 | 4)
     assert rc == 0 and info.path == 2
+    rc, dinfo = gen(a, b, c)                                        # device preliminary: path known at bind
+    assert rc == 0 and dinfo.path == 2 and dinfo.halo_l == 0 and dinfo.P == info.P
+    assert dinfo.workspace_bytes >= info.workspace_bytes + 24 * N
     rc, info = gen(a[:1000], b[:1000], c[:1000])
     assert rc == 0 and (info.P - 1) * info.n + info.n_last == 1000
     bad = b.copy()

@@ -38,33 +38,92 @@ def gen_solve(D, a, b, c, F, **kw):
     return x, plan.info
 
 
+HOST, DEVICE = 4, 8   # where the preliminary step runs (DICH_FLAG_HOST_PRELIM / _DEVICE_PRELIM)
+
+
+@pytest.mark.parametrize("prelim", [HOST, DEVICE])
 @pytest.mark.parametrize("N", [1, 2, 3, 5, 31, 1000, 4097, 100003, 1 << 20])
-def test_general_random_dominant(D, N):
+def test_general_random_dominant(D, N, prelim):
     a, b, c = dominant(N, N)
     F = np.random.default_rng(N + 1).standard_normal(N)
-    x, info = gen_solve(D, a, b, c, F)
+    x, info = gen_solve(D, a, b, c, F, flags=prelim)
     assert rel(x, oracle.thomas_tridiag(a, b, c, F)) < TOL, info
 
 
+@pytest.mark.parametrize("prelim", [HOST, DEVICE])
 @pytest.mark.parametrize("threads", [64, 128, 256])
 @pytest.mark.parametrize("bs", [2, 3, 16, 45])
 @pytest.mark.parametrize("flags", [0, 1])
-def test_general_geometry_and_paths(D, threads, bs, flags):
+def test_general_geometry_and_paths(D, threads, bs, flags, prelim):
     N = 77777
     a, b, c = dominant(N, 5)
     F = np.random.default_rng(6).standard_normal(N)
-    x, info = gen_solve(D, a, b, c, F, threads=threads, block_size=bs, flags=flags)
+    x, info = gen_solve(D, a, b, c, F, threads=threads, block_size=bs, flags=flags | prelim)
     if flags:
         assert info["path"] == 2
     assert rel(x, oracle.thomas_tridiag(a, b, c, F)) < TOL, info
 
 
-def test_general_weak_dominance_takes_the_general_path(D):
+@pytest.mark.parametrize("prelim", [HOST, DEVICE])
+def test_general_weak_dominance(D, prelim):
     N = 300001
     a, b, c = dominant(N, 7, margin=(1e-3, 1e-2))
     F = np.random.default_rng(8).standard_normal(N)
-    x, info = gen_solve(D, a, b, c, F)
+    x, info = gen_solve(D, a, b, c, F, flags=prelim)
     assert rel(x, oracle.thomas_tridiag(a, b, c, F)) < TOL, info
+
+
+@pytest.mark.parametrize("prelim", [HOST, DEVICE])
+def test_general_slow_decay_takes_the_general_path(D, prelim):
+    """Off-diagonals near -1 and a diagonal margin of 0.002..0.01: the coupling between blocks
+    decays too slowly for halo windows, so the interface values come from the block scan."""
+    N = 300001
+    rng = np.random.default_rng(7)
+    a, c = -rng.uniform(0.9, 1.0, N), -rng.uniform(0.9, 1.0, N)
+    b = np.abs(a) + np.abs(c) + rng.uniform(2e-3, 1e-2, N)
+    F = np.random.default_rng(8).standard_normal(N)
+    x, info = gen_solve(D, a, b, c, F, flags=prelim)
+    assert info["path"] == 2
+    assert rel(x, oracle.thomas_tridiag(a, b, c, F)) < TOL, info
+
+
+@pytest.mark.parametrize("N,bs", [(2, 0), (65, 3), (8192 * 32 + 77, 32), (3 * 8192 * 32 + 1, 32), (1 << 20, 0)])
+def test_device_preliminary_matches_the_host_one(D, N, bs):
+    """The device preliminary (block composites, chunked prefix and suffix products of 2x2
+    elimination matrices) gives the same path and halos as the host's row-by-row pass and
+    solutions equal to the last few ulps; sizes span one, several and a ragged last scan chunk
+    of 256 blocks."""
+    a, b, c = dominant(N, 12 + N)
+    F = np.random.default_rng(13 + N).standard_normal(N)
+    xh, ih = gen_solve(D, a, b, c, F, flags=HOST, block_size=bs)
+    xd, idv = gen_solve(D, a, b, c, F, flags=DEVICE, block_size=bs)
+    for k in ("path", "halo_l", "halo_r", "n", "P", "tiles"):
+        assert ih[k] == idv[k], (k, ih, idv)
+    assert rel(xd, xh) < 1e-13
+    assert rel(xd, oracle.thomas_tridiag(a, b, c, F)) < TOL
+
+
+@pytest.mark.parametrize("k", [None, 3210, 3231])
+def test_device_preliminary_refuses_a_zero_pivot(D, k):
+    """A weakly dominant matrix with an exactly singular 2x2 diagonal block [[1, 1], [1, 1]]
+    (rows k, k+1; a_k = c_{k+1} = 0, so the determinant factorises): both preliminaries refuse it,
+    the host one at plan time, the device one at bind time; k = 3231 puts the zero pivot on the
+    first row of a block (the whole-system factor carried in from the block before)."""
+    if k is None:
+        a, b, c = np.array([0.0, 1.0]), np.array([1.0, 1.0]), np.array([1.0, 0.0])
+        k = 0
+    else:
+        N = 100000
+        a, b, c = dominant(N, 14)
+        a[k], b[k], c[k] = 0.0, 1.0, 1.0
+        a[k + 1], b[k + 1], c[k + 1] = 1.0, 1.0, 0.0
+    bs = 32 if b.size > 2 else 0
+    with pytest.raises(D.DichotomyError) as e:
+        D.GenPlan(a, b, c, flags=HOST, block_size=bs)
+    assert e.value.code == 3 and "dichotomy_gen_plan" in str(e.value)
+    with pytest.raises(D.DichotomyError) as e:
+        D.GenPlan(a, b, c, flags=DEVICE, block_size=bs)
+    assert e.value.code == 3 and "dichotomy_gen_bind" in str(e.value)
 
 
 def test_general_with_constant_rows_equals_the_toeplitz_solve(D):
