@@ -206,15 +206,23 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   // ---------------------------------------------------------------- F -> smem (transposed, async)
   {
     const double* src = A.F + (int64_t)blockIdx.y * A.ldf + off + row_lo;
-    int b = tid / n, i = tid - (tid / n) * n;
-    const int db = NT / n, di = NT - (NT / n) * n;
-    for (int j = tid; j < len; j += NT) {
-      cp_async8(&S[(size_t)i * LD + b], src + j);
-      i += di;
-      b += db;
-      if (i >= n) {
-        i -= n;
-        ++b;
+    if (n == 16) {
+      // element j = tid + k NT sits in row tid % 16 of block tid / 16 + k NT / 16: fixed strides
+      double* d = S + (size_t)(tid & 15) * LD + (tid >> 4);
+      const int cnt = (len - tid + NT - 1) / NT;
+#pragma unroll 4
+      for (int k = 0; k < cnt; ++k) cp_async8(d + k * (NT / 16), src + tid + k * NT);
+    } else {
+      int b = tid / n, i = tid - (tid / n) * n;
+      const int db = NT / n, di = NT - (NT / n) * n;
+      for (int j = tid; j < len; j += NT) {
+        cp_async8(&S[(size_t)i * LD + b], src + j);
+        i += di;
+        b += db;
+        if (i >= n) {
+          i -= n;
+          ++b;
+        }
       }
     }
   }
@@ -253,8 +261,8 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
       for (int i = 0; i < nrow; ++i) {
         const uint4 q = *reinterpret_cast<const uint4*>(S + (size_t)i * LD + 2 * tid);
         const unsigned a = q.y & 0x7FFFFFFFu, c = q.w & 0x7FFFFFFFu;
-        hmax = max(hmax, max(a, c));
-        hmin = min(hmin, min(a, c));
+        hmax = __vimax3_u32(hmax, a, c);
+        hmin = __vimin3_u32(hmin, a, c);
       }
     } else {
       for (int i = 0; i < nrow; ++i) {
@@ -480,33 +488,41 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
         if (r + 1 < N) gp = fma(dv, xr[1], gp);
       }
     };
-    if ((n & 1) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0u) {
-      // even n: rows j, j + 1 (j even) are consecutive rows of one block -> one 16-byte store
+    // rows j, j + 1 (j even) of one block (column b, rows i, i + 1 of the tile): one 16-byte store
+    auto put2 = [&](int j, const double* col) {
+      const double d0 = col[0];
+      if (j + 1 < jhi) {
+        const double d1 = col[LD];
+        __stcs(reinterpret_cast<double2*>(dst + j), make_double2(d0, d1));
+        if (A.check_finite && (((__double2hiint(d0) >> 20) & 0x7FF) == 0x7FF ||
+                               ((__double2hiint(d1) >> 20) & 0x7FF) == 0x7FF))
+          bad = 1u;
+        if (adj) {  // rows r, r + 1: four loads of the forward solution, two accumulator sets
+          const int64_t r = row_lo + j;
+          const double* xr = A.xf + off + r;
+          const double xm1 = (r > 0) ? xr[-1] : 0.0, x0 = xr[0], x1 = xr[1], x2 = (r + 2 < N) ? xr[2] : 0.0;
+          g0 = fma(d0, x0, g0);
+          gm = fma(d0, xm1, gm);
+          gp = fma(d0, x1, gp);
+          g0b = fma(d1, x1, g0b);
+          gmb = fma(d1, x0, gmb);
+          gpb = fma(d1, x2, gpb);
+        }
+      } else {
+        __stcs(dst + j, d0);
+        take(d0, j);
+      }
+    };
+    if (n == 16 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0u) {
+      // jlo is a multiple of 16: row 2 (tid % 8) of block hl + tid / 8 + k NT / 8, fixed strides
+      const double* col = S + (size_t)(2 * (tid & 7)) * LD + hl + (tid >> 3);
+#pragma unroll 1
+      for (int j = jlo + 2 * tid; j < jhi; j += 2 * NT, col += NT / 8) put2(j, col);
+    } else if ((n & 1) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0u) {
       int b = (jlo + 2 * tid) / n, i = (jlo + 2 * tid) - ((jlo + 2 * tid) / n) * n;
       const int db = (2 * NT) / n, di = (2 * NT) - ((2 * NT) / n) * n;
       for (int j = jlo + 2 * tid; j < jhi; j += 2 * NT) {
-        const double d0 = S[(size_t)i * LD + b];
-        if (j + 1 < jhi) {
-          const double d1 = S[(size_t)(i + 1) * LD + b];
-          __stcs(reinterpret_cast<double2*>(dst + j), make_double2(d0, d1));
-          if (A.check_finite && (((__double2hiint(d0) >> 20) & 0x7FF) == 0x7FF ||
-                                 ((__double2hiint(d1) >> 20) & 0x7FF) == 0x7FF))
-            bad = 1u;
-          if (adj) {  // rows r, r + 1: four loads of the forward solution, two accumulator sets
-            const int64_t r = row_lo + j;
-            const double* xr = A.xf + off + r;
-            const double xm1 = (r > 0) ? xr[-1] : 0.0, x0 = xr[0], x1 = xr[1], x2 = (r + 2 < N) ? xr[2] : 0.0;
-            g0 = fma(d0, x0, g0);
-            gm = fma(d0, xm1, gm);
-            gp = fma(d0, x1, gp);
-            g0b = fma(d1, x1, g0b);
-            gmb = fma(d1, x0, gmb);
-            gpb = fma(d1, x2, gpb);
-          }
-        } else {
-          __stcs(dst + j, d0);
-          take(d0, j);
-        }
+        put2(j, S + (size_t)i * LD + b);
         i += di;
         b += db;
         if (i >= n) {
