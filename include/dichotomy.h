@@ -154,6 +154,26 @@ int dichotomy_solve(dich_plan_t plan, const double* d_F, double* d_x, void* stre
 int dichotomy_solve_series(dich_plan_t plan, int64_t M, const double* d_F, int64_t ldf, double* d_x,
                            int64_t ldx, void* stream);
 
+/* x = T^-1 F with F and x in host memory (not in the paper: the solve of eq. 1 fed from and
+ * returned to the host).  h_F, h_x: N doubles each in host memory, no aliasing; d_F, d_x: N
+ * doubles each of device staging memory owned by the caller.  Two ways, chosen by `chunks`:
+ *  - chunks = 0 and h_F, h_x page-locked memory mapped into the device's address space
+ *    (cudaHostAlloc, cudaHostRegister, torch pin_memory): the window kernels read F and write x
+ *    there directly, one pass over the host link (d_F, d_x unused, may be NULL); not on the
+ *    general path (it reads F twice), which takes the copies below;
+ *  - otherwise the copies: on the halo path of a Toeplitz plan the rows go to d_F in `chunks`
+ *    pieces of whole windows (0 = min(16, windows); 1 = no pipeline), the windows of a piece are
+ *    solved on `stream` as soon as the rows they read (their own and the right halo) have
+ *    arrived, and their own rows of x go back from d_x while later pieces are still being copied
+ *    in and solved (copy-in, kernels and copy-out overlap on `stream` and two copy streams the
+ *    plan creates on first use; pageable host memory works, its copies serialise).  Other plans
+ *    (one window, the general path, quasi-Toeplitz corners): copy in, solve, copy out.
+ * Enqueues only: h_x is complete once `stream` has synchronized; h_F, h_x, d_F, d_x must not be
+ * reused before.  Errors: DICH_ERR_ARG (null/misaligned pointers, h_* on the device, d_* not on
+ * the device when needed, chunks < 0), DICH_ERR_ALIAS, DICH_ERR_UNBOUND, DICH_ERR_CUDA. */
+int dichotomy_solve_host(dich_plan_t plan, const double* h_F, double* h_x, double* d_F, double* d_x, int32_t chunks,
+                         void* stream);
+
 /* Adjoint of L(x) with x = T^-1 F, given d_w = dL/dx and the forward solution d_x:
  *   d_gF = lambda = T^-T w   (the same Dichotomy solve for T^T = tridiag{t_1, t_0, t_-1}),
  *   d_gt[0..2] = (dL/dt_-1, dL/dt_0, dL/dt_1) = -(sum_i lambda_i x_{i-1},

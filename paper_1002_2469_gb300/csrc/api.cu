@@ -342,6 +342,14 @@ struct dich_plan_s {
   std::vector<unsigned char> staging;  // [plans | status | tables]
   char* d_ws = nullptr;
   size_t d_ws_bytes = 0;
+  // host-memory solves: copy-in and copy-out streams and the pipeline's events (created on first use)
+  cudaStream_t hs[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> hev;
+  ~dich_plan_s() {
+    for (cudaEvent_t ev : hev) cudaEventDestroy(ev);
+    for (cudaStream_t h : hs)
+      if (h) cudaStreamDestroy(h);
+  }
 };
 
 extern "C" {
@@ -633,7 +641,8 @@ int dichotomy_plan_bind(dich_plan_t p, void* d_ws, size_t bytes, void* stream) {
 }
 
 static int plan_launch(dich_plan_t p, const double* F, double* x, const double* xf, double* gt, bool adjoint,
-                       cudaStream_t st, int64_t M = 1, int64_t ldf = 0, int64_t ldx = 0) {
+                       cudaStream_t st, int64_t M = 1, int64_t ldf = 0, int64_t ldx = 0, int64_t win0 = 0,
+                       int64_t nwin = -1) {
   const SysPlan* d_plans = (const SysPlan*)(p->d_ws + p->off_plans);
   const double* d_tabs = (const double*)(p->d_ws + p->off_tabs);
   unsigned* d_status = (unsigned*)(p->d_ws + p->off_status);
@@ -662,14 +671,17 @@ static int plan_launch(dich_plan_t p, const double* F, double* x, const double* 
   a.ldf = ldf;
   a.ldx = ldx;
   const size_t smem = smem_bytes(p->NT, p->n_smem, p->form);
+  // windows [win0, win0 + grid) of the single and halo paths (all of them unless a range is given)
+  const int grid = (int)((nwin < 0) ? p->tiles : nwin);
   auto launch = [&](const WinArgs& w, int gy) {
-    return p->form == FORM_F64 ? launch_window_f64(p->NT, (int)p->tiles, smem, st, w, gy)
-                               : launch_window_mixed(p->NT, (int)p->tiles, smem, st, w, gy);
+    return p->form == FORM_F64 ? launch_window_f64(p->NT, grid, smem, st, w, gy)
+                               : launch_window_mixed(p->NT, grid, smem, st, w, gy);
   };
   cudaError_t e;
   if (p->path != PATH_GENERAL) {
     // every right-hand side of a series in one launch (grid.y), at most 65535 per launch
     a.mode = MODE_FULL;
+    a.win0 = win0;
     for (int64_t k0 = 0; k0 < M; k0 += 65535) {
       WinArgs w = a;
       w.F = F + k0 * ldf;
@@ -723,6 +735,96 @@ int dichotomy_solve(dich_plan_t p, const double* d_F, double* d_x, void* stream)
   if (overlap(d_F, nb, d_x, nb)) return DICH_ERR_ALIAS;
   if (!is_device_ptr(d_F) || !is_device_ptr(d_x)) return DICH_ERR_ARG;
   return plan_launch(p, d_F, d_x, nullptr, nullptr, false, (cudaStream_t)stream);
+}
+
+int dichotomy_solve_host(dich_plan_t p, const double* h_F, double* h_x, double* d_F, double* d_x, int32_t chunks,
+                         void* stream) {
+  if (!p || chunks < 0) return DICH_ERR_ARG;
+  if (!p->d_ws) return DICH_ERR_UNBOUND;
+  if (p->N == 0) return DICH_OK;
+  if (!h_F || !h_x || !aligned8(h_F) || !aligned8(h_x)) return DICH_ERR_ARG;
+  const int64_t N = p->N;
+  const size_t nb = sizeof(double) * (size_t)N;
+  if (overlap(h_F, nb, h_x, nb)) return DICH_ERR_ALIAS;
+  if (is_device_ptr(h_F) || is_device_ptr(h_x)) return DICH_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  // page-locked buffers mapped into the device's address space: the kernels read F and write x
+  // there directly (one pass over the host link, no staging), except on the general path, which
+  // reads F twice
+  if (chunks == 0 && p->path != PATH_GENERAL) {
+    auto mapped = [](const void* h) -> void* {
+      cudaPointerAttributes a;
+      if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      return (a.type == cudaMemoryTypeHost) ? a.devicePointer : nullptr;
+    };
+    const double* zF = (const double*)mapped(h_F);
+    double* zx = (double*)mapped(h_x);
+    if (zF && zx) return plan_launch(p, zF, zx, nullptr, nullptr, false, st);
+  }
+  if (!d_F || !d_x || !aligned8(d_F) || !aligned8(d_x)) return DICH_ERR_ARG;
+  if (overlap(d_F, nb, d_x, nb)) return DICH_ERR_ALIAS;
+  if (!is_device_ptr(d_F) || !is_device_ptr(d_x)) return DICH_ERR_ARG;
+  const int64_t T = p->tiles;
+  // only independent windows pipeline: the halo path of a plain Toeplitz plan with two or more windows
+  const bool pipe = p->N >= 2 && p->path == PATH_HALO && !p->quasi && T >= 2 && chunks != 1;
+  if (!pipe) {
+    e = cudaMemcpyAsync(d_F, h_F, nb, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int rc = plan_launch(p, d_F, d_x, nullptr, nullptr, false, st);
+    if (rc != DICH_OK) return rc;
+    e = cudaMemcpyAsync(h_x, d_x, nb, cudaMemcpyDeviceToHost, st);
+    return e == cudaSuccess ? DICH_OK : cuda_fail(e);
+  }
+  const int64_t K = std::min<int64_t>(T, chunks ? chunks : 16);   // pieces of whole windows
+  // streams and 2K + 2 events, kept by the plan
+  for (cudaStream_t& h : p->hs)
+    if (!h && (e = cudaStreamCreateWithFlags(&h, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e);
+  while ((int64_t)p->hev.size() < 2 * K + 2) {
+    cudaEvent_t ev;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e);
+    p->hev.push_back(ev);
+  }
+  cudaEvent_t* evin = p->hev.data();           // [K]: chunk k of F is on the device
+  cudaEvent_t* evk = evin + K;                 // [K]: the windows of chunk k are solved
+  cudaEvent_t evs = evk[K], eve = evk[K + 1];  // start (on st), end (copy-out stream)
+  const SysPlan& r = p->fwd.rec;
+  const int64_t rows_w = (int64_t)r.own * r.n;   // rows owned by a window
+  auto row_of = [&](int64_t w) { return std::min<int64_t>(N, w * rows_w); };
+  auto win_of = [&](int64_t k) { return T * k / K; };
+  if ((e = cudaEventRecord(evs, st)) != cudaSuccess) return cuda_fail(e);
+  for (cudaStream_t h : p->hs)
+    if ((e = cudaStreamWaitEvent(h, evs, 0)) != cudaSuccess) return cuda_fail(e);
+  // F in K chunks of whole windows' own rows, in order on the copy-in stream
+  for (int64_t k = 0; k < K; ++k) {
+    const int64_t r0 = row_of(win_of(k)), r1 = row_of(win_of(k + 1));
+    e = cudaMemcpyAsync(d_F + r0, h_F + r0, sizeof(double) * (size_t)(r1 - r0), cudaMemcpyHostToDevice, p->hs[0]);
+    if (e == cudaSuccess) e = cudaEventRecord(evin[k], p->hs[0]);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  // chunk k's windows once every row they read (own rows plus the right halo) has arrived; its own
+  // rows of x go back on the copy-out stream while later chunks are copied in and solved
+  int64_t j = 0;
+  for (int64_t k = 0; k < K; ++k) {
+    const int64_t w0 = win_of(k), w1 = win_of(k + 1);
+    const int64_t need = std::min<int64_t>(N, (w1 * (int64_t)r.own + r.hr) * r.n);
+    while (row_of(win_of(j + 1)) < need) ++j;
+    if ((e = cudaStreamWaitEvent(st, evin[j], 0)) != cudaSuccess) return cuda_fail(e);
+    const int rc = plan_launch(p, d_F, d_x, nullptr, nullptr, false, st, 1, 0, 0, w0, w1 - w0);
+    if (rc != DICH_OK) return rc;
+    if ((e = cudaEventRecord(evk[k], st)) != cudaSuccess) return cuda_fail(e);
+    const int64_t r0 = row_of(w0), r1 = row_of(w1);
+    e = cudaStreamWaitEvent(p->hs[1], evk[k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h_x + r0, d_x + r0, sizeof(double) * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, p->hs[1]);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  e = cudaEventRecord(eve, p->hs[1]);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, eve, 0);
+  return e == cudaSuccess ? DICH_OK : cuda_fail(e);
 }
 
 int dichotomy_solve_series(dich_plan_t p, int64_t M, const double* d_F, int64_t ldf, double* d_x, int64_t ldx,

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kPreThreads) k_pre_records(const PreArgs A) {
   // state entering the block: forward (p, q) at row s - 1 from (0, 1) at row -1; backward at
   // row e + 1 from (0, 1) at row N
   const int n = A.n, nb = (m == A.P - 1) ? A.nlast : n;
-  const int64_t s = m * n, e = s + nb - 1, N = A.N, P = A.P;
+  const int64_t s = m * n, N = A.N, P = A.P;
   const double cp_in = (m > 0) ? fex.b / fex.d : 0.0;   // (p, q) = fex (0, 1)
   const double cq_in = (m < P - 1) ? bex.b / bex.d : 0.0;
   // whole-system factors over the block's rows: products of -cp_i and -cq_i

@@ -44,6 +44,7 @@ struct WinArgs {
   int32_t n_smem;         // shared-memory rows (>= largest block size in the launch)
   int32_t sys_offset;     // added to the item's system index (adjoint twin records)
   int64_t ldf, ldx;       // series: right-hand side blockIdx.y starts at F + y ldf, its solution at x + y ldx
+  int64_t win0;           // single system: window of CTA blockIdx.x is win0 + blockIdx.x
 };
 
 // shared memory bytes for a window kernel of width NT and n_smem rows
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   const int64_t P = pp->P;
   if (!A.items) {
     nown = pp->own;
-    m0 = (int64_t)blockIdx.x * nown;
+    m0 = ((int64_t)blockIdx.x + A.win0) * nown;
     if (m0 + nown > P) nown = (int)(P - m0);
   }
   int hl = 0, hr = 0;

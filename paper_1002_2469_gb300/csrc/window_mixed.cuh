@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   const int64_t P = pp->P;
   if (!A.items) {
     nown = pp->own;
-    m0 = (int64_t)blockIdx.x * nown;
+    m0 = ((int64_t)blockIdx.x + A.win0) * nown;
     if (m0 + nown > P) nown = (int)(P - m0);
   }
   int hl = 0, hr = 0;

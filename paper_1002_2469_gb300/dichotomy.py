@@ -19,7 +19,7 @@ from ._lib import (FLAG_CHECK_FINITE, FLAG_DEVICE_PRELIM, FLAG_FORCE_GENERAL, FL
 
 __all__ = [
     "dichotomy_plan", "dichotomy_plan_quasi", "dichotomy_plan_info", "dichotomy_plan_workspace_bytes", "dichotomy_plan_bind",
-    "dichotomy_solve", "dichotomy_solve_series", "dichotomy_adjoint", "dichotomy_status", "dichotomy_destroy",
+    "dichotomy_solve", "dichotomy_solve_series", "dichotomy_solve_host", "dichotomy_adjoint", "dichotomy_status", "dichotomy_destroy",
     "dichotomy_batch_prepare", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
     "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
     "dichotomy_batch_destroy", "Plan", "Batch", "GenPlan", "solve", "DichotomySolve", "DichotomySolveBatched",
@@ -106,6 +106,25 @@ def dichotomy_solve_series(plan, F: torch.Tensor, x: torch.Tensor, stream=None) 
         raise ValueError("F and x must have the same shape")
     check(_lib.load().dichotomy_solve_series(plan, int(F.shape[0]), pF, ldf, px, ldx, _stream(stream)),
           "dichotomy_solve_series")
+
+
+def _host(t: torch.Tensor, name: str, n: int):
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CPU tensor")
+    if t.numel() != n:
+        raise ValueError(f"{name} must hold {n} values")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def dichotomy_solve_host(plan, F: torch.Tensor, x: torch.Tensor, dF: torch.Tensor | None, dx: torch.Tensor | None,
+                         chunks=0, stream=None) -> None:
+    """Enqueue x = T^-1 F for host tensors F, x: directly from and to pinned memory (chunks = 0),
+    else through the device staging tensors dF, dx; x is complete once the stream has synchronized."""
+    n = F.numel()
+    pF = _dev(dF, "dF") if dF is not None else None
+    px = _dev(dx, "dx") if dx is not None else None
+    check(_lib.load().dichotomy_solve_host(plan, _host(F, "F", n), _host(x, "x", n), pF, px, int(chunks),
+                                           _stream(stream)), "dichotomy_solve_host")
 
 
 def dichotomy_adjoint(plan, w: torch.Tensor, x: torch.Tensor, gF: torch.Tensor, gt: torch.Tensor,
@@ -224,6 +243,38 @@ class Plan:
         """Every row of F ([M, N]) solved with this plan (a series with a constant matrix)."""
         x = torch.empty_like(F) if out is None else out
         dichotomy_solve_series(self._h, F, x, stream)
+        return x
+
+    def solve_host(self, F: torch.Tensor, out: torch.Tensor | None = None, chunks: int = 0, stream=None) -> torch.Tensor:
+        """x = T^-1 F for a CPU tensor F: with pinned F and x (and chunks = 0) the kernels read and
+        write them directly over the host link; otherwise pipelined copy-in, solve and copy-out
+        through device staging tensors kept by the plan.  Returns once x is complete."""
+        x = torch.empty(F.shape, dtype=F.dtype, pin_memory=F.is_pinned()) if out is None else out
+        direct = chunks == 0 and F.is_pinned() and x.is_pinned() and self.info["path"] != 2
+        if not direct and getattr(self, "_staging", None) is None:
+            dev = self.workspace.device
+            self._staging = (torch.empty(self.N, dtype=torch.float64, device=dev),
+                             torch.empty(self.N, dtype=torch.float64, device=dev))
+        if direct:
+            try:
+                dichotomy_solve_host(self._h, F, x, None, None, 0, stream)
+                direct = True
+            except DichotomyError as err:   # pinned but not mapped into the device's address space
+                if err.code != 1:
+                    raise
+                direct = False
+                if getattr(self, "_staging", None) is None:
+                    dev = self.workspace.device
+                    self._staging = (torch.empty(self.N, dtype=torch.float64, device=dev),
+                                     torch.empty(self.N, dtype=torch.float64, device=dev))
+        if not direct:
+            dichotomy_solve_host(self._h, F, x, self._staging[0], self._staging[1], chunks, stream)
+        if isinstance(stream, torch.cuda.Stream):
+            stream.synchronize()
+        elif stream is None:
+            torch.cuda.current_stream(self.workspace.device).synchronize()
+        else:
+            torch.cuda.synchronize(self.workspace.device)
         return x
 
     def adjoint(self, w: torch.Tensor, x: torch.Tensor, stream=None):
