@@ -258,7 +258,7 @@ def run_gpu(args):
     # the batched configurations, timed the same way (device events, inputs resident)
     others = {}
     if not args.no_other_configs:
-        del F, x, Fd, xd, results
+        del F, x, results, F_pin, x_pin
         head.pop("x", None)
         f64.pop("x", None)
         torch.cuda.empty_cache()
@@ -349,6 +349,69 @@ def backward_error(t, F, x):
     return float(np.max(np.abs(r)) / (normT * np.max(np.abs(x)) + np.max(np.abs(F))))
 
 
+def cusparse_comparator(W, oracle, stream, steps):
+    """The vendor library beside the Dichotomy kernels: cuSPARSE's gtsv2_nopivot (general
+    tridiagonal, no pivoting: the fair choice for a diagonally dominant matrix) on the headline
+    system tridiag{-1.2, 2.5, -0.8}, N = 2^26.  It overwrites its right-hand side, so every step
+    copies F into it first; the copy's own time is reported beside it."""
+    import ctypes
+    import torch
+    lib = None
+    for name in ("libcusparse.so.12", os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64",
+                                                   "libcusparse.so.12")):
+        try:
+            lib = ctypes.CDLL(name)
+            break
+        except OSError:
+            pass
+    if lib is None:
+        return {"unavailable": "libcusparse.so.12 not found"}
+    P, I = ctypes.c_void_p, ctypes.c_int
+    lib.cusparseCreate.argtypes = [ctypes.POINTER(P)]
+    lib.cusparseSetStream.argtypes = [P, P]
+    lib.cusparseDestroy.argtypes = [P]
+    lib.cusparseDgtsv2_nopivot_bufferSizeExt.argtypes = [P, I, I, P, P, P, P, I, ctypes.POINTER(ctypes.c_size_t)]
+    lib.cusparseDgtsv2_nopivot.argtypes = [P, I, I, P, P, P, P, I, P]
+    t, F_h = W.single_c2()
+    N = F_h.size
+    F = torch.from_numpy(F_h).cuda()
+    dl = torch.full((N,), t[0], dtype=torch.float64, device="cuda")
+    d = torch.full((N,), t[1], dtype=torch.float64, device="cuda")
+    du = torch.full((N,), t[2], dtype=torch.float64, device="cuda")
+    dl[0] = 0.0
+    du[-1] = 0.0
+    B = torch.empty_like(F)
+    h = P()
+    if lib.cusparseCreate(ctypes.byref(h)) != 0:
+        return {"unavailable": "cusparseCreate failed"}
+    try:
+        lib.cusparseSetStream(h, P(stream.cuda_stream))
+        nbuf = ctypes.c_size_t()
+        ptr = lambda x: P(x.data_ptr())
+        rc = lib.cusparseDgtsv2_nopivot_bufferSizeExt(h, N, 1, ptr(dl), ptr(d), ptr(du), ptr(B), N, ctypes.byref(nbuf))
+        if rc != 0:
+            return {"unavailable": f"gtsv2_nopivot_bufferSizeExt status {rc}"}
+        buf = torch.empty(max(1, nbuf.value), dtype=torch.uint8, device="cuda")
+        status = []
+
+        def step():
+            B.copy_(F)
+            status.append(lib.cusparseDgtsv2_nopivot(h, N, 1, ptr(dl), ptr(d), ptr(du), ptr(B), N, ptr(buf)))
+
+        ms = _time_batch(step, steps, 1, stream)
+        ms_copy = _time_batch(lambda: B.copy_(F), steps, 1, stream)
+        if any(status):
+            return {"unavailable": f"gtsv2_nopivot status {max(status)}"}
+        step()
+        x_ref = oracle.thomas(t, F_h)
+        err = float(np.max(np.abs(B.cpu().numpy() - x_ref)) / np.max(np.abs(x_ref)))
+        return {"routine": "cusparseDgtsv2_nopivot", "unknowns": N, "ms": round(ms, 4), "ms_copy_of_F": round(ms_copy, 4),
+                "Gunknowns_s": round(N / ms / 1e6, 2), "Gunknowns_s_without_copy": round(N / (ms - ms_copy) / 1e6, 2),
+                "workspace_bytes": int(nbuf.value), "rel_err": err}
+    finally:
+        lib.cusparseDestroy(h)
+
+
 def other_configs(D, W, oracle, stream, world, steps=10):
     """C1 (latency), the weakly dominant C2 variant, C3 (2-D Poisson modes), C4 (uneven series),
     C5 (adjoint): time and Gunknowns/s per form, with the error against the oracle (on a
@@ -368,6 +431,9 @@ def other_configs(D, W, oracle, stream, world, steps=10):
             ref = solve((tm1[s_], t0[s_], tp1[s_]), Fd[o:o + n].cpu().numpy())
             errs.append(float(np.max(np.abs(xd[o:o + n].cpu().numpy() - ref)) / max(np.max(np.abs(ref)), 1e-300)))
         return max(errs)
+
+    out["cusparse_gtsv2_nopivot_c2"] = cusparse_comparator(W, oracle, stream, steps)
+    torch.cuda.empty_cache()
 
     # C1: tridiag{-1, 4, -1}, N = 65536 (1 MB in, 1 MB out): latency of one solve, three
     # buffer sets in rotation, many back-to-back solves between two events
