@@ -104,3 +104,48 @@ def test_fuzz_batches(D, seed):
         o, n = int(off[s]), int(N[s])
         if n:
             check((tm1[s], t0[s], tp1[s]), F[o:o + n], x[o:o + n])
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_fuzz_general_matrices(D, seed):
+    """Random general tridiagonal matrices (per-row dominance margins from 1e-4 to 3, random
+    signs, zero off-diagonals), both preliminary steps, every width and path flag."""
+    rng = np.random.default_rng(3000 + seed)
+    for _ in range(4):
+        N = int(10 ** rng.uniform(0.31, 6.0))
+        a = rng.uniform(-1, 1, N) * (rng.uniform(size=N) > 0.05)
+        c = rng.uniform(-1, 1, N) * (rng.uniform(size=N) > 0.05)
+        margin = 10 ** rng.uniform(-4, 0.5, N)
+        b = (np.abs(a) + np.abs(c)) * (1 + margin) + 1e-3 * (np.abs(a) + np.abs(c) == 0)
+        b *= rng.choice([-1.0, 1.0], N)
+        flags = int(rng.choice([4, 8])) | int(rng.choice([0, 1]))
+        threads = int(rng.choice([0, 64, 128, 256]))
+        plan = D.GenPlan(a, b, c, threads=threads, flags=flags)
+        F = rng.standard_normal(N)
+        x = plan.solve(torch.from_numpy(F).cuda()).cpu().numpy()
+        assert plan.status() == 0
+        ref = oracle.thomas_tridiag(a, b, c, F)
+        assert rel(x, ref) < 1e-11, (N, flags, plan.info)
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_fuzz_quasi_toeplitz(D, seed):
+    """Random quasi-Toeplitz matrices (eq. 21): corner entries t_0 + psi, t_0 + chi kept dominant."""
+    rng = np.random.default_rng(4000 + seed)
+    for _ in range(4):
+        t, margin = draw_t(rng)
+        N = int(10 ** rng.uniform(0.31, 6.0))
+        s0 = np.sign(t[1])
+        # |t_0 + psi| >= |t_1| and |t_0 + chi| >= |t_-1| with a margin
+        psi = s0 * (abs(t[2]) * (1 + rng.uniform(0.01, 1)) - abs(t[1])) * rng.uniform(0, 0.9)
+        chi = s0 * (abs(t[0]) * (1 + rng.uniform(0.01, 1)) - abs(t[1])) * rng.uniform(0, 0.9)
+        prec = int(rng.choice([0, 2]))
+        try:
+            plan = D.Plan(*t, N, psi=psi, chi=chi, precision=prec)
+        except D.DichotomyError as err:   # a corner system that is singular or loses dominance
+            assert err.code in (2, 3)
+            continue
+        F = rng.standard_normal(N)
+        x = plan.solve(torch.from_numpy(F).cuda()).cpu().numpy()
+        assert plan.status() == 0
+        assert rel(x, oracle.thomas_quasi(t, psi, chi, F)) < TOL, (t, psi, chi, N, plan.info)
