@@ -18,7 +18,8 @@
 //      coalesced store of the own rows.
 // Windows of a long system overlap by halo blocks on each side whose coupling into the
 // own blocks has decayed below 2^-64 (the truncation is exact to that level); on the
-// general path the window instead takes the first/last values from a global scan.
+// general path the window instead takes the first/last values from a global scan (the FP64
+// form's beta pass leaves xp in x and its apply pass starts from there, without new sweeps).
 //
 // This file holds the FP64 form (one block per thread) and what both window kernels share;
 // the MIXED form's kernel is in window_mixed.cuh.
@@ -180,8 +181,10 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   const int len = nwin * n - (has_last ? (n - nlast) : 0);  // rows in the window
 
   // ---------------------------------------------------------------- F -> smem (transposed, async)
+  // (MODE_APPLY: the block solutions y the beta pass left in x, instead of F)
   {
-    const double* src = A.F + (int64_t)blockIdx.y * A.ldf + off + row_lo;
+    const double* src = (A.mode == MODE_APPLY) ? (A.x + (int64_t)blockIdx.y * A.ldx + off + row_lo)
+                                               : (A.F + (int64_t)blockIdx.y * A.ldf + off + row_lo);
     int b = tid / n, i = tid - (tid / n) * n;
     const int db = NT / n, di = NT - (NT / n) * n;
     for (int j = tid; j < len; j += NT) {
@@ -211,7 +214,9 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   const bool lastb = act && (mb == P - 1);
   const int nbk = lastb ? nlast : n;
   double xm1 = 0.0, alpha = 0.0, omega = 0.0;
-  if (act) {
+  if (act && A.mode == MODE_APPLY) {
+    xm1 = pp->ib * S[tid];   // xp(-1) = g ib X_0 = ib y_0
+  } else if (act) {
     const double rs = pp->rs, ib = pp->ib, g = pp->g;
     double* col = S + tid;
     double u = 0.0;
@@ -270,10 +275,23 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   const double bL = act ? fma(bc[BC_M00], alpha, bc[BC_M01] * omega) : 0.0;
   const double bR = act ? fma(bc[BC_M10], alpha, bc[BC_M11] * omega) : 0.0;
 
-  if (A.mode == MODE_BETA) {  // general path: beta leaves the window
+  if (A.mode == MODE_BETA) {  // general path: beta and the block solutions y leave the window
     if (act) {
       A.beta[2 * (pp->gboff + mb)] = bL;
       A.beta[2 * (pp->gboff + mb) + 1] = bR;
+    }
+    __syncthreads();
+    double* dst = A.x + (int64_t)blockIdx.y * A.ldx + off + row_lo;
+    int b = tid / n, i = tid - (tid / n) * n;
+    const int db = NT / n, di = NT - (NT / n) * n;
+    for (int j = tid; j < len; j += NT) {
+      dst[j] = S[i * LD + b];
+      i += di;
+      b += db;
+      if (i >= n) {
+        i -= n;
+        ++b;
+      }
     }
     return;
   }

@@ -12,6 +12,8 @@
 //     v = T_m^-1 (-a_s e_0), w = T_m^-1 (-c_e e_{n-1}) stored per row.
 // Per-row tables are interleaved by groups of 32 blocks (gen_index), so that the threads of a
 // warp -- consecutive blocks, one per thread -- read row i of their blocks contiguously.
+// General path: the beta pass (MODE_BETA) leaves the local solutions y in x, and the apply
+// pass (MODE_APPLY) reads them back instead of F, so the local solve runs once.
 #pragma once
 #include "window.cuh"
 
@@ -72,8 +74,9 @@ __global__ void __launch_bounds__(NT) k_window_gen(const GenArgs G) {
   double* xw = A.x + (int64_t)blockIdx.y * A.ldx;
 
   // ---------------------------------------------------------------- F -> smem (transposed, async)
+  // (MODE_APPLY: the block solutions y the beta pass left in x, instead of F)
   {
-    const double* src = Fw + row_lo;
+    const double* src = ((A.mode == MODE_APPLY) ? xw : Fw) + row_lo;
     int b = tid / n, i = tid - (tid / n) * n;
     const int db = NT / n, di = NT - (NT / n) * n;
     for (int j = tid; j < len; j += NT) {
@@ -100,18 +103,45 @@ __global__ void __launch_bounds__(NT) k_window_gen(const GenArgs G) {
   const double* rw = G.rows + GF_W * G.stride;
   double alpha = 0.0, omega = 0.0;
   double* col = S + tid;
-  if (act) {
+  const int64_t k0 = gen_index(act ? mb : 0, 0, n);   // row i of the block at k0 + 32 i
+  if (act && A.mode != MODE_APPLY) {
+    // the per-row factors of four rows are loaded ahead of their dependent recurrence steps
     double z = 0.0;
-#pragma unroll 4
-    for (int i = 0; i < nbk; ++i) {
-      const int64_t k = gen_index(mb, i, n);
+    int i = 0;
+    for (; i + 4 <= nbk; i += 4) {
+      const int64_t k = k0 + 32 * i;
+      const double a0 = ra[k], a1 = ra[k + 32], a2 = ra[k + 64], a3 = ra[k + 96];
+      const double d0 = rd[k], d1 = rd[k + 32], d2 = rd[k + 64], d3 = rd[k + 96];
+      z = fma(-a0, z, col[i * LD]) * d0;
+      col[i * LD] = z;
+      z = fma(-a1, z, col[(i + 1) * LD]) * d1;
+      col[(i + 1) * LD] = z;
+      z = fma(-a2, z, col[(i + 2) * LD]) * d2;
+      col[(i + 2) * LD] = z;
+      z = fma(-a3, z, col[(i + 3) * LD]) * d3;
+      col[(i + 3) * LD] = z;
+    }
+    for (; i < nbk; ++i) {
+      const int64_t k = k0 + 32 * i;
       z = fma(-ra[k], z, col[i * LD]) * rd[k];
       col[i * LD] = z;
     }
     double y = 0.0;
-#pragma unroll 4
-    for (int i = nbk - 1; i >= 0; --i) {
-      y = fma(-rc[gen_index(mb, i, n)], y, col[i * LD]);
+    i = nbk - 1;
+    for (; i - 3 >= 0; i -= 4) {
+      const int64_t k = k0 + 32 * i;
+      const double c0 = rc[k], c1 = rc[k - 32], c2 = rc[k - 64], c3 = rc[k - 96];
+      y = fma(-c0, y, col[i * LD]);
+      col[i * LD] = y;
+      y = fma(-c1, y, col[(i - 1) * LD]);
+      col[(i - 1) * LD] = y;
+      y = fma(-c2, y, col[(i - 2) * LD]);
+      col[(i - 2) * LD] = y;
+      y = fma(-c3, y, col[(i - 3) * LD]);
+      col[(i - 3) * LD] = y;
+    }
+    for (; i >= 0; --i) {
+      y = fma(-rc[k0 + 32 * i], y, col[i * LD]);
       col[i * LD] = y;
     }
     alpha = col[0];
@@ -122,10 +152,22 @@ __global__ void __launch_bounds__(NT) k_window_gen(const GenArgs G) {
   const double* bc = A.tabs + pp->o_bcl + (act ? mb : 0) * kBC;
   const double bL = act ? fma(bc[BC_M00], alpha, bc[BC_M01] * omega) : 0.0;
   const double bR = act ? fma(bc[BC_M10], alpha, bc[BC_M11] * omega) : 0.0;
-  if (A.mode == MODE_BETA) {
+  if (A.mode == MODE_BETA) {   // beta and the block solutions y leave the window
     if (act) {
       A.beta[2 * (pp->gboff + mb)] = bL;
       A.beta[2 * (pp->gboff + mb) + 1] = bR;
+    }
+    __syncthreads();
+    int b = tid / n, i = tid - (tid / n) * n;
+    const int db = NT / n, di = NT - (NT / n) * n;
+    for (int j = tid; j < len; j += NT) {
+      xw[row_lo + j] = S[i * LD + b];
+      i += di;
+      b += db;
+      if (i >= n) {
+        i -= n;
+        ++b;
+      }
     }
     return;
   }
@@ -142,7 +184,7 @@ __global__ void __launch_bounds__(NT) k_window_gen(const GenArgs G) {
   if (act) {
 #pragma unroll 4
     for (int i = 0; i < nbk; ++i) {
-      const int64_t k = gen_index(mb, i, n);
+      const int64_t k = k0 + 32 * i;
       col[i * LD] = fma(XR, rw[k], fma(XL, rv[k], col[i * LD]));
     }
   }
