@@ -23,7 +23,7 @@ def declared_symbols():
     return sorted(set(re.findall(r"\b(dichotomy_\w+)\s*\(", text)))
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_solver_entry_points():
     syms = declared_symbols()
     for s in ("dichotomy_plan", "dichotomy_solve", "dichotomy_solve_batched", "dichotomy_adjoint"):
         assert s in syms

@@ -1,7 +1,7 @@
 """Seeded random cases through the C ABI against the oracle: random dominant Toeplitz matrices
 (mixed signs, one-sided, near-equality dominance), sizes from 2 to 1.6e6, every precision form,
 window width, block size and flag, series of right-hand sides with padded rows, and batches of
-random systems.  The bar is the spec one (1e-12 norm-wise against the FP64 oracle); where
+random systems.  The bar is 1e-12 norm-wise against the FP64 oracle; where
 the FP64 oracle itself is that far from the binary128 oracle (ill-conditioned draws), the GPU
 result must stay within 20 times the FP64 oracle's own error from binary128."""
 import numpy as np

@@ -1,7 +1,7 @@
 """Solves from and to host memory (dichotomy_solve_host): the kernels reading and writing
 pinned host memory directly (chunks = 0), and the pipelined copy-in / solve / copy-out (chunks
 >= 1, pageable buffers), give bitwise the device solve of the same plan and the oracle's
-solution to the benchmark spec's tolerance, for every chunking and the paths that do not pipeline
+solution to 1e-12 norm-wise, for every chunking and the paths that do not pipeline
 (one window, the general path, quasi-Toeplitz corners)."""
 import ctypes
 

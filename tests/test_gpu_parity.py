@@ -1,6 +1,6 @@
 """GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
 
-Bar (the benchmark spec's tolerance): norm-wise relative error max|x - x_oracle| / max|x_oracle|
+Bar: norm-wise relative error max|x - x_oracle| / max|x_oracle|
 <= 1e-12 for diagonally dominant FP64 systems, in both the FP64 and the MIXED form.  For the
 ill-conditioned extras (weak dominance, the 1-D Laplacian) the binary128 oracle arbitrates:
 the GPU error against it must stay within the FP64 oracle's own error (times a small factor).
