@@ -10,6 +10,8 @@ arbiter.  Functions:
 
 * ``thomas(t, F)``            sequential Thomas, FP64 (Sec. 2.2, eq. 7).
 * ``thomas_q(t, F)``          the same in binary128, rounded to FP64.
+* ``thomas_tridiag(a, b, c, F)`` Thomas for a general tridiagonal matrix (Sec. 2), FP64.
+* ``thomas_quasi(t, psi, chi, F)`` the quasi-Toeplitz matrix of eq. 21 through ``thomas_tridiag``.
 * ``thomas_batched(...)``     one Thomas per system on a thread pool.
 * ``adjoint(t, w, x)``        lambda = T^-T w and dL/d(t_-1, t_0, t_1).
 * ``dich_eq15(t, F, starts)`` the paper's formulas eq. 9-16 + eq. 7.
@@ -17,6 +19,8 @@ arbiter.  Functions:
 * ``dich_prelim(t, N, starts)`` the preliminary vectors G (eq. 9) and Z (eq. 10-12).
 
 ``t`` is always the triple ``(t_-1, t_0, t_1)``: sub-, main and super-diagonal.
+``oracle.poisson`` holds the 2-D Poisson oracle (Sec. 3.2, Sec. 4); ``build_variant`` compiles
+the C part with one deliberate mistake planted, for the tests that show the pins catch it.
 """
 from __future__ import annotations
 
