@@ -94,6 +94,9 @@ typedef struct {
   double rs, ib;           /* roots: |rs| <= 1 <= |1/ib| of t_1 r^2 + t_0 r + t_-1 = 0 */
   double z;                /* rs * ib */
   size_t workspace_bytes;
+  size_t beta_offset;      /* general path: byte offsets into the workspace of the per-block */
+  size_t iface_offset;     /* (beta^L, beta^R) of eq. 16 and first/last values (x_s, x_e) of
+                              eq. 18 the last solve left there, 2 doubles per block; 0 otherwise */
 } dich_plan_info;
 
 typedef struct dich_plan_s* dich_plan_t;

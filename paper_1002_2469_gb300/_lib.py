@@ -58,7 +58,8 @@ class dich_plan_info(ctypes.Structure):
     _fields_ = [("N", c_int64), ("P", c_int64), ("n", c_int32), ("n_last", c_int32), ("threads", c_int32),
                 ("halo_l", c_int32), ("halo_r", c_int32), ("path", c_int32), ("precision", c_int32),
                 ("tiles", c_int64), ("Lv", c_int32), ("Lw", c_int32), ("kl", c_int32), ("kr", c_int32),
-                ("rs", c_double), ("ib", c_double), ("z", c_double), ("workspace_bytes", c_size_t)]
+                ("rs", c_double), ("ib", c_double), ("z", c_double), ("workspace_bytes", c_size_t),
+                ("beta_offset", c_size_t), ("iface_offset", c_size_t)]
 
 
 _lib_obj = None

@@ -619,6 +619,10 @@ int dichotomy_plan_info(dich_plan_t p, dich_plan_info* info) {
   info->ib = rt.ib;
   info->z = rt.z;
   info->workspace_bytes = p->ws_bytes;
+  if (p->path == PATH_GENERAL) {
+    info->beta_offset = p->off_beta;
+    info->iface_offset = p->off_iface;
+  }
   return DICH_OK;
 }
 

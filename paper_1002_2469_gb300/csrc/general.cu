@@ -438,6 +438,10 @@ int dichotomy_gen_info(dich_gen_t g, dich_plan_info* info) {
   info->precision = DICH_PREC_F64;
   info->tiles = g->tiles;
   info->workspace_bytes = g->ws_bytes;
+  if (g->path == PATH_GENERAL) {
+    info->beta_offset = g->off_beta;
+    info->iface_offset = g->off_iface;
+  }
   return DICH_OK;
 }
 
