@@ -122,8 +122,8 @@ int dichotomy_plan_ex(double t_m1, double t_0, double t_1, int64_t N, const dich
  * followed by the rank-2 corner correction x = y - c_0 g - c_1 h (Sherman-Morrison-Woodbury:
  * g, h are the first and last columns of T^-1 in closed form, kept where they exceed the
  * truncation threshold, and (c_0, c_1) solves a 2x2 system in psi y_0, chi y_{N-1}); two extra
- * small kernels per solve.  psi = chi = 0 gives the plain Toeplitz plan.  dichotomy_solve and
- * dichotomy_solve_series serve the plan; dichotomy_adjoint returns DICH_ERR_UNSUPPORTED.
+ * small kernels per solve.  psi = chi = 0 gives the plain Toeplitz plan.  dichotomy_solve,
+ * dichotomy_solve_series and dichotomy_adjoint (with dL/dpsi, dL/dchi) serve the plan.
  * Errors: as dichotomy_plan_ex; DICH_ERR_NOT_DOMINANT when an end row loses dominance
  * (|t_0 + psi| < |t_1| or |t_0 + chi| < |t_-1|), DICH_ERR_SINGULAR when the corner system is. */
 int dichotomy_plan_quasi(double t_m1, double t_0, double t_1, double psi, double chi, int64_t N,
@@ -181,7 +181,10 @@ int dichotomy_solve_host(dich_plan_t plan, const double* h_F, double* h_x, doubl
  *   d_gF = lambda = T^-T w   (the same Dichotomy solve for T^T = tridiag{t_1, t_0, t_-1}),
  *   d_gt[0..2] = (dL/dt_-1, dL/dt_0, dL/dt_1) = -(sum_i lambda_i x_{i-1},
  *                sum_i lambda_i x_i, sum_i lambda_i x_{i+1}).
- * Not in the paper.  d_gt is 3 doubles on the device.  d_gF may not alias d_w or d_x. */
+ * Quasi-Toeplitz plans (eq. 21, psi or chi nonzero): lambda = A^-T w (the transposed corner
+ * correction after T^-T w) and d_gt holds 5 doubles, adding dL/dpsi = -lambda_0 x_0 and
+ * dL/dchi = -lambda_{N-1} x_{N-1}.  Not in the paper.  d_gt is 3 (5) doubles on the device.
+ * d_gF may not alias d_w or d_x. */
 int dichotomy_adjoint(dich_plan_t plan, const double* d_w, const double* d_x, double* d_gF,
                       double* d_gt, void* stream);
 

@@ -12,6 +12,7 @@ arbiter.  Functions:
 * ``thomas_q(t, F)``          the same in binary128, rounded to FP64.
 * ``thomas_tridiag(a, b, c, F)`` Thomas for a general tridiagonal matrix (Sec. 2), FP64.
 * ``thomas_quasi(t, psi, chi, F)`` the quasi-Toeplitz matrix of eq. 21 through ``thomas_tridiag``.
+* ``adjoint_quasi(t, psi, chi, w, x)`` its adjoint: A^-T w and the five parameter gradients.
 * ``thomas_batched(...)``     one Thomas per system on a thread pool.
 * ``adjoint(t, w, x)``        lambda = T^-T w and dL/d(t_-1, t_0, t_1).
 * ``dich_eq15(t, F, starts)`` the paper's formulas eq. 9-16 + eq. 7.
@@ -121,6 +122,23 @@ def thomas_quasi(t, psi, chi, F) -> np.ndarray:
         dia[0] += psi
         dia[-1] += chi
     return thomas_tridiag(np.full(n, float(t[0])), dia, np.full(n, float(t[2])), F)
+
+
+def adjoint_quasi(t, psi, chi, w, x):
+    """Adjoint of L(x), x = A^-1 F, for the quasi-Toeplitz A of eq. 21, given w = dL/dx and x:
+    lambda = A^-T w (A^T is the quasi-Toeplitz matrix of tridiag{t_1, t_0, t_-1} with the same
+    corners) and the gradient (dL/dt_-1, dL/dt_0, dL/dt_1, dL/dpsi, dL/dchi) =
+    -(sum lambda_i x_{i-1}, sum lambda_i x_i, sum lambda_i x_{i+1}, lambda_0 x_0, lambda_{N-1} x_{N-1})."""
+    w, x = _f64(w), _f64(x)
+    lam = thomas_quasi((t[2], t[1], t[0]), psi, chi, w)
+    g = np.zeros(5)
+    if x.size:
+        g[0] = -float(np.dot(lam[1:], x[:-1]))
+        g[1] = -float(np.dot(lam, x))
+        g[2] = -float(np.dot(lam[:-1], x[1:]))
+        g[3] = -lam[0] * x[0]
+        g[4] = -lam[-1] * x[-1]
+    return lam, g
 
 
 def thomas_q(t, F) -> np.ndarray:

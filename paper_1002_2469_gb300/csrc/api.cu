@@ -332,9 +332,11 @@ struct dich_plan_s {
   SysBuild fwd, adj;
   // quasi-Toeplitz corners (eq. 21): t_0 + psi in row 0, t_0 + chi in row N-1
   bool quasi = false;
+  bool corners = false;                // psi or chi nonzero: the adjoint also returns dL/dpsi, dL/dchi
   double psi = 0.0, chi = 0.0;
   int64_t Lg = 0, Lh = 0;              // kept rows of g = T^-1 e_0 and h = T^-1 e_{N-1}
   double W[4] = {1.0, 0.0, 0.0, 1.0};  // (I + K)^-1 of the Sherman-Morrison-Woodbury step
+  double Wt[4] = {1.0, 0.0, 0.0, 1.0}; // the same for A^T (its corner vectors are h and g reversed)
   std::vector<double> corner;          // g[Lg], then h[Lh] (h[k] is row N-1-k)
   // workspace layout (bytes)
   size_t ws_bytes = 0, off_plans = 0, off_status = 0, off_tabs = 0, off_beta = 0, off_iface = 0,
@@ -560,6 +562,7 @@ int dichotomy_plan_quasi(double t_m1, double t_0, double t_1, double psi, double
   int rc = dichotomy_plan_ex(t_m1, t_0, t_1, N, opts, &p);
   if (rc) return rc;
   p->quasi = (psi != 0.0 || chi != 0.0);
+  p->corners = p->quasi;
   p->psi = psi;
   p->chi = chi;
   if (p->quasi && N == 1) {
@@ -590,6 +593,12 @@ int dichotomy_plan_quasi(double t_m1, double t_0, double t_1, double psi, double
     p->W[1] = -k01 / det;
     p->W[2] = -k10 / det;
     p->W[3] = k00 / det;
+    // A^T: Toeplitz inverses are persymmetric, so (T^-T e_0)_i = h at row N-1-i and
+    // (T^-T e_{N-1})_i = g at row N-1-i; the 2x2 system has the same determinant
+    p->Wt[0] = k11 / det;
+    p->Wt[1] = -psi * gN / det;
+    p->Wt[2] = -chi * h0 / det;
+    p->Wt[3] = k00 / det;
     plan_layout(p);
   }
   *out = p;
@@ -721,6 +730,14 @@ static int plan_launch(dich_plan_t p, const double* F, double* x, const double* 
     e = launch_adj_finalize(a.part, nullptr, nullptr, nullptr, p->tiles, 1, gt, st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
+  if (p->quasi && adjoint) {
+    // lambda = A^-T w from T^-T w: the corner correction with the transposed corner vectors, and
+    // its share of the gradient sums plus dL/dpsi, dL/dchi (read before lambda is corrected)
+    const double* ctab = d_tabs + p->fwd.tab.size() + p->adj.tab.size();
+    CornerArgs c{p->N, p->Lh, p->Lg, ctab + p->Lg, ctab, p->psi, p->chi, p->Wt[0], p->Wt[1], p->Wt[2], p->Wt[3]};
+    e = launch_corner_adjoint(xf, x, gt, c, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   if (p->quasi && !adjoint && !(p->path == PATH_GENERAL && M > 1)) {
     const double* ctab = d_tabs + p->fwd.tab.size() + p->adj.tab.size();
     CornerArgs c{p->N, p->Lg, p->Lh, ctab, ctab + p->Lg, p->psi, p->chi, p->W[0], p->W[1], p->W[2], p->W[3]};
@@ -850,18 +867,24 @@ int dichotomy_solve_series(dich_plan_t p, int64_t M, const double* d_F, int64_t 
 int dichotomy_adjoint(dich_plan_t p, const double* d_w, const double* d_x, double* d_gF, double* d_gt,
                       void* stream) {
   if (!p) return DICH_ERR_ARG;
-  if (p->quasi) return DICH_ERR_UNSUPPORTED;
   if (!p->d_ws) return DICH_ERR_UNBOUND;
   if (!d_gt || !aligned8(d_gt) || !is_device_ptr(d_gt)) return DICH_ERR_ARG;
+  const size_t ngt = sizeof(double) * (p->corners ? 5 : 3);
+  cudaStream_t st = (cudaStream_t)stream;
   if (p->N == 0) {
-    cudaError_t e = cudaMemsetAsync(d_gt, 0, 3 * sizeof(double), (cudaStream_t)stream);
+    cudaError_t e = cudaMemsetAsync(d_gt, 0, ngt, st);
     return e == cudaSuccess ? DICH_OK : cuda_fail(e);
   }
   if (!d_w || !d_x || !d_gF || !aligned8(d_w) || !aligned8(d_x) || !aligned8(d_gF)) return DICH_ERR_ARG;
   const size_t nb = sizeof(double) * (size_t)p->N;
-  if (overlap(d_gF, nb, d_w, nb) || overlap(d_gF, nb, d_x, nb) || overlap(d_gt, 24, d_gF, nb)) return DICH_ERR_ALIAS;
+  if (overlap(d_gF, nb, d_w, nb) || overlap(d_gF, nb, d_x, nb) || overlap(d_gt, ngt, d_gF, nb)) return DICH_ERR_ALIAS;
   if (!is_device_ptr(d_w) || !is_device_ptr(d_x) || !is_device_ptr(d_gF)) return DICH_ERR_ARG;
-  return plan_launch(p, d_w, d_gF, d_x, d_gt, true, (cudaStream_t)stream);
+  const int rc = plan_launch(p, d_w, d_gF, d_x, d_gt, true, st);
+  if (rc != DICH_OK || !p->corners || p->quasi) return rc;
+  // one row (t_0 + psi + chi): dL/dpsi = dL/dchi = dL/dt_0
+  cudaError_t e = cudaMemcpyAsync(d_gt + 3, d_gt + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_gt + 4, d_gt + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? DICH_OK : cuda_fail(e);
 }
 
 int dichotomy_status(dich_plan_t p, void* stream, int* device_status) {

@@ -367,4 +367,58 @@ cudaError_t launch_corner(double* x, int64_t M, int64_t ldx, const CornerArgs& c
   return cudaGetLastError();
 }
 
+// Adjoint of a quasi-Toeplitz plan, before the corner correction of lambda (launched after the
+// adjoint window kernels and k_adj_finalize): with lambda_T = T^-T w in lam and the transposed
+// corner vectors in c, lambda = lambda_T - c0 g - c1 h changes the gradient sums by
+// + c0 sum_i g_i x_{i+s} + c1 sum_i h_i x_{i+s} (s = -1, 0, 1; gt holds -sum lambda x), and
+// dL/dpsi = -lambda_0 x_0, dL/dchi = -lambda_{N-1} x_{N-1} come from the corrected end values.
+__global__ void __launch_bounds__(256) k_corner_adj(const double* xf, const double* lam, CornerArgs c, double* gt) {
+  __shared__ double sh[6 * 256];
+  const int64_t N = c.N;
+  const double y0 = lam[0], yn = lam[N - 1];
+  const double a = c.psi * y0, b = c.chi * yn;
+  const double c0 = fma(c.w00, a, c.w01 * b), c1 = fma(c.w10, a, c.w11 * b);
+  auto xv = [&](int64_t i) { return (i >= 0 && i < N) ? xf[i] : 0.0; };
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // sum g x_{i-1}, g x_i, g x_{i+1}, then h
+  for (int64_t i = threadIdx.x; i < c.Lg; i += 256) {
+    const double gi = c.g[i];
+    acc[0] = fma(gi, xv(i - 1), acc[0]);
+    acc[1] = fma(gi, xv(i), acc[1]);
+    acc[2] = fma(gi, xv(i + 1), acc[2]);
+  }
+  for (int64_t k = threadIdx.x; k < c.Lh; k += 256) {
+    const int64_t i = N - 1 - k;
+    const double hk = c.h[k];
+    acc[3] = fma(hk, xv(i - 1), acc[3]);
+    acc[4] = fma(hk, xv(i), acc[4]);
+    acc[5] = fma(hk, xv(i + 1), acc[5]);
+  }
+  for (int j = 0; j < 6; ++j) sh[j * 256 + threadIdx.x] = acc[j];
+  __syncthreads();
+  for (int d = 128; d > 0; d >>= 1) {
+    if ((int)threadIdx.x < d)
+      for (int j = 0; j < 6; ++j) sh[j * 256 + threadIdx.x] += sh[j * 256 + threadIdx.x + d];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 3; ++s) gt[s] += fma(c0, sh[s * 256], c1 * sh[(3 + s) * 256]);
+    // the corrected end values, in the corner kernel's order of operations
+    double l0 = y0, ln = yn;
+    if (0 < c.Lg) l0 = fma(-c0, c.g[0], l0);
+    if (N - 1 < c.Lh) l0 = fma(-c1, c.h[N - 1], l0);
+    if (N - 1 < c.Lg) ln = fma(-c0, c.g[N - 1], ln);
+    if (0 < c.Lh) ln = fma(-c1, c.h[0], ln);
+    gt[3] = -l0 * xf[0];
+    gt[4] = -ln * xf[N - 1];
+  }
+}
+
+cudaError_t launch_corner_adjoint(const double* xf, double* lam, double* gt, const CornerArgs& c, cudaStream_t st) {
+  if (c.N <= 0) return cudaSuccess;
+  k_corner_adj<<<1, 256, 0, st>>>(xf, lam, c, gt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_corner(lam, 1, 0, c, st);
+}
+
 }  // namespace dich

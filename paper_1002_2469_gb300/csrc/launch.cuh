@@ -57,5 +57,8 @@ struct CornerArgs {
 
 // x_k <- A^-1 F_k from y_k = T^-1 F_k (already in x_k = x + k ldx), k = 0..M-1: two kernels
 cudaError_t launch_corner(double* x, int64_t M, int64_t ldx, const CornerArgs& c, cudaStream_t st);
+// adjoint of a quasi-Toeplitz plan: gradient terms of the corner correction, dL/dpsi, dL/dchi
+// (gt[0..4]), then the corner correction of lambda (c: the transposed corner vectors)
+cudaError_t launch_corner_adjoint(const double* xf, double* lam, double* gt, const CornerArgs& c, cudaStream_t st);
 
 }  // namespace dich

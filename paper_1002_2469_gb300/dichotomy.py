@@ -278,8 +278,9 @@ class Plan:
         return x
 
     def adjoint(self, w: torch.Tensor, x: torch.Tensor, stream=None):
+        """lambda = A^-T w and dL/d(t_-1, t_0, t_1) (then dL/dpsi, dL/dchi for corner plans)."""
         gF = torch.empty_like(w)
-        gt = torch.empty(3, dtype=torch.float64, device=w.device)
+        gt = torch.empty(5 if any(self.corners) else 3, dtype=torch.float64, device=w.device)
         dichotomy_adjoint(self._h, w, x, gF, gt, stream)
         return gF, gt
 

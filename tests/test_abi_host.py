@@ -201,7 +201,7 @@ def test_quasi_plan_validation_and_series_arguments_without_a_gpu():
     h = ctypes.c_void_p()
     assert lib.dichotomy_plan_quasi(*t, 0.3, 0.2, 100, ctypes.byref(o), ctypes.byref(h)) == 0
     try:
-        assert lib.dichotomy_adjoint(h, None, None, None, None, None) == 11   # DICH_ERR_UNSUPPORTED
+        assert lib.dichotomy_adjoint(h, None, None, None, None, None) == 8    # unbound
         assert lib.dichotomy_solve_series(h, 2, None, 100, None, 100, None) == 8   # unbound
         assert lib.dichotomy_solve_series(h, -1, None, 100, None, 100, None) == 1  # M < 0
         assert lib.dichotomy_solve_host(h, None, None, None, None, 0, None) == 8    # unbound

@@ -259,6 +259,27 @@ def test_quasi_one_row(D):
     assert x[0] == 3.0 / 4.75
 
 
+@pytest.mark.parametrize("prec,flags", [(0, 0), (1, 0), (2, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("t,psi,chi", QUASI)
+@pytest.mark.parametrize("N", [1, 2, 3, 50, 4097, 300001])
+def test_quasi_toeplitz_adjoint(D, t, psi, chi, N, prec, flags):
+    """Adjoint of a quasi-Toeplitz plan: lambda = A^-T w and the five gradients
+    (t_-1, t_0, t_1, psi, chi) against the oracle's quasi adjoint, on the halo and general paths."""
+    rng = np.random.default_rng(N + 17)
+    F, w = rng.uniform(-1, 1, N), rng.uniform(-1, 1, N)
+    plan = D.Plan(*t, N, precision=prec, psi=psi, chi=chi, flags=flags)
+    x = plan.solve(torch.from_numpy(F).cuda())
+    gF, gt = plan.adjoint(torch.from_numpy(w).cuda(), x)
+    assert plan.status() == 0 and gt.numel() == 5
+    lam_ref, g_ref = oracle.adjoint_quasi(t, psi, chi, w, oracle.thomas_quasi(t, psi, chi, F))
+    lam = gF.cpu().numpy()
+    assert rel(lam, lam_ref) < TOL, plan.info
+    g = gt.cpu().numpy()
+    assert np.all(np.abs(g[:3] - g_ref[:3]) <= TOL * np.max(np.abs(g_ref[:3])) + 1e-300), (g, g_ref)
+    scale = np.max(np.abs(lam_ref)) * np.max(np.abs(x.cpu().numpy()))
+    assert np.all(np.abs(g[3:] - g_ref[3:]) <= TOL * scale), (g, g_ref)
+
+
 def test_trivial_sizes(D):
     for N in (0, 1, 2):
         F = np.arange(1, N + 1, dtype=np.float64)

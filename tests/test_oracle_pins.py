@@ -345,6 +345,35 @@ def test_quasi_toeplitz_eq21_vs_dense(t, psi, chi):
     assert rel(oracle.thomas_quasi(t, psi, chi, F), np.linalg.solve(A, F)) < 1e-14
 
 
+@pytest.mark.parametrize("t,psi,chi", [((-1.0, 2.5, -1.0), -1.0, -1.0), ((0.7, 2.5, -1.1), -0.5, 1.5),
+                                       ((-1.2, 2.5, -0.8), 0.0, 0.9)])
+def test_quasi_adjoint_vs_dense_and_finite_differences(t, psi, chi):
+    """The quasi-Toeplitz adjoint: lambda against a dense solve with A^T, the five gradients
+    against central finite differences of L = <w, A(t, psi, chi)^-1 F> with dense solves."""
+    N = 40
+    rng = np.random.default_rng(3)
+    F, w = rng.standard_normal(N), rng.standard_normal(N)
+
+    def dense(p):
+        tm1, t0, tp1, ps, ch = p
+        A = np.diag(np.full(N, t0)) + np.diag(np.full(N - 1, tm1), -1) + np.diag(np.full(N - 1, tp1), 1)
+        A[0, 0] += ps
+        A[N - 1, N - 1] += ch
+        return A
+
+    p0 = np.array([t[0], t[1], t[2], psi, chi])
+    x = np.linalg.solve(dense(p0), F)
+    lam, g = oracle.adjoint_quasi(t, psi, chi, w, x)
+    assert rel(lam, np.linalg.solve(dense(p0).T, w)) < 1e-13
+    assert abs(np.dot(w, x) - np.dot(lam, F)) < 1e-12 * np.abs(w).sum() * np.abs(x).max()
+    h = 1e-6
+    for k in range(5):
+        dp = np.zeros(5)
+        dp[k] = h
+        fd = (np.dot(w, np.linalg.solve(dense(p0 + dp), F)) - np.dot(w, np.linalg.solve(dense(p0 - dp), F))) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g[k])), (k, fd, g[k])
+
+
 # ------------------------------------------------------------------ 2-D Poisson by separation of variables
 def test_poisson2d_oracle_vs_dense_kronecker():
     """The separation-of-variables oracle against a dense solve of the five-point Laplacian,
