@@ -22,7 +22,7 @@ __all__ = [
     "dichotomy_solve", "dichotomy_solve_series", "dichotomy_solve_host", "dichotomy_adjoint", "dichotomy_status", "dichotomy_destroy",
     "dichotomy_batch_prepare", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
     "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
-    "dichotomy_batch_destroy", "Plan", "Batch", "GenPlan", "solve", "DichotomySolve", "DichotomySolveBatched",
+    "dichotomy_batch_destroy", "Plan", "Batch", "GenPlan", "solve", "DichotomySolve", "DichotomySolveQuasi", "DichotomySolveBatched",
     "PREC_F64", "PREC_MIXED", "PREC_AUTO", "FLAG_FORCE_GENERAL", "FLAG_CHECK_FINITE", "FLAG_HOST_PRELIM", "FLAG_DEVICE_PRELIM", "DichotomyError",
 ]
 
@@ -420,6 +420,30 @@ class DichotomySolve(torch.autograd.Function):
         (x,) = ctx.saved_tensors
         gF, gt = ctx.plan.adjoint(gx.contiguous(), x)
         return gF, gt.to(dtype=torch.float64), None
+
+
+class DichotomySolveQuasi(torch.autograd.Function):
+    """x = A^-1 F for the quasi-Toeplitz A of eq. 21; t = tensor([t_-1, t_0, t_1]), corners =
+    tensor([psi, chi]) (float64).  The backward pass is one adjoint call: dL/dF = A^-T dL/dx,
+    dL/dt and dL/d(psi, chi)."""
+
+    @staticmethod
+    def forward(ctx, F, t, corners, precision=PREC_F64):
+        tv = [float(v) for v in t.detach().cpu().tolist()]
+        psi, chi = (float(v) for v in corners.detach().cpu().tolist())
+        plan = Plan(tv[0], tv[1], tv[2], F.numel(), precision=precision, device=F.device, psi=psi, chi=chi)
+        x = plan.solve(F.detach().contiguous())
+        ctx.plan = plan
+        ctx.save_for_backward(x)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        gF, g = ctx.plan.adjoint(gx.contiguous(), x)
+        if g.numel() == 3:   # psi = chi = 0: a plain Toeplitz plan, dL/dpsi = -lambda_0 x_0 etc.
+            g = torch.cat([g, -(gF[:1] * x[:1]), -(gF[-1:] * x[-1:])])
+        return gF, g[:3], g[3:5], None
 
 
 class DichotomySolveBatched(torch.autograd.Function):

@@ -520,6 +520,25 @@ def test_autograd_function(D):
     assert np.max(np.abs(t.grad.cpu().numpy() - g)) <= TOL * np.max(np.abs(g))
 
 
+@pytest.mark.parametrize("corners", [(-0.8, 0.4), (0.0, 0.0), (0.0, 1.1)])
+def test_autograd_quasi(D, corners):
+    """Autograd through a quasi-Toeplitz solve: gradients of <w, x> with respect to F, t and the
+    corners, against the oracle's quasi adjoint."""
+    t = torch.tensor([-1.2, 2.5, -0.8], dtype=torch.float64, device="cuda", requires_grad=True)
+    c = torch.tensor(corners, dtype=torch.float64, device="cuda", requires_grad=True)
+    N = 3001
+    F = torch.from_numpy(np.random.default_rng(6).uniform(-1, 1, N)).cuda().requires_grad_(True)
+    w = torch.from_numpy(np.random.default_rng(7).uniform(-1, 1, N)).cuda()
+    x = D.DichotomySolveQuasi.apply(F, t, c)
+    (x * w).sum().backward()
+    tt = tuple(t.detach().cpu().tolist())
+    lam, g = oracle.adjoint_quasi(tt, corners[0], corners[1], w.cpu().numpy(),
+                                  oracle.thomas_quasi(tt, corners[0], corners[1], F.detach().cpu().numpy()))
+    assert rel(F.grad.cpu().numpy(), lam) < TOL
+    assert np.max(np.abs(t.grad.cpu().numpy() - g[:3])) <= TOL * np.max(np.abs(g[:3]))
+    assert np.max(np.abs(c.grad.cpu().numpy() - g[3:])) <= TOL * np.max(np.abs(lam)) * np.max(np.abs(x.detach().cpu().numpy()))
+
+
 @pytest.mark.parametrize("flags", [0, 1])
 def test_cuda_graph_capture_and_replay(D, flags):
     """A bound plan's solve only enqueues kernels on the caller's stream (no allocation, no host
