@@ -223,6 +223,16 @@ int dichotomy_solve_noalloc(double t_m1, double t_0, double t_1, int64_t N, cons
 int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_offset,
                             const double* h_tm1, const double* h_t0, const double* h_tp1,
                             const dich_opts* opts, dich_batch_t* out);
+
+/* A batch in which system s is the quasi-Toeplitz matrix of eq. 21: tridiag{t_-1, t_0, t_1}[s]
+ * with t_0 + psi[s] in its first row and t_0 + chi[s] in its last (host arrays of nsys entries;
+ * psi = chi = 0 leaves a system plain).  The Toeplitz solves run as in dichotomy_batch_prepare;
+ * then one CTA per quasi system applies its rank-2 corner correction (as dichotomy_plan_quasi).
+ * dichotomy_adjoint_batched returns DICH_ERR_UNSUPPORTED for a batch with corner systems.
+ * Errors: as dichotomy_batch_prepare and dichotomy_plan_quasi (per system). */
+int dichotomy_batch_prepare_quasi(int64_t nsys, const int64_t* h_N, const int64_t* h_offset, const double* h_tm1,
+                                  const double* h_t0, const double* h_tp1, const double* h_psi, const double* h_chi,
+                                  const dich_opts* opts, dich_batch_t* out);
 int dichotomy_batch_workspace_bytes(dich_batch_t batch, size_t* bytes);
 int dichotomy_batch_bind(dich_batch_t batch, void* d_workspace, size_t bytes, void* stream);
 /* Solve every system of the batch in one launch per precision form. */

@@ -29,7 +29,7 @@ EXPORTS = [
     "dichotomy_plan", "dichotomy_plan_ex", "dichotomy_plan_quasi", "dichotomy_plan_info", "dichotomy_plan_workspace_bytes",
     "dichotomy_plan_bind", "dichotomy_solve", "dichotomy_solve_series", "dichotomy_solve_host", "dichotomy_adjoint", "dichotomy_status", "dichotomy_destroy",
     "dichotomy_solve_noalloc",
-    "dichotomy_batch_prepare", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
+    "dichotomy_batch_prepare", "dichotomy_batch_prepare_quasi", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
     "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
     "dichotomy_batch_destroy", "dichotomy_strerror", "dichotomy_last_cuda_error", "dichotomy_version",
     "dichotomy_gen_plan", "dichotomy_gen_info", "dichotomy_gen_workspace_bytes", "dichotomy_gen_bind",
@@ -100,6 +100,8 @@ def load(build_if_missing: bool = True):
             "dichotomy_destroy": ([P], None),
             "dichotomy_solve_noalloc": ([c_double, c_double, c_double, c_int64, P, P, P], I),
             "dichotomy_batch_prepare": ([c_int64, P, P, P, P, P, ctypes.POINTER(dich_opts), ctypes.POINTER(P)], I),
+            "dichotomy_batch_prepare_quasi": ([c_int64, P, P, P, P, P, P, P, ctypes.POINTER(dich_opts),
+                                               ctypes.POINTER(P)], I),
             "dichotomy_batch_workspace_bytes": ([P, ctypes.POINTER(c_size_t)], I),
             "dichotomy_batch_bind": ([P, P, c_size_t, P], I),
             "dichotomy_solve_batched": ([P, P, P, P], I),

@@ -319,6 +319,59 @@ int map_status(unsigned s) {
 }  // namespace plan
 }  // namespace dich
 
+// ================================================================== quasi-Toeplitz corners (eq. 21)
+// Corner data of A = T + psi e_0 e_0^T + chi e_{N-1} e_{N-1}^T, N >= 2: g = T^-1 e_0 and
+// h = T^-1 e_{N-1} in closed form (the block spikes of a block of N rows), kept to Lg and Lh
+// rows (g_i = -(1/q) rs^i Q(N-i)/Q(N+1); h at row N-1-k = -(1/q) ib^k Q(N-k)/Q(N+1)), stored as
+// g[Lg] then h[Lh]; W = (I + K)^-1 of the Sherman-Morrison-Woodbury step and Wt the same for A^T
+// (Toeplitz inverses are persymmetric, so A^T's corner vectors are h and g read backwards and its
+// 2x2 system has the same determinant).  Returns DICH_ERR_SINGULAR when the 2x2 system is.
+struct Corners {
+  int64_t Lg = 0, Lh = 0;
+  std::vector<double> gh;
+  double W[4] = {1.0, 0.0, 0.0, 1.0}, Wt[4] = {1.0, 0.0, 0.0, 1.0};
+};
+
+static int corner_build(double t_m1, double t_0, double t_1, double psi, double chi, int64_t N, double eps,
+                        Corners& c) {
+  const Roots r = toeplitz_roots(t_m1, t_0, t_1);
+  c.Lg = decay_len(std::fabs(r.rs), eps, N);
+  c.Lh = decay_len(std::fabs(r.ib), eps, N);
+  c.gh.resize((size_t)(c.Lg + c.Lh));
+  for (int64_t i = 0; i < c.Lg; ++i) c.gh[(size_t)i] = r.g * ipow(r.rs, i) * spike_ratio(N, i, r);
+  for (int64_t k = 0; k < c.Lh; ++k) c.gh[(size_t)(c.Lg + k)] = r.g * ipow(r.ib, k) * spike_ratio(N, k, r);
+  const double qN1 = qnum(N + 1, r), qN = qnum(N, r);
+  const double g0 = r.g * qN / qN1, gN = r.g * ipow(r.rs, N - 1) / qN1;   // (T^-1)_{0,0}, (T^-1)_{N-1,0}
+  const double h0 = r.g * ipow(r.ib, N - 1) / qN1, hN = r.g * qN / qN1;   // (T^-1)_{0,N-1}, (T^-1)_{N-1,N-1}
+  const double k00 = 1.0 + psi * g0, k01 = psi * h0, k10 = chi * gN, k11 = 1.0 + chi * hN;
+  const double det = k00 * k11 - k01 * k10;
+  if (!std::isfinite(det) || std::fabs(det) <= 64.0 * DBL_EPSILON * (std::fabs(k00 * k11) + std::fabs(k01 * k10)))
+    return DICH_ERR_SINGULAR;
+  c.W[0] = k11 / det;
+  c.W[1] = -k01 / det;
+  c.W[2] = -k10 / det;
+  c.W[3] = k00 / det;
+  c.Wt[0] = k11 / det;
+  c.Wt[1] = -psi * gN / det;
+  c.Wt[2] = -chi * h0 / det;
+  c.Wt[3] = k00 / det;
+  return DICH_OK;
+}
+
+// the end rows of eq. 21 must keep dominance (eq. 32-33; the interior rows are T's)
+static int corner_check(double t_m1, double t_0, double t_1, double psi, double chi, int64_t N) {
+  if (!std::isfinite(psi) || !std::isfinite(chi)) return DICH_ERR_ARG;
+  if (N >= 2) {
+    const double tol = 1.0 - 4.0 * DBL_EPSILON;
+    if (std::fabs(t_0 + psi) < std::fabs(t_1) * tol || std::fabs(t_0 + chi) < std::fabs(t_m1) * tol)
+      return DICH_ERR_NOT_DOMINANT;
+    if (t_0 + psi == 0.0 || t_0 + chi == 0.0) return DICH_ERR_SINGULAR;
+  } else if (N == 1 && t_0 + psi + chi == 0.0) {
+    return DICH_ERR_SINGULAR;
+  }
+  return DICH_OK;
+}
+
 // ================================================================== single-system plan
 struct dich_plan_s {
   int64_t N = 0;
@@ -548,18 +601,10 @@ int dichotomy_plan_quasi(double t_m1, double t_0, double t_1, double psi, double
                          const dich_opts* opts, dich_plan_t* out) {
   if (!out) return DICH_ERR_ARG;
   *out = nullptr;
-  if (!std::isfinite(psi) || !std::isfinite(chi)) return DICH_ERR_ARG;
-  if (N >= 2) {
-    // the end rows of eq. 21 must keep dominance (eq. 32-33; the interior rows are T's)
-    const double tol = 1.0 - 4.0 * DBL_EPSILON;
-    if (std::fabs(t_0 + psi) < std::fabs(t_1) * tol || std::fabs(t_0 + chi) < std::fabs(t_m1) * tol)
-      return DICH_ERR_NOT_DOMINANT;
-    if (t_0 + psi == 0.0 || t_0 + chi == 0.0) return DICH_ERR_SINGULAR;
-  } else if (N == 1 && t_0 + psi + chi == 0.0) {
-    return DICH_ERR_SINGULAR;
-  }
+  int rc = corner_check(t_m1, t_0, t_1, psi, chi, N);
+  if (rc) return rc;
   dich_plan_t p = nullptr;
-  int rc = dichotomy_plan_ex(t_m1, t_0, t_1, N, opts, &p);
+  rc = dichotomy_plan_ex(t_m1, t_0, t_1, N, opts, &p);
   if (rc) return rc;
   p->quasi = (psi != 0.0 || chi != 0.0);
   p->corners = p->quasi;
@@ -571,34 +616,17 @@ int dichotomy_plan_quasi(double t_m1, double t_0, double t_1, double psi, double
     p->quasi = false;
     plan_layout(p);
   } else if (p->quasi && N >= 2) {
-    // g = T^-1 e_0 and h = T^-1 e_{N-1} in closed form (the block spikes of a block of N rows):
-    //   g_i = -(1/q) rs^i Q(N-i)/Q(N+1),   h at row N-1-k = -(1/q) ib^k Q(N-k)/Q(N+1)
-    const Roots r = toeplitz_roots(t_m1, t_0, t_1);
-    const double eps = p->opts.eps;
-    p->Lg = decay_len(std::fabs(r.rs), eps, N);
-    p->Lh = decay_len(std::fabs(r.ib), eps, N);
-    p->corner.resize((size_t)(p->Lg + p->Lh));
-    for (int64_t i = 0; i < p->Lg; ++i) p->corner[(size_t)i] = r.g * ipow(r.rs, i) * spike_ratio(N, i, r);
-    for (int64_t k = 0; k < p->Lh; ++k) p->corner[(size_t)(p->Lg + k)] = r.g * ipow(r.ib, k) * spike_ratio(N, k, r);
-    const double qN1 = qnum(N + 1, r), qN = qnum(N, r);
-    const double g0 = r.g * qN / qN1, gN = r.g * ipow(r.rs, N - 1) / qN1;   // (T^-1)_{0,0}, (T^-1)_{N-1,0}
-    const double h0 = r.g * ipow(r.ib, N - 1) / qN1, hN = r.g * qN / qN1;   // (T^-1)_{0,N-1}, (T^-1)_{N-1,N-1}
-    const double k00 = 1.0 + psi * g0, k01 = psi * h0, k10 = chi * gN, k11 = 1.0 + chi * hN;
-    const double det = k00 * k11 - k01 * k10;
-    if (!std::isfinite(det) || std::fabs(det) <= 64.0 * DBL_EPSILON * (std::fabs(k00 * k11) + std::fabs(k01 * k10))) {
+    Corners c;
+    rc = corner_build(t_m1, t_0, t_1, psi, chi, N, p->opts.eps, c);
+    if (rc) {
       dichotomy_destroy(p);
-      return DICH_ERR_SINGULAR;
+      return rc;
     }
-    p->W[0] = k11 / det;
-    p->W[1] = -k01 / det;
-    p->W[2] = -k10 / det;
-    p->W[3] = k00 / det;
-    // A^T: Toeplitz inverses are persymmetric, so (T^-T e_0)_i = h at row N-1-i and
-    // (T^-T e_{N-1})_i = g at row N-1-i; the 2x2 system has the same determinant
-    p->Wt[0] = k11 / det;
-    p->Wt[1] = -psi * gN / det;
-    p->Wt[2] = -chi * h0 / det;
-    p->Wt[3] = k00 / det;
+    p->Lg = c.Lg;
+    p->Lh = c.Lh;
+    p->corner = std::move(c.gh);
+    std::memcpy(p->W, c.W, sizeof(p->W));
+    std::memcpy(p->Wt, c.Wt, sizeof(p->Wt));
     plan_layout(p);
   }
   *out = p;
@@ -942,6 +970,10 @@ struct dich_batch_s {
   std::vector<unsigned char> staging;
   char* d_ws = nullptr;
   size_t d_ws_bytes = 0;
+  // quasi-Toeplitz systems (eq. 21): their corner records and corner vectors, after the rest
+  std::vector<CornerRec> crec;
+  std::vector<double> ctab;
+  size_t off_crec = 0, off_ctab = 0;
 };
 
 extern "C" {
@@ -1174,6 +1206,55 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
   return DICH_OK;
 }
 
+int dichotomy_batch_prepare_quasi(int64_t nsys, const int64_t* h_N, const int64_t* h_offset, const double* h_tm1,
+                                  const double* h_t0, const double* h_tp1, const double* h_psi, const double* h_chi,
+                                  const dich_opts* opts, dich_batch_t* out) {
+  if (!out) return DICH_ERR_ARG;
+  *out = nullptr;
+  if (nsys < 0 || (nsys > 0 && (!h_N || !h_offset || !h_tm1 || !h_t0 || !h_tp1 || !h_psi || !h_chi)))
+    return DICH_ERR_ARG;
+  // one-row systems read t_0 + psi + chi (and have no off-diagonal entries)
+  std::vector<double> tm1e(h_tm1, h_tm1 + nsys), t0e(h_t0, h_t0 + nsys), tp1e(h_tp1, h_tp1 + nsys);
+  for (int64_t s = 0; s < nsys; ++s) {
+    const int rc = corner_check(h_tm1[s], h_t0[s], h_tp1[s], h_psi[s], h_chi[s], h_N[s]);
+    if (rc) return rc;
+    if (h_N[s] == 1) {
+      t0e[(size_t)s] = h_t0[s] + h_psi[s] + h_chi[s];
+      tm1e[(size_t)s] = tp1e[(size_t)s] = 0.0;
+    }
+  }
+  dich_batch_t b = nullptr;
+  int rc = dichotomy_batch_prepare(nsys, h_N, h_offset, tm1e.data(), t0e.data(), tp1e.data(), opts, &b);
+  if (rc) return rc;
+  for (int64_t s = 0; s < nsys; ++s) {
+    if (h_N[s] < 2 || (h_psi[s] == 0.0 && h_chi[s] == 0.0)) continue;
+    Corners c;
+    rc = corner_build(h_tm1[s], h_t0[s], h_tp1[s], h_psi[s], h_chi[s], h_N[s], b->opts.eps, c);
+    if (rc) {
+      dichotomy_batch_destroy(b);
+      return rc;
+    }
+    const int64_t og = (int64_t)b->ctab.size();
+    b->ctab.insert(b->ctab.end(), c.gh.begin(), c.gh.end());
+    b->crec.push_back(CornerRec{h_N[s], h_offset[s], c.Lg, c.Lh, og, og + c.Lg, h_psi[s], h_chi[s], c.W[0], c.W[1],
+                                c.W[2], c.W[3]});
+  }
+  if (!b->crec.empty()) {
+    // appended after the workspace (and staged whole: the scratch in between is uploaded as zeros)
+    size_t o_ = b->ws_bytes;
+    b->off_crec = o_;
+    o_ += align_up(sizeof(CornerRec) * b->crec.size());
+    b->off_ctab = o_;
+    o_ += align_up(sizeof(double) * std::max<size_t>(1, b->ctab.size()));
+    b->ws_bytes = o_;
+    b->staging.resize(o_, 0);
+    std::memcpy(b->staging.data() + b->off_crec, b->crec.data(), sizeof(CornerRec) * b->crec.size());
+    if (!b->ctab.empty()) std::memcpy(b->staging.data() + b->off_ctab, b->ctab.data(), sizeof(double) * b->ctab.size());
+  }
+  *out = b;
+  return DICH_OK;
+}
+
 int dichotomy_batch_workspace_bytes(dich_batch_t b, size_t* bytes) {
   if (!b || !bytes) return DICH_ERR_ARG;
   *bytes = b->ws_bytes;
@@ -1302,6 +1383,12 @@ static int batch_launch(dich_batch_t b, const double* F, double* x, const double
                               (const int64_t*)(b->d_ws + b->off_gcount[f]), 0, (int64_t)b->gsys[f].size(), gt, st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
+  // quasi-Toeplitz systems: the corner correction on the Toeplitz solutions (all streams joined)
+  if (!adjoint && !b->crec.empty()) {
+    cudaError_t e = launch_corner_batch((const CornerRec*)(b->d_ws + b->off_crec), (int64_t)b->crec.size(),
+                                        (const double*)(b->d_ws + b->off_ctab), x, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   return DICH_OK;
 }
 
@@ -1324,6 +1411,7 @@ int dichotomy_adjoint_batched(dich_batch_t b, const double* d_w, const double* d
   if (!aligned8(d_w) || !aligned8(d_x) || !aligned8(d_gF) || !aligned8(d_gt)) return DICH_ERR_ARG;
   if (!is_device_ptr(d_w) || !is_device_ptr(d_x) || !is_device_ptr(d_gF) || !is_device_ptr(d_gt)) return DICH_ERR_ARG;
   if (d_gF == d_w || d_gF == d_x) return DICH_ERR_ALIAS;
+  if (!b->crec.empty()) return DICH_ERR_UNSUPPORTED;   // quasi-Toeplitz systems: single plans only
   cudaError_t e = cudaMemsetAsync(d_gt, 0, sizeof(double) * 3 * (size_t)b->nsys, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e);
   return batch_launch(b, d_w, d_gF, d_x, d_gt, true, (cudaStream_t)stream);

@@ -413,6 +413,37 @@ __global__ void __launch_bounds__(256) k_corner_adj(const double* xf, const doub
   }
 }
 
+// Batched corner correction: every thread reads both end values of its system before any row
+// is corrected (one barrier), then rows [0, Lg) and [N - Lh, N) are corrected once each, with the
+// single-system kernel's order of operations.
+__global__ void __launch_bounds__(256) k_corner_batch(const CornerRec* recs, const double* tab, double* x) {
+  const CornerRec c = recs[blockIdx.x];
+  double* xr = x + c.off;
+  const int64_t N = c.N;
+  const double y0 = xr[0], yn = xr[N - 1];
+  __syncthreads();
+  const double a = c.psi * y0, b = c.chi * yn;
+  const double c0 = fma(c.w00, a, c.w01 * b), c1 = fma(c.w10, a, c.w11 * b);
+  const double* g = tab + c.og;
+  const double* h = tab + c.oh;
+  auto corr = [&](int64_t i) {
+    double v = xr[i];
+    if (i < c.Lg) v = fma(-c0, g[i], v);
+    const int64_t k = N - 1 - i;
+    if (k < c.Lh) v = fma(-c1, h[k], v);
+    xr[i] = v;
+  };
+  const int64_t hi1 = min(c.Lg, N), lo2 = max(N - c.Lh, hi1);
+  for (int64_t i = threadIdx.x; i < hi1; i += 256) corr(i);
+  for (int64_t i = lo2 + threadIdx.x; i < N; i += 256) corr(i);
+}
+
+cudaError_t launch_corner_batch(const CornerRec* recs, int64_t n, const double* tab, double* x, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_corner_batch<<<(unsigned)n, 256, 0, st>>>(recs, tab, x);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_corner_adjoint(const double* xf, double* lam, double* gt, const CornerArgs& c, cudaStream_t st) {
   if (c.N <= 0) return cudaSuccess;
   k_corner_adj<<<1, 256, 0, st>>>(xf, lam, c, gt);

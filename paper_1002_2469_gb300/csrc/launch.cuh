@@ -57,6 +57,15 @@ struct CornerArgs {
 
 // x_k <- A^-1 F_k from y_k = T^-1 F_k (already in x_k = x + k ldx), k = 0..M-1: two kernels
 cudaError_t launch_corner(double* x, int64_t M, int64_t ldx, const CornerArgs& c, cudaStream_t st);
+// one quasi-Toeplitz system of a batch: rows [off, off + N), corner vectors at tab + og (Lg
+// entries) and tab + oh (Lh entries), corners psi, chi, (I + K)^-1 = [[w00, w01], [w10, w11]]
+struct CornerRec {
+  int64_t N, off, Lg, Lh, og, oh;
+  double psi, chi, w00, w01, w10, w11;
+};
+// x <- A_s^-1 F_s from y_s = T_s^-1 F_s (already in x) for every listed system: one CTA each
+cudaError_t launch_corner_batch(const CornerRec* recs, int64_t n, const double* tab, double* x, cudaStream_t st);
+
 // adjoint of a quasi-Toeplitz plan: gradient terms of the corner correction, dL/dpsi, dL/dchi
 // (gt[0..4]), then the corner correction of lambda (c: the transposed corner vectors)
 cudaError_t launch_corner_adjoint(const double* xf, double* lam, double* gt, const CornerArgs& c, cudaStream_t st);

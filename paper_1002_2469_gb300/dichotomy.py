@@ -153,7 +153,8 @@ def _host_f64(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
 
 
-def dichotomy_batch_prepare(N, offset, t_m1, t_0, t_1, opts=None) -> ctypes.c_void_p:
+def dichotomy_batch_prepare(N, offset, t_m1, t_0, t_1, opts=None, psi=None, chi=None) -> ctypes.c_void_p:
+    """Prepare a batch; with psi / chi arrays, a batch of quasi-Toeplitz systems (eq. 21)."""
     N, offset = _host_i64(N), _host_i64(offset)
     tm1, t0, tp1 = _host_f64(t_m1), _host_f64(t_0), _host_f64(t_1)
     nsys = N.size
@@ -161,9 +162,18 @@ def dichotomy_batch_prepare(N, offset, t_m1, t_0, t_1, opts=None) -> ctypes.c_vo
         raise ValueError("batch arrays must have one entry per system")
     h = ctypes.c_void_p()
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
-    check(_lib.load().dichotomy_batch_prepare(nsys, p(N), p(offset), p(tm1), p(t0), p(tp1),
-                                              ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)),
-          "dichotomy_batch_prepare")
+    o = ctypes.byref(opts) if opts is not None else None
+    if psi is None and chi is None:
+        check(_lib.load().dichotomy_batch_prepare(nsys, p(N), p(offset), p(tm1), p(t0), p(tp1), o, ctypes.byref(h)),
+              "dichotomy_batch_prepare")
+        return h
+    import numpy as np
+    ps = _host_f64(psi if psi is not None else np.zeros(nsys))
+    ch = _host_f64(chi if chi is not None else np.zeros(nsys))
+    if not (ps.size == ch.size == nsys):
+        raise ValueError("psi and chi must have one entry per system")
+    check(_lib.load().dichotomy_batch_prepare_quasi(nsys, p(N), p(offset), p(tm1), p(t0), p(tp1), p(ps), p(ch), o,
+                                                    ctypes.byref(h)), "dichotomy_batch_prepare_quasi")
     return h
 
 
@@ -294,10 +304,11 @@ class Plan:
 
 
 class Batch:
-    """A bound batch of independent Toeplitz systems stored back to back in one vector."""
+    """A bound batch of independent Toeplitz systems stored back to back in one vector (with psi,
+    chi arrays: quasi-Toeplitz systems, eq. 21)."""
 
     def __init__(self, N, t_m1, t_0, t_1, offset=None, block_size=0, precision=PREC_F64, threads=0, flags=0,
-                 trunc_eps=0.0, device=None, stream=None):
+                 trunc_eps=0.0, device=None, stream=None, psi=None, chi=None):
         import numpy as np
         N = _host_i64(N)
         if offset is None:
@@ -307,7 +318,7 @@ class Batch:
         self.total = int((self.offset + N).max()) if N.size else 0
         self._h = None
         opts = make_opts(block_size, precision, threads, flags, trunc_eps)
-        self._h = dichotomy_batch_prepare(N, self.offset, t_m1, t_0, t_1, opts)
+        self._h = dichotomy_batch_prepare(N, self.offset, t_m1, t_0, t_1, opts, psi=psi, chi=chi)
         self.info = dichotomy_batch_info(self._h)
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.workspace = torch.empty(max(1, dichotomy_batch_workspace_bytes(self._h)), dtype=torch.uint8, device=dev)

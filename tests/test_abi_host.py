@@ -264,3 +264,30 @@ def test_batch_with_long_coupling_prepares_without_a_gpu():
         assert D.dichotomy_batch_workspace_bytes(h) > 32 * (1 << 20) // 16   # beta and first/last values
     finally:
         D.dichotomy_batch_destroy(h)
+
+
+def test_quasi_batch_validation_without_a_gpu():
+    from paper_1002_2469_gb300 import dichotomy as D
+    N = np.array([1000, 1, 50], dtype=np.int64)
+    tm1, t0, tp1 = np.array([-1.0, -1.0, -1.2]), np.array([2.5, 4.0, 2.5]), np.array([-1.0, -1.0, -0.8])
+    o = D.make_opts(precision=2)
+    h = D.dichotomy_batch_prepare(N, np.array([0, 1000, 1001]), tm1, t0, tp1, o,
+                                  psi=np.array([-1.0, 0.5, 0.0]), chi=np.array([-1.0, 0.25, 0.7]))
+    try:
+        plain = D.dichotomy_batch_prepare(N, np.array([0, 1000, 1001]), tm1, t0, tp1, o)
+        assert D.dichotomy_batch_workspace_bytes(h) > D.dichotomy_batch_workspace_bytes(plain)   # corner data
+        D.dichotomy_batch_destroy(plain)
+    finally:
+        D.dichotomy_batch_destroy(h)
+    with pytest.raises(D.DichotomyError) as e:      # first row of system 0 loses dominance
+        D.dichotomy_batch_prepare(N, np.array([0, 1000, 1001]), tm1, t0, tp1, o, psi=np.array([-2.0, 0, 0]),
+                                  chi=np.zeros(3))
+    assert e.value.code == 2
+    with pytest.raises(D.DichotomyError) as e:      # one row with t_0 + psi + chi = 0
+        D.dichotomy_batch_prepare(N, np.array([0, 1000, 1001]), tm1, t0, tp1, o, psi=np.array([0, -3.0, 0]),
+                                  chi=np.array([0, -1.0, 0]))
+    assert e.value.code == 3
+    with pytest.raises(D.DichotomyError) as e:
+        D.dichotomy_batch_prepare(N, np.array([0, 1000, 1001]), tm1, t0, tp1, o, psi=np.array([np.nan, 0, 0]),
+                                  chi=np.zeros(3))
+    assert e.value.code == 1

@@ -259,6 +259,34 @@ def test_quasi_one_row(D):
     assert x[0] == 3.0 / 4.75
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_quasi_toeplitz_batch(D, prec):
+    """Batches of quasi-Toeplitz systems (eq. 21) beside plain ones: every system against the
+    oracle's Thomas on its own matrix; long-coupling systems (general path), one-row systems and
+    systems without corners included."""
+    rng = np.random.default_rng(40 + prec)
+    nsys = 60
+    N = np.where(rng.uniform(size=nsys) < 0.1, rng.integers(1, 4, nsys), (10 ** rng.uniform(0.5, 5.3, nsys)).astype(np.int64))
+    tm1, tp1 = -rng.uniform(0.5, 1.0, nsys), -rng.uniform(0.5, 1.0, nsys)
+    t0 = (np.abs(tm1) + np.abs(tp1)) * (1 + 10 ** rng.uniform(-3.5, 0.3, nsys))
+    psi = np.where(rng.uniform(size=nsys) < 0.7, (np.abs(tp1) * 1.01 - t0) * rng.uniform(0, 0.9, nsys), 0.0)
+    chi = np.where(rng.uniform(size=nsys) < 0.7, (np.abs(tm1) * 1.01 - t0) * rng.uniform(0, 0.9, nsys), 0.0)
+    F = rng.standard_normal(int(N.sum()))
+    b = D.Batch(N, tm1, t0, tp1, precision=prec, psi=psi, chi=chi)
+    x = b.solve(torch.from_numpy(F).cuda()).cpu().numpy()
+    assert b.status() == 0
+    off = np.concatenate([[0], np.cumsum(N)[:-1]])
+    for s_ in range(nsys):
+        o, n = int(off[s_]), int(N[s_])
+        t = (tm1[s_], t0[s_], tp1[s_])
+        ref = oracle.thomas_quasi(t, psi[s_], chi[s_], F[o:o + n])
+        assert rel(x[o:o + n], ref) < TOL, (s_, n, t, psi[s_], chi[s_])
+    w = torch.zeros_like(torch.from_numpy(F).cuda())
+    with pytest.raises(D.DichotomyError) as err:
+        b.adjoint(w, w)
+    assert err.value.code == 11
+
+
 @pytest.mark.parametrize("prec,flags", [(0, 0), (1, 0), (2, 0), (0, 1), (1, 1)])
 @pytest.mark.parametrize("t,psi,chi", QUASI)
 @pytest.mark.parametrize("N", [1, 2, 3, 50, 4097, 300001])
