@@ -549,6 +549,24 @@ def other_configs(D, W, oracle, stream, world, steps=10):
     del fd, rhs, v, solver
     torch.cuda.empty_cache()
 
+    # f2 + f3: the same driver with Neumann conditions in y (4096 cell centres): every mode is a
+    # quasi-Toeplitz system of eq. 21 (psi = chi = -1), solved in one batch with the corner step
+    My = 4096
+    us = np.random.default_rng(0).uniform(-1.0, 1.0, (M, My))
+    fd = torch.from_numpy(OP.laplacian5_neumann_y(us)).cuda()
+    solver = PS.Poisson2D(M, My=My, bc_y="neumann")
+    ms_total = _time_batch(lambda: solver.solve(fd), steps, world, stream)
+    rhs = torch.empty(M * My, dtype=torch.float64, device="cuda")
+    v = torch.empty_like(rhs)
+    ms_solve = _time_batch(lambda: solver.batch.solve(rhs, out=v), steps, world, stream)
+    u = solver.solve(fd).cpu().numpy()
+    out["f3_poisson2d_neumann_y_4095x4096"] = {
+        "unknowns": M * My, "ms_total": round(ms_total, 4), "ms_dichotomy": round(ms_solve, 4),
+        "Gunknowns_s": round(M * My / ms_total / 1e6, 2), "form": "AUTO per mode, quasi-Toeplitz corners",
+        "rel_err_vs_manufactured": float(np.max(np.abs(u - us)) / np.max(np.abs(us)))}
+    del fd, rhs, v, solver
+    torch.cuda.empty_cache()
+
     # f4: a general tridiagonal matrix, N = 2^24: |a_i|, |c_i| <= 1 random, b_i = +-(|a_i| + |c_i| + U[0.3, 1.5]),
     # F ~ N(0, 1); the O(N) preliminary step (plan and bind: on the device by default, plan_s; on
     # the host, plan_s_host_prelim), then FP64 solves on the device

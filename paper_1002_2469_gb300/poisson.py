@@ -11,6 +11,12 @@ the series of Sec. 3.2 with one t_0 per mode.  All M systems are solved as one b
 Dichotomy kernels (the library's batched entry point); the inverse DST-I (the same transform)
 returns u.  The transforms use torch's FFT (cuFFT): DST-I of length M through a real FFT of
 length 2 (M + 1).
+
+Neumann conditions in y (bc_y="neumann"): My cell-centred unknowns y_j = (j + 1/2) / My with
+du/dy = 0 at y = 0 and y = 1 (ghost cells equal to their neighbours).  Mode k then leaves the
+quasi-Toeplitz system of eq. 21 (Sec. 3.1), tridiag{-1, t_0(k), -1} with
+t_0(k) = 2 + (hy / hx)^2 4 sin^2(k pi / (2 (M + 1))) and psi = chi = -1 in its first and last
+rows, right-hand side hy^2 fhat_k; the batch's corner step handles the two rows.
 """
 from __future__ import annotations
 
@@ -42,22 +48,34 @@ def mode_t0(M: int) -> np.ndarray:
 
 
 class Poisson2D:
-    """Solver for an [M, M] interior grid; the batch of M mode systems is planned once."""
+    """Solver for an [M, My] grid (My = M by default): Dirichlet in x; Dirichlet (My interior
+    nodes, hy = 1 / (My + 1)) or Neumann (My cell centres, hy = 1 / My) in y.  The batch of M
+    mode systems is planned once."""
 
-    def __init__(self, M: int, precision: int = _d.PREC_AUTO, device=None):
+    def __init__(self, M: int, precision: int = _d.PREC_AUTO, device=None, My: int | None = None,
+                 bc_y: str = "dirichlet"):
         self.M = int(M)
-        self.h = 1.0 / (self.M + 1)
-        t0 = mode_t0(self.M)
+        self.My = int(My) if My is not None else self.M
+        if bc_y not in ("dirichlet", "neumann"):
+            raise ValueError("bc_y must be 'dirichlet' or 'neumann'")
+        self.bc_y = bc_y
+        self.hx = 1.0 / (self.M + 1)
+        self.hy = 1.0 / (self.My + 1) if bc_y == "dirichlet" else 1.0 / self.My
+        self.h = self.hy
+        k = np.arange(1, self.M + 1, dtype=np.float64)
+        t0 = 2.0 + (self.hy / self.hx) ** 2 * 4.0 * np.sin(k * math.pi / (2.0 * (self.M + 1))) ** 2
         ones = np.ones(self.M)
-        self.batch = _d.Batch(np.full(self.M, self.M, dtype=np.int64), -ones, t0, -ones, precision=precision)
+        corners = dict(psi=-ones, chi=-ones) if bc_y == "neumann" else {}
+        self.batch = _d.Batch(np.full(self.M, self.My, dtype=np.int64), -ones, t0, -ones, precision=precision,
+                              **corners)
         self.device = device
 
     def solve(self, f: torch.Tensor) -> torch.Tensor:
-        """u for the right-hand side f ([M, M], float64, CUDA)."""
-        if f.shape != (self.M, self.M):
-            raise ValueError(f"f must be [{self.M}, {self.M}]")
-        rhs = (self.h * self.h) * dst1(f, dim=0)                  # [k, j]: mode k along y
-        v = self.batch.solve(rhs.reshape(-1)).reshape(self.M, self.M)
+        """u for the right-hand side f ([M, My], float64, CUDA)."""
+        if f.shape != (self.M, self.My):
+            raise ValueError(f"f must be [{self.M}, {self.My}]")
+        rhs = (self.hy * self.hy) * dst1(f, dim=0)                # [k, j]: mode k along y
+        v = self.batch.solve(rhs.reshape(-1)).reshape(self.M, self.My)
         return dst1(v, dim=0)
 
     def status(self) -> int:

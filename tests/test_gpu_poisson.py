@@ -64,3 +64,23 @@ def test_poisson2d_manufactured(P):
     f = OP.laplacian5(us)
     u = P.Poisson2D(M).solve(torch.from_numpy(f).cuda()).cpu().numpy()
     assert rel(u, us) < 1e-9        # kappa ~ 0.4 (M + 1)^2 = 4e5 times the FP64 unit roundoff
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("M,My", [(1, 2), (31, 17), (255, 300)])
+def test_poisson2d_neumann_y_matches_oracle_pipeline(P, M, My, prec):
+    """Neumann in y: every mode a quasi-Toeplitz system (eq. 21) in one batch."""
+    f = np.random.default_rng(M + My).standard_normal((M, My))
+    solver = P.Poisson2D(M, precision=prec, My=My, bc_y="neumann")
+    u = solver.solve(torch.from_numpy(f).cuda()).cpu().numpy()
+    assert solver.status() == 0
+    assert rel(u, OP.poisson2d_neumann_y(f)) < max(1e-13, 4e-16 * 0.4 * max(M + 1, My) ** 2 * 10)
+    assert rel(OP.laplacian5_neumann_y(u), f) < 1e-9
+
+
+def test_poisson2d_neumann_y_manufactured(P):
+    M, My = 511, 400
+    us = np.random.default_rng(2).uniform(-1, 1, (M, My))
+    f = OP.laplacian5_neumann_y(us)
+    u = P.Poisson2D(M, My=My, bc_y="neumann").solve(torch.from_numpy(f).cuda()).cpu().numpy()
+    assert rel(u, us) < 1e-10

@@ -389,6 +389,38 @@ def test_poisson2d_oracle_vs_dense_kronecker():
     assert rel(OP.laplacian5(u), f) < 1e-12
 
 
+def test_poisson2d_neumann_y_vs_dense_kronecker():
+    """Dirichlet in x, Neumann in y (cell-centred): the separation-of-variables oracle (modes solved
+    as quasi-Toeplitz systems, eq. 21) against a dense solve of the Kronecker sum of the two 1-D
+    operators, the y one assembled with its Neumann end rows [1, -1] / hy^2."""
+    from oracle import poisson as OP
+    M, My = 11, 7
+    hx, hy = 1.0 / (M + 1), 1.0 / My
+    Tx = (np.diag(np.full(M, 2.0)) - np.diag(np.ones(M - 1), 1) - np.diag(np.ones(M - 1), -1)) / (hx * hx)
+    Ty = np.diag(np.full(My, 2.0)) - np.diag(np.ones(My - 1), 1) - np.diag(np.ones(My - 1), -1)
+    Ty[0, 0] = Ty[-1, -1] = 1.0
+    Ty /= hy * hy
+    L = np.kron(Tx, np.eye(My)) + np.kron(np.eye(M), Ty)        # row-major [i, j] -> i * My + j
+    f = np.random.default_rng(5).standard_normal((M, My))
+    u = np.linalg.solve(L, f.reshape(-1)).reshape(M, My)
+    assert rel(OP.poisson2d_neumann_y(f), u) < 1e-13
+    assert rel(OP.laplacian5_neumann_y(u), f) < 1e-12
+
+
+def test_poisson2d_neumann_y_second_order():
+    """u = sin(pi x) cos(pi y) solves -Laplace u = 2 pi^2 u with u = 0 at x = 0, 1 and du/dy = 0 at
+    y = 0, 1: the discrete solution converges to it at second order."""
+    from oracle import poisson as OP
+    errs = []
+    for M in (15, 31, 63):
+        My = M + 1
+        x = np.arange(1, M + 1) / (M + 1)
+        y = (np.arange(My) + 0.5) / My
+        us = np.outer(np.sin(math.pi * x), np.cos(math.pi * y))
+        errs.append(np.max(np.abs(OP.poisson2d_neumann_y(2 * math.pi ** 2 * us) - us)))
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
+
+
 @pytest.mark.parametrize("p,q", [(1, 1), (3, 5), (20, 2)])
 def test_poisson2d_single_mode(p, q):
     """f = sin(p pi x) sin(q pi y) excites one mode: u = f / lambda_pq, lambda_pq =
