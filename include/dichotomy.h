@@ -260,20 +260,23 @@ const char* dichotomy_version(void);
  * factors and spikes, and the block maps of the dichotomy tree.  It runs on the device at bind
  * time (from 2^15 rows, or with DICH_FLAG_DEVICE_PRELIM: the elimination factors as prefix and
  * suffix products of 2x2 matrices over the blocks) or on the host at plan time (below 2^15 rows,
- * or with DICH_FLAG_HOST_PRELIM).  Every solve of a series (eq. 2) reuses it.  FP64 only.  The
+ * or with DICH_FLAG_HOST_PRELIM).  Every solve of a series (eq. 2) reuses it.  FP64 or
+ * float-float (see dichotomy_gen_plan).  The
  * plan keeps 5 doubles per row in the device workspace (40 bytes per row, plus 80 bytes per
  * block); the device preliminary adds 24 bytes per row (the matrix) and 64 per block. */
 
 /* Plan for the N x N matrix given by the host arrays h_a (sub-diagonal), h_b (diagonal), h_c
  * (super-diagonal), N entries each (copied; the caller keeps ownership).  opts as for
- * dichotomy_plan_ex (precision DICH_PREC_MIXED: DICH_ERR_UNSUPPORTED).  Every row must satisfy
+ * dichotomy_plan_ex; DICH_PREC_MIXED runs the local solves and the correction in float-float
+ * (factors within 2^-40..2^40, else DICH_ERR_UNSUPPORTED -- from dichotomy_gen_bind with the
+ * device preliminary); DICH_PREC_AUTO takes FP64, the faster form of this kernel on GB300.  Every row must satisfy
  * |b_i| >= |a_i| + |c_i| (eq. 32-33).  Errors: DICH_ERR_ARG (null, negative N, non-finite entry,
  * bad opts), DICH_ERR_NOT_DOMINANT, DICH_ERR_SINGULAR (a zero pivot; with the device preliminary
  * reported by dichotomy_gen_bind), DICH_ERR_UNSUPPORTED. */
 int dichotomy_gen_plan(int64_t N, const double* h_a, const double* h_b, const double* h_c, const dich_opts* opts,
                        dich_gen_t* out);
 /* Geometry of a general plan (the Toeplitz-only fields are zero).  With the device preliminary,
- * path, halo_l, halo_r and tiles are provisional (general path) until dichotomy_gen_bind has
+ * path, halo_l, halo_r, tiles and precision are provisional (general path) until dichotomy_gen_bind has
  * returned.  Errors: DICH_ERR_ARG. */
 int dichotomy_gen_info(dich_gen_t plan, dich_plan_info* info);
 /* Bytes of device workspace (256-byte aligned region). */

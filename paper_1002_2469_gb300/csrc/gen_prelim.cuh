@@ -50,8 +50,12 @@ struct PreArgs {
   Mat2* fwd;            // per block: forward composite (rows s..e)
   Mat2* bwd;            // per block: backward composite (rows e..s)
   Mat2* chunk;          // 2 per chunk: forward, backward chunk products, then the incoming products
-  unsigned long long* maxes;   // [3]: bits of max |a_m| (m < P-1), max |c_m| (m > 0); a failure flag
+  unsigned long long* maxes;   // [8]: bits of max |a_m| (m < P-1), max |c_m| (m > 0); a failure flag;
+                               // then for the precision choice: the largest forward and backward error
+                               // gains, max |rd_i|, ~bits of min |rd_i|, max |a_i|, |cp_i|, |v_i|, |w_i|
 };
+
+__device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(fabs(v)); }
 
 // 1. per block: local factors, spikes, composites
 __global__ void __launch_bounds__(kPreThreads) k_pre_blocks(const PreArgs A) {
@@ -66,6 +70,9 @@ __global__ void __launch_bounds__(kPreThreads) k_pre_blocks(const PreArgs A) {
   double* fw = A.rows + GF_W * A.stride;
   // local Thomas factors; z of the spike v = T_m^-1 (-a_s e_0) in the V field for now
   double lcp = 0.0, z = 0.0;
+  // for the precision choice: the error gains of the two local recurrences (gf_i = 1 + |a_i rd_i|
+  // gf_{i-1}, gb_i = 1 + |cp_i| gb_{i+1}), the range of rd and the largest other factor
+  double fm = 0.0, bm = 0.0, rmax = 0.0, rmin = INFINITY, omax = 0.0, gf = 1.0;
   Mat2 F{1.0, 0.0, 0.0, 1.0};
   for (int i = 0; i < nb; ++i) {
     const int64_t r = s + i;
@@ -81,12 +88,20 @@ __global__ void __launch_bounds__(kPreThreads) k_pre_blocks(const PreArgs A) {
     z = (i == 0) ? -ar * rd : -ar * z * rd;
     fv[k] = z;
     F = mat_norm(mat_mul(Mat2{0.0, cr, -ar, br}, F));
+    gf = (i > 0) ? fma(fabs(ar * rd), gf, 1.0) : 1.0;
+    fm = fmax(fm, gf);
+    rmax = fmax(rmax, fabs(rd));
+    rmin = fmin(rmin, fabs(rd));
+    omax = fmax(omax, fmax(fabs(fa[k]), fabs(lcp)));
   }
   // backward: v_i = z_i - lcp_i v_{i+1}; w_i = -lcp_i w_{i+1} from w_e = -c_e rd_e
   const double ce = (e < N - 1) ? A.c[e] : 0.0;
   double v = fv[gen_index(m, nb - 1, n)];
   double w = -ce * frd[gen_index(m, nb - 1, n)];
   fw[gen_index(m, nb - 1, n)] = w;
+  omax = fmax(omax, fmax(fabs(v), fabs(w)));
+  double gb = 1.0;
+  bm = 1.0;
   Mat2 B{1.0, 0.0, 0.0, 1.0};
   {
     const int64_t r = e;
@@ -99,12 +114,30 @@ __global__ void __launch_bounds__(kPreThreads) k_pre_blocks(const PreArgs A) {
     fv[k] = v;
     w = -fcp[k] * w;
     fw[k] = w;
+    omax = fmax(omax, fmax(fabs(v), fabs(w)));
+    gb = fma(fabs(fcp[k]), gb, 1.0);
+    bm = fmax(bm, gb);
     const int64_t r = s + i;
     const double ar = (r > 0) ? A.a[r] : 0.0, br = A.b[r], cr = (r < N - 1) ? A.c[r] : 0.0;
     B = mat_norm(mat_mul(Mat2{0.0, ar, -cr, br}, B));
   }
   A.fwd[m] = F;
   A.bwd[m] = B;
+  atomicMax(&A.maxes[3], dbits(fm));
+  atomicMax(&A.maxes[4], dbits(bm));
+  atomicMax(&A.maxes[5], dbits(rmax));
+  atomicMax(&A.maxes[6], ~dbits(rmin));
+  atomicMax(&A.maxes[7], dbits(omax));
+}
+
+// the per-row tables as float-float pairs (hi, lo) in their own 8-byte slots (MIXED form)
+__global__ void k_pre_to_ff(double* rows, int64_t count) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count; j += (int64_t)gridDim.x * blockDim.x) {
+    const double d = rows[j];
+    const float h = __double2float_rn(d);
+    const float l = __double2float_rn(d - (double)h);
+    reinterpret_cast<float2*>(rows)[j] = make_float2(h, l);
+  }
 }
 
 // CTA-wide inclusive scan of 2x2 matrices: forward (later blocks multiply on the left) or

@@ -42,7 +42,26 @@ static cudaError_t launch_gen_one(int grid, int grid_y, size_t smem, cudaStream_
   return cudaGetLastError();
 }
 
-static cudaError_t launch_window_gen(int NT, int grid, size_t smem, cudaStream_t st, const GenArgs& a, int grid_y) {
+template <int NT>
+static cudaError_t launch_gen_ff_one(int grid, int grid_y, size_t smem, cudaStream_t st, const GenArgs& a) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_window_gen_ff<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_window_gen_ff<NT><<<dim3(grid, grid_y), NT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_window_gen(int NT, int grid, size_t smem, cudaStream_t st, const GenArgs& a, int grid_y,
+                                     int form) {
+  if (form == FORM_MIXED) {
+    switch (NT) {
+      case 64: return launch_gen_ff_one<64>(grid, grid_y, smem, st, a);
+      case 128: return launch_gen_ff_one<128>(grid, grid_y, smem, st, a);
+      case 256: return launch_gen_ff_one<256>(grid, grid_y, smem, st, a);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (NT) {
     case 64: return launch_gen_one<64>(grid, grid_y, smem, st, a);
     case 128: return launch_gen_one<128>(grid, grid_y, smem, st, a);
@@ -58,6 +77,7 @@ struct dich_gen_s {
   Opts opts;
   int NT = 64;
   int path = PATH_SINGLE;
+  int form = FORM_F64;                // FP64 or MIXED (float-float rows)
   int64_t tiles = 0;
   int64_t stride = 0;                 // doubles per per-row field
   SysPlan rec{};                      // geometry record read by the kernels
@@ -131,6 +151,24 @@ void gen_decide(dich_gen_s* g, double amax, double cmax) {
     r.own = NT;
   }
   g->tiles = ceil_div(P, (int64_t)r.own);
+}
+
+// precision form.  MIXED (asked for explicitly) needs the factors within 2^-40..2^40 for its float
+// range; its error grows with the error gains of the two recurrences, gf (largest
+// 1 + |a_i rd_i| gf_{i-1} over the rows of a block) and gb (largest 1 + |cp_i| gb_{i+1}), which for
+// a Toeplitz matrix are 1/(1 - |rs|) and 1/(1 - |ib|).  AUTO takes FP64: with one block per thread
+// and FP64 beta and tree, the float-float form of this kernel runs slower than the FP64 one.
+int gen_choose_form(dich_gen_s* g, double gf, double gb, double rmax, double rmin, double omax) {
+  const double big = 1099511627776.0;   // 2^40
+  const bool range = rmax <= big && rmin >= 1.0 / big && omax <= big;
+  (void)gf;
+  (void)gb;
+  g->form = FORM_F64;
+  if (g->opts.prec == DICH_PREC_MIXED) {
+    if (!range) return DICH_ERR_UNSUPPORTED;
+    g->form = FORM_MIXED;
+  }
+  return DICH_OK;
 }
 
 // the O(N) preliminary step on the host; returns a status code
@@ -233,6 +271,36 @@ int gen_host_tables(dich_gen_s* g, const double* a, const double* b, const doubl
   }
 
   gen_decide(g, amax, cmax);
+  // precision form from the tables, then (MIXED) the tables as float-float pairs in place
+  double fm = 1.0, bm = 1.0, rmax = 0.0, rmin = INFINITY, omax = 0.0;
+  for (int64_t m = 0; m < P; ++m) {   // error gains of the two recurrences, block by block
+    const int nb = (m == P - 1) ? r.nlast : n;
+    double gfi = 1.0, gbi = 1.0;
+    for (int i = 1; i < nb; ++i) {
+      const int64_t k = gen_index(m, i, n);
+      gfi = 1.0 + std::fabs(fa[k] * frd[k]) * gfi;
+      fm = std::max(fm, gfi);
+    }
+    for (int i = nb - 2; i >= 0; --i) {
+      gbi = 1.0 + std::fabs(fcp[gen_index(m, i, n)]) * gbi;
+      bm = std::max(bm, gbi);
+    }
+  }
+  for (int64_t k = 0; k < g->stride; ++k) {
+    if (frd[k] != 0.0) {
+      rmax = std::max(rmax, std::fabs(frd[k]));
+      rmin = std::min(rmin, std::fabs(frd[k]));
+    }
+    omax = std::max({omax, std::fabs(fa[k]), std::fabs(fcp[k]), std::fabs(fv[k]), std::fabs(fw[k])});
+  }
+  const int rc = gen_choose_form(g, fm, bm, rmax, rmin, omax);
+  if (rc) return rc;
+  if (g->form == FORM_MIXED) {
+    for (double& d : g->rows) {
+      const float hl2[2] = {(float)d, (float)(d - (double)(float)d)};
+      std::memcpy(&d, hl2, sizeof(double));
+    }
+  }
   return DICH_OK;
 }
 
@@ -296,14 +364,14 @@ int gen_device_tables(dich_gen_s* g, char* base, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(raw + N, g->hb.data(), nb, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(raw + 2 * N, g->hc.data(), nb, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(A.rows, 0, sizeof(double) * (size_t)(kGenFields * g->stride), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(A.maxes, 0, 3 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A.maxes, 0, 8 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return cuda_fail(e);
   k_pre_blocks<<<(unsigned)nch, kPreThreads, 0, st>>>(A);
   k_pre_chunk<<<(unsigned)nch, kPreThreads, 0, st>>>(A);
   k_pre_top<<<1, 32, 0, st>>>(A, nch);
   k_pre_records<<<(unsigned)nch, kPreThreads, 0, st>>>(A);
   e = cudaGetLastError();
-  unsigned long long mx[3] = {0, 0, 0};
+  unsigned long long mx[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(mx, A.maxes, sizeof(mx), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -312,6 +380,17 @@ int gen_device_tables(dich_gen_s* g, char* base, cudaStream_t st) {
   std::memcpy(&amax, &mx[0], sizeof(double));
   std::memcpy(&cmax, &mx[1], sizeof(double));
   gen_decide(g, amax, cmax);
+  double q[5];   // forward and backward error gains, max |rd|, min |rd|, max of the other factors
+  mx[6] = ~mx[6];
+  for (int j = 0; j < 5; ++j) std::memcpy(&q[j], &mx[3 + j], sizeof(double));
+  const int rc = gen_choose_form(g, q[0], q[1], q[2], q[3], q[4]);
+  if (rc) return rc;
+  if (g->form == FORM_MIXED) {
+    k_pre_to_ff<<<(unsigned)std::min<int64_t>(ceil_div(kGenFields * g->stride, (int64_t)256), (int64_t)4096), 256, 0,
+                  st>>>(A.rows, kGenFields * g->stride);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   return DICH_OK;
 }
 
@@ -344,7 +423,7 @@ int gen_launch(dich_gen_s* g, const double* F, double* x, cudaStream_t st, int64
       GenArgs w = ga;
       w.w.F = F + k0 * ldf;
       w.w.x = x + k0 * ldx;
-      e = launch_window_gen(g->NT, (int)g->tiles, smem, st, w, (int)std::min<int64_t>(65535, M - k0));
+      e = launch_window_gen(g->NT, (int)g->tiles, smem, st, w, (int)std::min<int64_t>(65535, M - k0), g->form);
       if (e != cudaSuccess) return cuda_fail(e);
     }
     return DICH_OK;
@@ -358,13 +437,13 @@ int gen_launch(dich_gen_s* g, const double* F, double* x, cudaStream_t st, int64
     w.w.x = x + k * ldx;
     w.w.mode = MODE_BETA;
     w.w.beta = beta;
-    e = launch_window_gen(g->NT, (int)g->tiles, smem, st, w, 1);
+    e = launch_window_gen(g->NT, (int)g->tiles, smem, st, w, 1, g->form);
     if (e != cudaSuccess) return cuda_fail(e);
     e = launch_block_scan(d_plan, d_recs, g->rec.P, beta, iface, scan, st);
     if (e != cudaSuccess) return cuda_fail(e);
     w.w.mode = MODE_APPLY;
     w.w.iface = iface;
-    e = launch_window_gen(g->NT, (int)g->tiles, smem, st, w, 1);
+    e = launch_window_gen(g->NT, (int)g->tiles, smem, st, w, 1, g->form);
     if (e != cudaSuccess) return cuda_fail(e);
   }
   return DICH_OK;
@@ -382,7 +461,6 @@ int dichotomy_gen_plan(int64_t N, const double* h_a, const double* h_b, const do
   Opts o;
   int rc = read_opts(opts, o);
   if (rc) return rc;
-  if (o.prec == DICH_PREC_MIXED) return DICH_ERR_UNSUPPORTED;
   // eq. 32-33 row by row (a_0 and c_{N-1} lie outside the matrix)
   for (int64_t i = 0; i < N; ++i) {
     const double ai = (i > 0) ? h_a[i] : 0.0, ci = (i < N - 1) ? h_c[i] : 0.0;
@@ -435,7 +513,7 @@ int dichotomy_gen_info(dich_gen_t g, dich_plan_info* info) {
   info->halo_l = g->rec.hl;
   info->halo_r = g->rec.hr;
   info->path = g->path;
-  info->precision = DICH_PREC_F64;
+  info->precision = (g->form == FORM_MIXED) ? DICH_PREC_MIXED : DICH_PREC_F64;
   info->tiles = g->tiles;
   info->workspace_bytes = g->ws_bytes;
   if (g->path == PATH_GENERAL) {

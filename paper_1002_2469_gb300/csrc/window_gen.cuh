@@ -15,6 +15,7 @@
 // General path: the beta pass (MODE_BETA) leaves the local solutions y in x, and the apply
 // pass (MODE_APPLY) reads them back instead of F, so the local solve runs once.
 #pragma once
+#include "ff.cuh"
 #include "window.cuh"
 
 namespace dich {
@@ -186,6 +187,236 @@ __global__ void __launch_bounds__(NT) k_window_gen(const GenArgs G) {
     for (int i = 0; i < nbk; ++i) {
       const int64_t k = k0 + 32 * i;
       col[i * LD] = fma(XR, rw[k], fma(XL, rv[k], col[i * LD]));
+    }
+  }
+  __syncthreads();
+
+  // ---------------------------------------------------------------- coalesced store of the own rows
+  unsigned bad = 0u;
+  {
+    const int jlo = hl * n;
+    const int jhi = min(len, (hl + nown) * n);
+    double* dst = xw + row_lo;
+    int b = (jlo + tid) / n, i = (jlo + tid) - ((jlo + tid) / n) * n;
+    const int db = NT / n, di = NT - (NT / n) * n;
+    for (int j = jlo + tid; j < jhi; j += NT) {
+      const double dv = S[i * LD + b];
+      __stcs(dst + j, dv);
+      if (A.check_finite && !isfinite(dv)) bad = 1u;
+      i += di;
+      b += db;
+      if (i >= n) {
+        i -= n;
+        ++b;
+      }
+    }
+  }
+  if (bad) atomicOr(A.status, (unsigned)ST_NONFINITE);
+}
+
+// ---------------------------------------------------------------- MIXED form
+// The same steps with the per-row work in float-float arithmetic (ff.cuh) on values scaled per
+// window by one exact power of two (largest |F| of the window near 2^16): the per-row tables
+// hold float-float pairs (hi, lo) in the 8-byte slots of the FP64 tables, the local solve runs
+// z_i = (F_i - a_i z_{i-1}) rd_i and y_i = z_i - cp_i y_{i+1} in float-float, the block ends
+// alpha, omega leave as FP64 for the FP64 beta map and tree (one block per thread, so the tree
+// costs a few FP64 operations per row), and the correction x = y + x_{s-1} v + x_{e+1} w runs in
+// float-float before one join to FP64 per row.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_window_gen_ff(const GenArgs G) {
+  constexpr int LD = NT + 1;
+  constexpr int NW = NT / 32;
+  const WinArgs& A = G.w;
+  extern __shared__ __align__(16) double sm[];
+  const int tid = threadIdx.x;
+  const int ns = A.n_smem;
+  double* S = sm;
+  double* sxs = S + (size_t)ns * LD;
+  double* sxe = sxs + NT;
+  double* scl = sxe + NT;
+  double* scr = scl + NT;
+  double* swa = scr + NT;                          // 4 * NW scan scratch (also the exponent maxima)
+
+  const SysPlan* pp = A.plans;
+  const int64_t P = pp->P;
+  const int nown0 = pp->own;
+  const int64_t m0 = (int64_t)blockIdx.x * nown0;
+  const int nown = (int)min((int64_t)nown0, P - m0);
+  int hl = 0, hr = 0;
+  if (A.mode == MODE_FULL) {
+    hl = (int)min((int64_t)pp->hl, m0);
+    hr = (int)min((int64_t)pp->hr, P - m0 - nown);
+  }
+  const int64_t wlo = m0 - hl;
+  const int nwin = hl + nown + hr;
+  const int n = pp->n, nlast = pp->nlast;
+  const bool has_last = (wlo + nwin == P);
+  const int64_t row_lo = wlo * (int64_t)n;
+  const int len = nwin * n - (has_last ? (n - nlast) : 0);
+  const double* Fw = A.F + (int64_t)blockIdx.y * A.ldf;
+  double* xw = A.x + (int64_t)blockIdx.y * A.ldx;
+
+  // ---------------------------------------------------------------- F (or y) -> smem (transposed)
+  {
+    const double* src = ((A.mode == MODE_APPLY) ? xw : Fw) + row_lo;
+    int b = tid / n, i = tid - (tid / n) * n;
+    const int db = NT / n, di = NT - (NT / n) * n;
+    for (int j = tid; j < len; j += NT) {
+      cp_async8(&S[i * LD + b], src + j);
+      i += di;
+      b += db;
+      if (i >= n) {
+        i -= n;
+        ++b;
+      }
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  const bool act = tid < nwin;
+  const int64_t mb = wlo + tid;
+  const int nbk = (act && mb == P - 1) ? nlast : n;
+  double* col = S + tid;
+
+  // ---------------------------------------------------------------- window scale
+  int wscale;
+  {
+    unsigned hmax = 0u;
+    if (act)
+      for (int i = 0; i < nbk; ++i) hmax = max(hmax, (unsigned)__double2hiint(col[i * LD]) & 0x7FFFFFFFu);
+    hmax = __reduce_max_sync(0xffffffffu, hmax);
+    unsigned* sexp = reinterpret_cast<unsigned*>(swa);
+    if ((tid & 31) == 0) sexp[tid >> 5] = hmax;
+    __syncthreads();
+    hmax = 0u;
+    for (int w = 0; w < NW; ++w) hmax = max(hmax, sexp[w]);
+    __syncthreads();
+    const int emax = (int)(hmax >> 20);
+    wscale = (emax == 2047) ? 0 : ((emax == 0) ? 1000 : max(-1000, min(1000, (1023 + 16) - emax)));
+  }
+
+  const float2* ra = reinterpret_cast<const float2*>(G.rows + GF_A * G.stride);
+  const float2* rd = reinterpret_cast<const float2*>(G.rows + GF_RD * G.stride);
+  const float2* rc = reinterpret_cast<const float2*>(G.rows + GF_CP * G.stride);
+  const float2* rv = reinterpret_cast<const float2*>(G.rows + GF_V * G.stride);
+  const float2* rw = reinterpret_cast<const float2*>(G.rows + GF_W * G.stride);
+  const int64_t k0 = gen_index(act ? mb : 0, 0, n);   // row i of the block at k0 + 32 i
+  float2* colf = reinterpret_cast<float2*>(col);     // the same slots, as float-float pairs (stride LD)
+  auto ldff = [](const float2* t, int64_t k) {
+    const float2 v = t[k];
+    return ffv{v.x, v.y};
+  };
+
+  // ---------------------------------------------------------------- local solves (a1), float-float
+  double alpha = 0.0, omega = 0.0;
+  if (act && A.mode != MODE_APPLY) {
+    // the factors of four rows are loaded ahead of their dependent steps (the per-row global
+    // loads would otherwise sit on the recurrence's critical path)
+    ffv z = ff_zero();
+    int i = 0;
+    for (; i + 4 <= nbk; i += 4) {
+      const int64_t k = k0 + 32 * i;
+      ffv a4[4], d4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a4[u] = ldff(ra, k + 32 * u);
+        d4[u] = ldff(rd, k + 32 * u);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float fh, fl;
+        split_sc(col[(i + u) * LD], wscale, fh, fl);
+        z = ff_mul(ff_fma(ff_neg(a4[u]), z, ffv{fh, fl}), d4[u]);
+        colf[(i + u) * LD] = make_float2(z.h, z.l);
+      }
+    }
+    for (; i < nbk; ++i) {
+      const int64_t k = k0 + 32 * i;
+      float fh, fl;
+      split_sc(col[i * LD], wscale, fh, fl);
+      z = ff_mul(ff_fma(ff_neg(ldff(ra, k)), z, ffv{fh, fl}), ldff(rd, k));
+      colf[i * LD] = make_float2(z.h, z.l);
+    }
+    ffv y = ff_zero();
+    i = nbk - 1;
+    for (; i - 3 >= 0; i -= 4) {
+      ffv c4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) c4[u] = ldff(rc, k0 + 32 * (i - u));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2 zz = colf[(i - u) * LD];
+        y = ff_fma(ff_neg(c4[u]), y, ffv{zz.x, zz.y});
+        colf[(i - u) * LD] = make_float2(y.h, y.l);
+      }
+    }
+    for (; i >= 0; --i) {
+      const float2 zz = colf[i * LD];
+      y = ff_fma(ff_neg(ldff(rc, k0 + 32 * i)), y, ffv{zz.x, zz.y});
+      colf[i * LD] = make_float2(y.h, y.l);
+    }
+    const float2 y0 = colf[0], ye = colf[(nbk - 1) * LD];
+    alpha = join_dadd(y0.x, y0.y, wscale);
+    omega = join_dadd(ye.x, ye.y, wscale);
+  }
+
+  // ---------------------------------------------------------------- beta (eq. 16), FP64
+  const double* bc = A.tabs + pp->o_bcl + (act ? mb : 0) * kBC;
+  const double bL = act ? fma(bc[BC_M00], alpha, bc[BC_M01] * omega) : 0.0;
+  const double bR = act ? fma(bc[BC_M10], alpha, bc[BC_M11] * omega) : 0.0;
+  if (A.mode == MODE_BETA) {   // beta and the block solutions y (joined to FP64) leave the window
+    if (act) {
+      A.beta[2 * (pp->gboff + mb)] = bL;
+      A.beta[2 * (pp->gboff + mb) + 1] = bR;
+      for (int i = 0; i < nbk; ++i) {
+        const float2 yy = colf[i * LD];
+        col[i * LD] = join_dadd(yy.x, yy.y, wscale);
+      }
+    }
+    __syncthreads();
+    int b = tid / n, i = tid - (tid / n) * n;
+    const int db = NT / n, di = NT - (NT / n) * n;
+    for (int j = tid; j < len; j += NT) {
+      xw[row_lo + j] = S[i * LD + b];
+      i += di;
+      b += db;
+      if (i >= n) {
+        i -= n;
+        ++b;
+      }
+    }
+    return;
+  }
+
+  double XL = 0.0, XR = 0.0;
+  if (A.mode == MODE_FULL) {
+    tree_f64<NT>(bc, act, bL, bR, mb, P, nwin, tid, swa, sxs, sxe, XL, XR);
+  } else if (act) {
+    XL = (mb == 0) ? 0.0 : A.iface[2 * (pp->gboff + mb - 1) + 1];
+    XR = (mb == P - 1) ? 0.0 : A.iface[2 * (pp->gboff + mb + 1)];
+  }
+
+  // ---------------------------------------------------------------- interiors (eq. 7), float-float
+  if (act) {
+    float ch, cl, dh, dl;
+    split_sc(XL, wscale, ch, cl);
+    split_sc(XR, wscale, dh, dl);
+    const ffv cL{ch, cl}, cR{dh, dl};
+#pragma unroll 4
+    for (int i = 0; i < nbk; ++i) {
+      const int64_t k = k0 + 32 * i;
+      ffv y;
+      if (A.mode == MODE_APPLY) {
+        float yh, yl;
+        split_sc(col[i * LD], wscale, yh, yl);
+        y = ffv{yh, yl};
+      } else {
+        const float2 yy = colf[i * LD];
+        y = ffv{yy.x, yy.y};
+      }
+      const ffv xv = ff_fma(cR, ldff(rw, k), ff_fma(cL, ldff(rv, k), y));
+      col[i * LD] = join_dadd(xv.h, xv.l, wscale);
     }
   }
   __syncthreads();

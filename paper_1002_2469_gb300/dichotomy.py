@@ -357,7 +357,8 @@ class GenPlan:
     host arrays of N entries; a[0] and c[N-1] are ignored): the general O(N) preliminary step of
     the Dichotomy Algorithm, then any number of FP64 solves."""
 
-    def __init__(self, a, b, c, block_size=0, threads=0, flags=0, trunc_eps=0.0, device=None, stream=None):
+    def __init__(self, a, b, c, block_size=0, threads=0, flags=0, trunc_eps=0.0, device=None, stream=None,
+                 precision=PREC_F64):
         a, b, c = _host_f64(a), _host_f64(b), _host_f64(c)
         if not (a.size == b.size == c.size):
             raise ValueError("a, b and c must have one entry per row")
@@ -365,7 +366,7 @@ class GenPlan:
         self._h = None
         L = _lib.load()
         h = ctypes.c_void_p()
-        opts = make_opts(block_size, PREC_F64, threads, flags, trunc_eps)
+        opts = make_opts(block_size, precision, threads, flags, trunc_eps)
         check(L.dichotomy_gen_plan(self.N, a.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p),
                                    c.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts), ctypes.byref(h)),
               "dichotomy_gen_plan")

@@ -249,7 +249,12 @@ def test_general_plan_validation_and_geometry_without_a_gpu():
     nan = b.copy()
     nan[5] = np.nan
     assert gen(a, nan, c)[0] == 1
-    assert gen(a, b, c, precision=1)[0] == 11                       # FP64 only
+    rc, info = gen(a, b, c, precision=1, flags=4)                   # MIXED (float-float rows)
+    assert rc == 0 and info.precision == 1
+    rc, info = gen(a, b, c, precision=2, flags=4)                   # AUTO: the faster FP64 form
+    assert rc == 0 and info.precision == 0
+    rc, info = gen(a * 1e30, b * 1e30, c * 1e30, precision=1, flags=4)   # factors beyond 2^40: refused
+    assert rc == 11
     assert gen([0.0], [2.0], [0.0])[0] == 0
 
 

@@ -33,6 +33,7 @@ def dominant(N, seed, margin=(0.3, 1.5)):
 
 def gen_solve(D, a, b, c, F, **kw):
     plan = D.GenPlan(a, b, c, **kw)
+    assert plan.info["precision"] in (0, 1)
     x = plan.solve(torch.from_numpy(F).cuda()).cpu().numpy()
     assert plan.status() == 0
     return x, plan.info
@@ -41,12 +42,41 @@ def gen_solve(D, a, b, c, F, **kw):
 HOST, DEVICE = 4, 8   # where the preliminary step runs (DICH_FLAG_HOST_PRELIM / _DEVICE_PRELIM)
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("prelim", [HOST, DEVICE])
 @pytest.mark.parametrize("N", [1, 2, 3, 5, 31, 1000, 4097, 100003, 1 << 20])
-def test_general_random_dominant(D, N, prelim):
+def test_general_random_dominant(D, N, prelim, prec):
     a, b, c = dominant(N, N)
     F = np.random.default_rng(N + 1).standard_normal(N)
-    x, info = gen_solve(D, a, b, c, F, flags=prelim)
+    x, info = gen_solve(D, a, b, c, F, flags=prelim, precision=prec)
+    if N > 1:
+        assert info["precision"] == (1 if prec == 1 else 0)   # AUTO takes the (faster) FP64 form
+    assert rel(x, oracle.thomas_tridiag(a, b, c, F)) < TOL, info
+
+
+@pytest.mark.parametrize("prelim", [HOST, DEVICE])
+@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("threads", [64, 128, 256])
+@pytest.mark.parametrize("bs", [2, 3, 16, 45])
+def test_general_mixed_geometry_and_paths(D, threads, bs, flags, prelim):
+    N = 77777
+    a, b, c = dominant(N, 15)
+    F = np.random.default_rng(16).standard_normal(N) * 1e-7
+    x, info = gen_solve(D, a, b, c, F, threads=threads, block_size=bs, flags=flags | prelim, precision=1)
+    assert info["precision"] == 1 and (info["path"] == 2 or not flags)
+    assert rel(x, oracle.thomas_tridiag(a, b, c, F)) < TOL, info
+
+
+def test_general_mixed_scaled_rows(D):
+    """Rows scaled by powers of ten from 1e-9 to 1e9 (factors within 2^40): the window scale and
+    the float-float factors keep 1e-12 norm-wise."""
+    N = 200003
+    a, b, c = dominant(N, 17)
+    s = 10.0 ** np.random.default_rng(18).uniform(-9, 9, N)
+    a, b, c = a * s, b * s, c * s
+    F = np.random.default_rng(19).standard_normal(N) * s
+    x, info = gen_solve(D, a, b, c, F, precision=1)
+    assert info["precision"] == 1
     assert rel(x, oracle.thomas_tridiag(a, b, c, F)) < TOL, info
 
 
