@@ -228,7 +228,8 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
  * with t_0 + psi[s] in its first row and t_0 + chi[s] in its last (host arrays of nsys entries;
  * psi = chi = 0 leaves a system plain).  The Toeplitz solves run as in dichotomy_batch_prepare;
  * then one CTA per quasi system applies its rank-2 corner correction (as dichotomy_plan_quasi).
- * dichotomy_adjoint_batched returns DICH_ERR_UNSUPPORTED for a batch with corner systems.
+ * dichotomy_adjoint_batched on such a batch returns lambda_s = A_s^-T w_s and 5 doubles per
+ * system in d_gt: dL/dt_-1, dL/dt_0, dL/dt_1, dL/dpsi, dL/dchi (as dichotomy_adjoint).
  * Errors: as dichotomy_batch_prepare and dichotomy_plan_quasi (per system). */
 int dichotomy_batch_prepare_quasi(int64_t nsys, const int64_t* h_N, const int64_t* h_offset, const double* h_tm1,
                                   const double* h_t0, const double* h_tp1, const double* h_psi, const double* h_chi,
@@ -237,7 +238,8 @@ int dichotomy_batch_workspace_bytes(dich_batch_t batch, size_t* bytes);
 int dichotomy_batch_bind(dich_batch_t batch, void* d_workspace, size_t bytes, void* stream);
 /* Solve every system of the batch in one launch per precision form. */
 int dichotomy_solve_batched(dich_batch_t batch, const double* d_F, double* d_x, void* stream);
-/* Batched adjoint: d_gF like d_x; d_gt is nsys x 3 doubles (dL/dt_-1, dL/dt_0, dL/dt_1). */
+/* Batched adjoint: d_gF like d_x; d_gt is nsys x 3 doubles (dL/dt_-1, dL/dt_0, dL/dt_1), or
+ * nsys x 5 for a batch from dichotomy_batch_prepare_quasi (adding dL/dpsi, dL/dchi). */
 int dichotomy_adjoint_batched(dich_batch_t batch, const double* d_w, const double* d_x,
                               double* d_gF, double* d_gt, void* stream);
 int dichotomy_batch_status(dich_batch_t batch, void* stream, int* device_status);

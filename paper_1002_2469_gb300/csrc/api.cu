@@ -973,7 +973,8 @@ struct dich_batch_s {
   // quasi-Toeplitz systems (eq. 21): their corner records and corner vectors, after the rest
   std::vector<CornerRec> crec;
   std::vector<double> ctab;
-  size_t off_crec = 0, off_ctab = 0;
+  std::vector<CornerRec> crec_adj;         // every system: its transposed corner record (adjoint)
+  size_t off_crec = 0, off_ctab = 0, off_crec_adj = 0, off_gt3 = 0;
 };
 
 extern "C" {
@@ -1226,30 +1227,46 @@ int dichotomy_batch_prepare_quasi(int64_t nsys, const int64_t* h_N, const int64_
   dich_batch_t b = nullptr;
   int rc = dichotomy_batch_prepare(nsys, h_N, h_offset, tm1e.data(), t0e.data(), tp1e.data(), opts, &b);
   if (rc) return rc;
+  b->crec_adj.reserve((size_t)nsys);
   for (int64_t s = 0; s < nsys; ++s) {
-    if (h_N[s] < 2 || (h_psi[s] == 0.0 && h_chi[s] == 0.0)) continue;
-    Corners c;
-    rc = corner_build(h_tm1[s], h_t0[s], h_tp1[s], h_psi[s], h_chi[s], h_N[s], b->opts.eps, c);
-    if (rc) {
-      dichotomy_batch_destroy(b);
-      return rc;
+    // the adjoint's record: plain systems keep empty corner vectors (their dL/dpsi, dL/dchi are
+    // still -lambda_0 x_0 and -lambda_{N-1} x_{N-1})
+    CornerRec adj{h_N[s], h_offset[s], 0, 0, 0, 0, h_psi[s], h_chi[s], 1.0, 0.0, 0.0, 1.0};
+    if (h_N[s] >= 2 && (h_psi[s] != 0.0 || h_chi[s] != 0.0)) {
+      Corners c;
+      rc = corner_build(h_tm1[s], h_t0[s], h_tp1[s], h_psi[s], h_chi[s], h_N[s], b->opts.eps, c);
+      if (rc) {
+        dichotomy_batch_destroy(b);
+        return rc;
+      }
+      const int64_t og = (int64_t)b->ctab.size();
+      b->ctab.insert(b->ctab.end(), c.gh.begin(), c.gh.end());
+      b->crec.push_back(CornerRec{h_N[s], h_offset[s], c.Lg, c.Lh, og, og + c.Lg, h_psi[s], h_chi[s], c.W[0], c.W[1],
+                                  c.W[2], c.W[3]});
+      // A^T: corner vectors h and g read backwards (persymmetry), the transposed 2x2 inverse
+      adj = CornerRec{h_N[s], h_offset[s], c.Lh, c.Lg, og + c.Lg, og, h_psi[s], h_chi[s], c.Wt[0], c.Wt[1], c.Wt[2],
+                      c.Wt[3]};
     }
-    const int64_t og = (int64_t)b->ctab.size();
-    b->ctab.insert(b->ctab.end(), c.gh.begin(), c.gh.end());
-    b->crec.push_back(CornerRec{h_N[s], h_offset[s], c.Lg, c.Lh, og, og + c.Lg, h_psi[s], h_chi[s], c.W[0], c.W[1],
-                                c.W[2], c.W[3]});
+    b->crec_adj.push_back(adj);
   }
-  if (!b->crec.empty()) {
+  {
     // appended after the workspace (and staged whole: the scratch in between is uploaded as zeros)
     size_t o_ = b->ws_bytes;
     b->off_crec = o_;
-    o_ += align_up(sizeof(CornerRec) * b->crec.size());
+    o_ += align_up(sizeof(CornerRec) * std::max<size_t>(1, b->crec.size()));
     b->off_ctab = o_;
     o_ += align_up(sizeof(double) * std::max<size_t>(1, b->ctab.size()));
+    b->off_crec_adj = o_;
+    o_ += align_up(sizeof(CornerRec) * std::max<size_t>(1, b->crec_adj.size()));
+    const size_t staged = o_;
+    b->off_gt3 = o_;   // the Toeplitz gradients of the adjoint, 3 per system (scratch)
+    o_ += align_up(sizeof(double) * 3 * (size_t)std::max<int64_t>(1, nsys));
     b->ws_bytes = o_;
-    b->staging.resize(o_, 0);
-    std::memcpy(b->staging.data() + b->off_crec, b->crec.data(), sizeof(CornerRec) * b->crec.size());
+    b->staging.resize(staged, 0);
+    if (!b->crec.empty()) std::memcpy(b->staging.data() + b->off_crec, b->crec.data(), sizeof(CornerRec) * b->crec.size());
     if (!b->ctab.empty()) std::memcpy(b->staging.data() + b->off_ctab, b->ctab.data(), sizeof(double) * b->ctab.size());
+    if (!b->crec_adj.empty())
+      std::memcpy(b->staging.data() + b->off_crec_adj, b->crec_adj.data(), sizeof(CornerRec) * b->crec_adj.size());
   }
   *out = b;
   return DICH_OK;
@@ -1411,10 +1428,22 @@ int dichotomy_adjoint_batched(dich_batch_t b, const double* d_w, const double* d
   if (!aligned8(d_w) || !aligned8(d_x) || !aligned8(d_gF) || !aligned8(d_gt)) return DICH_ERR_ARG;
   if (!is_device_ptr(d_w) || !is_device_ptr(d_x) || !is_device_ptr(d_gF) || !is_device_ptr(d_gt)) return DICH_ERR_ARG;
   if (d_gF == d_w || d_gF == d_x) return DICH_ERR_ALIAS;
-  if (!b->crec.empty()) return DICH_ERR_UNSUPPORTED;   // quasi-Toeplitz systems: single plans only
-  cudaError_t e = cudaMemsetAsync(d_gt, 0, sizeof(double) * 3 * (size_t)b->nsys, (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (b->crec_adj.empty()) {
+    cudaError_t e = cudaMemsetAsync(d_gt, 0, sizeof(double) * 3 * (size_t)b->nsys, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return batch_launch(b, d_w, d_gF, d_x, d_gt, true, st);
+  }
+  // a batch prepared with corners: the Toeplitz adjoint into scratch, then per system the corner
+  // terms, dL/dpsi, dL/dchi (5 gradients per system in d_gt) and the correction of lambda
+  double* gt3 = (double*)(b->d_ws + b->off_gt3);
+  cudaError_t e = cudaMemsetAsync(gt3, 0, sizeof(double) * 3 * (size_t)b->nsys, st);
   if (e != cudaSuccess) return cuda_fail(e);
-  return batch_launch(b, d_w, d_gF, d_x, d_gt, true, (cudaStream_t)stream);
+  const int rc = batch_launch(b, d_w, d_gF, d_x, gt3, true, st);
+  if (rc != DICH_OK) return rc;
+  e = launch_corner_adjoint_batch((const CornerRec*)(b->d_ws + b->off_crec_adj), b->nsys,
+                                  (const double*)(b->d_ws + b->off_ctab), d_x, d_gF, gt3, d_gt, st);
+  return e == cudaSuccess ? DICH_OK : cuda_fail(e);
 }
 
 int dichotomy_batch_status(dich_batch_t b, void* stream, int* device_status) {

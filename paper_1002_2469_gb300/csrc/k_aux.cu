@@ -444,6 +444,79 @@ cudaError_t launch_corner_batch(const CornerRec* recs, int64_t n, const double* 
   return cudaGetLastError();
 }
 
+// Batched adjoint with corners: one CTA per system (every system of the batch).  gt3 holds the
+// Toeplitz adjoint's -sum lambda_T x products (3 per system); gt5 receives the five gradients
+// (t_-1, t_0, t_1, psi, chi).  A system with corners (Lg or Lh nonzero in its transposed record)
+// adds its corner correction's share to the sums and has lambda corrected in place; one-row
+// systems (psi and chi folded into t_0) repeat dL/dt_0.
+__global__ void __launch_bounds__(256) k_corner_adj_batch(const CornerRec* recs, const double* tab, const double* xf,
+                                                          double* lam, const double* gt3, double* gt5) {
+  __shared__ double sh[6 * 256];
+  const int64_t s = blockIdx.x;
+  const CornerRec c = recs[s];
+  const int64_t N = c.N;
+  double* out = gt5 + 5 * s;
+  if (N <= 1) {
+    if (threadIdx.x < 5) out[threadIdx.x] = (N == 0) ? 0.0 : gt3[3 * s + ((threadIdx.x < 3) ? threadIdx.x : 1)];
+    return;
+  }
+  const double* x = xf + c.off;
+  double* l = lam + c.off;
+  const double y0 = l[0], yn = l[N - 1];
+  const double a = c.psi * y0, b = c.chi * yn;
+  const double c0 = fma(c.w00, a, c.w01 * b), c1 = fma(c.w10, a, c.w11 * b);
+  const double* g = tab + c.og;
+  const double* h = tab + c.oh;
+  auto xv = [&](int64_t i) { return (i >= 0 && i < N) ? x[i] : 0.0; };
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = threadIdx.x; i < c.Lg; i += 256) {
+    acc[0] = fma(g[i], xv(i - 1), acc[0]);
+    acc[1] = fma(g[i], xv(i), acc[1]);
+    acc[2] = fma(g[i], xv(i + 1), acc[2]);
+  }
+  for (int64_t k = threadIdx.x; k < c.Lh; k += 256) {
+    const int64_t i = N - 1 - k;
+    acc[3] = fma(h[k], xv(i - 1), acc[3]);
+    acc[4] = fma(h[k], xv(i), acc[4]);
+    acc[5] = fma(h[k], xv(i + 1), acc[5]);
+  }
+  for (int j = 0; j < 6; ++j) sh[j * 256 + threadIdx.x] = acc[j];
+  __syncthreads();
+  for (int d = 128; d > 0; d >>= 1) {
+    if ((int)threadIdx.x < d)
+      for (int j = 0; j < 6; ++j) sh[j * 256 + threadIdx.x] += sh[j * 256 + threadIdx.x + d];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < 3; ++j) out[j] = gt3[3 * s + j] + fma(c0, sh[j * 256], c1 * sh[(3 + j) * 256]);
+    double l0 = y0, ln = yn;
+    if (0 < c.Lg) l0 = fma(-c0, g[0], l0);
+    if (N - 1 < c.Lh) l0 = fma(-c1, h[N - 1], l0);
+    if (N - 1 < c.Lg) ln = fma(-c0, g[N - 1], ln);
+    if (0 < c.Lh) ln = fma(-c1, h[0], ln);
+    out[3] = -l0 * x[0];
+    out[4] = -ln * x[N - 1];
+  }
+  // lambda = lambda_T - c0 g - c1 h on the corner rows (both end values were read above)
+  const int64_t hi1 = min(c.Lg, N), lo2 = max(N - c.Lh, hi1);
+  auto corr = [&](int64_t i) {
+    double v = l[i];
+    if (i < c.Lg) v = fma(-c0, g[i], v);
+    const int64_t k = N - 1 - i;
+    if (k < c.Lh) v = fma(-c1, h[k], v);
+    l[i] = v;
+  };
+  for (int64_t i = threadIdx.x; i < hi1; i += 256) corr(i);
+  for (int64_t i = lo2 + threadIdx.x; i < N; i += 256) corr(i);
+}
+
+cudaError_t launch_corner_adjoint_batch(const CornerRec* recs, int64_t nsys, const double* tab, const double* xf,
+                                        double* lam, const double* gt3, double* gt5, cudaStream_t st) {
+  if (nsys <= 0) return cudaSuccess;
+  k_corner_adj_batch<<<(unsigned)nsys, 256, 0, st>>>(recs, tab, xf, lam, gt3, gt5);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_corner_adjoint(const double* xf, double* lam, double* gt, const CornerArgs& c, cudaStream_t st) {
   if (c.N <= 0) return cudaSuccess;
   k_corner_adj<<<1, 256, 0, st>>>(xf, lam, c, gt);

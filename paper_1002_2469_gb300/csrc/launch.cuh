@@ -66,6 +66,10 @@ struct CornerRec {
 // x <- A_s^-1 F_s from y_s = T_s^-1 F_s (already in x) for every listed system: one CTA each
 cudaError_t launch_corner_batch(const CornerRec* recs, int64_t n, const double* tab, double* x, cudaStream_t st);
 
+// adjoint of a batch with quasi-Toeplitz systems: recs are the transposed corner records of every
+// system; gt3 the Toeplitz gradients (3 per system), gt5 the result (5 per system)
+cudaError_t launch_corner_adjoint_batch(const CornerRec* recs, int64_t nsys, const double* tab, const double* xf,
+                                        double* lam, const double* gt3, double* gt5, cudaStream_t st);
 // adjoint of a quasi-Toeplitz plan: gradient terms of the corner correction, dL/dpsi, dL/dchi
 // (gt[0..4]), then the corner correction of lambda (c: the transposed corner vectors)
 cudaError_t launch_corner_adjoint(const double* xf, double* lam, double* gt, const CornerArgs& c, cudaStream_t st);

@@ -318,6 +318,7 @@ class Batch:
         self.total = int((self.offset + N).max()) if N.size else 0
         self._h = None
         opts = make_opts(block_size, precision, threads, flags, trunc_eps)
+        self.corners = psi is not None or chi is not None
         self._h = dichotomy_batch_prepare(N, self.offset, t_m1, t_0, t_1, opts, psi=psi, chi=chi)
         self.info = dichotomy_batch_info(self._h)
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -339,7 +340,7 @@ class Batch:
 
     def adjoint(self, w: torch.Tensor, x: torch.Tensor, stream=None):
         gF = torch.empty_like(w)
-        gt = torch.empty((self.nsys, 3), dtype=torch.float64, device=w.device)
+        gt = torch.empty((self.nsys, 5 if self.corners else 3), dtype=torch.float64, device=w.device)
         dichotomy_adjoint_batched(self._h, w, x, gF, gt, stream)
         return gF, gt
 

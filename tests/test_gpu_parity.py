@@ -281,10 +281,19 @@ def test_quasi_toeplitz_batch(D, prec):
         t = (tm1[s_], t0[s_], tp1[s_])
         ref = oracle.thomas_quasi(t, psi[s_], chi[s_], F[o:o + n])
         assert rel(x[o:o + n], ref) < TOL, (s_, n, t, psi[s_], chi[s_])
-    w = torch.zeros_like(torch.from_numpy(F).cuda())
-    with pytest.raises(D.DichotomyError) as err:
-        b.adjoint(w, w)
-    assert err.value.code == 11
+    # the adjoint: lambda_s = A_s^-T w_s and the five gradients per system
+    wh = rng.uniform(-1, 1, F.size)
+    gF, gt = b.adjoint(torch.from_numpy(wh).cuda(), torch.from_numpy(x).cuda())
+    assert b.status() == 0 and gt.shape == (nsys, 5)
+    lam, g = gF.cpu().numpy(), gt.cpu().numpy()
+    for s_ in range(nsys):
+        o, n = int(off[s_]), int(N[s_])
+        t = (tm1[s_], t0[s_], tp1[s_])
+        lref, gref = oracle.adjoint_quasi(t, psi[s_], chi[s_], wh[o:o + n], x[o:o + n])
+        assert rel(lam[o:o + n], lref) < TOL, (s_, n)
+        sc = np.max(np.abs(lref)) * np.max(np.abs(x[o:o + n]))
+        assert np.all(np.abs(g[s_, :3] - gref[:3]) <= TOL * max(np.max(np.abs(gref[:3])), sc)), (s_, g[s_], gref)
+        assert np.all(np.abs(g[s_, 3:] - gref[3:]) <= TOL * sc), (s_, g[s_], gref)
 
 
 @pytest.mark.parametrize("prec,flags", [(0, 0), (1, 0), (2, 0), (0, 1), (1, 1)])
