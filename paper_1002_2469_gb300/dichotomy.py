@@ -22,7 +22,7 @@ __all__ = [
     "dichotomy_solve", "dichotomy_solve_series", "dichotomy_solve_host", "dichotomy_adjoint", "dichotomy_status", "dichotomy_destroy",
     "dichotomy_batch_prepare", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
     "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
-    "dichotomy_batch_destroy", "Plan", "Batch", "GenPlan", "solve", "DichotomySolve", "DichotomySolveQuasi", "DichotomySolveBatched",
+    "dichotomy_batch_destroy", "Plan", "Batch", "GenPlan", "solve", "DichotomySolve", "DichotomySolveQuasi", "DichotomySolveBatched", "DichotomySolveBatchedQuasi",
     "PREC_F64", "PREC_MIXED", "PREC_AUTO", "FLAG_FORCE_GENERAL", "FLAG_CHECK_FINITE", "FLAG_HOST_PRELIM", "FLAG_DEVICE_PRELIM", "DichotomyError",
 ]
 
@@ -476,3 +476,24 @@ class DichotomySolveBatched(torch.autograd.Function):
         (x,) = ctx.saved_tensors
         gF, gt = ctx.batch.adjoint(gx.contiguous(), x)
         return gF, gt, None, None
+
+
+class DichotomySolveBatchedQuasi(torch.autograd.Function):
+    """Batched quasi-Toeplitz solves (eq. 21): F [sum N], t [nsys, 3], corners [nsys, 2] = (psi, chi)."""
+
+    @staticmethod
+    def forward(ctx, F, t, corners, N, precision=PREC_F64):
+        tv = t.detach().cpu().double().numpy()
+        cv = corners.detach().cpu().double().numpy()
+        batch = Batch(N, tv[:, 0], tv[:, 1], tv[:, 2], precision=precision, device=F.device, psi=cv[:, 0],
+                      chi=cv[:, 1])
+        x = batch.solve(F.detach().contiguous())
+        ctx.batch = batch
+        ctx.save_for_backward(x)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        gF, g = ctx.batch.adjoint(gx.contiguous(), x)
+        return gF, g[:, :3], g[:, 3:], None, None

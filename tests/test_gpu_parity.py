@@ -576,6 +576,30 @@ def test_autograd_quasi(D, corners):
     assert np.max(np.abs(c.grad.cpu().numpy() - g[3:])) <= TOL * np.max(np.abs(lam)) * np.max(np.abs(x.detach().cpu().numpy()))
 
 
+def test_autograd_batched_quasi(D):
+    """Autograd through a batch of quasi-Toeplitz systems: gradients for F, t and the corners."""
+    rng = np.random.default_rng(8)
+    N = np.array([3000, 1, 70000, 17], dtype=np.int64)
+    tv = np.array([[-1.0, 2.5, -1.0], [-1.0, 4.0, -1.0], [-1.2, 2.5, -0.8], [0.7, 2.5, -1.1]])
+    cv = np.array([[-1.0, -1.0], [0.5, 0.25], [0.3, -0.4], [0.0, 0.0]])
+    t = torch.tensor(tv, device="cuda", requires_grad=True)
+    c = torch.tensor(cv, device="cuda", requires_grad=True)
+    F = torch.from_numpy(rng.uniform(-1, 1, int(N.sum()))).cuda().requires_grad_(True)
+    w = torch.from_numpy(rng.uniform(-1, 1, int(N.sum()))).cuda()
+    x = D.DichotomySolveBatchedQuasi.apply(F, t, c, N)
+    (x * w).sum().backward()
+    off = np.concatenate([[0], np.cumsum(N)[:-1]])
+    Fh, wh, xh = F.detach().cpu().numpy(), w.cpu().numpy(), x.detach().cpu().numpy()
+    for s_ in range(N.size):
+        o, n = int(off[s_]), int(N[s_])
+        lam, g = oracle.adjoint_quasi(tuple(tv[s_]), cv[s_, 0], cv[s_, 1], wh[o:o + n],
+                                      oracle.thomas_quasi(tuple(tv[s_]), cv[s_, 0], cv[s_, 1], Fh[o:o + n]))
+        assert rel(F.grad.cpu().numpy()[o:o + n], lam) < TOL
+        sc = np.max(np.abs(lam)) * np.max(np.abs(xh[o:o + n]))
+        assert np.all(np.abs(t.grad.cpu().numpy()[s_] - g[:3]) <= TOL * max(np.max(np.abs(g[:3])), sc))
+        assert np.all(np.abs(c.grad.cpu().numpy()[s_] - g[3:]) <= TOL * sc)
+
+
 @pytest.mark.parametrize("flags", [0, 1])
 def test_cuda_graph_capture_and_replay(D, flags):
     """A bound plan's solve only enqueues kernels on the caller's stream (no allocation, no host
