@@ -69,7 +69,9 @@ enum {
   DICH_FLAG_FORCE_GENERAL = 1,  /* never truncate cross-tile coupling (3-kernel path) */
   DICH_FLAG_CHECK_FINITE = 2,   /* latch DICH_ERR_NONFINITE if any output is not finite */
   DICH_FLAG_HOST_PRELIM = 4,    /* general matrices: preliminary step on the host at plan time */
-  DICH_FLAG_DEVICE_PRELIM = 8   /* general matrices: preliminary step on the device at bind time */
+  DICH_FLAG_DEVICE_PRELIM = 8,  /* general matrices: preliminary step on the device at bind time */
+  DICH_FLAG_ALLOW_NOT_DOMINANT = 16  /* general matrices: accept rows without diagonal dominance; judge
+                                        the result by dich_plan_info.growth and dichotomy_gen_residual */
 };
 
 typedef struct {
@@ -97,6 +99,9 @@ typedef struct {
   size_t beta_offset;      /* general path: byte offsets into the workspace of the per-block */
   size_t iface_offset;     /* (beta^L, beta^R) of eq. 16 and first/last values (x_s, x_e) of
                               eq. 18 the last solve left there, 2 doubles per block; 0 otherwise */
+  double growth;           /* general matrices: the a priori error growth gamma^l of the error
+                              estimate after eq. 33 (gamma: the largest block map factor, at least 1;
+                              l = ceil(log2 P) dichotomy levels); 1 under diagonal dominance */
 } dich_plan_info;
 
 typedef struct dich_plan_s* dich_plan_t;
@@ -264,15 +269,18 @@ const char* dichotomy_version(void);
  * suffix products of 2x2 matrices over the blocks) or on the host at plan time (below 2^15 rows,
  * or with DICH_FLAG_HOST_PRELIM).  Every solve of a series (eq. 2) reuses it.  FP64 or
  * float-float (see dichotomy_gen_plan).  The
- * plan keeps 5 doubles per row in the device workspace (40 bytes per row, plus 80 bytes per
- * block); the device preliminary adds 24 bytes per row (the matrix) and 64 per block. */
+ * plan keeps 5 doubles per row of factors and spikes and the matrix itself (for the residual
+ * check) in the device workspace (64 bytes per row, plus 80 bytes per block); the device
+ * preliminary adds 64 bytes per block. */
 
 /* Plan for the N x N matrix given by the host arrays h_a (sub-diagonal), h_b (diagonal), h_c
  * (super-diagonal), N entries each (copied; the caller keeps ownership).  opts as for
  * dichotomy_plan_ex; DICH_PREC_MIXED runs the local solves and the correction in float-float
  * (factors within 2^-40..2^40, else DICH_ERR_UNSUPPORTED -- from dichotomy_gen_bind with the
- * device preliminary); DICH_PREC_AUTO takes FP64, the faster form of this kernel on GB300.  Every row must satisfy
- * |b_i| >= |a_i| + |c_i| (eq. 32-33).  Errors: DICH_ERR_ARG (null, negative N, non-finite entry,
+ * device preliminary); DICH_PREC_AUTO takes FP64, the faster form of this kernel on GB300.
+ * Every row must satisfy |b_i| >= |a_i| + |c_i| (eq. 32-33) unless DICH_FLAG_ALLOW_NOT_DOMINANT
+ * is set; then the block maps may grow (dich_plan_info.growth bounds the error growth a priori)
+ * and dichotomy_gen_residual checks the solution a posteriori.  Errors: DICH_ERR_ARG (null, negative N, non-finite entry,
  * bad opts), DICH_ERR_NOT_DOMINANT, DICH_ERR_SINGULAR (a zero pivot; with the device preliminary
  * reported by dichotomy_gen_bind), DICH_ERR_UNSUPPORTED. */
 int dichotomy_gen_plan(int64_t N, const double* h_a, const double* h_b, const double* h_c, const dich_opts* opts,
@@ -293,6 +301,11 @@ int dichotomy_gen_solve(dich_gen_t plan, const double* d_F, double* d_x, void* s
 /* The series form (as dichotomy_solve_series). */
 int dichotomy_gen_solve_series(dich_gen_t plan, int64_t M, const double* d_F, int64_t ldf, double* d_x,
                                int64_t ldx, void* stream);
+/* The a posteriori check recommended after eq. 33: with F and x (N doubles each on the device),
+ * h_out[0] = max_i |F_i - (A x)_i| and h_out[1] = the norm-wise backward error
+ * max|F - A x| / (||A||_inf max|x| + max|F|) (2 doubles on the host).  Synchronizes `stream`.
+ * Errors: DICH_ERR_ARG, DICH_ERR_UNBOUND, DICH_ERR_CUDA. */
+int dichotomy_gen_residual(dich_gen_t plan, const double* d_F, const double* d_x, double* h_out, void* stream);
 /* Synchronize, read and clear the device status word (as dichotomy_status). */
 int dichotomy_gen_status(dich_gen_t plan, void* stream, int* device_status);
 void dichotomy_gen_destroy(dich_gen_t plan);

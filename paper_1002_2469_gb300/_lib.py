@@ -23,7 +23,7 @@ STATUS_NAMES = {
     9: "DICH_ERR_WORKSPACE", 10: "DICH_ERR_SCHEDULE", 11: "DICH_ERR_UNSUPPORTED",
 }
 PREC_F64, PREC_MIXED, PREC_AUTO = 0, 1, 2
-FLAG_FORCE_GENERAL, FLAG_CHECK_FINITE, FLAG_HOST_PRELIM, FLAG_DEVICE_PRELIM = 1, 2, 4, 8
+FLAG_FORCE_GENERAL, FLAG_CHECK_FINITE, FLAG_HOST_PRELIM, FLAG_DEVICE_PRELIM, FLAG_ALLOW_NOT_DOMINANT = 1, 2, 4, 8, 16
 
 EXPORTS = [
     "dichotomy_plan", "dichotomy_plan_ex", "dichotomy_plan_quasi", "dichotomy_plan_info", "dichotomy_plan_workspace_bytes",
@@ -33,7 +33,7 @@ EXPORTS = [
     "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
     "dichotomy_batch_destroy", "dichotomy_strerror", "dichotomy_last_cuda_error", "dichotomy_version",
     "dichotomy_gen_plan", "dichotomy_gen_info", "dichotomy_gen_workspace_bytes", "dichotomy_gen_bind",
-    "dichotomy_gen_solve", "dichotomy_gen_solve_series", "dichotomy_gen_status", "dichotomy_gen_destroy",
+    "dichotomy_gen_solve", "dichotomy_gen_solve_series", "dichotomy_gen_residual", "dichotomy_gen_status", "dichotomy_gen_destroy",
 ]
 
 
@@ -59,7 +59,7 @@ class dich_plan_info(ctypes.Structure):
                 ("halo_l", c_int32), ("halo_r", c_int32), ("path", c_int32), ("precision", c_int32),
                 ("tiles", c_int64), ("Lv", c_int32), ("Lw", c_int32), ("kl", c_int32), ("kr", c_int32),
                 ("rs", c_double), ("ib", c_double), ("z", c_double), ("workspace_bytes", c_size_t),
-                ("beta_offset", c_size_t), ("iface_offset", c_size_t)]
+                ("beta_offset", c_size_t), ("iface_offset", c_size_t), ("growth", c_double)]
 
 
 _lib_obj = None
@@ -118,6 +118,7 @@ def load(build_if_missing: bool = True):
             "dichotomy_gen_bind": ([P, P, c_size_t, P], I),
             "dichotomy_gen_solve": ([P, P, P, P], I),
             "dichotomy_gen_solve_series": ([P, c_int64, P, c_int64, P, c_int64, P], I),
+            "dichotomy_gen_residual": ([P, P, P, ctypes.POINTER(c_double), P], I),
             "dichotomy_gen_status": ([P, P, ctypes.POINTER(I)], I),
             "dichotomy_gen_destroy": ([P], None),
         }

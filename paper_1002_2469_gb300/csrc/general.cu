@@ -72,6 +72,34 @@ static cudaError_t launch_window_gen(int NT, int grid, size_t smem, cudaStream_t
 
 }  // namespace dich
 
+namespace dich {
+
+// the a posteriori check: max |F - A x|, max |x|, max |F| (bits of non-negative doubles)
+__global__ void __launch_bounds__(256) k_gen_residual(int64_t N, const double* a, const double* b, const double* c,
+                                                       const double* F, const double* x, unsigned long long* res) {
+  double r = 0.0, xm = 0.0, fm = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double ax = b[i] * x[i];
+    if (i > 0) ax = fma(a[i], x[i - 1], ax);
+    if (i + 1 < N) ax = fma(c[i], x[i + 1], ax);
+    r = fmax(r, fabs(F[i] - ax));
+    xm = fmax(xm, fabs(x[i]));
+    fm = fmax(fm, fabs(F[i]));
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    r = fmax(r, __shfl_xor_sync(0xffffffffu, r, d));
+    xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, d));
+    fm = fmax(fm, __shfl_xor_sync(0xffffffffu, fm, d));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&res[0], (unsigned long long)__double_as_longlong(r));
+    atomicMax(&res[1], (unsigned long long)__double_as_longlong(xm));
+    atomicMax(&res[2], (unsigned long long)__double_as_longlong(fm));
+  }
+}
+
+}  // namespace dich
+
 struct dich_gen_s {
   int64_t N = 0;
   Opts opts;
@@ -84,6 +112,9 @@ struct dich_gen_s {
   std::vector<double> recs;           // block records, kBC doubles per block (host preliminary)
   std::vector<double> rows;           // per-row fields (window_gen.cuh layout; host preliminary)
   bool device_prelim = false;         // preliminary step on the device at bind time
+  double norm_inf = 0.0;              // ||A||_inf, for the backward error of the residual check
+  double gamma = 1.0;                 // largest block map factor (at least 1): the a priori growth base
+  size_t off_res = 0;                 // residual check: 3 maxima
   std::vector<double> ha, hb, hc;     // the matrix, kept for the device preliminary
   size_t ws_bytes = 0, off_plan = 0, off_status = 0, off_recs = 0, off_rows = 0, off_beta = 0, off_iface = 0,
          off_scan = 0, off_raw = 0, off_comp = 0, off_chunk = 0, off_max = 0;
@@ -127,6 +158,7 @@ int gen_geometry(dich_gen_s* g, double b0) {
 // windows: one window, halo windows (coupling beyond the halo below eps), or the general path,
 // from the largest |a| over blocks 0..P-2 and |c| over blocks 1..P-1 of the block maps
 void gen_decide(dich_gen_s* g, double amax, double cmax) {
+  g->gamma = std::max({1.0, amax, cmax});
   SysPlan& r = g->rec;
   const int64_t P = r.P;
   const int NT = g->NT;
@@ -314,10 +346,12 @@ void gen_layout(dich_gen_s* g) {
   o += align_up(sizeof(double) * kBC * (size_t)g->rec.P);
   g->off_rows = o;
   if (g->N > 1) o += align_up(sizeof(double) * (size_t)(kGenFields * g->stride));
-  if (g->device_prelim) {   // the matrix, block composites, chunk products, largest map factors
+  g->off_raw = o;   // the matrix
+  o += align_up(sizeof(double) * 3 * (size_t)g->N);
+  g->off_res = o;
+  o += kAlign;
+  if (g->device_prelim) {   // block composites, chunk products, largest map factors
     const int64_t nch = ceil_div(g->rec.P, (int64_t)kPreChunk);
-    g->off_raw = o;
-    o += align_up(sizeof(double) * 3 * (size_t)g->N);
     g->off_comp = o;
     o += align_up(sizeof(Mat2) * 2 * (size_t)g->rec.P);
     g->off_chunk = o;
@@ -461,36 +495,39 @@ int dichotomy_gen_plan(int64_t N, const double* h_a, const double* h_b, const do
   Opts o;
   int rc = read_opts(opts, o);
   if (rc) return rc;
-  // eq. 32-33 row by row (a_0 and c_{N-1} lie outside the matrix)
+  // eq. 32-33 row by row (a_0 and c_{N-1} lie outside the matrix), unless waived; ||A||_inf
+  const bool waive = (o.flags & DICH_FLAG_ALLOW_NOT_DOMINANT) != 0;
+  double norm_inf = 0.0;
   for (int64_t i = 0; i < N; ++i) {
     const double ai = (i > 0) ? h_a[i] : 0.0, ci = (i < N - 1) ? h_c[i] : 0.0;
     if (!std::isfinite(ai) || !std::isfinite(h_b[i]) || !std::isfinite(ci)) return DICH_ERR_ARG;
-    if (h_b[i] == 0.0) return (ai == 0.0 && ci == 0.0) ? DICH_ERR_SINGULAR : DICH_ERR_NOT_DOMINANT;
-    if (std::fabs(h_b[i]) < (std::fabs(ai) + std::fabs(ci)) * (1.0 - 4.0 * DBL_EPSILON)) return DICH_ERR_NOT_DOMINANT;
+    if (h_b[i] == 0.0 && ai == 0.0 && ci == 0.0) return DICH_ERR_SINGULAR;
+    if (!waive && (h_b[i] == 0.0 || std::fabs(h_b[i]) < (std::fabs(ai) + std::fabs(ci)) * (1.0 - 4.0 * DBL_EPSILON)))
+      return DICH_ERR_NOT_DOMINANT;
+    norm_inf = std::max(norm_inf, std::fabs(ai) + std::fabs(h_b[i]) + std::fabs(ci));
   }
   dich_gen_s* g = new (std::nothrow) dich_gen_s();
   if (!g) return DICH_ERR_ARG;
   g->N = N;
   g->opts = o;
   g->NT = o.NT ? o.NT : 64;
+  g->norm_inf = norm_inf;
   if (N >= 1) {
     rc = gen_geometry(g, h_b[0]);
+    // the matrix is kept (on the device too) for the a posteriori residual and the device preliminary
+    try {
+      g->ha.assign(h_a, h_a + N);
+      g->hb.assign(h_b, h_b + N);
+      g->hc.assign(h_c, h_c + N);
+      g->ha[0] = 0.0;
+      g->hc[(size_t)N - 1] = 0.0;
+    } catch (...) {
+      rc = DICH_ERR_ARG;
+    }
     if (rc == DICH_OK && N > 1) {
       g->device_prelim = (o.flags & DICH_FLAG_DEVICE_PRELIM) ||
                          (!(o.flags & DICH_FLAG_HOST_PRELIM) && N >= kGenDevicePrelimMin);
-      if (g->device_prelim) {
-        try {
-          g->ha.assign(h_a, h_a + N);
-          g->hb.assign(h_b, h_b + N);
-          g->hc.assign(h_c, h_c + N);
-          g->ha[0] = 0.0;
-          g->hc[(size_t)N - 1] = 0.0;
-        } catch (...) {
-          rc = DICH_ERR_ARG;
-        }
-      } else {
-        rc = gen_host_tables(g, h_a, h_b, h_c);
-      }
+      if (!g->device_prelim) rc = gen_host_tables(g, h_a, h_b, h_c);
     }
     if (rc) {
       delete g;
@@ -516,6 +553,12 @@ int dichotomy_gen_info(dich_gen_t g, dich_plan_info* info) {
   info->precision = (g->form == FORM_MIXED) ? DICH_PREC_MIXED : DICH_PREC_F64;
   info->tiles = g->tiles;
   info->workspace_bytes = g->ws_bytes;
+  {
+    const int64_t P = std::max<int64_t>(1, g->rec.P);
+    int levels = 0;
+    while (((int64_t)1 << levels) < P) ++levels;
+    info->growth = std::min(std::pow(g->gamma, (double)levels), 1e300);
+  }
   if (g->path == PATH_GENERAL) {
     info->beta_offset = g->off_beta;
     info->iface_offset = g->off_iface;
@@ -545,6 +588,13 @@ int dichotomy_gen_bind(dich_gen_t g, void* d_ws, size_t bytes, void* stream) {
     e = cudaMemcpyAsync(base + g->off_recs, g->recs.data(), sizeof(double) * g->recs.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !g->rows.empty())
     e = cudaMemcpyAsync(base + g->off_rows, g->rows.data(), sizeof(double) * g->rows.size(), cudaMemcpyHostToDevice, st);
+  if (!g->device_prelim && g->N > 0) {   // the matrix, for the residual check
+    double* raw = (double*)(base + g->off_raw);
+    const size_t nb = sizeof(double) * (size_t)g->N;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(raw, g->ha.data(), nb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(raw + g->N, g->hb.data(), nb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(raw + 2 * g->N, g->hc.data(), nb, cudaMemcpyHostToDevice, st);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the host tables may be freed or reused after bind
   if (e != cudaSuccess) return cuda_fail(e);
   g->d_ws = base;
@@ -569,6 +619,36 @@ int dichotomy_gen_solve_series(dich_gen_t g, int64_t M, const double* d_F, int64
 
 int dichotomy_gen_solve(dich_gen_t g, const double* d_F, double* d_x, void* stream) {
   return dichotomy_gen_solve_series(g, 1, d_F, 0, d_x, 0, stream);
+}
+
+int dichotomy_gen_residual(dich_gen_t g, const double* d_F, const double* d_x, double* h_out, void* stream) {
+  if (!g || !h_out) return DICH_ERR_ARG;
+  if (!g->d_ws) return DICH_ERR_UNBOUND;
+  h_out[0] = h_out[1] = 0.0;
+  if (g->N == 0) return DICH_OK;
+  if (!d_F || !d_x || !aligned8(d_F) || !aligned8(d_x) || !is_device_ptr(d_F) || !is_device_ptr(d_x))
+    return DICH_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const double* raw = (const double*)(g->d_ws + g->off_raw);
+  unsigned long long* res = (unsigned long long*)(g->d_ws + g->off_res);
+  cudaError_t e = cudaMemsetAsync(res, 0, 3 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g->N, (int64_t)256), 4 * 1184));
+    k_gen_residual<<<grid, 256, 0, st>>>(g->N, raw, raw + g->N, raw + 2 * g->N, d_F, d_x, res);
+    e = cudaGetLastError();
+  }
+  unsigned long long m[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m, res, sizeof(m), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  double r, xm, fm;
+  std::memcpy(&r, &m[0], sizeof(double));
+  std::memcpy(&xm, &m[1], sizeof(double));
+  std::memcpy(&fm, &m[2], sizeof(double));
+  const double den = g->norm_inf * xm + fm;
+  h_out[0] = r;
+  h_out[1] = (den > 0.0) ? r / den : 0.0;
+  return DICH_OK;
 }
 
 int dichotomy_gen_status(dich_gen_t g, void* stream, int* device_status) {

@@ -14,7 +14,7 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import (FLAG_CHECK_FINITE, FLAG_DEVICE_PRELIM, FLAG_FORCE_GENERAL, FLAG_HOST_PRELIM, PREC_AUTO, PREC_F64, PREC_MIXED, DichotomyError,
+from ._lib import (FLAG_ALLOW_NOT_DOMINANT, FLAG_CHECK_FINITE, FLAG_DEVICE_PRELIM, FLAG_FORCE_GENERAL, FLAG_HOST_PRELIM, PREC_AUTO, PREC_F64, PREC_MIXED, DichotomyError,
                    check, make_opts)
 
 __all__ = [
@@ -23,7 +23,7 @@ __all__ = [
     "dichotomy_batch_prepare", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
     "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
     "dichotomy_batch_destroy", "Plan", "Batch", "GenPlan", "solve", "DichotomySolve", "DichotomySolveQuasi", "DichotomySolveBatched", "DichotomySolveBatchedQuasi",
-    "PREC_F64", "PREC_MIXED", "PREC_AUTO", "FLAG_FORCE_GENERAL", "FLAG_CHECK_FINITE", "FLAG_HOST_PRELIM", "FLAG_DEVICE_PRELIM", "DichotomyError",
+    "PREC_F64", "PREC_MIXED", "PREC_AUTO", "FLAG_FORCE_GENERAL", "FLAG_CHECK_FINITE", "FLAG_HOST_PRELIM", "FLAG_DEVICE_PRELIM", "FLAG_ALLOW_NOT_DOMINANT", "DichotomyError",
 ]
 
 
@@ -396,6 +396,13 @@ class GenPlan:
         check(_lib.load().dichotomy_gen_solve_series(self._h, int(F.shape[0]), pF, ldf, px, ldx, _stream(stream)),
               "dichotomy_gen_solve_series")
         return x
+
+    def residual(self, F: torch.Tensor, x: torch.Tensor, stream=None):
+        """The a posteriori check: (max |F - A x|, norm-wise backward error)."""
+        out = (ctypes.c_double * 2)()
+        check(_lib.load().dichotomy_gen_residual(self._h, _dev(F, "F"), _dev(x, "x"), out, _stream(stream)),
+              "dichotomy_gen_residual")
+        return float(out[0]), float(out[1])
 
     def status(self, stream=None) -> int:
         s = ctypes.c_int(0)

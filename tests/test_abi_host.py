@@ -237,12 +237,16 @@ def test_general_plan_validation_and_geometry_without_a_gpu():
     assert rc == 0 and info.path == 2
     rc, dinfo = gen(a, b, c)                                        # device preliminary: path known at bind
     assert rc == 0 and dinfo.path == 2 and dinfo.halo_l == 0 and dinfo.P == info.P
-    assert dinfo.workspace_bytes >= info.workspace_bytes + 24 * N
+    assert dinfo.workspace_bytes > info.workspace_bytes            # block composites, scan chunks
+    assert info.workspace_bytes >= 40 * N + 24 * N                   # factors and spikes, the matrix
+    assert info.growth == 1.0                                        # dominant: maps contract
     rc, info = gen(a[:1000], b[:1000], c[:1000])
     assert rc == 0 and (info.P - 1) * info.n + info.n_last == 1000
     bad = b.copy()
     bad[17] = 0.5 * (abs(a[17]) + abs(c[17]))
     assert gen(a, bad, c)[0] == 2                                   # a row without dominance
+    rc, info = gen(a, bad, c, flags=16 | 4)                         # ... accepted when waived
+    assert rc == 0 and info.growth >= 1.0
     z = b.copy()
     z[0] = 0.0
     assert gen(np.zeros(N), z, np.zeros(N))[0] == 3                 # zero row: singular

@@ -174,3 +174,84 @@ def test_general_series(D):
     assert plan.status() == 0
     for k in range(M):
         assert rel(X[k], oracle.thomas_tridiag(a, b, c, F[k])) < TOL
+
+
+def host_residual(a, b, c, F, x):
+    """max |F - A x| and the norm-wise backward error, computed on the host (the definition)."""
+    ax = b * x
+    ax[1:] += a[1:] * x[:-1]
+    ax[:-1] += c[:-1] * x[1:]
+    r = np.max(np.abs(F - ax))
+    nA = np.max(np.abs(np.r_[0.0, a[1:]]) + np.abs(b) + np.abs(np.r_[c[:-1], 0.0]))
+    return r, r / (nA * np.max(np.abs(x)) + np.max(np.abs(F)))
+
+
+@pytest.mark.parametrize("prelim", [HOST, DEVICE])
+def test_residual_check_on_dominant_matrices(D, prelim):
+    N = 300001
+    a, b, c = dominant(N, 21)
+    F = np.random.default_rng(22).standard_normal(N)
+    plan = D.GenPlan(a, b, c, flags=prelim)
+    Fd = torch.from_numpy(F).cuda()
+    xd = plan.solve(Fd)
+    r, be = plan.residual(Fd, xd)
+    rh, beh = host_residual(a, b, c, F, xd.cpu().numpy())
+    # both residuals carry FP64 rounding of their own (different orders): agree to ~4 ulp of the scale
+    assert abs(be - beh) <= 1e-15 + 1e-3 * beh and be < 1e-15 and plan.info["growth"] == 1.0
+
+
+@pytest.mark.parametrize("prelim", [HOST, DEVICE])
+@pytest.mark.parametrize("N", [5000, 300001])
+def test_not_dominant_spd_matrices_with_a_posteriori_check(D, N, prelim):
+    """Symmetric positive definite tridiagonal matrices A = L L^T (L lower bidiagonal) are mostly
+    not diagonally dominant; with the dominance check waived the solve is compared with LAPACK's
+    banded LU with partial pivoting (scipy) and judged by its own residual check (the a posteriori
+    check recommended after eq. 33)."""
+    linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(N + 23)
+    d, e = rng.uniform(1.0, 2.0, N), rng.uniform(-1.0, 1.0, N)
+    b = d * d + np.r_[0.0, e[1:] ** 2]
+    off = e[1:] * d[:-1]                       # A[i, i-1] = A[i-1, i]
+    a, c = np.r_[0.0, off], np.r_[off, 0.0]
+    assert np.any(np.abs(b) < np.abs(a) + np.abs(c))    # some rows lose dominance
+    F = rng.standard_normal(N)
+    with pytest.raises(D.DichotomyError):
+        D.GenPlan(a, b, c, flags=prelim)
+    plan = D.GenPlan(a, b, c, flags=prelim | D.FLAG_ALLOW_NOT_DOMINANT)
+    Fd = torch.from_numpy(F).cuda()
+    xd = plan.solve(Fd)
+    assert plan.status() == 0 and plan.info["growth"] >= 1.0
+    ab = np.zeros((3, N))
+    ab[0, 1:] = c[:-1]
+    ab[1] = b
+    ab[2, :-1] = a[1:]
+    ref = linalg.solve_banded((1, 1), ab, F)
+    x = xd.cpu().numpy()
+    r, be = plan.residual(Fd, xd)
+    rh, beh = host_residual(a, b, c, F, x)
+    assert abs(be - beh) <= 1e-15 + 1e-3 * beh
+    assert be < 1e-13, (be, plan.info)
+    assert rel(x, ref) < 1e-10, plan.info
+
+
+def test_residual_check_reports_what_it_sees(D):
+    """A non-dominant matrix with oscillating rows: whatever the solve returns, the residual check
+    agrees with the residual computed on the host."""
+    N = 20000
+    rng = np.random.default_rng(25)
+    a, c = rng.uniform(-1, 1, N), rng.uniform(-1, 1, N)
+    b = rng.uniform(0.2, 1.5, N) * rng.choice([-1.0, 1.0], N)
+    F = rng.standard_normal(N)
+    try:
+        plan = D.GenPlan(a, b, c, flags=HOST | D.FLAG_ALLOW_NOT_DOMINANT)
+    except D.DichotomyError as err:     # a zero pivot in some block: refused as singular
+        assert err.code == 3
+        return
+    Fd = torch.from_numpy(F).cuda()
+    xd = plan.solve(Fd)
+    x = xd.cpu().numpy()
+    if not np.all(np.isfinite(x)):
+        return
+    r, be = plan.residual(Fd, xd)
+    rh, beh = host_residual(a, b, c, F, x)
+    assert abs(be - beh) <= 1e-15 + 1e-3 * beh and plan.info["growth"] >= 1.0
