@@ -193,6 +193,12 @@ int dichotomy_solve_host(dich_plan_t plan, const double* h_F, double* h_x, doubl
 int dichotomy_adjoint(dich_plan_t plan, const double* d_w, const double* d_x, double* d_gF,
                       double* d_gt, void* stream);
 
+/* A posteriori check of a solution (as dichotomy_gen_residual): h_out[0] = max_i |F_i - (T x)_i|,
+ * h_out[1] = max|F - T x| / (||T||_inf max|x| + max|F|), with the corners of eq. 21 for
+ * quasi-Toeplitz plans.  d_F, d_x: N doubles on the device; h_out: 2 doubles on the host.
+ * Synchronizes `stream`.  Errors: DICH_ERR_ARG, DICH_ERR_UNBOUND, DICH_ERR_CUDA. */
+int dichotomy_residual(dich_plan_t plan, const double* d_F, const double* d_x, double* h_out, void* stream);
+
 /* Synchronize `stream`, read and clear the device status word of a bound plan.
  * *device_status receives DICH_OK or the first latched device error. */
 int dichotomy_status(dich_plan_t plan, void* stream, int* device_status);

@@ -27,7 +27,7 @@ FLAG_FORCE_GENERAL, FLAG_CHECK_FINITE, FLAG_HOST_PRELIM, FLAG_DEVICE_PRELIM, FLA
 
 EXPORTS = [
     "dichotomy_plan", "dichotomy_plan_ex", "dichotomy_plan_quasi", "dichotomy_plan_info", "dichotomy_plan_workspace_bytes",
-    "dichotomy_plan_bind", "dichotomy_solve", "dichotomy_solve_series", "dichotomy_solve_host", "dichotomy_adjoint", "dichotomy_status", "dichotomy_destroy",
+    "dichotomy_plan_bind", "dichotomy_solve", "dichotomy_solve_series", "dichotomy_solve_host", "dichotomy_adjoint", "dichotomy_residual", "dichotomy_status", "dichotomy_destroy",
     "dichotomy_solve_noalloc",
     "dichotomy_batch_prepare", "dichotomy_batch_prepare_quasi", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
     "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
             "dichotomy_solve_series": ([P, c_int64, P, c_int64, P, c_int64, P], I),
             "dichotomy_solve_host": ([P, P, P, P, P, c_int32, P], I),
             "dichotomy_adjoint": ([P, P, P, P, P, P], I),
+            "dichotomy_residual": ([P, P, P, ctypes.POINTER(c_double), P], I),
             "dichotomy_status": ([P, P, ctypes.POINTER(I)], I),
             "dichotomy_destroy": ([P], None),
             "dichotomy_solve_noalloc": ([c_double, c_double, c_double, c_int64, P, P, P], I),

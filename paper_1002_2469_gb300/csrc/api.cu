@@ -656,6 +656,7 @@ int dichotomy_plan_info(dich_plan_t p, dich_plan_info* info) {
   info->ib = rt.ib;
   info->z = rt.z;
   info->workspace_bytes = p->ws_bytes;
+  info->growth = 1.0;   // dominant Toeplitz matrices: every block map contracts
   if (p->path == PATH_GENERAL) {
     info->beta_offset = p->off_beta;
     info->iface_offset = p->off_iface;
@@ -913,6 +914,36 @@ int dichotomy_adjoint(dich_plan_t p, const double* d_w, const double* d_x, doubl
   cudaError_t e = cudaMemcpyAsync(d_gt + 3, d_gt + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_gt + 4, d_gt + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
   return e == cudaSuccess ? DICH_OK : cuda_fail(e);
+}
+
+int dichotomy_residual(dich_plan_t p, const double* d_F, const double* d_x, double* h_out, void* stream) {
+  if (!p || !h_out) return DICH_ERR_ARG;
+  if (!p->d_ws) return DICH_ERR_UNBOUND;
+  h_out[0] = h_out[1] = 0.0;
+  if (p->N == 0) return DICH_OK;
+  if (!d_F || !d_x || !aligned8(d_F) || !aligned8(d_x) || !is_device_ptr(d_F) || !is_device_ptr(d_x))
+    return DICH_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  // three maxima in the status region's spare bytes (the status word is its first 4 bytes)
+  unsigned long long* res = (unsigned long long*)(p->d_ws + p->off_status + 64);
+  const double t0 = (p->corners && p->N == 1) ? p->fwd.rec.t0 : p->t0;
+  cudaError_t e = launch_toeplitz_residual(p->N, p->tm1, t0, p->tp1, p->quasi ? p->psi : 0.0,
+                                           p->quasi ? p->chi : 0.0, d_F, d_x, res, st);
+  unsigned long long m[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m, res, sizeof(m), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  double r, xm, fm;
+  std::memcpy(&r, &m[0], sizeof(double));
+  std::memcpy(&xm, &m[1], sizeof(double));
+  std::memcpy(&fm, &m[2], sizeof(double));
+  double nA = std::fabs(p->tm1) + std::fabs(p->t0) + std::fabs(p->tp1);
+  if (p->quasi) nA = std::max({nA, std::fabs(p->t0 + p->psi) + std::fabs(p->tp1), std::fabs(p->tm1) + std::fabs(p->t0 + p->chi)});
+  if (p->N == 1) nA = std::fabs(t0);
+  const double den = nA * xm + fm;
+  h_out[0] = r;
+  h_out[1] = (den > 0.0) ? r / den : 0.0;
+  return DICH_OK;
 }
 
 int dichotomy_status(dich_plan_t p, void* stream, int* device_status) {

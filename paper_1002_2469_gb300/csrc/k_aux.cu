@@ -517,6 +517,44 @@ cudaError_t launch_corner_adjoint_batch(const CornerRec* recs, int64_t nsys, con
   return cudaGetLastError();
 }
 
+// residual check of a (quasi-)Toeplitz system: max |F - A x|, max |x|, max |F| as bits of
+// non-negative doubles in res[0..2] (zeroed here first)
+__global__ void __launch_bounds__(256) k_toeplitz_residual(int64_t N, double tm1, double t0, double tp1, double psi,
+                                                           double chi, const double* F, const double* x,
+                                                           unsigned long long* res) {
+  double r = 0.0, xm = 0.0, fm = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double d = t0;
+    if (i == 0) d += psi;
+    if (i == N - 1) d += chi;
+    double ax = d * x[i];
+    if (i > 0) ax = fma(tm1, x[i - 1], ax);
+    if (i + 1 < N) ax = fma(tp1, x[i + 1], ax);
+    r = fmax(r, fabs(F[i] - ax));
+    xm = fmax(xm, fabs(x[i]));
+    fm = fmax(fm, fabs(F[i]));
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    r = fmax(r, __shfl_xor_sync(0xffffffffu, r, d));
+    xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, d));
+    fm = fmax(fm, __shfl_xor_sync(0xffffffffu, fm, d));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&res[0], (unsigned long long)__double_as_longlong(r));
+    atomicMax(&res[1], (unsigned long long)__double_as_longlong(xm));
+    atomicMax(&res[2], (unsigned long long)__double_as_longlong(fm));
+  }
+}
+
+cudaError_t launch_toeplitz_residual(int64_t N, double tm1, double t0, double tp1, double psi, double chi,
+                                     const double* F, const double* x, unsigned long long* res, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(res, 0, 3 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)max((int64_t)1, min((N + 255) / 256, (int64_t)4 * 1184));
+  k_toeplitz_residual<<<grid, 256, 0, st>>>(N, tm1, t0, tp1, psi, chi, F, x, res);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_corner_adjoint(const double* xf, double* lam, double* gt, const CornerArgs& c, cudaStream_t st) {
   if (c.N <= 0) return cudaSuccess;
   k_corner_adj<<<1, 256, 0, st>>>(xf, lam, c, gt);

@@ -66,6 +66,9 @@ struct CornerRec {
 // x <- A_s^-1 F_s from y_s = T_s^-1 F_s (already in x) for every listed system: one CTA each
 cudaError_t launch_corner_batch(const CornerRec* recs, int64_t n, const double* tab, double* x, cudaStream_t st);
 
+// residual check of one (quasi-)Toeplitz system (res: 3 maxima, zeroed first)
+cudaError_t launch_toeplitz_residual(int64_t N, double tm1, double t0, double tp1, double psi, double chi,
+                                     const double* F, const double* x, unsigned long long* res, cudaStream_t st);
 // adjoint of a batch with quasi-Toeplitz systems: recs are the transposed corner records of every
 // system; gt3 the Toeplitz gradients (3 per system), gt5 the result (5 per system)
 cudaError_t launch_corner_adjoint_batch(const CornerRec* recs, int64_t nsys, const double* tab, const double* xf,

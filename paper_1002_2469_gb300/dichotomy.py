@@ -294,6 +294,13 @@ class Plan:
         dichotomy_adjoint(self._h, w, x, gF, gt, stream)
         return gF, gt
 
+    def residual(self, F: torch.Tensor, x: torch.Tensor, stream=None):
+        """The a posteriori check: (max |F - A x|, norm-wise backward error)."""
+        out = (ctypes.c_double * 2)()
+        check(_lib.load().dichotomy_residual(self._h, _dev(F, "F"), _dev(x, "x"), out, _stream(stream)),
+              "dichotomy_residual")
+        return float(out[0]), float(out[1])
+
     def status(self, stream=None) -> int:
         return dichotomy_status(self._h, stream)
 

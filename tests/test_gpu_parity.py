@@ -317,6 +317,32 @@ def test_quasi_toeplitz_adjoint(D, t, psi, chi, N, prec, flags):
     assert np.all(np.abs(g[3:] - g_ref[3:]) <= TOL * scale), (g, g_ref)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("t,psi,chi,N", [((-1.2, 2.5, -0.8), 0.0, 0.0, 300001), ((-1.0, 2.5, -1.0), -1.0, -0.5, 70001),
+                                         ((-1.0, 4.0, -1.0), 0.5, 0.25, 1), ((0.7, 2.5, -1.1), 0.0, 0.9, 2)])
+def test_residual_check(D, t, psi, chi, N, prec):
+    """The a posteriori check of a Toeplitz or quasi-Toeplitz solve against the residual computed
+    on the host from the definition of the matrix (eq. 21 for the corners)."""
+    F = np.random.default_rng(N).standard_normal(N)
+    plan = D.Plan(*t, N, precision=prec, psi=psi, chi=chi)
+    Fd = torch.from_numpy(F).cuda()
+    xd = plan.solve(Fd)
+    r, be = plan.residual(Fd, xd)
+    x = xd.cpu().numpy()
+    d = np.full(N, t[1])
+    d[0] += psi
+    d[-1] += chi
+    ax = d * x
+    ax[1:] += t[0] * x[:-1]
+    ax[:-1] += t[2] * x[1:]
+    rh = np.max(np.abs(F - ax))
+    nA = max(abs(t[0]) + abs(t[1]) + abs(t[2]), abs(t[1] + psi) + abs(t[2]), abs(t[0]) + abs(t[1] + chi))
+    if N == 1:
+        nA = abs(t[1] + psi + chi)
+    beh = rh / (nA * np.max(np.abs(x)) + np.max(np.abs(F)))
+    assert abs(be - beh) <= 1e-15 + 1e-3 * beh and be < (1e-15 if prec == 0 else 1e-13)
+
+
 def test_trivial_sizes(D):
     for N in (0, 1, 2):
         F = np.arange(1, N + 1, dtype=np.float64)
