@@ -438,7 +438,8 @@ def other_configs(D, W, oracle, stream, world, steps=10):
     torch.cuda.empty_cache()
 
     # C1: tridiag{-1, 4, -1}, N = 65536 (1 MB in, 1 MB out): latency of one solve, three
-    # buffer sets in rotation, many back-to-back solves between two events
+    # buffer sets in rotation, back-to-back solves between two events (replays of a CUDA graph;
+    # the loop of Python calls is reported beside it)
     t1, F1 = W.single_c1()
     sets = [(torch.from_numpy(F1 * (1.0 + 0.1 * k)).cuda(), torch.empty(F1.size, dtype=torch.float64, device="cuda"))
             for k in range(3)]
@@ -446,11 +447,26 @@ def other_configs(D, W, oracle, stream, world, steps=10):
     for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
         plan = D.Plan(*t1, F1.size, precision=prec)
         reps = 300
-        us = 1e3 * _time_batch(lambda: [plan.solve(Fk, out=xk) for Fk, xk in sets], reps, world, stream) / 3
+        us_host = 1e3 * _time_batch(lambda: [plan.solve(Fk, out=xk) for Fk, xk in sets], reps, world, stream) / 3
+        # device latency: 90 solves captured in one CUDA graph, replayed between two events (the
+        # Python call overhead of each solve is then off the timeline)
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for Fk, xk in sets:
+                plan.solve(Fk, out=xk)
+        torch.cuda.current_stream().wait_stream(side)
+        with torch.cuda.graph(graph):
+            for _ in range(30):
+                for Fk, xk in sets:
+                    plan.solve(Fk, out=xk)
+        us = 1e3 * _time_batch(graph.replay, 10, world, stream) / 90
         err = max(float(np.max(np.abs(xk.cpu().numpy() - oracle.thomas(t1, Fk.cpu().numpy())))
                         / np.max(np.abs(oracle.thomas(t1, Fk.cpu().numpy())))) for Fk, xk in sets)
-        c1[name] = {"us_per_solve": round(us, 2), "Gunknowns_s": round(F1.size / us / 1e3, 2), "windows": plan.info["tiles"],
-                    "rel_err": err}
+        c1[name] = {"us_per_solve": round(us, 2), "us_per_solve_python_loop": round(us_host, 2),
+                    "Gunknowns_s": round(F1.size / us / 1e3, 2), "windows": plan.info["tiles"], "rel_err": err}
+        del graph
     out["c1_latency_65536"] = c1
     del sets
 

@@ -10,8 +10,17 @@ static cudaError_t launch_one(int grid, int grid_y, size_t smem, cudaStream_t st
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_window<NT><<<dim3(grid, grid_y), NT, smem, st>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, grid_y);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_window<NT>, a);
 }
 
 cudaError_t launch_window_f64(int NT, int grid, size_t smem, cudaStream_t st, const WinArgs& a, int grid_y) {

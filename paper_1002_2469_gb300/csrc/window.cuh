@@ -130,6 +130,9 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   constexpr int NW = NT / 32;
   constexpr int LD = NT + 1;
   extern __shared__ __align__(16) double sm[];
+  // launched with programmatic stream serialization: this grid may start while the previous
+  // kernel of the stream finishes; nothing is read or written before that kernel has completed
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int ns = A.n_smem;
   double* S = sm;
@@ -310,6 +313,8 @@ __global__ void __launch_bounds__(NT) k_window(const WinArgs A) {
   scr[tid] = XR;
   __syncthreads();
 
+  // the next kernel of the stream may begin its launch (it waits for this grid to complete)
+  asm volatile("griddepcontrol.launch_dependents;");
   // ---------------------------------------------------------------- correction + store (a3)
   const bool adj = (A.xf != nullptr);
   double g0 = 0.0, gm = 0.0, gp = 0.0;

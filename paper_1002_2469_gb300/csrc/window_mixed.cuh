@@ -157,6 +157,9 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   constexpr int LD = 2 * NT + 2;   // shared row stride in doubles (even: 16-byte pairs)
   using O = OpsFF;
   extern __shared__ __align__(16) double sm[];
+  // launched with programmatic stream serialization: this grid may start while the previous
+  // kernel of the stream finishes; nothing is read or written before that kernel has completed
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int ns = A.n_smem;
   double* S = sm;
@@ -467,6 +470,8 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
                                   wscale);
   __syncthreads();
 
+  // the next kernel of the stream may begin its launch (it waits for this grid to complete)
+  asm volatile("griddepcontrol.launch_dependents;");
   // ---------------------------------------------------------------- coalesced store of the own rows
   const bool adj = (A.xf != nullptr);
   double g0 = 0.0, gm = 0.0, gp = 0.0;
