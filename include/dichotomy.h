@@ -70,8 +70,11 @@ enum {
   DICH_FLAG_CHECK_FINITE = 2,   /* latch DICH_ERR_NONFINITE if any output is not finite */
   DICH_FLAG_HOST_PRELIM = 4,    /* general matrices: preliminary step on the host at plan time */
   DICH_FLAG_DEVICE_PRELIM = 8,  /* general matrices: preliminary step on the device at bind time */
-  DICH_FLAG_ALLOW_NOT_DOMINANT = 16  /* general matrices: accept rows without diagonal dominance; judge
-                                        the result by dich_plan_info.growth and dichotomy_gen_residual */
+  DICH_FLAG_ALLOW_NOT_DOMINANT = 16  /* accept matrices without diagonal dominance.  Toeplitz plans and
+                                        batches: when the roots of t_1 r^2 + t_0 r + t_-1 are real and
+                                        separated by the unit circle (what the recurrences need);
+                                        general matrices: any rows, judged by dich_plan_info.growth;
+                                        check results with dichotomy_residual / dichotomy_gen_residual */
 };
 
 typedef struct {

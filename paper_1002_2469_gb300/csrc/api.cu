@@ -54,13 +54,19 @@ int default_threads(int form) { return form == FORM_F64 ? 64 : 128; }
 // several CTAs share an SM so loads, sweeps, tree and stores of different windows overlap)
 int default_rows(int form) { return form == FORM_F64 ? 64 : 16; }
 
-int validate_t(double tm1, double t0, double tp1) {
+int validate_t(double tm1, double t0, double tp1, int flags) {
   if (!std::isfinite(tm1) || !std::isfinite(t0) || !std::isfinite(tp1)) return DICH_ERR_ARG;
-  if (t0 == 0.0) return (tm1 == 0.0 && tp1 == 0.0) ? DICH_ERR_SINGULAR : DICH_ERR_NOT_DOMINANT;
+  if (t0 == 0.0 && tm1 == 0.0 && tp1 == 0.0) return DICH_ERR_SINGULAR;
   const double off = std::fabs(tm1) + std::fabs(tp1);
   // eq. 32-33: |b| >= |a| + |c| (equality accepted: the end rows are then strict)
-  if (std::fabs(t0) < off * (1.0 - 4.0 * DBL_EPSILON)) return DICH_ERR_NOT_DOMINANT;
-  return DICH_OK;
+  if (t0 != 0.0 && std::fabs(t0) >= off * (1.0 - 4.0 * DBL_EPSILON)) return DICH_OK;
+  // without dominance, on request: what the two recurrences need is real roots of
+  // t_1 r^2 + t_0 r + t_-1 = 0 separated by the unit circle (|rs| < 1 < |1/ib|)
+  if (!(flags & DICH_FLAG_ALLOW_NOT_DOMINANT)) return DICH_ERR_NOT_DOMINANT;
+  if (t0 * t0 - 4.0 * tm1 * tp1 <= 0.0) return DICH_ERR_NOT_DOMINANT;
+  const Roots r = toeplitz_roots(tm1, t0, tp1);
+  const double lim = 1.0 - 1e-12;
+  return (r.ok && std::fabs(r.rs) < lim && std::fabs(r.ib) < lim) ? DICH_OK : DICH_ERR_NOT_DOMINANT;
 }
 
 int read_opts(const dich_opts* o, Opts& out) {
@@ -359,9 +365,11 @@ static int corner_build(double t_m1, double t_0, double t_1, double psi, double 
 }
 
 // the end rows of eq. 21 must keep dominance (eq. 32-33; the interior rows are T's)
-static int corner_check(double t_m1, double t_0, double t_1, double psi, double chi, int64_t N) {
+static int corner_check(double t_m1, double t_0, double t_1, double psi, double chi, int64_t N, int flags) {
   if (!std::isfinite(psi) || !std::isfinite(chi)) return DICH_ERR_ARG;
-  if (N >= 2) {
+  if (N >= 2 && (flags & DICH_FLAG_ALLOW_NOT_DOMINANT)) {   // only a zero corner pivot is refused here
+    if (t_0 + psi == 0.0 || t_0 + chi == 0.0) return DICH_ERR_SINGULAR;
+  } else if (N >= 2) {
     const double tol = 1.0 - 4.0 * DBL_EPSILON;
     if (std::fabs(t_0 + psi) < std::fabs(t_1) * tol || std::fabs(t_0 + chi) < std::fabs(t_m1) * tol)
       return DICH_ERR_NOT_DOMINANT;
@@ -527,7 +535,7 @@ int dichotomy_plan_ex(double t_m1, double t_0, double t_1, int64_t N, const dich
   Opts o;
   int rc = read_opts(opts, o);
   if (rc) return rc;
-  rc = validate_t(t_m1, t_0, t_1);
+  rc = validate_t(t_m1, t_0, t_1, o.flags);
   if (rc) return rc;
   dich_plan_s* p = new (std::nothrow) dich_plan_s();
   if (!p) return DICH_ERR_ARG;
@@ -601,7 +609,7 @@ int dichotomy_plan_quasi(double t_m1, double t_0, double t_1, double psi, double
                          const dich_opts* opts, dich_plan_t* out) {
   if (!out) return DICH_ERR_ARG;
   *out = nullptr;
-  int rc = corner_check(t_m1, t_0, t_1, psi, chi, N);
+  int rc = corner_check(t_m1, t_0, t_1, psi, chi, N, opts ? opts->flags : 0);
   if (rc) return rc;
   dich_plan_t p = nullptr;
   rc = dichotomy_plan_ex(t_m1, t_0, t_1, N, opts, &p);
@@ -1045,7 +1053,7 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
       delete b;
       return DICH_ERR_ARG;
     }
-    rc = validate_t(h_tm1[s], h_t0[s], h_tp1[s]);
+    rc = validate_t(h_tm1[s], h_t0[s], h_tp1[s], o.flags);
     if (rc) {
       delete b;
       return rc;
@@ -1248,7 +1256,7 @@ int dichotomy_batch_prepare_quasi(int64_t nsys, const int64_t* h_N, const int64_
   // one-row systems read t_0 + psi + chi (and have no off-diagonal entries)
   std::vector<double> tm1e(h_tm1, h_tm1 + nsys), t0e(h_t0, h_t0 + nsys), tp1e(h_tp1, h_tp1 + nsys);
   for (int64_t s = 0; s < nsys; ++s) {
-    const int rc = corner_check(h_tm1[s], h_t0[s], h_tp1[s], h_psi[s], h_chi[s], h_N[s]);
+    const int rc = corner_check(h_tm1[s], h_t0[s], h_tp1[s], h_psi[s], h_chi[s], h_N[s], opts ? opts->flags : 0);
     if (rc) return rc;
     if (h_N[s] == 1) {
       t0e[(size_t)s] = h_t0[s] + h_psi[s] + h_chi[s];

@@ -46,7 +46,7 @@ size_t smem_bytes(int NT, int n, int form);
 int max_rows(int NT, int form, size_t budget);
 int default_threads(int form);
 int default_rows(int form);
-int validate_t(double tm1, double t0, double tp1);
+int validate_t(double tm1, double t0, double tp1, int flags = 0);
 int read_opts(const dich_opts* o, Opts& out);
 int pick_form(int prec, const Roots& r);
 int64_t ceil_div(int64_t a, int64_t b);

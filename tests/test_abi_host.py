@@ -300,3 +300,25 @@ def test_quasi_batch_validation_without_a_gpu():
         D.dichotomy_batch_prepare(N, np.array([0, 1000, 1001]), tm1, t0, tp1, o, psi=np.array([np.nan, 0, 0]),
                                   chi=np.zeros(3))
     assert e.value.code == 1
+
+
+def test_toeplitz_without_dominance_needs_split_roots():
+    """Without dominance a Toeplitz plan is accepted only on request, and only when the roots of
+    t_1 r^2 + t_0 r + t_-1 are real and separated by the unit circle."""
+    from paper_1002_2469_gb300 import _lib as L
+    lib = L.load()
+
+    def plan(t, flags):
+        h = ctypes.c_void_p()
+        o = L.make_opts(flags=flags)
+        rc = lib.dichotomy_plan_ex(*t, 1000, ctypes.byref(o), ctypes.byref(h))
+        if rc == 0:
+            lib.dichotomy_destroy(h)
+        return rc
+
+    assert plan((1.0, 1.5, -1.0), 0) == 2            # |1.5| < 2: not dominant
+    assert plan((1.0, 1.5, -1.0), 16) == 0           # roots -0.5 and 2: split
+    assert plan((1.0, 0.3, -1.0), 16) == 0
+    assert plan((1.0, 1.0, 1.0), 16) == 2            # complex roots
+    assert plan((-1.0, 1.0, -1.0), 16) == 2          # roots on one side of the unit circle
+    assert plan((1.0, 0.0, 1.0), 16) == 2            # roots +-i

@@ -343,6 +343,31 @@ def test_residual_check(D, t, psi, chi, N, prec):
     assert abs(be - beh) <= 1e-15 + 1e-3 * beh and be < (1e-15 if prec == 0 else 1e-13)
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("t", [(1.0, 1.5, -1.0), (1.0, 0.3, -1.0), (0.5, -0.8, -1.0)])
+def test_toeplitz_without_dominance(D, t, prec):
+    """Matrices without diagonal dominance whose characteristic roots are real and split by the
+    unit circle, accepted with DICH_FLAG_ALLOW_NOT_DOMINANT: against LAPACK's banded LU with
+    partial pivoting (scipy; Thomas without pivoting is no reference here) and the residual check."""
+    linalg = pytest.importorskip("scipy.linalg")
+    N = 300001
+    F = np.random.default_rng(31).standard_normal(N)
+    with pytest.raises(D.DichotomyError):
+        D.Plan(*t, N, precision=prec)
+    plan = D.Plan(*t, N, precision=prec, flags=D.FLAG_ALLOW_NOT_DOMINANT)
+    Fd = torch.from_numpy(F).cuda()
+    xd = plan.solve(Fd)
+    assert plan.status() == 0
+    ab = np.zeros((3, N))
+    ab[0, 1:] = t[2]
+    ab[1] = t[1]
+    ab[2, :-1] = t[0]
+    ref = linalg.solve_banded((1, 1), ab, F)
+    assert rel(xd.cpu().numpy(), ref) < TOL, plan.info
+    r, be = plan.residual(Fd, xd)
+    assert be < (1e-15 if plan.info["precision"] == 0 else 1e-13)
+
+
 def test_trivial_sizes(D):
     for N in (0, 1, 2):
         F = np.arange(1, N + 1, dtype=np.float64)
