@@ -12,7 +12,11 @@
  *     rejected with DICH_ERR_ARG; the library has no CPU fallback.
  *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
  *     Solve/adjoint calls only enqueue work: they never synchronize, never allocate
- *     device memory and are safe to capture in a CUDA graph once the plan is bound.
+ *     device memory and are safe to capture in a CUDA graph once the plan is bound
+ *     (dichotomy_solve_host creates its two copy streams and events on first use; binds,
+ *     status reads and the residual checks synchronize).
+ *   - Plan and batch objects are not locked: calls on one object from several host threads
+ *     must be serialized by the caller; distinct objects are independent.
  *   - Device memory is owned by the caller.  The library owns only host-side plan
  *     objects (freed by dichotomy_destroy / dichotomy_batch_destroy).
  *   - Every function returns a dich_status (0 = DICH_OK).  Errors detected on the GPU
