@@ -587,7 +587,8 @@ def other_configs(D, W, oracle, stream, world, steps=10):
 
     # f4: a general tridiagonal matrix, N = 2^24: |a_i|, |c_i| <= 1 random, b_i = +-(|a_i| + |c_i| + U[0.3, 1.5]),
     # F ~ N(0, 1); the O(N) preliminary step (plan and bind: on the device by default, plan_s; on
-    # the host, plan_s_host_prelim), then FP64 solves on the device
+    # the host, plan_s_host_prelim), then solves on the device in the AUTO form (float-float here)
+    # and in the plain FP64 form
     Ng = 1 << 24
     rng = np.random.default_rng(1)
     ga, gc = rng.uniform(-1, 1, Ng), rng.uniform(-1, 1, Ng)
@@ -597,20 +598,24 @@ def other_configs(D, W, oracle, stream, world, steps=10):
     D.GenPlan(ga, gb, gc, flags=D.FLAG_HOST_PRELIM)
     plan_s_host = time.perf_counter() - t0_
     torch.cuda.empty_cache()
-    t0_ = time.perf_counter()
-    gplan = D.GenPlan(ga, gb, gc)
-    plan_s = time.perf_counter() - t0_
     gFd = torch.from_numpy(gF).cuda()
     gxd = torch.empty_like(gFd)
-    ms_g = _time_batch(lambda: gplan.solve(gFd, out=gxd), steps, world, stream)
-    gx = gxd.cpu().numpy()
     gref = oracle.thomas_tridiag(ga, gb, gc, gF)
-    out["f4_general_2e24"] = {"unknowns": Ng, "ms": round(ms_g, 4), "Gunknowns_s": round(Ng / ms_g / 1e6, 2),
-                              "hbm_GBs": round(56 * Ng / ms_g / 1e6, 1), "bytes_per_unknown": 56,
-                              "plan_s": round(plan_s, 3), "plan_s_host_prelim": round(plan_s_host, 3), "path": ["single", "halo", "general"][gplan.info["path"]],
-                              "block_size": gplan.info["n"], "form": "f64",
-                              "rel_err": float(np.max(np.abs(gx - gref)) / np.max(np.abs(gref)))}
-    del gplan, gFd, gxd
+    f4 = {"unknowns": Ng, "bytes_per_unknown": 56, "plan_s_host_prelim": round(plan_s_host, 3)}
+    for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
+        t0_ = time.perf_counter()
+        gplan = D.GenPlan(ga, gb, gc, precision=prec)
+        plan_s = time.perf_counter() - t0_
+        ms_g = _time_batch(lambda: gplan.solve(gFd, out=gxd), steps, world, stream)
+        gx = gxd.cpu().numpy()
+        f4[name] = {"ms": round(ms_g, 4), "Gunknowns_s": round(Ng / ms_g / 1e6, 2),
+                    "hbm_GBs": round(56 * Ng / ms_g / 1e6, 1), "plan_s": round(plan_s, 3),
+                    "path": ["single", "halo", "general"][gplan.info["path"]], "block_size": gplan.info["n"],
+                    "threads": gplan.info["threads"], "form": "mixed" if gplan.info["precision"] == 1 else "f64",
+                    "rel_err": float(np.max(np.abs(gx - gref)) / np.max(np.abs(gref)))}
+        del gplan
+    out["f4_general_2e24"] = f4
+    del gFd, gxd
     torch.cuda.empty_cache()
 
     # the paper's largest 2-D Poisson run (Table 1: 65536 x 65536, Stage 2 = the dichotomy process):

@@ -290,7 +290,10 @@ const char* dichotomy_version(void);
  * (super-diagonal), N entries each (copied; the caller keeps ownership).  opts as for
  * dichotomy_plan_ex; DICH_PREC_MIXED runs the local solves and the correction in float-float
  * (factors within 2^-40..2^40, else DICH_ERR_UNSUPPORTED -- from dichotomy_gen_bind with the
- * device preliminary); DICH_PREC_AUTO takes FP64, the faster form of this kernel on GB300.
+ * device preliminary); DICH_PREC_AUTO takes MIXED when the local recurrences' error gains
+ * stay below 24 (as for Toeplitz plans) and the factors are in range, else FP64.  Default
+ * geometry: 64-thread windows of 32-row blocks for FP64 plans, 128-thread windows of 16-row
+ * blocks for MIXED and AUTO plans.
  * Every row must satisfy |b_i| >= |a_i| + |c_i| (eq. 32-33) unless DICH_FLAG_ALLOW_NOT_DOMINANT
  * is set; then the block maps may grow (dich_plan_info.growth bounds the error growth a priori)
  * and dichotomy_gen_residual checks the solution a posteriori.  Errors: DICH_ERR_ARG (null, negative N, non-finite entry,

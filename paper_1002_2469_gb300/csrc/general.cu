@@ -123,7 +123,12 @@ struct dich_gen_s {
 
 namespace {
 
+// default geometry (measured on GB300 at N = 2^24): the FP64 kernel is bound by its FP64 pipe and
+// prefers 32-row blocks in 64-thread windows; the float-float kernel, bound by the latency of its
+// coefficient loads, prefers 16-row blocks in 128-thread windows (more warps per SM).  AUTO plans
+// take the float-float geometry, as they usually run in that form.
 constexpr int kGenDefaultRows = 32;
+constexpr int kGenDefaultRowsFF = 16;
 constexpr int64_t kGenDevicePrelimMin = 1 << 15;   // default: device preliminary from this many rows
 
 // block geometry (block size n, P blocks, the last one nlast rows); returns a status code
@@ -138,7 +143,7 @@ int gen_geometry(dich_gen_s* g, double b0) {
   const size_t budget = g->opts.n_req > 0 ? kSmemMax : kSmemBudget;
   int nmax = 2;
   while (window_gen_smem_bytes(NT, nmax + 1) <= budget) ++nmax;
-  const int n = choose_n(N, NT, nmax, g->opts.n_req, kGenDefaultRows);
+  const int n = choose_n(N, NT, nmax, g->opts.n_req, g->opts.prec == DICH_PREC_F64 ? kGenDefaultRows : kGenDefaultRowsFF);
   const int64_t P = ceil_div(N, n);
   r.n = n;
   r.P = P;
@@ -185,19 +190,18 @@ void gen_decide(dich_gen_s* g, double amax, double cmax) {
   g->tiles = ceil_div(P, (int64_t)r.own);
 }
 
-// precision form.  MIXED (asked for explicitly) needs the factors within 2^-40..2^40 for its float
-// range; its error grows with the error gains of the two recurrences, gf (largest
-// 1 + |a_i rd_i| gf_{i-1} over the rows of a block) and gb (largest 1 + |cp_i| gb_{i+1}), which for
-// a Toeplitz matrix are 1/(1 - |rs|) and 1/(1 - |ib|).  AUTO takes FP64: with one block per thread
-// and FP64 beta and tree, the float-float form of this kernel runs slower than the FP64 one.
+// precision form.  MIXED needs the factors within 2^-40..2^40 for its float range; its error grows
+// with the error gains of the two recurrences, gf (largest 1 + |a_i rd_i| gf_{i-1} over the rows
+// of a block) and gb (largest 1 + |cp_i| gb_{i+1}), which for a Toeplitz matrix are 1/(1 - |rs|)
+// and 1/(1 - |ib|): AUTO takes MIXED while gf + gb <= 24, as the Toeplitz policy does.
 int gen_choose_form(dich_gen_s* g, double gf, double gb, double rmax, double rmin, double omax) {
   const double big = 1099511627776.0;   // 2^40
   const bool range = rmax <= big && rmin >= 1.0 / big && omax <= big;
-  (void)gf;
-  (void)gb;
   g->form = FORM_F64;
   if (g->opts.prec == DICH_PREC_MIXED) {
     if (!range) return DICH_ERR_UNSUPPORTED;
+    g->form = FORM_MIXED;
+  } else if (g->opts.prec == DICH_PREC_AUTO && range && gf + gb <= 24.0) {
     g->form = FORM_MIXED;
   }
   return DICH_OK;
@@ -510,7 +514,7 @@ int dichotomy_gen_plan(int64_t N, const double* h_a, const double* h_b, const do
   if (!g) return DICH_ERR_ARG;
   g->N = N;
   g->opts = o;
-  g->NT = o.NT ? o.NT : 64;
+  g->NT = o.NT ? o.NT : (o.prec == DICH_PREC_F64 ? 64 : 128);
   g->norm_inf = norm_inf;
   if (N >= 1) {
     rc = gen_geometry(g, h_b[0]);

@@ -255,7 +255,10 @@ def test_general_plan_validation_and_geometry_without_a_gpu():
     assert gen(a, nan, c)[0] == 1
     rc, info = gen(a, b, c, precision=1, flags=4)                   # MIXED (float-float rows)
     assert rc == 0 and info.precision == 1
-    rc, info = gen(a, b, c, precision=2, flags=4)                   # AUTO: the faster FP64 form
+    rc, info = gen(a, b, c, precision=2, flags=4)                   # AUTO: strongly dominant -> MIXED
+    assert rc == 0 and info.precision == 1 and info.n == 16 and info.threads == 128
+    wb = np.abs(a) + np.abs(c) + 1e-6                               # weakly dominant: AUTO -> FP64
+    rc, info = gen(a, wb, c, precision=2, flags=4)
     assert rc == 0 and info.precision == 0
     rc, info = gen(a * 1e30, b * 1e30, c * 1e30, precision=1, flags=4)   # factors beyond 2^40: refused
     assert rc == 11

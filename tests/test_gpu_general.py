@@ -50,7 +50,7 @@ def test_general_random_dominant(D, N, prelim, prec):
     F = np.random.default_rng(N + 1).standard_normal(N)
     x, info = gen_solve(D, a, b, c, F, flags=prelim, precision=prec)
     if N > 1:
-        assert info["precision"] == (1 if prec == 1 else 0)   # AUTO takes the (faster) FP64 form
+        assert info["precision"] == (1 if prec else 0)   # strongly dominant: AUTO takes MIXED
     assert rel(x, oracle.thomas_tridiag(a, b, c, F)) < TOL, info
 
 
