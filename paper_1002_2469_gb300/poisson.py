@@ -32,13 +32,26 @@ __all__ = ["dst1", "mode_t0", "Poisson2D"]
 
 def dst1(a: torch.Tensor, dim: int = 0) -> torch.Tensor:
     """Orthonormal DST-I along `dim`: X_k = sqrt(2 / (M + 1)) sum_j a_j sin(pi j k / (M + 1)),
-    j, k = 1..M.  It is its own inverse.  With a zero-padded to 2 (M + 1) points (a_j at
-    position j, j = 1..M), the real FFT gives Y_k = sum_j a_j exp(-i pi j k / (M + 1)), so the
-    sine sum is -Im(Y_k)."""
-    M = a.shape[dim]
-    pad = torch.nn.functional.pad(a.movedim(dim, -1), (1, 0)).movedim(-1, dim)    # a_j at position j
-    Y = torch.fft.rfft(pad, n=2 * (M + 1), dim=dim)
-    return (Y.imag.narrow(dim, 1, M) * (-math.sqrt(2.0 / (M + 1)))).contiguous()
+    j, k = 1..M.  It is its own inverse.  One real FFT of length N = M + 1 (half the padded
+    length): with a_0 = a_N = 0, y_j = sin(pi j / N) (a_j + a_{N-j}) + (a_j - a_{N-j}) / 2 has
+    C_k - i S_k = sum_j y_j exp(-2 pi i j k / N) with S_k = X_{2k} (the antisymmetric part) and
+    C_k = X_{2k+1} - X_{2k-1} (the symmetric part, by the product-to-sum identity), so the odd
+    outputs are the running sums X_{2k+1} = C_0 / 2 + C_1 + ... + C_k."""
+    x = a.movedim(dim, -1)
+    M = x.shape[-1]
+    N = M + 1
+    z = torch.zeros(x.shape[:-1] + (1,), dtype=x.dtype, device=x.device)
+    xp = torch.cat([z, x], dim=-1)                       # a_j, j = 0..N-1
+    xr = torch.cat([z, x.flip(-1)], dim=-1)              # a_{N-j}
+    s = torch.sin(torch.arange(N, dtype=x.dtype, device=x.device) * (math.pi / N))
+    y = s * (xp + xr) + 0.5 * (xp - xr)
+    Y = torch.fft.rfft(y, dim=-1)
+    out = torch.empty_like(x)
+    out[..., 1::2] = -Y.imag[..., 1:1 + M // 2]            # X_{2m}, m = 1..M/2
+    C = Y.real
+    odd = torch.cumsum(C, dim=-1) - 0.5 * C[..., :1]       # X_{2m+1}, m = 0..(M-1)/2
+    out[..., 0::2] = odd[..., :(M + 1) // 2]
+    return (out * math.sqrt(2.0 / N)).movedim(-1, dim).contiguous()
 
 
 def mode_t0(M: int) -> np.ndarray:
