@@ -11,7 +11,10 @@
 //      kPreChunk blocks (chunk products, a one-CTA pass over the chunks, chunk-local scans), every
 //      partial product rescaled by a power of two (ratios are unchanged, nothing overflows);
 //   3. per block: from the incoming cp_{s-1} and cq_{e+1}, the block's exterior ratios, block maps
-//      and 2x2 beta map (the record of the dichotomy tree), and the largest |a|, |c| map factors.
+//      and 2x2 beta map (the record of the dichotomy tree), and the largest |a|, |c| map factors;
+//      step 1 also records what the precision choice needs (the error gains of the two local
+//      recurrences, the range of the factors), and for the float-float form the tables are then
+//      rewritten as (hi, lo) pairs in place (k_pre_to_ff).
 #pragma once
 #include "window_gen.cuh"
 

@@ -1,6 +1,8 @@
-// general.cu -- general (non-Toeplitz) tridiagonal systems: the O(N) preliminary step of the
-// Dichotomy Algorithm on the host (Sec. 2.3) and the solve by the window kernel of
-// window_gen.cuh, behind the dichotomy_gen_* entry points of include/dichotomy.h.
+// general.cu -- general (non-Toeplitz) tridiagonal systems behind the dichotomy_gen_* entry
+// points of include/dichotomy.h: the O(N) preliminary step of the Dichotomy Algorithm (Sec. 2.3)
+// on the host at plan time or on the device at bind time (gen_prelim.cuh), the choice of the
+// precision form and of the path, the solves by the window kernels of window_gen.cuh (FP64 or
+// float-float), and the a posteriori residual check for matrices without dominance.
 //
 // Preliminary step, in the terms of the Toeplitz restatement (exterior ratios and block maps
 // from the homogeneous solutions phi, vanishing left of row 0, and psi, vanishing right of row

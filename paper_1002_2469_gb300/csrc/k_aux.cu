@@ -1,5 +1,6 @@
 // k_aux.cu -- general-path block scan, adjoint gradient finalisation, one-row systems,
-// quasi-Toeplitz corner correction.
+// quasi-Toeplitz corner corrections (single plans and batches, forward and adjoint), and the
+// residual check of Toeplitz plans.
 #include "launch.cuh"
 
 namespace dich {
