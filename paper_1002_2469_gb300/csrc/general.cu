@@ -40,8 +40,17 @@ static cudaError_t launch_gen_one(int grid, int grid_y, size_t smem, cudaStream_
     cudaError_t e = cudaFuncSetAttribute(k_window_gen<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_window_gen<NT><<<dim3(grid, grid_y), NT, smem, st>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, grid_y);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_window_gen<NT>, a);
 }
 
 template <int NT>
@@ -50,8 +59,17 @@ static cudaError_t launch_gen_ff_one(int grid, int grid_y, size_t smem, cudaStre
     cudaError_t e = cudaFuncSetAttribute(k_window_gen_ff<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_window_gen_ff<NT><<<dim3(grid, grid_y), NT, smem, st>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, grid_y);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_window_gen_ff<NT>, a);
 }
 
 static cudaError_t launch_window_gen(int NT, int grid, size_t smem, cudaStream_t st, const GenArgs& a, int grid_y,

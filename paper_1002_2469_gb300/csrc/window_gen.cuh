@@ -45,6 +45,9 @@ __global__ void __launch_bounds__(NT) k_window_gen(const GenArgs G) {
   constexpr int LD = NT + 1;
   const WinArgs& A = G.w;
   extern __shared__ __align__(16) double sm[];
+  // launched with programmatic stream serialization: nothing is read or written before the
+  // previous kernel of the stream has completed
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int tid = threadIdx.x;
   const int ns = A.n_smem;
   double* S = sm;
@@ -191,6 +194,7 @@ __global__ void __launch_bounds__(NT) k_window_gen(const GenArgs G) {
   }
   __syncthreads();
 
+  asm volatile("griddepcontrol.launch_dependents;");   // the next kernel may begin its launch
   // ---------------------------------------------------------------- coalesced store of the own rows
   unsigned bad = 0u;
   {
@@ -228,6 +232,9 @@ __global__ void __launch_bounds__(NT) k_window_gen_ff(const GenArgs G) {
   constexpr int NW = NT / 32;
   const WinArgs& A = G.w;
   extern __shared__ __align__(16) double sm[];
+  // launched with programmatic stream serialization: nothing is read or written before the
+  // previous kernel of the stream has completed
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int tid = threadIdx.x;
   const int ns = A.n_smem;
   double* S = sm;
@@ -421,6 +428,7 @@ __global__ void __launch_bounds__(NT) k_window_gen_ff(const GenArgs G) {
   }
   __syncthreads();
 
+  asm volatile("griddepcontrol.launch_dependents;");   // the next kernel may begin its launch
   // ---------------------------------------------------------------- coalesced store of the own rows
   unsigned bad = 0u;
   {
