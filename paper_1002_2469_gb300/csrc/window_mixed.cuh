@@ -14,6 +14,7 @@
 // Arithmetic: compensated FP32 sweeps, float-float block quantities and tree, one exact
 // power-of-two scale per window (see ff.cuh).
 #pragma once
+#include <type_traits>
 #include "ff.cuh"
 #include "window.cuh"
 
@@ -92,8 +93,10 @@ __device__ __forceinline__ void sweep_pair(double* S, int tid, int nrow_, int nb
 // tv4[i] = (v_h, v_h, v_l, v_l) and tw4[j] = (w_h, w_h, w_l, w_l) hold the full-size blocks' spikes
 // (w reversed) with both lanes filled and zeros past their truncation lengths, so the full-block
 // loop needs neither bounds nor lane moves.  The system's last block (size nlast) reads its own
-// spikes from global memory (tvl, twl: float-float pairs).
-template <int LD, bool GUARD, bool FAST, int NR = 0>
+// spikes from global memory (tvl, twl: float-float pairs).  KEEP: no join; each block's corrected
+// value stays a float-float pair (h, l) in its FP64 slot of the row (the adjoint's store loop
+// joins it and also forms the gradient products from it).
+template <int LD, bool GUARD, bool FAST, int NR = 0, bool KEEP = false>
 __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow_, int nb0, int nb1, bool last0,
                                              bool last1, int n, const float4* tv4, const float4* tw4,
                                              const float2* tvl, const float2* twl, const ff2& cL, const ff2& cR,
@@ -111,7 +114,9 @@ __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow_, int 
       const float4 v = tv4[i], w = tw4[n - 1 - i];
       ff_fma_acc2(clh, cll, make_float2(v.x, v.y), make_float2(v.z, v.w), xh, xl);
       ff_fma_acc2(crh, crl, make_float2(w.x, w.y), make_float2(w.z, w.w), xh, xl);
-      if (FAST)
+      if (KEEP)
+        *reinterpret_cast<float4*>(row) = make_float4(xh.x, xl.x, xh.y, xl.y);
+      else if (FAST)
         *reinterpret_cast<double2*>(row) =
             make_double2(join_fast(xh.x, xl.x, wscale, fk), join_fast(xh.y, xl.y, wscale, fk));
       else
@@ -143,14 +148,19 @@ __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow_, int 
       }
       ff_fma_acc2(clh, cll, vh, vl, xh, xl);
       ff_fma_acc2(crh, crl, wh, wl, xh, xl);
-      double d0 = (i < nb0) ? join_dadd(xh.x, xl.x, wscale) : 0.0;
-      double d1 = (i < nb1) ? join_dadd(xh.y, xl.y, wscale) : 0.0;
-      *reinterpret_cast<double2*>(row) = make_double2(d0, d1);
+      if (KEEP) {
+        *reinterpret_cast<float4*>(row) = make_float4(i < nb0 ? xh.x : 0.f, i < nb0 ? xl.x : 0.f,
+                                                      i < nb1 ? xh.y : 0.f, i < nb1 ? xl.y : 0.f);
+      } else {
+        double d0 = (i < nb0) ? join_dadd(xh.x, xl.x, wscale) : 0.0;
+        double d1 = (i < nb1) ? join_dadd(xh.y, xl.y, wscale) : 0.0;
+        *reinterpret_cast<double2*>(row) = make_double2(d0, d1);
+      }
     }
   }
 }
 
-template <int NT>
+template <int NT, bool ADJ>
 __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   constexpr int NW = NT / 32;
   constexpr int WB = 2 * NT;       // window blocks
@@ -238,6 +248,21 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
       tw4[i] = make_float4(w.x, w.x, w.y, w.y);
     }
   }
+  // the adjoint: exponent range of the forward solution over the rows its gradient sums read
+  // (the own rows and one beyond each end), loaded while the right-hand side streams in
+  unsigned xhmax = 0u, xhmin = 0xFFFFFFFFu;
+  if constexpr (ADJ) {
+    const int jlo = hl * n, jhi = min(len, (hl + nown) * n);
+    const unsigned* xw = reinterpret_cast<const unsigned*>(A.xf + off + row_lo) + 1;   // high words
+    const int klo = (row_lo + jlo > 0) ? jlo - 1 : jlo;
+    const int khi = (row_lo + jhi < pp->N) ? jhi + 1 : jhi;
+#pragma unroll 16
+    for (int k = klo + tid; k < khi; k += NT) {
+      const unsigned h = __ldg(xw + 2 * k) & 0x7FFFFFFFu;
+      xhmax = max(xhmax, h);
+      xhmin = min(xhmin, h);
+    }
+  }
   cp_async_wait_all();
   __syncthreads();
 
@@ -255,8 +280,8 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   // smallest FP64 high words (sign cleared) give the exponent range of the window: a window of
   // normal values within 2^119 of each other, not too close to the ends of the FP64 range,
   // takes the fast split and join (ff.cuh).
-  int wscale;
-  bool fast;
+  int wscale, xscale = 0;
+  bool fast, xfast = false;   // x: the adjoint's forward solution (gradient sums)
   {
     unsigned hmax = 0u, hmin = 0xFFFFFFFFu;
     if (full) {
@@ -282,10 +307,18 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
     }
     hmax = __reduce_max_sync(0xffffffffu, hmax);
     hmin = __reduce_min_sync(0xffffffffu, hmin);
+    if (ADJ) {
+      xhmax = __reduce_max_sync(0xffffffffu, xhmax);
+      xhmin = __reduce_min_sync(0xffffffffu, xhmin);
+    }
     unsigned* sexp = reinterpret_cast<unsigned*>(swv);
     if (lane == 0) {
       sexp[wid] = hmax;
       sexp[NW + wid] = hmin;
+      if (ADJ) {
+        sexp[2 * NW + wid] = xhmax;
+        sexp[3 * NW + wid] = xhmin;
+      }
     }
     __syncthreads();
     hmax = 0u;
@@ -293,11 +326,19 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
     for (int w = 0; w < NW; ++w) {
       hmax = max(hmax, sexp[w]);
       hmin = min(hmin, sexp[NW + w]);
+      if (ADJ) {
+        xhmax = max(xhmax, sexp[2 * NW + w]);
+        xhmin = min(xhmin, sexp[3 * NW + w]);
+      }
     }
     __syncthreads();
-    const int emax = (int)(hmax >> 20), emin = (int)(hmin >> 20);
-    wscale = (emax == 2047) ? 0 : ((emax == 0) ? 1000 : max(-1000, min(1000, (1023 + 16) - emax)));
-    fast = (emin >= 1) && (emax >= 239) && (emax <= 1935) && (emax - emin <= 119);
+    auto scale_of = [](unsigned hmx, unsigned hmn, int& sc, bool& fs) {
+      const int emax = (int)(hmx >> 20), emin = (int)(hmn >> 20);
+      sc = (emax == 2047) ? 0 : ((emax == 0) ? 1000 : max(-1000, min(1000, (1023 + 16) - emax)));
+      fs = (emin >= 1) && (emax >= 239) && (emax <= 1935) && (emax - emin <= 119);
+    };
+    scale_of(hmax, hmin, wscale, fast);
+    if (ADJ) scale_of(xhmax, xhmin, xscale, xfast);
   }
 
   // ---------------------------------------------------------------- local sweeps (a1)
@@ -457,65 +498,39 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   const bool owns = (b1 >= hl) && (b0 < hl + nown);
   if (!owns) {
   } else if (full && fast && n == 16)
-    correct_pair<LD, false, true, 16>(S, tid, nrow, nb0, nb1, last0, last1, n, tv4, tw4, tvl_g, twl_g, cL, cR,
+    correct_pair<LD, false, true, 16, ADJ>(S, tid, nrow, nb0, nb1, last0, last1, n, tv4, tw4, tvl_g, twl_g, cL, cR,
                                   wscale);
   else if (full && fast)
-    correct_pair<LD, false, true>(S, tid, nrow, nb0, nb1, last0, last1, n, tv4, tw4, tvl_g, twl_g, cL, cR,
+    correct_pair<LD, false, true, 0, ADJ>(S, tid, nrow, nb0, nb1, last0, last1, n, tv4, tw4, tvl_g, twl_g, cL, cR,
                                   wscale);
   else if (full)
-    correct_pair<LD, false, false>(S, tid, nrow, nb0, nb1, last0, last1, n, tv4, tw4, tvl_g, twl_g, cL, cR,
+    correct_pair<LD, false, false, 0, ADJ>(S, tid, nrow, nb0, nb1, last0, last1, n, tv4, tw4, tvl_g, twl_g, cL, cR,
                                   wscale);
   else if (nrow > 0)
-    correct_pair<LD, true, false>(S, tid, nrow, nb0, nb1, last0, last1, n, tv4, tw4, tvl_g, twl_g, cL, cR,
+    correct_pair<LD, true, false, 0, ADJ>(S, tid, nrow, nb0, nb1, last0, last1, n, tv4, tw4, tvl_g, twl_g, cL, cR,
                                   wscale);
   __syncthreads();
 
   // the next kernel of the stream may begin its launch (it waits for this grid to complete)
   asm volatile("griddepcontrol.launch_dependents;");
   // ---------------------------------------------------------------- coalesced store of the own rows
-  const bool adj = (A.xf != nullptr);
-  double g0 = 0.0, gm = 0.0, gp = 0.0;
-  double g0b = 0.0, gmb = 0.0, gpb = 0.0;   // second accumulator set: independent FP64 chains
   unsigned bad = 0u;
   const int64_t N = pp->N;
-  {
-    const int jlo = hl * n;
-    const int jhi = min(len, (hl + nown) * n);
-    double* dst = A.x + (int64_t)blockIdx.y * A.ldx + off + row_lo;
-    // per stored value: the non-finite flag and the adjoint's gradient partials
-    auto take = [&](double dv, int j) {
-      if (A.check_finite && ((__double2hiint(dv) >> 20) & 0x7FF) == 0x7FF) bad = 1u;
-      if (adj) {
-        const int64_t r = row_lo + j;
-        const double* xr = A.xf + off + r;
-        g0 = fma(dv, xr[0], g0);
-        if (r > 0) gm = fma(dv, xr[-1], gm);
-        if (r + 1 < N) gp = fma(dv, xr[1], gp);
-      }
-    };
+  const int jlo = hl * n;
+  const int jhi = min(len, (hl + nown) * n);
+  double* dst = A.x + (int64_t)blockIdx.y * A.ldx + off + row_lo;
+  auto nonfinite = [](double d) { return ((__double2hiint(d) >> 20) & 0x7FF) == 0x7FF; };
+  if constexpr (!ADJ) {
     // rows j, j + 1 (j even) of one block (column b, rows i, i + 1 of the tile): one 16-byte store
     auto put2 = [&](int j, const double* col) {
       const double d0 = col[0];
       if (j + 1 < jhi) {
         const double d1 = col[LD];
         __stcs(reinterpret_cast<double2*>(dst + j), make_double2(d0, d1));
-        if (A.check_finite && (((__double2hiint(d0) >> 20) & 0x7FF) == 0x7FF ||
-                               ((__double2hiint(d1) >> 20) & 0x7FF) == 0x7FF))
-          bad = 1u;
-        if (adj) {  // rows r, r + 1: four loads of the forward solution, two accumulator sets
-          const int64_t r = row_lo + j;
-          const double* xr = A.xf + off + r;
-          const double xm1 = (r > 0) ? xr[-1] : 0.0, x0 = xr[0], x1 = xr[1], x2 = (r + 2 < N) ? xr[2] : 0.0;
-          g0 = fma(d0, x0, g0);
-          gm = fma(d0, xm1, gm);
-          gp = fma(d0, x1, gp);
-          g0b = fma(d1, x1, g0b);
-          gmb = fma(d1, x0, gmb);
-          gpb = fma(d1, x2, gpb);
-        }
+        if (A.check_finite && (nonfinite(d0) || nonfinite(d1))) bad = 1u;
       } else {
         __stcs(dst + j, d0);
-        take(d0, j);
+        if (A.check_finite && nonfinite(d0)) bad = 1u;
       }
     };
     if (n == 16 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0u) {
@@ -541,7 +556,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
       for (int j = jlo + tid; j < jhi; j += NT) {
         const double dv = S[(size_t)i * LD + b];
         __stcs(dst + j, dv);
-        take(dv, j);
+        if (A.check_finite && nonfinite(dv)) bad = 1u;
         i += di;
         b += db;
         if (i >= n) {
@@ -550,30 +565,191 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
         }
       }
     }
-  }
-  if (bad) atomicOr(A.status, (unsigned)ST_NONFINITE);
-  if (adj) {
-    g0 += g0b;
-    gm += gmb;
-    gp += gpb;
+    if (bad) atomicOr(A.status, (unsigned)ST_NONFINITE);
+  } else {
+    // The adjoint: the tile holds lambda as float-float pairs (window scale 2^wscale); the store
+    // joins them, and the gradient sums (a5) -- sum_r lambda_r x_{r-1}, x_r, x_{r+1} over the own
+    // rows -- are accumulated from the same pairs.  Where the forward solution x qualifies for the
+    // fast split with its own power-of-two scale (all rows the sums read normal and within 2^119
+    // of each other), each product is formed error-free in FP32 (FMA) and summed with TwoSum into
+    // packed float-float accumulators (units 2^(wscale + xscale)); otherwise the FP64 pipe takes
+    // the products.
+    const FastK fk = fast_k(wscale), fkx = fast_k(xscale);
+    float2 s0h = f2(0.f), s0l = f2(0.f), smh = f2(0.f), sml = f2(0.f), sph = f2(0.f), spl = f2(0.f);
+    double g0 = 0.0, gm = 0.0, gp = 0.0;
+    double g0b = 0.0, gmb = 0.0, gpb = 0.0;   // second FP64 set: independent chains
+    struct X4 {
+      double a, b, c, d;   // x_{r-1}, x_r, x_{r+1}, x_{r+2}
+    };
+    // x rows of the pair at row r; rows outside the system read row r instead (masked later)
+    auto loadx = [&](int j) {
+      const int64_t r = row_lo + j;
+      const double* xr = A.xf + off + r;
+      return X4{__ldg(xr + ((r > 0) ? -1 : 0)), __ldg(xr), __ldg(xr + ((r + 1 < N) ? 1 : 0)),
+                __ldg(xr + ((r + 2 < N) ? 2 : 0))};
+    };
+    // one instantiation per (join form, product form): no FP64 work of the other form is
+    // if-converted into the loop
+    auto body = [&](auto fj_, auto xf_) {
+      constexpr bool FJ = decltype(fj_)::value, XF = decltype(xf_)::value;
+      auto join = [&](float2 v) {
+        if constexpr (FJ)
+          return join_fast(v.x, v.y, wscale, fk);
+        else
+          return join_dadd(v.x, v.y, wscale);
+      };
+      auto take = [&](double dv, int j) {
+        if (A.check_finite && nonfinite(dv)) bad = 1u;
+        const int64_t r = row_lo + j;
+        const double* xr = A.xf + off + r;
+        g0 = fma(dv, xr[0], g0);
+        if (r > 0) gm = fma(dv, xr[-1], gm);
+        if (r + 1 < N) gp = fma(dv, xr[1], gp);
+      };
+      // float-float products of rows r (lane x) and r + 1 (lane y; v1 = 0 for a lone row)
+      auto ffrow = [&](int64_t r, float2 v0, float2 v1, const X4& xq) {
+        float ha, la, h0, l0, h1, l1, hb, lb;
+        split_fast(xq.a, fkx, ha, la);
+        split_fast(xq.b, fkx, h0, l0);
+        split_fast(xq.c, fkx, h1, l1);
+        split_fast(xq.d, fkx, hb, lb);
+        if (r == 0) ha = la = 0.f;
+        if (r + 1 >= N) h1 = l1 = 0.f;
+        if (r + 2 >= N) hb = lb = 0.f;
+        const float2 ah = make_float2(v0.x, v1.x), al = make_float2(v0.y, v1.y);
+        ff_fma_acc2(ah, al, make_float2(h0, h1), make_float2(l0, l1), s0h, s0l);
+        ff_fma_acc2(ah, al, make_float2(ha, h0), make_float2(la, l0), smh, sml);
+        ff_fma_acc2(ah, al, make_float2(h1, hb), make_float2(l1, lb), sph, spl);
+      };
+      // rows j, j + 1 (j even) of one block: col[0], col[LD] hold their (h, l) pairs
+      auto put2 = [&](int j, const double* col, const X4& xq) {
+        const float2 v0 = *reinterpret_cast<const float2*>(col);
+        if (j + 1 < jhi) {
+          const float2 v1 = *reinterpret_cast<const float2*>(col + LD);
+          const double d0 = join(v0), d1 = join(v1);
+          __stcs(reinterpret_cast<double2*>(dst + j), make_double2(d0, d1));
+          if (A.check_finite && (nonfinite(d0) || nonfinite(d1))) bad = 1u;
+          const int64_t r = row_lo + j;
+          if constexpr (XF) {
+            ffrow(r, v0, v1, xq);
+          } else {
+            g0 = fma(d0, xq.b, g0);
+            gm = fma(d0, (r > 0) ? xq.a : 0.0, gm);
+            gp = fma(d0, xq.c, gp);
+            g0b = fma(d1, xq.c, g0b);
+            gmb = fma(d1, xq.b, gmb);
+            gpb = fma(d1, (r + 2 < N) ? xq.d : 0.0, gpb);
+          }
+        } else {
+          const double d0 = join(v0);
+          __stcs(dst + j, d0);
+          if constexpr (XF) {
+            if (A.check_finite && nonfinite(d0)) bad = 1u;
+            ffrow(row_lo + j, v0, make_float2(0.f, 0.f), xq);
+          } else {
+            take(d0, j);
+          }
+        }
+      };
+      if (n == 16 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0u) {
+        // the x rows of the next pair are loaded one step ahead
+        const double* col = S + (size_t)(2 * (tid & 7)) * LD + hl + (tid >> 3);
+        int j = jlo + 2 * tid;
+        X4 xq{0.0, 0.0, 0.0, 0.0};
+        if (j < jhi) xq = loadx(j);
+#pragma unroll 1
+        for (; j < jhi; j += 2 * NT, col += NT / 8) {
+          const X4 cur = xq;
+          if (j + 2 * NT < jhi) xq = loadx(j + 2 * NT);
+          put2(j, col, cur);
+        }
+      } else if ((n & 1) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0u) {
+        int b = (jlo + 2 * tid) / n, i = (jlo + 2 * tid) - ((jlo + 2 * tid) / n) * n;
+        const int db = (2 * NT) / n, di = (2 * NT) - ((2 * NT) / n) * n;
+        for (int j = jlo + 2 * tid; j < jhi; j += 2 * NT) {
+          put2(j, S + (size_t)i * LD + b, loadx(j));
+          i += di;
+          b += db;
+          if (i >= n) {
+            i -= n;
+            ++b;
+          }
+        }
+      } else {
+        int b = (jlo + tid) / n, i = (jlo + tid) - ((jlo + tid) / n) * n;
+        const int db = NT / n, di = NT - (NT / n) * n;
+        for (int j = jlo + tid; j < jhi; j += NT) {
+          const float2 v = *reinterpret_cast<const float2*>(S + (size_t)i * LD + b);
+          const double dv = join(v);
+          __stcs(dst + j, dv);
+          if constexpr (XF) {
+            if (A.check_finite && nonfinite(dv)) bad = 1u;
+            ffrow(row_lo + j, v, make_float2(0.f, 0.f), loadx(j));
+          } else {
+            take(dv, j);
+          }
+          i += di;
+          b += db;
+          if (i >= n) {
+            i -= n;
+            ++b;
+          }
+        }
+      }
+    };
+    if (fast) {
+      if (xfast)
+        body(std::true_type(), std::true_type());
+      else
+        body(std::true_type(), std::false_type());
+    } else {
+      if (xfast)
+        body(std::false_type(), std::true_type());
+      else
+        body(std::false_type(), std::false_type());
+    }
+    if (bad) atomicOr(A.status, (unsigned)ST_NONFINITE);
+    __syncthreads();   // the scan scratch takes the per-warp sums
+    if (xfast) {
+      // float-float sums (FP32 pipes): the thread's two lanes, the warp, the CTA; one join to
+      // FP64 per sum, in units 2^wscale, then the exact power of two 2^-wscale
+      ffv a[3] = {ff_add(ffv{smh.x, sml.x}, ffv{smh.y, sml.y}), ff_add(ffv{s0h.x, s0l.x}, ffv{s0h.y, s0l.y}),
+                  ff_add(ffv{sph.x, spl.x}, ffv{sph.y, spl.y})};
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      g0 += __shfl_down_sync(0xffffffffu, g0, d);
-      gm += __shfl_down_sync(0xffffffffu, gm, d);
-      gp += __shfl_down_sync(0xffffffffu, gp, d);
-    }
-    double* sred = reinterpret_cast<double*>(swv);
-    __syncthreads();
-    if (lane == 0) {
-      sred[wid] = gm;
-      sred[NW + wid] = g0;
-      sred[2 * NW + wid] = gp;
-    }
-    __syncthreads();
-    if (tid < 3) {
-      double s = 0.0;
-      for (int w = 0; w < NW; ++w) s += sred[tid * NW + w];
-      A.part[3 * (size_t)blockIdx.x + tid] = s;
+      for (int d = 16; d > 0; d >>= 1)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[k] = ff_add(a[k], ff_shfl_down(a[k], d));
+      if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) swv[k * NW + wid] = a[k];
+      __syncthreads();
+      if (tid < 3) {
+        ffv sum = ff_zero();
+        for (int w = 0; w < NW; ++w) sum = ff_add(sum, swv[tid * NW + w]);
+        A.part[3 * (size_t)blockIdx.x + tid] = join_dadd(sum.h, sum.l, xscale) * pow2i(-wscale);
+      }
+    } else {
+      g0 += g0b;
+      gm += gmb;
+      gp += gpb;
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        g0 += __shfl_down_sync(0xffffffffu, g0, d);
+        gm += __shfl_down_sync(0xffffffffu, gm, d);
+        gp += __shfl_down_sync(0xffffffffu, gp, d);
+      }
+      double* sred = reinterpret_cast<double*>(swv);
+      if (lane == 0) {
+        sred[wid] = gm;
+        sred[NW + wid] = g0;
+        sred[2 * NW + wid] = gp;
+      }
+      __syncthreads();
+      if (tid < 3) {
+        double sum = 0.0;
+        for (int w = 0; w < NW; ++w) sum += sred[tid * NW + w];
+        A.part[3 * (size_t)blockIdx.x + tid] = sum;
+      }
     }
   }
 }

@@ -540,6 +540,37 @@ def test_adjoint_single(D, t, N, prec):
     assert np.all(np.abs(g - gt_ref) <= TOL * np.max(np.abs(gt_ref)) + 1e-300)
 
 
+@pytest.mark.parametrize("kind", ["uniform", "zeros", "wide", "1e200", "1e-200", "1e-300", "1e300", "mixed"])
+@pytest.mark.parametrize("bs,threads", [(0, 0), (14, 128), (15, 64), (16, 256)])
+def test_adjoint_gradient_sums_x_ranges(D, kind, bs, threads):
+    """The MIXED adjoint forms the gradient sums in float-float where the forward solution of a
+    window has a narrow exponent range, else on the FP64 pipe: both against the oracle's sums
+    with x given directly (zeros, 200 decades, the ends of the FP64 range, windows of both kinds)."""
+    t = (-1.2, 2.5, -0.8)
+    N = 70001
+    rng = np.random.default_rng(17)
+    w = rng.uniform(-1, 1, N)
+    x = rng.uniform(-1, 1, N)
+    if kind == "zeros":
+        x[rng.integers(0, N, 50)] = 0.0
+    elif kind == "wide":
+        x *= 10.0 ** rng.uniform(-100, 100, N)
+    elif kind == "mixed":   # every third window of 4096 rows spans 80 decades
+        for k in range(0, N, 3 * 4096):
+            x[k:k + 4096] *= 10.0 ** rng.uniform(-40, 40, len(x[k:k + 4096]))
+    elif kind != "uniform":
+        x *= float(kind)
+    plan = D.Plan(*t, N, precision=1, block_size=bs, threads=threads)
+    gF, gt = plan.adjoint(torch.from_numpy(w).cuda(), torch.from_numpy(x).cuda())
+    assert plan.status() == 0
+    lam_ref, gt_ref = oracle.adjoint(t, w, x)
+    assert rel(gF.cpu().numpy(), lam_ref) < TOL
+    # each sum against the sum of its terms' magnitudes (the bound of an FP64 dot product)
+    mag = np.array([np.dot(np.abs(lam_ref[1:]), np.abs(x[:-1])), np.dot(np.abs(lam_ref), np.abs(x)),
+                    np.dot(np.abs(lam_ref[:-1]), np.abs(x[1:]))])
+    assert np.all(np.abs(gt.cpu().numpy() - gt_ref) <= TOL * mag), (gt.cpu().numpy(), gt_ref)
+
+
 def test_adjoint_general_path(D):
     t = (-1.2, 2.5, -0.8)
     N = 1 << 18
