@@ -264,7 +264,8 @@ def run_gpu(args):
         head.pop("x", None)
         f64.pop("x", None)
         torch.cuda.empty_cache()
-        others = other_configs(D, W, oracle, stream, world, steps=max(5, min(args.steps, 20)))
+        only = None if args.only is None else set(args.only.split(","))
+        others = other_configs(D, W, oracle, stream, world, steps=max(5, min(args.steps, 20)), only=only)
 
     if rank != 0:
         return
@@ -414,12 +415,20 @@ def cusparse_comparator(W, oracle, stream, steps):
         lib.cusparseDestroy(h)
 
 
-def other_configs(D, W, oracle, stream, world, steps=10):
+OTHER_CONFIGS = ("cusparse", "c1", "c2w", "c3", "c4", "c5", "f3", "f3n", "f4", "table1")
+
+
+def other_configs(D, W, oracle, stream, world, steps=10, only=None):
     """C1 (latency), the weakly dominant C2 variant, C3 (2-D Poisson modes), C4 (uneven series),
-    C5 (adjoint): time and Gunknowns/s per form, with the error against the oracle (on a
-    sample of systems for the batches)."""
+    C5 (adjoint), the rows beyond the hot path and the paper's Table 1 run: time and Gunknowns/s
+    per form, with the error against the oracle (on a sample of systems for the batches).
+    only: the names (OTHER_CONFIGS) to run; None runs all."""
     import torch
     out = {}
+
+    def want(name):
+        return only is None or name in only
+
     rng = np.random.default_rng(0)
 
     def sample_err(xd, Fd, N, off, tm1, t0, tp1, k=24, exact=False):
@@ -434,221 +443,231 @@ def other_configs(D, W, oracle, stream, world, steps=10):
             errs.append(float(np.max(np.abs(xd[o:o + n].cpu().numpy() - ref)) / max(np.max(np.abs(ref)), 1e-300)))
         return max(errs)
 
-    out["cusparse_gtsv2_nopivot_c2"] = cusparse_comparator(W, oracle, stream, steps)
-    torch.cuda.empty_cache()
+    if want("cusparse"):
+        out["cusparse_gtsv2_nopivot_c2"] = cusparse_comparator(W, oracle, stream, steps)
+        torch.cuda.empty_cache()
 
-    # C1: tridiag{-1, 4, -1}, N = 65536 (1 MB in, 1 MB out): latency of one solve, three
-    # buffer sets in rotation, back-to-back solves between two events (replays of a CUDA graph;
-    # the loop of Python calls is reported beside it)
-    t1, F1 = W.single_c1()
-    sets = [(torch.from_numpy(F1 * (1.0 + 0.1 * k)).cuda(), torch.empty(F1.size, dtype=torch.float64, device="cuda"))
-            for k in range(3)]
-    c1 = {"unknowns": int(F1.size)}
-    for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
-        plan = D.Plan(*t1, F1.size, precision=prec)
-        reps = 300
-        us_host = 1e3 * _time_batch(lambda: [plan.solve(Fk, out=xk) for Fk, xk in sets], reps, world, stream) / 3
-        # device latency: 90 solves captured in one CUDA graph, replayed between two events (the
-        # Python call overhead of each solve is then off the timeline)
-        graph = torch.cuda.CUDAGraph()
-        side = torch.cuda.Stream()
-        side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side):
-            for Fk, xk in sets:
-                plan.solve(Fk, out=xk)
-        torch.cuda.current_stream().wait_stream(side)
-        with torch.cuda.graph(graph):
-            for _ in range(30):
+    if want("c1"):
+        # C1: tridiag{-1, 4, -1}, N = 65536 (1 MB in, 1 MB out): latency of one solve, three
+        # buffer sets in rotation, back-to-back solves between two events (replays of a CUDA graph;
+        # the loop of Python calls is reported beside it)
+        t1, F1 = W.single_c1()
+        sets = [(torch.from_numpy(F1 * (1.0 + 0.1 * k)).cuda(), torch.empty(F1.size, dtype=torch.float64, device="cuda"))
+                for k in range(3)]
+        c1 = {"unknowns": int(F1.size)}
+        for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
+            plan = D.Plan(*t1, F1.size, precision=prec)
+            reps = 300
+            us_host = 1e3 * _time_batch(lambda: [plan.solve(Fk, out=xk) for Fk, xk in sets], reps, world, stream) / 3
+            # device latency: 90 solves captured in one CUDA graph, replayed between two events (the
+            # Python call overhead of each solve is then off the timeline)
+            graph = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
                 for Fk, xk in sets:
                     plan.solve(Fk, out=xk)
-        us = 1e3 * _time_batch(graph.replay, 10, world, stream) / 90
-        err = max(float(np.max(np.abs(xk.cpu().numpy() - oracle.thomas(t1, Fk.cpu().numpy())))
-                        / np.max(np.abs(oracle.thomas(t1, Fk.cpu().numpy())))) for Fk, xk in sets)
-        c1[name] = {"us_per_solve": round(us, 2), "us_per_solve_python_loop": round(us_host, 2),
-                    "Gunknowns_s": round(F1.size / us / 1e3, 2), "windows": plan.info["tiles"], "rel_err": err}
-        del graph
-    out["c1_latency_65536"] = c1
-    del sets
+            torch.cuda.current_stream().wait_stream(side)
+            with torch.cuda.graph(graph):
+                for _ in range(30):
+                    for Fk, xk in sets:
+                        plan.solve(Fk, out=xk)
+            us = 1e3 * _time_batch(graph.replay, 10, world, stream) / 90
+            err = max(float(np.max(np.abs(xk.cpu().numpy() - oracle.thomas(t1, Fk.cpu().numpy())))
+                            / np.max(np.abs(oracle.thomas(t1, Fk.cpu().numpy())))) for Fk, xk in sets)
+            c1[name] = {"us_per_solve": round(us, 2), "us_per_solve_python_loop": round(us_host, 2),
+                        "Gunknowns_s": round(F1.size / us / 1e3, 2), "windows": plan.info["tiles"], "rel_err": err}
+            del graph
+        out["c1_latency_65536"] = c1
+        del sets
 
-    # C2 variant: the weakly dominant tridiag{-1, 2.001, -1} at N = 2^26 (decay length ~1400
-    # rows; the AUTO policy takes the FP64 form here, gain 64 > 24)
-    t2w, F2w = W.single_c2(weak=True)
-    Fd = torch.from_numpy(F2w).cuda()
-    xd = torch.empty_like(Fd)
-    ref2w = oracle.thomas(t2w, F2w)
-    c2w = {"unknowns": int(F2w.size)}
-    for name, prec in (("auto", D.PREC_AUTO), ("mixed", D.PREC_MIXED), ("fp64_plain", D.PREC_F64)):
-        plan = D.Plan(*t2w, F2w.size, precision=prec)
-        ms = _time_batch(lambda: plan.solve(Fd, out=xd), steps, world, stream)
-        xh = xd.cpu().numpy()
-        c2w[name] = {"ms": round(ms, 4), "Gunknowns_s": round(F2w.size / ms / 1e6, 2),
-                     "form": ["f64", "mixed"][plan.info["precision"]], "path": ["single", "halo", "general"][plan.info["path"]],
-                     "block_size": plan.info["n"], "halo": [plan.info["halo_l"], plan.info["halo_r"]],
-                     "rel_err": float(np.max(np.abs(xh - ref2w)) / np.max(np.abs(ref2w))),
-                     "backward_err": backward_error(t2w, F2w, xh)}
-    out["c2_weak_2e26"] = c2w
-    del Fd, xd, ref2w
+    if want("c2w"):
+        # C2 variant: the weakly dominant tridiag{-1, 2.001, -1} at N = 2^26 (decay length ~1400
+        # rows; the AUTO policy takes the FP64 form here, gain 64 > 24)
+        t2w, F2w = W.single_c2(weak=True)
+        Fd = torch.from_numpy(F2w).cuda()
+        xd = torch.empty_like(Fd)
+        ref2w = oracle.thomas(t2w, F2w)
+        c2w = {"unknowns": int(F2w.size)}
+        for name, prec in (("auto", D.PREC_AUTO), ("mixed", D.PREC_MIXED), ("fp64_plain", D.PREC_F64)):
+            plan = D.Plan(*t2w, F2w.size, precision=prec)
+            ms = _time_batch(lambda: plan.solve(Fd, out=xd), steps, world, stream)
+            xh = xd.cpu().numpy()
+            c2w[name] = {"ms": round(ms, 4), "Gunknowns_s": round(F2w.size / ms / 1e6, 2),
+                         "form": ["f64", "mixed"][plan.info["precision"]], "path": ["single", "halo", "general"][plan.info["path"]],
+                         "block_size": plan.info["n"], "halo": [plan.info["halo_l"], plan.info["halo_r"]],
+                         "rel_err": float(np.max(np.abs(xh - ref2w)) / np.max(np.abs(ref2w))),
+                         "backward_err": backward_error(t2w, F2w, xh)}
+        out["c2_weak_2e26"] = c2w
+        del Fd, xd, ref2w
 
-    # C3: 4096 Poisson modes of N = 4096 (DST of a seeded smooth source)
-    tm1, t0, tp1, N, rhs = W.poisson_c3()
-    off = W.offsets(N)
-    Fd = torch.from_numpy(rhs.reshape(-1)).cuda()
-    xd = torch.empty_like(Fd)
-    c3 = {"unknowns": int(N.sum())}
-    for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
-        b = D.Batch(N, tm1, t0, tp1, precision=prec)
-        ms = _time_batch(lambda: b.solve(Fd, out=xd), steps, world, stream)
-        forms = b.info["form"]
-        c3[name] = {"ms": round(ms, 4), "Gunknowns_s": round(N.sum() / ms / 1e6, 2),
-                    "hbm_GBs": round(16 * N.sum() / ms / 1e6, 1), "mixed_systems": int(forms.sum()),
-                    "max_rel_err_sampled_vs_binary128": sample_err(xd, Fd, N, off, tm1, t0, tp1, exact=True)}
-    out["c3_poisson_4096x4096"] = c3
-    del Fd, xd
+    if want("c3"):
+        # C3: 4096 Poisson modes of N = 4096 (DST of a seeded smooth source)
+        tm1, t0, tp1, N, rhs = W.poisson_c3()
+        off = W.offsets(N)
+        Fd = torch.from_numpy(rhs.reshape(-1)).cuda()
+        xd = torch.empty_like(Fd)
+        c3 = {"unknowns": int(N.sum())}
+        for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
+            b = D.Batch(N, tm1, t0, tp1, precision=prec)
+            ms = _time_batch(lambda: b.solve(Fd, out=xd), steps, world, stream)
+            forms = b.info["form"]
+            c3[name] = {"ms": round(ms, 4), "Gunknowns_s": round(N.sum() / ms / 1e6, 2),
+                        "hbm_GBs": round(16 * N.sum() / ms / 1e6, 1), "mixed_systems": int(forms.sum()),
+                        "max_rel_err_sampled_vs_binary128": sample_err(xd, Fd, N, off, tm1, t0, tp1, exact=True)}
+        out["c3_poisson_4096x4096"] = c3
+        del Fd, xd
 
-    # C4: 10000 systems, N log-uniform in [256, 2^20]
-    N, off, tm1, t0, tp1, _ = W.uneven_c4(with_rhs=False)
-    Fd = W.device_uniform(int(N.sum()), W.SEED_RHS, "cuda")
-    xd = torch.empty_like(Fd)
-    c4 = {"unknowns": int(N.sum())}
-    for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
-        b = D.Batch(N, tm1, t0, tp1, precision=prec)
-        ms = _time_batch(lambda: b.solve(Fd, out=xd), max(3, steps // 2), world, stream)
-        c4[name] = {"ms": round(ms, 3), "Gunknowns_s": round(N.sum() / ms / 1e6, 2),
-                    "hbm_GBs": round(16 * N.sum() / ms / 1e6, 1), "windows": int(b.info["windows"]),
-                    "max_rel_err_sampled": sample_err(xd, Fd, N, off, tm1, t0, tp1)}
-    out["c4_uneven_10000"] = c4
-    del Fd, xd
-    torch.cuda.empty_cache()
+    if want("c4"):
+        # C4: 10000 systems, N log-uniform in [256, 2^20]
+        N, off, tm1, t0, tp1, _ = W.uneven_c4(with_rhs=False)
+        Fd = W.device_uniform(int(N.sum()), W.SEED_RHS, "cuda")
+        xd = torch.empty_like(Fd)
+        c4 = {"unknowns": int(N.sum())}
+        for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
+            b = D.Batch(N, tm1, t0, tp1, precision=prec)
+            ms = _time_batch(lambda: b.solve(Fd, out=xd), max(3, steps // 2), world, stream)
+            c4[name] = {"ms": round(ms, 3), "Gunknowns_s": round(N.sum() / ms / 1e6, 2),
+                        "hbm_GBs": round(16 * N.sum() / ms / 1e6, 1), "windows": int(b.info["windows"]),
+                        "max_rel_err_sampled": sample_err(xd, Fd, N, off, tm1, t0, tp1)}
+        out["c4_uneven_10000"] = c4
+        del Fd, xd
+        torch.cuda.empty_cache()
 
-    # C5: forward + adjoint over 1024 systems of N = 65536
-    Ns, off, tm1, t0, tp1, _, _ = W.adjoint_c5(with_data=False)
-    Fd = W.device_uniform(int(Ns.sum()), W.SEED_RHS, "cuda")
-    wd = W.device_uniform(int(Ns.sum()), W.SEED_W, "cuda")
-    xd = torch.empty_like(Fd)
-    c5 = {"unknowns": int(Ns.sum())}
-    for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
-        b = D.Batch(Ns, tm1, t0, tp1, precision=prec)
-        gF = torch.empty_like(Fd)
-        gt = torch.empty((Ns.size, 3), dtype=torch.float64, device="cuda")
+    if want("c5"):
+        # C5: forward + adjoint over 1024 systems of N = 65536
+        Ns, off, tm1, t0, tp1, _, _ = W.adjoint_c5(with_data=False)
+        Fd = W.device_uniform(int(Ns.sum()), W.SEED_RHS, "cuda")
+        wd = W.device_uniform(int(Ns.sum()), W.SEED_W, "cuda")
+        xd = torch.empty_like(Fd)
+        c5 = {"unknowns": int(Ns.sum())}
+        for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
+            b = D.Batch(Ns, tm1, t0, tp1, precision=prec)
+            gF = torch.empty_like(Fd)
+            gt = torch.empty((Ns.size, 3), dtype=torch.float64, device="cuda")
 
-        def step():
-            b.solve(Fd, out=xd)
-            D.dichotomy_adjoint_batched(b.handle, wd, xd, gF, gt)
-        ms = _time_batch(step, steps, world, stream)
-        s_ = 7
-        o, n = int(off[s_]), int(Ns[s_])
-        tt = (tm1[s_], t0[s_], tp1[s_])
-        lam, g = oracle.adjoint(tt, wd[o:o + n].cpu().numpy(), oracle.thomas(tt, Fd[o:o + n].cpu().numpy()))
-        c5[name] = {"ms_forward_plus_adjoint": round(ms, 4), "Gunknowns_s": round(Ns.sum() / ms / 1e6, 2),
-                    "rel_err_gF_sys7": float(np.max(np.abs(gF[o:o + n].cpu().numpy() - lam)) / np.max(np.abs(lam))),
-                    "rel_err_gt_sys7": float(np.max(np.abs(gt[s_].cpu().numpy() - g)) / np.max(np.abs(g)))}
-    out["c5_adjoint_1024x65536"] = c5
-    del Fd, wd, xd
-    torch.cuda.empty_cache()
+            def step():
+                b.solve(Fd, out=xd)
+                D.dichotomy_adjoint_batched(b.handle, wd, xd, gF, gt)
+            ms = _time_batch(step, steps, world, stream)
+            s_ = 7
+            o, n = int(off[s_]), int(Ns[s_])
+            tt = (tm1[s_], t0[s_], tp1[s_])
+            lam, g = oracle.adjoint(tt, wd[o:o + n].cpu().numpy(), oracle.thomas(tt, Fd[o:o + n].cpu().numpy()))
+            c5[name] = {"ms_forward_plus_adjoint": round(ms, 4), "Gunknowns_s": round(Ns.sum() / ms / 1e6, 2),
+                        "rel_err_gF_sys7": float(np.max(np.abs(gF[o:o + n].cpu().numpy() - lam)) / np.max(np.abs(lam))),
+                        "rel_err_gt_sys7": float(np.max(np.abs(gt[s_].cpu().numpy() - g)) / np.max(np.abs(g)))}
+        out["c5_adjoint_1024x65536"] = c5
+        del Fd, wd, xd
+        torch.cuda.empty_cache()
 
-    # f3: 2-D Dirichlet Poisson by separation of variables on a 4096 x 4096-interval grid
-    # (M = 4095 interior points per direction): DST-I along x, the 4095 mode systems through the
-    # batched Dichotomy solve, inverse DST-I; manufactured solution u* ~ U[-1, 1]
-    from paper_1002_2469_gb300 import poisson as PS
-    from oracle import poisson as OP
-    M = 4095
-    us = np.random.default_rng(0).uniform(-1.0, 1.0, (M, M))
-    fd = torch.from_numpy(OP.laplacian5(us)).cuda()
-    solver = PS.Poisson2D(M)
-    ms_total = _time_batch(lambda: solver.solve(fd), steps, world, stream)
-    rhs = torch.empty(M * M, dtype=torch.float64, device="cuda")
-    v = torch.empty_like(rhs)
-    ms_solve = _time_batch(lambda: solver.batch.solve(rhs, out=v), steps, world, stream)
-    u = solver.solve(fd).cpu().numpy()
-    out["f3_poisson2d_4095"] = {"unknowns": M * M, "ms_total": round(ms_total, 4), "ms_dichotomy": round(ms_solve, 4),
-                                "Gunknowns_s": round(M * M / ms_total / 1e6, 2),
-                                "form": "AUTO per mode", "transform": "DST-I via torch.fft (cuFFT)",
-                                "rel_err_vs_manufactured": float(np.max(np.abs(u - us)) / np.max(np.abs(us)))}
-    del fd, rhs, v, solver
-    torch.cuda.empty_cache()
+    if want("f3"):
+        # f3: 2-D Dirichlet Poisson by separation of variables on a 4096 x 4096-interval grid
+        # (M = 4095 interior points per direction): DST-I along x, the 4095 mode systems through the
+        # batched Dichotomy solve, inverse DST-I; manufactured solution u* ~ U[-1, 1]
+        from paper_1002_2469_gb300 import poisson as PS
+        from oracle import poisson as OP
+        M = 4095
+        us = np.random.default_rng(0).uniform(-1.0, 1.0, (M, M))
+        fd = torch.from_numpy(OP.laplacian5(us)).cuda()
+        solver = PS.Poisson2D(M)
+        ms_total = _time_batch(lambda: solver.solve(fd), steps, world, stream)
+        rhs = torch.empty(M * M, dtype=torch.float64, device="cuda")
+        v = torch.empty_like(rhs)
+        ms_solve = _time_batch(lambda: solver.batch.solve(rhs, out=v), steps, world, stream)
+        u = solver.solve(fd).cpu().numpy()
+        out["f3_poisson2d_4095"] = {"unknowns": M * M, "ms_total": round(ms_total, 4), "ms_dichotomy": round(ms_solve, 4),
+                                    "Gunknowns_s": round(M * M / ms_total / 1e6, 2),
+                                    "form": "AUTO per mode", "transform": "DST-I via torch.fft (cuFFT)",
+                                    "rel_err_vs_manufactured": float(np.max(np.abs(u - us)) / np.max(np.abs(us)))}
+        del fd, rhs, v, solver
+        torch.cuda.empty_cache()
 
-    # f2 + f3: the same driver with Neumann conditions in y (4096 cell centres): every mode is a
-    # quasi-Toeplitz system of eq. 21 (psi = chi = -1), solved in one batch with the corner step
-    My = 4096
-    us = np.random.default_rng(0).uniform(-1.0, 1.0, (M, My))
-    fd = torch.from_numpy(OP.laplacian5_neumann_y(us)).cuda()
-    solver = PS.Poisson2D(M, My=My, bc_y="neumann")
-    ms_total = _time_batch(lambda: solver.solve(fd), steps, world, stream)
-    rhs = torch.empty(M * My, dtype=torch.float64, device="cuda")
-    v = torch.empty_like(rhs)
-    ms_solve = _time_batch(lambda: solver.batch.solve(rhs, out=v), steps, world, stream)
-    u = solver.solve(fd).cpu().numpy()
-    out["f3_poisson2d_neumann_y_4095x4096"] = {
-        "unknowns": M * My, "ms_total": round(ms_total, 4), "ms_dichotomy": round(ms_solve, 4),
-        "Gunknowns_s": round(M * My / ms_total / 1e6, 2), "form": "AUTO per mode, quasi-Toeplitz corners",
-        "rel_err_vs_manufactured": float(np.max(np.abs(u - us)) / np.max(np.abs(us)))}
-    del fd, rhs, v, solver
-    torch.cuda.empty_cache()
+    if want("f3n"):
+        # f2 + f3: the same driver with Neumann conditions in y (4096 cell centres): every mode is a
+        # quasi-Toeplitz system of eq. 21 (psi = chi = -1), solved in one batch with the corner step
+        My = 4096
+        us = np.random.default_rng(0).uniform(-1.0, 1.0, (M, My))
+        fd = torch.from_numpy(OP.laplacian5_neumann_y(us)).cuda()
+        solver = PS.Poisson2D(M, My=My, bc_y="neumann")
+        ms_total = _time_batch(lambda: solver.solve(fd), steps, world, stream)
+        rhs = torch.empty(M * My, dtype=torch.float64, device="cuda")
+        v = torch.empty_like(rhs)
+        ms_solve = _time_batch(lambda: solver.batch.solve(rhs, out=v), steps, world, stream)
+        u = solver.solve(fd).cpu().numpy()
+        out["f3_poisson2d_neumann_y_4095x4096"] = {
+            "unknowns": M * My, "ms_total": round(ms_total, 4), "ms_dichotomy": round(ms_solve, 4),
+            "Gunknowns_s": round(M * My / ms_total / 1e6, 2), "form": "AUTO per mode, quasi-Toeplitz corners",
+            "rel_err_vs_manufactured": float(np.max(np.abs(u - us)) / np.max(np.abs(us)))}
+        del fd, rhs, v, solver
+        torch.cuda.empty_cache()
 
-    # f4: a general tridiagonal matrix, N = 2^24: |a_i|, |c_i| <= 1 random, b_i = +-(|a_i| + |c_i| + U[0.3, 1.5]),
-    # F ~ N(0, 1); the O(N) preliminary step (plan and bind: on the device by default, plan_s; on
-    # the host, plan_s_host_prelim), then solves on the device in the AUTO form (float-float here)
-    # and in the plain FP64 form
-    Ng = 1 << 24
-    rng = np.random.default_rng(1)
-    ga, gc = rng.uniform(-1, 1, Ng), rng.uniform(-1, 1, Ng)
-    gb = (np.abs(ga) + np.abs(gc) + rng.uniform(0.3, 1.5, Ng)) * rng.choice([-1.0, 1.0], Ng)
-    gF = np.random.default_rng(2).standard_normal(Ng)
-    t0_ = time.perf_counter()
-    D.GenPlan(ga, gb, gc, flags=D.FLAG_HOST_PRELIM)
-    plan_s_host = time.perf_counter() - t0_
-    torch.cuda.empty_cache()
-    gFd = torch.from_numpy(gF).cuda()
-    gxd = torch.empty_like(gFd)
-    gref = oracle.thomas_tridiag(ga, gb, gc, gF)
-    f4 = {"unknowns": Ng, "bytes_per_unknown": 56, "plan_s_host_prelim": round(plan_s_host, 3)}
-    for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
+    if want("f4"):
+        # f4: a general tridiagonal matrix, N = 2^24: |a_i|, |c_i| <= 1 random, b_i = +-(|a_i| + |c_i| + U[0.3, 1.5]),
+        # F ~ N(0, 1); the O(N) preliminary step (plan and bind: on the device by default, plan_s; on
+        # the host, plan_s_host_prelim), then solves on the device in the AUTO form (float-float here)
+        # and in the plain FP64 form
+        Ng = 1 << 24
+        rng = np.random.default_rng(1)
+        ga, gc = rng.uniform(-1, 1, Ng), rng.uniform(-1, 1, Ng)
+        gb = (np.abs(ga) + np.abs(gc) + rng.uniform(0.3, 1.5, Ng)) * rng.choice([-1.0, 1.0], Ng)
+        gF = np.random.default_rng(2).standard_normal(Ng)
         t0_ = time.perf_counter()
-        gplan = D.GenPlan(ga, gb, gc, precision=prec)
-        plan_s = time.perf_counter() - t0_
-        ms_g = _time_batch(lambda: gplan.solve(gFd, out=gxd), steps, world, stream)
-        gx = gxd.cpu().numpy()
-        f4[name] = {"ms": round(ms_g, 4), "Gunknowns_s": round(Ng / ms_g / 1e6, 2),
-                    "hbm_GBs": round(56 * Ng / ms_g / 1e6, 1), "plan_s": round(plan_s, 3),
-                    "path": ["single", "halo", "general"][gplan.info["path"]], "block_size": gplan.info["n"],
-                    "threads": gplan.info["threads"], "form": "mixed" if gplan.info["precision"] == 1 else "f64",
-                    "rel_err": float(np.max(np.abs(gx - gref)) / np.max(np.abs(gref)))}
-        del gplan
-    out["f4_general_2e24"] = f4
-    del gFd, gxd
-    torch.cuda.empty_cache()
+        D.GenPlan(ga, gb, gc, flags=D.FLAG_HOST_PRELIM)
+        plan_s_host = time.perf_counter() - t0_
+        torch.cuda.empty_cache()
+        gFd = torch.from_numpy(gF).cuda()
+        gxd = torch.empty_like(gFd)
+        gref = oracle.thomas_tridiag(ga, gb, gc, gF)
+        f4 = {"unknowns": Ng, "bytes_per_unknown": 56, "plan_s_host_prelim": round(plan_s_host, 3)}
+        for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
+            t0_ = time.perf_counter()
+            gplan = D.GenPlan(ga, gb, gc, precision=prec)
+            plan_s = time.perf_counter() - t0_
+            ms_g = _time_batch(lambda: gplan.solve(gFd, out=gxd), steps, world, stream)
+            gx = gxd.cpu().numpy()
+            f4[name] = {"ms": round(ms_g, 4), "Gunknowns_s": round(Ng / ms_g / 1e6, 2),
+                        "hbm_GBs": round(56 * Ng / ms_g / 1e6, 1), "plan_s": round(plan_s, 3),
+                        "path": ["single", "halo", "general"][gplan.info["path"]], "block_size": gplan.info["n"],
+                        "threads": gplan.info["threads"], "form": "mixed" if gplan.info["precision"] == 1 else "f64",
+                        "rel_err": float(np.max(np.abs(gx - gref)) / np.max(np.abs(gref)))}
+            del gplan
+        out["f4_general_2e24"] = f4
+        del gFd, gxd
+        torch.cuda.empty_cache()
 
-    # the paper's largest 2-D Poisson run (Table 1: 65536 x 65536, Stage 2 = the dichotomy process):
-    # the 65536 mode systems of N = 65536 (4.3e9 unknowns, 34 GB per vector) as one batch; the
-    # right-hand sides are synthetic (U[-1, 1] drawn on the device) in place of the DST of a source.
-    # Stage 1 here is the batch plan on the host.  The paper's times are context only (4096 MPI
-    # processes on Xeon X5570 nodes).
-    Mp = 65536
-    t0p = PS.mode_t0(Mp)
-    onesp = np.ones(Mp)
-    t1_ = time.perf_counter()
-    bp = D.Batch(np.full(Mp, Mp, dtype=np.int64), -onesp, t0p, -onesp, precision=D.PREC_AUTO)
-    stage1_s = time.perf_counter() - t1_
-    Fp = W.device_uniform(Mp * Mp, W.SEED_RHS, "cuda")
-    xp = torch.empty_like(Fp)
-    ms_p = _time_batch(lambda: bp.solve(Fp, out=xp), max(3, steps // 4), world, stream)
-    errs, oerrs = [], []
-    for k in (1, 2, 100, 30000, 65535):      # sampled modes against the binary128 oracle
-        row = slice((k - 1) * Mp, k * Mp)
-        tk = (-1.0, float(t0p[k - 1]), -1.0)
-        Fk = Fp[row].cpu().numpy()
-        ref = oracle.thomas_q(tk, Fk)
-        errs.append(float(np.max(np.abs(xp[row].cpu().numpy() - ref)) / np.max(np.abs(ref))))
-        oerrs.append(float(np.max(np.abs(oracle.thomas(tk, Fk) - ref)) / np.max(np.abs(ref))))
-    out["paper_table1_poisson_65536"] = {
-        "unknowns": Mp * Mp, "stage2_ms": round(ms_p, 3), "Gunknowns_s": round(Mp * Mp / ms_p / 1e6, 2),
-        "hbm_GBs": round(16 * Mp * Mp / ms_p / 1e6, 1), "stage1_host_s": round(stage1_s, 3),
-        "mixed_systems": int(bp.info["form"].sum()), "sampled_modes": [1, 2, 100, 30000, 65535],
-        "rel_err_vs_binary128": errs, "fp64_oracle_rel_err_vs_binary128": oerrs,
-        "paper_context": {"stage2_s": {"p=256": 3.83, "p=4096": 0.35}, "stage1_toeplitz_s": {"p=4096": 0.30},
-                          "hardware": "Lomonosov cluster, Xeon X5570 nodes, MPI (Table 1)"}}
-    del bp, Fp, xp
-    torch.cuda.empty_cache()
+    if want("table1"):
+        # the paper's largest 2-D Poisson run (Table 1: 65536 x 65536, Stage 2 = the dichotomy process):
+        # the 65536 mode systems of N = 65536 (4.3e9 unknowns, 34 GB per vector) as one batch; the
+        # right-hand sides are synthetic (U[-1, 1] drawn on the device) in place of the DST of a source.
+        # Stage 1 here is the batch plan on the host.  The paper's times are context only (4096 MPI
+        # processes on Xeon X5570 nodes).
+        Mp = 65536
+        t0p = PS.mode_t0(Mp)
+        onesp = np.ones(Mp)
+        t1_ = time.perf_counter()
+        bp = D.Batch(np.full(Mp, Mp, dtype=np.int64), -onesp, t0p, -onesp, precision=D.PREC_AUTO)
+        stage1_s = time.perf_counter() - t1_
+        Fp = W.device_uniform(Mp * Mp, W.SEED_RHS, "cuda")
+        xp = torch.empty_like(Fp)
+        ms_p = _time_batch(lambda: bp.solve(Fp, out=xp), max(3, steps // 4), world, stream)
+        errs, oerrs = [], []
+        for k in (1, 2, 100, 30000, 65535):      # sampled modes against the binary128 oracle
+            row = slice((k - 1) * Mp, k * Mp)
+            tk = (-1.0, float(t0p[k - 1]), -1.0)
+            Fk = Fp[row].cpu().numpy()
+            ref = oracle.thomas_q(tk, Fk)
+            errs.append(float(np.max(np.abs(xp[row].cpu().numpy() - ref)) / np.max(np.abs(ref))))
+            oerrs.append(float(np.max(np.abs(oracle.thomas(tk, Fk) - ref)) / np.max(np.abs(ref))))
+        out["paper_table1_poisson_65536"] = {
+            "unknowns": Mp * Mp, "stage2_ms": round(ms_p, 3), "Gunknowns_s": round(Mp * Mp / ms_p / 1e6, 2),
+            "hbm_GBs": round(16 * Mp * Mp / ms_p / 1e6, 1), "stage1_host_s": round(stage1_s, 3),
+            "mixed_systems": int(bp.info["form"].sum()), "sampled_modes": [1, 2, 100, 30000, 65535],
+            "rel_err_vs_binary128": errs, "fp64_oracle_rel_err_vs_binary128": oerrs,
+            "paper_context": {"stage2_s": {"p=256": 3.83, "p=4096": 0.35}, "stage1_toeplitz_s": {"p=4096": 0.30},
+                              "hardware": "Lomonosov cluster, Xeon X5570 nodes, MPI (Table 1)"}}
+        del bp, Fp, xp
+        torch.cuda.empty_cache()
     return out
 
 
@@ -711,6 +730,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-configs", action="store_true")
+    ap.add_argument("--only", default=None,
+                    help="comma-separated subset of the other configurations: " + ",".join(OTHER_CONFIGS))
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
