@@ -541,8 +541,8 @@ def test_adjoint_single(D, t, N, prec):
 
 
 @pytest.mark.parametrize("kind", ["uniform", "zeros", "wide", "1e200", "1e-200", "1e-300", "1e300", "mixed"])
-@pytest.mark.parametrize("bs,threads", [(0, 0), (14, 128), (15, 64), (16, 256)])
-def test_adjoint_gradient_sums_x_ranges(D, kind, bs, threads):
+@pytest.mark.parametrize("bs,threads,flags", [(0, 0, 0), (14, 128, 0), (15, 64, 0), (16, 256, 0), (0, 0, 1)])
+def test_adjoint_gradient_sums_x_ranges(D, kind, bs, threads, flags):
     """The MIXED adjoint forms the gradient sums in float-float where the forward solution of a
     window has a narrow exponent range, else on the FP64 pipe: both against the oracle's sums
     with x given directly (zeros, 200 decades, the ends of the FP64 range, windows of both kinds)."""
@@ -560,15 +560,53 @@ def test_adjoint_gradient_sums_x_ranges(D, kind, bs, threads):
             x[k:k + 4096] *= 10.0 ** rng.uniform(-40, 40, len(x[k:k + 4096]))
     elif kind != "uniform":
         x *= float(kind)
-    plan = D.Plan(*t, N, precision=1, block_size=bs, threads=threads)
+    plan = D.Plan(*t, N, precision=1, block_size=bs, threads=threads, flags=flags)
     gF, gt = plan.adjoint(torch.from_numpy(w).cuda(), torch.from_numpy(x).cuda())
     assert plan.status() == 0
+    assert (plan.info["path"] == 2) == bool(flags)
     lam_ref, gt_ref = oracle.adjoint(t, w, x)
     assert rel(gF.cpu().numpy(), lam_ref) < TOL
     # each sum against the sum of its terms' magnitudes (the bound of an FP64 dot product)
     mag = np.array([np.dot(np.abs(lam_ref[1:]), np.abs(x[:-1])), np.dot(np.abs(lam_ref), np.abs(x)),
                     np.dot(np.abs(lam_ref[:-1]), np.abs(x[1:]))])
     assert np.all(np.abs(gt.cpu().numpy() - gt_ref) <= TOL * mag), (gt.cpu().numpy(), gt_ref)
+
+
+def test_adjoint_batched_gradient_sums_x_ranges(D):
+    """The batched MIXED adjoint with forward solutions of every kind in one batch: per-system
+    sums from float-float and FP64 windows, combined by the fixed-order finalisation."""
+    rng = np.random.default_rng(23)
+    Ns = np.array([5000, 70001, 4096, 300, 123457, 65536], dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(Ns)[:-1]]).astype(np.int64)
+    tm1 = rng.uniform(-1.0, -0.5, Ns.size)
+    tp1 = rng.uniform(-1.0, -0.5, Ns.size)
+    t0 = rng.uniform(2.3, 4.0, Ns.size)
+    w = rng.uniform(-1, 1, int(Ns.sum()))
+    x = rng.uniform(-1, 1, int(Ns.sum()))
+    kinds = ["uniform", "zeros", "wide", "1e-250", "mixed", "1e250"]
+    for s_, k in enumerate(kinds):
+        sl = slice(off[s_], off[s_] + Ns[s_])
+        if k == "zeros":
+            x[sl][rng.integers(0, Ns[s_], 20)] = 0.0
+        elif k == "wide":
+            x[sl] *= 10.0 ** rng.uniform(-100, 100, Ns[s_])
+        elif k == "mixed":
+            x[sl][: Ns[s_] // 2] *= 10.0 ** rng.uniform(-60, 60, Ns[s_] // 2)
+        elif k != "uniform":
+            x[sl] *= float(k)
+    b = D.Batch(Ns, tm1, t0, tp1, precision=1)
+    gF, gt = b.adjoint(torch.from_numpy(w).cuda(), torch.from_numpy(x).cuda())
+    assert b.status() == 0
+    gF, gt = gF.cpu().numpy(), gt.cpu().numpy()
+    for s_ in range(Ns.size):
+        sl = slice(off[s_], off[s_] + Ns[s_])
+        tt = (tm1[s_], t0[s_], tp1[s_])
+        lam, g = oracle.adjoint(tt, w[sl], x[sl])
+        xs = x[sl]
+        mag = np.array([np.dot(np.abs(lam[1:]), np.abs(xs[:-1])), np.dot(np.abs(lam), np.abs(xs)),
+                        np.dot(np.abs(lam[:-1]), np.abs(xs[1:]))])
+        assert rel(gF[sl], lam) < TOL, kinds[s_]
+        assert np.all(np.abs(gt[s_] - g) <= TOL * mag), (kinds[s_], gt[s_], g)
 
 
 def test_adjoint_general_path(D):
