@@ -118,7 +118,7 @@ __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow_, int 
         *reinterpret_cast<float4*>(row) = make_float4(xh.x, xl.x, xh.y, xl.y);
       else if (FAST)
         *reinterpret_cast<double2*>(row) =
-            make_double2(join_fast(xh.x, xl.x, wscale, fk), join_fast(xh.y, xl.y, wscale, fk));
+            make_double2(join_fast(xh.x, xl.x, fk), join_fast(xh.y, xl.y, fk));
       else
         *reinterpret_cast<double2*>(row) =
             make_double2(join_dadd(xh.x, xl.x, wscale), join_dadd(xh.y, xl.y, wscale));
@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
       constexpr bool FJ = decltype(fj_)::value, XF = decltype(xf_)::value;
       auto join = [&](float2 v) {
         if constexpr (FJ)
-          return join_fast(v.x, v.y, wscale, fk);
+          return join_fast(v.x, v.y, fk);
         else
           return join_dadd(v.x, v.y, wscale);
       };
