@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
     if (n == 16 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0u) {
       // jlo is a multiple of 16: row 2 (tid % 8) of block hl + tid / 8 + k NT / 8, fixed strides
       const double* col = S + (size_t)(2 * (tid & 7)) * LD + hl + (tid >> 3);
-#pragma unroll 1
+#pragma unroll 2
       for (int j = jlo + 2 * tid; j < jhi; j += 2 * NT, col += NT / 8) put2(j, col);
     } else if ((n & 1) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0u) {
       int b = (jlo + 2 * tid) / n, i = (jlo + 2 * tid) - ((jlo + 2 * tid) / n) * n;
