@@ -15,6 +15,7 @@
 // General path: the beta pass (MODE_BETA) leaves the local solutions y in x, and the apply
 // pass (MODE_APPLY) reads them back instead of F, so the local solve runs once.
 #pragma once
+#include <type_traits>
 #include "ff.cuh"
 #include "window.cuh"
 
@@ -287,21 +288,45 @@ __global__ void __launch_bounds__(NT) k_window_gen_ff(const GenArgs G) {
   double* col = S + tid;
 
   // ---------------------------------------------------------------- window scale
+  // largest |value| of the tile near 2^16; a tile of normal values within 2^119 of each other
+  // (not near the ends of the FP64 range) takes the fast split and join of ff.cuh
   int wscale;
+  bool fast;
   {
-    unsigned hmax = 0u;
+    unsigned hmax = 0u, hmin = 0xFFFFFFFFu;
     if (act)
-      for (int i = 0; i < nbk; ++i) hmax = max(hmax, (unsigned)__double2hiint(col[i * LD]) & 0x7FFFFFFFu);
+      for (int i = 0; i < nbk; ++i) {
+        const unsigned h = (unsigned)__double2hiint(col[i * LD]) & 0x7FFFFFFFu;
+        hmax = max(hmax, h);
+        hmin = min(hmin, h);
+      }
     hmax = __reduce_max_sync(0xffffffffu, hmax);
+    hmin = __reduce_min_sync(0xffffffffu, hmin);
     unsigned* sexp = reinterpret_cast<unsigned*>(swa);
-    if ((tid & 31) == 0) sexp[tid >> 5] = hmax;
+    if ((tid & 31) == 0) {
+      sexp[tid >> 5] = hmax;
+      sexp[NW + (tid >> 5)] = hmin;
+    }
     __syncthreads();
     hmax = 0u;
-    for (int w = 0; w < NW; ++w) hmax = max(hmax, sexp[w]);
+    hmin = 0xFFFFFFFFu;
+    for (int w = 0; w < NW; ++w) {
+      hmax = max(hmax, sexp[w]);
+      hmin = min(hmin, sexp[NW + w]);
+    }
     __syncthreads();
-    const int emax = (int)(hmax >> 20);
+    const int emax = (int)(hmax >> 20), emin = (int)(hmin >> 20);
     wscale = (emax == 2047) ? 0 : ((emax == 0) ? 1000 : max(-1000, min(1000, (1023 + 16) - emax)));
+    fast = (emin >= 1) && (emax >= 239) && (emax <= 1935) && (emax - emin <= 119);
   }
+  const FastK fk = fast_k(wscale);
+  // the tile's FP64 value -> (h, l) at the window scale; FASTC: std::true_type in a fast tile
+  auto split_t = [&](double d, float& h, float& l, auto fastc) {
+    if constexpr (decltype(fastc)::value)
+      split_fast(d, fk, h, l);
+    else
+      split_sc(d, wscale, h, l);
+  };
 
   const float2* ra = reinterpret_cast<const float2*>(G.rows + GF_A * G.stride);
   const float2* rd = reinterpret_cast<const float2*>(G.rows + GF_RD * G.stride);
@@ -320,49 +345,55 @@ __global__ void __launch_bounds__(NT) k_window_gen_ff(const GenArgs G) {
   if (act && A.mode != MODE_APPLY) {
     // the factors of four rows are loaded ahead of their dependent steps (the per-row global
     // loads would otherwise sit on the recurrence's critical path)
-    ffv z = ff_zero();
-    int i = 0;
-    for (; i + 4 <= nbk; i += 4) {
-      const int64_t k = k0 + 32 * i;
-      ffv a4[4], d4[4];
+    auto sweeps = [&](auto fastc) {
+      ffv z = ff_zero();
+      int i = 0;
+      for (; i + 4 <= nbk; i += 4) {
+        const int64_t k = k0 + 32 * i;
+        ffv a4[4], d4[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        a4[u] = ldff(ra, k + 32 * u);
-        d4[u] = ldff(rd, k + 32 * u);
+        for (int u = 0; u < 4; ++u) {
+          a4[u] = ldff(ra, k + 32 * u);
+          d4[u] = ldff(rd, k + 32 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float fh, fl;
+          split_t(col[(i + u) * LD], fh, fl, fastc);
+          z = ff_mul(ff_fma(ff_neg(a4[u]), z, ffv{fh, fl}), d4[u]);
+          colf[(i + u) * LD] = make_float2(z.h, z.l);
+        }
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (; i < nbk; ++i) {
+        const int64_t k = k0 + 32 * i;
         float fh, fl;
-        split_sc(col[(i + u) * LD], wscale, fh, fl);
-        z = ff_mul(ff_fma(ff_neg(a4[u]), z, ffv{fh, fl}), d4[u]);
-        colf[(i + u) * LD] = make_float2(z.h, z.l);
+        split_t(col[i * LD], fh, fl, fastc);
+        z = ff_mul(ff_fma(ff_neg(ldff(ra, k)), z, ffv{fh, fl}), ldff(rd, k));
+        colf[i * LD] = make_float2(z.h, z.l);
       }
-    }
-    for (; i < nbk; ++i) {
-      const int64_t k = k0 + 32 * i;
-      float fh, fl;
-      split_sc(col[i * LD], wscale, fh, fl);
-      z = ff_mul(ff_fma(ff_neg(ldff(ra, k)), z, ffv{fh, fl}), ldff(rd, k));
-      colf[i * LD] = make_float2(z.h, z.l);
-    }
-    ffv y = ff_zero();
-    i = nbk - 1;
-    for (; i - 3 >= 0; i -= 4) {
-      ffv c4[4];
+      ffv y = ff_zero();
+      i = nbk - 1;
+      for (; i - 3 >= 0; i -= 4) {
+        ffv c4[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) c4[u] = ldff(rc, k0 + 32 * (i - u));
+        for (int u = 0; u < 4; ++u) c4[u] = ldff(rc, k0 + 32 * (i - u));
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float2 zz = colf[(i - u) * LD];
-        y = ff_fma(ff_neg(c4[u]), y, ffv{zz.x, zz.y});
-        colf[(i - u) * LD] = make_float2(y.h, y.l);
+        for (int u = 0; u < 4; ++u) {
+          const float2 zz = colf[(i - u) * LD];
+          y = ff_fma(ff_neg(c4[u]), y, ffv{zz.x, zz.y});
+          colf[(i - u) * LD] = make_float2(y.h, y.l);
+        }
       }
-    }
-    for (; i >= 0; --i) {
-      const float2 zz = colf[i * LD];
-      y = ff_fma(ff_neg(ldff(rc, k0 + 32 * i)), y, ffv{zz.x, zz.y});
-      colf[i * LD] = make_float2(y.h, y.l);
-    }
+      for (; i >= 0; --i) {
+        const float2 zz = colf[i * LD];
+        y = ff_fma(ff_neg(ldff(rc, k0 + 32 * i)), y, ffv{zz.x, zz.y});
+        colf[i * LD] = make_float2(y.h, y.l);
+      }
+    };
+    if (fast)
+      sweeps(std::true_type());
+    else
+      sweeps(std::false_type());
     const float2 y0 = colf[0], ye = colf[(nbk - 1) * LD];
     alpha = join_dadd(y0.x, y0.y, wscale);
     omega = join_dadd(ye.x, ye.y, wscale);
@@ -410,21 +441,30 @@ __global__ void __launch_bounds__(NT) k_window_gen_ff(const GenArgs G) {
     split_sc(XL, wscale, ch, cl);
     split_sc(XR, wscale, dh, dl);
     const ffv cL{ch, cl}, cR{dh, dl};
+    auto interiors = [&](auto fastc) {
 #pragma unroll 4
-    for (int i = 0; i < nbk; ++i) {
-      const int64_t k = k0 + 32 * i;
-      ffv y;
-      if (A.mode == MODE_APPLY) {
-        float yh, yl;
-        split_sc(col[i * LD], wscale, yh, yl);
-        y = ffv{yh, yl};
-      } else {
-        const float2 yy = colf[i * LD];
-        y = ffv{yy.x, yy.y};
+      for (int i = 0; i < nbk; ++i) {
+        const int64_t k = k0 + 32 * i;
+        ffv y;
+        if (A.mode == MODE_APPLY) {
+          float yh, yl;
+          split_t(col[i * LD], yh, yl, fastc);
+          y = ffv{yh, yl};
+        } else {
+          const float2 yy = colf[i * LD];
+          y = ffv{yy.x, yy.y};
+        }
+        const ffv xv = ff_fma(cR, ldff(rw, k), ff_fma(cL, ldff(rv, k), y));
+        if constexpr (decltype(fastc)::value)
+          col[i * LD] = join_fast(xv.h, xv.l, fk);
+        else
+          col[i * LD] = join_dadd(xv.h, xv.l, wscale);
       }
-      const ffv xv = ff_fma(cR, ldff(rw, k), ff_fma(cL, ldff(rv, k), y));
-      col[i * LD] = join_dadd(xv.h, xv.l, wscale);
-    }
+    };
+    if (fast)
+      interiors(std::true_type());
+    else
+      interiors(std::false_type());
   }
   __syncthreads();
 

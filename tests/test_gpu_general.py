@@ -80,6 +80,27 @@ def test_general_mixed_scaled_rows(D):
     assert rel(x, oracle.thomas_tridiag(a, b, c, F)) < TOL, info
 
 
+@pytest.mark.parametrize("kind", ["zeros", "wide", "1e250", "1e-250", "1e300"])
+@pytest.mark.parametrize("flags", [0, 1])
+def test_general_mixed_right_hand_side_ranges(D, kind, flags):
+    """Tiles outside the fast split and join (exact zeros, 200 decades, the ends of the FP64
+    range) take the general conversions; tiles inside take the fast ones; both forms of path."""
+    N = 150001
+    a, b, c = dominant(N, 21)
+    rng = np.random.default_rng(22)
+    F = rng.standard_normal(N)
+    if kind == "zeros":
+        F[rng.integers(0, N, 500)] = 0.0
+        F[40000:45000] = 0.0
+    elif kind == "wide":
+        F *= 10.0 ** rng.uniform(-100, 100, N)
+    else:
+        F *= float(kind)
+    x, info = gen_solve(D, a, b, c, F, precision=1, flags=flags)
+    assert info["precision"] == 1 and (info["path"] == 2 or not flags)
+    assert rel(x, oracle.thomas_tridiag(a, b, c, F)) < TOL, info
+
+
 @pytest.mark.parametrize("prelim", [HOST, DEVICE])
 @pytest.mark.parametrize("threads", [64, 128, 256])
 @pytest.mark.parametrize("bs", [2, 3, 16, 45])
