@@ -64,9 +64,12 @@ typedef enum {
 /* ---------------------------------------------------------------- options */
 typedef enum {
   DICH_PREC_F64 = 0,    /* every step in FP64 */
-  DICH_PREC_MIXED = 1,  /* local sweeps in FP32 with error-free transformations (compensated),
-                           interface tree, beta and scan coefficients in FP64 */
-  DICH_PREC_AUTO = 2    /* MIXED where its error bound is below 1e-13 relative, else F64 */
+  DICH_PREC_MIXED = 1,  /* local sweeps and spike correction in compensated FP32 (float-float, one
+                           power-of-two scale per window); block quantities and tree in float-float
+                           (Toeplitz) or FP64 (general matrices).  Toeplitz plans need the scale
+                           factor g = -1/q (T = -q (1 - rs E^-1)(1 - ib E)) within 2^-60..2^60 */
+  DICH_PREC_AUTO = 2    /* MIXED where the two recurrences' error gain is at most 24 (error about
+                           1e-14 relative) and MIXED's range conditions hold, else F64 */
 } dich_precision;
 
 enum {
@@ -123,7 +126,8 @@ typedef struct dich_gen_s* dich_gen_t;
  * the spikes of the block operator and the per-block exterior ratios (eq. 24-25 in
  * overflow-free factored form).  N = 0 and N = 1 are accepted (trivial solves).
  * Errors: DICH_ERR_ARG (N < 0, out == NULL, bad opts), DICH_ERR_NOT_DOMINANT,
- * DICH_ERR_SINGULAR (t_0 == 0).  On error *out is set to NULL. */
+ * DICH_ERR_SINGULAR (t_0 == 0), DICH_ERR_UNSUPPORTED (DICH_PREC_MIXED requested with the scale
+ * factor g outside 2^-60..2^60).  On error *out is set to NULL. */
 int dichotomy_plan(double t_m1, double t_0, double t_1, int64_t N, dich_plan_t* out);
 int dichotomy_plan_ex(double t_m1, double t_0, double t_1, int64_t N, const dich_opts* opts,
                       dich_plan_t* out);
@@ -237,7 +241,8 @@ int dichotomy_solve_noalloc(double t_m1, double t_0, double t_1, int64_t N, cons
  * Prepare (host only) runs the preliminary step of every system, chooses block sizes,
  * the precision form per system (DICH_PREC_AUTO) and an LPT-ordered list of windows.
  * h_N, h_offset, h_tm1, h_t0, h_tp1: nsys entries each on the host.
- * Errors: DICH_ERR_ARG, DICH_ERR_NOT_DOMINANT / DICH_ERR_SINGULAR (first bad system). */
+ * Errors: DICH_ERR_ARG, DICH_ERR_NOT_DOMINANT / DICH_ERR_SINGULAR (first bad system),
+ * DICH_ERR_UNSUPPORTED (DICH_PREC_MIXED with a system's scale factor outside 2^-60..2^60). */
 int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_offset,
                             const double* h_tm1, const double* h_t0, const double* h_tp1,
                             const dich_opts* opts, dich_batch_t* out);

@@ -95,10 +95,19 @@ double recurrence_gain(const Roots& r) {
 // errors by at most this factor.
 constexpr double kMixedGainLimit = 24.0;
 
+// MIXED holds xp = g X at the window scale of F in float-float, so the scale factor g = -1/q
+// of T = -q (1 - rs E^-1)(1 - ib E) must keep the scaled solution and its low parts inside the
+// float range: |g| within 2^-60..2^60 (|t| roughly within the same range).
+bool mixed_scale_ok(const Roots& r) {
+  const double a = std::fabs(r.g);
+  return a >= 0x1p-60 && a <= 0x1p60;
+}
+
+// the form of a system; -1: MIXED requested where its scale range does not hold
 int pick_form(int prec, const Roots& r) {
   if (prec == DICH_PREC_F64) return FORM_F64;
-  if (prec == DICH_PREC_MIXED) return FORM_MIXED;
-  return recurrence_gain(r) <= kMixedGainLimit ? FORM_MIXED : FORM_F64;
+  if (prec == DICH_PREC_MIXED) return mixed_scale_ok(r) ? FORM_MIXED : -1;
+  return (recurrence_gain(r) <= kMixedGainLimit && mixed_scale_ok(r)) ? FORM_MIXED : FORM_F64;
 }
 
 void split_ff(double d, float& h, float& l) {
@@ -546,6 +555,10 @@ int dichotomy_plan_ex(double t_m1, double t_0, double t_1, int64_t N, const dich
   p->opts = o;
   const Roots r = toeplitz_roots(t_m1, t_0, t_1);
   p->form = pick_form(o.prec, r);
+  if (p->form < 0) {
+    delete p;
+    return DICH_ERR_UNSUPPORTED;
+  }
   p->NT = o.NT ? o.NT : default_threads(p->form);
   if (N >= 2) {
     const int n0 = choose_n(N, window_blocks(p->NT, p->form),
@@ -1060,6 +1073,10 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
     }
     const Roots r = toeplitz_roots(h_tm1[s], h_t0[s], h_tp1[s]);
     b->form[s] = pick_form(o.prec, r);
+    if (b->form[s] < 0) {
+      delete b;
+      return DICH_ERR_UNSUPPORTED;
+    }
     if (h_N[s] < 2) {
       SysPlan& q = b->fwd[s].rec;
       std::memset(&q, 0, sizeof(q));

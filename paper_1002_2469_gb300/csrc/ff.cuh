@@ -251,18 +251,16 @@ __device__ __forceinline__ void split_fast(double d, const FastK& k, float& hi, 
 // (h, l) * 2^-s -> FP64 in a fast window: both floats rebuilt as exact FP64 bit patterns and
 // added once on the FP64 pipe.  A float's bits shifted right by 3 (sign kept) give the FP64
 // fraction and exponent fields; adding (896 - s) << 20 rebiases and unscales the exponent,
-// which stays inside [1, 2046] for every normal float because s is in [-896, 800].  A zero
-// or subnormal l contributes nothing (exactly zero, or a subnormal FP64 far below half an
-// ulp of the result when s <= 800); a zero h contributes zero, and a subnormal h (below 2^-126
-// in window units, under 2^-142 of the window's largest |F|) is dropped -- no branch, so the
-// per-row loops stay free of divergent calls.
+// which stays inside [1, 2046] for every normal float because s is in [-896, 800].  No part is
+// tested: a zero or subnormal part is rebuilt as if its exponent field were that of a normal
+// float, i.e. as a value of magnitude below 2^-126 in window units -- at most 2^-141 of the
+// window's largest |F| for both parts together, far inside the form's norm-wise error -- so the
+// per-row loops carry neither branches nor selects.
 __device__ __forceinline__ double join_fast(float h, float l, const FastK& k) {
   const unsigned bh = __float_as_uint(h), bl = __float_as_uint(l);
-  const bool nh = (bh & 0x7F800000u) != 0u, nl = (bl & 0x7F800000u) != 0u;
-  const unsigned hh = nh ? ((unsigned)((int)bh >> 3) & 0x8FFFFFFFu) + k.join : (bh & 0x80000000u);
-  const unsigned hw = nh ? (bh << 29) : 0u;
-  const unsigned lh = ((unsigned)((int)bl >> 3) & 0x8FFFFFFFu) + (nl ? k.join : 0u);
-  return __dadd_rn(__hiloint2double((int)hh, (int)hw), __hiloint2double((int)lh, (int)(bl << 29)));
+  const unsigned hh = ((unsigned)((int)bh >> 3) & 0x8FFFFFFFu) + k.join;
+  const unsigned lh = ((unsigned)((int)bl >> 3) & 0x8FFFFFFFu) + k.join;
+  return __dadd_rn(__hiloint2double((int)hh, (int)(bh << 29)), __hiloint2double((int)lh, (int)(bl << 29)));
 }
 
 // (h, l) * 2^-s -> FP64 in any window: both parts converted exactly by integer operations and

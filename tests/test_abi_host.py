@@ -149,6 +149,25 @@ def test_precision_policy_auto():
     assert strong["precision"] == 1 and weak["precision"] == 0
 
 
+def test_precision_policy_scale_range():
+    """MIXED keeps g X at the window scale of F: |g| = 1/|q| within 2^-60..2^60.  Outside it AUTO
+    takes FP64 and an explicit MIXED request is refused (DICH_ERR_UNSUPPORTED)."""
+    t = np.array([-1.2, 2.5, -0.8])
+    for k in (-40, 0, 40):
+        assert plan_info(tuple(t * 2.0 ** k), 1 << 16, precision=2)["precision"] == 1
+        assert status_of(tuple(t * 2.0 ** k), 1 << 16, precision=1) == 0
+    for k in (-80, 80):
+        assert plan_info(tuple(t * 2.0 ** k), 1 << 16, precision=2)["precision"] == 0
+        assert status_of(tuple(t * 2.0 ** k), 1 << 16, precision=1) == 11
+        assert status_of(tuple(t * 2.0 ** k), 1 << 16, precision=0) == 0
+    from paper_1002_2469_gb300 import dichotomy as D
+    N = np.array([1000, 2000])
+    with pytest.raises(D.DichotomyError):
+        D.dichotomy_batch_prepare(N, np.array([0, 1000]), np.array([-1.2, -1.2 * 2.0 ** 80]),
+                                  np.array([2.5, 2.5 * 2.0 ** 80]), np.array([-0.8, -0.8 * 2.0 ** 80]),
+                                  D.make_opts(precision=1))
+
+
 def test_batch_prepare_host_only():
     from paper_1002_2469_gb300 import dichotomy as D
     N = np.array([0, 1, 2, 100, 5000, 300000])

@@ -523,6 +523,18 @@ def test_c4_full_size_sampled(D):
         assert rel(xd[o:o + n].cpu().numpy(), ref) < TOL, s
 
 
+@pytest.mark.parametrize("k", [-100, -80, -40, 0, 40, 80, 100])
+def test_scaled_coefficients(D, k):
+    """T scaled by 2^k: AUTO keeps MIXED while the scale factor g stays within 2^-60..2^60 and
+    takes FP64 beyond; both stay within the tolerance (and with F scaled the other way)."""
+    t = tuple(np.array([-1.2, 2.5, -0.8]) * 2.0 ** k)
+    N = 300001
+    F = np.random.default_rng(5).standard_normal(N) * 2.0 ** (k // 2)
+    x, info = gpu_solve(D, t, F, precision=2)
+    assert info["precision"] == (1 if abs(k) <= 40 else 0)
+    assert rel(x, oracle.thomas(t, F)) < TOL
+
+
 # ------------------------------------------------------------------ adjoint
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("t", [(-1.2, 2.5, -0.8), (0.7, 2.5, -1.1), (-1.0, 4.0, -1.0)])
