@@ -227,6 +227,76 @@ __global__ void __launch_bounds__(NT) k_window_gen(const GenArgs G) {
 // alpha, omega leave as FP64 for the FP64 beta map and tree (one block per thread, so the tree
 // costs a few FP64 operations per row), and the correction x = y + x_{s-1} v + x_{e+1} w runs in
 // float-float before one join to FP64 per row.
+// block record entry j as a float-float pair (the records are ratios of order one on the paths
+// that run the tree in the window; the general split flushes what lies below the float range)
+__device__ __forceinline__ ffv gen_rec_ff(const double* bc, int j) {
+  float h, l;
+  split_sc(bc[j], 0, h, l);
+  return ffv{h, l};
+}
+
+// the dichotomy tree of one window (eq. 15, 17-19) in float-float, one block per thread: the
+// steps of tree_f64 with the block's beta and the returned first/last values of the neighbours
+// in window units (XL = x_{s-1}, XR = x_{e+1}; left untouched at the ends of the system)
+template <int NT>
+__device__ __forceinline__ void tree_gen_ff(const double* bc, bool act, ffv bL, ffv bR, int64_t mb, int64_t P,
+                                            int nwin, int tid, double* swa, double* sxs, double* sxe, ffv& XL,
+                                            ffv& XR) {
+  constexpr int NW = NT / 32;
+  const int lane = tid & 31, wid = tid >> 5;
+  ffv pa = act ? gen_rec_ff(bc, BC_A) : ff_one();
+  ffv pb = act ? ff_mul(gen_rec_ff(bc, BC_B), bR) : ff_zero();
+  ffv qa = act ? gen_rec_ff(bc, BC_C) : ff_one();
+  ffv qb = act ? ff_mul(gen_rec_ff(bc, BC_D), bL) : ff_zero();
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const ffv ya = ff_shfl_up(pa, d), yb = ff_shfl_up(pb, d);
+    const ffv za = ff_shfl_down(qa, d), zb = ff_shfl_down(qb, d);
+    if (lane >= d) {
+      pb = ff_fma(pa, yb, pb);
+      pa = ff_mul(pa, ya);
+    }
+    if (lane + d < 32) {
+      qb = ff_fma(qa, zb, qb);
+      qa = ff_mul(qa, za);
+    }
+  }
+  ffv* sw = reinterpret_cast<ffv*>(swa);   // 4 NW pairs in the 4 NW doubles of the scratch
+  if (lane == 31) {
+    sw[wid] = pa;
+    sw[NW + wid] = pb;
+  }
+  if (lane == 0) {
+    sw[2 * NW + wid] = qa;
+    sw[3 * NW + wid] = qb;
+  }
+  // previous lane's inclusive prefix, next lane's inclusive suffix
+  ffv ea = ff_shfl_up(pa, 1), eb = ff_shfl_up(pb, 1);
+  ffv fa = ff_shfl_down(qa, 1), fb = ff_shfl_down(qb, 1);
+  if (lane == 0) {
+    ea = ff_one();
+    eb = ff_zero();
+  }
+  if (lane == 31) {
+    fa = ff_one();
+    fb = ff_zero();
+  }
+  __syncthreads();
+  ffv Aw = ff_zero(), Bw = ff_zero();   // zero coupling enters at both window ends
+  for (int w = 0; w < wid; ++w) Aw = ff_fma(sw[w], Aw, sw[NW + w]);
+  for (int w = NW - 1; w > wid; --w) Bw = ff_fma(sw[2 * NW + w], Bw, sw[3 * NW + w]);
+  const ffv Am = ff_fma(ea, Aw, eb), Bm = ff_fma(fa, Bw, fb);
+  ffv* fs = reinterpret_cast<ffv*>(sxs);
+  ffv* fe = reinterpret_cast<ffv*>(sxe);
+  fs[tid] = ff_add(ff_fma(gen_rec_ff(bc, BC_TL), Bm, bL), Am);   // x_s (eq. 18)
+  fe[tid] = ff_fma(gen_rec_ff(bc, BC_TR), Am, ff_add(bR, Bm));   // x_e
+  __syncthreads();
+  if (act) {
+    if (!(mb == 0 || tid == 0)) XL = fe[tid - 1];
+    if (!(mb == P - 1 || tid + 1 >= nwin)) XR = fs[tid + 1];
+  }
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) k_window_gen_ff(const GenArgs G) {
   constexpr int LD = NT + 1;
@@ -341,7 +411,6 @@ __global__ void __launch_bounds__(NT) k_window_gen_ff(const GenArgs G) {
   };
 
   // ---------------------------------------------------------------- local solves (a1), float-float
-  double alpha = 0.0, omega = 0.0;
   if (act && A.mode != MODE_APPLY) {
     // the factors of four rows are loaded ahead of their dependent steps (the per-row global
     // loads would otherwise sit on the recurrence's critical path)
@@ -394,19 +463,16 @@ __global__ void __launch_bounds__(NT) k_window_gen_ff(const GenArgs G) {
       sweeps(std::true_type());
     else
       sweeps(std::false_type());
-    const float2 y0 = colf[0], ye = colf[(nbk - 1) * LD];
-    alpha = join_dadd(y0.x, y0.y, wscale);
-    omega = join_dadd(ye.x, ye.y, wscale);
   }
 
-  // ---------------------------------------------------------------- beta (eq. 16), FP64
+  // ---------------------------------------------------------------- beta (eq. 16)
   const double* bc = A.tabs + pp->o_bcl + (act ? mb : 0) * kBC;
-  const double bL = act ? fma(bc[BC_M00], alpha, bc[BC_M01] * omega) : 0.0;
-  const double bR = act ? fma(bc[BC_M10], alpha, bc[BC_M11] * omega) : 0.0;
-  if (A.mode == MODE_BETA) {   // beta and the block solutions y (joined to FP64) leave the window
+  if (A.mode == MODE_BETA) {   // beta (FP64) and the block solutions y (joined) leave the window
     if (act) {
-      A.beta[2 * (pp->gboff + mb)] = bL;
-      A.beta[2 * (pp->gboff + mb) + 1] = bR;
+      const float2 y0 = colf[0], ye = colf[(nbk - 1) * LD];
+      const double alpha = join_dadd(y0.x, y0.y, wscale), omega = join_dadd(ye.x, ye.y, wscale);
+      A.beta[2 * (pp->gboff + mb)] = fma(bc[BC_M00], alpha, bc[BC_M01] * omega);
+      A.beta[2 * (pp->gboff + mb) + 1] = fma(bc[BC_M10], alpha, bc[BC_M11] * omega);
       for (int i = 0; i < nbk; ++i) {
         const float2 yy = colf[i * LD];
         col[i * LD] = join_dadd(yy.x, yy.y, wscale);
@@ -427,20 +493,29 @@ __global__ void __launch_bounds__(NT) k_window_gen_ff(const GenArgs G) {
     return;
   }
 
-  double XL = 0.0, XR = 0.0;
-  if (A.mode == MODE_FULL) {
-    tree_f64<NT>(bc, act, bL, bR, mb, P, nwin, tid, swa, sxs, sxe, XL, XR);
+  // the neighbours' end values x_{s-1}, x_{e+1} in window units
+  ffv cL = ff_zero(), cR = ff_zero();
+  if (A.mode == MODE_FULL) {   // beta and the tree in float-float (window units)
+    ffv bL = ff_zero(), bR = ff_zero();
+    if (act) {
+      const float2 y0 = colf[0], ye = colf[(nbk - 1) * LD];
+      const ffv al{y0.x, y0.y}, om{ye.x, ye.y};
+      bL = ff_fma(gen_rec_ff(bc, BC_M00), al, ff_mul(gen_rec_ff(bc, BC_M01), om));
+      bR = ff_fma(gen_rec_ff(bc, BC_M10), al, ff_mul(gen_rec_ff(bc, BC_M11), om));
+    }
+    tree_gen_ff<NT>(bc, act, bL, bR, mb, P, nwin, tid, swa, sxs, sxe, cL, cR);
   } else if (act) {
-    XL = (mb == 0) ? 0.0 : A.iface[2 * (pp->gboff + mb - 1) + 1];
-    XR = (mb == P - 1) ? 0.0 : A.iface[2 * (pp->gboff + mb + 1)];
+    const double XL = (mb == 0) ? 0.0 : A.iface[2 * (pp->gboff + mb - 1) + 1];
+    const double XR = (mb == P - 1) ? 0.0 : A.iface[2 * (pp->gboff + mb + 1)];
+    float ch, cl, dh, dl;
+    split_sc(XL, wscale, ch, cl);
+    split_sc(XR, wscale, dh, dl);
+    cL = ffv{ch, cl};
+    cR = ffv{dh, dl};
   }
 
   // ---------------------------------------------------------------- interiors (eq. 7), float-float
   if (act) {
-    float ch, cl, dh, dl;
-    split_sc(XL, wscale, ch, cl);
-    split_sc(XR, wscale, dh, dl);
-    const ffv cL{ch, cl}, cR{dh, dl};
     auto interiors = [&](auto fastc) {
 #pragma unroll 4
       for (int i = 0; i < nbk; ++i) {
