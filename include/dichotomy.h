@@ -65,9 +65,10 @@ typedef enum {
 typedef enum {
   DICH_PREC_F64 = 0,    /* every step in FP64 */
   DICH_PREC_MIXED = 1,  /* local sweeps and spike correction in compensated FP32 (float-float, one
-                           power-of-two scale per window); block quantities and tree in float-float
-                           (Toeplitz) or FP64 (general matrices).  Toeplitz plans need the scale
-                           factor g = -1/q (T = -q (1 - rs E^-1)(1 - ib E)) within 2^-60..2^60 */
+                           power-of-two scale per window); block quantities and the in-window tree
+                           in float-float, the general path's block scan in FP64.  Toeplitz plans
+                           need the scale factor g = -1/q (T = -q (1 - rs E^-1)(1 - ib E)) within
+                           2^-60..2^60 */
   DICH_PREC_AUTO = 2    /* MIXED where the two recurrences' error gain is at most 24 (error about
                            1e-14 relative) and MIXED's range conditions hold, else F64 */
 } dich_precision;

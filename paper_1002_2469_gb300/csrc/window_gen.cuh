@@ -223,10 +223,11 @@ __global__ void __launch_bounds__(NT) k_window_gen(const GenArgs G) {
 // The same steps with the per-row work in float-float arithmetic (ff.cuh) on values scaled per
 // window by one exact power of two (largest |F| of the window near 2^16): the per-row tables
 // hold float-float pairs (hi, lo) in the 8-byte slots of the FP64 tables, the local solve runs
-// z_i = (F_i - a_i z_{i-1}) rd_i and y_i = z_i - cp_i y_{i+1} in float-float, the block ends
-// alpha, omega leave as FP64 for the FP64 beta map and tree (one block per thread, so the tree
-// costs a few FP64 operations per row), and the correction x = y + x_{s-1} v + x_{e+1} w runs in
-// float-float before one join to FP64 per row.
+// z_i = (F_i - a_i z_{i-1}) rd_i and y_i = z_i - cp_i y_{i+1} in float-float; in a window that
+// runs the tree (MODE_FULL) beta and the tree are float-float too (tree_gen_ff: the block records
+// split once per block, so no FP64 work per block), on the general path beta leaves as FP64 for
+// the FP64 block scan; the correction x = y + x_{s-1} v + x_{e+1} w runs in float-float before
+// one join to FP64 per row.  Tiles of narrow exponent range take the fast split and join.
 // block record entry j as a float-float pair (the records are ratios of order one on the paths
 // that run the tree in the window; the general split flushes what lies below the float range)
 __device__ __forceinline__ ffv gen_rec_ff(const double* bc, int j) {
