@@ -63,17 +63,71 @@ def _src_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel_key: str):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+def _profiled(kernel_key: str):
+    """The committed ncu record of a kernel (DRAM bytes per launch, what binds it), if it was
+    taken on the current source; else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             d = json.load(fh)
         ent = d.get(kernel_key)
         if ent and ent.get("src_hash") == _src_hash():
-            return ent.get("dram_bytes_per_launch")
+            return ent
     except Exception:
         pass
     return None
+
+
+def _traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+    ent = _profiled(kernel_key)
+    return ent.get("dram_bytes_per_launch") if ent else None
+
+
+def _bound(kernel_key: str, default: str):
+    """What binds the kernel according to its committed profile (current source only)."""
+    ent = _profiled(kernel_key)
+    return ent.get("bound", default) if ent else default
+
+
+def batched_cpu_baseline(tm1, t0, tp1, N, off, F, budget_s=4.0, adjoint_w=None):
+    """The oracle's per-system Thomas (and, with adjoint_w, its adjoint) over all visible host
+    cores, on the whole batch or on its first systems up to about budget_s seconds of work.
+    Returns the cpu_baseline record (Gunknowns/s, cores, what the sample was)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    cores = len(os.sched_getaffinity(0))
+    N = np.asarray(N, dtype=np.int64)
+    off = np.asarray(off, dtype=np.int64)
+    # a first pass on a small prefix estimates the rate, which sizes the timed sample
+    k0 = int(min(N.size, max(1, np.searchsorted(np.cumsum(N), 1 << 22) + 1)))
+
+    def run(k):
+        if adjoint_w is None:
+            oracle.thomas_batched(tm1[:k], t0[:k], tp1[:k], N[:k], off[:k] - off[0], F[off[0]:off[k - 1] + N[k - 1]])
+            return
+        def one(s):
+            sl = slice(int(off[s]), int(off[s] + N[s]))
+            tt = (tm1[s], t0[s], tp1[s])
+            oracle.adjoint(tt, adjoint_w[sl], oracle.thomas(tt, F[sl]))
+        with ThreadPoolExecutor(cores) as ex:
+            list(ex.map(one, range(k)))
+
+    t_ = time.perf_counter()
+    run(k0)
+    rate = int(N[:k0].sum()) / max(time.perf_counter() - t_, 1e-6)
+    k = int(min(N.size, max(k0, np.searchsorted(np.cumsum(N), rate * budget_s) + 1)))
+    reps, t_ = 0, time.perf_counter()
+    while True:
+        run(k)
+        reps += 1
+        el = time.perf_counter() - t_
+        if el > 0.5 * budget_s or reps >= 20:
+            break
+    unk = int(N[:k].sum())
+    what = "forward Thomas + adjoint (transposed Thomas, three sums)" if adjoint_w is not None else "Thomas"
+    return {"value": round(reps * unk / el / 1e9, 4), "unit": "Gunknowns/s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} pass(es) over the first {k} of {N.size} systems ({unk} unknowns): the oracle's FP64 "
+                      f"{what} per system over a pool of {cores} host threads"}
 
 
 class ClockSampler:
@@ -265,7 +319,8 @@ def run_gpu(args):
         f64.pop("x", None)
         torch.cuda.empty_cache()
         only = None if args.only is None else set(args.only.split(","))
-        others = other_configs(D, W, oracle, stream, world, steps=max(5, min(args.steps, 20)), only=only)
+        others = other_configs(D, W, oracle, stream, world, steps=max(5, min(args.steps, 20)), only=only,
+                               cpu_leg=(rank == 0 and not args.no_cpu_baseline))
 
     if rank != 0:
         return
@@ -307,7 +362,8 @@ def run_gpu(args):
                        "backward_err": f64["backward_err"],
                        "bound": "alu (FP64 pipe)", "block_size": f64["info"]["n"],
                        "threads_per_window": f64["info"]["threads"], "device_status": f64["status"]},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": _bound(kernel_key, "unprofiled"), "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": _traffic(kernel_key),
                      "peak_kind": peak_kind, "kernel": kernel_key,
                      "algorithmic_bytes_per_launch": BYTES_PER_UNKNOWN * N},
@@ -418,11 +474,12 @@ def cusparse_comparator(W, oracle, stream, steps):
 OTHER_CONFIGS = ("cusparse", "c1", "c2w", "c3", "c4", "c5", "f3", "f3n", "f4", "table1")
 
 
-def other_configs(D, W, oracle, stream, world, steps=10, only=None):
+def other_configs(D, W, oracle, stream, world, steps=10, only=None, cpu_leg=True):
     """C1 (latency), the weakly dominant C2 variant, C3 (2-D Poisson modes), C4 (uneven series),
     C5 (adjoint), the rows beyond the hot path and the paper's Table 1 run: time and Gunknowns/s
     per form, with the error against the oracle (on a sample of systems for the batches).
-    only: the names (OTHER_CONFIGS) to run; None runs all."""
+    only: the names (OTHER_CONFIGS) to run; None runs all.  cpu_leg: time the oracle beside the
+    batched configurations (C3, C4, C5) on all host cores."""
     import torch
     out = {}
 
@@ -515,6 +572,8 @@ def other_configs(D, W, oracle, stream, world, steps=10, only=None):
             c3[name] = {"ms": round(ms, 4), "Gunknowns_s": round(N.sum() / ms / 1e6, 2),
                         "hbm_GBs": round(16 * N.sum() / ms / 1e6, 1), "mixed_systems": int(forms.sum()),
                         "max_rel_err_sampled_vs_binary128": sample_err(xd, Fd, N, off, tm1, t0, tp1, exact=True)}
+        if cpu_leg:
+            c3["cpu_baseline"] = batched_cpu_baseline(tm1, t0, tp1, N, off, rhs.reshape(-1))
         out["c3_poisson_4096x4096"] = c3
         del Fd, xd
 
@@ -530,6 +589,10 @@ def other_configs(D, W, oracle, stream, world, steps=10, only=None):
             c4[name] = {"ms": round(ms, 3), "Gunknowns_s": round(N.sum() / ms / 1e6, 2),
                         "hbm_GBs": round(16 * N.sum() / ms / 1e6, 1), "windows": int(b.info["windows"]),
                         "max_rel_err_sampled": sample_err(xd, Fd, N, off, tm1, t0, tp1)}
+        if cpu_leg:
+            nh = int(np.searchsorted(np.cumsum(N), 1 << 28) + 1)      # the first ~2 GB of systems
+            c4["cpu_baseline"] = batched_cpu_baseline(tm1[:nh], t0[:nh], tp1[:nh], N[:nh], off[:nh],
+                                                      Fd[:int(off[nh - 1] + N[nh - 1])].cpu().numpy())
         out["c4_uneven_10000"] = c4
         del Fd, xd
         torch.cuda.empty_cache()
@@ -557,6 +620,9 @@ def other_configs(D, W, oracle, stream, world, steps=10, only=None):
             c5[name] = {"ms_forward_plus_adjoint": round(ms, 4), "Gunknowns_s": round(Ns.sum() / ms / 1e6, 2),
                         "rel_err_gF_sys7": float(np.max(np.abs(gF[o:o + n].cpu().numpy() - lam)) / np.max(np.abs(lam))),
                         "rel_err_gt_sys7": float(np.max(np.abs(gt[s_].cpu().numpy() - g)) / np.max(np.abs(g)))}
+        if cpu_leg:
+            c5["cpu_baseline"] = batched_cpu_baseline(tm1, t0, tp1, Ns, off, Fd.cpu().numpy(),
+                                                      adjoint_w=wd.cpu().numpy())
         out["c5_adjoint_1024x65536"] = c5
         del Fd, wd, xd
         torch.cuda.empty_cache()

@@ -14,7 +14,8 @@
  *     Solve/adjoint calls only enqueue work: they never synchronize, never allocate
  *     device memory and are safe to capture in a CUDA graph once the plan is bound
  *     (dichotomy_solve_host creates its two copy streams and events on first use; binds,
- *     status reads and the residual checks synchronize).
+ *     status reads and the residual checks synchronize; dichotomy_solve_noalloc stages its
+ *     plan from pageable host memory and refuses capture, see there).
  *   - Plan and batch objects are not locked: calls on one object from several host threads
  *     must be serialized by the caller; distinct objects are independent.
  *   - Device memory is owned by the caller.  The library owns only host-side plan
@@ -51,7 +52,7 @@ typedef enum {
   DICH_ERR_ARG = 1,           /* bad size, NULL / host / misaligned pointer, bad option */
   DICH_ERR_NOT_DOMINANT = 2,  /* |t_0| < |t_-1| + |t_1|: eq. 32-33 fails (not supported) */
   DICH_ERR_SINGULAR = 3,      /* t_0 = 0 with dominance, or a zero block pivot (Theorem 1) */
-  DICH_ERR_TIMEOUT = 4,       /* a bounded device wait ran out (reserved) */
+  DICH_ERR_TIMEOUT = 4,       /* never returned by this build: no kernel waits on another */
   DICH_ERR_NONFINITE = 5,     /* a NaN/Inf was produced on the device */
   DICH_ERR_CUDA = 6,          /* a CUDA runtime call failed; see dichotomy_last_cuda_error */
   DICH_ERR_ALIAS = 7,         /* output aliases an input */
@@ -198,9 +199,10 @@ int dichotomy_solve_host(dich_plan_t plan, const double* h_F, double* h_x, doubl
  *   d_gF = lambda = T^-T w   (the same Dichotomy solve for T^T = tridiag{t_1, t_0, t_-1}),
  *   d_gt[0..2] = (dL/dt_-1, dL/dt_0, dL/dt_1) = -(sum_i lambda_i x_{i-1},
  *                sum_i lambda_i x_i, sum_i lambda_i x_{i+1}).
- * Quasi-Toeplitz plans (eq. 21, psi or chi nonzero): lambda = A^-T w (the transposed corner
- * correction after T^-T w) and d_gt holds 5 doubles, adding dL/dpsi = -lambda_0 x_0 and
- * dL/dchi = -lambda_{N-1} x_{N-1}.  Not in the paper.  d_gt is 3 (5) doubles on the device.
+ * Plans made by dichotomy_plan_quasi (eq. 21; zero corners included): lambda = A^-T w (the
+ * transposed corner correction after T^-T w, none for zero corners) and d_gt holds 5 doubles,
+ * adding dL/dpsi = -lambda_0 x_0 and dL/dchi = -lambda_{N-1} x_{N-1}, all computed on the
+ * device.  Not in the paper.  d_gt is 3 (5) doubles on the device.
  * d_gF may not alias d_w or d_x. */
 int dichotomy_adjoint(dich_plan_t plan, const double* d_w, const double* d_x, double* d_gF,
                       double* d_gt, void* stream);
@@ -228,10 +230,16 @@ void dichotomy_destroy(dich_plan_t plan);
  * and first/last values plus the block-scan scratch) must fit the array; larger needs --
  * long systems whose coupling does not decay, such as the 1-D Laplacian -- return
  * DICH_ERR_WORKSPACE (use dichotomy_plan + dichotomy_solve with a caller workspace).
- * Every call reuses the same array (its status word is cleared on each call): calls whose
- * kernels overlap on the GPU (other streams, other host threads) race; calls on one stream
- * are ordered.  The first call on a device looks up the array's device address; make it
- * before any stream capture. */
+ * Every call reuses the same array (its status word is cleared on each call, so these solves
+ * report no device status): calls whose kernels overlap on the GPU (other streams, other host
+ * threads) race; calls on one stream are ordered.  The first call on a device looks up the
+ * array's device address.  Unlike the other solve calls this one may block the host: the plan
+ * reaches the array by a copy from a static pageable host buffer, which waits until `stream`
+ * has reached it.  It cannot be captured in a CUDA graph: a capturing stream gets
+ * DICH_ERR_UNSUPPORTED (a captured copy would replay the buffer's later contents).
+ * Errors: DICH_ERR_ARG (N < 0, null/misaligned pointers, pointers not on the current device),
+ * DICH_ERR_NOT_DOMINANT, DICH_ERR_SINGULAR, DICH_ERR_ALIAS, DICH_ERR_WORKSPACE,
+ * DICH_ERR_UNSUPPORTED, DICH_ERR_CUDA. */
 int dichotomy_solve_noalloc(double t_m1, double t_0, double t_1, int64_t N, const double* d_F, double* d_x,
                             void* stream);
 

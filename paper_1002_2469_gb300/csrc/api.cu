@@ -314,7 +314,15 @@ bool is_device_ptr(const void* p) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  if (a.type != cudaMemoryTypeDevice) return false;
+  // device memory of another GPU would be read by kernels launched on this one
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.device == dev;
 }
 
 bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
@@ -628,7 +636,7 @@ int dichotomy_plan_quasi(double t_m1, double t_0, double t_1, double psi, double
   rc = dichotomy_plan_ex(t_m1, t_0, t_1, N, opts, &p);
   if (rc) return rc;
   p->quasi = (psi != 0.0 || chi != 0.0);
-  p->corners = p->quasi;
+  p->corners = true;   // a corner plan reports dL/dpsi and dL/dchi, zero corners included
   p->psi = psi;
   p->chi = chi;
   if (p->quasi && N == 1) {
@@ -788,6 +796,11 @@ static int plan_launch(dich_plan_t p, const double* F, double* x, const double* 
     e = launch_corner_adjoint(xf, x, gt, c, st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
+  if (!p->quasi && p->corners && adjoint && p->N >= 2) {
+    // zero corners: lambda needs no correction; dL/dpsi = -lambda_0 x_0, dL/dchi = -lambda_{N-1} x_{N-1}
+    e = launch_end_gradients(xf, x, gt, p->N, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   if (p->quasi && !adjoint && !(p->path == PATH_GENERAL && M > 1)) {
     const double* ctab = d_tabs + p->fwd.tab.size() + p->adj.tab.size();
     CornerArgs c{p->N, p->Lg, p->Lh, ctab, ctab + p->Lg, p->psi, p->chi, p->W[0], p->W[1], p->W[2], p->W[3]};
@@ -930,7 +943,7 @@ int dichotomy_adjoint(dich_plan_t p, const double* d_w, const double* d_x, doubl
   if (overlap(d_gF, nb, d_w, nb) || overlap(d_gF, nb, d_x, nb) || overlap(d_gt, ngt, d_gF, nb)) return DICH_ERR_ALIAS;
   if (!is_device_ptr(d_w) || !is_device_ptr(d_x) || !is_device_ptr(d_gF)) return DICH_ERR_ARG;
   const int rc = plan_launch(p, d_w, d_gF, d_x, d_gt, true, st);
-  if (rc != DICH_OK || !p->corners || p->quasi) return rc;
+  if (rc != DICH_OK || !p->corners || p->quasi || p->N != 1) return rc;
   // one row (t_0 + psi + chi): dL/dpsi = dL/dchi = dL/dt_0
   cudaError_t e = cudaMemcpyAsync(d_gt + 3, d_gt + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_gt + 4, d_gt + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);

@@ -556,6 +556,15 @@ cudaError_t launch_toeplitz_residual(int64_t N, double tm1, double t0, double tp
   return cudaGetLastError();
 }
 
+cudaError_t launch_end_gradients(const double* xf, const double* lam, double* gt, int64_t N, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  // empty corner vectors and zero corners: the kernel adds nothing to the three sums and writes
+  // gt[3] = -lambda_0 x_0, gt[4] = -lambda_{N-1} x_{N-1}
+  const CornerArgs c{N, 0, 0, nullptr, nullptr, 0.0, 0.0, 1.0, 0.0, 0.0, 1.0};
+  k_corner_adj<<<1, 256, 0, st>>>(xf, lam, c, gt);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_corner_adjoint(const double* xf, double* lam, double* gt, const CornerArgs& c, cudaStream_t st) {
   if (c.N <= 0) return cudaSuccess;
   k_corner_adj<<<1, 256, 0, st>>>(xf, lam, c, gt);

@@ -76,5 +76,8 @@ cudaError_t launch_corner_adjoint_batch(const CornerRec* recs, int64_t nsys, con
 // adjoint of a quasi-Toeplitz plan: gradient terms of the corner correction, dL/dpsi, dL/dchi
 // (gt[0..4]), then the corner correction of lambda (c: the transposed corner vectors)
 cudaError_t launch_corner_adjoint(const double* xf, double* lam, double* gt, const CornerArgs& c, cudaStream_t st);
+// dL/dpsi = -lambda_0 x_0 and dL/dchi = -lambda_{N-1} x_{N-1} (gt[3], gt[4]) of a corner plan whose
+// corners are zero (lambda needs no correction there)
+cudaError_t launch_end_gradients(const double* xf, const double* lam, double* gt, int64_t N, cudaStream_t st);
 
 }  // namespace dich

@@ -13,8 +13,10 @@
 // status word included, cleared on every call), so two calls whose kernels overlap on the
 // GPU -- different streams, or different host threads -- race on it; calls on one stream are
 // ordered and safe.  The first call on a device looks the array's device address up
-// (cudaGetSymbolAddress, with that device current); make that first call before any stream
-// capture.
+// (cudaGetSymbolAddress, with that device current).  The plan goes from the static host buffer
+// to the array by a copy from pageable memory, which may hold the host until the stream has
+// reached it; a stream that is being captured is refused (the captured copy would replay the
+// buffer's later contents).  No device status is reported: the word is cleared by every call.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -69,11 +71,17 @@ extern "C" int dichotomy_solve_noalloc(double t_m1, double t_0, double t_1, int6
   int rc = validate_t(t_m1, t_0, t_1);
   if (rc) return rc;
   if (N == 0) return DICH_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the staging copy reads the static host buffer, which the next call overwrites: a captured
+  // copy would replay whatever plan the buffer holds then, so a capturing stream is refused
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(st, &cap);
+  if (ce != cudaSuccess) return cuda_fail(ce);
+  if (cap != cudaStreamCaptureStatusNone) return DICH_ERR_UNSUPPORTED;
   if (!d_F || !d_x || !aligned8(d_F) || !aligned8(d_x)) return DICH_ERR_ARG;
   const size_t nb = sizeof(double) * (size_t)N;
   if (overlap(d_F, nb, d_x, nb)) return DICH_ERR_ALIAS;
   if (!is_device_ptr(d_F) || !is_device_ptr(d_x)) return DICH_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
 
   std::lock_guard<std::mutex> lock(g_mu);
   void* base = nullptr;

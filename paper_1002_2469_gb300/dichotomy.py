@@ -225,14 +225,16 @@ class Plan:
     psi, chi: the quasi-Toeplitz matrix of eq. 21, t_0 + psi in the first row, t_0 + chi in the last)."""
 
     def __init__(self, t_m1, t_0, t_1, N, block_size=0, precision=PREC_F64, threads=0, flags=0, trunc_eps=0.0,
-                 device=None, stream=None, psi=0.0, chi=0.0):
+                 device=None, stream=None, psi=None, chi=None):
         self.t = (float(t_m1), float(t_0), float(t_1))
         self.N = int(N)
-        self.corners = (float(psi), float(chi))
+        # psi / chi given (zeros included): a corner plan, whose adjoint also returns dL/dpsi, dL/dchi
+        self.quasi = psi is not None or chi is not None
+        self.corners = (float(psi or 0.0), float(chi or 0.0))
         self._h = None
         opts = make_opts(block_size, precision, threads, flags, trunc_eps)
-        if psi or chi:
-            self._h = dichotomy_plan_quasi(t_m1, t_0, t_1, psi, chi, N, opts)
+        if self.quasi:
+            self._h = dichotomy_plan_quasi(t_m1, t_0, t_1, self.corners[0], self.corners[1], N, opts)
         else:
             self._h = dichotomy_plan(t_m1, t_0, t_1, N, opts)
         self.info = dichotomy_plan_info(self._h)
@@ -290,7 +292,7 @@ class Plan:
     def adjoint(self, w: torch.Tensor, x: torch.Tensor, stream=None):
         """lambda = A^-T w and dL/d(t_-1, t_0, t_1) (then dL/dpsi, dL/dchi for corner plans)."""
         gF = torch.empty_like(w)
-        gt = torch.empty(5 if any(self.corners) else 3, dtype=torch.float64, device=w.device)
+        gt = torch.empty(5 if self.quasi else 3, dtype=torch.float64, device=w.device)
         dichotomy_adjoint(self._h, w, x, gF, gt, stream)
         return gF, gt
 
@@ -439,6 +441,7 @@ class DichotomySolve(torch.autograd.Function):
         plan = Plan(tv[0], tv[1], tv[2], F.numel(), precision=precision, device=F.device)
         x = plan.solve(F.detach().contiguous())
         ctx.plan = plan
+        ctx.t_device = t.device
         ctx.save_for_backward(x)
         return x
 
@@ -446,7 +449,7 @@ class DichotomySolve(torch.autograd.Function):
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
         gF, gt = ctx.plan.adjoint(gx.contiguous(), x)
-        return gF, gt.to(dtype=torch.float64), None
+        return gF, gt.to(device=ctx.t_device, dtype=torch.float64), None
 
 
 class DichotomySolveQuasi(torch.autograd.Function):
@@ -461,16 +464,16 @@ class DichotomySolveQuasi(torch.autograd.Function):
         plan = Plan(tv[0], tv[1], tv[2], F.numel(), precision=precision, device=F.device, psi=psi, chi=chi)
         x = plan.solve(F.detach().contiguous())
         ctx.plan = plan
+        ctx.devices = (t.device, corners.device)
         ctx.save_for_backward(x)
         return x
 
     @staticmethod
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
+        # a corner plan (zero corners included): the library returns all five gradients
         gF, g = ctx.plan.adjoint(gx.contiguous(), x)
-        if g.numel() == 3:   # psi = chi = 0: a plain Toeplitz plan, dL/dpsi = -lambda_0 x_0 etc.
-            g = torch.cat([g, -(gF[:1] * x[:1]), -(gF[-1:] * x[-1:])])
-        return gF, g[:3], g[3:5], None
+        return gF, g[:3].to(ctx.devices[0]), g[3:5].to(ctx.devices[1]), None
 
 
 class DichotomySolveBatched(torch.autograd.Function):
@@ -482,6 +485,7 @@ class DichotomySolveBatched(torch.autograd.Function):
         batch = Batch(N, tv[:, 0], tv[:, 1], tv[:, 2], precision=precision, device=F.device)
         x = batch.solve(F.detach().contiguous())
         ctx.batch = batch
+        ctx.t_device = t.device
         ctx.save_for_backward(x)
         return x
 
@@ -489,7 +493,7 @@ class DichotomySolveBatched(torch.autograd.Function):
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
         gF, gt = ctx.batch.adjoint(gx.contiguous(), x)
-        return gF, gt, None, None
+        return gF, gt.to(ctx.t_device), None, None
 
 
 class DichotomySolveBatchedQuasi(torch.autograd.Function):
@@ -503,6 +507,7 @@ class DichotomySolveBatchedQuasi(torch.autograd.Function):
                       chi=cv[:, 1])
         x = batch.solve(F.detach().contiguous())
         ctx.batch = batch
+        ctx.devices = (t.device, corners.device)
         ctx.save_for_backward(x)
         return x
 
@@ -510,4 +515,4 @@ class DichotomySolveBatchedQuasi(torch.autograd.Function):
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
         gF, g = ctx.batch.adjoint(gx.contiguous(), x)
-        return gF, g[:, :3], g[:, 3:], None, None
+        return gF, g[:, :3].to(ctx.devices[0]), g[:, 3:].to(ctx.devices[1]), None, None

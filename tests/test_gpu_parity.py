@@ -224,7 +224,8 @@ QUASI = [((-1.0, 2.5, -1.0), -1.0, -1.0),      # Neumann-type ends
          ((-1.2, 2.5, -0.8), 0.7, -0.3),       # Robin-type, non-symmetric
          ((0.7, 2.5, -1.1), -0.5, 1.5),
          ((-1.0, 2.001, -1.0), -0.9, 0.0),     # weakly dominant: long corner columns
-         ((-1.0, 4.0, -1.0), 2.0, -2.5)]
+         ((-1.0, 4.0, -1.0), 2.0, -2.5),
+         ((-1.2, 2.5, -0.8), 0.0, 0.0)]      # zero corners: still a corner plan (five gradients)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -706,6 +707,32 @@ def test_autograd_quasi(D, corners):
     assert rel(F.grad.cpu().numpy(), lam) < TOL
     assert np.max(np.abs(t.grad.cpu().numpy() - g[:3])) <= TOL * np.max(np.abs(g[:3]))
     assert np.max(np.abs(c.grad.cpu().numpy() - g[3:])) <= TOL * np.max(np.abs(lam)) * np.max(np.abs(x.detach().cpu().numpy()))
+
+
+def test_autograd_with_cpu_coefficients(D):
+    """Coefficients kept on the host (natural for three numbers): their gradients come back on the
+    host, for the single, quasi-Toeplitz and batched Functions."""
+    N = 4000
+    rng = np.random.default_rng(11)
+    F = torch.from_numpy(rng.uniform(-1, 1, N)).cuda().requires_grad_(True)
+    w = torch.from_numpy(rng.uniform(-1, 1, N)).cuda()
+    t = torch.tensor([-1.2, 2.5, -0.8], dtype=torch.float64, requires_grad=True)
+    (D.DichotomySolve.apply(F, t) * w).sum().backward()
+    assert t.grad.device.type == "cpu"
+    tt = tuple(t.detach().tolist())
+    lam, g = oracle.adjoint(tt, w.cpu().numpy(), oracle.thomas(tt, F.detach().cpu().numpy()))
+    assert np.max(np.abs(t.grad.numpy() - g)) <= TOL * np.max(np.abs(g))
+    t2 = torch.tensor([-1.2, 2.5, -0.8], dtype=torch.float64, requires_grad=True)
+    c2 = torch.tensor([0.0, 0.0], dtype=torch.float64, requires_grad=True)
+    (D.DichotomySolveQuasi.apply(F, t2, c2) * w).sum().backward()
+    assert t2.grad.device.type == "cpu" and c2.grad.device.type == "cpu"
+    x = oracle.thomas(tt, F.detach().cpu().numpy())
+    lq, gq = oracle.adjoint_quasi(tt, 0.0, 0.0, w.cpu().numpy(), x)
+    assert np.max(np.abs(c2.grad.numpy() - gq[3:])) <= TOL * np.max(np.abs(lq)) * np.max(np.abs(x))
+    Nb = np.array([1000, 3000], dtype=np.int64)
+    tb = torch.tensor([[-1.0, 2.5, -1.0], [0.7, 2.5, -1.1]], dtype=torch.float64, requires_grad=True)
+    (D.DichotomySolveBatched.apply(F, tb, Nb) * w).sum().backward()
+    assert tb.grad.device.type == "cpu" and tb.grad.shape == (2, 3)
 
 
 def test_autograd_batched_quasi(D):

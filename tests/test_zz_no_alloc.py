@@ -1,8 +1,10 @@
 """dichotomy_solve_noalloc: the single-system solve for callers that cannot allocate device
-memory.  It is called here through the C ABI (ctypes) and compared with the regular entry
-point (dichotomy_plan + bind + dichotomy_solve) on two calls in a row, within the tolerance
-the other GPU tests use.  The file is named to be collected last, so a run that stops at the
-first failure has already run every other test; it also passes on its own in a fresh process.
+memory.  It is called here through the C ABI (ctypes) and compared, on two calls in a row, with
+the CPU oracle's Thomas solve (the binary128 Thomas arbitrating for the weakly dominant case, as
+in the other parity tests) and with the regular entry point (dichotomy_plan + bind +
+dichotomy_solve), within the tolerance the other GPU tests use.  The file is named to be
+collected last, so a run that stops at the first failure has already run every other test; it
+also passes on its own in a fresh process.
 """
 import ctypes
 
@@ -34,24 +36,66 @@ def _noalloc(lib, t, F, x):
                                        ctypes.c_void_p(x.data_ptr()), stream)
 
 
-@pytest.mark.parametrize("t,N", [((-1.2, 2.5, -0.8), 1 << 20), ((-1.0, 4.0, -1.0), 65537), ((0.7, 2.5, -1.1), 3001),
-                                 ((-1.0, 2.001, -1.0), 200000), ((-1.0, 4.0, -1.0), 1), ((-0.5, 3.0, -1.2), 2)])
-def test_noalloc_matches_regular_solve_twice(lib, t, N):
+def _close_to_oracle(x, t, F):
+    """Within TOL of the FP64 oracle, or (ill-conditioned systems) no farther from the binary128
+    solution than the FP64 oracle is, times two."""
+    import oracle
+    ref = oracle.thomas(t, F)
+    if _rel(x, ref) < TOL:
+        return True
+    refq = oracle.thomas_q(t, F)
+    return _rel(x, refq) <= max(TOL, 2.0 * _rel(ref, refq))
+
+
+# path expected of the library's planner (0 single window, 1 halo windows, 2 general path)
+CASES = [((-1.2, 2.5, -0.8), 1 << 20, 1), ((-1.0, 4.0, -1.0), 65537, 1), ((0.7, 2.5, -1.1), 3001, 0),
+         ((-1.0, 2.001, -1.0), 200000, 2), ((-1.0, 4.0, -1.0), 1, None), ((-0.5, 3.0, -1.2), 2, 0)]
+
+
+@pytest.mark.parametrize("t,N,path", CASES)
+def test_noalloc_matches_oracle_and_regular_solve_twice(lib, t, N, path):
     import paper_1002_2469_gb300 as D
     rng = np.random.default_rng(N)
-    F1 = torch.from_numpy(rng.standard_normal(N)).cuda()
-    F2 = torch.from_numpy(rng.uniform(-1, 1, N)).cuda()
-    ref1 = D.Plan(*t, N, precision=D.PREC_AUTO).solve(F1).cpu().numpy()
-    ref2 = D.Plan(*t, N, precision=D.PREC_AUTO).solve(F2).cpu().numpy()
+    F1h, F2h = rng.standard_normal(N), rng.uniform(-1, 1, N)
+    F1, F2 = torch.from_numpy(F1h).cuda(), torch.from_numpy(F2h).cuda()
+    plan = D.Plan(*t, N, precision=D.PREC_AUTO)
+    if path is not None:
+        # the planner the allocation-free call shares puts this system on the expected path
+        assert plan.info["path"] == path, plan.info
+    ref1 = plan.solve(F1).cpu().numpy()
+    ref2 = plan.solve(F2).cpu().numpy()
     x = torch.full_like(F1, float("nan"))
     # two calls in a row on the same stream; the second reuses the library's static array
     assert _noalloc(lib, t, F1, x) == 0
     torch.cuda.synchronize()
-    assert _rel(x.cpu().numpy(), ref1) < TOL
+    x1h = x.cpu().numpy()
+    assert _close_to_oracle(x1h, t, F1h)
+    assert _rel(x1h, ref1) < TOL
     x2 = torch.full_like(F2, float("nan"))
     assert _noalloc(lib, t, F2, x2) == 0
     torch.cuda.synchronize()
-    assert _rel(x2.cpu().numpy(), ref2) < TOL
+    x2h = x2.cpu().numpy()
+    assert _close_to_oracle(x2h, t, F2h)
+    assert _rel(x2h, ref2) < TOL
+
+
+def test_noalloc_refuses_a_capturing_stream(lib):
+    # the staging copy reads a host buffer that later calls overwrite: capture is refused
+    N = 4096
+    F = torch.ones(N, dtype=torch.float64, device="cuda")
+    x = torch.empty_like(F)
+    assert _noalloc(lib, (-1.0, 4.0, -1.0), F, x) == 0      # first call on the device: set-up
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    rc = None
+    with torch.cuda.stream(s):
+        g.capture_begin(capture_error_mode="relaxed")
+        try:
+            rc = _noalloc(lib, (-1.0, 4.0, -1.0), F, x)
+        finally:
+            g.capture_end()
+    assert rc == 11               # DICH_ERR_UNSUPPORTED
 
 
 def test_noalloc_rejects_what_exceeds_its_static_array(lib):
