@@ -306,6 +306,7 @@ def run_gpu(args):
     e_ms = max_over_ranks((time.perf_counter() - e0) * 1e3 / esteps, world)
     e_err = float(np.max(np.abs(x_pin.numpy() - x_ref)) / np.max(np.abs(x_ref)))
     e_same = bool(np.array_equal(x_pin.numpy(), results["auto"]["x"]))
+    e_diff = float(np.max(np.abs(x_pin.numpy() - results["auto"]["x"])) / np.max(np.abs(results["auto"]["x"])))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -371,7 +372,8 @@ def run_gpu(args):
                 "ms_per_step": round(e_ms, 3), "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
                 "includes": "plan + dichotomy_solve_host (pinned F, x: the window kernels read F from and write x to "
                             "host memory over the host link)",
-                "rel_err_vs_oracle": e_err, "bitwise_equal_to_device_solve": e_same},
+                "rel_err_vs_oracle": e_err, "bitwise_equal_to_device_solve": e_same,
+                "rel_diff_vs_device_solve": e_diff},
         "gpu_launches": args.steps * (3 if head["info"]["path"] == 2 else 1),
         "clocks": clocks,
     }

@@ -52,7 +52,8 @@ typedef enum {
   DICH_ERR_ARG = 1,           /* bad size, NULL / host / misaligned pointer, bad option */
   DICH_ERR_NOT_DOMINANT = 2,  /* |t_0| < |t_-1| + |t_1|: eq. 32-33 fails (not supported) */
   DICH_ERR_SINGULAR = 3,      /* t_0 = 0 with dominance, or a zero block pivot (Theorem 1) */
-  DICH_ERR_TIMEOUT = 4,       /* never returned by this build: no kernel waits on another */
+  DICH_ERR_TIMEOUT = 4,       /* a bounded wait for a kernel's own bulk copies ran out (not
+                                 expected; no kernel waits on another CTA or rank) */
   DICH_ERR_NONFINITE = 5,     /* a NaN/Inf was produced on the device */
   DICH_ERR_CUDA = 6,          /* a CUDA runtime call failed; see dichotomy_last_cuda_error */
   DICH_ERR_ALIAS = 7,         /* output aliases an input */

@@ -256,6 +256,7 @@ int build_system(double tm1, double t0, double tp1, int64_t N, int NT, int form,
   p.o_bclf = take(kl * kBC);
   p.o_bcrf = take(kr * kBC);
   split_ff(r.g * r.ib, p.gib_h, p.gib_l);
+  split_ff(-r.q, p.q_h, p.q_l);
   split_ff(p.v0, p.v0_h, p.v0_l);
   split_ff(p.vend, p.vend_h, p.vend_l);
   split_ff(p.v0l, p.v0l_h, p.v0l_l);
@@ -336,6 +337,7 @@ bool overlap(const void* a, size_t na, const void* b, size_t nb) {
 int map_status(unsigned s) {
   if (s & ST_NONFINITE) return DICH_ERR_NONFINITE;
   if (s & ST_SCHEDULE) return DICH_ERR_SCHEDULE;
+  if (s & ST_TIMEOUT) return DICH_ERR_TIMEOUT;
   return DICH_OK;
 }
 
@@ -711,9 +713,11 @@ int dichotomy_plan_bind(dich_plan_t p, void* d_ws, size_t bytes, void* stream) {
   return DICH_OK;
 }
 
+// device_mem: F and x are device memory (false: mapped host memory, read and written by the kernels
+// over the host link), which lets aligned windows use bulk copies
 static int plan_launch(dich_plan_t p, const double* F, double* x, const double* xf, double* gt, bool adjoint,
                        cudaStream_t st, int64_t M = 1, int64_t ldf = 0, int64_t ldx = 0, int64_t win0 = 0,
-                       int64_t nwin = -1) {
+                       int64_t nwin = -1, bool device_mem = true) {
   const SysPlan* d_plans = (const SysPlan*)(p->d_ws + p->off_plans);
   const double* d_tabs = (const double*)(p->d_ws + p->off_tabs);
   unsigned* d_status = (unsigned*)(p->d_ws + p->off_status);
@@ -741,6 +745,7 @@ static int plan_launch(dich_plan_t p, const double* F, double* x, const double* 
   a.sys_offset = sys_offset;
   a.ldf = ldf;
   a.ldx = ldx;
+  a.bulk = device_mem ? 1 : 0;
   const size_t smem = smem_bytes(p->NT, p->n_smem, p->form);
   // windows [win0, win0 + grid) of the single and halo paths (all of them unless a range is given)
   const int grid = (int)((nwin < 0) ? p->tiles : nwin);
@@ -847,7 +852,7 @@ int dichotomy_solve_host(dich_plan_t p, const double* h_F, double* h_x, double* 
     };
     const double* zF = (const double*)mapped(h_F);
     double* zx = (double*)mapped(h_x);
-    if (zF && zx) return plan_launch(p, zF, zx, nullptr, nullptr, false, st);
+    if (zF && zx) return plan_launch(p, zF, zx, nullptr, nullptr, false, st, 1, 0, 0, 0, -1, false);
   }
   if (!d_F || !d_x || !aligned8(d_F) || !aligned8(d_x)) return DICH_ERR_ARG;
   if (overlap(d_F, nb, d_x, nb)) return DICH_ERR_ALIAS;
@@ -1402,6 +1407,7 @@ static int batch_launch(dich_batch_t b, const double* F, double* x, const double
     a.check_finite = (b->opts.flags & DICH_FLAG_CHECK_FINITE) ? 1 : 0;
     a.n_smem = b->n_smem[f];
     a.sys_offset = sys_offset;
+    a.bulk = 1;   // batch vectors are device memory
     const size_t smem = smem_bytes(b->NT[f], a.n_smem, f);
     cudaError_t e = (f == FORM_F64) ? launch_window_f64(b->NT[f], (int)nitems, smem, sf, a)
                                     : launch_window_mixed(b->NT[f], (int)nitems, smem, sf, a);

@@ -60,6 +60,7 @@ enum Mode : int32_t {
 enum StatusBits : uint32_t {
   ST_NONFINITE = 1u,
   ST_SCHEDULE = 2u,
+  ST_TIMEOUT = 4u,    // a bounded wait for the CTA's own bulk copies ran out (the CTA stored nothing)
 };
 
 // Device-side plan record of one system (256 bytes, 8-byte fields first).
@@ -89,6 +90,7 @@ struct SysPlan {
   // float-float copies of g * ib and of the corner spikes (MIXED form)
   float gib_h, gib_l;
   float v0_h, v0_l, vend_h, vend_l, v0l_h, v0l_l, vendl_h, vendl_l;
+  float q_h, q_l;   // float-float 1/g = -q (spike coefficients in units of X, register path)
 };
 static_assert(sizeof(SysPlan) % 8 == 0, "SysPlan must be 8-byte granular");
 

@@ -137,6 +137,7 @@ extern "C" int dichotomy_solve_noalloc(double t_m1, double t_0, double t_1, int6
   a.status = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(base) + kStatusOff);
   a.mode = MODE_FULL;
   a.n_smem = n;
+  a.bulk = 1;   // F and x are device memory (checked above)
   const int64_t tiles = ceil_div(sb.rec.P, sb.rec.own);
   const size_t smem = smem_bytes(NT, n, form);
   auto launch = [&](const WinArgs& w) {

@@ -46,6 +46,7 @@ struct WinArgs {
   int32_t sys_offset;     // added to the item's system index (adjoint twin records)
   int64_t ldf, ldx;       // series: right-hand side blockIdx.y starts at F + y ldf, its solution at x + y ldx
   int64_t win0;           // single system: window of CTA blockIdx.x is win0 + blockIdx.x
+  int32_t bulk;           // F and x are device memory: 16-byte aligned windows may use bulk copies
 };
 
 // shared memory bytes for a window kernel of width NT and n_smem rows

@@ -34,12 +34,6 @@ struct OpsFF {
   }
 };
 
-// shared memory of the MIXED window kernel: NT threads, 2 NT window blocks, n_smem rows
-__host__ __device__ inline size_t window2_smem_bytes(int NT, int n_smem) {
-  const size_t nw = (size_t)(NT / 32);
-  const size_t LD = 2 * (size_t)NT + 2;
-  return sizeof(double) * ((size_t)n_smem * LD + 4 * (size_t)n_smem + 4 * (size_t)NT + 4 * nw + 8);
-}
 
 // forward and backward sweeps of a thread's pair of blocks, in place.  GUARD: the two blocks
 // may differ in size (the system's last block) or be inactive (nb = 0): rows at or beyond a
@@ -160,8 +154,132 @@ __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow_, int 
   }
 }
 
+// The dichotomy tree of one MIXED window (a2): the prefix and suffix affine scans of eq. 15 over the
+// window's blocks in packed float-float (five warp-shuffle levels, one shared-memory level), the
+// first/last values of every block (eq. 18) in sxs/sxe, and the neighbours' values the correction of
+// the thread's two blocks needs: XL = x_{s-1}, XR = x_{e+1} (zero coupling enters at both window
+// ends).  bc2(j): coefficient j of both blocks' records; bL, bR: beta (eq. 16) of both blocks.
+template <int NT, class BC>
+__device__ __forceinline__ void tree2(const BC& bc2, bool act0, bool act1, int64_t mb0, int64_t mb1, int64_t P,
+                                      int nwin, int tid, const ff2& bL, const ff2& bR, ffv* swv, ffv* sxs, ffv* sxe,
+                                      ffv& XL0, ffv& XR0, ffv& XL1, ffv& XR1) {
+  using O = OpsFF;
+  constexpr int NW = NT / 32;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int b0 = 2 * tid, b1 = 2 * tid + 1;
+  const ff2 one2{f2(1.f), f2(0.f)};
+  // ------------------------------------------------------------ dichotomy tree (a2)
+  // block maps: prefix A -> a A + b beta^R, suffix B -> c B + d beta^L
+  const ff2 av = ff2_sel(act0, act1, bc2(BC_A), one2), cv = ff2_sel(act0, act1, bc2(BC_C), one2);
+  const ff2 pbv = ff2_mul(bc2(BC_B), bR), qbv = ff2_mul(bc2(BC_D), bL);
+  // the thread's composite maps, lane x the prefix (block 1 after block 0), lane y the suffix
+  // (block 0 after block 1): (a1 a0, c0 c1) and (a1 pb0 + pb1, c0 qb1 + qb0)
+  const ff2 m1{make_float2(av.h.y, cv.h.x), make_float2(av.l.y, cv.l.x)};
+  ff2 Sv = ff2_mul(m1, ff2{make_float2(av.h.x, cv.h.y), make_float2(av.l.x, cv.l.y)});
+  ff2 Tv = ff2_fma(m1, ff2{make_float2(pbv.h.x, qbv.h.y), make_float2(pbv.l.x, qbv.l.y)},
+                   ff2{make_float2(pbv.h.y, qbv.h.x), make_float2(pbv.l.y, qbv.l.x)});
+  // warp scans: the prefix from lane - d, the suffix from lane + d; identity maps past the ends
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float yah = __shfl_up_sync(0xffffffffu, Sv.h.x, d), yal = __shfl_up_sync(0xffffffffu, Sv.l.x, d);
+    const float ybh = __shfl_up_sync(0xffffffffu, Tv.h.x, d), ybl = __shfl_up_sync(0xffffffffu, Tv.l.x, d);
+    const float zah = __shfl_down_sync(0xffffffffu, Sv.h.y, d), zal = __shfl_down_sync(0xffffffffu, Sv.l.y, d);
+    const float zbh = __shfl_down_sync(0xffffffffu, Tv.h.y, d), zbl = __shfl_down_sync(0xffffffffu, Tv.l.y, d);
+    const bool up = lane >= d, dn = lane + d < 32;
+    const ff2 Ya{make_float2(up ? yah : 1.f, dn ? zah : 1.f), make_float2(up ? yal : 0.f, dn ? zal : 0.f)};
+    const ff2 Yb{make_float2(up ? ybh : 0.f, dn ? zbh : 0.f), make_float2(up ? ybl : 0.f, dn ? zbl : 0.f)};
+    Tv = ff2_fma(Sv, Yb, Tv);
+    Sv = ff2_mul(Sv, Ya);
+  }
+  const ffv pa = ff2_x(Sv), pb = ff2_x(Tv), qa = ff2_y(Sv), qb = ff2_y(Tv);
+  if (lane == 31) {
+    swv[wid] = pa;
+    swv[NW + wid] = pb;
+  }
+  if (lane == 0) {
+    swv[2 * NW + wid] = qa;
+    swv[3 * NW + wid] = qb;
+  }
+  ffv ea = O::up(pa, 1), eb = O::up(pb, 1);
+  ffv fa = O::down(qa, 1), fb = O::down(qb, 1);
+  if (lane == 0) {
+    ea = ff_one();
+    eb = ff_zero();
+  }
+  if (lane == 31) {
+    fa = ff_one();
+    fb = ff_zero();
+  }
+  __syncthreads();
+  ffv Aw = ff_zero(), Bw = ff_zero();  // zero coupling enters at both window ends
+  for (int w = 0; w < wid; ++w) Aw = O::fma(swv[w], Aw, swv[NW + w]);
+  for (int w = NW - 1; w > wid; --w) Bw = O::fma(swv[2 * NW + w], Bw, swv[3 * NW + w]);
+  // (A entering block 0, B beyond block 1), then (A entering block 1, B beyond block 0)
+  const ff2 E = ff2_fma(ff2_pair(ea, fa), ff2_pair(Aw, Bw), ff2_pair(eb, fb));
+  const ff2 G = ff2_fma(ff2_pair(ff2_x(av), ff2_y(cv)), E, ff2_pair(ff2_x(pbv), ff2_y(qbv)));
+  const ff2 Av{make_float2(E.h.x, G.h.x), make_float2(E.l.x, G.l.x)};   // (A_0, A_1)
+  const ff2 Bv{make_float2(G.h.y, E.h.y), make_float2(G.l.y, E.l.y)};   // (B_0, B_1)
+  // first/last values of both blocks (eq. 18)
+  const ff2 xs = ff2_add(ff2_fma(bc2(BC_TL), Bv, bL), Av);
+  const ff2 xe = ff2_fma(bc2(BC_TR), Av, ff2_add(bR, Bv));
+  if (act0) {
+    sxs[b0] = ff2_x(xs);
+    sxe[b0] = ff2_x(xe);
+  }
+  if (act1) {
+    sxs[b1] = ff2_y(xs);
+    sxe[b1] = ff2_y(xe);
+  }
+  __syncthreads();
+  if (act0) {
+    if (!(mb0 == 0 || b0 == 0)) XL0 = sxe[b0 - 1];
+    if (!(mb0 == P - 1 || b0 + 1 >= nwin)) XR0 = sxs[b0 + 1];
+  }
+  if (act1) {
+    XL1 = sxe[b0];
+    if (!(mb1 == P - 1 || b1 + 1 >= nwin)) XR1 = sxs[b1 + 1];
+  }
+}
+
+// coefficient records of a thread's two blocks (the float-float copies of the plan tables)
+struct Recs2 {
+  const float2* tf;
+  int64_t r0, r1;
+  __device__ __forceinline__ ff2 operator()(int j) const {  // coefficient j of both blocks' records
+    const float2 c0 = tf[r0 + j], c1 = tf[r1 + j];
+    return ff2_make(make_float2(c0.x, c1.x), make_float2(c0.y, c1.y));
+  }
+};
+__device__ __forceinline__ Recs2 recs2(const SysPlan* pp, const double* tab, int64_t P, bool act0, bool act1,
+                                       int64_t mb0, int64_t mb1) {
+  auto rec_of = [&](int64_t m) -> int64_t {
+    if (m < pp->kl) return pp->o_bclf + m * kBC;
+    if (m >= P - pp->kr) return pp->o_bcrf + (m - (P - pp->kr)) * kBC;
+    return pp->o_bcmf;
+  };
+  return Recs2{reinterpret_cast<const float2*>(tab), act0 ? rec_of(mb0) : pp->o_bcmf,
+               act1 ? rec_of(mb1) : pp->o_bcmf};
+}
+
+}  // namespace dich
+#include "window_reg.cuh"
+namespace dich {
+
+// shared memory of the MIXED window kernel: NT threads, 2 NT window blocks, n_smem rows (at least
+// what the register path needs when blocks of its size may occur)
+__host__ __device__ inline size_t window2_smem_bytes(int NT, int n_smem) {
+  const size_t nw = (size_t)(NT / 32);
+  const size_t LD = 2 * (size_t)NT + 2;
+  const size_t tile = sizeof(double) * ((size_t)n_smem * LD + 4 * (size_t)n_smem + 4 * (size_t)NT + 4 * nw + 8);
+  if (n_smem < kRegRows) return tile;
+  const size_t reg = window_reg_smem_bytes(NT);
+  return tile > reg ? tile : reg;
+}
+
+// ADJ: the adjoint's instantiation (80 registers: six CTAs of 128 threads per SM); the forward one
+// allows the 128 registers of the register path (four CTAs of 128 threads per SM)
 template <int NT, bool ADJ>
-__global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
+__global__ void __launch_bounds__(NT, (ADJ ? 768 : 512) / NT) k_window2(const WinArgs A) {
   constexpr int NW = NT / 32;
   constexpr int WB = 2 * NT;       // window blocks
   constexpr int LD = 2 * NT + 2;   // shared row stride in doubles (even: 16-byte pairs)
@@ -215,6 +333,16 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   const bool has_last = (wlo + nwin == P);
   const int64_t row_lo = wlo * (int64_t)n;
   const int len = nwin * n - (has_last ? (n - nlast) : 0);
+
+  if constexpr (!ADJ) {
+    // 16-row blocks, all of full size, 16-byte aligned device memory: the register path
+    if (A.bulk && A.mode == MODE_FULL && n == kRegRows && (!has_last || nlast == kRegRows) && !A.check_finite &&
+        ((reinterpret_cast<uintptr_t>(A.F + (int64_t)blockIdx.y * A.ldf + off + row_lo) |
+          reinterpret_cast<uintptr_t>(A.x + (int64_t)blockIdx.y * A.ldx + off + row_lo)) & 15u) == 0u) {
+      window_reg<NT>(A, pp, tab, P, wlo, nwin, hl, nown, row_lo, reinterpret_cast<unsigned char*>(sm));
+      return;
+    }
+  }
 
   // ---------------------------------------------------------------- F -> smem (transposed, async)
   {
@@ -373,18 +501,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
   }
 
   // ---------------------------------------------------------------- beta (eq. 16)
-  auto rec_of = [&](int64_t m) -> int64_t {
-    if (m < pp->kl) return pp->o_bclf + m * kBC;
-    if (m >= P - pp->kr) return pp->o_bcrf + (m - (P - pp->kr)) * kBC;
-    return pp->o_bcmf;
-  };
-  const int64_t r0 = act0 ? rec_of(mb0) : pp->o_bcmf;
-  const int64_t r1 = act1 ? rec_of(mb1) : pp->o_bcmf;
-  const float2* tf = reinterpret_cast<const float2*>(tab);
-  auto bc2 = [&](int j) {  // coefficient j of both blocks' records
-    const float2 c0 = tf[r0 + j], c1 = tf[r1 + j];
-    return ff2_make(make_float2(c0.x, c1.x), make_float2(c0.y, c1.y));
-  };
+  const Recs2 bc2 = recs2(pp, tab, P, act0, act1, mb0, mb1);
   const ff2 bL = ff2_sel(act0, act1, ff2_fma(bc2(BC_M00), al, ff2_mul(bc2(BC_M01), om)), zero2);
   const ff2 bR = ff2_sel(act0, act1, ff2_fma(bc2(BC_M10), al, ff2_mul(bc2(BC_M11), om)), zero2);
 
@@ -403,77 +520,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_window2(const WinArgs A) {
 
   ffv XL0 = ff_zero(), XR0 = ff_zero(), XL1 = ff_zero(), XR1 = ff_zero();
   if (A.mode == MODE_FULL) {
-    // ------------------------------------------------------------ dichotomy tree (a2)
-    // block maps: prefix A -> a A + b beta^R, suffix B -> c B + d beta^L
-    const ff2 av = ff2_sel(act0, act1, bc2(BC_A), one2), cv = ff2_sel(act0, act1, bc2(BC_C), one2);
-    const ff2 pbv = ff2_mul(bc2(BC_B), bR), qbv = ff2_mul(bc2(BC_D), bL);
-    // the thread's composite maps, lane x the prefix (block 1 after block 0), lane y the suffix
-    // (block 0 after block 1): (a1 a0, c0 c1) and (a1 pb0 + pb1, c0 qb1 + qb0)
-    const ff2 m1{make_float2(av.h.y, cv.h.x), make_float2(av.l.y, cv.l.x)};
-    ff2 Sv = ff2_mul(m1, ff2{make_float2(av.h.x, cv.h.y), make_float2(av.l.x, cv.l.y)});
-    ff2 Tv = ff2_fma(m1, ff2{make_float2(pbv.h.x, qbv.h.y), make_float2(pbv.l.x, qbv.l.y)},
-                     ff2{make_float2(pbv.h.y, qbv.h.x), make_float2(pbv.l.y, qbv.l.x)});
-    // warp scans: the prefix from lane - d, the suffix from lane + d; identity maps past the ends
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const float yah = __shfl_up_sync(0xffffffffu, Sv.h.x, d), yal = __shfl_up_sync(0xffffffffu, Sv.l.x, d);
-      const float ybh = __shfl_up_sync(0xffffffffu, Tv.h.x, d), ybl = __shfl_up_sync(0xffffffffu, Tv.l.x, d);
-      const float zah = __shfl_down_sync(0xffffffffu, Sv.h.y, d), zal = __shfl_down_sync(0xffffffffu, Sv.l.y, d);
-      const float zbh = __shfl_down_sync(0xffffffffu, Tv.h.y, d), zbl = __shfl_down_sync(0xffffffffu, Tv.l.y, d);
-      const bool up = lane >= d, dn = lane + d < 32;
-      const ff2 Ya{make_float2(up ? yah : 1.f, dn ? zah : 1.f), make_float2(up ? yal : 0.f, dn ? zal : 0.f)};
-      const ff2 Yb{make_float2(up ? ybh : 0.f, dn ? zbh : 0.f), make_float2(up ? ybl : 0.f, dn ? zbl : 0.f)};
-      Tv = ff2_fma(Sv, Yb, Tv);
-      Sv = ff2_mul(Sv, Ya);
-    }
-    const ffv pa = ff2_x(Sv), pb = ff2_x(Tv), qa = ff2_y(Sv), qb = ff2_y(Tv);
-    if (lane == 31) {
-      swv[wid] = pa;
-      swv[NW + wid] = pb;
-    }
-    if (lane == 0) {
-      swv[2 * NW + wid] = qa;
-      swv[3 * NW + wid] = qb;
-    }
-    ffv ea = O::up(pa, 1), eb = O::up(pb, 1);
-    ffv fa = O::down(qa, 1), fb = O::down(qb, 1);
-    if (lane == 0) {
-      ea = ff_one();
-      eb = ff_zero();
-    }
-    if (lane == 31) {
-      fa = ff_one();
-      fb = ff_zero();
-    }
-    __syncthreads();
-    ffv Aw = ff_zero(), Bw = ff_zero();  // zero coupling enters at both window ends
-    for (int w = 0; w < wid; ++w) Aw = O::fma(swv[w], Aw, swv[NW + w]);
-    for (int w = NW - 1; w > wid; --w) Bw = O::fma(swv[2 * NW + w], Bw, swv[3 * NW + w]);
-    // (A entering block 0, B beyond block 1), then (A entering block 1, B beyond block 0)
-    const ff2 E = ff2_fma(ff2_pair(ea, fa), ff2_pair(Aw, Bw), ff2_pair(eb, fb));
-    const ff2 G = ff2_fma(ff2_pair(ff2_x(av), ff2_y(cv)), E, ff2_pair(ff2_x(pbv), ff2_y(qbv)));
-    const ff2 Av{make_float2(E.h.x, G.h.x), make_float2(E.l.x, G.l.x)};   // (A_0, A_1)
-    const ff2 Bv{make_float2(G.h.y, E.h.y), make_float2(G.l.y, E.l.y)};   // (B_0, B_1)
-    // first/last values of both blocks (eq. 18)
-    const ff2 xs = ff2_add(ff2_fma(bc2(BC_TL), Bv, bL), Av);
-    const ff2 xe = ff2_fma(bc2(BC_TR), Av, ff2_add(bR, Bv));
-    if (act0) {
-      sxs[b0] = ff2_x(xs);
-      sxe[b0] = ff2_x(xe);
-    }
-    if (act1) {
-      sxs[b1] = ff2_y(xs);
-      sxe[b1] = ff2_y(xe);
-    }
-    __syncthreads();
-    if (act0) {
-      if (!(mb0 == 0 || b0 == 0)) XL0 = sxe[b0 - 1];
-      if (!(mb0 == P - 1 || b0 + 1 >= nwin)) XR0 = sxs[b0 + 1];
-    }
-    if (act1) {
-      XL1 = sxe[b0];
-      if (!(mb1 == P - 1 || b1 + 1 >= nwin)) XR1 = sxs[b1 + 1];
-    }
+    tree2<NT>(bc2, act0, act1, mb0, mb1, P, nwin, tid, bL, bR, swv, sxs, sxe, XL0, XR0, XL1, XR1);
   } else {  // MODE_APPLY: neighbours' first/last values from the global scan (unscaled FP64)
     const double upw = pow2i(wscale);
     auto to_ff = [&](double d) {

@@ -1,0 +1,312 @@
+// window_reg.cuh -- the register-resident path of the MIXED window kernel (16-row blocks).
+//
+// A window whose blocks all have 16 rows, whose right-hand side and solution are 16-byte aligned
+// device memory and whose launch asks for the full solve (MODE_FULL, forward) is solved with a
+// thread's pair of blocks (2 x 16 unknowns) kept in registers from the load to the store:
+//   - the window's rows of F arrive by bulk asynchronous copies (cp.async.bulk: one per thread, its
+//     two blocks, 256 contiguous bytes) into shared-memory slots of 272 bytes (the pair plus 16
+//     bytes of padding, so that the per-thread 16-byte reads of eight consecutive threads fall in
+//     eight different bank groups); one mbarrier counts the bytes, its wait is bounded;
+//   - the exponent range of the window (its power-of-two scale), the split into float-float, the
+//     two constant-coefficient recurrences (a1), the block-end quantities, beta (eq. 16) and the
+//     dichotomy tree (a2, shared with the shared-memory path), the spike correction of eq. 7 (a3)
+//     and the join back to FP64 all work on registers: no shared-memory round trip per row;
+//   - the output scale g = -1/q is folded into the join: the backward recurrence leaves X with
+//     x = g X, the spike correction works in units of X (its coefficients times 1/g = -q), and each
+//     output is one FP64 FMA, g * hi + (g * lo), with the window scale undone in the exponent bits;
+//   - the solution goes back through the same shared-memory slots, and each thread's own (non-halo)
+//     blocks leave by bulk copies to global memory.
+// Windows of any other shape, the adjoint and the general path's passes take the shared-memory
+// path of window_mixed.cuh.  Included by window_mixed.cuh after the tree (tree2, Recs2).
+#pragma once
+#include <type_traits>
+#include "ff.cuh"
+#include "window.cuh"
+
+namespace dich {
+
+struct Recs2;
+
+constexpr int kRegRows = 16;                            // block size of the register path
+constexpr int kRegPairBytes = 2 * kRegRows * 8 + 16;    // a thread's two blocks + 16 bytes of padding
+
+// shared memory of the register path for NT threads: the pair slots, the two spike tables, the
+// first/last values of the window's blocks, the scan scratch, the exponent maxima and the mbarrier
+__host__ __device__ inline size_t window_reg_smem_bytes(int NT) {
+  const size_t nw = (size_t)(NT / 32);
+  return (size_t)NT * kRegPairBytes + 2 * 16 * (size_t)kRegRows + 2 * 8 * 2 * (size_t)NT + 8 * 4 * nw +
+         4 * 2 * nw + 16;
+}
+
+// ---------------------------------------------------------------- mbarrier and bulk copies (PTX)
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  unsigned long long state;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+               : "=l"(state)
+               : "r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  (void)state;
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// global -> shared, completion counted in bytes on the mbarrier (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(sdst)),
+               "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// shared -> global in the thread's bulk group
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_addr(ssrc)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the thread's bulk stores have read their shared-memory source (the CTA may then exit)
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// generic-proxy writes to shared memory become visible to the bulk copies issued after this fence
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// a float's bits rebuilt as an FP64 bit pattern with the exponent rebias k (fast windows, ff.cuh)
+__device__ __forceinline__ double f32_as_f64(float f, unsigned k) {
+  const unsigned b = __float_as_uint(f);
+  return __hiloint2double((int)((((unsigned)((int)b >> 3)) & 0x8FFFFFFFu) + k), (int)(b << 29));
+}
+
+// Iterations of the bounded wait for the window's bulk loads (each try_wait may also suspend the
+// thread for a while); running out latches ST_TIMEOUT and the CTA returns without a store.
+constexpr int kBulkWaitIters = 1 << 22;
+
+template <int NT>
+__device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, const double* tab, int64_t P,
+                                           int64_t wlo, int nwin, int hl, int nown, int64_t row_lo,
+                                           unsigned char* smem) {
+  constexpr int NW = NT / 32;
+  constexpr int R = kRegRows;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  unsigned char* mine = smem + (size_t)tid * kRegPairBytes;
+  float4* tv4 = reinterpret_cast<float4*>(smem + (size_t)NT * kRegPairBytes);   // spikes, both lanes
+  float4* tw4 = tv4 + R;
+  ffv* sxs = reinterpret_cast<ffv*>(tw4 + R);
+  ffv* sxe = sxs + 2 * NT;
+  ffv* swv = sxe + 2 * NT;                                                       // 4 NW scan scratch
+  unsigned* sexp = reinterpret_cast<unsigned*>(swv + 4 * NW);                    // 2 NW exponent maxima
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sexp + 2 * NW);
+
+  const int b0 = 2 * tid, b1 = b0 + 1;
+  const bool act0 = b0 < nwin, act1 = b1 < nwin;
+  const int64_t mb0 = wlo + b0, mb1 = wlo + b1;
+  const bool last0 = act0 && (mb0 == P - 1), last1 = act1 && (mb1 == P - 1);
+  const double* src = A.F + (int64_t)blockIdx.y * A.ldf + pp->off + row_lo;
+  double* dst = A.x + (int64_t)blockIdx.y * A.ldx + pp->off + row_lo;
+
+  // ---------------------------------------------------------------- F -> the pair slots (bulk, async)
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) mbar_arrive_expect_tx(bar, (unsigned)(nwin * R * 8));
+  const unsigned mybytes = (act1 ? 2u : (act0 ? 1u : 0u)) * R * 8u;
+  if (mybytes) bulk_load(mine, src + (int64_t)b0 * R, mybytes, bar);
+  if (tid < R) {   // spike tables with both lanes filled and zeros past the truncation lengths
+    const float2* tf = reinterpret_cast<const float2*>(tab);
+    const float2 v = (tid < pp->Lv) ? tf[pp->o_vf + tid] : make_float2(0.f, 0.f);
+    const float2 w = (tid < pp->Lw) ? tf[pp->o_wf + tid] : make_float2(0.f, 0.f);
+    tv4[tid] = make_float4(v.x, v.x, v.y, v.y);
+    tw4[tid] = make_float4(w.x, w.x, w.y, w.y);
+  }
+  bool arrived = false;
+  for (int it = 0; it < kBulkWaitIters && !arrived; ++it) arrived = mbar_try_wait(bar, 0u);
+  if (!__syncthreads_and(arrived)) {
+    if (tid == 0) atomicOr(A.status, (unsigned)ST_TIMEOUT);
+    return;
+  }
+
+  // ---------------------------------------------------------------- the pair in registers
+  // a[k] = rows 2k, 2k+1 of block 2t; b[k] the same of block 2t+1 (inactive blocks: zeros)
+  double2 a[R / 2], b[R / 2];
+#pragma unroll
+  for (int k = 0; k < R / 2; ++k) {
+    a[k] = act0 ? *reinterpret_cast<const double2*>(mine + 16 * k) : make_double2(0.0, 0.0);
+    b[k] = act1 ? *reinterpret_cast<const double2*>(mine + 8 * R + 16 * k) : make_double2(0.0, 0.0);
+  }
+
+  // window scale (largest |F| near 2^16, an exact power of two) and the fast criterion: the
+  // largest and smallest FP64 high words with the sign cleared, over the active blocks
+  int wscale;
+  bool fast;
+  {
+    unsigned hmax = 0u, hmin = 0xFFFFFFFFu;
+    if (act0) {
+#pragma unroll
+      for (int k = 0; k < R / 2; ++k) {
+        const unsigned u = (unsigned)__double2hiint(a[k].x) & 0x7FFFFFFFu, v = (unsigned)__double2hiint(a[k].y) & 0x7FFFFFFFu;
+        hmax = __vimax3_u32(hmax, u, v);
+        hmin = __vimin3_u32(hmin, u, v);
+      }
+    }
+    if (act1) {
+#pragma unroll
+      for (int k = 0; k < R / 2; ++k) {
+        const unsigned u = (unsigned)__double2hiint(b[k].x) & 0x7FFFFFFFu, v = (unsigned)__double2hiint(b[k].y) & 0x7FFFFFFFu;
+        hmax = __vimax3_u32(hmax, u, v);
+        hmin = __vimin3_u32(hmin, u, v);
+      }
+    }
+    hmax = __reduce_max_sync(0xffffffffu, hmax);
+    hmin = __reduce_min_sync(0xffffffffu, hmin);
+    if (lane == 0) {
+      sexp[wid] = hmax;
+      sexp[NW + wid] = hmin;
+    }
+    __syncthreads();
+    hmax = sexp[0];
+    hmin = sexp[NW];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) {
+      hmax = max(hmax, sexp[w]);
+      hmin = min(hmin, sexp[NW + w]);
+    }
+    const int emax = (int)(hmax >> 20), emin = (int)(hmin >> 20);
+    wscale = (emax == 2047) ? 0 : ((emax == 0) ? 1000 : max(-1000, min(1000, (1023 + 16) - emax)));
+    fast = (emin >= 1) && (emax >= 239) && (emax <= 1935) && (emax - emin <= 119);
+  }
+
+  auto body = [&](auto fast_) {
+    constexpr bool FAST = decltype(fast_)::value;
+    const FastK fk = fast_k(wscale);
+    float2 H[R], L[R];   // (block 2t, block 2t+1) of row i: hi and lo parts
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const double d0 = (i & 1) ? a[i / 2].y : a[i / 2].x;
+      const double d1 = (i & 1) ? b[i / 2].y : b[i / 2].x;
+      if (FAST) {
+        split_fast(d0, fk, H[i].x, L[i].x);
+        split_fast(d1, fk, H[i].y, L[i].y);
+      } else {
+        split_sc(d0, wscale, H[i].x, L[i].x);
+        split_sc(d1, wscale, H[i].y, L[i].y);
+      }
+    }
+    if (!act0) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) H[i].x = L[i].x = 0.f;
+    }
+    if (!act1) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) H[i].y = L[i].y = 0.f;
+    }
+
+    // ------------------------------------------------------------ local recurrences (a1)
+    {  // u_i = f_i + rs u_{i-1}, u_{-1} = 0
+      const float2 rh = f2(pp->rs_h), rl = f2(pp->rs_l);
+      float2 uh = f2(0.f), ul = f2(0.f);
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        ff_axpy2(H[i], L[i], rh, rl, uh, ul, uh, ul);
+        H[i] = uh;
+        L[i] = ul;
+      }
+    }
+    {  // X_i = u_i + ib X_{i+1}, X_R = 0   (the particular solution is xp = g X)
+      const float2 bh = f2(pp->ib_h), bl = f2(pp->ib_l);
+      float2 xh = f2(0.f), xl = f2(0.f);
+#pragma unroll
+      for (int i = R - 1; i >= 0; --i) {
+        ff_axpy2(H[i], L[i], bh, bl, xh, xl, xh, xl);
+        H[i] = xh;
+        L[i] = xl;
+      }
+    }
+
+    // ------------------------------------------------------------ block ends, beta (eq. 16), tree (a2)
+    // xp(-1) = g ib X_0, alpha = xp_0 - xp(-1) v_0, omega = xp_{n-1} - xp(-1) v_{n-1}
+    const ff2 zero2{f2(0.f), f2(0.f)};
+    const ff2 g2 = ff2_bcast(ffv{pp->g_h, pp->g_l});
+    const ff2 X0 = ff2_make(H[0], L[0]);
+    const ff2 xm = ff2_mul(ff2_bcast(ffv{pp->gib_h, pp->gib_l}), X0);
+    ff2 al, om;
+    {
+      const ffv v0f{pp->v0_h, pp->v0_l}, v0l{pp->v0l_h, pp->v0l_l}, vef{pp->vend_h, pp->vend_l},
+          vel{pp->vendl_h, pp->vendl_l};
+      const ff2 v0 = ff2_pair(last0 ? v0l : v0f, last1 ? v0l : v0f);
+      const ff2 ve = ff2_pair(last0 ? vel : vef, last1 ? vel : vef);
+      al = ff2_sub(ff2_mul(g2, X0), ff2_mul(xm, v0));
+      om = ff2_sub(ff2_mul(g2, ff2_make(H[R - 1], L[R - 1])), ff2_mul(xm, ve));
+    }
+    const Recs2 bc2 = recs2(pp, tab, P, act0, act1, mb0, mb1);
+    const ff2 bL = ff2_sel(act0, act1, ff2_fma(bc2(BC_M00), al, ff2_mul(bc2(BC_M01), om)), zero2);
+    const ff2 bR = ff2_sel(act0, act1, ff2_fma(bc2(BC_M10), al, ff2_mul(bc2(BC_M11), om)), zero2);
+    ffv XL0 = ff_zero(), XR0 = ff_zero(), XL1 = ff_zero(), XR1 = ff_zero();
+    tree2<NT>(bc2, act0, act1, mb0, mb1, P, nwin, tid, bL, bR, swv, sxs, sxe, XL0, XR0, XL1, XR1);
+
+    // the next kernel of the stream may begin its launch (it waits for this grid to complete)
+    asm volatile("griddepcontrol.launch_dependents;");
+
+    // ------------------------------------------------------------ correction (a3), join, store
+    const bool own0 = act0 && b0 >= hl && b0 < hl + nown;
+    const bool own1 = act1 && b1 >= hl && b1 < hl + nown;
+    if (!(own0 || own1)) return;
+    // x = xp + (x_{s-1} - xp(-1)) v + x_{e+1} w, in units of X: coefficients times 1/g = -q
+    const ff2 qv = ff2_bcast(ffv{pp->q_h, pp->q_l});
+    const ff2 cL = ff2_mul(ff2_sub(ff2_pair(XL0, XL1), xm), qv);
+    const ff2 cR = ff2_mul(ff2_pair(XR0, XR1), qv);
+    const float2 gh = f2(pp->g_h), glo = f2(pp->g_l);
+    const double gd = pp->g;
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+      double o0[2], o1[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int i = 2 * k + j;
+        float2 xh = H[i], xl = L[i];
+        const float4 v = tv4[i], w = tw4[R - 1 - i];
+        ff_fma_acc2(cL.h, cL.l, make_float2(v.x, v.y), make_float2(v.z, v.w), xh, xl);
+        ff_fma_acc2(cR.h, cR.l, make_float2(w.x, w.y), make_float2(w.z, w.w), xh, xl);
+        if (FAST) {
+          // x = g (hi + lo) 2^-wscale: both parts rebuilt as FP64 bit patterns, one FMA
+          const float2 lg = mul2(xl, gh);
+          o0[j] = fma(f32_as_f64(xh.x, fk.join), gd, f32_as_f64(lg.x, fk.join));
+          o1[j] = fma(f32_as_f64(xh.y, fk.join), gd, f32_as_f64(lg.y, fk.join));
+        } else {
+          float2 yh, yl;
+          ff_mul2(gh, glo, xh, xl, yh, yl);
+          o0[j] = join_dadd(yh.x, yl.x, wscale);
+          o1[j] = join_dadd(yh.y, yl.y, wscale);
+        }
+      }
+      *reinterpret_cast<double2*>(mine + 16 * k) = make_double2(o0[0], o0[1]);
+      *reinterpret_cast<double2*>(mine + 8 * R + 16 * k) = make_double2(o1[0], o1[1]);
+    }
+    fence_async_smem();
+    if (own0 && own1)
+      bulk_store(dst + (int64_t)b0 * R, mine, 2u * R * 8u);
+    else if (own0)
+      bulk_store(dst + (int64_t)b0 * R, mine, R * 8u);
+    else
+      bulk_store(dst + (int64_t)b1 * R, mine + 8 * R, R * 8u);
+    bulk_commit();
+    bulk_wait_read();
+  };
+  if (fast)
+    body(std::true_type());
+  else
+    body(std::false_type());
+}
+
+}  // namespace dich

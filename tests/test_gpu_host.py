@@ -1,8 +1,11 @@
 """Solves from and to host memory (dichotomy_solve_host): the kernels reading and writing
 pinned host memory directly (chunks = 0), and the pipelined copy-in / solve / copy-out (chunks
->= 1, pageable buffers), give bitwise the device solve of the same plan and the oracle's
-solution to 1e-12 norm-wise, for every chunking and the paths that do not pipeline
-(one window, the general path, quasi-Toeplitz corners)."""
+>= 1, pageable buffers), give the oracle's solution to 1e-12 norm-wise, for every chunking and
+the paths that do not pipeline (one window, the general path, quasi-Toeplitz corners).  The
+pipelined solves run the device solve's kernels on device staging buffers and give it bitwise;
+the direct reads and writes of host memory keep to the shared-memory path of the window kernel
+(bulk copies serve device memory only), so they agree with the device solve -- which takes the
+register path for 16-row blocks -- to rounding (1e-13 norm-wise)."""
 import ctypes
 
 import numpy as np
@@ -38,7 +41,10 @@ def check_host_solve(D, t, N, chunks, prec, pinned=True, seed=0, **kw):
     xh = plan.solve_host(Fh, chunks=chunks)
     assert plan.status() == 0
     xd = plan.solve(torch.from_numpy(F).cuda()).cpu()
-    assert torch.equal(xh, xd), (N, chunks, plan.info)          # same windows, same kernels
+    if chunks == 0 and pinned:
+        assert rel(xh.numpy(), xd.numpy()) < 1e-13, (N, chunks, plan.info)
+    else:
+        assert torch.equal(xh, xd), (N, chunks, plan.info)      # same windows, same kernels
     if N <= 1 << 20:
         assert rel(xh.numpy(), oracle.thomas(t, F)) < TOL
     return plan.info
@@ -81,7 +87,7 @@ def test_host_solve_full_size(D):
     plan = D.Plan(*t, N, precision=2)
     xh = plan.solve_host(F)
     xd = plan.solve(F.cuda()).cpu()
-    assert plan.status() == 0 and torch.equal(xh, xd)
+    assert plan.status() == 0 and rel(xh.numpy(), xd.numpy()) < 1e-13
     idx = np.random.default_rng(6).integers(0, N - 4096, 4)
     Fn = F.numpy()
     for i0 in idx:   # sampled rows against the oracle on a stretch wide enough for the decay
