@@ -255,6 +255,20 @@ int build_system(double tm1, double t0, double tp1, int64_t N, int NT, int form,
   p.o_bcmf = take(kBC);
   p.o_bclf = take(kl * kBC);
   p.o_bcrf = take(kr * kBC);
+  p.o_kmf = take(4);
+  p.o_klf = take(kl * 4);
+  p.o_krf = take(kr * 4);
+  p.o_midf = take(66);
+  // warp-scan levels of the MIXED tree: a contribution from 2^(lev+1) or more blocks away carries a
+  // product of ratios below |rs|^(n 2^(lev+1)) (prefix) or |ib|^(n 2^(lev+1)) (suffix): below eps
+  auto levels = [&](int64_t Lrows) {
+    if (Lrows >= BIG) return 5;
+    const int64_t kb = ceil_div(Lrows, n);
+    int lev = 0;
+    while (lev < 5 && ((int64_t)2 << lev) < kb) ++lev;
+    return lev;
+  };
+  p.lev = std::max(levels(Ls), levels(Lb));
   split_ff(r.g * r.ib, p.gib_h, p.gib_l);
   split_ff(-r.q, p.q_h, p.q_l);
   split_ff(p.v0, p.v0_h, p.v0_l);
@@ -305,6 +319,31 @@ int build_system(double tm1, double t0, double tp1, int64_t N, int NT, int form,
   for (int j = 0; j < kBC; ++j) put_ff(p.o_bcmf + j, T[p.o_bcm + j]);
   for (int64_t j = 0; j < kl * kBC; ++j) put_ff(p.o_bclf + (int32_t)j, T[p.o_bcl + j]);
   for (int64_t j = 0; j < kr * kBC; ++j) put_ff(p.o_bcrf + (int32_t)j, T[p.o_bcr + j]);
+  // beta records (K1..K4) of the middle record and of the end tables, float-float
+  {
+    double k4[4];
+    beta_coeffs(&T[p.o_bcm], r.g, r.ib, p.v0, p.vend, k4);
+    for (int j = 0; j < 4; ++j) put_ff(p.o_kmf + j, k4[j]);
+    for (int64_t m = 0; m < kl; ++m) {
+      const bool lb = (m == P - 1);
+      beta_coeffs(&T[p.o_bcl + m * kBC], r.g, r.ib, lb ? p.v0l : p.v0, lb ? p.vendl : p.vend, k4);
+      for (int j = 0; j < 4; ++j) put_ff(p.o_klf + (int32_t)(m * 4 + j), k4[j]);
+    }
+    for (int64_t k = 0; k < kr; ++k) {
+      const bool lb = (P - kr + k == P - 1);
+      beta_coeffs(&T[p.o_bcr + k * kBC], r.g, r.ib, lb ? p.v0l : p.v0, lb ? p.vendl : p.vend, k4);
+      for (int j = 0; j < 4; ++j) put_ff(p.o_krf + (int32_t)(k * 4 + j), k4[j]);
+    }
+    // powers of the middle record's pair maps: (a^2)^t and (c^2)^t, t = 0..32
+    const double a2 = T[p.o_bcm + BC_A] * T[p.o_bcm + BC_A], c2 = T[p.o_bcm + BC_C] * T[p.o_bcm + BC_C];
+    double pa = 1.0, pc = 1.0;
+    for (int t = 0; t <= 32; ++t) {
+      put_ff(p.o_midf + t, pa);
+      put_ff(p.o_midf + 33 + t, pc);
+      pa *= a2;
+      pc *= c2;
+    }
+  }
   return DICH_OK;
 }
 

@@ -159,10 +159,12 @@ __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow_, int 
 // first/last values of every block (eq. 18) in sxs/sxe, and the neighbours' values the correction of
 // the thread's two blocks needs: XL = x_{s-1}, XR = x_{e+1} (zero coupling enters at both window
 // ends).  bc2(j): coefficient j of both blocks' records; bL, bR: beta (eq. 16) of both blocks.
+// lev: warp-scan levels that run (the plan's; contributions from 2^(lev+1) or more blocks away are
+// below its truncation threshold, 5 = the whole warp).
 template <int NT, class BC>
 __device__ __forceinline__ void tree2(const BC& bc2, bool act0, bool act1, int64_t mb0, int64_t mb1, int64_t P,
                                       int nwin, int tid, const ff2& bL, const ff2& bR, ffv* swv, ffv* sxs, ffv* sxe,
-                                      ffv& XL0, ffv& XR0, ffv& XL1, ffv& XR1) {
+                                      ffv& XL0, ffv& XR0, ffv& XL1, ffv& XR1, int lev = 5) {
   using O = OpsFF;
   constexpr int NW = NT / 32;
   const int lane = tid & 31, wid = tid >> 5;
@@ -179,8 +181,10 @@ __device__ __forceinline__ void tree2(const BC& bc2, bool act0, bool act1, int64
   ff2 Tv = ff2_fma(m1, ff2{make_float2(pbv.h.x, qbv.h.y), make_float2(pbv.l.x, qbv.l.y)},
                    ff2{make_float2(pbv.h.y, qbv.h.x), make_float2(pbv.l.y, qbv.l.x)});
   // warp scans: the prefix from lane - d, the suffix from lane + d; identity maps past the ends
+  const int dlim = 1 << lev;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
+    if (d >= dlim) break;
     const float yah = __shfl_up_sync(0xffffffffu, Sv.h.x, d), yal = __shfl_up_sync(0xffffffffu, Sv.l.x, d);
     const float ybh = __shfl_up_sync(0xffffffffu, Tv.h.x, d), ybl = __shfl_up_sync(0xffffffffu, Tv.l.x, d);
     const float zah = __shfl_down_sync(0xffffffffu, Sv.h.y, d), zal = __shfl_down_sync(0xffffffffu, Sv.l.y, d);
@@ -241,12 +245,17 @@ __device__ __forceinline__ void tree2(const BC& bc2, bool act0, bool act1, int64
   }
 }
 
-// coefficient records of a thread's two blocks (the float-float copies of the plan tables)
+// coefficient records of a thread's two blocks (the float-float copies of the plan tables) and
+// their beta records (K1..K4 of beta_coeffs)
 struct Recs2 {
   const float2* tf;
-  int64_t r0, r1;
+  int64_t r0, r1, k0, k1;
   __device__ __forceinline__ ff2 operator()(int j) const {  // coefficient j of both blocks' records
     const float2 c0 = tf[r0 + j], c1 = tf[r1 + j];
+    return ff2_make(make_float2(c0.x, c1.x), make_float2(c0.y, c1.y));
+  }
+  __device__ __forceinline__ ff2 k(int j) const {           // beta coefficient K_{j+1} of both blocks
+    const float2 c0 = tf[k0 + j], c1 = tf[k1 + j];
     return ff2_make(make_float2(c0.x, c1.x), make_float2(c0.y, c1.y));
   }
 };
@@ -257,8 +266,13 @@ __device__ __forceinline__ Recs2 recs2(const SysPlan* pp, const double* tab, int
     if (m >= P - pp->kr) return pp->o_bcrf + (m - (P - pp->kr)) * kBC;
     return pp->o_bcmf;
   };
+  auto krec_of = [&](int64_t m) -> int64_t {
+    if (m < pp->kl) return pp->o_klf + m * 4;
+    if (m >= P - pp->kr) return pp->o_krf + (m - (P - pp->kr)) * 4;
+    return pp->o_kmf;
+  };
   return Recs2{reinterpret_cast<const float2*>(tab), act0 ? rec_of(mb0) : pp->o_bcmf,
-               act1 ? rec_of(mb1) : pp->o_bcmf};
+               act1 ? rec_of(mb1) : pp->o_bcmf, act0 ? krec_of(mb0) : pp->o_kmf, act1 ? krec_of(mb1) : pp->o_kmf};
 }
 
 }  // namespace dich
@@ -520,7 +534,7 @@ __global__ void __launch_bounds__(NT, (ADJ ? 768 : 512) / NT) k_window2(const Wi
 
   ffv XL0 = ff_zero(), XR0 = ff_zero(), XL1 = ff_zero(), XR1 = ff_zero();
   if (A.mode == MODE_FULL) {
-    tree2<NT>(bc2, act0, act1, mb0, mb1, P, nwin, tid, bL, bR, swv, sxs, sxe, XL0, XR0, XL1, XR1);
+    tree2<NT>(bc2, act0, act1, mb0, mb1, P, nwin, tid, bL, bR, swv, sxs, sxe, XL0, XR0, XL1, XR1, pp->lev);
   } else {  // MODE_APPLY: neighbours' first/last values from the global scan (unscaled FP64)
     const double upw = pow2i(wscale);
     auto to_ff = [&](double d) {

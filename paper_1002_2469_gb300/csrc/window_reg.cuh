@@ -87,6 +87,76 @@ __device__ __forceinline__ double f32_as_f64(float f, unsigned k) {
   return __hiloint2double((int)((((unsigned)((int)b >> 3)) & 0x8FFFFFFFu) + k), (int)(b << 29));
 }
 
+// The dichotomy tree (a2) of a window whose blocks all carry the middle record -- every block at
+// least kl blocks from the system's start and kr from its end, where the ratios of eq. 15-18 are the
+// same constants for every block (the Toeplitz saving of Sec. 3.1).  Same scans and first/last
+// values as tree2, with uniform coefficients: a thread's pair of blocks composes to the prefix map
+// A -> a^2 A + b (a beta^R_0 + beta^R_1) and the suffix map B -> c^2 B + d (c beta^L_1 + beta^L_0),
+// level d of the warp scans multiplies by (a^2)^d, (c^2)^d from the plan's power table (tf + o_midf:
+// (a^2)^t then (c^2)^t, t = 0..32), and only the plan's `lev` levels run.  A warp's totals enter the
+// following warps through (a^2)^32 (prefix) and (c^2)^32 (suffix); lane t of a warp receives the
+// prefix of the warps before it times (a^2)^t and the suffix of the warps after it times (c^2)^(31-t).
+template <int NT>
+__device__ __forceinline__ void tree_mid(const float2* tf, const SysPlan* pp, int nwin, int tid, const ff2& bL,
+                                         const ff2& bR, ffv* swv, ffv* sxs, ffv* sxe, ffv& XL0, ffv& XR0, ffv& XL1,
+                                         ffv& XR1) {
+  constexpr int NW = NT / 32;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int b0 = 2 * tid, b1 = b0 + 1;
+  auto ld = [&](int64_t at) { return ff_of(tf[at]); };
+  const int64_t rm = pp->o_bcmf, pw = pp->o_midf;
+  const ffv a = ld(rm + BC_A), b = ld(rm + BC_B), c = ld(rm + BC_C), d = ld(rm + BC_D);
+  const ff2 ac = ff2_pair(a, c);
+  // lane x: the prefix (b beta^R of both blocks), lane y: the suffix (d beta^L of both blocks)
+  const ff2 pbv = ff2_mul(ff2_bcast(b), bR), qbv = ff2_mul(ff2_bcast(d), bL);
+  // composite maps of the pair: prefix a pb_0 + pb_1, suffix c qb_1 + qb_0
+  const ff2 p0 = ff2{make_float2(pbv.h.x, qbv.h.y), make_float2(pbv.l.x, qbv.l.y)};   // (pb_0, qb_1)
+  const ff2 p1 = ff2{make_float2(pbv.h.y, qbv.h.x), make_float2(pbv.l.y, qbv.l.x)};   // (pb_1, qb_0)
+  ff2 Tv = ff2_fma(ac, p0, p1);
+  const int lev = pp->lev;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    if (k >= lev) break;
+    const int dd = 1 << k;
+    const ff2 M = ff2_pair(ld(pw + dd), ld(pw + 33 + dd));
+    const float yh = __shfl_up_sync(0xffffffffu, Tv.h.x, dd), yl = __shfl_up_sync(0xffffffffu, Tv.l.x, dd);
+    const float zh = __shfl_down_sync(0xffffffffu, Tv.h.y, dd), zl = __shfl_down_sync(0xffffffffu, Tv.l.y, dd);
+    const bool up = lane >= dd, dn = lane + dd < 32;
+    const ff2 Y{make_float2(up ? yh : 0.f, dn ? zh : 0.f), make_float2(up ? yl : 0.f, dn ? zl : 0.f)};
+    Tv = ff2_fma(M, Y, Tv);
+  }
+  if (lane == 31) swv[wid] = ff2_x(Tv);
+  if (lane == 0) swv[NW + wid] = ff2_y(Tv);
+  // inclusive values of the neighbouring lanes (the prefix entering the pair, the suffix beyond it)
+  float eh = __shfl_up_sync(0xffffffffu, Tv.h.x, 1), el = __shfl_up_sync(0xffffffffu, Tv.l.x, 1);
+  float fh = __shfl_down_sync(0xffffffffu, Tv.h.y, 1), fl = __shfl_down_sync(0xffffffffu, Tv.l.y, 1);
+  if (lane == 0) eh = el = 0.f;
+  if (lane == 31) fh = fl = 0.f;
+  __syncthreads();
+  ffv Aw = ff_zero(), Bw = ff_zero();   // zero coupling enters at both window ends
+  const ffv a32 = ld(pw + 32), c32 = ld(pw + 33 + 32);
+  for (int w = 0; w < wid; ++w) Aw = ff_fma(a32, Aw, swv[w]);
+  for (int w = NW - 1; w > wid; --w) Bw = ff_fma(c32, Bw, swv[NW + w]);
+  const ff2 E = ff2_fma(ff2_pair(ld(pw + lane), ld(pw + 33 + (31 - lane))), ff2_pair(Aw, Bw),
+                        ff2{make_float2(eh, fh), make_float2(el, fl)});
+  // (A entering block 1, B beyond block 0)
+  const ff2 G = ff2_fma(ac, E, p0);
+  const ff2 Av{make_float2(E.h.x, G.h.x), make_float2(E.l.x, G.l.x)};   // (A_0, A_1)
+  const ff2 Bv{make_float2(G.h.y, E.h.y), make_float2(G.l.y, E.l.y)};   // (B_0, B_1)
+  // first/last values of both blocks (eq. 18)
+  const ff2 xs = ff2_add(ff2_fma(ff2_bcast(ld(rm + BC_TL)), Bv, bL), Av);
+  const ff2 xe = ff2_fma(ff2_bcast(ld(rm + BC_TR)), Av, ff2_add(bR, Bv));
+  sxs[b0] = ff2_x(xs);
+  sxe[b0] = ff2_x(xe);
+  sxs[b1] = ff2_y(xs);
+  sxe[b1] = ff2_y(xe);
+  __syncthreads();
+  if (b0 > 0) XL0 = sxe[b0 - 1];
+  XR0 = sxs[b1];
+  XL1 = sxe[b0];
+  if (b1 + 1 < nwin) XR1 = sxs[b1 + 1];
+}
+
 // Iterations of the bounded wait for the window's bulk loads (each try_wait may also suspend the
 // thread for a while); running out latches ST_TIMEOUT and the CTA returns without a store.
 constexpr int kBulkWaitIters = 1 << 22;
@@ -234,26 +304,28 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
       }
     }
 
-    // ------------------------------------------------------------ block ends, beta (eq. 16), tree (a2)
-    // xp(-1) = g ib X_0, alpha = xp_0 - xp(-1) v_0, omega = xp_{n-1} - xp(-1) v_{n-1}
+    // ------------------------------------------------------------ beta (eq. 16), tree (a2)
+    // beta^L = K1 X_0 + K2 X_{n-1}, beta^R = K3 X_0 + K4 X_{n-1} (the block's beta record: the 2x2 map M
+    // of eq. 16 applied to alpha = g X_0 - g ib v_0 X_0, omega = g X_{n-1} - g ib v_{n-1} X_0)
     const ff2 zero2{f2(0.f), f2(0.f)};
-    const ff2 g2 = ff2_bcast(ffv{pp->g_h, pp->g_l});
-    const ff2 X0 = ff2_make(H[0], L[0]);
-    const ff2 xm = ff2_mul(ff2_bcast(ffv{pp->gib_h, pp->gib_l}), X0);
-    ff2 al, om;
-    {
-      const ffv v0f{pp->v0_h, pp->v0_l}, v0l{pp->v0l_h, pp->v0l_l}, vef{pp->vend_h, pp->vend_l},
-          vel{pp->vendl_h, pp->vendl_l};
-      const ff2 v0 = ff2_pair(last0 ? v0l : v0f, last1 ? v0l : v0f);
-      const ff2 ve = ff2_pair(last0 ? vel : vef, last1 ? vel : vef);
-      al = ff2_sub(ff2_mul(g2, X0), ff2_mul(xm, v0));
-      om = ff2_sub(ff2_mul(g2, ff2_make(H[R - 1], L[R - 1])), ff2_mul(xm, ve));
-    }
-    const Recs2 bc2 = recs2(pp, tab, P, act0, act1, mb0, mb1);
-    const ff2 bL = ff2_sel(act0, act1, ff2_fma(bc2(BC_M00), al, ff2_mul(bc2(BC_M01), om)), zero2);
-    const ff2 bR = ff2_sel(act0, act1, ff2_fma(bc2(BC_M10), al, ff2_mul(bc2(BC_M11), om)), zero2);
+    const ff2 X0 = ff2_make(H[0], L[0]), Xe = ff2_make(H[R - 1], L[R - 1]);
+    const float2* tf = reinterpret_cast<const float2*>(tab);
+    // every block of the window carries the middle record: uniform coefficients (tree_mid)
+    const bool mid = (nwin == 2 * NT) && (wlo >= pp->kl) && (wlo + nwin <= P - pp->kr);
+    ff2 bL, bR;
     ffv XL0 = ff_zero(), XR0 = ff_zero(), XL1 = ff_zero(), XR1 = ff_zero();
-    tree2<NT>(bc2, act0, act1, mb0, mb1, P, nwin, tid, bL, bR, swv, sxs, sxe, XL0, XR0, XL1, XR1);
+    if (mid) {
+      const ffv k1 = ff_of(tf[pp->o_kmf]), k2 = ff_of(tf[pp->o_kmf + 1]), k3 = ff_of(tf[pp->o_kmf + 2]),
+                k4 = ff_of(tf[pp->o_kmf + 3]);
+      bL = ff2_fma(ff2_bcast(k2), Xe, ff2_mul(ff2_bcast(k1), X0));
+      bR = ff2_fma(ff2_bcast(k4), Xe, ff2_mul(ff2_bcast(k3), X0));
+      tree_mid<NT>(tf, pp, nwin, tid, bL, bR, swv, sxs, sxe, XL0, XR0, XL1, XR1);
+    } else {
+      const Recs2 bc2 = recs2(pp, tab, P, act0, act1, mb0, mb1);
+      bL = ff2_sel(act0, act1, ff2_fma(bc2.k(1), Xe, ff2_mul(bc2.k(0), X0)), zero2);
+      bR = ff2_sel(act0, act1, ff2_fma(bc2.k(3), Xe, ff2_mul(bc2.k(2), X0)), zero2);
+      tree2<NT>(bc2, act0, act1, mb0, mb1, P, nwin, tid, bL, bR, swv, sxs, sxe, XL0, XR0, XL1, XR1, pp->lev);
+    }
 
     // the next kernel of the stream may begin its launch (it waits for this grid to complete)
     asm volatile("griddepcontrol.launch_dependents;");
@@ -262,9 +334,11 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     const bool own0 = act0 && b0 >= hl && b0 < hl + nown;
     const bool own1 = act1 && b1 >= hl && b1 < hl + nown;
     if (!(own0 || own1)) return;
-    // x = xp + (x_{s-1} - xp(-1)) v + x_{e+1} w, in units of X: coefficients times 1/g = -q
+    // x = xp + (x_{s-1} - xp(-1)) v + x_{e+1} w, in units of X (x = g X): the coefficients are
+    // x_{s-1} / g - ib X_0 and x_{e+1} / g, with 1/g = -q
     const ff2 qv = ff2_bcast(ffv{pp->q_h, pp->q_l});
-    const ff2 cL = ff2_mul(ff2_sub(ff2_pair(XL0, XL1), xm), qv);
+    const ff2 ibx = ff2_mul(ff2_bcast(ffv{pp->ib_h, pp->ib_l}), X0);
+    const ff2 cL = ff2_fma(qv, ff2_pair(XL0, XL1), ff2{make_float2(-ibx.h.x, -ibx.h.y), make_float2(-ibx.l.x, -ibx.l.y)});
     const ff2 cR = ff2_mul(ff2_pair(XR0, XR1), qv);
     const float2 gh = f2(pp->g_h), glo = f2(pp->g_l);
     const double gd = pp->g;
