@@ -86,6 +86,11 @@ __device__ __forceinline__ double f32_as_f64(float f, unsigned k) {
   const unsigned b = __float_as_uint(f);
   return __hiloint2double((int)((((unsigned)((int)b >> 3)) & 0x8FFFFFFFu) + k), (int)(b << 29));
 }
+// the same without the rebias: exactly f * 2^-896 (zeros and subnormal floats included)
+__device__ __forceinline__ double f32_as_f64_unbiased(float f) {
+  const unsigned b = __float_as_uint(f);
+  return __hiloint2double((int)(((unsigned)((int)b >> 3)) & 0x8FFFFFFFu), (int)(b << 29));
+}
 
 // The dichotomy tree (a2) of a window whose blocks all carry the middle record -- every block at
 // least kl blocks from the system's start and kr from its end, where the ratios of eq. 15-18 are the
@@ -135,8 +140,13 @@ __device__ __forceinline__ void tree_mid(const float2* tf, const SysPlan* pp, in
   __syncthreads();
   ffv Aw = ff_zero(), Bw = ff_zero();   // zero coupling enters at both window ends
   const ffv a32 = ld(pw + 32), c32 = ld(pw + 33 + 32);
-  for (int w = 0; w < wid; ++w) Aw = ff_fma(a32, Aw, swv[w]);
-  for (int w = NW - 1; w > wid; --w) Bw = ff_fma(c32, Bw, swv[NW + w]);
+  if (lev < 5) {   // couplings reach fewer than 2^(lev+1) <= 32 blocks: only the neighbouring warps'
+    if (wid > 0) Aw = swv[wid - 1];
+    if (wid < NW - 1) Bw = swv[NW + wid + 1];
+  } else {
+    for (int w = 0; w < wid; ++w) Aw = ff_fma(a32, Aw, swv[w]);
+    for (int w = NW - 1; w > wid; --w) Bw = ff_fma(c32, Bw, swv[NW + w]);
+  }
   const ff2 E = ff2_fma(ff2_pair(ld(pw + lane), ld(pw + 33 + (31 - lane))), ff2_pair(Aw, Bw),
                         ff2{make_float2(eh, fh), make_float2(el, fl)});
   // (A entering block 1, B beyond block 0)
@@ -257,8 +267,14 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     fast = (emin >= 1) && (emax >= 239) && (emax <= 1935) && (emax - emin <= 119);
   }
 
-  auto body = [&](auto fast_) {
+  // fast windows: the FP64 multiplier of the join, G = g 2^(896 - wscale), folds the rebias of the
+  // leading part into the FMA when its exponent stays in range (|F| up to about 2^80 at |g| <= 2^60)
+  const int ghw = __double2hiint(pp->g);
+  const bool gfold = ((ghw >> 20) & 0x7FF) + 896 - wscale <= 2046;
+  const double G = __hiloint2double((int)((unsigned)ghw + ((unsigned)(896 - wscale) << 20)), __double2loint(pp->g));
+  auto body = [&](auto fast_, auto gfold_) {
     constexpr bool FAST = decltype(fast_)::value;
+    constexpr bool GFOLD = decltype(gfold_)::value;
     const FastK fk = fast_k(wscale);
     float2 H[R], L[R];   // (block 2t, block 2t+1) of row i: hi and lo parts
 #pragma unroll
@@ -352,8 +368,13 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
         const float4 v = tv4[i], w = tw4[R - 1 - i];
         ff_fma_acc2(cL.h, cL.l, make_float2(v.x, v.y), make_float2(v.z, v.w), xh, xl);
         ff_fma_acc2(cR.h, cR.l, make_float2(w.x, w.y), make_float2(w.z, w.w), xh, xl);
-        if (FAST) {
-          // x = g (hi + lo) 2^-wscale: both parts rebuilt as FP64 bit patterns, one FMA
+        if (FAST && GFOLD) {
+          // x = g (hi + lo) 2^-wscale = G (hi 2^-896) + (g lo) 2^-wscale: both parts rebuilt as FP64
+          // bit patterns (the leading one without rebias), one FMA
+          const float2 lg = mul2(xl, gh);
+          o0[j] = fma(f32_as_f64_unbiased(xh.x), G, f32_as_f64(lg.x, fk.join));
+          o1[j] = fma(f32_as_f64_unbiased(xh.y), G, f32_as_f64(lg.y, fk.join));
+        } else if (FAST) {
           const float2 lg = mul2(xl, gh);
           o0[j] = fma(f32_as_f64(xh.x, fk.join), gd, f32_as_f64(lg.x, fk.join));
           o1[j] = fma(f32_as_f64(xh.y, fk.join), gd, f32_as_f64(lg.y, fk.join));
@@ -377,10 +398,12 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     bulk_commit();
     bulk_wait_read();
   };
-  if (fast)
-    body(std::true_type());
+  if (fast && gfold)
+    body(std::true_type(), std::true_type());
+  else if (fast)
+    body(std::true_type(), std::false_type());
   else
-    body(std::false_type());
+    body(std::false_type(), std::false_type());
 }
 
 }  // namespace dich
