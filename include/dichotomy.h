@@ -80,11 +80,18 @@ enum {
   DICH_FLAG_CHECK_FINITE = 2,   /* latch DICH_ERR_NONFINITE if any output is not finite */
   DICH_FLAG_HOST_PRELIM = 4,    /* general matrices: preliminary step on the host at plan time */
   DICH_FLAG_DEVICE_PRELIM = 8,  /* general matrices: preliminary step on the device at bind time */
-  DICH_FLAG_ALLOW_NOT_DOMINANT = 16  /* accept matrices without diagonal dominance.  Toeplitz plans and
+  DICH_FLAG_ALLOW_NOT_DOMINANT = 16, /* accept matrices without diagonal dominance.  Toeplitz plans and
                                         batches: when the roots of t_1 r^2 + t_0 r + t_-1 are real and
                                         separated by the unit circle (what the recurrences need);
                                         general matrices: any rows, judged by dich_plan_info.growth;
                                         check results with dichotomy_residual / dichotomy_gen_residual */
+  /* MIXED-form window kernel of Toeplitz plans and batches (the results agree to rounding):
+   * the register path keeps a thread's two 16-row blocks in registers (bulk copies in and out,
+   * four CTAs per SM); the shared-memory path sweeps the window's tile in shared memory (six CTAs
+   * per SM).  Default: the register path for single plans, and for batches unless most of their
+   * MIXED windows are whole one-window systems (latency-bound windows, where occupancy wins). */
+  DICH_FLAG_REG_PATH = 32,           /* the register path wherever its window shape allows */
+  DICH_FLAG_SMEM_PATH = 64           /* the shared-memory path for every window */
 };
 
 typedef struct {

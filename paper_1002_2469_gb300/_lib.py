@@ -24,6 +24,7 @@ STATUS_NAMES = {
 }
 PREC_F64, PREC_MIXED, PREC_AUTO = 0, 1, 2
 FLAG_FORCE_GENERAL, FLAG_CHECK_FINITE, FLAG_HOST_PRELIM, FLAG_DEVICE_PRELIM, FLAG_ALLOW_NOT_DOMINANT = 1, 2, 4, 8, 16
+FLAG_REG_PATH, FLAG_SMEM_PATH = 32, 64
 
 EXPORTS = [
     "dichotomy_plan", "dichotomy_plan_ex", "dichotomy_plan_quasi", "dichotomy_plan_info", "dichotomy_plan_workspace_bytes",

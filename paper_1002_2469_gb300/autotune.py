@@ -130,14 +130,17 @@ def plan(t, N: int, precision: int = D.PREC_AUTO, tune_if_missing: bool = False)
     return D.Plan(*t, N, **kw)
 
 
-BATCH_CANDIDATES = [(0, 0), (64, 16), (128, 16), (64, 32), (128, 24), (256, 16)]
+# (threads, block size, flags): 0 = the library's choice; the flags pick the MIXED window kernel's
+# register path or shared-memory path (by default a per-batch heuristic)
+BATCH_CANDIDATES = [(0, 0, 0), (0, 0, D.FLAG_REG_PATH), (0, 0, D.FLAG_SMEM_PATH), (64, 16, 0), (128, 24, 0),
+                    (64, 32, 0), (256, 16, 0)]
 
 
 def tune_batch(N, t_m1, t_0, t_1, precision: int = D.PREC_AUTO, candidates=None, verbose: bool = False) -> dict:
-    """Time (threads, block size) candidates for one batch of systems (sizes N, coefficient
+    """Time (threads, block size, flags) candidates for one batch of systems (sizes N, coefficient
     arrays) with the library's batched solve and return the fastest as {"threads",
-    "block_size", "ms"}; (0, 0) is the library's default choice.  Not cached: a batch's
-    composition is its own key."""
+    "block_size", "flags", "ms"}; (0, 0, 0) is the library's default choice.  Not cached: a
+    batch's composition is its own key."""
     import numpy as np
     N = np.asarray(N, dtype=np.int64)
     g = torch.Generator(device="cuda")
@@ -145,14 +148,16 @@ def tune_batch(N, t_m1, t_0, t_1, precision: int = D.PREC_AUTO, candidates=None,
     F = torch.randn(int(N.sum()), dtype=torch.float64, device="cuda", generator=g)
     x = torch.empty_like(F)
     best = None
-    for nt, bs in (candidates or BATCH_CANDIDATES):
+    for cand in (candidates or BATCH_CANDIDATES):
+        nt, bs, fl = (tuple(cand) + (0,))[:3]
         try:
-            b = D.Batch(N, t_m1, t_0, t_1, precision=precision, threads=nt, block_size=bs)
+            b = D.Batch(N, t_m1, t_0, t_1, precision=precision, threads=nt, block_size=bs, flags=fl)
         except D.DichotomyError:
             continue
         ms = _time(b, F, x)
         if verbose:
-            print(f"threads={nt} n={bs} -> {ms:.4f} ms")
+            print(f"threads={nt} n={bs} flags={fl} -> {ms:.4f} ms")
         if best is None or ms < best["ms"]:
-            best = {"threads": nt, "block_size": bs, "ms": ms}
+            best = {"threads": nt, "block_size": bs, "flags": fl, "ms": ms}
+        del b
     return best

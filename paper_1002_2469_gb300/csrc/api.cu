@@ -76,6 +76,7 @@ int read_opts(const dich_opts* o, Opts& out) {
   if (o->precision < 0 || o->precision > 2) return DICH_ERR_ARG;
   if (o->threads != 0 && o->threads != 64 && o->threads != 128 && o->threads != 256) return DICH_ERR_ARG;
   if (!(o->trunc_eps >= 0.0) || o->trunc_eps >= 1e-3) return DICH_ERR_ARG;
+  if ((o->flags & DICH_FLAG_REG_PATH) && (o->flags & DICH_FLAG_SMEM_PATH)) return DICH_ERR_ARG;
   out.n_req = o->block_size;
   out.prec = o->precision;
   out.NT = o->threads;
@@ -784,7 +785,9 @@ static int plan_launch(dich_plan_t p, const double* F, double* x, const double* 
   a.sys_offset = sys_offset;
   a.ldf = ldf;
   a.ldx = ldx;
-  a.bulk = device_mem ? 1 : 0;
+  // the register path (bulk copies) only for full solves of device memory, unless the plan asks
+  // for the shared-memory path (the general path's passes always take that one)
+  a.bulk = (device_mem && p->path != PATH_GENERAL && !(p->opts.flags & DICH_FLAG_SMEM_PATH)) ? 1 : 0;
   const size_t smem = smem_bytes(p->NT, p->n_smem, p->form);
   // windows [win0, win0 + grid) of the single and halo paths (all of them unless a range is given)
   const int grid = (int)((nwin < 0) ? p->tiles : nwin);
@@ -1050,6 +1053,7 @@ struct dich_batch_s {
   }
   int64_t nsys = 0;
   Opts opts;
+  bool reg_path = true;                   // MIXED windows on the register path (else shared memory)
   // a second stream for the FP64-form windows when a batch has both forms: the two launches
   // overlap (fork/join through events on the caller's stream; CUDA-graph capture follows them)
   cudaStream_t aux = nullptr;
@@ -1204,6 +1208,19 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
     b->first[f].push_back(first);
     b->count[f].push_back((int64_t)b->items[f].size() - first);
     b->n_smem[f] = std::max(b->n_smem[f], q.n);
+  }
+  // MIXED windows: the register path unless most of them are whole one-window systems, whose
+  // windows are latency-bound (their own tables, no halo to amortise the set-up): there the
+  // shared-memory path's six CTAs per SM win (4096 Poisson modes of 4096 rows: 101 us against
+  // 106-110 us); explicit flags decide otherwise
+  {
+    int64_t whole = 0;
+    for (int64_t s : order)
+      if (b->form[s] == FORM_MIXED && b->fwd[s].rec.P <= window_blocks(b->NT[FORM_MIXED], FORM_MIXED)) ++whole;
+    const int64_t nmix = (int64_t)b->items[FORM_MIXED].size();
+    b->reg_path = (o.flags & DICH_FLAG_REG_PATH) ? true
+                  : (o.flags & DICH_FLAG_SMEM_PATH) ? false
+                                                    : (2 * whole <= nmix);
   }
   // general-path systems: block offsets in the shared buffers, windows without halo, scan chunks
   for (int32_t s : b->general) {
@@ -1446,7 +1463,7 @@ static int batch_launch(dich_batch_t b, const double* F, double* x, const double
     a.check_finite = (b->opts.flags & DICH_FLAG_CHECK_FINITE) ? 1 : 0;
     a.n_smem = b->n_smem[f];
     a.sys_offset = sys_offset;
-    a.bulk = 1;   // batch vectors are device memory
+    a.bulk = b->reg_path ? 1 : 0;   // batch vectors are device memory
     const size_t smem = smem_bytes(b->NT[f], a.n_smem, f);
     cudaError_t e = (f == FORM_F64) ? launch_window_f64(b->NT[f], (int)nitems, smem, sf, a)
                                     : launch_window_mixed(b->NT[f], (int)nitems, smem, sf, a);

@@ -3,11 +3,12 @@
 
 namespace dich {
 
-// ADJ: the adjoint's instantiation (gradient sums in the store loop), chosen by a.xf
-template <int NT, bool ADJ>
+// KIND: the adjoint's instantiation (gradient sums in the store loop) when a.xf is set, else the
+// register-path one when a.bulk allows bulk copies, else the shared-memory one (six CTAs per SM)
+template <int NT, int KIND>
 static cudaError_t launch_one(int grid, int grid_y, size_t smem, cudaStream_t st, const WinArgs& a) {
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_window2<NT, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_window2<NT, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -21,15 +22,21 @@ static cudaError_t launch_one(int grid, int grid_y, size_t smem, cudaStream_t st
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_window2<NT, ADJ>, a);
+  return cudaLaunchKernelEx(&cfg, k_window2<NT, KIND>, a);
+}
+
+template <int NT>
+static cudaError_t launch_kind(int grid, int grid_y, size_t smem, cudaStream_t st, const WinArgs& a) {
+  if (a.xf != nullptr) return launch_one<NT, KIND_ADJ>(grid, grid_y, smem, st, a);
+  if (a.bulk) return launch_one<NT, KIND_REG>(grid, grid_y, smem, st, a);
+  return launch_one<NT, KIND_SMEM>(grid, grid_y, smem, st, a);
 }
 
 cudaError_t launch_window_mixed(int NT, int grid, size_t smem, cudaStream_t st, const WinArgs& a, int grid_y) {
-  const bool adj = (a.xf != nullptr);
   switch (NT) {
-    case 64: return adj ? launch_one<64, true>(grid, grid_y, smem, st, a) : launch_one<64, false>(grid, grid_y, smem, st, a);
-    case 128: return adj ? launch_one<128, true>(grid, grid_y, smem, st, a) : launch_one<128, false>(grid, grid_y, smem, st, a);
-    case 256: return adj ? launch_one<256, true>(grid, grid_y, smem, st, a) : launch_one<256, false>(grid, grid_y, smem, st, a);
+    case 64: return launch_kind<64>(grid, grid_y, smem, st, a);
+    case 128: return launch_kind<128>(grid, grid_y, smem, st, a);
+    case 256: return launch_kind<256>(grid, grid_y, smem, st, a);
     default: return cudaErrorInvalidValue;
   }
 }

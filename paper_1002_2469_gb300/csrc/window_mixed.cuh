@@ -290,10 +290,15 @@ __host__ __device__ inline size_t window2_smem_bytes(int NT, int n_smem) {
   return tile > reg ? tile : reg;
 }
 
-// ADJ: the adjoint's instantiation (80 registers: six CTAs of 128 threads per SM); the forward one
-// allows the 128 registers of the register path (four CTAs of 128 threads per SM)
-template <int NT, bool ADJ>
-__global__ void __launch_bounds__(NT, (ADJ ? 768 : 512) / NT) k_window2(const WinArgs A) {
+// Instantiations: KIND_REG -- the forward solve with the register path for windows it serves (up to
+// 128 registers: four CTAs of 128 threads per SM); KIND_SMEM -- the forward solve on the shared-memory
+// path only (80 registers: six CTAs per SM, for launches of many short, latency-bound windows);
+// KIND_ADJ -- the adjoint (shared-memory path, gradient sums in the store loop, six CTAs per SM).
+enum WinKind : int { KIND_REG = 0, KIND_ADJ = 1, KIND_SMEM = 2 };
+
+template <int NT, int KIND>
+__global__ void __launch_bounds__(NT, (KIND == KIND_REG ? 512 : 768) / NT) k_window2(const WinArgs A) {
+  constexpr bool ADJ = (KIND == KIND_ADJ);
   constexpr int NW = NT / 32;
   constexpr int WB = 2 * NT;       // window blocks
   constexpr int LD = 2 * NT + 2;   // shared row stride in doubles (even: 16-byte pairs)
@@ -348,7 +353,7 @@ __global__ void __launch_bounds__(NT, (ADJ ? 768 : 512) / NT) k_window2(const Wi
   const int64_t row_lo = wlo * (int64_t)n;
   const int len = nwin * n - (has_last ? (n - nlast) : 0);
 
-  if constexpr (!ADJ) {
+  if constexpr (KIND == KIND_REG) {
     // 16-row blocks, all of full size, 16-byte aligned device memory: the register path
     if (A.bulk && A.mode == MODE_FULL && n == kRegRows && (!has_last || nlast == kRegRows) && !A.check_finite &&
         ((reinterpret_cast<uintptr_t>(A.F + (int64_t)blockIdx.y * A.ldf + off + row_lo) |

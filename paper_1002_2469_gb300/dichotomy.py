@@ -14,7 +14,7 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import (FLAG_ALLOW_NOT_DOMINANT, FLAG_CHECK_FINITE, FLAG_DEVICE_PRELIM, FLAG_FORCE_GENERAL, FLAG_HOST_PRELIM, PREC_AUTO, PREC_F64, PREC_MIXED, DichotomyError,
+from ._lib import (FLAG_ALLOW_NOT_DOMINANT, FLAG_CHECK_FINITE, FLAG_DEVICE_PRELIM, FLAG_FORCE_GENERAL, FLAG_HOST_PRELIM, FLAG_REG_PATH, FLAG_SMEM_PATH, PREC_AUTO, PREC_F64, PREC_MIXED, DichotomyError,
                    check, make_opts)
 
 __all__ = [
@@ -23,7 +23,7 @@ __all__ = [
     "dichotomy_batch_prepare", "dichotomy_batch_workspace_bytes", "dichotomy_batch_bind",
     "dichotomy_solve_batched", "dichotomy_adjoint_batched", "dichotomy_batch_status", "dichotomy_batch_info",
     "dichotomy_batch_destroy", "Plan", "Batch", "GenPlan", "solve", "DichotomySolve", "DichotomySolveQuasi", "DichotomySolveBatched", "DichotomySolveBatchedQuasi",
-    "PREC_F64", "PREC_MIXED", "PREC_AUTO", "FLAG_FORCE_GENERAL", "FLAG_CHECK_FINITE", "FLAG_HOST_PRELIM", "FLAG_DEVICE_PRELIM", "FLAG_ALLOW_NOT_DOMINANT", "DichotomyError",
+    "PREC_F64", "PREC_MIXED", "PREC_AUTO", "FLAG_FORCE_GENERAL", "FLAG_CHECK_FINITE", "FLAG_HOST_PRELIM", "FLAG_DEVICE_PRELIM", "FLAG_ALLOW_NOT_DOMINANT", "FLAG_REG_PATH", "FLAG_SMEM_PATH", "DichotomyError",
 ]
 
 

@@ -344,3 +344,12 @@ def test_toeplitz_without_dominance_needs_split_roots():
     assert plan((1.0, 1.0, 1.0), 16) == 2            # complex roots
     assert plan((-1.0, 1.0, -1.0), 16) == 2          # roots on one side of the unit circle
     assert plan((1.0, 0.0, 1.0), 16) == 2            # roots +-i
+
+
+def test_kernel_path_flags():
+    """The MIXED window kernel's register and shared-memory paths are chosen by flags: each alone
+    is accepted, both together are refused."""
+    t = (-1.2, 2.5, -0.8)
+    assert status_of(t, 100000, precision=1, flags=32) == 0
+    assert status_of(t, 100000, precision=1, flags=64) == 0
+    assert status_of(t, 100000, precision=1, flags=96) == 1

@@ -709,6 +709,35 @@ def test_autograd_quasi(D, corners):
     assert np.max(np.abs(c.grad.cpu().numpy() - g[3:])) <= TOL * np.max(np.abs(lam)) * np.max(np.abs(x.detach().cpu().numpy()))
 
 
+@pytest.mark.parametrize("flags", [0, 32, 64])
+def test_mixed_kernel_paths(D, flags):
+    """The MIXED form through the register path (flag 32), the shared-memory path (64) and the
+    library's choice (0): single plans of halo and one-window shape, a batch with one-window, halo,
+    ragged and one-row systems, and a series; all against the oracle."""
+    rng = np.random.default_rng(77 + flags)
+    for t, N in [((-1.2, 2.5, -0.8), 300001), ((-1.0, 4.0, -1.0), 4096), ((0.7, 2.5, -1.1), 4099),
+                 ((-1.0, 2.3, -1.0), 1 << 20)]:
+        F = rng.standard_normal(N)
+        x, info = gpu_solve(D, t, F, precision=1, flags=flags)
+        assert rel(x, oracle.thomas(t, F)) < TOL, (t, N, flags, info)
+    Ns = np.array([4096, 4096, 1, 70001, 4100, 300000, 16, 33], dtype=np.int64)
+    tm1, tp1 = -rng.uniform(0.5, 1.0, Ns.size), -rng.uniform(0.5, 1.0, Ns.size)
+    t0 = (np.abs(tm1) + np.abs(tp1)) * rng.uniform(1.05, 2.0, Ns.size)
+    off = np.concatenate([[0], np.cumsum(Ns)[:-1]])
+    F = rng.uniform(-1, 1, int(Ns.sum()))
+    b = D.Batch(Ns, tm1, t0, tp1, precision=1, flags=flags)
+    x = b.solve(torch.from_numpy(F).cuda()).cpu().numpy()
+    assert b.status() == 0
+    for s_ in range(Ns.size):
+        o, n = int(off[s_]), int(Ns[s_])
+        assert rel(x[o:o + n], oracle.thomas((tm1[s_], t0[s_], tp1[s_]), F[o:o + n])) < TOL, (s_, flags)
+    plan = D.Plan(-1.2, 2.5, -0.8, 70000, precision=1, flags=flags)
+    Fs = rng.standard_normal((3, 70000))
+    X = plan.solve_series(torch.from_numpy(Fs).cuda()).cpu().numpy()
+    for k in range(3):
+        assert rel(X[k], oracle.thomas((-1.2, 2.5, -0.8), Fs[k])) < TOL
+
+
 def test_autograd_with_cpu_coefficients(D):
     """Coefficients kept on the host (natural for three numbers): their gradients come back on the
     host, for the single, quasi-Toeplitz and batched Functions."""
