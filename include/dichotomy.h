@@ -251,6 +251,43 @@ void dichotomy_destroy(dich_plan_t plan);
 int dichotomy_solve_noalloc(double t_m1, double t_0, double t_1, int64_t N, const double* d_F, double* d_x,
                             void* stream);
 
+/* ---------------------------------------------------------------- one system in shards */
+
+/* The paper's distributed dichotomy process (Sec. 2.4-2.5: blocks spread over p processes, the
+ * interface values gathered by eq. 17-19's levels) for callers that split one system across
+ * devices or processes: shard k of nshards owns a contiguous range of whole windows of the plan
+ * (blocks [block_lo, block_hi), rows [row_lo, row_hi)) and holds only its own rows of F and x.
+ * Because the dichotomy tree's maps compose associatively (Sec. 2.5), the levels collapse into one
+ * exchange of four numbers per shard plus one value to each neighbour:
+ *   1. dichotomy_shard_reduce:  beta of the shard's blocks (eq. 16) and its block scan; returns
+ *      the shard's composite maps h_maps = (prefix a, b, suffix a, b) of eq. 15's two scans;
+ *   2. the caller all-gathers the 4 numbers of every shard (h_all_maps[4 nshards], in shard order);
+ *   3. dichotomy_shard_bounds:  folds the other shards' maps into the prefix entering the shard
+ *      and the suffix beyond it (on the device) and finishes its first/last values (eq. 18);
+ *      returns h_ends = (x at row_lo, x at row_hi - 1);
+ *   4. the caller passes each neighbour its boundary value: shard k receives
+ *      h_nbr = (h_ends[1] of shard k-1, h_ends[0] of shard k+1), zeros at the system's ends;
+ *   5. dichotomy_shard_finish:  the shard's interiors (eq. 7) into d_x.
+ * Any plan of N >= 2 rows without quasi-Toeplitz corners serves (its tables must be bound);
+ * nshards <= the plan's windows (dich_plan_info.tiles).  d_F, d_x: the shard's rows only, device,
+ * no aliasing (d_x also receives intermediate values between steps 1 and 5 in the FP64 form).
+ * d_ws: the shard's own device workspace of dich_shard_info.workspace_bytes (256-byte aligned),
+ * kept from step 1 to step 5.  Steps 1 and 3 synchronize `stream` (they return host values).
+ * Errors: DICH_ERR_ARG, DICH_ERR_ALIAS, DICH_ERR_UNBOUND, DICH_ERR_WORKSPACE, DICH_ERR_UNSUPPORTED
+ * (N < 2, corners), DICH_ERR_CUDA. */
+typedef struct {
+  int64_t row_lo, row_hi;      /* the shard's rows of the system */
+  int64_t block_lo, block_hi;  /* its blocks */
+  size_t workspace_bytes;      /* device workspace one shard needs */
+} dich_shard_info;
+int dichotomy_shard_info(dich_plan_t plan, int32_t nshards, int32_t k, dich_shard_info* info);
+int dichotomy_shard_reduce(dich_plan_t plan, int32_t nshards, int32_t k, const double* d_F, double* d_x,
+                           void* d_ws, size_t ws_bytes, double* h_maps, void* stream);
+int dichotomy_shard_bounds(dich_plan_t plan, int32_t nshards, int32_t k, const double* h_all_maps, void* d_ws,
+                           size_t ws_bytes, double* h_ends, void* stream);
+int dichotomy_shard_finish(dich_plan_t plan, int32_t nshards, int32_t k, const double* d_F, double* d_x,
+                           const double* h_nbr, void* d_ws, size_t ws_bytes, void* stream);
+
 /* ---------------------------------------------------------------- batches */
 
 /* A series of independent systems (the paper's eq. 2 series, or separation-of-variables

@@ -35,6 +35,7 @@ EXPORTS = [
     "dichotomy_batch_destroy", "dichotomy_strerror", "dichotomy_last_cuda_error", "dichotomy_version",
     "dichotomy_gen_plan", "dichotomy_gen_info", "dichotomy_gen_workspace_bytes", "dichotomy_gen_bind",
     "dichotomy_gen_solve", "dichotomy_gen_solve_series", "dichotomy_gen_residual", "dichotomy_gen_status", "dichotomy_gen_destroy",
+    "dichotomy_shard_info", "dichotomy_shard_reduce", "dichotomy_shard_bounds", "dichotomy_shard_finish",
 ]
 
 
@@ -61,6 +62,11 @@ class dich_plan_info(ctypes.Structure):
                 ("tiles", c_int64), ("Lv", c_int32), ("Lw", c_int32), ("kl", c_int32), ("kr", c_int32),
                 ("rs", c_double), ("ib", c_double), ("z", c_double), ("workspace_bytes", c_size_t),
                 ("beta_offset", c_size_t), ("iface_offset", c_size_t), ("growth", c_double)]
+
+
+class dich_shard_info(ctypes.Structure):
+    _fields_ = [("row_lo", c_int64), ("row_hi", c_int64), ("block_lo", c_int64), ("block_hi", c_int64),
+                ("workspace_bytes", c_size_t)]
 
 
 _lib_obj = None
@@ -123,6 +129,11 @@ def load(build_if_missing: bool = True):
             "dichotomy_gen_residual": ([P, P, P, ctypes.POINTER(c_double), P], I),
             "dichotomy_gen_status": ([P, P, ctypes.POINTER(I)], I),
             "dichotomy_gen_destroy": ([P], None),
+            "dichotomy_shard_info": ([P, c_int32, c_int32, ctypes.POINTER(dich_shard_info)], I),
+            "dichotomy_shard_reduce": ([P, c_int32, c_int32, P, P, P, c_size_t, ctypes.POINTER(c_double), P], I),
+            "dichotomy_shard_bounds": ([P, c_int32, c_int32, ctypes.POINTER(c_double), P, c_size_t,
+                                        ctypes.POINTER(c_double), P], I),
+            "dichotomy_shard_finish": ([P, c_int32, c_int32, P, P, ctypes.POINTER(c_double), P, c_size_t, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)

@@ -1042,6 +1042,169 @@ int dichotomy_status(dich_plan_t p, void* stream, int* device_status) {
 
 void dichotomy_destroy(dich_plan_t p) { delete p; }
 
+// ================================================================== sharded solve of one system
+// Shard k of nshards owns the windows [k T / S, (k + 1) T / S) of the plan (T windows of `own`
+// blocks, S shards): blocks [block_lo, block_hi), rows [row_lo, row_hi).  The shard runs the beta
+// pass and the block scan over its own blocks only; what crosses shards is the paper's exchange
+// between processes (Sec. 2.4-2.5, eq. 17-19, collapsed by associativity to one level): the four
+// numbers of each shard's composite prefix and suffix maps, then one boundary value to each
+// neighbour.  Workspace of one shard (caller-owned, 256-byte aligned): totals [4], every shard's
+// totals [4 S], beta [2 nb], first/last values with one neighbour entry on each side [2 (nb + 2)],
+// scan scratch [6 chunks].
+namespace {
+struct ShardGeo {
+  int64_t w_lo, w_hi, block_lo, block_hi, row_lo, row_hi, nb, nch;
+  size_t off_tot, off_maps, off_beta, off_iface, off_scan, bytes;
+};
+int shard_geo(dich_plan_t p, int32_t nshards, int32_t k, ShardGeo& g) {
+  if (!p || nshards < 1 || k < 0 || k >= nshards) return DICH_ERR_ARG;
+  if (p->N < 2 || p->quasi) return DICH_ERR_UNSUPPORTED;
+  const SysPlan& r = p->fwd.rec;
+  const int64_t own = r.own, P = r.P, T = ceil_div(P, own);
+  if (nshards > T) return DICH_ERR_ARG;
+  g.w_lo = (int64_t)k * T / nshards;
+  g.w_hi = (int64_t)(k + 1) * T / nshards;
+  g.block_lo = g.w_lo * own;
+  g.block_hi = std::min<int64_t>(P, g.w_hi * own);
+  g.row_lo = g.block_lo * r.n;
+  g.row_hi = std::min<int64_t>(p->N, g.block_hi * r.n);
+  g.nb = g.block_hi - g.block_lo;
+  g.nch = ceil_div(g.nb, kScanChunk);
+  size_t o = 0;
+  g.off_tot = o;
+  o = align_up(o + sizeof(double) * 4);
+  g.off_maps = o;
+  o = align_up(o + sizeof(double) * 4 * (size_t)nshards);
+  g.off_beta = o;
+  o = align_up(o + sizeof(double) * 2 * (size_t)g.nb);
+  g.off_iface = o;
+  o = align_up(o + sizeof(double) * 2 * (size_t)(g.nb + 2));
+  g.off_scan = o;
+  o = align_up(o + sizeof(double) * 6 * (size_t)g.nch);
+  g.bytes = o;
+  return DICH_OK;
+}
+int shard_check(dich_plan_t p, const ShardGeo& g, const void* d_ws, size_t ws_bytes) {
+  if (!p->d_ws) return DICH_ERR_UNBOUND;
+  if (!d_ws || ((uintptr_t)d_ws & (kAlign - 1)) != 0 || ws_bytes < g.bytes) return DICH_ERR_WORKSPACE;
+  if (!is_device_ptr(d_ws)) return DICH_ERR_ARG;
+  return DICH_OK;
+}
+// the shard's windows in one mode (beta pass or apply pass); F and x hold the shard's rows only
+cudaError_t shard_windows(dich_plan_t p, const ShardGeo& g, int mode, const double* d_F, double* d_x, double* beta,
+                          const double* iface, cudaStream_t st) {
+  WinArgs a{};
+  a.plans = (const SysPlan*)(p->d_ws + p->off_plans);
+  a.tabs = (const double*)(p->d_ws + p->off_tabs);
+  a.F = d_F - g.row_lo;   // the kernels index rows of the whole system
+  a.x = d_x - g.row_lo;
+  a.status = (unsigned*)(p->d_ws + p->off_status);
+  a.mode = mode;
+  a.beta = beta;
+  a.iface = iface;
+  a.check_finite = (p->opts.flags & DICH_FLAG_CHECK_FINITE) ? 1 : 0;
+  a.n_smem = p->n_smem;
+  a.win0 = g.w_lo;
+  const int grid = (int)(g.w_hi - g.w_lo);
+  const size_t smem = smem_bytes(p->NT, p->n_smem, p->form);
+  return p->form == FORM_F64 ? launch_window_f64(p->NT, grid, smem, st, a, 1)
+                             : launch_window_mixed(p->NT, grid, smem, st, a, 1);
+}
+}  // namespace
+
+int dichotomy_shard_info(dich_plan_t p, int32_t nshards, int32_t k, dich_shard_info* info) {
+  if (!info) return DICH_ERR_ARG;
+  ShardGeo g;
+  const int rc = shard_geo(p, nshards, k, g);
+  if (rc) return rc;
+  info->row_lo = g.row_lo;
+  info->row_hi = g.row_hi;
+  info->block_lo = g.block_lo;
+  info->block_hi = g.block_hi;
+  info->workspace_bytes = g.bytes;
+  return DICH_OK;
+}
+
+int dichotomy_shard_reduce(dich_plan_t p, int32_t nshards, int32_t k, const double* d_F, double* d_x, void* d_ws,
+                           size_t ws_bytes, double* h_maps, void* stream) {
+  ShardGeo g;
+  int rc = shard_geo(p, nshards, k, g);
+  if (rc) return rc;
+  if ((rc = shard_check(p, g, d_ws, ws_bytes))) return rc;
+  if (!h_maps || !d_F || !d_x || !aligned8(d_F) || !aligned8(d_x)) return DICH_ERR_ARG;
+  const size_t nr = sizeof(double) * (size_t)(g.row_hi - g.row_lo);
+  if (overlap(d_F, nr, d_x, nr)) return DICH_ERR_ALIAS;
+  if (!is_device_ptr(d_F) || !is_device_ptr(d_x)) return DICH_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = (char*)d_ws;
+  double* beta = (double*)(w + g.off_beta);
+  // beta of the shard's blocks (eq. 16); the kernels index blocks of the whole system
+  cudaError_t e = shard_windows(p, g, MODE_BETA, d_F, d_x, beta - 2 * g.block_lo, nullptr, st);
+  ScanMap m{};
+  m.mbase = g.block_lo;
+  m.mend = g.block_hi;
+  m.shard = k;
+  m.nshards = nshards;
+  m.tot = (double*)(w + g.off_tot);
+  if (e == cudaSuccess)
+    e = launch_shard_scan_reduce((const SysPlan*)(p->d_ws + p->off_plans), (const double*)(p->d_ws + p->off_tabs), m,
+                                 beta - 2 * g.block_lo, (double*)(w + g.off_scan), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_maps, w + g.off_tot, sizeof(double) * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? DICH_OK : cuda_fail(e);
+}
+
+int dichotomy_shard_bounds(dich_plan_t p, int32_t nshards, int32_t k, const double* h_all_maps, void* d_ws,
+                           size_t ws_bytes, double* h_ends, void* stream) {
+  ShardGeo g;
+  int rc = shard_geo(p, nshards, k, g);
+  if (rc) return rc;
+  if ((rc = shard_check(p, g, d_ws, ws_bytes))) return rc;
+  if (!h_all_maps || !h_ends) return DICH_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = (char*)d_ws;
+  double* maps = (double*)(w + g.off_maps);
+  double* iface = (double*)(w + g.off_iface);
+  cudaError_t e = cudaMemcpyAsync(maps, h_all_maps, sizeof(double) * 4 * (size_t)nshards, cudaMemcpyHostToDevice, st);
+  ScanMap m{};
+  m.mbase = g.block_lo;
+  m.mend = g.block_hi;
+  m.maps = maps;
+  m.shard = k;
+  m.nshards = nshards;
+  double* beta = (double*)(w + g.off_beta);
+  if (e == cudaSuccess)
+    e = launch_shard_scan_apply((const SysPlan*)(p->d_ws + p->off_plans), (const double*)(p->d_ws + p->off_tabs), m,
+                                beta - 2 * g.block_lo, iface - 2 * (g.block_lo - 1), (double*)(w + g.off_scan), st);
+  // x at the shard's first row (x_s of its first block) and last row (x_e of its last block)
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_ends, iface + 2, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h_ends + 1, iface + 2 * g.nb + 1, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? DICH_OK : cuda_fail(e);
+}
+
+int dichotomy_shard_finish(dich_plan_t p, int32_t nshards, int32_t k, const double* d_F, double* d_x,
+                           const double* h_nbr, void* d_ws, size_t ws_bytes, void* stream) {
+  ShardGeo g;
+  int rc = shard_geo(p, nshards, k, g);
+  if (rc) return rc;
+  if ((rc = shard_check(p, g, d_ws, ws_bytes))) return rc;
+  if (!h_nbr || !d_F || !d_x || !aligned8(d_F) || !aligned8(d_x)) return DICH_ERR_ARG;
+  const size_t nr = sizeof(double) * (size_t)(g.row_hi - g.row_lo);
+  if (overlap(d_F, nr, d_x, nr)) return DICH_ERR_ALIAS;
+  if (!is_device_ptr(d_F) || !is_device_ptr(d_x)) return DICH_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = (char*)d_ws;
+  double* iface = (double*)(w + g.off_iface);
+  // the neighbours' boundary values: x_e of the block before the shard, x_s of the block after it
+  cudaError_t e = cudaMemcpyAsync(iface + 1, h_nbr, sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(iface + 2 * (g.nb + 1), h_nbr + 1, sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = shard_windows(p, g, MODE_APPLY, d_F, d_x, nullptr, iface - 2 * (g.block_lo - 1), st);
+  return e == cudaSuccess ? DICH_OK : cuda_fail(e);
+}
+
 }  // extern "C"
 
 // ================================================================== batches

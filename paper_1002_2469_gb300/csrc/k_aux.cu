@@ -125,9 +125,10 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan_reduce(const SysPlan* pl
   const SysPlan* pp = chunk_system(plans, map, blockIdx.x, lc);
   const double* tab = tabs + pp->tab;
   const double* beta = beta_base + 2 * pp->gboff;
-  const int64_t m_first = lc * kScanChunk + (int64_t)threadIdx.x * kScanPer;
+  const int64_t mb = map.cmap ? 0 : map.mbase, me = (map.cmap || map.mend == 0) ? pp->P : map.mend;
+  const int64_t m_first = mb + lc * kScanChunk + (int64_t)threadIdx.x * kScanPer;
   double pa, pb, sa, sb, ea, eb;
-  thread_maps(pp, tab, pp->P, beta, m_first, pa, pb, sa, sb);
+  thread_maps(pp, tab, me, beta, m_first, pa, pb, sa, sb);
   cta_prefix<kScanThreads>(pa, pb, ea, eb, sh);
   cta_suffix<kScanThreads>(sa, sb, ea, eb, sh);
   if (threadIdx.x == kScanThreads - 1) {
@@ -146,12 +147,26 @@ __global__ void __launch_bounds__(1024) k_bscan_top(const SysPlan* plans, ScanMa
                                                     double* carry) {
   __shared__ double sh[4 * 1024 / 32];
   __shared__ double run;
+  __shared__ double cin[2], runa;
   const SysPlan* pp = map.cmap ? plans + map.sys[blockIdx.x] : plans;
   const int64_t cbase = map.cmap ? map.c0[blockIdx.x] : 0;
-  const int64_t nchunks = (pp->P + kScanChunk - 1) / kScanChunk;
+  const int64_t nb = (map.cmap || map.mend == 0) ? pp->P : map.mend - map.mbase;
+  const int64_t nchunks = (nb + kScanChunk - 1) / kScanChunk;
   const double* ag = agg + 4 * cbase;
   double* ca = carry + 2 * cbase;
-  if (threadIdx.x == 0) run = 0.0;
+  if (threadIdx.x == 0) {
+    // a shard: the prefix entering it composes the totals of the shards before it (the paper's
+    // dichotomy levels across processes, eq. 17-19, in one fold), the suffix those after it
+    double A = 0.0, B = 0.0;
+    if (!map.cmap && map.maps) {
+      for (int j = 0; j < map.shard; ++j) A = fma(map.maps[4 * j], A, map.maps[4 * j + 1]);
+      for (int j = map.nshards - 1; j > map.shard; --j) B = fma(map.maps[4 * j + 2], B, map.maps[4 * j + 3]);
+    }
+    cin[0] = A;
+    cin[1] = B;
+    run = A;
+    runa = 1.0;
+  }
   __syncthreads();
   for (int64_t g0 = 0; g0 < nchunks; g0 += 1024) {
     const int64_t c = g0 + threadIdx.x;
@@ -164,10 +179,20 @@ __global__ void __launch_bounds__(1024) k_bscan_top(const SysPlan* plans, ScanMa
     const double r = run;
     if (c < nchunks) ca[2 * c] = fma(ea, r, eb);
     __syncthreads();
-    if (threadIdx.x == 1023) run = fma(ia, r, ib);
+    if (threadIdx.x == 1023) {
+      run = fma(ia, r, ib);
+      runa *= ia;
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) run = 0.0;
+  if (threadIdx.x == 0) {
+    if (!map.cmap && map.tot) {   // the shard's prefix total map (zero carry-in: run is its b part)
+      map.tot[0] = runa;
+      map.tot[1] = run;
+    }
+    run = cin[1];
+    runa = 1.0;
+  }
   __syncthreads();
   const int64_t ngroups = (nchunks + 1023) / 1024;
   for (int64_t g = ngroups - 1; g >= 0; --g) {
@@ -181,8 +206,15 @@ __global__ void __launch_bounds__(1024) k_bscan_top(const SysPlan* plans, ScanMa
     const double r = run;
     if (c < nchunks) ca[2 * c + 1] = fma(ea, r, eb);
     __syncthreads();
-    if (threadIdx.x == 0) run = fma(ia, r, ib);
+    if (threadIdx.x == 0) {
+      run = fma(ia, r, ib);
+      runa *= ia;
+    }
     __syncthreads();
+  }
+  if (threadIdx.x == 0 && !map.cmap && map.tot) {
+    map.tot[2] = runa;
+    map.tot[3] = run;
   }
 }
 
@@ -192,11 +224,11 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan_apply(const SysPlan* pla
   __shared__ double sh[4 * kScanThreads / 32];
   int64_t lc;
   const SysPlan* pp = chunk_system(plans, map, blockIdx.x, lc);
-  const int64_t P = pp->P;
+  const int64_t P = (map.cmap || map.mend == 0) ? pp->P : map.mend;   // end of the scanned blocks
   const double* tab = tabs + pp->tab;
   const double* beta = beta_base + 2 * pp->gboff;
   double* iface = iface_base + 2 * pp->gboff;
-  const int64_t m_first = lc * kScanChunk + (int64_t)threadIdx.x * kScanPer;
+  const int64_t m_first = (map.cmap ? 0 : map.mbase) + lc * kScanChunk + (int64_t)threadIdx.x * kScanPer;
   double pa, pb, sa, sb, ea, eb, fa, fb;
   thread_maps(pp, tab, P, beta, m_first, pa, pb, sa, sb);
   cta_prefix<kScanThreads>(pa, pb, ea, eb, sh);
@@ -235,6 +267,28 @@ cudaError_t launch_block_scan(const SysPlan* plan, const double* tabs, int64_t P
                               double* iface, double* scratch, cudaStream_t st) {
   const int64_t nchunks = (P + kScanChunk - 1) / kScanChunk;
   return launch_block_scan_batched(plan, tabs, ScanMap{}, nchunks, 1, beta, iface, scratch, st);
+}
+
+cudaError_t launch_shard_scan_reduce(const SysPlan* plan, const double* tabs, const ScanMap& map, const double* beta,
+                                     double* scratch, cudaStream_t st) {
+  const int64_t nchunks = (map.mend - map.mbase + kScanChunk - 1) / kScanChunk;
+  if (nchunks <= 0) return cudaErrorInvalidValue;
+  ScanMap m = map;
+  m.maps = nullptr;   // totals with zero carry-ins
+  k_bscan_reduce<<<(unsigned)nchunks, kScanThreads, 0, st>>>(plan, tabs, m, beta, scratch);
+  k_bscan_top<<<1, 1024, 0, st>>>(plan, m, scratch, scratch + 4 * nchunks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shard_scan_apply(const SysPlan* plan, const double* tabs, const ScanMap& map, const double* beta,
+                                    double* iface, double* scratch, cudaStream_t st) {
+  const int64_t nchunks = (map.mend - map.mbase + kScanChunk - 1) / kScanChunk;
+  if (nchunks <= 0) return cudaErrorInvalidValue;
+  ScanMap m = map;
+  m.tot = nullptr;
+  k_bscan_top<<<1, 1024, 0, st>>>(plan, m, scratch, scratch + 4 * nchunks);
+  k_bscan_apply<<<(unsigned)nchunks, kScanThreads, 0, st>>>(plan, tabs, m, beta, scratch + 4 * nchunks, iface);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_block_scan_batched(const SysPlan* plans, const double* tabs, const ScanMap& map, int64_t nchunks,

@@ -27,11 +27,25 @@ struct ScanMap {
   const int32_t* cmap;
   const int32_t* sys;
   const int64_t* c0;
+  // single system (cmap null): the scan covers blocks [mbase, mend) (mend 0: the whole system).
+  // A shard of a sharded solve passes its block range, `maps` = every shard's totals (4 doubles per
+  // shard: prefix a, b, suffix a, b) with its index `shard` (the carry-ins are folded from them), and
+  // or `tot` = where its own totals go (4 doubles); null maps: zero coupling enters at both ends.
+  int64_t mbase, mend;
+  const double* maps;
+  int32_t shard, nshards;
+  double* tot;
 };
 //   scratch: 6 doubles per chunk; nsys systems, nchunks chunks in all
 cudaError_t launch_block_scan_batched(const SysPlan* plans, const double* tabs, const ScanMap& map, int64_t nchunks,
                                       int64_t nsys, const double* beta, double* iface, double* scratch,
                                       cudaStream_t st);
+// a shard's block scan in two halves: reduce (chunk aggregates and the shard's totals into map.tot,
+// zero carry-ins), then apply (carry-ins folded from map.maps, first/last values into iface)
+cudaError_t launch_shard_scan_reduce(const SysPlan* plan, const double* tabs, const ScanMap& map, const double* beta,
+                                     double* scratch, cudaStream_t st);
+cudaError_t launch_shard_scan_apply(const SysPlan* plan, const double* tabs, const ScanMap& map, const double* beta,
+                                    double* iface, double* scratch, cudaStream_t st);
 
 // adjoint: gt[3 s + j] = -(sum of part[3 i + j] over the CTAs i of system s), fixed order.
 //   For k = 0..nsys-1: s = sys_ids[k], CTAs first[k] .. first[k] + count[k] - 1 (device
