@@ -3,8 +3,9 @@
 
 namespace dich {
 
-// KIND: the adjoint's instantiation (gradient sums in the store loop) when a.xf is set, else the
-// register-path one when a.bulk allows bulk copies, else the shared-memory one (six CTAs per SM)
+// KIND: the adjoint's instantiations (gradient sums in the store loop) when a.xf is set, else the
+// forward ones; the register-path kind when a.bulk allows bulk copies, else the shared-memory one
+// (six CTAs per SM)
 template <int NT, int KIND>
 static cudaError_t launch_one(int grid, int grid_y, size_t smem, cudaStream_t st, const WinArgs& a) {
   if (smem > 48 * 1024) {
@@ -27,7 +28,8 @@ static cudaError_t launch_one(int grid, int grid_y, size_t smem, cudaStream_t st
 
 template <int NT>
 static cudaError_t launch_kind(int grid, int grid_y, size_t smem, cudaStream_t st, const WinArgs& a) {
-  if (a.xf != nullptr) return launch_one<NT, KIND_ADJ>(grid, grid_y, smem, st, a);
+  if (a.xf != nullptr)
+    return a.bulk ? launch_one<NT, KIND_REGADJ>(grid, grid_y, smem, st, a) : launch_one<NT, KIND_ADJ>(grid, grid_y, smem, st, a);
   if (a.bulk) return launch_one<NT, KIND_REG>(grid, grid_y, smem, st, a);
   return launch_one<NT, KIND_SMEM>(grid, grid_y, smem, st, a);
 }

@@ -294,11 +294,13 @@ __host__ __device__ inline size_t window2_smem_bytes(int NT, int n_smem) {
 // 128 registers: four CTAs of 128 threads per SM); KIND_SMEM -- the forward solve on the shared-memory
 // path only (80 registers: six CTAs per SM, for launches of many short, latency-bound windows);
 // KIND_ADJ -- the adjoint (shared-memory path, gradient sums in the store loop, six CTAs per SM).
-enum WinKind : int { KIND_REG = 0, KIND_ADJ = 1, KIND_SMEM = 2 };
+// KIND_REGADJ -- the adjoint with the register path for the windows it serves (four CTAs per SM).
+enum WinKind : int { KIND_REG = 0, KIND_ADJ = 1, KIND_SMEM = 2, KIND_REGADJ = 3 };
 
 template <int NT, int KIND>
-__global__ void __launch_bounds__(NT, (KIND == KIND_REG ? 512 : 768) / NT) k_window2(const WinArgs A) {
-  constexpr bool ADJ = (KIND == KIND_ADJ);
+__global__ void __launch_bounds__(NT, ((KIND == KIND_REG || KIND == KIND_REGADJ) ? 512 : 768) / NT)
+    k_window2(const WinArgs A) {
+  constexpr bool ADJ = (KIND == KIND_ADJ || KIND == KIND_REGADJ);
   constexpr int NW = NT / 32;
   constexpr int WB = 2 * NT;       // window blocks
   constexpr int LD = 2 * NT + 2;   // shared row stride in doubles (even: 16-byte pairs)
@@ -353,12 +355,13 @@ __global__ void __launch_bounds__(NT, (KIND == KIND_REG ? 512 : 768) / NT) k_win
   const int64_t row_lo = wlo * (int64_t)n;
   const int len = nwin * n - (has_last ? (n - nlast) : 0);
 
-  if constexpr (KIND == KIND_REG) {
+  if constexpr (KIND == KIND_REG || KIND == KIND_REGADJ) {
     // 16-row blocks, all of full size, 16-byte aligned device memory: the register path
     if (A.bulk && A.mode == MODE_FULL && n == kRegRows && (!has_last || nlast == kRegRows) && !A.check_finite &&
         ((reinterpret_cast<uintptr_t>(A.F + (int64_t)blockIdx.y * A.ldf + off + row_lo) |
-          reinterpret_cast<uintptr_t>(A.x + (int64_t)blockIdx.y * A.ldx + off + row_lo)) & 15u) == 0u) {
-      window_reg<NT>(A, pp, tab, P, wlo, nwin, hl, nown, row_lo, reinterpret_cast<unsigned char*>(sm));
+          reinterpret_cast<uintptr_t>(A.x + (int64_t)blockIdx.y * A.ldx + off + row_lo) |
+          (ADJ ? reinterpret_cast<uintptr_t>(A.xf + off + row_lo) : (uintptr_t)0)) & 15u) == 0u) {
+      window_reg<NT, ADJ>(A, pp, tab, P, wlo, nwin, hl, nown, row_lo, reinterpret_cast<unsigned char*>(sm));
       return;
     }
   }

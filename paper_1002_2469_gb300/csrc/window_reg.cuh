@@ -31,11 +31,12 @@ constexpr int kRegRows = 16;                            // block size of the reg
 constexpr int kRegPairBytes = 2 * kRegRows * 8 + 16;    // a thread's two blocks + 16 bytes of padding
 
 // shared memory of the register path for NT threads: the pair slots, the two spike tables, the
-// first/last values of the window's blocks, the scan scratch, the exponent maxima and the mbarrier
+// first/last values of the window's blocks, the scan scratch, the exponent maxima (of the right-hand
+// side and, for the adjoint, of the forward solution) and the mbarrier
 __host__ __device__ inline size_t window_reg_smem_bytes(int NT) {
   const size_t nw = (size_t)(NT / 32);
   return (size_t)NT * kRegPairBytes + 2 * 16 * (size_t)kRegRows + 2 * 8 * 2 * (size_t)NT + 8 * 4 * nw +
-         4 * 2 * nw + 16;
+         4 * 4 * nw + 16;
 }
 
 // ---------------------------------------------------------------- mbarrier and bulk copies (PTX)
@@ -171,7 +172,12 @@ __device__ __forceinline__ void tree_mid(const float2* tf, const SysPlan* pp, in
 // thread for a while); running out latches ST_TIMEOUT and the CTA returns without a store.
 constexpr int kBulkWaitIters = 1 << 22;
 
-template <int NT>
+// ADJ: the adjoint (a5) -- A.F is w, the plan the transposed one, A.x receives lambda, and the
+// gradient sums -(sum lambda_r x_{r-1}, sum lambda_r x_r, sum lambda_r x_{r+1}) over the window's own
+// rows go to A.part (three per CTA).  The forward solution x (A.xf) comes into the pair slots by a
+// second bulk copy as soon as w has moved to registers, and is read back row by row as lambda is
+// written over it.
+template <int NT, bool ADJ = false>
 __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, const double* tab, int64_t P,
                                            int64_t wlo, int nwin, int hl, int nown, int64_t row_lo,
                                            unsigned char* smem) {
@@ -185,7 +191,8 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
   ffv* sxe = sxs + 2 * NT;
   ffv* swv = sxe + 2 * NT;                                                       // 4 NW scan scratch
   unsigned* sexp = reinterpret_cast<unsigned*>(swv + 4 * NW);                    // 2 NW exponent maxima
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sexp + 2 * NW);
+  unsigned* sexpx = sexp + 2 * NW;                                               // the same for x
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sexpx + 2 * NW);
 
   const int b0 = 2 * tid, b1 = b0 + 1;
   const bool act0 = b0 < nwin, act1 = b1 < nwin;
@@ -265,6 +272,12 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     const int emax = (int)(hmax >> 20), emin = (int)(hmin >> 20);
     wscale = (emax == 2047) ? 0 : ((emax == 0) ? 1000 : max(-1000, min(1000, (1023 + 16) - emax)));
     fast = (emin >= 1) && (emax >= 239) && (emax <= 1935) && (emax - emin <= 119);
+  }
+  if constexpr (ADJ) {
+    // the slot's values are in registers: it now takes the forward solution x (mbarrier phase 1)
+    fence_async_smem();
+    if (tid == 0) mbar_arrive_expect_tx(bar, (unsigned)(nwin * R * 8));
+    if (mybytes) bulk_load(mine, A.xf + pp->off + row_lo + (int64_t)b0 * R, mybytes, bar);
   }
 
   // fast windows: the FP64 multiplier of the join, G = g 2^(896 - wscale), folds the rebias of the
@@ -349,7 +362,7 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     // ------------------------------------------------------------ correction (a3), join, store
     const bool own0 = act0 && b0 >= hl && b0 < hl + nown;
     const bool own1 = act1 && b1 >= hl && b1 < hl + nown;
-    if (!(own0 || own1)) return;
+    if (!ADJ && !(own0 || own1)) return;
     // x = xp + (x_{s-1} - xp(-1)) v + x_{e+1} w, in units of X (x = g X): the coefficients are
     // x_{s-1} / g - ib X_0 and x_{e+1} / g, with 1/g = -q
     const ff2 qv = ff2_bcast(ffv{pp->q_h, pp->q_l});
@@ -358,16 +371,105 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     const ff2 cR = ff2_mul(ff2_pair(XR0, XR1), qv);
     const float2 gh = f2(pp->g_h), glo = f2(pp->g_l);
     const double gd = pp->g;
+
+    // the adjoint: x in the slots, its own power-of-two scale, the neighbours' boundary rows
+    int xsc = 0;
+    bool xfast = false;
+    double xlb = 0.0, xrb = 0.0;
+    if constexpr (ADJ) {
+      bool got = false;
+      for (int it = 0; it < kBulkWaitIters && !got; ++it) got = mbar_try_wait(bar, 1u);
+      if (!__syncthreads_and(got)) {
+        if (tid == 0) atomicOr(A.status, (unsigned)ST_TIMEOUT);
+        return;
+      }
+      unsigned hmax = 0u, hmin = 0xFFFFFFFFu;
+#pragma unroll
+      for (int k = 0; k < R / 2; ++k) {
+        if (act0) {
+          const uint4 q = *reinterpret_cast<const uint4*>(mine + 16 * k);
+          hmax = __vimax3_u32(hmax, q.y & 0x7FFFFFFFu, q.w & 0x7FFFFFFFu);
+          hmin = __vimin3_u32(hmin, q.y & 0x7FFFFFFFu, q.w & 0x7FFFFFFFu);
+        }
+        if (act1) {
+          const uint4 q = *reinterpret_cast<const uint4*>(mine + 8 * R + 16 * k);
+          hmax = __vimax3_u32(hmax, q.y & 0x7FFFFFFFu, q.w & 0x7FFFFFFFu);
+          hmin = __vimin3_u32(hmin, q.y & 0x7FFFFFFFu, q.w & 0x7FFFFFFFu);
+        }
+      }
+      hmax = __reduce_max_sync(0xffffffffu, hmax);
+      hmin = __reduce_min_sync(0xffffffffu, hmin);
+      if (lane == 0) {
+        sexpx[wid] = hmax;
+        sexpx[NW + wid] = hmin;
+      }
+      // rows beyond the window's loaded blocks are the system's ends there (x = 0), or belong to halo
+      // blocks, which contribute no sums
+      if (act0 && b0 > 0) xlb = *reinterpret_cast<const double*>(mine - kRegPairBytes + 8 * (2 * R - 1));
+      if (b1 + 1 < nwin) xrb = *reinterpret_cast<const double*>(mine + kRegPairBytes);
+      __syncthreads();   // every thread holds its neighbours' rows before any slot takes lambda
+      hmax = sexpx[0];
+      hmin = sexpx[NW];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) {
+        hmax = max(hmax, sexpx[w]);
+        hmin = min(hmin, sexpx[NW + w]);
+      }
+      const int emax = (int)(hmax >> 20), emin = (int)(hmin >> 20);
+      xsc = (emax == 2047) ? 0 : ((emax == 0) ? 1000 : max(-1000, min(1000, (1023 + 16) - emax)));
+      xfast = (emin >= 1) && (emax >= 239) && (emax <= 1935) && (emax - emin <= 119);
+    }
+    const FastK fkx = fast_k(xsc);
+    // the gradient sums of the thread's rows, lane x block 2t, lane y block 2t+1: float-float
+    // (units 2^(wscale + xscale) / g) in windows whose x is fast, else FP64
+    float2 smh = f2(0.f), sml = f2(0.f), s0h = f2(0.f), s0l = f2(0.f), sph = f2(0.f), spl = f2(0.f);
+    double dm0 = 0.0, dm1 = 0.0, d00 = 0.0, d01 = 0.0, dp0 = 0.0, dp1 = 0.0;
+    // x rows as float-float pairs (lane x block 2t, lane y block 2t+1).  In a fast x window every value
+    // of the active blocks is normal; only the markers of the system's ends (x_{-1} = x_N = 0) can be
+    // zero, and Z says where they may occur: they become (0, 0)
+    auto xsplit = [&](double u0, double u1, float2& hh, float2& ll, bool Z) {
+      split_fast(u0, fkx, hh.x, ll.x);
+      split_fast(u1, fkx, hh.y, ll.y);
+      if (Z) {
+        if ((__double2hiint(u0) & 0x7FF00000) == 0) hh.x = ll.x = 0.f;
+        if ((__double2hiint(u1) & 0x7FF00000) == 0) hh.y = ll.y = 0.f;
+      }
+    };
+    float2 xph = f2(0.f), xpl = f2(0.f), xch = f2(0.f), xcl = f2(0.f);   // x_{r-1}, x_r split
+    double2 xa{0.0, 0.0}, xb{0.0, 0.0};   // x rows 2k, 2k+1 of both blocks (pair k)
+    double x0e = 0.0, x1s = 0.0;          // block 2t's last row, block 2t+1's first row
+    double2 xprev{0.0, 0.0};              // x of the row before the current pair, both lanes
+    if constexpr (ADJ) {
+      if (act0) xa = *reinterpret_cast<const double2*>(mine);
+      if (act1) xb = *reinterpret_cast<const double2*>(mine + 8 * R);
+      if (act0) x0e = *reinterpret_cast<const double*>(mine + 8 * (R - 1));
+      x1s = xb.x;
+      xprev = make_double2(xlb, x0e);
+      if (xfast) {
+        xsplit(xprev.x, xprev.y, xph, xpl, true);
+        xsplit(xa.x, xb.x, xch, xcl, false);
+      }
+    }
+
 #pragma unroll
     for (int k = 0; k < R / 2; ++k) {
       double o0[2], o1[2];
+      double2 na{0.0, 0.0}, nb2{0.0, 0.0};   // the next pair (x of rows 2k+2, 2k+3), read before the
+      if constexpr (ADJ) {                   // slot's rows 2k, 2k+1 take lambda
+        if (k + 1 < R / 2) {
+          if (act0) na = *reinterpret_cast<const double2*>(mine + 16 * (k + 1));
+          if (act1) nb2 = *reinterpret_cast<const double2*>(mine + 8 * R + 16 * (k + 1));
+        }
+      }
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int i = 2 * k + j;
         float2 xh = H[i], xl = L[i];
-        const float4 v = tv4[i], w = tw4[R - 1 - i];
-        ff_fma_acc2(cL.h, cL.l, make_float2(v.x, v.y), make_float2(v.z, v.w), xh, xl);
-        ff_fma_acc2(cR.h, cR.l, make_float2(w.x, w.y), make_float2(w.z, w.w), xh, xl);
+        if (own0 || own1) {
+          const float4 v = tv4[i], w = tw4[R - 1 - i];
+          ff_fma_acc2(cL.h, cL.l, make_float2(v.x, v.y), make_float2(v.z, v.w), xh, xl);
+          ff_fma_acc2(cR.h, cR.l, make_float2(w.x, w.y), make_float2(w.z, w.w), xh, xl);
+        }
         if (FAST && GFOLD) {
           // x = g (hi + lo) 2^-wscale = G (hi 2^-896) + (g lo) 2^-wscale: both parts rebuilt as FP64
           // bit patterns (the leading one without rebias), one FMA
@@ -384,19 +486,99 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
           o0[j] = join_dadd(yh.x, yl.x, wscale);
           o1[j] = join_dadd(yh.y, yl.y, wscale);
         }
+        if constexpr (ADJ) {
+          // x_{r-1}, x_r, x_{r+1} of row i in both blocks
+          const double2 xc = (j == 0) ? make_double2(xa.x, xb.x) : make_double2(xa.y, xb.y);
+          double2 xn;
+          if (j == 0)
+            xn = make_double2(xa.y, xb.y);
+          else if (k + 1 < R / 2)
+            xn = make_double2(na.x, nb2.x);
+          else
+            xn = make_double2(x1s, xrb);
+          if (xfast) {
+            float2 nh, nl;
+            xsplit(xn.x, xn.y, nh, nl, i == R - 1);
+            ff_fma_acc2(xh, xl, xph, xpl, smh, sml);
+            ff_fma_acc2(xh, xl, xch, xcl, s0h, s0l);
+            ff_fma_acc2(xh, xl, nh, nl, sph, spl);
+            xph = xch;
+            xpl = xcl;
+            xch = nh;
+            xcl = nl;
+          } else {
+            dm0 = fma(o0[j], xprev.x, dm0);
+            dm1 = fma(o1[j], xprev.y, dm1);
+            d00 = fma(o0[j], xc.x, d00);
+            d01 = fma(o1[j], xc.y, d01);
+            dp0 = fma(o0[j], xn.x, dp0);
+            dp1 = fma(o1[j], xn.y, dp1);
+          }
+          xprev = xc;
+        }
       }
-      *reinterpret_cast<double2*>(mine + 16 * k) = make_double2(o0[0], o0[1]);
-      *reinterpret_cast<double2*>(mine + 8 * R + 16 * k) = make_double2(o1[0], o1[1]);
+      if (own0 || own1) {
+        *reinterpret_cast<double2*>(mine + 16 * k) = make_double2(o0[0], o0[1]);
+        *reinterpret_cast<double2*>(mine + 8 * R + 16 * k) = make_double2(o1[0], o1[1]);
+      }
+      if constexpr (ADJ) {
+        xa = na;
+        xb = nb2;
+      }
     }
-    fence_async_smem();
-    if (own0 && own1)
-      bulk_store(dst + (int64_t)b0 * R, mine, 2u * R * 8u);
-    else if (own0)
-      bulk_store(dst + (int64_t)b0 * R, mine, R * 8u);
-    else
-      bulk_store(dst + (int64_t)b1 * R, mine + 8 * R, R * 8u);
-    bulk_commit();
-    bulk_wait_read();
+    if (own0 || own1) {
+      fence_async_smem();
+      if (own0 && own1)
+        bulk_store(dst + (int64_t)b0 * R, mine, 2u * R * 8u);
+      else if (own0)
+        bulk_store(dst + (int64_t)b0 * R, mine, R * 8u);
+      else
+        bulk_store(dst + (int64_t)b1 * R, mine + 8 * R, R * 8u);
+      bulk_commit();
+    }
+    if constexpr (ADJ) {
+      // the CTA's three sums: the thread's own lanes, the warp, the CTA (fixed order), one join
+      __syncthreads();   // the scan scratch takes the per-warp sums
+      if (xfast) {
+        auto lanes = [&](float2 h, float2 l) {
+          const ffv a0 = own0 ? ffv{h.x, l.x} : ff_zero(), a1 = own1 ? ffv{h.y, l.y} : ff_zero();
+          return ff_add(a0, a1);
+        };
+        ffv a3[3] = {lanes(smh, sml), lanes(s0h, s0l), lanes(sph, spl)};
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) a3[q] = ff_add(a3[q], ff_shfl_down(a3[q], d));
+        if (lane == 0)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) swv[q * NW + wid] = a3[q];
+        __syncthreads();
+        if (tid < 3) {
+          ffv sum = ff_zero();
+          for (int w = 0; w < NW; ++w) sum = ff_add(sum, swv[tid * NW + w]);
+          // lambda = g X 2^-wscale, x = x' 2^-xscale
+          A.part[3 * (size_t)blockIdx.x + tid] = join_dadd(sum.h, sum.l, xsc) * pow2i(-wscale) * gd;
+        }
+      } else {
+        double a3[3] = {(own0 ? dm0 : 0.0) + (own1 ? dm1 : 0.0), (own0 ? d00 : 0.0) + (own1 ? d01 : 0.0),
+                        (own0 ? dp0 : 0.0) + (own1 ? dp1 : 0.0)};
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) a3[q] += __shfl_down_sync(0xffffffffu, a3[q], d);
+        double* sred = reinterpret_cast<double*>(swv);
+        if (lane == 0)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) sred[q * NW + wid] = a3[q];
+        __syncthreads();
+        if (tid < 3) {
+          double sum = 0.0;
+          for (int w = 0; w < NW; ++w) sum += sred[tid * NW + w];
+          A.part[3 * (size_t)blockIdx.x + tid] = sum;
+        }
+      }
+    }
+    if (own0 || own1) bulk_wait_read();
   };
   if (fast && gfold)
     body(std::true_type(), std::true_type());
