@@ -419,6 +419,10 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
       xsc = (emax == 2047) ? 0 : ((emax == 0) ? 1000 : max(-1000, min(1000, (1023 + 16) - emax)));
       xfast = (emin >= 1) && (emax >= 239) && (emax <= 1935) && (emax - emin <= 119);
     }
+    // the store loop in two instantiations: float-float gradient sums (x fast) or FP64 sums, so
+    // that neither keeps the other's accumulators live through the unrolled rows
+    auto store_loop = [&](auto xf_) {
+    constexpr bool XF = decltype(xf_)::value;
     const FastK fkx = fast_k(xsc);
     // the gradient sums of the thread's rows, lane x block 2t, lane y block 2t+1: float-float
     // (units 2^(wscale + xscale) / g) in windows whose x is fast, else FP64
@@ -445,7 +449,7 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
       if (act0) x0e = *reinterpret_cast<const double*>(mine + 8 * (R - 1));
       x1s = xb.x;
       xprev = make_double2(xlb, x0e);
-      if (xfast) {
+      if constexpr (XF) {
         xsplit(xprev.x, xprev.y, xph, xpl, true);
         xsplit(xa.x, xb.x, xch, xcl, false);
       }
@@ -496,7 +500,7 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
             xn = make_double2(na.x, nb2.x);
           else
             xn = make_double2(x1s, xrb);
-          if (xfast) {
+          if constexpr (XF) {
             float2 nh, nl;
             xsplit(xn.x, xn.y, nh, nl, i == R - 1);
             ff_fma_acc2(xh, xl, xph, xpl, smh, sml);
@@ -539,7 +543,7 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     if constexpr (ADJ) {
       // the CTA's three sums: the thread's own lanes, the warp, the CTA (fixed order), one join
       __syncthreads();   // the scan scratch takes the per-warp sums
-      if (xfast) {
+      if constexpr (XF) {
         auto lanes = [&](float2 h, float2 l) {
           const ffv a0 = own0 ? ffv{h.x, l.x} : ff_zero(), a1 = own1 ? ffv{h.y, l.y} : ff_zero();
           return ff_add(a0, a1);
@@ -578,6 +582,11 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
         }
       }
     }
+    };
+    if (!ADJ || xfast)
+      store_loop(std::true_type());
+    else
+      store_loop(std::false_type());
     if (own0 || own1) bulk_wait_read();
   };
   if (fast && gfold)
