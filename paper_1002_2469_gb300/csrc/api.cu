@@ -271,7 +271,6 @@ int build_system(double tm1, double t0, double tp1, int64_t N, int NT, int form,
   };
   p.lev = std::max(levels(Ls), levels(Lb));
   split_ff(r.g * r.ib, p.gib_h, p.gib_l);
-  split_ff(-r.q, p.q_h, p.q_l);
   split_ff(p.v0, p.v0_h, p.v0_l);
   split_ff(p.vend, p.vend_h, p.vend_l);
   split_ff(p.v0l, p.v0l_h, p.v0l_l);
@@ -320,19 +319,19 @@ int build_system(double tm1, double t0, double tp1, int64_t N, int NT, int form,
   for (int j = 0; j < kBC; ++j) put_ff(p.o_bcmf + j, T[p.o_bcm + j]);
   for (int64_t j = 0; j < kl * kBC; ++j) put_ff(p.o_bclf + (int32_t)j, T[p.o_bcl + j]);
   for (int64_t j = 0; j < kr * kBC; ++j) put_ff(p.o_bcrf + (int32_t)j, T[p.o_bcr + j]);
-  // beta records (K1..K4) of the middle record and of the end tables, float-float
+  // beta records (K1..K4, units of X) of the middle record and of the end tables, float-float
   {
     double k4[4];
-    beta_coeffs(&T[p.o_bcm], r.g, r.ib, p.v0, p.vend, k4);
+    beta_coeffs(&T[p.o_bcm], r.ib, p.v0, p.vend, k4);
     for (int j = 0; j < 4; ++j) put_ff(p.o_kmf + j, k4[j]);
     for (int64_t m = 0; m < kl; ++m) {
       const bool lb = (m == P - 1);
-      beta_coeffs(&T[p.o_bcl + m * kBC], r.g, r.ib, lb ? p.v0l : p.v0, lb ? p.vendl : p.vend, k4);
+      beta_coeffs(&T[p.o_bcl + m * kBC], r.ib, lb ? p.v0l : p.v0, lb ? p.vendl : p.vend, k4);
       for (int j = 0; j < 4; ++j) put_ff(p.o_klf + (int32_t)(m * 4 + j), k4[j]);
     }
     for (int64_t k = 0; k < kr; ++k) {
       const bool lb = (P - kr + k == P - 1);
-      beta_coeffs(&T[p.o_bcr + k * kBC], r.g, r.ib, lb ? p.v0l : p.v0, lb ? p.vendl : p.vend, k4);
+      beta_coeffs(&T[p.o_bcr + k * kBC], r.ib, lb ? p.v0l : p.v0, lb ? p.vendl : p.vend, k4);
       for (int j = 0; j < 4; ++j) put_ff(p.o_krf + (int32_t)(k * 4 + j), k4[j]);
     }
     // powers of the middle record's pair maps: (a^2)^t and (c^2)^t, t = 0..32

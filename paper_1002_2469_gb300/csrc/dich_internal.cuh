@@ -90,7 +90,6 @@ struct SysPlan {
   // float-float copies of g * ib and of the corner spikes (MIXED form)
   float gib_h, gib_l;
   float v0_h, v0_l, vend_h, vend_l, v0l_h, v0l_l, vendl_h, vendl_l;
-  float q_h, q_l;   // float-float 1/g = -q (spike coefficients in units of X, register path)
   // MIXED form: warp-scan levels of the tree (couplings beyond 2^(lev+1) blocks are below the
   // truncation threshold), beta records from the block-end values (4 float-float entries per
   // record: middle, left table [kl], right table [kr]) and the middle record's map powers
@@ -175,16 +174,18 @@ DICH_HD int64_t decay_len(double absr, double eps, int64_t cap) {
   return L < 1.0 ? 1 : (int64_t)L;
 }
 
-// beta of a block (eq. 16) from the ends X_0, X_{n-1} of its local backward recurrence (the
-// particular solution is xp = g X):  alpha = g X_0 - g ib v_0 X_0, omega = g X_{n-1} - g ib v_{n-1} X_0,
-// (beta^L, beta^R) = M (alpha, omega)  =>  beta^L = K1 X_0 + K2 X_{n-1},  beta^R = K3 X_0 + K4 X_{n-1}.
+// beta of a block (eq. 16) in units of X from the ends X_0, X_{n-1} of its local backward
+// recurrence (the particular solution is xp = g X):  alpha = g (X_0 - ib v_0 X_0),
+// omega = g (X_{n-1} - ib v_{n-1} X_0), (beta^L, beta^R) = M (alpha, omega); so beta / g is
+//   beta^L / g = K1 X_0 + K2 X_{n-1},  beta^R / g = K3 X_0 + K4 X_{n-1}
+// with K1 = M00 (1 - ib v_0) - M01 ib v_{n-1}, K2 = M01, K3 = M10 (1 - ib v_0) - M11 ib v_{n-1}, K4 = M11.
 // bc: the block's record (BC_*), v0 / vend: its corner spikes; out[0..3] = K1..K4.
-DICH_HD void beta_coeffs(const double* bc, double g, double ib, double v0, double vend, double* out) {
-  const double ca = g * (1.0 - ib * v0), cw = -g * ib * vend;
+DICH_HD void beta_coeffs(const double* bc, double ib, double v0, double vend, double* out) {
+  const double ca = 1.0 - ib * v0, cw = -ib * vend;
   out[0] = bc[BC_M00] * ca + bc[BC_M01] * cw;
-  out[1] = bc[BC_M01] * g;
+  out[1] = bc[BC_M01];
   out[2] = bc[BC_M10] * ca + bc[BC_M11] * cw;
-  out[3] = bc[BC_M11] * g;
+  out[3] = bc[BC_M11];
 }
 
 // Block coefficients of block [s, e] of a system of N rows (eq. 15-18 restated):

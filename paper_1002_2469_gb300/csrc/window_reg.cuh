@@ -334,8 +334,9 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     }
 
     // ------------------------------------------------------------ beta (eq. 16), tree (a2)
-    // beta^L = K1 X_0 + K2 X_{n-1}, beta^R = K3 X_0 + K4 X_{n-1} (the block's beta record: the 2x2 map M
-    // of eq. 16 applied to alpha = g X_0 - g ib v_0 X_0, omega = g X_{n-1} - g ib v_{n-1} X_0)
+    // in units of X (x = g X; the maps of eq. 15 are linear, so the tree runs in any unit):
+    // beta^L / g = K1 X_0 + K2 X_{n-1}, beta^R / g = K3 X_0 + K4 X_{n-1} (the block's beta record: the
+    // 2x2 map M of eq. 16 applied to alpha / g = X_0 - ib v_0 X_0, omega / g = X_{n-1} - ib v_{n-1} X_0)
     const ff2 zero2{f2(0.f), f2(0.f)};
     const ff2 X0 = ff2_make(H[0], L[0]), Xe = ff2_make(H[R - 1], L[R - 1]);
     const float2* tf = reinterpret_cast<const float2*>(tab);
@@ -363,12 +364,11 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     const bool own0 = act0 && b0 >= hl && b0 < hl + nown;
     const bool own1 = act1 && b1 >= hl && b1 < hl + nown;
     if (!ADJ && !(own0 || own1)) return;
-    // x = xp + (x_{s-1} - xp(-1)) v + x_{e+1} w, in units of X (x = g X): the coefficients are
-    // x_{s-1} / g - ib X_0 and x_{e+1} / g, with 1/g = -q
-    const ff2 qv = ff2_bcast(ffv{pp->q_h, pp->q_l});
+    // x = xp + (x_{s-1} - xp(-1)) v + x_{e+1} w, in units of X (x = g X; the tree's first/last values
+    // are in those units already): the coefficients are X_{s-1} - ib X_0 and X_{e+1}
     const ff2 ibx = ff2_mul(ff2_bcast(ffv{pp->ib_h, pp->ib_l}), X0);
-    const ff2 cL = ff2_fma(qv, ff2_pair(XL0, XL1), ff2{make_float2(-ibx.h.x, -ibx.h.y), make_float2(-ibx.l.x, -ibx.l.y)});
-    const ff2 cR = ff2_mul(ff2_pair(XR0, XR1), qv);
+    const ff2 cL = ff2_sub(ff2_pair(XL0, XL1), ibx);
+    const ff2 cR = ff2_pair(XR0, XR1);
     const float2 gh = f2(pp->g_h), glo = f2(pp->g_l);
     const double gd = pp->g;
 
