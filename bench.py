@@ -574,7 +574,7 @@ def other_configs(D, W, oracle, stream, world, steps=10, only=None, cpu_leg=True
         xd = torch.empty_like(Fd)
         c3 = {"unknowns": int(N.sum())}
         from paper_1002_2469_gb300 import autotune as AT
-        tb = AT.tune_batch(N, tm1, t0, tp1, precision=D.PREC_AUTO)
+        tb = AT.tune_batch(N, tm1, t0, tp1, precision=D.PREC_AUTO, F=Fd)
         c3["autotuned"] = tb
         for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
             kw = {k: tb[k] for k in ("threads", "block_size", "flags")} if (tb and prec == D.PREC_AUTO) else {}
@@ -596,7 +596,7 @@ def other_configs(D, W, oracle, stream, world, steps=10, only=None, cpu_leg=True
         xd = torch.empty_like(Fd)
         c4 = {"unknowns": int(N.sum())}
         from paper_1002_2469_gb300 import autotune as AT
-        tb = AT.tune_batch(N, tm1, t0, tp1, precision=D.PREC_AUTO,
+        tb = AT.tune_batch(N, tm1, t0, tp1, precision=D.PREC_AUTO, F=Fd,
                            candidates=[(0, 0, 0), (0, 0, D.FLAG_SMEM_PATH), (64, 16, 0), (256, 16, 0)])
         c4["autotuned"] = tb
         for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):

@@ -136,16 +136,19 @@ BATCH_CANDIDATES = [(0, 0, 0), (0, 0, D.FLAG_REG_PATH), (0, 0, D.FLAG_SMEM_PATH)
                     (64, 32, 0), (256, 16, 0)]
 
 
-def tune_batch(N, t_m1, t_0, t_1, precision: int = D.PREC_AUTO, candidates=None, verbose: bool = False) -> dict:
+def tune_batch(N, t_m1, t_0, t_1, precision: int = D.PREC_AUTO, candidates=None, verbose: bool = False,
+               F: "torch.Tensor | None" = None) -> dict:
     """Time (threads, block size, flags) candidates for one batch of systems (sizes N, coefficient
     arrays) with the library's batched solve and return the fastest as {"threads",
-    "block_size", "flags", "ms"}; (0, 0, 0) is the library's default choice.  Not cached: a
-    batch's composition is its own key."""
+    "block_size", "flags", "ms"}; (0, 0, 0) is the library's default choice.  F: the right-hand
+    sides to time with (their exponent ranges decide which conversions a window takes), else
+    seeded normal values.  Not cached: a batch's composition is its own key."""
     import numpy as np
     N = np.asarray(N, dtype=np.int64)
-    g = torch.Generator(device="cuda")
-    g.manual_seed(0)
-    F = torch.randn(int(N.sum()), dtype=torch.float64, device="cuda", generator=g)
+    if F is None:
+        g = torch.Generator(device="cuda")
+        g.manual_seed(0)
+        F = torch.randn(int(N.sum()), dtype=torch.float64, device="cuda", generator=g)
     x = torch.empty_like(F)
     best = None
     for cand in (candidates or BATCH_CANDIDATES):

@@ -248,6 +248,17 @@ __device__ __forceinline__ void split_fast(double d, const FastK& k, float& hi, 
   lo = __fsub_rn(__uint_as_float(b | ((lw >> 6) & 0x7FFFFFu)), __uint_as_float(b));
 }
 
+// split_fast in a window whose largest |F| qualifies (emax in [239, 1935], no Inf/NaN) while some of
+// its values lie further than 2^119 below it (zeros and subnormals included -- the usual shape of a
+// spectrum that decays over hundreds of decades): those values, whose FP64 high word (sign cleared)
+// is below hlo = (emax - 119) << 20, become (0, 0).  They are below 2^-103 of the window's largest
+// |F| in window units -- under the floor the conversions already put under the error (values below
+// 2^-126 window units are not resolved) -- so the window keeps the fast conversions.
+__device__ __forceinline__ void split_fast_flush(double d, const FastK& k, unsigned hlo, float& hi, float& lo) {
+  split_fast(d, k, hi, lo);
+  if (((unsigned)__double2hiint(d) & 0x7FFFFFFFu) < hlo) hi = lo = 0.f;
+}
+
 // (h, l) * 2^-s -> FP64 in a fast window: both floats rebuilt as exact FP64 bit patterns and
 // added once on the FP64 pipe.  A float's bits shifted right by 3 (sign kept) give the FP64
 // fraction and exponent fields; adding (896 - s) << 20 rebiases and unscales the exponent,

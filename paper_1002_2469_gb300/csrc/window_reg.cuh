@@ -236,7 +236,8 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
   // window scale (largest |F| near 2^16, an exact power of two) and the fast criterion: the
   // largest and smallest FP64 high words with the sign cleared, over the active blocks
   int wscale;
-  bool fast;
+  bool fast, flush;   // flush: fast conversions with the window's far-smaller values set to zero
+  unsigned hlo;
   {
     unsigned hmax = 0u, hmin = 0xFFFFFFFFu;
     if (act0) {
@@ -272,6 +273,8 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     const int emax = (int)(hmax >> 20), emin = (int)(hmin >> 20);
     wscale = (emax == 2047) ? 0 : ((emax == 0) ? 1000 : max(-1000, min(1000, (1023 + 16) - emax)));
     fast = (emin >= 1) && (emax >= 239) && (emax <= 1935) && (emax - emin <= 119);
+    flush = !fast && (emax >= 239) && (emax <= 1935);
+    hlo = (unsigned)(emax - 119) << 20;
   }
   if constexpr (ADJ) {
     // the slot's values are in registers: it now takes the forward solution x (mbarrier phase 1)
@@ -285,16 +288,20 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
   const int ghw = __double2hiint(pp->g);
   const bool gfold = ((ghw >> 20) & 0x7FF) + 896 - wscale <= 2046;
   const double G = __hiloint2double((int)((unsigned)ghw + ((unsigned)(896 - wscale) << 20)), __double2loint(pp->g));
-  auto body = [&](auto fast_, auto gfold_) {
+  auto body = [&](auto fast_, auto gfold_, auto flush_) {
     constexpr bool FAST = decltype(fast_)::value;
     constexpr bool GFOLD = decltype(gfold_)::value;
+    constexpr bool FLUSH = decltype(flush_)::value;
     const FastK fk = fast_k(wscale);
     float2 H[R], L[R];   // (block 2t, block 2t+1) of row i: hi and lo parts
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const double d0 = (i & 1) ? a[i / 2].y : a[i / 2].x;
       const double d1 = (i & 1) ? b[i / 2].y : b[i / 2].x;
-      if (FAST) {
+      if (FAST && FLUSH) {
+        split_fast_flush(d0, fk, hlo, H[i].x, L[i].x);
+        split_fast_flush(d1, fk, hlo, H[i].y, L[i].y);
+      } else if (FAST) {
         split_fast(d0, fk, H[i].x, L[i].x);
         split_fast(d1, fk, H[i].y, L[i].y);
       } else {
@@ -590,11 +597,13 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     if (own0 || own1) bulk_wait_read();
   };
   if (fast && gfold)
-    body(std::true_type(), std::true_type());
+    body(std::true_type(), std::true_type(), std::false_type());
+  else if (flush && gfold)
+    body(std::true_type(), std::true_type(), std::true_type());
   else if (fast)
-    body(std::true_type(), std::false_type());
+    body(std::true_type(), std::false_type(), std::false_type());
   else
-    body(std::false_type(), std::false_type());
+    body(std::false_type(), std::false_type(), std::false_type());
 }
 
 }  // namespace dich

@@ -738,6 +738,37 @@ def test_mixed_kernel_paths(D, flags):
         assert rel(X[k], oracle.thomas((-1.2, 2.5, -0.8), Fs[k])) < TOL
 
 
+@pytest.mark.parametrize("flags", [32, 64])
+def test_windows_of_wide_dynamic_range(D, flags):
+    """Right-hand sides whose windows span hundreds of decades with exact zeros (the spectrum of a
+    smooth source: the largest values qualify for the fast conversions, the smallest lie far below
+    them), through both MIXED paths, against the oracle norm-wise; and the 4096 Poisson modes of
+    the smooth source, every mode against the oracle with binary128 arbitrating."""
+    rng = np.random.default_rng(91)
+    for t, N in [((-1.2, 2.5, -0.8), 300001), ((-1.0, 4.0, -1.0), 4096)]:
+        F = rng.standard_normal(N) * 10.0 ** (-rng.uniform(0, 300, N))
+        F[rng.uniform(size=N) < 0.2] = 0.0
+        F[::1000] = rng.standard_normal(F[::1000].size)     # the windows' largest values stay O(1)
+        x, info = gpu_solve(D, t, F, precision=1, flags=flags)
+        assert rel(x, oracle.thomas(t, F)) < TOL, (t, N, flags)
+    tm1, t0, tp1, Ns, rhs = W.poisson_c3()
+    off = W.offsets(Ns)
+    F = rhs.reshape(-1)
+    b = D.Batch(Ns, tm1, t0, tp1, precision=2, flags=flags)
+    x = b.solve(torch.from_numpy(F).cuda()).cpu().numpy()
+    assert b.status() == 0
+    ref = oracle.thomas_batched(tm1, t0, tp1, Ns, off, F)
+    bad = []
+    for k in range(Ns.size):
+        sl = slice(int(off[k]), int(off[k] + Ns[k]))
+        if rel(x[sl], ref[sl]) < TOL:
+            continue
+        refq = oracle.thomas_q((tm1[k], t0[k], tp1[k]), F[sl])
+        if rel(x[sl], refq) > max(TOL, 2.0 * rel(ref[sl], refq)):
+            bad.append(k)
+    assert not bad, bad[:10]
+
+
 def test_autograd_with_cpu_coefficients(D):
     """Coefficients kept on the host (natural for three numbers): their gradients come back on the
     host, for the single, quasi-Toeplitz and batched Functions."""
