@@ -291,14 +291,15 @@ __host__ __device__ inline size_t window2_smem_bytes(int NT, int n_smem) {
 }
 
 // Instantiations: KIND_REG -- the forward solve with the register path for windows it serves (up to
-// 128 registers: four CTAs of 128 threads per SM); KIND_SMEM -- the forward solve on the shared-memory
+// 96 registers: five CTAs of 128 threads per SM, the shared-memory limit of its slots); KIND_SMEM -- the forward solve on the shared-memory
 // path only (80 registers: six CTAs per SM, for launches of many short, latency-bound windows);
 // KIND_ADJ -- the adjoint (shared-memory path, gradient sums in the store loop, six CTAs per SM).
-// KIND_REGADJ -- the adjoint with the register path for the windows it serves (four CTAs per SM).
+// KIND_REGADJ -- the adjoint with the register path for the windows it serves (up to 128 registers:
+// four CTAs per SM; its slots hold x during the tree).
 enum WinKind : int { KIND_REG = 0, KIND_ADJ = 1, KIND_SMEM = 2, KIND_REGADJ = 3 };
 
 template <int NT, int KIND>
-__global__ void __launch_bounds__(NT, ((KIND == KIND_REG || KIND == KIND_REGADJ) ? 512 : 768) / NT)
+__global__ void __launch_bounds__(NT, (KIND == KIND_REG ? 640 : (KIND == KIND_REGADJ ? 512 : 768)) / NT)
     k_window2(const WinArgs A) {
   constexpr bool ADJ = (KIND == KIND_ADJ || KIND == KIND_REGADJ);
   constexpr int NW = NT / 32;

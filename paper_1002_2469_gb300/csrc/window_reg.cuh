@@ -346,6 +346,18 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     // 2x2 map M of eq. 16 applied to alpha / g = X_0 - ib v_0 X_0, omega / g = X_{n-1} - ib v_{n-1} X_0)
     const ff2 zero2{f2(0.f), f2(0.f)};
     const ff2 X0 = ff2_make(H[0], L[0]), Xe = ff2_make(H[R - 1], L[R - 1]);
+    // forward solve: the slot is idle until the output, so the 64 data registers wait there while
+    // the tree runs (five CTAs fit per SM instead of four).  Layout: row i of block 2t at
+    // 8 i, of block 2t+1 at 8 R + 8 i, (hi, lo) per row -- where the output of row i goes, so each
+    // row is read back before its result overwrites it.
+    if constexpr (!ADJ) {
+#pragma unroll
+      for (int k = 0; k < R / 2; ++k) {
+        *reinterpret_cast<float4*>(mine + 16 * k) = make_float4(H[2 * k].x, L[2 * k].x, H[2 * k + 1].x, L[2 * k + 1].x);
+        *reinterpret_cast<float4*>(mine + 8 * R + 16 * k) =
+            make_float4(H[2 * k].y, L[2 * k].y, H[2 * k + 1].y, L[2 * k + 1].y);
+      }
+    }
     const float2* tf = reinterpret_cast<const float2*>(tab);
     // every block of the window carries the middle record: uniform coefficients (tree_mid)
     const bool mid = (nwin == 2 * NT) && (wlo >= pp->kl) && (wlo + nwin <= P - pp->kr);
@@ -476,6 +488,12 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
       for (int j = 0; j < 2; ++j) {
         const int i = 2 * k + j;
         float2 xh = H[i], xl = L[i];
+        if constexpr (!ADJ) {   // back from the slot (stored before the tree)
+          const float2 s0 = *reinterpret_cast<const float2*>(mine + 8 * i);
+          const float2 s1 = *reinterpret_cast<const float2*>(mine + 8 * R + 8 * i);
+          xh = make_float2(s0.x, s1.x);
+          xl = make_float2(s0.y, s1.y);
+        }
         if (own0 || own1) {
           const float4 v = tv4[i], w = tw4[R - 1 - i];
           ff_fma_acc2(cL.h, cL.l, make_float2(v.x, v.y), make_float2(v.z, v.w), xh, xl);
