@@ -154,16 +154,37 @@ __device__ __forceinline__ void correct_pair(double* S, int tid, int nrow_, int 
   }
 }
 
+// After the tree: the values of the neighbouring blocks a thread's pair needs -- x_e of block 2t-1
+// (the previous thread's second block) and x_s of block 2t+2 (the next thread's first block) -- by
+// warp shuffles, across warp boundaries through sbd (2 NW entries: each warp's last x_e, first x_s).
+// Zeros beyond the window's ends; the caller masks the system's ends and inactive blocks.
+template <int NT>
+__device__ __forceinline__ void pair_neighbours(const ff2& xs, const ff2& xe, int tid, ffv* sbd, ffv& xe_prev,
+                                                ffv& xs_next) {
+  constexpr int NW = NT / 32;
+  const int lane = tid & 31, wid = tid >> 5;
+  ffv up{__shfl_up_sync(0xffffffffu, xe.h.y, 1), __shfl_up_sync(0xffffffffu, xe.l.y, 1)};
+  ffv dn{__shfl_down_sync(0xffffffffu, xs.h.x, 1), __shfl_down_sync(0xffffffffu, xs.l.x, 1)};
+  if (lane == 31) sbd[wid] = ff2_y(xe);
+  if (lane == 0) sbd[NW + wid] = ff2_x(xs);
+  __syncthreads();
+  if (lane == 0) up = (wid > 0) ? sbd[wid - 1] : ff_zero();
+  if (lane == 31) dn = (wid < NW - 1) ? sbd[NW + wid + 1] : ff_zero();
+  xe_prev = up;
+  xs_next = dn;
+}
+
 // The dichotomy tree of one MIXED window (a2): the prefix and suffix affine scans of eq. 15 over the
 // window's blocks in packed float-float (five warp-shuffle levels, one shared-memory level), the
-// first/last values of every block (eq. 18) in sxs/sxe, and the neighbours' values the correction of
-// the thread's two blocks needs: XL = x_{s-1}, XR = x_{e+1} (zero coupling enters at both window
-// ends).  bc2(j): coefficient j of both blocks' records; bL, bR: beta (eq. 16) of both blocks.
+// first/last values of every block (eq. 18), and the neighbours' values the correction of the
+// thread's two blocks needs: XL = x_{s-1}, XR = x_{e+1} (zero coupling enters at both window ends).
+// bc2(j): coefficient j of both blocks' records; bL, bR: beta (eq. 16) of both blocks; sbd: 2 NW
+// entries of shared memory for the exchange across warps.
 // lev: warp-scan levels that run (the plan's; contributions from 2^(lev+1) or more blocks away are
 // below its truncation threshold, 5 = the whole warp).
 template <int NT, class BC>
 __device__ __forceinline__ void tree2(const BC& bc2, bool act0, bool act1, int64_t mb0, int64_t mb1, int64_t P,
-                                      int nwin, int tid, const ff2& bL, const ff2& bR, ffv* swv, ffv* sxs, ffv* sxe,
+                                      int nwin, int tid, const ff2& bL, const ff2& bR, ffv* swv, ffv* sbd,
                                       ffv& XL0, ffv& XR0, ffv& XL1, ffv& XR1, int lev = 5) {
   using O = OpsFF;
   constexpr int NW = NT / 32;
@@ -226,22 +247,15 @@ __device__ __forceinline__ void tree2(const BC& bc2, bool act0, bool act1, int64
   // first/last values of both blocks (eq. 18)
   const ff2 xs = ff2_add(ff2_fma(bc2(BC_TL), Bv, bL), Av);
   const ff2 xe = ff2_fma(bc2(BC_TR), Av, ff2_add(bR, Bv));
+  ffv xe_prev, xs_next;
+  pair_neighbours<NT>(xs, xe, tid, sbd, xe_prev, xs_next);
   if (act0) {
-    sxs[b0] = ff2_x(xs);
-    sxe[b0] = ff2_x(xe);
+    if (!(mb0 == 0 || b0 == 0)) XL0 = xe_prev;
+    if (!(mb0 == P - 1 || b0 + 1 >= nwin)) XR0 = ff2_y(xs);
   }
   if (act1) {
-    sxs[b1] = ff2_y(xs);
-    sxe[b1] = ff2_y(xe);
-  }
-  __syncthreads();
-  if (act0) {
-    if (!(mb0 == 0 || b0 == 0)) XL0 = sxe[b0 - 1];
-    if (!(mb0 == P - 1 || b0 + 1 >= nwin)) XR0 = sxs[b0 + 1];
-  }
-  if (act1) {
-    XL1 = sxe[b0];
-    if (!(mb1 == P - 1 || b1 + 1 >= nwin)) XR1 = sxs[b1 + 1];
+    XL1 = ff2_x(xe);
+    if (!(mb1 == P - 1 || b1 + 1 >= nwin)) XR1 = xs_next;
   }
 }
 
@@ -284,14 +298,14 @@ namespace dich {
 __host__ __device__ inline size_t window2_smem_bytes(int NT, int n_smem) {
   const size_t nw = (size_t)(NT / 32);
   const size_t LD = 2 * (size_t)NT + 2;
-  const size_t tile = sizeof(double) * ((size_t)n_smem * LD + 4 * (size_t)n_smem + 4 * (size_t)NT + 4 * nw + 8);
+  const size_t tile = sizeof(double) * ((size_t)n_smem * LD + 4 * (size_t)n_smem + 2 * nw + 4 * nw + 8);
   if (n_smem < kRegRows) return tile;
   const size_t reg = window_reg_smem_bytes(NT);
   return tile > reg ? tile : reg;
 }
 
 // Instantiations: KIND_REG -- the forward solve with the register path for windows it serves (up to
-// 96 registers: five CTAs of 128 threads per SM, the shared-memory limit of its slots); KIND_SMEM -- the forward solve on the shared-memory
+// 80 registers: six CTAs of 128 threads per SM); KIND_SMEM -- the forward solve on the shared-memory
 // path only (80 registers: six CTAs per SM, for launches of many short, latency-bound windows);
 // KIND_ADJ -- the adjoint (shared-memory path, gradient sums in the store loop, six CTAs per SM).
 // KIND_REGADJ -- the adjoint with the register path for the windows it serves (up to 128 registers:
@@ -299,7 +313,7 @@ __host__ __device__ inline size_t window2_smem_bytes(int NT, int n_smem) {
 enum WinKind : int { KIND_REG = 0, KIND_ADJ = 1, KIND_SMEM = 2, KIND_REGADJ = 3 };
 
 template <int NT, int KIND>
-__global__ void __launch_bounds__(NT, (KIND == KIND_REG ? 640 : (KIND == KIND_REGADJ ? 512 : 768)) / NT)
+__global__ void __launch_bounds__(NT, (KIND == KIND_REGADJ ? 512 : 768) / NT)
     k_window2(const WinArgs A) {
   constexpr bool ADJ = (KIND == KIND_ADJ || KIND == KIND_REGADJ);
   constexpr int NW = NT / 32;
@@ -315,9 +329,8 @@ __global__ void __launch_bounds__(NT, (KIND == KIND_REG ? 640 : (KIND == KIND_RE
   double* S = sm;
   float4* tv4 = reinterpret_cast<float4*>(S + (size_t)ns * LD);   // spikes, both lanes, zero-padded
   float4* tw4 = tv4 + ns;
-  ffv* sxs = reinterpret_cast<ffv*>(tw4 + ns);
-  ffv* sxe = sxs + WB;
-  ffv* swv = sxe + WB;  // 4 * NW scan scratch (also the exponent maxima)
+  ffv* sbd = reinterpret_cast<ffv*>(tw4 + ns);   // 2 * NW warp-boundary first/last values
+  ffv* swv = sbd + 2 * NW;                       // 4 * NW scan scratch (also the exponent maxima)
 
   // ---------------------------------------------------------------- the window
   int sys;
@@ -543,7 +556,7 @@ __global__ void __launch_bounds__(NT, (KIND == KIND_REG ? 640 : (KIND == KIND_RE
 
   ffv XL0 = ff_zero(), XR0 = ff_zero(), XL1 = ff_zero(), XR1 = ff_zero();
   if (A.mode == MODE_FULL) {
-    tree2<NT>(bc2, act0, act1, mb0, mb1, P, nwin, tid, bL, bR, swv, sxs, sxe, XL0, XR0, XL1, XR1, pp->lev);
+    tree2<NT>(bc2, act0, act1, mb0, mb1, P, nwin, tid, bL, bR, swv, sbd, XL0, XR0, XL1, XR1, pp->lev);
   } else {  // MODE_APPLY: neighbours' first/last values from the global scan (unscaled FP64)
     const double upw = pow2i(wscale);
     auto to_ff = [&](double d) {

@@ -31,12 +31,11 @@ constexpr int kRegRows = 16;                            // block size of the reg
 constexpr int kRegPairBytes = 2 * kRegRows * 8 + 16;    // a thread's two blocks + 16 bytes of padding
 
 // shared memory of the register path for NT threads: the pair slots, the two spike tables, the
-// first/last values of the window's blocks, the scan scratch, the exponent maxima (of the right-hand
-// side and, for the adjoint, of the forward solution) and the mbarrier
+// warp-boundary first/last values, the scan scratch, the exponent maxima (of the right-hand side
+// and, for the adjoint, of the forward solution) and the mbarrier
 __host__ __device__ inline size_t window_reg_smem_bytes(int NT) {
   const size_t nw = (size_t)(NT / 32);
-  return (size_t)NT * kRegPairBytes + 2 * 16 * (size_t)kRegRows + 2 * 8 * 2 * (size_t)NT + 8 * 4 * nw +
-         4 * 4 * nw + 16;
+  return (size_t)NT * kRegPairBytes + 2 * 16 * (size_t)kRegRows + 8 * 2 * nw + 8 * 4 * nw + 4 * 4 * nw + 16;
 }
 
 // ---------------------------------------------------------------- mbarrier and bulk copies (PTX)
@@ -104,7 +103,7 @@ __device__ __forceinline__ double f32_as_f64_unbiased(float f) {
 // prefix of the warps before it times (a^2)^t and the suffix of the warps after it times (c^2)^(31-t).
 template <int NT>
 __device__ __forceinline__ void tree_mid(const float2* tf, const SysPlan* pp, int nwin, int tid, const ff2& bL,
-                                         const ff2& bR, ffv* swv, ffv* sxs, ffv* sxe, ffv& XL0, ffv& XR0, ffv& XL1,
+                                         const ff2& bR, ffv* swv, ffv* sbd, ffv& XL0, ffv& XR0, ffv& XL1,
                                          ffv& XR1) {
   constexpr int NW = NT / 32;
   const int lane = tid & 31, wid = tid >> 5;
@@ -157,15 +156,12 @@ __device__ __forceinline__ void tree_mid(const float2* tf, const SysPlan* pp, in
   // first/last values of both blocks (eq. 18)
   const ff2 xs = ff2_add(ff2_fma(ff2_bcast(ld(rm + BC_TL)), Bv, bL), Av);
   const ff2 xe = ff2_fma(ff2_bcast(ld(rm + BC_TR)), Av, ff2_add(bR, Bv));
-  sxs[b0] = ff2_x(xs);
-  sxe[b0] = ff2_x(xe);
-  sxs[b1] = ff2_y(xs);
-  sxe[b1] = ff2_y(xe);
-  __syncthreads();
-  if (b0 > 0) XL0 = sxe[b0 - 1];
-  XR0 = sxs[b1];
-  XL1 = sxe[b0];
-  if (b1 + 1 < nwin) XR1 = sxs[b1 + 1];
+  ffv xe_prev, xs_next;
+  pair_neighbours<NT>(xs, xe, tid, sbd, xe_prev, xs_next);
+  if (b0 > 0) XL0 = xe_prev;
+  XR0 = ff2_y(xs);
+  XL1 = ff2_x(xe);
+  if (b1 + 1 < nwin) XR1 = xs_next;
 }
 
 // Iterations of the bounded wait for the window's bulk loads (each try_wait may also suspend the
@@ -187,9 +183,8 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
   unsigned char* mine = smem + (size_t)tid * kRegPairBytes;
   float4* tv4 = reinterpret_cast<float4*>(smem + (size_t)NT * kRegPairBytes);   // spikes, both lanes
   float4* tw4 = tv4 + R;
-  ffv* sxs = reinterpret_cast<ffv*>(tw4 + R);
-  ffv* sxe = sxs + 2 * NT;
-  ffv* swv = sxe + 2 * NT;                                                       // 4 NW scan scratch
+  ffv* sbd = reinterpret_cast<ffv*>(tw4 + R);                                   // 2 NW warp-boundary values
+  ffv* swv = sbd + 2 * NW;                                                       // 4 NW scan scratch
   unsigned* sexp = reinterpret_cast<unsigned*>(swv + 4 * NW);                    // 2 NW exponent maxima
   unsigned* sexpx = sexp + 2 * NW;                                               // the same for x
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(sexpx + 2 * NW);
@@ -368,12 +363,12 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
                 k4 = ff_of(tf[pp->o_kmf + 3]);
       bL = ff2_fma(ff2_bcast(k2), Xe, ff2_mul(ff2_bcast(k1), X0));
       bR = ff2_fma(ff2_bcast(k4), Xe, ff2_mul(ff2_bcast(k3), X0));
-      tree_mid<NT>(tf, pp, nwin, tid, bL, bR, swv, sxs, sxe, XL0, XR0, XL1, XR1);
+      tree_mid<NT>(tf, pp, nwin, tid, bL, bR, swv, sbd, XL0, XR0, XL1, XR1);
     } else {
       const Recs2 bc2 = recs2(pp, tab, P, act0, act1, mb0, mb1);
       bL = ff2_sel(act0, act1, ff2_fma(bc2.k(1), Xe, ff2_mul(bc2.k(0), X0)), zero2);
       bR = ff2_sel(act0, act1, ff2_fma(bc2.k(3), Xe, ff2_mul(bc2.k(2), X0)), zero2);
-      tree2<NT>(bc2, act0, act1, mb0, mb1, P, nwin, tid, bL, bR, swv, sxs, sxe, XL0, XR0, XL1, XR1, pp->lev);
+      tree2<NT>(bc2, act0, act1, mb0, mb1, P, nwin, tid, bL, bR, swv, sbd, XL0, XR0, XL1, XR1, pp->lev);
     }
 
     // the next kernel of the stream may begin its launch (it waits for this grid to complete)
