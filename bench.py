@@ -264,8 +264,15 @@ def run_gpu(args):
     # the window geometry of the headline form: the project's autotuner times (threads, block size)
     # candidates with the library's own solve on this GPU before anything is timed
     from paper_1002_2469_gb300 import autotune as AT
-    tuned = AT.tune(t, N, precision=D.PREC_AUTO, candidates=[(128, 16), (64, 16), (256, 16), (128, 24)])
-    tuned_kw = {"threads": tuned["threads"], "block_size": tuned["block_size"]} if tuned else {}
+    if args.geometry:
+        # a fixed (threads, block size), e.g. to profile one geometry without the tuner's launches
+        th, bs = (int(v) for v in args.geometry.split(","))
+        tuned_kw = {"threads": th, "block_size": bs}
+        geometry = "fixed: " + json.dumps(tuned_kw)
+    else:
+        tuned = AT.tune(t, N, precision=D.PREC_AUTO, candidates=[(128, 16), (64, 16), (256, 16), (128, 24)])
+        tuned_kw = {"threads": tuned["threads"], "block_size": tuned["block_size"]} if tuned else {}
+        geometry = "autotuned: " + json.dumps(tuned_kw)
     # the FP64 comparator first: its ~50 ms of solves also bring the GPU out of idle before the
     # headline form's timed steps
     for name, prec in (("fp64_plain", D.PREC_F64), ("auto", D.PREC_AUTO)):
@@ -356,7 +363,7 @@ def run_gpu(args):
                    "threads_per_window": head["info"]["threads"], "halo": [head["info"]["halo_l"],
                                                                           head["info"]["halo_r"]],
                    "path": ["single", "halo", "general"][head["info"]["path"]], "l2": "inputs > L2 (no flush)",
-                   "geometry": "autotuned: " + json.dumps(tuned_kw),
+                   "geometry": geometry,
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "hbm_gbs": round(achieved, 1),
         "hbm_pct_of_8tbs": round(100.0 * achieved / 8000.0, 1),
@@ -813,6 +820,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-configs", action="store_true")
+    ap.add_argument("--geometry", default=None,
+                    help="threads,block_size of the headline solve instead of the autotuner's choice")
     ap.add_argument("--only", default=None,
                     help="comma-separated subset of the other configurations: " + ",".join(OTHER_CONFIGS))
     args = ap.parse_args()

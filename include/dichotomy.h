@@ -99,7 +99,9 @@ typedef struct {
   int32_t precision;     /* dich_precision */
   int32_t threads;       /* window width in blocks (CTA size): 0 = default; 64, 128 or 256 */
   int32_t flags;         /* DICH_FLAG_* */
-  double trunc_eps;      /* relative truncation of geometrically small terms; 0 = 2^-64 */
+  double trunc_eps;      /* relative truncation of geometrically small terms; 0 = the
+                            default: 2^-64 for F64 plans, 2^-56 for MIXED plans (whose
+                            float-float values carry about 48 bits) */
 } dich_opts;
 
 /* Read-only description of a plan (for tests, tuning and reporting). */

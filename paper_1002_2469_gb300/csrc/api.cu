@@ -81,7 +81,10 @@ int read_opts(const dich_opts* o, Opts& out) {
   out.prec = o->precision;
   out.NT = o->threads;
   out.flags = o->flags;
-  if (o->trunc_eps > 0.0) out.eps = o->trunc_eps;
+  if (o->trunc_eps > 0.0) {
+    out.eps = o->trunc_eps;
+    out.eps_given = true;
+  }
   return DICH_OK;
 }
 
@@ -172,7 +175,7 @@ int build_system(double tm1, double t0, double tp1, int64_t N, int NT, int form,
 
   // truncation: geometric terms below eps (relative) are dropped; for z < 0 the Q ratios can
   // exceed 1 by up to 2/(1-|z|), which the threshold absorbs
-  double eps = o.eps;
+  double eps = (form == FORM_MIXED && !o.eps_given) ? kEpsMixed : o.eps;
   if (r.z < 0.0) eps *= 0.5 * r.omz;
   const int64_t BIG = (int64_t)1 << 62;
   const int64_t Ls = decay_len(std::fabs(r.rs), eps, BIG);

@@ -24,8 +24,13 @@ struct Opts {
   int prec = DICH_PREC_F64;
   int NT = 0;
   int flags = 0;
-  double eps = 0x1p-64;
+  double eps = 0x1p-64;     // caller's threshold, or the F64 default
+  bool eps_given = false;   // false: MIXED plans use kEpsMixed
 };
+
+// default truncation of the MIXED form: its float-float values carry about 48 bits, so terms
+// below 2^-56 of the coupling are far inside its own rounding
+constexpr double kEpsMixed = 0x1p-56;
 
 // Host construction of one system's plan record and tables.  Tables go to `tab`, or to the
 // caller's buffer `ext` of `ext_cap` doubles when it is set (no allocation in that case).

@@ -17,7 +17,8 @@
 //      where the spikes v, w exceed the truncation threshold, and a contiguous,
 //      coalesced store of the own rows.
 // Windows of a long system overlap by halo blocks on each side whose coupling into the
-// own blocks has decayed below 2^-64 (the truncation is exact to that level); on the
+// own blocks has decayed below the truncation threshold (2^-64 for FP64 plans, 2^-56 for
+// MIXED ones, whose float-float values hold about 48 bits); on the
 // general path the window instead takes the first/last values from a global scan (the FP64
 // form's beta pass leaves xp in x and its apply pass starts from there, without new sweeps).
 //

@@ -106,6 +106,14 @@ def test_halo_path_and_general_path():
     # the halo covers the decay of the coupling: |rs|^(n * halo_l) is below 2^-64
     assert abs(strong["rs"]) ** (strong["n"] * strong["halo_l"]) < 2.0 ** -64
     assert abs(strong["ib"]) ** (strong["n"] * strong["halo_r"]) < 2.0 ** -64
+    # MIXED plans truncate at 2^-56 unless the caller sets a threshold
+    mixed = plan_info((-1.2, 2.5, -0.8), 1 << 24, precision=1)
+    assert mixed["precision"] == 1
+    assert abs(mixed["rs"]) ** (mixed["n"] * mixed["halo_l"]) < 2.0 ** -56
+    assert abs(mixed["ib"]) ** (mixed["n"] * mixed["halo_r"]) < 2.0 ** -56
+    tight = plan_info((-1.2, 2.5, -0.8), 1 << 24, precision=1, trunc_eps=2.0 ** -64)
+    assert abs(tight["rs"]) ** (tight["n"] * tight["halo_l"]) < 2.0 ** -64
+    assert mixed["halo_l"] + mixed["halo_r"] < tight["halo_l"] + tight["halo_r"]
     forced = plan_info((-1.2, 2.5, -0.8), 1 << 24, flags=1)
     assert forced["path"] == 2 and forced["halo_l"] == 0
     # the 1-D Laplacian has a double root on the unit circle: no decay, general path
