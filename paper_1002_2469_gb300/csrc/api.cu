@@ -339,6 +339,7 @@ int build_system(double tm1, double t0, double tp1, int64_t N, int NT, int form,
     }
     // powers of the middle record's pair maps: (a^2)^t and (c^2)^t, t = 0..32
     const double a2 = T[p.o_bcm + BC_A] * T[p.o_bcm + BC_A], c2 = T[p.o_bcm + BC_C] * T[p.o_bcm + BC_C];
+    p.tcheap = (a2 <= 0x1p-24 && c2 <= 0x1p-24) ? 1 : 0;
     double pa = 1.0, pc = 1.0;
     for (int t = 0; t <= 32; ++t) {
       put_ff(p.o_midf + t, pa);

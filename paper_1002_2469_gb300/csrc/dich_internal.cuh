@@ -93,8 +93,10 @@ struct SysPlan {
   // MIXED form: warp-scan levels of the tree (couplings beyond 2^(lev+1) blocks are below the
   // truncation threshold), beta records from the block-end values (4 float-float entries per
   // record: middle, left table [kl], right table [kr]) and the middle record's map powers
-  // ((a^2)^t, t = 0..32, then (c^2)^t)
-  int32_t lev, o_kmf, o_klf, o_krf, o_midf, pad4_;
+  // ((a^2)^t, t = 0..32, then (c^2)^t); tcheap: both pair-map factors a^2, c^2 are at most 2^-24,
+  // so that every level of the middle-window scan multiplies by at most 2^-24 (its products need
+  // only their leading parts)
+  int32_t lev, o_kmf, o_klf, o_krf, o_midf, tcheap;
 };
 static_assert(sizeof(SysPlan) % 8 == 0, "SysPlan must be 8-byte granular");
 

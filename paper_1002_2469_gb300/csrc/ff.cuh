@@ -44,7 +44,9 @@ __device__ __forceinline__ ffv ff_make(float h, float l) {  // FastTwoSum renorm
   const float s = __fadd_rn(h, l);
   return ffv{s, __fsub_rn(l, __fsub_rn(s, h))};
 }
-__device__ __forceinline__ ffv ff_of(float2 v) { return ff_make(v.x, v.y); }
+// a (hi, lo) pair of the plan's float tables: the host splits each FP64 entry as hi = float(d),
+// lo = float(d - hi), already normalised, so the pair is taken as it is
+__device__ __forceinline__ ffv ff_of(float2 v) { return ffv{v.x, v.y}; }
 __device__ __forceinline__ ffv ff_zero() { return ffv{0.f, 0.f}; }
 __device__ __forceinline__ ffv ff_one() { return ffv{1.f, 0.f}; }
 __device__ __forceinline__ ffv ff_neg(ffv a) { return ffv{-a.h, -a.l}; }
@@ -172,6 +174,13 @@ __device__ __forceinline__ ff2 ff2_fma(const ff2& a, const ff2& b, const ff2& c)
   float2 lo = add2(add2(e, f), c.l);
   lo = fma2(a.h, b.l, fma2(a.l, b.h, lo));
   return ff2_make(s, lo);
+}
+// error-free renormalisation of a pair whose low part may exceed half an ulp of its high part
+// (TwoSum: no ordering of |h| and |l| assumed)
+__device__ __forceinline__ ff2 ff2_renorm(const ff2& a) {
+  const float2 s = add2(a.h, a.l);
+  const float2 bb = sub2(s, a.h);
+  return ff2{s, add2(sub2(a.h, sub2(s, bb)), sub2(a.l, bb))};
 }
 // per-lane choice: lane x from a if px else from b, lane y likewise
 __device__ __forceinline__ ff2 ff2_sel(bool px, bool py, const ff2& a, const ff2& b) {

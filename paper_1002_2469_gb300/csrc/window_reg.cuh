@@ -119,16 +119,34 @@ __device__ __forceinline__ void tree_mid(const float2* tf, const SysPlan* pp, in
   const ff2 p1 = ff2{make_float2(pbv.h.y, qbv.h.x), make_float2(pbv.l.y, qbv.l.x)};   // (pb_1, qb_0)
   ff2 Tv = ff2_fma(ac, p0, p1);
   const int lev = pp->lev;
+  const bool cheap = pp->tcheap != 0;
+  if (cheap) {
+    // every level multiplies by at most 2^-24: the product of the leading parts, added to the low
+    // part by one FMA, carries the level's term to within about 2^-46 of the larger of the two
+    // values (the two dropped cross products, 2^-48 each, and the FMA's rounding); one
+    // renormalisation after the levels
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    if (k >= lev) break;
-    const int dd = 1 << k;
-    const ff2 M = ff2_pair(ld(pw + dd), ld(pw + 33 + dd));
-    const float yh = __shfl_up_sync(0xffffffffu, Tv.h.x, dd), yl = __shfl_up_sync(0xffffffffu, Tv.l.x, dd);
-    const float zh = __shfl_down_sync(0xffffffffu, Tv.h.y, dd), zl = __shfl_down_sync(0xffffffffu, Tv.l.y, dd);
-    const bool up = lane >= dd, dn = lane + dd < 32;
-    const ff2 Y{make_float2(up ? yh : 0.f, dn ? zh : 0.f), make_float2(up ? yl : 0.f, dn ? zl : 0.f)};
-    Tv = ff2_fma(M, Y, Tv);
+    for (int k = 0; k < 5; ++k) {
+      if (k >= lev) break;
+      const int dd = 1 << k;
+      const float2 M = make_float2(tf[pw + dd].x, tf[pw + 33 + dd].x);
+      const float yh = __shfl_up_sync(0xffffffffu, Tv.h.x, dd);
+      const float zh = __shfl_down_sync(0xffffffffu, Tv.h.y, dd);
+      Tv.l = fma2(M, make_float2(lane >= dd ? yh : 0.f, lane + dd < 32 ? zh : 0.f), Tv.l);
+    }
+    Tv = ff2_renorm(Tv);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      if (k >= lev) break;
+      const int dd = 1 << k;
+      const ff2 M = ff2_pair(ld(pw + dd), ld(pw + 33 + dd));
+      const float yh = __shfl_up_sync(0xffffffffu, Tv.h.x, dd), yl = __shfl_up_sync(0xffffffffu, Tv.l.x, dd);
+      const float zh = __shfl_down_sync(0xffffffffu, Tv.h.y, dd), zl = __shfl_down_sync(0xffffffffu, Tv.l.y, dd);
+      const bool up = lane >= dd, dn = lane + dd < 32;
+      const ff2 Y{make_float2(up ? yh : 0.f, dn ? zh : 0.f), make_float2(up ? yl : 0.f, dn ? zl : 0.f)};
+      Tv = ff2_fma(M, Y, Tv);
+    }
   }
   if (lane == 31) swv[wid] = ff2_x(Tv);
   if (lane == 0) swv[NW + wid] = ff2_y(Tv);
@@ -147,8 +165,18 @@ __device__ __forceinline__ void tree_mid(const float2* tf, const SysPlan* pp, in
     for (int w = 0; w < wid; ++w) Aw = ff_fma(a32, Aw, swv[w]);
     for (int w = NW - 1; w > wid; --w) Bw = ff_fma(c32, Bw, swv[NW + w]);
   }
-  const ff2 E = ff2_fma(ff2_pair(ld(pw + lane), ld(pw + 33 + (31 - lane))), ff2_pair(Aw, Bw),
-                        ff2{make_float2(eh, fh), make_float2(el, fl)});
+  ff2 E;
+  if (cheap) {
+    // lane 0 of the prefix and lane 31 of the suffix take the other warps' value with factor 1 and
+    // no neighbour value: exactly (Aw, Bw); every other lane's factor is at most 2^-24
+    const float mx = tf[pw + lane].x, my = tf[pw + 33 + (31 - lane)].x;
+    E = ff2_renorm(ff2{make_float2(lane == 0 ? Aw.h : eh, lane == 31 ? Bw.h : fh),
+                       make_float2(lane == 0 ? Aw.l : __fmaf_rn(mx, Aw.h, el),
+                                   lane == 31 ? Bw.l : __fmaf_rn(my, Bw.h, fl))});
+  } else {
+    E = ff2_fma(ff2_pair(ld(pw + lane), ld(pw + 33 + (31 - lane))), ff2_pair(Aw, Bw),
+                ff2{make_float2(eh, fh), make_float2(el, fl)});
+  }
   // (A entering block 1, B beyond block 0)
   const ff2 G = ff2_fma(ac, E, p0);
   const ff2 Av{make_float2(E.h.x, G.h.x), make_float2(E.l.x, G.l.x)};   // (A_0, A_1)
@@ -342,15 +370,15 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     const ff2 zero2{f2(0.f), f2(0.f)};
     const ff2 X0 = ff2_make(H[0], L[0]), Xe = ff2_make(H[R - 1], L[R - 1]);
     // forward solve: the slot is idle until the output, so the 64 data registers wait there while
-    // the tree runs (five CTAs fit per SM instead of four).  Layout: row i of block 2t at
-    // 8 i, of block 2t+1 at 8 R + 8 i, (hi, lo) per row -- where the output of row i goes, so each
-    // row is read back before its result overwrites it.
+    // the tree runs.  Layout: the packed hi pair of row i (both blocks) at 8 i, the lo pair at
+    // 8 R + 8 i, as the packed instructions take them; the output rows 2k, 2k+1 of block 2t go to
+    // 16 k and those of block 2t+1 to 8 R + 16 k, the places of the pairs of rows 2k, 2k+1, which
+    // are read back just before.
     if constexpr (!ADJ) {
 #pragma unroll
       for (int k = 0; k < R / 2; ++k) {
-        *reinterpret_cast<float4*>(mine + 16 * k) = make_float4(H[2 * k].x, L[2 * k].x, H[2 * k + 1].x, L[2 * k + 1].x);
-        *reinterpret_cast<float4*>(mine + 8 * R + 16 * k) =
-            make_float4(H[2 * k].y, L[2 * k].y, H[2 * k + 1].y, L[2 * k + 1].y);
+        *reinterpret_cast<float4*>(mine + 16 * k) = make_float4(H[2 * k].x, H[2 * k].y, H[2 * k + 1].x, H[2 * k + 1].y);
+        *reinterpret_cast<float4*>(mine + 8 * R + 16 * k) = make_float4(L[2 * k].x, L[2 * k].y, L[2 * k + 1].x, L[2 * k + 1].y);
       }
     }
     const float2* tf = reinterpret_cast<const float2*>(tab);
@@ -484,10 +512,8 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
         const int i = 2 * k + j;
         float2 xh = H[i], xl = L[i];
         if constexpr (!ADJ) {   // back from the slot (stored before the tree)
-          const float2 s0 = *reinterpret_cast<const float2*>(mine + 8 * i);
-          const float2 s1 = *reinterpret_cast<const float2*>(mine + 8 * R + 8 * i);
-          xh = make_float2(s0.x, s1.x);
-          xl = make_float2(s0.y, s1.y);
+          xh = *reinterpret_cast<const float2*>(mine + 8 * i);
+          xl = *reinterpret_cast<const float2*>(mine + 8 * R + 8 * i);
         }
         if (own0 || own1) {
           const float4 v = tv4[i], w = tw4[R - 1 - i];
