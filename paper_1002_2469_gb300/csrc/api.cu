@@ -556,7 +556,10 @@ static int plan_geometry(dich_plan_s* p, const Opts& o, int NT, int n) {
     build_system(p->tm1, p->t0, p->tp1, p->N, NT, p->form, n, og, true, p->fwd);
     build_system(p->tp1, p->t0, p->tm1, p->N, NT, p->form, n, og, true, p->adj);
   }
-  if (p->path == PATH_HALO) {  // one window geometry for both directions
+  // the transposed system swaps the decay lengths, so its halos are the forward ones mirrored and
+  // both directions own the same blocks per window (the same tiles); otherwise one geometry for both
+  const bool mirrored = p->fwd.rec.hl == p->adj.rec.hr && p->fwd.rec.hr == p->adj.rec.hl;
+  if (p->path == PATH_HALO && !mirrored) {
     const int hl = std::max(p->fwd.rec.hl, p->adj.rec.hl), hr = std::max(p->fwd.rec.hr, p->adj.rec.hr);
     for (SysBuild* sb : {&p->fwd, &p->adj}) {
       sb->rec.hl = hl;
@@ -1327,7 +1330,9 @@ int dichotomy_batch_prepare(int64_t nsys, const int64_t* h_N, const int64_t* h_o
     }
     const int WBs = window_blocks(NTs, b->form[s]);
     bool general = (b->fwd[s].path == PATH_GENERAL || b->adj[s].path == PATH_GENERAL);
-    if (!general && (b->fwd[s].path == PATH_HALO || b->adj[s].path == PATH_HALO)) {
+    const bool mirrored = b->fwd[s].path == PATH_HALO && b->adj[s].path == PATH_HALO &&
+                          b->fwd[s].rec.hl == b->adj[s].rec.hr && b->fwd[s].rec.hr == b->adj[s].rec.hl;
+    if (!general && !mirrored && (b->fwd[s].path == PATH_HALO || b->adj[s].path == PATH_HALO)) {
       const int hl = std::max(b->fwd[s].rec.hl, b->adj[s].rec.hl);
       const int hr = std::max(b->fwd[s].rec.hr, b->adj[s].rec.hr);
       if (hl + hr > WBs / 2) {

@@ -248,12 +248,15 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
   }
 
   // ---------------------------------------------------------------- the pair in registers
-  // a[k] = rows 2k, 2k+1 of block 2t; b[k] the same of block 2t+1 (inactive blocks: zeros)
+  // a[k] = rows 2k, 2k+1 of block 2t; b[k] the same of block 2t+1.  The slot part of an inactive
+  // block (past the window's end) holds stale values: they are read without a branch, kept out of
+  // the exponent range below, and what they become is never stored (the tree takes zero block
+  // values for inactive blocks)
   double2 a[R / 2], b[R / 2];
 #pragma unroll
   for (int k = 0; k < R / 2; ++k) {
-    a[k] = act0 ? *reinterpret_cast<const double2*>(mine + 16 * k) : make_double2(0.0, 0.0);
-    b[k] = act1 ? *reinterpret_cast<const double2*>(mine + 8 * R + 16 * k) : make_double2(0.0, 0.0);
+    a[k] = *reinterpret_cast<const double2*>(mine + 16 * k);
+    b[k] = *reinterpret_cast<const double2*>(mine + 8 * R + 16 * k);
   }
 
   // window scale (largest |F| near 2^16, an exact power of two) and the fast criterion: the
@@ -262,23 +265,18 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
   bool fast, flush;   // flush: fast conversions with the window's far-smaller values set to zero
   unsigned hlo;
   {
-    unsigned hmax = 0u, hmin = 0xFFFFFFFFu;
-    if (act0) {
+    unsigned hmax0 = 0u, hmin0 = 0xFFFFFFFFu, hmax1 = 0u, hmin1 = 0xFFFFFFFFu;
 #pragma unroll
-      for (int k = 0; k < R / 2; ++k) {
-        const unsigned u = (unsigned)__double2hiint(a[k].x) & 0x7FFFFFFFu, v = (unsigned)__double2hiint(a[k].y) & 0x7FFFFFFFu;
-        hmax = __vimax3_u32(hmax, u, v);
-        hmin = __vimin3_u32(hmin, u, v);
-      }
+    for (int k = 0; k < R / 2; ++k) {
+      const unsigned u = (unsigned)__double2hiint(a[k].x) & 0x7FFFFFFFu, v = (unsigned)__double2hiint(a[k].y) & 0x7FFFFFFFu;
+      hmax0 = __vimax3_u32(hmax0, u, v);
+      hmin0 = __vimin3_u32(hmin0, u, v);
+      const unsigned y = (unsigned)__double2hiint(b[k].x) & 0x7FFFFFFFu, z = (unsigned)__double2hiint(b[k].y) & 0x7FFFFFFFu;
+      hmax1 = __vimax3_u32(hmax1, y, z);
+      hmin1 = __vimin3_u32(hmin1, y, z);
     }
-    if (act1) {
-#pragma unroll
-      for (int k = 0; k < R / 2; ++k) {
-        const unsigned u = (unsigned)__double2hiint(b[k].x) & 0x7FFFFFFFu, v = (unsigned)__double2hiint(b[k].y) & 0x7FFFFFFFu;
-        hmax = __vimax3_u32(hmax, u, v);
-        hmin = __vimin3_u32(hmin, u, v);
-      }
-    }
+    unsigned hmax = max(act0 ? hmax0 : 0u, act1 ? hmax1 : 0u);
+    unsigned hmin = min(act0 ? hmin0 : 0xFFFFFFFFu, act1 ? hmin1 : 0xFFFFFFFFu);
     hmax = __reduce_max_sync(0xffffffffu, hmax);
     hmin = __reduce_min_sync(0xffffffffu, hmin);
     if (lane == 0) {
@@ -331,14 +329,6 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
         split_sc(d0, wscale, H[i].x, L[i].x);
         split_sc(d1, wscale, H[i].y, L[i].y);
       }
-    }
-    if (!act0) {
-#pragma unroll
-      for (int i = 0; i < R; ++i) H[i].x = L[i].x = 0.f;
-    }
-    if (!act1) {
-#pragma unroll
-      for (int i = 0; i < R; ++i) H[i].y = L[i].y = 0.f;
     }
 
     // ------------------------------------------------------------ local recurrences (a1)
@@ -406,6 +396,7 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     const bool own0 = act0 && b0 >= hl && b0 < hl + nown;
     const bool own1 = act1 && b1 >= hl && b1 < hl + nown;
     if (!ADJ && !(own0 || own1)) return;
+    const bool anyown = ADJ ? (own0 || own1) : true;   // forward: every thread past here owns a block
     // x = xp + (x_{s-1} - xp(-1)) v + x_{e+1} w, in units of X (x = g X; the tree's first/last values
     // are in those units already): the coefficients are X_{s-1} - ib X_0 and X_{e+1}
     const ff2 ibx = ff2_mul(ff2_bcast(ffv{pp->ib_h, pp->ib_l}), X0);
@@ -515,7 +506,7 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
           xh = *reinterpret_cast<const float2*>(mine + 8 * i);
           xl = *reinterpret_cast<const float2*>(mine + 8 * R + 8 * i);
         }
-        if (own0 || own1) {
+        if (anyown) {
           const float4 v = tv4[i], w = tw4[R - 1 - i];
           ff_fma_acc2(cL.h, cL.l, make_float2(v.x, v.y), make_float2(v.z, v.w), xh, xl);
           ff_fma_acc2(cR.h, cR.l, make_float2(w.x, w.y), make_float2(w.z, w.w), xh, xl);
@@ -567,7 +558,7 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
           xprev = xc;
         }
       }
-      if (own0 || own1) {
+      if (anyown) {
         *reinterpret_cast<double2*>(mine + 16 * k) = make_double2(o0[0], o0[1]);
         *reinterpret_cast<double2*>(mine + 8 * R + 16 * k) = make_double2(o1[0], o1[1]);
       }
@@ -576,7 +567,7 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
         xb = nb2;
       }
     }
-    if (own0 || own1) {
+    if (anyown) {
       fence_async_smem();
       if (own0 && own1)
         bulk_store(dst + (int64_t)b0 * R, mine, 2u * R * 8u);
@@ -633,7 +624,7 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
       store_loop(std::true_type());
     else
       store_loop(std::false_type());
-    if (own0 || own1) bulk_wait_read();
+    if (anyown) bulk_wait_read();
   };
   if (fast && gfold)
     body(std::true_type(), std::true_type(), std::false_type());
