@@ -29,13 +29,18 @@ struct Recs2;
 
 constexpr int kRegRows = 16;                            // block size of the register path
 constexpr int kRegPairBytes = 2 * kRegRows * 8 + 16;    // a thread's two blocks + 16 bytes of padding
+// the middle record's float-float entries a window copies to shared memory at its start (the
+// per-system tables of a batch are then read once per CTA, not at first touch inside the tree): the
+// block-coefficient record, the four beta coefficients and the 66 pair-map powers
+constexpr int kMidRec = 0, kMidK = 10, kMidPow = 14, kMidEntries = 80;
 
 // shared memory of the register path for NT threads: the pair slots, the two spike tables, the
 // warp-boundary first/last values, the scan scratch, the exponent maxima (of the right-hand side
-// and, for the adjoint, of the forward solution) and the mbarrier
+// and, for the adjoint, of the forward solution), the middle record's entries and the mbarrier
 __host__ __device__ inline size_t window_reg_smem_bytes(int NT) {
   const size_t nw = (size_t)(NT / 32);
-  return (size_t)NT * kRegPairBytes + 2 * 16 * (size_t)kRegRows + 8 * 2 * nw + 8 * 4 * nw + 4 * 4 * nw + 16;
+  return (size_t)NT * kRegPairBytes + 2 * 16 * (size_t)kRegRows + 8 * 2 * nw + 8 * 4 * nw + 4 * 4 * nw +
+         8 * (size_t)kMidEntries + 16;
 }
 
 // ---------------------------------------------------------------- mbarrier and bulk copies (PTX)
@@ -97,19 +102,19 @@ __device__ __forceinline__ double f32_as_f64_unbiased(float f) {
 // same constants for every block (the Toeplitz saving of Sec. 3.1).  Same scans and first/last
 // values as tree2, with uniform coefficients: a thread's pair of blocks composes to the prefix map
 // A -> a^2 A + b (a beta^R_0 + beta^R_1) and the suffix map B -> c^2 B + d (c beta^L_1 + beta^L_0),
-// level d of the warp scans multiplies by (a^2)^d, (c^2)^d from the plan's power table (tf + o_midf:
-// (a^2)^t then (c^2)^t, t = 0..32), and only the plan's `lev` levels run.  A warp's totals enter the
+// level d of the warp scans multiplies by (a^2)^d, (c^2)^d from the plan's power table ((a^2)^t then
+// (c^2)^t, t = 0..32, staged in shared memory with the record), and only the plan's `lev` levels run.  A warp's totals enter the
 // following warps through (a^2)^32 (prefix) and (c^2)^32 (suffix); lane t of a warp receives the
 // prefix of the warps before it times (a^2)^t and the suffix of the warps after it times (c^2)^(31-t).
 template <int NT>
-__device__ __forceinline__ void tree_mid(const float2* tf, const SysPlan* pp, int nwin, int tid, const ff2& bL,
-                                         const ff2& bR, ffv* swv, ffv* sbd, ffv& XL0, ffv& XR0, ffv& XL1,
-                                         ffv& XR1) {
+__device__ __forceinline__ void tree_mid(const float2* tf, int rm, int pw, const SysPlan* pp, int nwin, int tid,
+                                         const ff2& bL, const ff2& bR, ffv* swv, ffv* sbd, ffv& XL0, ffv& XR0,
+                                         ffv& XL1, ffv& XR1) {
+  // tf + rm: the middle block-coefficient record, tf + pw: the pair-map powers
   constexpr int NW = NT / 32;
   const int lane = tid & 31, wid = tid >> 5;
   const int b0 = 2 * tid, b1 = b0 + 1;
-  auto ld = [&](int64_t at) { return ff_of(tf[at]); };
-  const int64_t rm = pp->o_bcmf, pw = pp->o_midf;
+  auto ld = [&](int at) { return ff_of(tf[at]); };
   const ffv a = ld(rm + BC_A), b = ld(rm + BC_B), c = ld(rm + BC_C), d = ld(rm + BC_D);
   const ff2 ac = ff2_pair(a, c);
   // lane x: the prefix (b beta^R of both blocks), lane y: the suffix (d beta^L of both blocks)
@@ -215,7 +220,8 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
   ffv* swv = sbd + 2 * NW;                                                       // 4 NW scan scratch
   unsigned* sexp = reinterpret_cast<unsigned*>(swv + 4 * NW);                    // 2 NW exponent maxima
   unsigned* sexpx = sexp + 2 * NW;                                               // the same for x
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sexpx + 2 * NW);
+  float2* mt = reinterpret_cast<float2*>(sexpx + 2 * NW);                        // middle record entries
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(mt + kMidEntries);
 
   const int b0 = 2 * tid, b1 = b0 + 1;
   const bool act0 = b0 < nwin, act1 = b1 < nwin;
@@ -233,6 +239,13 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
   if (tid == 0) mbar_arrive_expect_tx(bar, (unsigned)(nwin * R * 8));
   const unsigned mybytes = (act1 ? 2u : (act0 ? 1u : 0u)) * R * 8u;
   if (mybytes) bulk_load(mine, src + (int64_t)b0 * R, mybytes, bar);
+  if constexpr (!ADJ) {   // (the adjoint, at four CTAs per SM, reads them from the tables: measured faster)
+    const float2* tf = reinterpret_cast<const float2*>(tab);
+    for (int i = tid; i < kMidEntries; i += NT) {
+      const int64_t at = (i < kMidK) ? pp->o_bcmf + i : (i < kMidPow ? pp->o_kmf + (i - kMidK) : pp->o_midf + (i - kMidPow));
+      mt[i] = tf[at];
+    }
+  }
   if (tid < R) {   // spike tables with both lanes filled and zeros past the truncation lengths
     const float2* tf = reinterpret_cast<const float2*>(tab);
     const float2 v = (tid < pp->Lv) ? tf[pp->o_vf + tid] : make_float2(0.f, 0.f);
@@ -377,11 +390,13 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
     ff2 bL, bR;
     ffv XL0 = ff_zero(), XR0 = ff_zero(), XL1 = ff_zero(), XR1 = ff_zero();
     if (mid) {
-      const ffv k1 = ff_of(tf[pp->o_kmf]), k2 = ff_of(tf[pp->o_kmf + 1]), k3 = ff_of(tf[pp->o_kmf + 2]),
-                k4 = ff_of(tf[pp->o_kmf + 3]);
+      // the middle record's entries: staged in shared memory (forward) or in the plan's tables (adjoint)
+      const float2* me = ADJ ? tf : mt;
+      const int rm = ADJ ? pp->o_bcmf : kMidRec, pw = ADJ ? pp->o_midf : kMidPow, km = ADJ ? pp->o_kmf : kMidK;
+      const ffv k1 = ff_of(me[km]), k2 = ff_of(me[km + 1]), k3 = ff_of(me[km + 2]), k4 = ff_of(me[km + 3]);
       bL = ff2_fma(ff2_bcast(k2), Xe, ff2_mul(ff2_bcast(k1), X0));
       bR = ff2_fma(ff2_bcast(k4), Xe, ff2_mul(ff2_bcast(k3), X0));
-      tree_mid<NT>(tf, pp, nwin, tid, bL, bR, swv, sbd, XL0, XR0, XL1, XR1);
+      tree_mid<NT>(me, rm, pw, pp, nwin, tid, bL, bR, swv, sbd, XL0, XR0, XL1, XR1);
     } else {
       const Recs2 bc2 = recs2(pp, tab, P, act0, act1, mb0, mb1);
       bL = ff2_sel(act0, act1, ff2_fma(bc2.k(1), Xe, ff2_mul(bc2.k(0), X0)), zero2);
