@@ -598,21 +598,31 @@ def other_configs(D, W, oracle, stream, world, steps=10, only=None, cpu_leg=True
 
     if want("c4"):
         # C4: 10000 systems, N log-uniform in [256, 2^20]
-        N, off, tm1, t0, tp1, _ = W.uneven_c4(with_rhs=False)
-        Fd = W.device_uniform(int(N.sum()), W.SEED_RHS, "cuda")
+        N, off_tight, tm1, t0, tp1, _ = W.uneven_c4(with_rhs=False)
+        # layout: every system at a 16-byte aligned offset (even row), where the register path's bulk
+        # copies can start; the tightly packed layout (odd offsets after odd sizes) is timed beside it
+        off = W.offsets(N + (N & 1))
+        Fd = W.device_uniform(int(off[-1] + N[-1]), W.SEED_RHS, "cuda")
         xd = torch.empty_like(Fd)
-        c4 = {"unknowns": int(N.sum())}
+        c4 = {"unknowns": int(N.sum()), "layout": "systems at 16-byte aligned (even-row) offsets"}
         from paper_1002_2469_gb300 import autotune as AT
-        tb = AT.tune_batch(N, tm1, t0, tp1, precision=D.PREC_AUTO, F=Fd,
+        tb = AT.tune_batch(N, tm1, t0, tp1, precision=D.PREC_AUTO, F=Fd, offset=off,
                            candidates=[(0, 0, 0), (0, 0, D.FLAG_SMEM_PATH), (64, 16, 0), (256, 16, 0)])
         c4["autotuned"] = tb
         for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
             kw = {k: tb[k] for k in ("threads", "block_size", "flags")} if (tb and prec == D.PREC_AUTO) else {}
-            b = D.Batch(N, tm1, t0, tp1, precision=prec, **kw)
+            b = D.Batch(N, tm1, t0, tp1, offset=off, precision=prec, **kw)
             ms = _time_batch(lambda: b.solve(Fd, out=xd), max(3, steps // 2), world, stream)
             c4[name] = {"ms": round(ms, 3), "Gunknowns_s": round(N.sum() / ms / 1e6, 2),
                         "hbm_GBs": round(16 * N.sum() / ms / 1e6, 1), "windows": int(b.info["windows"]),
                         "max_rel_err_sampled": sample_err(xd, Fd, N, off, tm1, t0, tp1)}
+            if prec == D.PREC_AUTO:
+                bt = D.Batch(N, tm1, t0, tp1, offset=off_tight, precision=prec, **kw)
+                mst = _time_batch(lambda: bt.solve(Fd, out=xd), max(3, steps // 2), world, stream)
+                c4["auto_tight_layout"] = {"ms": round(mst, 3), "Gunknowns_s": round(N.sum() / mst / 1e6, 2),
+                                           "odd_offsets": int((off_tight & 1).sum()),
+                                           "note": "systems at odd offsets take the shared-memory path"}
+                del bt
         if cpu_leg:
             nh = int(np.searchsorted(np.cumsum(N), 1 << 28) + 1)      # the first ~2 GB of systems
             c4["cpu_baseline"] = batched_cpu_baseline(tm1[:nh], t0[:nh], tp1[:nh], N[:nh], off[:nh],

@@ -137,24 +137,26 @@ BATCH_CANDIDATES = [(0, 0, 0), (0, 0, D.FLAG_REG_PATH), (0, 0, D.FLAG_SMEM_PATH)
 
 
 def tune_batch(N, t_m1, t_0, t_1, precision: int = D.PREC_AUTO, candidates=None, verbose: bool = False,
-               F: "torch.Tensor | None" = None) -> dict:
+               F: "torch.Tensor | None" = None, offset=None) -> dict:
     """Time (threads, block size, flags) candidates for one batch of systems (sizes N, coefficient
-    arrays) with the library's batched solve and return the fastest as {"threads",
-    "block_size", "flags", "ms"}; (0, 0, 0) is the library's default choice.  F: the right-hand
-    sides to time with (their exponent ranges decide which conversions a window takes), else
-    seeded normal values.  Not cached: a batch's composition is its own key."""
+    arrays, row offsets: packed back to back when None) with the library's batched solve and return
+    the fastest as {"threads", "block_size", "flags", "ms"}; (0, 0, 0) is the library's default
+    choice.  F: the right-hand sides to time with (their exponent ranges decide which conversions a
+    window takes), else seeded normal values.  Not cached: a batch's composition is its own key."""
     import numpy as np
     N = np.asarray(N, dtype=np.int64)
     if F is None:
+        total = int(N.sum()) if offset is None else int((np.asarray(offset) + N).max())
         g = torch.Generator(device="cuda")
         g.manual_seed(0)
-        F = torch.randn(int(N.sum()), dtype=torch.float64, device="cuda", generator=g)
+        F = torch.randn(total, dtype=torch.float64, device="cuda", generator=g)
     x = torch.empty_like(F)
     best = None
     for cand in (candidates or BATCH_CANDIDATES):
         nt, bs, fl = (tuple(cand) + (0,))[:3]
         try:
-            b = D.Batch(N, t_m1, t_0, t_1, precision=precision, threads=nt, block_size=bs, flags=fl)
+            b = D.Batch(N, t_m1, t_0, t_1, offset=offset, precision=precision, threads=nt, block_size=bs,
+                        flags=fl)
         except D.DichotomyError:
             continue
         ms = _time(b, F, x)

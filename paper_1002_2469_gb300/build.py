@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdichotomy.so")
-SOURCES = ["api.cu", "k_f64.cu", "k_mixed.cu", "k_aux.cu", "noalloc.cu", "general.cu"]
+SOURCES = ["api.cu", "k_f64.cu", "k_mixed.cu", "k_mixed_64.cu", "k_mixed_128.cu", "k_mixed_256.cu", "k_aux.cu", "noalloc.cu",
+           "general.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

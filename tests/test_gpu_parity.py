@@ -738,6 +738,45 @@ def test_mixed_kernel_paths(D, flags):
         assert rel(X[k], oracle.thomas((-1.2, 2.5, -0.8), Fs[k])) < TOL
 
 
+def test_odd_offsets(D):
+    """Systems of a batch at odd row offsets (their rows start 8 bytes past a 16-byte boundary, where
+    the register path's bulk copies cannot start) take the shared-memory path: the same solutions, up
+    to rounding order, as the batch laid out at even offsets, and the oracle's.  A plan solve on a
+    view one element into a buffer likewise."""
+    rng = np.random.default_rng(123)
+    Ns = np.array([70001, 4099, 65536, 300000, 33, 1 << 17, 8192, 9], dtype=np.int64)
+    tm1, tp1 = -rng.uniform(0.5, 1.0, Ns.size), -rng.uniform(0.5, 1.0, Ns.size)
+    t0 = (np.abs(tm1) + np.abs(tp1)) * rng.uniform(1.05, 2.0, Ns.size)
+    tight = np.concatenate([[0], np.cumsum(Ns)[:-1]]).astype(np.int64)   # odd offsets from the second on
+    Ne = Ns + (Ns & 1)
+    even = np.concatenate([[0], np.cumsum(Ne)[:-1]]).astype(np.int64)
+    assert (tight & 1).any() and not (even & 1).any()
+    Fs = [rng.uniform(-1, 1, int(n)) for n in Ns]
+    out = {}
+    for name, off in (("tight", tight), ("even", even)):
+        tot = int(off[-1] + Ns[-1])
+        F = np.zeros(tot + 1)
+        for s_, o in enumerate(off):
+            F[int(o):int(o) + int(Ns[s_])] = Fs[s_]
+        b = D.Batch(Ns, tm1, t0, tp1, offset=off, precision=1, flags=32)
+        x = b.solve(torch.from_numpy(F).cuda()).cpu().numpy()
+        assert b.status() == 0
+        out[name] = [x[int(o):int(o) + int(n)] for o, n in zip(off, Ns)]
+    for s_ in range(Ns.size):
+        assert rel(out["tight"][s_], out["even"][s_]) < 1e-13, s_
+        assert rel(out["tight"][s_], oracle.thomas((tm1[s_], t0[s_], tp1[s_]), Fs[s_])) < TOL, s_
+    t, N = (-1.2, 2.5, -0.8), 200000
+    F = rng.standard_normal(N)
+    buf = torch.zeros(N + 1, dtype=torch.float64, device="cuda")
+    xbuf = torch.zeros(N + 1, dtype=torch.float64, device="cuda")
+    buf[1:] = torch.from_numpy(F).cuda()
+    plan = D.Plan(*t, N, precision=1, flags=32)
+    plan.solve(buf[1:], out=xbuf[1:])
+    assert plan.status() == 0
+    assert xbuf[0].item() == 0.0
+    assert rel(xbuf[1:].cpu().numpy(), oracle.thomas(t, F)) < TOL
+
+
 @pytest.mark.parametrize("flags", [32, 64])
 def test_windows_of_wide_dynamic_range(D, flags):
     """Right-hand sides whose windows span hundreds of decades with exact zeros (the spectrum of a
