@@ -333,7 +333,7 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         only = None if args.only is None else set(args.only.split(","))
         others = other_configs(D, W, oracle, stream, world, steps=max(5, min(args.steps, 20)), only=only,
-                               cpu_leg=(rank == 0 and not args.no_cpu_baseline))
+                               cpu_leg=(rank == 0 and not args.no_cpu_baseline), c4_systems=args.c4_systems)
 
     if rank != 0:
         return
@@ -397,7 +397,9 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
 
 
-def _time_batch(solve, steps, world, stream):
+def _time_batch(solve, steps, world, stream, label=None):
+    """Device time per call of solve() over `steps` calls after 3 warm-up calls.  label: the name of
+    an NVTX range around the timed calls (a profiler can select their kernels by it)."""
     import torch
     for _ in range(3):
         solve()
@@ -405,10 +407,14 @@ def _time_batch(solve, steps, world, stream):
     barrier(world)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    if label:
+        torch.cuda.nvtx.range_push(label)
     e0.record(stream)
     for _ in range(steps):
         solve()
     e1.record(stream)
+    if label:
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     return max_over_ranks(e0.elapsed_time(e1), world) / steps
 
@@ -489,7 +495,7 @@ def cusparse_comparator(W, oracle, stream, steps):
 OTHER_CONFIGS = ("cusparse", "c1", "c2w", "c3", "c4", "c5", "f3", "f3n", "f4", "table1")
 
 
-def other_configs(D, W, oracle, stream, world, steps=10, only=None, cpu_leg=True):
+def other_configs(D, W, oracle, stream, world, steps=10, only=None, cpu_leg=True, c4_systems=0):
     """C1 (latency), the weakly dominant C2 variant, C3 (2-D Poisson modes), C4 (uneven series),
     C5 (adjoint), the rows beyond the hot path and the paper's Table 1 run: time and Gunknowns/s
     per form, with the error against the oracle (on a sample of systems for the batches).
@@ -586,7 +592,7 @@ def other_configs(D, W, oracle, stream, world, steps=10, only=None, cpu_leg=True
         for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
             kw = {k: tb[k] for k in ("threads", "block_size", "flags")} if (tb and prec == D.PREC_AUTO) else {}
             b = D.Batch(N, tm1, t0, tp1, precision=prec, **kw)
-            ms = _time_batch(lambda: b.solve(Fd, out=xd), steps, world, stream)
+            ms = _time_batch(lambda: b.solve(Fd, out=xd), steps, world, stream, label=f"c3_{name}")
             forms = b.info["form"]
             c3[name] = {"ms": round(ms, 4), "Gunknowns_s": round(N.sum() / ms / 1e6, 2),
                         "hbm_GBs": round(16 * N.sum() / ms / 1e6, 1), "mixed_systems": int(forms.sum()),
@@ -599,6 +605,9 @@ def other_configs(D, W, oracle, stream, world, steps=10, only=None, cpu_leg=True
     if want("c4"):
         # C4: 10000 systems, N log-uniform in [256, 2^20]
         N, off_tight, tm1, t0, tp1, _ = W.uneven_c4(with_rhs=False)
+        if c4_systems:   # the first systems only (a smaller case of the same series, for profiling)
+            N, off_tight, tm1, t0, tp1 = N[:c4_systems], off_tight[:c4_systems], tm1[:c4_systems], \
+                t0[:c4_systems], tp1[:c4_systems]
         # layout: every system at a 16-byte aligned offset (even row), where the register path's bulk
         # copies can start; the tightly packed layout (odd offsets after odd sizes) is timed beside it
         off = W.offsets(N + (N & 1))
@@ -612,7 +621,7 @@ def other_configs(D, W, oracle, stream, world, steps=10, only=None, cpu_leg=True
         for name, prec in (("auto", D.PREC_AUTO), ("fp64_plain", D.PREC_F64)):
             kw = {k: tb[k] for k in ("threads", "block_size", "flags")} if (tb and prec == D.PREC_AUTO) else {}
             b = D.Batch(N, tm1, t0, tp1, offset=off, precision=prec, **kw)
-            ms = _time_batch(lambda: b.solve(Fd, out=xd), max(3, steps // 2), world, stream)
+            ms = _time_batch(lambda: b.solve(Fd, out=xd), max(3, steps // 2), world, stream, label=f"c4_{name}")
             c4[name] = {"ms": round(ms, 3), "Gunknowns_s": round(N.sum() / ms / 1e6, 2),
                         "hbm_GBs": round(16 * N.sum() / ms / 1e6, 1), "windows": int(b.info["windows"]),
                         "max_rel_err_sampled": sample_err(xd, Fd, N, off, tm1, t0, tp1)}
@@ -646,7 +655,7 @@ def other_configs(D, W, oracle, stream, world, steps=10, only=None, cpu_leg=True
             def step():
                 b.solve(Fd, out=xd)
                 D.dichotomy_adjoint_batched(b.handle, wd, xd, gF, gt)
-            ms = _time_batch(step, steps, world, stream)
+            ms = _time_batch(step, steps, world, stream, label=f"c5_{name}")
             s_ = 7
             o, n = int(off[s_]), int(Ns[s_])
             tt = (tm1[s_], t0[s_], tp1[s_])
@@ -830,6 +839,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-configs", action="store_true")
+    ap.add_argument("--c4-systems", type=int, default=0,
+                    help="time only the first K systems of the uneven series (a smaller case for profiling)")
     ap.add_argument("--geometry", default=None,
                     help="threads,block_size of the headline solve instead of the autotuner's choice")
     ap.add_argument("--only", default=None,
