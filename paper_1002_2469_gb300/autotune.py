@@ -60,7 +60,7 @@ def _save(d):
     os.replace(tmp, CACHE)
 
 
-def _time(plan, F, x, reps=5, inner=5):
+def _time(plan, F, x, reps=7, inner=10):
     """Median over `reps` of the mean device time (ms) of `inner` solves of a Plan or Batch."""
     for _ in range(3):
         plan.solve(F, out=x)

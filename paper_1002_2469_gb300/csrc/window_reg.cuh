@@ -503,7 +503,11 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
       }
     }
 
-#pragma unroll
+    // the forward solve reads its rows back from the slot, so its loop need not be unrolled all the
+    // way (half the code: measured 2.8% faster, the instruction cache then missing less); the
+    // adjoint's rows are in registers
+    constexpr int KUNROLL = ADJ ? R / 2 : 4;
+#pragma unroll KUNROLL
     for (int k = 0; k < R / 2; ++k) {
       double o0[2], o1[2];
       double2 na{0.0, 0.0}, nb2{0.0, 0.0};   // the next pair (x of rows 2k+2, 2k+3), read before the
@@ -516,8 +520,11 @@ __device__ __forceinline__ void window_reg(const WinArgs& A, const SysPlan* pp, 
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int i = 2 * k + j;
-        float2 xh = H[i], xl = L[i];
-        if constexpr (!ADJ) {   // back from the slot (stored before the tree)
+        float2 xh, xl;
+        if constexpr (ADJ) {
+          xh = H[i];
+          xl = L[i];
+        } else {   // back from the slot (stored before the tree)
           xh = *reinterpret_cast<const float2*>(mine + 8 * i);
           xl = *reinterpret_cast<const float2*>(mine + 8 * R + 8 * i);
         }
