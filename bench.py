@@ -225,24 +225,26 @@ def whole_job_value(units_per_rank: int, ms_per_rank: float, world: int) -> floa
 
 
 def time_solves(plan, F, x, steps, warmup, world, events_stream):
-    """Device time of `steps` solves (CUDA events on the launching stream, barrier + sync
-    on both sides, max over ranks).  Returns (total ms, per-launch ms list)."""
+    """Device time of `steps` back-to-back solves (two CUDA events on the launching stream around
+    them, barrier + sync on both sides, max over ranks).  Returns (total ms, [average ms per
+    launch]): a solve of this plan is one kernel launch, and no event sits between two launches
+    (an event between them would keep each launch from starting while the previous one drains)."""
     import torch
     for _ in range(warmup):
         plan.solve(F, out=x)
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-    ev[0].record(events_stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(events_stream)
     for k in range(steps):
         plan.solve(F, out=x)
-        ev[k + 1].record(events_stream)
+    e1.record(events_stream)
     torch.cuda.synchronize()
     barrier(world)
-    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
-    total = ev[0].elapsed_time(ev[steps])
-    return max_over_ranks(total, world), per
+    total = e0.elapsed_time(e1)
+    return max_over_ranks(total, world), [total / steps]
 
 
 def run_gpu(args):
