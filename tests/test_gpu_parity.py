@@ -738,6 +738,33 @@ def test_mixed_kernel_paths(D, flags):
         assert rel(X[k], oracle.thomas((-1.2, 2.5, -0.8), Fs[k])) < TOL
 
 
+@pytest.mark.parametrize("rs", [0.5, 0.5922, 0.5946, 0.5960, 0.62])
+@pytest.mark.parametrize("shape", ["random", "one_block", "alternating_scale"])
+def test_tree_levels_either_side_of_the_cheap_bound(D, rs, shape):
+    """Middle-window trees take their levels by one FMA on the low part when both pair-map factors
+    are at most 2^-24 (about |rs|, |ib| <= 0.5946 for 16-row blocks) and by full float-float products
+    otherwise: systems on both sides of the bound, with right-hand sides that put all of a window's
+    weight in one block (the other blocks' scan values start from zero) or alternate between
+    magnitudes 1e-30 and 1, against the oracle."""
+    # T = tridiag{-rs, 1 + rs ib, -ib} = (1 - rs E^-1)(1 - ib E) on bi-infinite sequences: the roots
+    # of t_1 r^2 + t_0 r + t_-1 are rs and 1 / ib
+    ib = 0.7 * rs
+    t = (-rs, 1.0 + rs * ib, -ib)
+    N = 1 << 18
+    rng = np.random.default_rng(int(rs * 1e4))
+    if shape == "random":
+        F = rng.standard_normal(N)
+    elif shape == "one_block":
+        F = np.zeros(N)
+        for w0 in range(0, N, 4096):
+            F[w0 + 2000:w0 + 2016] = rng.standard_normal(16)
+    else:
+        F = rng.standard_normal(N) * np.where((np.arange(N) // 16) % 2 == 0, 1.0, 1e-30)
+    x, info = gpu_solve(D, t, F, precision=1, flags=32)
+    assert info["path"] == 1, info
+    assert rel(x, oracle.thomas(t, F)) < TOL, (rs, shape)
+
+
 def test_odd_offsets(D):
     """Systems of a batch at odd row offsets (their rows start 8 bytes past a 16-byte boundary, where
     the register path's bulk copies cannot start) take the shared-memory path: the same solutions, up
